@@ -1,0 +1,196 @@
+"""Planted mistakes in the oracle (on the CPU) must be caught by its pins.
+
+Each case monkeypatches one plausible slip into oracle code -- a dropped term, a wrong
+sign, a wrong scale, a swapped axis -- and checks that at least one of the pin checks
+below fails, while all of them pass on the unmodified oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fd, iteration as it, multigrid as mg
+from paper_2308_11469_gb300 import inputs
+
+
+def _rand_c(rng, shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def pin_quadratic():
+    n, h = 7, 0.13
+    xs = inputs.node_coords(3, n, h)
+    L = fd.apply_laplacian(xs[0] ** 2 + 3 * xs[1] ** 2 - xs[2] ** 2, h)
+    return np.allclose(L, 6.0, atol=1e-10)
+
+
+def pin_plane_wave():
+    D, n, k = 2, 31, 3.0
+    h = 1.0 / (n + 1)
+    d = (0.6, 0.8)
+    kap = fd.discrete_wavenumber(k, h, d)
+    w = inputs.plane_wave(D, n, h, kap, d)
+    u = fd.solve_exact_splu(np.zeros((n, n), complex), w, h, k)
+    return (np.max(np.abs(u - w)) < 1e-12
+            and np.max(np.abs(fd.apply_helmholtz(w, h, k))) < 1e-9 * k * k)
+
+
+def pin_hand_relres():
+    # one interior node, worked by hand: relres_N = 16^-N, u^(1) = (11 + 10i)/16
+    f = np.full((1, 1), 1 + 2j)
+    g = np.zeros((3, 3), complex)
+    g[1, 0], g[1, 2], g[0, 1], g[2, 1] = 1, 2j, -1, 3 + 1j
+    res = it.paper_iteration(f, g, 0.5, 1.0, tol=1e-300, max_outer=3, keep_iterates=True)
+    return (abs(res.iterates[1][1, 1] - (11 + 10j) / 16) < 1e-15
+            and np.allclose(res.relres, [1, 1 / 16, 1 / 256, 1 / 4096], rtol=1e-14, atol=0))
+
+
+def pin_partial_sums():
+    D, n = 2, 5
+    h = 1.0 / (n + 1)
+    rng = np.random.default_rng(3)
+    f = _rand_c(rng, (n, n))
+    g = _rand_c(rng, (n + 2, n + 2))
+    k = 0.8 * math.sqrt(2 * 4 / h ** 2 * math.sin(math.pi / (2 * (n + 1))) ** 2)
+    # the matrix series built from scratch here (no oracle helper)
+    A = np.zeros((n * n, n * n))
+    for j in range(n):
+        for i in range(n):
+            p = j * n + i
+            A[p, p] = -4 / h ** 2
+            for jj, ii in [(j, i - 1), (j, i + 1), (j - 1, i), (j + 1, i)]:
+                if 0 <= ii < n and 0 <= jj < n:
+                    A[p, jj * n + ii] = 1 / h ** 2
+    b = f.copy()
+    b[:, 0] -= g[1:-1, 0] / h ** 2
+    b[:, -1] -= g[1:-1, -1] / h ** 2
+    b[0, :] -= g[0, 1:-1] / h ** 2
+    b[-1, :] -= g[-1, 1:-1] / h ** 2
+    Ainv = np.linalg.inv(A)
+    term = Ainv @ b.reshape(-1)
+    partial = np.zeros_like(term)
+    res = it.paper_iteration(f, g, h, k, tol=1e-300, max_outer=6, keep_iterates=True)
+    for N in range(1, 7):
+        partial = partial + term
+        term = -(k * k) * (Ainv @ term)
+        if np.linalg.norm(fd.interior(res.iterates[N]).reshape(-1) - partial) > 1e-12 * np.linalg.norm(partial):
+            return False
+    return True
+
+
+def pin_sine_eigen():
+    n = 9
+    h = 1.0 / (n + 1)
+    s = fd.sine_mode(2, n, (2, 5))
+    lam = (4 / h ** 2) * (math.sin(2 * math.pi / 20) ** 2 + math.sin(5 * math.pi / 20) ** 2)
+    return np.allclose(fd.apply_laplacian(fd.padded_from(s), h), -lam * s, atol=1e-9 * lam)
+
+
+def pin_vcycle():
+    n = 31
+    h = 1.0 / (n + 1)
+    r = _rand_c(np.random.default_rng(4), (n, n))
+    exact = fd.dst_poisson(r, h)
+    E = np.zeros((n + 2, n + 2), complex)
+    for _ in range(14):
+        mg.vcycle(E, r, h)
+    return np.linalg.norm(fd.interior(E) - exact) < 1e-10 * np.linalg.norm(exact)
+
+
+def pin_kmax():
+    return abs(fd.k_max(2, 2 ** 12 - 1, 2.0 ** -12) - math.pi * math.sqrt(2)) < 1e-6
+
+
+PINS = [pin_quadratic, pin_plane_wave, pin_hand_relres, pin_partial_sums, pin_sine_eigen,
+        pin_vcycle, pin_kmax]
+
+
+def test_pins_pass_on_the_oracle():
+    assert all(p() for p in PINS)
+
+
+def _laplacian_no_minus_two(U, h):
+    c = fd.interior(U)
+    out = np.zeros(c.shape, dtype=np.result_type(U.dtype, np.float64))
+    for a in range(U.ndim):
+        out += (fd._shift(U, a, +1) - c + fd._shift(U, a, -1))
+    return out / (h * h)
+
+
+def _laplacian_one_axis_dropped(U, h):
+    c = fd.interior(U)
+    out = np.zeros(c.shape, dtype=np.result_type(U.dtype, np.float64))
+    for a in range(U.ndim - 1):
+        out += (fd._shift(U, a, +1) - 2 * c + fd._shift(U, a, -1))
+    return out / (h * h)
+
+
+def _helmholtz_wrong_sign(U, h, k):
+    return fd.apply_laplacian(U, h) - (k * k) * fd.interior(U)
+
+
+def _lifting_wrong_sign(f, g, h):
+    return f + fd.apply_laplacian(fd.ring_only(g), h)
+
+
+def _lambda_min_wrong_scale(D, n, h):
+    return D * (4.0 / (h * h)) * math.sin(math.pi / (n + 1)) ** 2
+
+
+def _eigenvalues_off_by_one(n, h):
+    m = np.arange(0, n, dtype=np.float64)
+    return (4.0 / (h * h)) * np.sin(m * math.pi / (2.0 * (n + 1))) ** 2
+
+
+def _restrict_unweighted(rf):
+    D = rf.ndim
+    return rf[(slice(1, None, 2),) * D].copy()
+
+
+def _half_sweep_wrong_h(E, r, h, color):
+    D = E.ndim
+    n = E.shape[0] - 2
+    nbr = np.zeros(r.shape, dtype=E.dtype)
+    for a in range(D):
+        nbr = nbr + fd._shift(E, a, +1) + fd._shift(E, a, -1)
+    new = (nbr - h * r) / (2.0 * D)
+    mask = mg.color_mask(D, n, color)
+    E[(slice(1, -1),) * D][mask] = new[mask]
+
+
+MUTATIONS = [
+    (fd, "apply_laplacian", _laplacian_no_minus_two),
+    (fd, "apply_laplacian", _laplacian_one_axis_dropped),
+    (fd, "apply_helmholtz", _helmholtz_wrong_sign),
+    (fd, "lifted_rhs", _lifting_wrong_sign),
+    (fd, "lambda_min", _lambda_min_wrong_scale),
+    (fd, "dirichlet_eigenvalues_1d", _eigenvalues_off_by_one),
+    (mg, "restrict_fw", _restrict_unweighted),
+    (mg, "rbgs_half_sweep", _half_sweep_wrong_h),
+]
+
+
+@pytest.mark.parametrize("mod,name,bad", MUTATIONS, ids=[m[2].__name__ for m in MUTATIONS])
+def test_planted_mistake_is_caught(monkeypatch, mod, name, bad):
+    monkeypatch.setattr(mod, name, bad)
+    results = []
+    for p in PINS:
+        try:
+            results.append(bool(p()))
+        except Exception:
+            results.append(False)
+    assert not all(results), f"mutation {bad.__name__} escaped every pin"
+
+
+def test_planted_iteration_sign_is_caught(monkeypatch):
+    # v_n = Delta^{-1}(+k^2 v_{n-1}) instead of -k^2: the iterates stop matching the series
+    orig = it.paper_iteration
+
+    def wrong(f, g, h, k, **kw):
+        return orig(f, g, h, 1j * k, **kw)   # k^2 -> -k^2 everywhere in the recursion
+    monkeypatch.setattr(it, "paper_iteration", wrong)
+    try:
+        ok = pin_partial_sums()
+    except Exception:
+        ok = False
+    assert not ok
