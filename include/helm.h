@@ -1,0 +1,173 @@
+/*
+ * helm.h -- C ABI of the GB300 finite-difference Poisson-iteration solver for the
+ * Dirichlet-cavity Helmholtz problem.
+ *
+ * Problem (Section 2.2, the cavity problem Eq. (2.4) with damping p = 0 and a wall that
+ * is Dirichlet everywhere; discretised as in Section 2.4):
+ *
+ *     (Delta_h + k^2) u = f on the n^D interior nodes of a cube of side (n+1) h,
+ *     u = g on the wall nodes,
+ *
+ * with Delta_h the 5-point (D = 2) / 7-point (D = 3) second-order Laplacian.  The solver
+ * runs the paper's recasting of Helmholtz as a sequence of Poisson problems (Eq. (1.4)
+ * and the cavity iteration Eq. (2.6)-(2.8) with alpha = k^2): each outer step solves
+ *
+ *     Delta_h e_n = r_n := f - (Delta_h + k^2) u_n,   e_n = 0 on the wall,
+ *     u_{n+1} = u_n + e_n,
+ *
+ * which is Delta_h u_{n+1} = f - k^2 u_n; with exact inner solves e_n = v_n + i w_n of the
+ * paper and u_N is the N-th partial sum of its series.  The inner Poisson solve is
+ * geometric multigrid (red-black Gauss-Seidel, full weighting, multilinear
+ * prolongation, exact coarsest solve), run in complex64 (HELM_PREC_MIXED: FP32 V-cycles,
+ * FP64 residual and solution, i.e. iterative refinement) or complex128 (HELM_PREC_FP64).
+ * The iteration converges iff k^2 < lambda_min(-Delta_h) (Section 2.4: the iteration
+ * matrix is G = -k^2 Delta_h^{-1}, the series converges iff its spectral radius is < 1).
+ *
+ * Memory layouts (all device pointers, the caller owns them):
+ *   complex128 = interleaved {re, im} doubles (the layout of torch.complex128);
+ *   complex64  = interleaved {re, im} floats  (torch.complex64);
+ *   an "interior" array holds n^D values, a "padded" array (n+2)^D values; index order
+ *   [z][y][x] with x fastest; padded node (i, j[, l]) sits at x = i h.
+ * Every pointer must be 16-byte aligned and device memory of the plan's device.
+ *
+ * Errors: every entry point returns a helm_status; nothing throws, exits or traps.
+ * Negative values are errors (the call had no effect on caller memory unless stated),
+ * non-negative values are outcomes of a solve.
+ *
+ * Threading: a plan / batch may be used by one host thread at a time.  All work runs on
+ * the CUDA stream given at creation.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HELM_API __attribute__((visibility("default")))
+#else
+#define HELM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HELM_CONVERGED = 0,      /* relres <= tol                                        */
+    HELM_OK = 0,
+    HELM_MAXITER = 1,        /* max_outer steps without convergence                 */
+    HELM_DIVERGED = 2,       /* relres > 1e4, or >= 20 steps and 10 non-decreasing  */
+    HELM_EINVAL = -1,        /* bad argument (null / misaligned pointer, bad size)  */
+    HELM_ENOMEM = -2,        /* device allocation failed / batch memory cap reached */
+    HELM_ECUDA = -3,         /* a CUDA runtime call failed                          */
+    HELM_ENONFINITE = -4,    /* NaN or Inf met in the residual                      */
+    HELM_ETIMEOUT = -5,      /* a bounded wait ran out                              */
+    HELM_EUNSUPPORTED = -6   /* valid request this build does not handle            */
+} helm_status;
+
+typedef enum { HELM_BC_DIRICHLET = 0 } helm_bc;
+typedef enum { HELM_PREC_FP64 = 0, HELM_PREC_MIXED = 1 } helm_prec;
+
+typedef struct helm_plan helm_plan;
+typedef struct helm_batch helm_batch;
+
+/* Human-readable name of a status code (static string, never NULL). */
+HELM_API const char* helm_status_str(int status);
+
+/* Text of the last CUDA error this library met on the calling thread ("" if none). */
+HELM_API const char* helm_last_error(void);
+
+/* Number of CUDA kernel launches this library has issued from the calling process
+ * (graph replays count every kernel node they run).  Used to report launch counts. */
+HELM_API uint64_t helm_launch_count(void);
+
+/*
+ * Plan: one cavity geometry (D, n, h), wave number k and precision, with its multigrid
+ * hierarchy and workspace allocated on the current CUDA device.
+ *   ndim      2 or 3.
+ *   n         ndim entries, all equal to 2^m - 1 with 1 <= m <= 15 (2D) / 11 (3D);
+ *             unequal entries -> HELM_EUNSUPPORTED.
+ *   h         grid spacing > 0 (the unit cube has h = 1/(n+1)).
+ *   k         wave number >= 0 (any value is accepted; k >= k_max diverges).
+ *   bc        HELM_BC_DIRICHLET.
+ *   prec      HELM_PREC_FP64 or HELM_PREC_MIXED.
+ *   cuda_stream  cudaStream_t (NULL = the legacy default stream).
+ * On success *out owns device memory until helm_plan_destroy.
+ */
+HELM_API helm_status helm_plan_create(helm_plan** out, int ndim, const int* n, double h, double k,
+                             int bc, int prec, void* cuda_stream);
+HELM_API helm_status helm_plan_destroy(helm_plan* plan);
+
+/* Closed forms of the plan (Section 2.4, Dirichlet case): lambda_min of -Delta_h,
+ * k_max = sqrt(lambda_min), rho = k^2 / lambda_min; and the workspace bytes owned.
+ * Any output pointer may be NULL. */
+HELM_API helm_status helm_plan_info(const helm_plan* plan, double* lambda_min, double* k_max,
+                           double* rho_pred, size_t* workspace_bytes);
+
+/* Inner-solve schedule: V(nu1, nu2) cycles, `cycles` V-cycles per outer step.
+ * Defaults: 2D (2, 2, 1), 3D (2, 2, 1).  nu1, nu2 in [0, 8] with nu1 + nu2 >= 1,
+ * cycles in [1, 16]. */
+HELM_API helm_status helm_plan_set_cycle(helm_plan* plan, int nu1, int nu2, int cycles);
+
+/*
+ * Solve (Delta_h + k^2) u = f, u = g on the wall, by the outer Poisson iteration.
+ *   f         interior complex128, n^D (device).
+ *   g         padded complex128, (n+2)^D (device); only its wall ring is read.
+ *   u         padded complex128, (n+2)^D (device).  In: the interior is the starting
+ *             iterate u_0 (zeros = the paper's start).  Out: the last iterate u_iters,
+ *             its wall ring overwritten with g.
+ *   tol       stop when relres_N = ||r_N||_2 / ||r_0||_2 <= tol (interior 2-norms).
+ *   max_outer >= 0 outer steps at most.
+ *   iters     (host, may be NULL) number of outer steps performed.
+ *   res_hist  (host, may be NULL) relres_0 .. relres_iters (iters + 1 doubles; the
+ *             caller provides max_outer + 1).  relres_0 = 1 unless r_0 = 0.
+ * Returns HELM_CONVERGED / HELM_MAXITER / HELM_DIVERGED / HELM_ENONFINITE, or an error.
+ * Synchronous: returns after the stream has finished the solve.
+ */
+HELM_API helm_status helm_solve(helm_plan* plan, const void* f, const void* g, void* u, double tol,
+                       int max_outer, int* iters, double* res_hist);
+
+/* As helm_solve, and also returns the increment sup-norms ||e_N||_inf, N = 0..iters-1
+ * (Section 3 proposes truncating on the size of successive iterates).  einf_hist may
+ * be NULL. */
+HELM_API helm_status helm_solve_ex(helm_plan* plan, const void* f, const void* g, void* u, double tol,
+                          int max_outer, int* iters, double* res_hist, double* einf_hist);
+
+/*
+ * One multigrid V(nu1, nu2)-cycle for Delta_h e = rhs with e = 0 on the wall, in the
+ * plan's inner precision (complex64 for HELM_PREC_MIXED, complex128 for HELM_PREC_FP64).
+ *   rhs  interior n^D (device), read.
+ *   e    interior n^D (device), in: initial guess, out: after one cycle.
+ * The inner solver of each outer step, exposed for standalone use.  Synchronous.
+ */
+HELM_API helm_status poisson_vcycle(helm_plan* plan, const void* rhs, void* e, int nu1, int nu2);
+
+/*
+ * Batch / serving: many independent solves of uneven size, dimension and k advanced
+ * together, each outer step of all active instances in one launch per kernel.
+ *   hbm_cap_bytes  device-memory cap for the instances' workspace (0 = no cap).
+ * helm_batch_submit copies the plan's parameters (the plan may be destroyed after) and
+ * reserves workspace; HELM_ENOMEM when the cap would be exceeded (retry after others
+ * finish).  f, g, u follow helm_solve and must stay valid until the solve is polled done.
+ * helm_batch_step runs up to `max_steps` outer steps (0 = until every active solve has
+ * finished).  helm_batch_poll reports a solve; once it returns done = 1 the result is in
+ * u (synchronised), the histories are copied (res_hist may be NULL), and the instance's
+ * workspace is released.
+ */
+HELM_API helm_status helm_batch_create(helm_batch** out, size_t hbm_cap_bytes, void* cuda_stream);
+HELM_API helm_status helm_batch_destroy(helm_batch* batch);
+HELM_API helm_status helm_batch_submit(helm_batch* batch, const helm_plan* plan, const void* f,
+                              const void* g, void* u, double tol, int max_outer,
+                              uint64_t* ticket);
+HELM_API helm_status helm_batch_step(helm_batch* batch, int max_steps);
+HELM_API helm_status helm_batch_poll(helm_batch* batch, uint64_t ticket, int* done, int* status,
+                            int* iters, double* res_hist);
+/* Active (submitted, not yet polled done) solves and the workspace bytes they hold. */
+HELM_API helm_status helm_batch_info(const helm_batch* batch, int* active, size_t* bytes_in_use);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELM_H */

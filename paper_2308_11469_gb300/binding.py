@@ -1,0 +1,270 @@
+"""ctypes binding of the C ABI in include/helm.h (argument marshalling only).
+
+Every function of the ABI appears here under the same name.  Arrays are torch tensors on
+the plan's CUDA device (PyTorch supplies device memory and streams); each call checks
+dtype / shape / contiguity, passes raw pointers, and raises ``HelmError`` on a negative
+status.  All arithmetic runs in the CUDA library: there is no fallback, and loading
+fails loudly when ``libhelm.so`` has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libhelm.so")
+
+HELM_CONVERGED = 0
+HELM_MAXITER = 1
+HELM_DIVERGED = 2
+HELM_EINVAL = -1
+HELM_ENOMEM = -2
+HELM_ECUDA = -3
+HELM_ENONFINITE = -4
+HELM_ETIMEOUT = -5
+HELM_EUNSUPPORTED = -6
+HELM_BC_DIRICHLET = 0
+HELM_PREC_FP64 = 0
+HELM_PREC_MIXED = 1
+
+# every symbol the header declares, with (restype, argtypes)
+_vp = C.c_void_p
+_SIGS = {
+    "helm_status_str": (C.c_char_p, [C.c_int]),
+    "helm_last_error": (C.c_char_p, []),
+    "helm_launch_count": (C.c_uint64, []),
+    "helm_plan_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(C.c_int), C.c_double,
+                                   C.c_double, C.c_int, C.c_int, _vp]),
+    "helm_plan_destroy": (C.c_int, [_vp]),
+    "helm_plan_info": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_size_t)]),
+    "helm_plan_set_cycle": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
+    "helm_solve": (C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int),
+                             C.POINTER(C.c_double)]),
+    "helm_solve_ex": (C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int),
+                                C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "poisson_vcycle": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int]),
+    "helm_batch_create": (C.c_int, [C.POINTER(_vp), C.c_size_t, _vp]),
+    "helm_batch_destroy": (C.c_int, [_vp]),
+    "helm_batch_submit": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_double, C.c_int,
+                                    C.POINTER(C.c_uint64)]),
+    "helm_batch_step": (C.c_int, [_vp, C.c_int]),
+    "helm_batch_poll": (C.c_int, [_vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "helm_batch_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_size_t)]),
+}
+
+_lib = None
+
+
+class HelmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        detail = ""
+        if _lib is not None:
+            detail = _lib.helm_last_error().decode()
+        super().__init__(f"{where}: {status_name(status)}" + (f" ({detail})" if detail else ""))
+
+
+def load(path: str = LIB_PATH):
+    """Load libhelm.so and declare the ABI.  Raises if the library has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build the CUDA library first "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_name(s: int) -> str:
+    if _lib is None:
+        return str(s)
+    return _lib.helm_status_str(int(s)).decode()
+
+
+def _check(status: int, where: str) -> int:
+    if status < 0 and status != HELM_ENONFINITE:
+        raise HelmError(status, where)
+    return status
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, dtype, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def helm_status_str(status: int) -> str:
+    return load().helm_status_str(int(status)).decode()
+
+
+def helm_last_error() -> str:
+    return load().helm_last_error().decode()
+
+
+def helm_launch_count() -> int:
+    return int(load().helm_launch_count())
+
+
+class _Plan:
+    """Handle returned by helm_plan_create (owns the C plan)."""
+
+    def __init__(self, handle, D, n, h, k, prec):
+        self.handle = handle
+        self.D, self.n, self.h, self.k, self.prec = D, n, h, k, prec
+
+    @property
+    def inner_dtype(self):
+        import torch
+        return torch.complex128 if self.prec == HELM_PREC_FP64 else torch.complex64
+
+    def __del__(self):
+        if self.handle is not None and _lib is not None:
+            _lib.helm_plan_destroy(self.handle)
+            self.handle = None
+
+
+def helm_plan_create(ndim: int, n: int, h: float, k: float, bc: int = HELM_BC_DIRICHLET,
+                     prec: int = HELM_PREC_MIXED, stream=None) -> _Plan:
+    lib = load()
+    out = C.c_void_p()
+    arr = (C.c_int * ndim)(*([n] * ndim))
+    st = lib.helm_plan_create(C.byref(out), ndim, arr, float(h), float(k), int(bc), int(prec),
+                              _stream_handle(stream))
+    _check(st, "helm_plan_create")
+    return _Plan(out, ndim, n, h, k, prec)
+
+
+def helm_plan_destroy(plan: _Plan) -> None:
+    if plan.handle is not None:
+        _check(load().helm_plan_destroy(plan.handle), "helm_plan_destroy")
+        plan.handle = None
+
+
+def helm_plan_info(plan: _Plan):
+    lm, km, rho = C.c_double(), C.c_double(), C.c_double()
+    ws = C.c_size_t()
+    _check(load().helm_plan_info(plan.handle, C.byref(lm), C.byref(km), C.byref(rho), C.byref(ws)),
+           "helm_plan_info")
+    return lm.value, km.value, rho.value, ws.value
+
+
+def helm_plan_set_cycle(plan: _Plan, nu1: int, nu2: int, cycles: int = 1) -> None:
+    _check(load().helm_plan_set_cycle(plan.handle, nu1, nu2, cycles), "helm_plan_set_cycle")
+
+
+def helm_solve_ex(plan: _Plan, f, g, u, tol: float, max_outer: int):
+    """Returns (status, iters, relres history, increment sup-norm history)."""
+    import torch
+    D, n = plan.D, plan.n
+    pf = _ptr(f, torch.complex128, (n,) * D, "f")
+    pg = _ptr(g, torch.complex128, (n + 2,) * D, "g")
+    pu = _ptr(u, torch.complex128, (n + 2,) * D, "u")
+    iters = C.c_int()
+    hist = np.zeros(max_outer + 1, dtype=np.float64)
+    einf = np.zeros(max(max_outer, 1), dtype=np.float64)
+    st = load().helm_solve_ex(plan.handle, pf, pg, pu, float(tol), int(max_outer), C.byref(iters),
+                              hist.ctypes.data_as(C.POINTER(C.c_double)),
+                              einf.ctypes.data_as(C.POINTER(C.c_double)))
+    _check(st, "helm_solve")
+    it = iters.value
+    return st, it, hist[: it + 1].copy(), einf[:it].copy()
+
+
+def helm_solve(plan: _Plan, f, g, u, tol: float, max_outer: int):
+    """Returns (status, iters, relres history)."""
+    st, it, hist, _ = helm_solve_ex(plan, f, g, u, tol, max_outer)
+    return st, it, hist
+
+
+def poisson_vcycle(plan: _Plan, rhs, e, nu1: int = 2, nu2: int = 2) -> None:
+    D, n = plan.D, plan.n
+    pr = _ptr(rhs, plan.inner_dtype, (n,) * D, "rhs")
+    pe = _ptr(e, plan.inner_dtype, (n,) * D, "e")
+    _check(load().poisson_vcycle(plan.handle, pr, pe, int(nu1), int(nu2)), "poisson_vcycle")
+
+
+class _Batch:
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if self.handle is not None and _lib is not None:
+            _lib.helm_batch_destroy(self.handle)
+            self.handle = None
+
+
+def helm_batch_create(hbm_cap_bytes: int = 0, stream=None) -> _Batch:
+    out = C.c_void_p()
+    _check(load().helm_batch_create(C.byref(out), int(hbm_cap_bytes), _stream_handle(stream)),
+           "helm_batch_create")
+    return _Batch(out)
+
+
+def helm_batch_destroy(batch: _Batch) -> None:
+    if batch.handle is not None:
+        _check(load().helm_batch_destroy(batch.handle), "helm_batch_destroy")
+        batch.handle = None
+
+
+def helm_batch_submit(batch: _Batch, plan: _Plan, f, g, u, tol: float, max_outer: int):
+    """Returns a ticket, or None when the memory cap does not admit the solve yet."""
+    import torch
+    D, n = plan.D, plan.n
+    pf = _ptr(f, torch.complex128, (n,) * D, "f")
+    pg = _ptr(g, torch.complex128, (n + 2,) * D, "g")
+    pu = _ptr(u, torch.complex128, (n + 2,) * D, "u")
+    t = C.c_uint64()
+    st = load().helm_batch_submit(batch.handle, plan.handle, pf, pg, pu, float(tol), int(max_outer),
+                                  C.byref(t))
+    if st == HELM_ENOMEM:
+        return None
+    _check(st, "helm_batch_submit")
+    return t.value
+
+
+def helm_batch_step(batch: _Batch, max_steps: int = 0) -> None:
+    _check(load().helm_batch_step(batch.handle, int(max_steps)), "helm_batch_step")
+
+
+def helm_batch_poll(batch: _Batch, ticket: int, max_outer: int):
+    """Returns None while running, else (status, iters, relres history)."""
+    done, status, iters = C.c_int(), C.c_int(), C.c_int()
+    hist = np.zeros(max_outer + 1, dtype=np.float64)
+    _check(load().helm_batch_poll(batch.handle, C.c_uint64(ticket), C.byref(done), C.byref(status),
+                                  C.byref(iters), hist.ctypes.data_as(C.POINTER(C.c_double))),
+           "helm_batch_poll")
+    if not done.value:
+        return None
+    return status.value, iters.value, hist[: iters.value + 1].copy()
+
+
+def helm_batch_info(batch: _Batch):
+    a = C.c_int()
+    b = C.c_size_t()
+    _check(load().helm_batch_info(batch.handle, C.byref(a), C.byref(b)), "helm_batch_info")
+    return a.value, b.value

@@ -1,0 +1,77 @@
+// Shared device-side definitions of the Helmholtz Poisson-iteration library.
+//
+// Layouts
+//  * outer arrays (caller memory, FP64): u padded (n+2)^D complex128, tight rows;
+//    f interior n^D complex128; g padded (n+2)^D complex128 (ring = Dirichlet data).
+//  * multigrid level arrays (library memory): padded (n_l+2)^D with the x pitch rounded
+//    up to a multiple of 16 elements, so every row starts 128/256-byte aligned; the ring
+//    of e is kept zero (homogeneous Dirichlet for the Poisson increments, Eq. (2.7) for
+//    n >= 1), rhs rows use the same indexing (its ring is never read).
+//  * complex numbers are interleaved {re, im} pairs (float2 / double2).  The inner
+//    operator is real, so the real and imaginary parts are two independent lanes of the
+//    same real stencil (Eq. (2.5) with p = 0: the two chains do not couple).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define HELM_MAXLEV 16
+
+// Instance status values kept on the device.  Non-negative values < 100 and negative
+// values are the public helm_status outcomes; ACTIVE means "still iterating".
+#define HELM_ST_ACTIVE 100
+#define HELM_ST_IDLE 101
+
+namespace helm {
+
+struct LevelDesc {
+    int n;        // interior nodes per axis, 2^(m-l) - 1
+    int pitch;    // elements per x row (>= n + 2, multiple of 16)
+    int rows;     // n + 2 rows per z plane
+    int pad_;
+    double h;     // spacing 2^l h
+    void* e;      // padded iterate of Delta_h e = rhs
+    void* rhs;    // right-hand side (same indexing as e)
+};
+
+struct InstDesc {
+    int D, n, nlev, ltail;      // ltail: first level solved inside the one-CTA tail kernel
+    int max_outer, nres_blocks; // residual tiles (one partial sum each)
+    int res_tx, res_ty;         // residual tile grid (x tiles, y tiles); z tiles = n (3D)
+    double h, k2, tol;
+    double2* u[2];              // u[0] = caller's array, u[1] = library buffer
+    const double2* f;
+    const double2* g;
+    double* part;               // [2 * nres_blocks]: sum |r|^2 partials, then max |e|
+    double* hist;               // relres_0..relres_max_outer
+    double* einf;               // ||e_N||_inf, N = 0..max_outer-1
+    LevelDesc lev[HELM_MAXLEV];
+};
+
+struct InstState {
+    int status;      // HELM_ST_ACTIVE while iterating, else the outcome
+    int it;          // outer steps performed (u_it lives in u[it & 1])
+    int run;         // consecutive non-decreasing relres steps
+    int pad_;
+    double norm0;    // ||r_0||_2
+    double prev;     // relres of the previous step
+};
+
+// Work item of a multigrid launch: one (instance, level) pair; blocks stride over it.
+struct MgItem {
+    int inst;
+    int level;
+};
+
+// Work item of a residual launch: one tile of one instance.
+struct ResItem {
+    int inst;
+    int tx, ty, tz;
+};
+
+template <typename R> struct C2;
+template <> struct C2<float>  { typedef float2  T; };
+template <> struct C2<double> { typedef double2 T; };
+
+__host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+}  // namespace helm

@@ -1,0 +1,918 @@
+// Host engine of the C ABI declared in include/helm.h.
+//
+// An Engine advances a set of independent instances of one kernel class (dimension D,
+// inner precision) together: every launch of an outer step covers all of its active
+// instances (work items (instance, level) for the multigrid kernels, (instance, tile)
+// for the residual), and instances that have finished are skipped on the device by
+// their status word.  One outer step is captured once into the body of a CUDA graph
+// WHILE node; the convergence kernel at the end of the body sets the loop condition,
+// so a whole solve runs as a single graph launch with no host round trip per step.
+//
+// A helm_plan owns one Engine with a single instance (helm_solve); a helm_batch owns
+// one Engine per kernel class and admits / retires instances between calls
+// (continuous batching for the served stream).
+#include "../../include/helm.h"
+#include "launch.h"
+
+#include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <vector>
+
+using namespace helm;
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+thread_local char g_errbuf[256] = "";
+
+#define HELM_CK(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t _e = (call);                                                          \
+        if (_e != cudaSuccess) {                                                          \
+            snprintf(g_errbuf, sizeof g_errbuf, "%s: %s (%s:%d)", #call,                  \
+                     cudaGetErrorString(_e), __FILE__, __LINE__);                         \
+            return HELM_ECUDA;                                                            \
+        }                                                                                 \
+    } while (0)
+
+int tail_n(int D) { return D == 2 ? TAIL_N_2D : TAIL_N_3D; }
+int elem_bytes(int prec) { return prec == HELM_PREC_FP64 ? 16 : 8; }
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool is_pow2m1(int n) { return n >= 1 && ((n + 1) & n) == 0; }
+
+int res_rows_per_tile(int D) { return D == 2 ? 32 : 16; }
+
+// Fill the geometry part of a descriptor and return the workspace bytes it needs (the
+// level arrays, the second iterate buffer and the residual partials).  With base != NULL
+// the pointers are carved out of it.
+size_t layout(InstDesc& d, int D, int n, double h, double k, int prec, char* base)
+{
+    d.D = D;
+    d.n = n;
+    d.h = h;
+    d.k2 = k * k;
+    int nl = 0, lt = -1;
+    for (int m = n; m >= 1 && nl < HELM_MAXLEV; m = (m - 1) / 2) {
+        if (lt < 0 && m <= tail_n(D)) lt = nl;
+        d.lev[nl].n = m;
+        ++nl;
+    }
+    d.nlev = nl;
+    d.ltail = lt;
+    size_t off = 0;
+    const size_t eb = elem_bytes(prec);
+    double hl = h;
+    for (int l = 0; l < nl; ++l) {
+        LevelDesc& L = d.lev[l];
+        L.h = hl;
+        hl *= 2.0;
+        L.rows = L.n + 2;
+        L.pitch = round_up(L.n + 2, 16);
+        L.e = nullptr;
+        L.rhs = nullptr;
+        if (l > lt) continue;               // deeper levels live only inside the tail kernel
+        const size_t planes = (D == 3) ? (size_t)L.rows : 1;
+        const size_t sz = align256((size_t)L.pitch * L.rows * planes * eb);
+        if (base) {
+            L.e = base + off;
+            L.rhs = base + off + sz;
+        }
+        off += 2 * sz;
+    }
+    const size_t S = (size_t)n + 2;
+    const size_t ubytes = align256(((D == 3) ? S * S * S : S * S) * 16);
+    if (base) d.u[1] = (double2*)(base + off);
+    off += ubytes;
+    d.res_tx = (n + 31) / 32;
+    d.res_ty = (n + res_rows_per_tile(D) - 1) / res_rows_per_tile(D);
+    d.nres_blocks = d.res_tx * d.res_ty * ((D == 3) ? n : 1);
+    if (base) d.part = (double*)(base + off);
+    off += align256((size_t)2 * d.nres_blocks * sizeof(double));
+    return off;
+}
+
+// bytes of the level arrays to clear at allocation (rings must be zero)
+struct Instance {
+    InstDesc d{};
+    int prec = 1;
+    char* ws = nullptr;          // workspace (levels, u[1], partials)
+    size_t ws_bytes = 0;
+    double* hist = nullptr;      // device: relres (cap + 1) then einf (cap)
+    int hist_cap = -1;
+    bool stream_ordered = false; // allocated with cudaMallocAsync
+    ResItem* d_res0 = nullptr;   // this instance's residual tiles (initial residual)
+    int nres0 = 0;
+};
+
+struct LaunchRec {
+    enum Kind { RBGS, RESTRICT, PROLONG, ZERO, TAIL, RESID, CHECK } kind;
+    int off, cnt, work, color, mode;
+};
+
+struct Engine {
+    int D = 2, prec = 1;
+    int nu1 = 2, nu2 = 2, cycles = 1;
+    cudaStream_t cap_stream = nullptr;
+    int cap = 0;                               // descriptor slots
+    std::vector<Instance*> slots;              // nullptr = free
+    InstDesc* d_desc = nullptr;
+    InstState* d_state = nullptr;
+    int* d_ctrl = nullptr;                     // [0] steps done, [1] step budget, [2] go
+    int* h_ctrl = nullptr;                     // pinned mirror
+    InstState* h_state = nullptr;              // pinned mirror (cap entries)
+    MgItem* d_mg = nullptr;
+    size_t mg_cap = 0;
+    ResItem* d_res = nullptr;
+    size_t res_cap = 0;
+    int nres = 0;
+    std::vector<LaunchRec> step;               // one outer step
+    std::vector<LaunchRec> vcyc_plain;         // one V-cycle from the current iterate
+    int max_tail = 1;
+    bool dirty = true;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+
+    ~Engine() { release(); }
+
+    void release()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        if (d_desc) cudaFree(d_desc);
+        if (d_state) cudaFree(d_state);
+        if (d_ctrl) cudaFree(d_ctrl);
+        if (h_ctrl) cudaFreeHost(h_ctrl);
+        if (h_state) cudaFreeHost(h_state);
+        if (d_mg) cudaFree(d_mg);
+        if (d_res) cudaFree(d_res);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        d_desc = nullptr; d_state = nullptr; d_ctrl = nullptr; h_ctrl = nullptr;
+        h_state = nullptr; d_mg = nullptr; d_res = nullptr; cap_stream = nullptr;
+    }
+
+    helm_status init(int D_, int prec_)
+    {
+        D = D_;
+        prec = prec_;
+        HELM_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+        HELM_CK(cudaMalloc(&d_ctrl, 4 * sizeof(int)));
+        HELM_CK(cudaMallocHost(&h_ctrl, 4 * sizeof(int)));
+        HELM_CK(setup_tail(D, prec == HELM_PREC_FP64 ? 0 : 1));
+        return grow(4);
+    }
+
+    helm_status grow(int want)
+    {
+        if (want <= cap) return HELM_OK;
+        int nc = std::max(want, cap * 2);
+        InstDesc* nd = nullptr;
+        InstState* ns = nullptr;
+        InstState* nh = nullptr;
+        HELM_CK(cudaMalloc(&nd, sizeof(InstDesc) * nc));
+        HELM_CK(cudaMalloc(&ns, sizeof(InstState) * nc));
+        HELM_CK(cudaMallocHost(&nh, sizeof(InstState) * nc));
+        std::vector<InstState> idle(nc);
+        for (auto& s : idle) { memset(&s, 0, sizeof s); s.status = HELM_ST_IDLE; }
+        if (cap > 0) {
+            HELM_CK(cudaMemcpy(nd, d_desc, sizeof(InstDesc) * cap, cudaMemcpyDeviceToDevice));
+            HELM_CK(cudaMemcpy(idle.data(), d_state, sizeof(InstState) * cap, cudaMemcpyDeviceToHost));
+        }
+        HELM_CK(cudaMemcpy(ns, idle.data(), sizeof(InstState) * nc, cudaMemcpyHostToDevice));
+        if (d_desc) cudaFree(d_desc);
+        if (d_state) cudaFree(d_state);
+        if (h_state) cudaFreeHost(h_state);
+        d_desc = nd;
+        d_state = ns;
+        h_state = nh;
+        slots.resize(nc, nullptr);
+        cap = nc;
+        dirty = true;
+        return HELM_OK;
+    }
+
+    // Rebuild the work-item lists and the launch sequence of one outer step for the
+    // instances currently in the slots.
+    helm_status rebuild_plan()
+    {
+        std::vector<MgItem> items;
+        std::vector<ResItem> res;
+        int J = 0;
+        max_tail = 1;
+        for (int i = 0; i < cap; ++i)
+            if (slots[i]) {
+                J = std::max(J, slots[i]->d.ltail);
+                max_tail = std::max(max_tail, slots[i]->d.lev[slots[i]->d.ltail].n);
+            }
+        struct Ph { int off, cnt, w_rb, w_rs, w_pr, w_z; };
+        std::vector<Ph> ph(J);
+        for (int j = 0; j < J; ++j) {
+            Ph p{(int)items.size(), 0, 0, 0, 0, 0};
+            for (int i = 0; i < cap; ++i) {
+                if (!slots[i]) continue;
+                const InstDesc& d = slots[i]->d;
+                const int l = j - (J - d.ltail);
+                if (l < 0) continue;
+                items.push_back(MgItem{i, l});
+                const int n = d.lev[l].n, nc = d.lev[l + 1].n;
+                const long rows = (D == 3) ? (long)n * n : n;
+                p.w_rb = (int)std::max<long>(p.w_rb, rows * ((n + 1) / 2));
+                p.w_rs = (int)std::max<long>(p.w_rs, (D == 3) ? (long)nc * nc * nc : (long)nc * nc);
+                p.w_pr = (int)std::max<long>(p.w_pr, (D == 3) ? (long)n * n * n : (long)n * n);
+                const long pz = (long)d.lev[l].pitch * d.lev[l].rows * ((D == 3) ? d.lev[l].rows : 1);
+                p.w_z = (int)std::max<long>(p.w_z, pz);
+                ++p.cnt;
+            }
+            ph[j] = p;
+        }
+        const int tail_off = (int)items.size();
+        int ntail = 0;
+        for (int i = 0; i < cap; ++i)
+            if (slots[i]) { items.push_back(MgItem{i, slots[i]->d.ltail}); ++ntail; }
+        // level-0 items (zeroing when nu1 == 0)
+        const int l0_off = (int)items.size();
+        int nl0 = 0, w_l0 = 0;
+        for (int i = 0; i < cap; ++i)
+            if (slots[i]) {
+                items.push_back(MgItem{i, 0});
+                ++nl0;
+                const LevelDesc& L = slots[i]->d.lev[0];
+                w_l0 = std::max(w_l0, L.pitch * L.rows * ((D == 3) ? L.rows : 1));
+            }
+        for (int i = 0; i < cap; ++i) {
+            if (!slots[i]) continue;
+            const InstDesc& d = slots[i]->d;
+            const int tz = (D == 3) ? d.n : 1;
+            for (int z = 0; z < tz; ++z)
+                for (int y = 0; y < d.res_ty; ++y)
+                    for (int x = 0; x < d.res_tx; ++x) res.push_back(ResItem{i, x, y, z});
+        }
+        if (items.size() > mg_cap) {
+            if (d_mg) cudaFree(d_mg);
+            mg_cap = std::max(items.size(), mg_cap * 2);
+            HELM_CK(cudaMalloc(&d_mg, mg_cap * sizeof(MgItem)));
+        }
+        if (res.size() > res_cap) {
+            if (d_res) cudaFree(d_res);
+            res_cap = std::max(res.size(), res_cap * 2);
+            HELM_CK(cudaMalloc(&d_res, res_cap * sizeof(ResItem)));
+        }
+        if (!items.empty())
+            HELM_CK(cudaMemcpy(d_mg, items.data(), items.size() * sizeof(MgItem), cudaMemcpyHostToDevice));
+        if (!res.empty())
+            HELM_CK(cudaMemcpy(d_res, res.data(), res.size() * sizeof(ResItem), cudaMemcpyHostToDevice));
+        nres = (int)res.size();
+
+        auto vcycle = [&](std::vector<LaunchRec>& out, bool zero_start) {
+            if (zero_start && nu1 == 0)
+                out.push_back({LaunchRec::ZERO, l0_off, nl0, w_l0, 0, 0});
+            for (int j = 0; j < J; ++j) {
+                for (int s = 0; s < nu1; ++s) {
+                    const int mode = (s == 0) ? (zero_start ? 2 : 1) : 0;
+                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 0, mode});
+                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 1, 0});
+                }
+                out.push_back({LaunchRec::RESTRICT, ph[j].off, ph[j].cnt, ph[j].w_rs, 0, 0});
+            }
+            out.push_back({LaunchRec::TAIL, tail_off, ntail, 0, 0, zero_start ? 0 : 1});
+            for (int j = J - 1; j >= 0; --j) {
+                out.push_back({LaunchRec::PROLONG, ph[j].off, ph[j].cnt, ph[j].w_pr, 0, 0});
+                for (int s = 0; s < nu2; ++s) {
+                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 0, 0});
+                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 1, 0});
+                }
+            }
+        };
+        step.clear();
+        for (int c = 0; c < cycles; ++c) vcycle(step, c == 0);
+        step.push_back({LaunchRec::RESID, 0, nres, 0, 0, 1});
+        step.push_back({LaunchRec::CHECK, 0, cap, 0, 0, 1});
+        vcyc_plain.clear();
+        vcycle(vcyc_plain, false);
+        return HELM_OK;
+    }
+
+    helm_status enqueue(const std::vector<LaunchRec>& seq, cudaStream_t s, bool use_cond)
+    {
+        for (const LaunchRec& L : seq) {
+            cudaError_t e = cudaSuccess;
+            switch (L.kind) {
+            case LaunchRec::RBGS:
+                e = launch_rbgs(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, L.color, L.mode, s);
+                break;
+            case LaunchRec::RESTRICT:
+                e = launch_restrict(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s);
+                break;
+            case LaunchRec::PROLONG:
+                e = launch_prolong(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s);
+                break;
+            case LaunchRec::ZERO:
+                e = launch_zero(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s);
+                break;
+            case LaunchRec::TAIL:
+                e = launch_tail(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, nu1, nu2, L.mode,
+                                max_tail, s);
+                break;
+            case LaunchRec::RESID:
+                e = launch_residual(D, prec, d_desc, d_state, d_res + L.off, L.cnt, L.mode, s);
+                break;
+            case LaunchRec::CHECK:
+                e = launch_check(d_desc, d_state, L.cnt, L.mode, d_ctrl, use_cond ? 1 : 0,
+                                 (unsigned long long)cond, s);
+                break;
+            }
+            if (e != cudaSuccess) {
+                snprintf(g_errbuf, sizeof g_errbuf, "kernel launch: %s", cudaGetErrorString(e));
+                return HELM_ECUDA;
+            }
+        }
+        return HELM_OK;
+    }
+
+    // (Re)build the graph: a single WHILE node whose body is one outer step.
+    helm_status build_graph()
+    {
+        if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+        if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
+        HELM_CK(cudaGraphCreate(&graph, 0));
+        HELM_CK(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+        p.conditional.handle = cond;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        HELM_CK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p));
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        HELM_CK(cudaStreamBeginCaptureToGraph(cap_stream, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal));
+        helm_status st = enqueue(step, cap_stream, true);
+        cudaGraph_t captured = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cap_stream, &captured);
+        if (st != HELM_OK) return st;
+        HELM_CK(e);
+        HELM_CK(cudaGraphInstantiate(&exec, graph, 0));
+        return HELM_OK;
+    }
+
+    helm_status prepare()
+    {
+        if (!dirty) return HELM_OK;
+        helm_status st = rebuild_plan();
+        if (st != HELM_OK) return st;
+        st = build_graph();
+        if (st != HELM_OK) return st;
+        dirty = false;
+        return HELM_OK;
+    }
+
+    int active_count() const
+    {
+        int c = 0;
+        for (auto* p : slots) c += p != nullptr;
+        return c;
+    }
+
+    // Initial residual and norm of one newly started instance.
+    helm_status start_instance(int slot, cudaStream_t s)
+    {
+        Instance* in = slots[slot];
+        InstState init;
+        memset(&init, 0, sizeof init);
+        init.status = HELM_ST_ACTIVE;
+        HELM_CK(cudaMemcpyAsync(d_desc + slot, &in->d, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
+        HELM_CK(cudaMemcpyAsync(d_state + slot, &init, sizeof(InstState), cudaMemcpyHostToDevice, s));
+        HELM_CK(launch_set_ring(D, d_desc, d_state, slot, in->d.n, s));
+        // the instance's own tile list names instance 0: offset the tables to its slot
+        HELM_CK(launch_residual(D, prec, d_desc + slot, d_state + slot, in->d_res0, in->nres0, 0, s));
+        // the check of the initial residual only touches this slot
+        HELM_CK(launch_check(d_desc + slot, d_state + slot, 1, 0, d_ctrl, 0, 0, s));
+        g_launches += 3;
+        return HELM_OK;
+    }
+
+    // Run outer steps until every active instance has finished or `budget` steps ran.
+    // Returns the number of steps executed (read back after the stream drains).
+    helm_status run(cudaStream_t s, int budget, int* steps_done)
+    {
+        helm_status st = prepare();
+        if (st != HELM_OK) return st;
+        h_ctrl[0] = 0;
+        h_ctrl[1] = budget > 0 ? budget : INT_MAX;
+        h_ctrl[2] = 1;
+        HELM_CK(cudaMemcpyAsync(d_ctrl, h_ctrl, 3 * sizeof(int), cudaMemcpyHostToDevice, s));
+        HELM_CK(cudaGraphLaunch(exec, s));
+        HELM_CK(cudaMemcpyAsync(h_ctrl, d_ctrl, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        HELM_CK(cudaMemcpyAsync(h_state, d_state, sizeof(InstState) * cap, cudaMemcpyDeviceToHost, s));
+        HELM_CK(cudaStreamSynchronize(s));
+        if (steps_done) *steps_done = h_ctrl[0];
+        g_launches += (uint64_t)h_ctrl[0] * step.size();
+        return HELM_OK;
+    }
+};
+
+helm_status alloc_instance(Instance& in, int D, int n, double h, double k, int prec,
+                           int max_outer, cudaStream_t s, bool stream_ordered)
+{
+    in.prec = prec;
+    in.stream_ordered = stream_ordered;
+    in.ws_bytes = layout(in.d, D, n, h, k, prec, nullptr);
+    if (stream_ordered) {
+        HELM_CK(cudaMallocAsync((void**)&in.ws, in.ws_bytes, s));
+    } else {
+        cudaError_t e = cudaMalloc((void**)&in.ws, in.ws_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            snprintf(g_errbuf, sizeof g_errbuf, "cudaMalloc(%zu): %s", in.ws_bytes, cudaGetErrorString(e));
+            return HELM_ENOMEM;
+        }
+    }
+    layout(in.d, D, n, h, k, prec, in.ws);
+    // rings of the level iterates must be zero; clear everything once
+    HELM_CK(cudaMemsetAsync(in.ws, 0, in.ws_bytes, s));
+    // residual tiles of this instance (for its initial residual)
+    std::vector<ResItem> r;
+    const int tz = (D == 3) ? n : 1;
+    for (int z = 0; z < tz; ++z)
+        for (int y = 0; y < in.d.res_ty; ++y)
+            for (int x = 0; x < in.d.res_tx; ++x) r.push_back(ResItem{0, x, y, z});
+    in.nres0 = (int)r.size();
+    const size_t rb = r.size() * sizeof(ResItem);
+    if (stream_ordered) HELM_CK(cudaMallocAsync((void**)&in.d_res0, rb, s));
+    else HELM_CK(cudaMalloc((void**)&in.d_res0, rb));
+    HELM_CK(cudaMemcpyAsync(in.d_res0, r.data(), rb, cudaMemcpyHostToDevice, s));
+    // history (relres and einf)
+    in.hist_cap = max_outer;
+    const size_t hb = (2 * (size_t)max_outer + 1) * sizeof(double);
+    if (stream_ordered) HELM_CK(cudaMallocAsync((void**)&in.hist, hb, s));
+    else HELM_CK(cudaMalloc((void**)&in.hist, hb));
+    in.d.hist = in.hist;
+    in.d.einf = in.hist + max_outer + 1;
+    return HELM_OK;
+}
+
+void free_instance(Instance& in, cudaStream_t s)
+{
+    if (in.stream_ordered) {
+        if (in.ws) cudaFreeAsync(in.ws, s);
+        if (in.d_res0) cudaFreeAsync(in.d_res0, s);
+        if (in.hist) cudaFreeAsync(in.hist, s);
+    } else {
+        if (in.ws) cudaFree(in.ws);
+        if (in.d_res0) cudaFree(in.d_res0);
+        if (in.hist) cudaFree(in.hist);
+    }
+    in.ws = nullptr;
+    in.d_res0 = nullptr;
+    in.hist = nullptr;
+}
+
+helm_status check_ptr(const void* p)
+{
+    if (!p) return HELM_EINVAL;
+    if (((uintptr_t)p & 15) != 0) return HELM_EINVAL;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return HELM_EINVAL;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return HELM_EINVAL;
+    return HELM_OK;
+}
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb)
+{
+    const char* x = (const char*)a;
+    const char* y = (const char*)b;
+    return x < y + nb && y < x + na;
+}
+
+double lambda_min_of(int D, int n, double h)
+{
+    const double pi = 3.14159265358979323846;
+    const double s = std::sin(pi / (2.0 * (n + 1)));
+    return D * 4.0 / (h * h) * s * s;
+}
+
+}  // namespace
+
+struct helm_plan {
+    int D, n, prec;
+    double h, k;
+    cudaStream_t stream;
+    Engine eng;
+    Instance inst;
+    size_t points() const { return D == 3 ? (size_t)n * n * n : (size_t)n * n; }
+    size_t padded() const { size_t s = n + 2; return D == 3 ? s * s * s : s * s; }
+};
+
+struct helm_batch {
+    size_t cap_bytes = 0, used = 0;
+    cudaStream_t stream = nullptr;
+    std::map<int, std::unique_ptr<Engine>> engines;   // key = 2 * D + prec
+    std::map<int, cudaStream_t> eng_streams;
+    cudaEvent_t fork = nullptr;
+    std::map<int, cudaEvent_t> join;
+    struct Rec {
+        int key = 0, slot = -1;
+        int done = 0, status = 0, iters = 0;
+        Instance* inst = nullptr;
+        void* u = nullptr;
+        size_t ubytes = 0;
+        std::vector<double> hist;
+    };
+    std::map<uint64_t, Rec> recs;
+    uint64_t next = 1;
+};
+
+extern "C" {
+
+const char* helm_status_str(int s)
+{
+    switch (s) {
+    case HELM_CONVERGED: return "HELM_CONVERGED";
+    case HELM_MAXITER: return "HELM_MAXITER";
+    case HELM_DIVERGED: return "HELM_DIVERGED";
+    case HELM_EINVAL: return "HELM_EINVAL";
+    case HELM_ENOMEM: return "HELM_ENOMEM";
+    case HELM_ECUDA: return "HELM_ECUDA";
+    case HELM_ENONFINITE: return "HELM_ENONFINITE";
+    case HELM_ETIMEOUT: return "HELM_ETIMEOUT";
+    case HELM_EUNSUPPORTED: return "HELM_EUNSUPPORTED";
+    default: return "HELM_UNKNOWN";
+    }
+}
+
+const char* helm_last_error(void) { return g_errbuf; }
+
+uint64_t helm_launch_count(void) { return g_launches.load(); }
+
+helm_status helm_plan_create(helm_plan** out, int ndim, const int* n, double h, double k, int bc,
+                             int prec, void* cuda_stream)
+{
+    if (!out || !n) return HELM_EINVAL;
+    *out = nullptr;
+    if (ndim != 2 && ndim != 3) return HELM_EINVAL;
+    if (bc != HELM_BC_DIRICHLET) return HELM_EUNSUPPORTED;
+    if (prec != HELM_PREC_FP64 && prec != HELM_PREC_MIXED) return HELM_EINVAL;
+    if (!(h > 0.0) || !std::isfinite(h) || !(k >= 0.0) || !std::isfinite(k)) return HELM_EINVAL;
+    for (int a = 0; a < ndim; ++a)
+        if (!is_pow2m1(n[a])) return HELM_EINVAL;
+    for (int a = 1; a < ndim; ++a)
+        if (n[a] != n[0]) return HELM_EUNSUPPORTED;
+    if ((ndim == 2 && n[0] > 32767) || (ndim == 3 && n[0] > 2047)) return HELM_EUNSUPPORTED;
+    std::unique_ptr<helm_plan> p(new helm_plan());
+    p->D = ndim;
+    p->n = n[0];
+    p->prec = prec;
+    p->h = h;
+    p->k = k;
+    p->stream = (cudaStream_t)cuda_stream;
+    helm_status st = p->eng.init(ndim, prec);
+    if (st != HELM_OK) return st;
+    st = alloc_instance(p->inst, ndim, n[0], h, k, prec, 1024, p->stream, false);
+    if (st != HELM_OK) return st;
+    p->eng.slots[0] = &p->inst;
+    p->eng.dirty = true;
+    HELM_CK(cudaStreamSynchronize(p->stream));
+    *out = p.release();
+    return HELM_OK;
+}
+
+helm_status helm_plan_destroy(helm_plan* p)
+{
+    if (!p) return HELM_EINVAL;
+    cudaStreamSynchronize(p->stream);
+    p->eng.release();
+    free_instance(p->inst, p->stream);
+    delete p;
+    return HELM_OK;
+}
+
+helm_status helm_plan_info(const helm_plan* p, double* lmin, double* kmax, double* rho, size_t* ws)
+{
+    if (!p) return HELM_EINVAL;
+    const double l = lambda_min_of(p->D, p->n, p->h);
+    if (lmin) *lmin = l;
+    if (kmax) *kmax = std::sqrt(l);
+    if (rho) *rho = p->k * p->k / l;
+    if (ws) *ws = p->inst.ws_bytes + (2 * (size_t)p->inst.hist_cap + 1) * sizeof(double);
+    return HELM_OK;
+}
+
+helm_status helm_plan_set_cycle(helm_plan* p, int nu1, int nu2, int cycles)
+{
+    if (!p) return HELM_EINVAL;
+    if (nu1 < 0 || nu1 > 8 || nu2 < 0 || nu2 > 8 || nu1 + nu2 < 1 || cycles < 1 || cycles > 16)
+        return HELM_EINVAL;
+    p->eng.nu1 = nu1;
+    p->eng.nu2 = nu2;
+    p->eng.cycles = cycles;
+    p->eng.dirty = true;
+    return HELM_OK;
+}
+
+helm_status helm_solve_ex(helm_plan* p, const void* f, const void* g, void* u, double tol,
+                          int max_outer, int* iters, double* res_hist, double* einf_hist)
+{
+    if (!p) return HELM_EINVAL;
+    if (max_outer < 0 || !(tol >= 0.0)) return HELM_EINVAL;
+    if (check_ptr(f) || check_ptr(g) || check_ptr(u)) return HELM_EINVAL;
+    const size_t fb = p->points() * 16, ub = p->padded() * 16;
+    if (overlap(f, fb, u, ub) || overlap(g, ub, u, ub)) return HELM_EINVAL;
+    Instance& in = p->inst;
+    if (max_outer > in.hist_cap) {
+        HELM_CK(cudaStreamSynchronize(p->stream));
+        if (in.hist) cudaFree(in.hist);
+        in.hist = nullptr;
+        const size_t hb = (2 * (size_t)max_outer + 1) * sizeof(double);
+        if (cudaMalloc((void**)&in.hist, hb) != cudaSuccess) { cudaGetLastError(); return HELM_ENOMEM; }
+        in.hist_cap = max_outer;
+        in.d.hist = in.hist;
+        in.d.einf = in.hist + max_outer + 1;
+    }
+    in.d.u[0] = (double2*)u;
+    in.d.f = (const double2*)f;
+    in.d.g = (const double2*)g;
+    in.d.tol = tol;
+    in.d.max_outer = max_outer;
+    in.d.k2 = p->k * p->k;
+    helm_status st = p->eng.prepare();
+    if (st != HELM_OK) return st;
+    st = p->eng.start_instance(0, p->stream);
+    if (st != HELM_OK) return st;
+    int steps = 0;
+    st = p->eng.run(p->stream, 0, &steps);
+    if (st != HELM_OK) return st;
+    const InstState s = p->eng.h_state[0];
+    if (s.it & 1) HELM_CK(cudaMemcpyAsync(u, in.d.u[1], ub, cudaMemcpyDeviceToDevice, p->stream));
+    if (res_hist) HELM_CK(cudaMemcpyAsync(res_hist, in.d.hist, (s.it + 1) * sizeof(double),
+                                          cudaMemcpyDeviceToHost, p->stream));
+    if (einf_hist && s.it > 0)
+        HELM_CK(cudaMemcpyAsync(einf_hist, in.d.einf, s.it * sizeof(double), cudaMemcpyDeviceToHost,
+                                p->stream));
+    HELM_CK(cudaStreamSynchronize(p->stream));
+    // leave the slot idle so standalone V-cycles see a known state
+    InstState idle;
+    memset(&idle, 0, sizeof idle);
+    idle.status = HELM_ST_IDLE;
+    HELM_CK(cudaMemcpy(p->eng.d_state, &idle, sizeof idle, cudaMemcpyHostToDevice));
+    if (iters) *iters = s.it;
+    return (helm_status)s.status;
+}
+
+helm_status helm_solve(helm_plan* p, const void* f, const void* g, void* u, double tol,
+                       int max_outer, int* iters, double* res_hist)
+{
+    return helm_solve_ex(p, f, g, u, tol, max_outer, iters, res_hist, nullptr);
+}
+
+helm_status poisson_vcycle(helm_plan* p, const void* rhs, void* e, int nu1, int nu2)
+{
+    if (!p) return HELM_EINVAL;
+    if (nu1 < 0 || nu1 > 8 || nu2 < 0 || nu2 > 8 || nu1 + nu2 < 1) return HELM_EINVAL;
+    if (check_ptr(rhs) || check_ptr(e)) return HELM_EINVAL;
+    const size_t b = p->points() * (size_t)elem_bytes(p->prec);
+    if (overlap(rhs, b, e, b)) return HELM_EINVAL;
+    Engine& E = p->eng;
+    const int s1 = E.nu1, s2 = E.nu2, sc = E.cycles;
+    E.nu1 = nu1;
+    E.nu2 = nu2;
+    E.cycles = 1;
+    helm_status st = E.rebuild_plan();
+    E.nu1 = s1;
+    E.nu2 = s2;
+    E.cycles = sc;
+    E.dirty = true;
+    if (st != HELM_OK) return st;
+    InstState act;
+    memset(&act, 0, sizeof act);
+    act.status = HELM_ST_ACTIVE;
+    HELM_CK(cudaMemcpyAsync(E.d_desc, &p->inst.d, sizeof(InstDesc), cudaMemcpyHostToDevice, p->stream));
+    HELM_CK(cudaMemcpyAsync(E.d_state, &act, sizeof act, cudaMemcpyHostToDevice, p->stream));
+    HELM_CK(launch_pack(p->D, p->prec == HELM_PREC_FP64 ? 0 : 1, E.d_desc, 0, p->n, rhs, 1, p->stream));
+    HELM_CK(launch_pack(p->D, p->prec == HELM_PREC_FP64 ? 0 : 1, E.d_desc, 0, p->n, e, 0, p->stream));
+    E.nu1 = nu1;
+    E.nu2 = nu2;
+    st = E.enqueue(E.vcyc_plain, p->stream, false);
+    E.nu1 = s1;
+    E.nu2 = s2;
+    if (st != HELM_OK) return st;
+    HELM_CK(launch_unpack(p->D, p->prec == HELM_PREC_FP64 ? 0 : 1, E.d_desc, 0, p->n, e, p->stream));
+    InstState idle;
+    memset(&idle, 0, sizeof idle);
+    idle.status = HELM_ST_IDLE;
+    HELM_CK(cudaMemcpyAsync(E.d_state, &idle, sizeof idle, cudaMemcpyHostToDevice, p->stream));
+    HELM_CK(cudaStreamSynchronize(p->stream));
+    g_launches += E.vcyc_plain.size() + 3;
+    return HELM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batch / serving
+// ---------------------------------------------------------------------------
+
+helm_status helm_batch_create(helm_batch** out, size_t cap, void* stream)
+{
+    if (!out) return HELM_EINVAL;
+    *out = nullptr;
+    std::unique_ptr<helm_batch> b(new helm_batch());
+    b->cap_bytes = cap;
+    b->stream = (cudaStream_t)stream;
+    HELM_CK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    // keep freed instance memory in the pool for the next admissions
+    int dev = 0;
+    HELM_CK(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    HELM_CK(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t thr = UINT64_MAX;
+    HELM_CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    *out = b.release();
+    return HELM_OK;
+}
+
+helm_status helm_batch_destroy(helm_batch* b)
+{
+    if (!b) return HELM_EINVAL;
+    cudaStreamSynchronize(b->stream);
+    for (auto& kv : b->recs)
+        if (kv.second.inst) {
+            free_instance(*kv.second.inst, b->stream);
+            delete kv.second.inst;
+        }
+    cudaStreamSynchronize(b->stream);
+    b->engines.clear();
+    for (auto& kv : b->eng_streams) cudaStreamDestroy(kv.second);
+    for (auto& kv : b->join) cudaEventDestroy(kv.second);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+    return HELM_OK;
+}
+
+helm_status helm_batch_submit(helm_batch* b, const helm_plan* p, const void* f, const void* g,
+                              void* u, double tol, int max_outer, uint64_t* ticket)
+{
+    if (!b || !p || !ticket) return HELM_EINVAL;
+    if (max_outer < 0 || !(tol >= 0.0)) return HELM_EINVAL;
+    if (check_ptr(f) || check_ptr(g) || check_ptr(u)) return HELM_EINVAL;
+    const size_t fb = p->points() * 16, ub = p->padded() * 16;
+    if (overlap(f, fb, u, ub) || overlap(g, ub, u, ub)) return HELM_EINVAL;
+    InstDesc probe{};
+    const size_t need = layout(probe, p->D, p->n, p->h, p->k, p->prec, nullptr) +
+                        (2 * (size_t)max_outer + 1) * sizeof(double);
+    if (b->cap_bytes && b->used + need > b->cap_bytes) return HELM_ENOMEM;
+    const int key = 2 * p->D + p->prec;
+    Engine* E = nullptr;
+    auto it = b->engines.find(key);
+    if (it == b->engines.end()) {
+        std::unique_ptr<Engine> ne(new Engine());
+        helm_status st = ne->init(p->D, p->prec);
+        if (st != HELM_OK) return st;
+        cudaStream_t es;
+        HELM_CK(cudaStreamCreateWithFlags(&es, cudaStreamNonBlocking));
+        cudaEvent_t ev;
+        HELM_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        b->eng_streams[key] = es;
+        b->join[key] = ev;
+        E = ne.get();
+        b->engines[key] = std::move(ne);
+    } else {
+        E = it->second.get();
+    }
+    int slot = -1;
+    for (int i = 0; i < E->cap; ++i)
+        if (!E->slots[i]) { slot = i; break; }
+    if (slot < 0) {
+        slot = E->cap;
+        helm_status st = E->grow(E->cap + 1);
+        if (st != HELM_OK) return st;
+    }
+    Instance* in = new Instance();
+    helm_status st = alloc_instance(*in, p->D, p->n, p->h, p->k, p->prec, max_outer, b->stream, true);
+    if (st != HELM_OK) { free_instance(*in, b->stream); delete in; return st; }
+    in->d.u[0] = (double2*)u;
+    in->d.f = (const double2*)f;
+    in->d.g = (const double2*)g;
+    in->d.tol = tol;
+    in->d.max_outer = max_outer;
+    E->slots[slot] = in;
+    E->dirty = true;
+    st = E->start_instance(slot, b->stream);
+    if (st != HELM_OK) return st;
+    helm_batch::Rec r;
+    r.key = key;
+    r.slot = slot;
+    r.inst = in;
+    r.u = u;
+    r.ubytes = ub;
+    const uint64_t t = b->next++;
+    b->recs[t] = r;
+    b->used += need;
+    *ticket = t;
+    return HELM_OK;
+}
+
+helm_status helm_batch_step(helm_batch* b, int max_steps)
+{
+    if (!b || max_steps < 0) return HELM_EINVAL;
+    // launch every engine with work on its own stream, forked from the batch stream
+    HELM_CK(cudaEventRecord(b->fork, b->stream));
+    std::vector<int> launched;
+    for (auto& kv : b->engines) {
+        Engine* E = kv.second.get();
+        if (E->active_count() == 0) continue;
+        cudaStream_t es = b->eng_streams[kv.first];
+        HELM_CK(cudaStreamWaitEvent(es, b->fork, 0));
+        helm_status st = E->prepare();
+        if (st != HELM_OK) return st;
+        E->h_ctrl[0] = 0;
+        E->h_ctrl[1] = max_steps > 0 ? max_steps : INT_MAX;
+        E->h_ctrl[2] = 1;
+        HELM_CK(cudaMemcpyAsync(E->d_ctrl, E->h_ctrl, 3 * sizeof(int), cudaMemcpyHostToDevice, es));
+        HELM_CK(cudaGraphLaunch(E->exec, es));
+        HELM_CK(cudaMemcpyAsync(E->h_ctrl, E->d_ctrl, 3 * sizeof(int), cudaMemcpyDeviceToHost, es));
+        HELM_CK(cudaMemcpyAsync(E->h_state, E->d_state, sizeof(InstState) * E->cap,
+                                cudaMemcpyDeviceToHost, es));
+        HELM_CK(cudaEventRecord(b->join[kv.first], es));
+        HELM_CK(cudaStreamWaitEvent(b->stream, b->join[kv.first], 0));
+        launched.push_back(kv.first);
+    }
+    HELM_CK(cudaStreamSynchronize(b->stream));
+    for (int key : launched) {
+        Engine* E = b->engines[key].get();
+        g_launches += (uint64_t)E->h_ctrl[0] * E->step.size();
+    }
+    // retire finished instances: result into the caller's u, histories to the host
+    std::vector<helm_batch::Rec*> fin;
+    for (auto& kv : b->recs) {
+        helm_batch::Rec& r = kv.second;
+        if (r.done || !r.inst) continue;
+        Engine* E = b->engines[r.key].get();
+        const InstState s = E->h_state[r.slot];
+        if (s.status == HELM_ST_ACTIVE || s.status == HELM_ST_IDLE) continue;
+        if (s.it & 1)
+            HELM_CK(cudaMemcpyAsync(r.u, r.inst->d.u[1], r.ubytes, cudaMemcpyDeviceToDevice, b->stream));
+        r.hist.resize(s.it + 1);
+        HELM_CK(cudaMemcpyAsync(r.hist.data(), r.inst->d.hist, (s.it + 1) * sizeof(double),
+                                cudaMemcpyDeviceToHost, b->stream));
+        r.status = s.status;
+        r.iters = s.it;
+        fin.push_back(&r);
+    }
+    if (fin.empty()) return HELM_OK;
+    HELM_CK(cudaStreamSynchronize(b->stream));
+    for (helm_batch::Rec* rp : fin) {
+        helm_batch::Rec& r = *rp;
+        Engine* E = b->engines[r.key].get();
+        E->h_state[r.slot].status = HELM_ST_IDLE;
+        HELM_CK(cudaMemcpyAsync(E->d_state + r.slot, &E->h_state[r.slot], sizeof(InstState),
+                                cudaMemcpyHostToDevice, b->stream));
+        InstDesc probe{};
+        b->used -= layout(probe, r.inst->d.D, r.inst->d.n, r.inst->d.h, 0.0, r.inst->prec, nullptr) +
+                   (2 * (size_t)r.inst->hist_cap + 1) * sizeof(double);
+        free_instance(*r.inst, b->stream);
+        delete r.inst;
+        r.inst = nullptr;
+        r.done = 1;
+        E->slots[r.slot] = nullptr;
+        E->dirty = true;
+    }
+    HELM_CK(cudaStreamSynchronize(b->stream));
+    return HELM_OK;
+}
+
+helm_status helm_batch_poll(helm_batch* b, uint64_t ticket, int* done, int* status, int* iters,
+                            double* res_hist)
+{
+    if (!b) return HELM_EINVAL;
+    auto it = b->recs.find(ticket);
+    if (it == b->recs.end()) return HELM_EINVAL;
+    helm_batch::Rec& r = it->second;
+    if (done) *done = r.done;
+    if (!r.done) return HELM_OK;
+    if (status) *status = r.status;
+    if (iters) *iters = r.iters;
+    if (res_hist) memcpy(res_hist, r.hist.data(), r.hist.size() * sizeof(double));
+    b->recs.erase(it);
+    return HELM_OK;
+}
+
+helm_status helm_batch_info(const helm_batch* b, int* active, size_t* bytes)
+{
+    if (!b) return HELM_EINVAL;
+    int a = 0;
+    for (auto& kv : b->recs) a += !kv.second.done;
+    if (active) *active = a;
+    if (bytes) *bytes = b->used;
+    return HELM_OK;
+}
+
+}  // extern "C"

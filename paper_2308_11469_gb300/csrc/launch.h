@@ -1,0 +1,56 @@
+// Host-side launchers of the library's kernels (one translation unit per kernel family).
+// Every launcher enqueues on `s` and returns the cudaError_t of the launch.
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace helm {
+
+// Tail-level bounds: levels with n <= these are solved inside one CTA in shared memory.
+constexpr int TAIL_N_2D = 63;
+constexpr int TAIL_N_3D = 15;
+
+// ---- multigrid (vcycle.cu); prec: 0 = double, 1 = float ----
+// mode 0: plain half-sweep; modes 1/2: first half-sweep of a pre-smoothing whose
+// iterate is known to be zero on levels > 0 (mode 1) or on every level (mode 2): it
+// writes both colours (this colour from rhs alone, the other colour as zero).
+cudaError_t launch_rbgs(int D, int prec, const InstDesc* insts, const InstState* st,
+                        const MgItem* items, int nitems, int work, int color, int mode,
+                        cudaStream_t s);
+// coarse rhs := full weighting of (rhs - Delta_h e) on level l, coarse e := 0
+cudaError_t launch_restrict(int D, int prec, const InstDesc* insts, const InstState* st,
+                            const MgItem* items, int nitems, int work, cudaStream_t s);
+// e_l += prolongation of e_{l+1}
+cudaError_t launch_prolong(int D, int prec, const InstDesc* insts, const InstState* st,
+                           const MgItem* items, int nitems, int work, cudaStream_t s);
+// zero the iterate of the listed levels (ring included)
+cudaError_t launch_zero(int D, int prec, const InstDesc* insts, const InstState* st,
+                        const MgItem* items, int nitems, int work, cudaStream_t s);
+// one CTA per item: V(nu1,nu2) on levels item.level..coarsest in shared memory.
+// load_e: start from the level's e in global memory instead of zero.
+cudaError_t launch_tail(int D, int prec, const InstDesc* insts, const InstState* st,
+                        const MgItem* items, int nitems, int nu1, int nu2, int load_e,
+                        int max_tail_n, cudaStream_t s);
+size_t tail_smem_bytes(int D, int prec, int n);
+// raise the tail kernel's dynamic shared-memory limit (once, before any capture)
+cudaError_t setup_tail(int D, int prec);
+
+// ---- outer FP64 iteration (outer.cu) ----
+// mode 0: r_0 from u[it&1]; mode 1: u[(it+1)&1] = u[it&1] + e_0, then r from it.
+// Writes r into level-0 rhs (inner precision) and per-tile partials.
+cudaError_t launch_residual(int D, int prec, const InstDesc* insts, const InstState* st,
+                            const ResItem* items, int nitems, int mode, cudaStream_t s);
+// Per-instance norms -> relres history, status rule; sets the while-loop condition.
+cudaError_t launch_check(const InstDesc* insts, InstState* st, int ninst, int mode,
+                         int* ctrl, int use_cond, unsigned long long cond_handle,
+                         cudaStream_t s);
+// u[0] and u[1] rings := g ring
+cudaError_t launch_set_ring(int D, const InstDesc* insts, const InstState* st, int inst,
+                            int n, cudaStream_t s);
+// interior tight <-> level-0 padded/pitched, inner precision
+cudaError_t launch_pack(int D, int prec, const InstDesc* insts, int inst, int n,
+                        const void* src, int which /*0 = e, 1 = rhs*/, cudaStream_t s);
+cudaError_t launch_unpack(int D, int prec, const InstDesc* insts, int inst, int n,
+                          void* dst, cudaStream_t s);
+
+}  // namespace helm

@@ -1,0 +1,514 @@
+// Geometric-multigrid kernels for the inner Poisson problem Delta_h e = rhs, e = 0 on
+// the wall: every outer step of the paper's iteration (Section 2.2, Eq. (2.6) with
+// alpha = k^2) is one such real Poisson problem per real/imaginary lane.  The paper
+// prescribes no inner solver; this file is the library's choice (see the header).
+//
+// Generic (any D in {2, 3}, float or double) kernels over lists of (instance, level)
+// work items, blocks striding over each item's nodes:
+//   k_rbgs      red-black Gauss-Seidel half-sweep (node colour = parity of the sum of
+//               its padded indices; red = 0); each updated node solves its own equation.
+//   k_restrict  coarse rhs = full weighting ([1,2,1]/4 per axis) of the fine residual
+//               rhs - Delta_h e, coarse iterate = 0.
+//   k_prolong   e_fine += multilinear interpolation of e_coarse.
+//   k_tail      one CTA per item runs the rest of the V-cycle (levels with n <= 63 in 2D,
+//               n <= 15 in 3D) entirely in shared memory, down to the one-node exact
+//               solve e = -h^2 rhs / (2D).
+#include "launch.h"
+
+namespace helm {
+namespace {
+
+template <int D>
+__device__ __forceinline__ size_t off(const LevelDesc& L, int x, int y, int z) {
+    return ((D == 3) ? ((size_t)z * L.rows + y) : (size_t)y) * (size_t)L.pitch + x;
+}
+
+template <typename T> __device__ __forceinline__ T cz() { T v; v.x = 0; v.y = 0; return v; }
+
+// ---------------------------------------------------------------------------
+// Red-black Gauss-Seidel half-sweep
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__global__ void __launch_bounds__(256)
+k_rbgs(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
+       const MgItem* __restrict__ items, int color, int mode)
+{
+    typedef typename C2<R>::T c2;
+    const MgItem item = items[blockIdx.y];
+    if (st[item.inst].status != HELM_ST_ACTIVE) return;
+    const LevelDesc L = insts[item.inst].lev[item.level];
+    const int n = L.n, half = (n + 1) >> 1;
+    const int rows = (D == 3) ? n * n : n;
+    const long total = (long)rows * half;
+    c2* __restrict__ e = (c2*)L.e;
+    const c2* __restrict__ r = (const c2*)L.rhs;
+    const long P = L.pitch;
+    const long PL = (long)L.pitch * L.rows;
+    const R h2 = (R)(L.h * L.h);
+    const R inv = (R)1 / (R)(2 * D);
+    // mode 2: the iterate of every level is zero; mode 1: only levels > 0 are (their
+    // iterate was cleared by the restriction); mode 0: plain half-sweep.
+    const bool zi = (mode == 2) || (mode == 1 && item.level > 0);
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
+         q += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(q % half);
+        const int row = (int)(q / half);
+        const int y = (D == 3) ? row % n + 1 : row + 1;
+        const int z = (D == 3) ? row / n + 1 : 0;
+        const int xa = 2 * j + 1;                       // pair {xa, xa + 1}
+        const int xc = (((xa + y + z) & 1) == color) ? xa : xa + 1;
+        const int xo = (xc == xa) ? xa + 1 : xa;
+        if (xc <= n) {
+            const long o = (long)off<D>(L, xc, y, z);
+            const c2 rr = r[o];
+            c2 v;
+            if (zi) {                                   // all neighbours are zero
+                v.x = -h2 * rr.x * inv;
+                v.y = -h2 * rr.y * inv;
+            } else {
+                const c2 a = e[o - 1], b = e[o + 1], c = e[o - P], d = e[o + P];
+                R sx = a.x + b.x + c.x + d.x;
+                R sy = a.y + b.y + c.y + d.y;
+                if (D == 3) {
+                    const c2 f = e[o - PL], g = e[o + PL];
+                    sx += f.x + g.x;
+                    sy += f.y + g.y;
+                }
+                v.x = (sx - h2 * rr.x) * inv;
+                v.y = (sy - h2 * rr.y) * inv;
+            }
+            e[o] = v;
+        }
+        if (zi && xo <= n) e[off<D>(L, xo, y, z)] = cz<c2>();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Residual + full-weighting restriction
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__global__ void __launch_bounds__(256)
+k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
+           const MgItem* __restrict__ items)
+{
+    typedef typename C2<R>::T c2;
+    const MgItem item = items[blockIdx.y];
+    if (st[item.inst].status != HELM_ST_ACTIVE) return;
+    const LevelDesc F = insts[item.inst].lev[item.level];
+    const LevelDesc C = insts[item.inst].lev[item.level + 1];
+    const int nc = C.n;
+    const long total = (D == 3) ? (long)nc * nc * nc : (long)nc * nc;
+    const c2* __restrict__ e = (const c2*)F.e;
+    const c2* __restrict__ r = (const c2*)F.rhs;
+    c2* __restrict__ cr = (c2*)C.rhs;
+    c2* __restrict__ ce = (c2*)C.e;
+    const long P = F.pitch;
+    const long PL = (long)F.pitch * F.rows;
+    const R ih2 = (R)(1.0 / (F.h * F.h));
+    const R scale = (D == 3) ? (R)(1.0 / 64.0) : (R)(1.0 / 16.0);
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
+         q += (long)gridDim.x * blockDim.x) {
+        const int X = (int)(q % nc) + 1;
+        const int Y = (int)((q / nc) % nc) + 1;
+        const int Z = (D == 3) ? (int)(q / ((long)nc * nc)) + 1 : 0;
+        R ax = 0, ay = 0;
+        const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
+        for (int dz = zlo; dz <= zhi; ++dz) {
+            const R wz = (D == 3) ? (dz == 0 ? (R)2 : (R)1) : (R)1;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const R wy = (dy == 0) ? (R)2 : (R)1;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const R w = wz * wy * ((dx == 0) ? (R)2 : (R)1);
+                    const long o = (long)off<D>(F, 2 * X + dx, 2 * Y + dy, 2 * Z + dz);
+                    const c2 c = e[o], a = e[o - 1], b = e[o + 1], u = e[o - P], d = e[o + P];
+                    R sx = a.x + b.x + u.x + d.x;
+                    R sy = a.y + b.y + u.y + d.y;
+                    if (D == 3) {
+                        const c2 f = e[o - PL], g = e[o + PL];
+                        sx += f.x + g.x;
+                        sy += f.y + g.y;
+                    }
+                    const c2 rr = r[o];
+                    ax += w * (rr.x - (sx - (R)(2 * D) * c.x) * ih2);
+                    ay += w * (rr.y - (sy - (R)(2 * D) * c.y) * ih2);
+                }
+            }
+        }
+        const size_t oc = off<D>(C, X, Y, Z);
+        c2 v;
+        v.x = ax * scale;
+        v.y = ay * scale;
+        cr[oc] = v;
+        ce[oc] = cz<c2>();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Multilinear prolongation + correction
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__global__ void __launch_bounds__(256)
+k_prolong(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
+          const MgItem* __restrict__ items)
+{
+    typedef typename C2<R>::T c2;
+    const MgItem item = items[blockIdx.y];
+    if (st[item.inst].status != HELM_ST_ACTIVE) return;
+    const LevelDesc F = insts[item.inst].lev[item.level];
+    const LevelDesc C = insts[item.inst].lev[item.level + 1];
+    const int n = F.n;
+    const long total = (D == 3) ? (long)n * n * n : (long)n * n;
+    c2* __restrict__ e = (c2*)F.e;
+    const c2* __restrict__ ce = (const c2*)C.e;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
+         q += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(q % n) + 1;
+        const int y = (int)((q / n) % n) + 1;
+        const int z = (D == 3) ? (int)(q / ((long)n * n)) + 1 : 0;
+        // per axis: even fine index -> one coarse node (weight 1), odd -> two (1/2 each)
+        const int x0 = x >> 1, x1 = (x + 1) >> 1;
+        const int y0 = y >> 1, y1 = (y + 1) >> 1;
+        const int z0 = z >> 1, z1 = (z + 1) >> 1;
+        R vx = 0, vy = 0;
+        const int nz = (D == 3) ? 2 : 1;
+        for (int iz = 0; iz < nz; ++iz) {
+            const int Z = iz ? z1 : z0;
+            for (int iy = 0; iy < 2; ++iy) {
+                const int Y = iy ? y1 : y0;
+                for (int ix = 0; ix < 2; ++ix) {
+                    const int X = ix ? x1 : x0;
+                    const c2 c = ce[off<D>(C, X, Y, Z)];
+                    vx += c.x;
+                    vy += c.y;
+                }
+            }
+        }
+        // each of the 2^D corner reads counts 1/2^D; coincident corners (even index)
+        // are read twice, which gives the weight 1 of an even fine index.
+        const R w = (D == 3) ? (R)0.125 : (R)0.25;
+        const long o = (long)off<D>(F, x, y, z);
+        c2 v = e[o];
+        v.x += w * vx;
+        v.y += w * vy;
+        e[o] = v;
+    }
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(256)
+k_zero(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
+       const MgItem* __restrict__ items)
+{
+    typedef typename C2<R>::T c2;
+    const MgItem item = items[blockIdx.y];
+    if (st[item.inst].status != HELM_ST_ACTIVE) return;
+    const LevelDesc L = insts[item.inst].lev[item.level];
+    const long total = (D == 3) ? (long)L.pitch * L.rows * L.rows : (long)L.pitch * L.rows;
+    c2* __restrict__ e = (c2*)L.e;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
+         q += (long)gridDim.x * blockDim.x)
+        e[q] = cz<c2>();
+}
+
+// ---------------------------------------------------------------------------
+// Tail: the coarse part of the V-cycle inside one CTA (shared memory)
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ int sidx(int n, int x, int y, int z) {
+    const int s = n + 2;
+    return ((D == 3) ? (z * s + y) : y) * s + x;
+}
+
+template <int D, typename R>
+__device__ void tail_half_sweep(typename C2<R>::T* e, const typename C2<R>::T* r, int n, R h,
+                                int color)
+{
+    typedef typename C2<R>::T c2;
+    const int half = (n + 1) >> 1;
+    const int rows = (D == 3) ? n * n : n;
+    const int total = rows * half;
+    const int s = n + 2, sp = s * s;
+    const R h2 = h * h;
+    const R inv = (R)1 / (R)(2 * D);
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        const int j = q % half;
+        const int row = q / half;
+        const int y = (D == 3) ? row % n + 1 : row + 1;
+        const int z = (D == 3) ? row / n + 1 : 0;
+        const int xa = 2 * j + 1;
+        const int xc = (((xa + y + z) & 1) == color) ? xa : xa + 1;
+        if (xc > n) continue;
+        const int o = sidx<D>(n, xc, y, z);
+        const c2 a = e[o - 1], b = e[o + 1], c = e[o - s], d = e[o + s];
+        R sx = a.x + b.x + c.x + d.x;
+        R sy = a.y + b.y + c.y + d.y;
+        if (D == 3) {
+            const c2 f = e[o - sp], g = e[o + sp];
+            sx += f.x + g.x;
+            sy += f.y + g.y;
+        }
+        const c2 rr = r[o];
+        c2 v;
+        v.x = (sx - h2 * rr.x) * inv;
+        v.y = (sy - h2 * rr.y) * inv;
+        e[o] = v;
+    }
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(512)
+k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
+       const MgItem* __restrict__ items, int nu1, int nu2, int load_e)
+{
+    typedef typename C2<R>::T c2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    c2* base = reinterpret_cast<c2*>(smem_raw);
+    const MgItem item = items[blockIdx.x];
+    if (st[item.inst].status != HELM_ST_ACTIVE) return;
+    const LevelDesc L0 = insts[item.inst].lev[item.level];
+    const int n0 = L0.n;
+    c2* E[8];
+    c2* Rr[8];
+    int N[8];
+    int T = 0;
+    int total = 0;
+    for (int m = n0; m >= 1 && T < 8; m = (m - 1) >> 1) {
+        const int sz = (D == 3) ? (m + 2) * (m + 2) * (m + 2) : (m + 2) * (m + 2);
+        N[T] = m;
+        E[T] = base + total;
+        total += sz;
+        Rr[T] = base + total;
+        total += sz;
+        ++T;
+    }
+    for (int i = threadIdx.x; i < total; i += blockDim.x) base[i] = cz<c2>();
+    __syncthreads();
+    {
+        const c2* gr = (const c2*)L0.rhs;
+        const c2* ge = (const c2*)L0.e;
+        const int tot = (D == 3) ? n0 * n0 * n0 : n0 * n0;
+        for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+            const int x = q % n0 + 1;
+            const int y = (q / n0) % n0 + 1;
+            const int z = (D == 3) ? q / (n0 * n0) + 1 : 0;
+            const size_t g = off<D>(L0, x, y, z);
+            const int s = sidx<D>(n0, x, y, z);
+            Rr[0][s] = gr[g];
+            if (load_e && item.level == 0) E[0][s] = ge[g];
+        }
+    }
+    __syncthreads();
+    R h = (R)L0.h;
+    // descent
+    for (int t = 0; t + 1 < T; ++t) {
+        const int n = N[t];
+        for (int it = 0; it < nu1; ++it) {
+            tail_half_sweep<D, R>(E[t], Rr[t], n, h, 0);
+            __syncthreads();
+            tail_half_sweep<D, R>(E[t], Rr[t], n, h, 1);
+            __syncthreads();
+        }
+        // restriction of the residual into Rr[t+1]
+        const int nc = N[t + 1];
+        const int tot = (D == 3) ? nc * nc * nc : nc * nc;
+        const int s = n + 2, sp = s * s;
+        const R ih2 = (R)1 / (h * h);
+        const R scale = (D == 3) ? (R)(1.0 / 64.0) : (R)(1.0 / 16.0);
+        for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+            const int X = q % nc + 1;
+            const int Y = (q / nc) % nc + 1;
+            const int Z = (D == 3) ? q / (nc * nc) + 1 : 0;
+            R ax = 0, ay = 0;
+            const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
+            for (int dz = zlo; dz <= zhi; ++dz) {
+                const R wz = (D == 3) ? (dz == 0 ? (R)2 : (R)1) : (R)1;
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const R wy = (dy == 0) ? (R)2 : (R)1;
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const R w = wz * wy * ((dx == 0) ? (R)2 : (R)1);
+                        const int o = sidx<D>(n, 2 * X + dx, 2 * Y + dy, 2 * Z + dz);
+                        const c2* e = E[t];
+                        const c2 c = e[o], a = e[o - 1], b = e[o + 1], u = e[o - s], d = e[o + s];
+                        R sx = a.x + b.x + u.x + d.x;
+                        R sy = a.y + b.y + u.y + d.y;
+                        if (D == 3) {
+                            const c2 f = e[o - sp], g = e[o + sp];
+                            sx += f.x + g.x;
+                            sy += f.y + g.y;
+                        }
+                        const c2 rr = Rr[t][o];
+                        ax += w * (rr.x - (sx - (R)(2 * D) * c.x) * ih2);
+                        ay += w * (rr.y - (sy - (R)(2 * D) * c.y) * ih2);
+                    }
+                }
+            }
+            c2 v;
+            v.x = ax * scale;
+            v.y = ay * scale;
+            Rr[t + 1][sidx<D>(nc, X, Y, Z)] = v;
+        }
+        __syncthreads();
+        h = h * (R)2;
+    }
+    // coarsest level: one node, exact
+    if (threadIdx.x == 0) {
+        const int o = sidx<D>(1, 1, 1, 1);
+        const c2 rr = Rr[T - 1][o];
+        const R c = -(h * h) / (R)(2 * D);
+        c2 v;
+        v.x = c * rr.x;
+        v.y = c * rr.y;
+        E[T - 1][o] = v;
+    }
+    __syncthreads();
+    // ascent
+    for (int t = T - 2; t >= 0; --t) {
+        h = h * (R)0.5;
+        const int n = N[t];
+        const int nc = N[t + 1];
+        const int tot = (D == 3) ? n * n * n : n * n;
+        for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+            const int x = q % n + 1;
+            const int y = (q / n) % n + 1;
+            const int z = (D == 3) ? q / (n * n) + 1 : 0;
+            const int x0 = x >> 1, x1 = (x + 1) >> 1;
+            const int y0 = y >> 1, y1 = (y + 1) >> 1;
+            const int z0 = z >> 1, z1 = (z + 1) >> 1;
+            R vx = 0, vy = 0;
+            const int nz = (D == 3) ? 2 : 1;
+            for (int iz = 0; iz < nz; ++iz)
+                for (int iy = 0; iy < 2; ++iy)
+                    for (int ix = 0; ix < 2; ++ix) {
+                        const c2 c = E[t + 1][sidx<D>(nc, ix ? x1 : x0, iy ? y1 : y0,
+                                                      iz ? z1 : z0)];
+                        vx += c.x;
+                        vy += c.y;
+                    }
+            const R w = (D == 3) ? (R)0.125 : (R)0.25;
+            const int o = sidx<D>(n, x, y, z);
+            c2 v = E[t][o];
+            v.x += w * vx;
+            v.y += w * vy;
+            E[t][o] = v;
+        }
+        __syncthreads();
+        for (int it = 0; it < nu2; ++it) {
+            tail_half_sweep<D, R>(E[t], Rr[t], n, h, 0);
+            __syncthreads();
+            tail_half_sweep<D, R>(E[t], Rr[t], n, h, 1);
+            __syncthreads();
+        }
+    }
+    {
+        c2* ge = (c2*)L0.e;
+        const int tot = (D == 3) ? n0 * n0 * n0 : n0 * n0;
+        for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+            const int x = q % n0 + 1;
+            const int y = (q / n0) % n0 + 1;
+            const int z = (D == 3) ? q / (n0 * n0) + 1 : 0;
+            ge[off<D>(L0, x, y, z)] = E[0][sidx<D>(n0, x, y, z)];
+        }
+    }
+}
+
+inline dim3 mg_grid(int work, int nitems) {
+    int bx = (work + 255) / 256;
+    if (bx < 1) bx = 1;
+    if (bx > 1216) bx = 1216;   // 152 SMs x 8 blocks; blocks stride over larger levels
+    return dim3(bx, nitems);
+}
+
+}  // namespace
+
+cudaError_t launch_rbgs(int D, int prec, const InstDesc* insts, const InstState* st,
+                        const MgItem* items, int nitems, int work, int color, int mode,
+                        cudaStream_t s)
+{
+    dim3 g = mg_grid(work, nitems);
+    if (D == 2 && prec == 0) k_rbgs<2, double><<<g, 256, 0, s>>>(insts, st, items, color, mode);
+    else if (D == 2) k_rbgs<2, float><<<g, 256, 0, s>>>(insts, st, items, color, mode);
+    else if (prec == 0) k_rbgs<3, double><<<g, 256, 0, s>>>(insts, st, items, color, mode);
+    else k_rbgs<3, float><<<g, 256, 0, s>>>(insts, st, items, color, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(int D, int prec, const InstDesc* insts, const InstState* st,
+                            const MgItem* items, int nitems, int work, cudaStream_t s)
+{
+    dim3 g = mg_grid(work, nitems);
+    if (D == 2 && prec == 0) k_restrict<2, double><<<g, 256, 0, s>>>(insts, st, items);
+    else if (D == 2) k_restrict<2, float><<<g, 256, 0, s>>>(insts, st, items);
+    else if (prec == 0) k_restrict<3, double><<<g, 256, 0, s>>>(insts, st, items);
+    else k_restrict<3, float><<<g, 256, 0, s>>>(insts, st, items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(int D, int prec, const InstDesc* insts, const InstState* st,
+                           const MgItem* items, int nitems, int work, cudaStream_t s)
+{
+    dim3 g = mg_grid(work, nitems);
+    if (D == 2 && prec == 0) k_prolong<2, double><<<g, 256, 0, s>>>(insts, st, items);
+    else if (D == 2) k_prolong<2, float><<<g, 256, 0, s>>>(insts, st, items);
+    else if (prec == 0) k_prolong<3, double><<<g, 256, 0, s>>>(insts, st, items);
+    else k_prolong<3, float><<<g, 256, 0, s>>>(insts, st, items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero(int D, int prec, const InstDesc* insts, const InstState* st,
+                        const MgItem* items, int nitems, int work, cudaStream_t s)
+{
+    dim3 g = mg_grid(work, nitems);
+    if (D == 2 && prec == 0) k_zero<2, double><<<g, 256, 0, s>>>(insts, st, items);
+    else if (D == 2) k_zero<2, float><<<g, 256, 0, s>>>(insts, st, items);
+    else if (prec == 0) k_zero<3, double><<<g, 256, 0, s>>>(insts, st, items);
+    else k_zero<3, float><<<g, 256, 0, s>>>(insts, st, items);
+    return cudaGetLastError();
+}
+
+size_t tail_smem_bytes(int D, int prec, int n)
+{
+    size_t elem = prec == 0 ? 16 : 8;
+    size_t tot = 0;
+    for (int m = n; m >= 1; m = (m - 1) >> 1) {
+        size_t s = (size_t)(m + 2);
+        tot += 2 * ((D == 3) ? s * s * s : s * s);
+    }
+    return tot * elem;
+}
+
+template <int D, typename R>
+static cudaError_t tail_launch(const InstDesc* insts, const InstState* st, const MgItem* items,
+                               int nitems, int nu1, int nu2, int load_e, int max_n,
+                               cudaStream_t s)
+{
+    const size_t smem = tail_smem_bytes(D, sizeof(R) == 8 ? 0 : 1, max_n);
+    k_tail<D, R><<<nitems, 512, smem, s>>>(insts, st, items, nu1, nu2, load_e);
+    return cudaGetLastError();
+}
+
+template <int D, typename R>
+static cudaError_t tail_attr()
+{
+    const size_t smem = tail_smem_bytes(D, sizeof(R) == 8 ? 0 : 1, D == 2 ? TAIL_N_2D : TAIL_N_3D);
+    return cudaFuncSetAttribute(k_tail<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t setup_tail(int D, int prec)
+{
+    if (D == 2 && prec == 0) return tail_attr<2, double>();
+    if (D == 2) return tail_attr<2, float>();
+    if (prec == 0) return tail_attr<3, double>();
+    return tail_attr<3, float>();
+}
+
+cudaError_t launch_tail(int D, int prec, const InstDesc* insts, const InstState* st,
+                        const MgItem* items, int nitems, int nu1, int nu2, int load_e,
+                        int max_tail_n, cudaStream_t s)
+{
+    if (D == 2 && prec == 0) return tail_launch<2, double>(insts, st, items, nitems, nu1, nu2, load_e, max_tail_n, s);
+    if (D == 2) return tail_launch<2, float>(insts, st, items, nitems, nu1, nu2, load_e, max_tail_n, s);
+    if (prec == 0) return tail_launch<3, double>(insts, st, items, nitems, nu1, nu2, load_e, max_tail_n, s);
+    return tail_launch<3, float>(insts, st, items, nitems, nu1, nu2, load_e, max_tail_n, s);
+}
+
+}  // namespace helm

@@ -1,0 +1,139 @@
+"""GPU batch / serving path: each result is the same alone and in the mix.
+
+Instances in a batch share every launch, but each one's arithmetic depends only on its
+own data (fixed tile partials, no cross-instance reduction), so results must be
+bit-identical to the single-solve path; admission respects the memory cap.
+"""
+import numpy as np
+import pytest
+
+from oracle import fd
+from paper_2308_11469_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_11469_gb300 import binding, build
+    build.build()
+    binding.load()
+    return binding
+
+
+def _solo(B, p, prec, tol, max_outer):
+    plan = B.helm_plan_create(p.D, p.n, p.h, p.k, prec=prec)
+    f = torch.from_numpy(p.f).to(DEV)
+    g = torch.from_numpy(p.g).to(DEV)
+    u = torch.zeros_like(g)
+    st, iters, hist = B.helm_solve(plan, f, g, u, tol, max_outer)
+    B.helm_plan_destroy(plan)
+    return st, iters, hist, u.cpu().numpy()
+
+
+def _mix():
+    probs = inputs.batched_instances(count=10, seed=4, sizes=(15, 31, 63, 127, 255))
+    probs.append(inputs.plane_wave_sine_cube(3.0, seed=3, n=15))
+    probs.append(inputs.plane_wave_sine_cube(4.0, seed=5, n=31))
+    probs.append(inputs.plane_wave_cavity_2d(2.0))
+    return probs
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_batch_equals_solo(B, prec):
+    probs = _mix()
+    tol, max_outer = 1e-8, 2000
+    batch = B.helm_batch_create(0)
+    keep = []
+    tickets = []
+    for p in probs:
+        plan = B.helm_plan_create(p.D, p.n, p.h, p.k, prec=prec)
+        f = torch.from_numpy(p.f).to(DEV)
+        g = torch.from_numpy(p.g).to(DEV)
+        u = torch.zeros_like(g)
+        keep.append((f, g, u))
+        tickets.append(B.helm_batch_submit(batch, plan, f, g, u, tol, max_outer))
+        B.helm_plan_destroy(plan)          # the batch copied what it needs
+    assert all(t is not None for t in tickets)
+    results = [None] * len(probs)
+    for _ in range(10000):
+        B.helm_batch_step(batch, 7)
+        for i, t in enumerate(tickets):
+            if results[i] is None:
+                r = B.helm_batch_poll(batch, t, max_outer)
+                if r is not None:
+                    results[i] = r
+        if all(r is not None for r in results):
+            break
+    assert B.helm_batch_info(batch) == (0, 0)
+    B.helm_batch_destroy(batch)
+    for i, p in enumerate(probs):
+        st, iters, hist = results[i]
+        s2, it2, h2, u2 = _solo(B, p, prec, tol, max_outer)
+        assert st == s2 == B.HELM_CONVERGED
+        assert iters == it2
+        assert np.array_equal(hist, h2)
+        assert np.array_equal(keep[i][2].cpu().numpy(), u2)
+        exact = fd.solve_exact_dst(p.f, p.g, p.h, p.k)
+        err = np.linalg.norm(u2 - exact) / np.linalg.norm(exact)
+        assert err <= (1e-6 if prec == 1 else 1e-7), (i, err)
+
+
+def test_admission_cap(B):
+    p = inputs.gaussian_cavity_2d(2.0, n=255)
+    plan = B.helm_plan_create(2, 255, p.h, p.k, prec=1)
+    lm, km, rho, ws = B.helm_plan_info(plan)
+    f = torch.from_numpy(p.f).to(DEV)
+    g = torch.from_numpy(p.g).to(DEV)
+    us = [torch.zeros_like(g) for _ in range(3)]
+    batch = B.helm_batch_create(int(ws * 2.5))
+    t0 = B.helm_batch_submit(batch, plan, f, g, us[0], 1e-8, 200)
+    t1 = B.helm_batch_submit(batch, plan, f, g, us[1], 1e-8, 200)
+    t2 = B.helm_batch_submit(batch, plan, f, g, us[2], 1e-8, 200)
+    assert t0 is not None and t1 is not None and t2 is None       # over the cap
+    active, used = B.helm_batch_info(batch)
+    assert active == 2 and 0 < used <= ws * 2.5
+    B.helm_batch_step(batch, 0)
+    assert B.helm_batch_poll(batch, t0, 200) is not None
+    assert B.helm_batch_poll(batch, t1, 200) is not None
+    t2 = B.helm_batch_submit(batch, plan, f, g, us[2], 1e-8, 200)  # room again
+    assert t2 is not None
+    B.helm_batch_step(batch, 0)
+    r2 = B.helm_batch_poll(batch, t2, 200)
+    assert r2 is not None and r2[0] == B.HELM_CONVERGED
+    assert torch.equal(us[0], us[2])
+    B.helm_batch_destroy(batch)
+    B.helm_plan_destroy(plan)
+
+
+def test_late_arrivals_join_running_batch(B):
+    # continuous batching: a solve submitted while another is mid-flight gives the
+    # same result as alone
+    a = inputs.gaussian_cavity_2d(4.0, n=127)
+    b = inputs.gaussian_cavity_2d(3.0, seed=9, n=63)
+    batch = B.helm_batch_create(0)
+    bufs = []
+    for p in (a, b):
+        f = torch.from_numpy(p.f).to(DEV)
+        g = torch.from_numpy(p.g).to(DEV)
+        bufs.append((f, g, torch.zeros_like(g)))
+    pa = B.helm_plan_create(2, a.n, a.h, a.k, prec=1)
+    pb = B.helm_plan_create(2, b.n, b.h, b.k, prec=1)
+    ta = B.helm_batch_submit(batch, pa, *bufs[0], 1e-8, 500)
+    B.helm_batch_step(batch, 5)
+    assert B.helm_batch_poll(batch, ta, 500) is None
+    tb = B.helm_batch_submit(batch, pb, *bufs[1], 1e-8, 500)
+    B.helm_batch_step(batch, 0)
+    ra = B.helm_batch_poll(batch, ta, 500)
+    rb = B.helm_batch_poll(batch, tb, 500)
+    for p, r, buf in ((a, ra, bufs[0]), (b, rb, bufs[1])):
+        st, iters, hist, u = _solo(B, p, 1, 1e-8, 500)
+        assert r[0] == st and r[1] == iters
+        assert np.array_equal(r[2], hist)
+        assert np.array_equal(buf[2].cpu().numpy(), u)
+    B.helm_batch_destroy(batch)
