@@ -1,0 +1,384 @@
+"""Benchmark: solves/s of the FP Poisson iteration on the 1023x1023 Gaussian cavity.
+
+Workload (one "step"): the four solves k in {1, 2, 3, 4} of the 1023x1023 unit-square
+Dirichlet cavity (h = 1/1024, g = 0, f = 8 seeded Gaussians of width 0.02) to
+relres 1e-8.
+
+* headline (``value``): mixed precision -- complex64 multigrid V-cycles, complex128
+  residual and solution (iterative refinement) -- the four solves advanced together
+  as one batch (one launch per kernel covers all active instances, each solve retires
+  when it converges), a whole batch step being one CUDA-graph launch.
+* ``fp64_single``: the plain FP64 form, each solve alone (complex128 everywhere).
+* ``e2e``: the headline measured through the public API with host buffers: pinned
+  host -> device copies of f and g, the solves, device -> host copy of u, every step.
+* ``roofline``: the kernel with the largest device-time share, from a replay of one
+  step with every launch bracketed by CUDA events on the launching stream.
+* ``cpu_baseline``: the CPU oracle (exact sine-basis Poisson solves, all host cores).
+
+Under torchrun each rank solves its own copy of the workload (weak scaling, no
+collective on the data path).  ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+KS = (1.0, 2.0, 3.0, 4.0)
+N_GRID = 1023
+TOL = 1e-8
+MAX_OUTER = 2000
+METRIC = "solves/s & stencil HBM GB/s (%peak) at relres 1e-8, mixed vs FP64; p50/p99"
+WORKLOAD = "gaussian_cavity_2d_1023_k1234"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_oracle_workload(problems, max_seconds: float = 60.0):
+    """The oracle on the bench workload: exact sine-basis inner solves on every host
+    core; also the exact discrete solutions used to state each result's error."""
+    from oracle import fd, iteration as it
+    workers = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    iters = []
+    times = []
+    for p in problems:
+        t = time.perf_counter()
+        r = it.paper_iteration(p.f, p.g, p.h, p.k, tol=TOL, max_outer=MAX_OUTER, poisson="dst",
+                               workers=workers)
+        times.append(time.perf_counter() - t)
+        iters.append(r.iters)
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    exact = [fd.solve_exact_dst(p.f, p.g, p.h, p.k, workers=workers) for p in problems]
+    return times, iters, exact, workers
+
+
+def run_reference(args):
+    """CPU oracle arm: each step solves one k of the workload (rotating), so the run stays
+    within minutes; solves/s = 4 / sum over k of the mean time of that k's solves."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import iteration as it
+    from paper_2308_11469_gb300 import inputs
+    problems = [inputs.gaussian_cavity_2d(k) for k in KS]
+    workers = os.cpu_count() or 1
+    nsteps = max(args.steps, len(KS))
+    for w in range(min(args.warmup, 1)):
+        p = problems[0]
+        it.paper_iteration(p.f, p.g, p.h, p.k, tol=TOL, max_outer=MAX_OUTER, poisson="dst",
+                           workers=workers)
+    per_k = {k: [] for k in KS}
+    for s in range(nsteps):
+        p = problems[s % len(KS)]
+        t = time.perf_counter()
+        it.paper_iteration(p.f, p.g, p.h, p.k, tol=TOL, max_outer=MAX_OUTER, poisson="dst",
+                           workers=workers)
+        per_k[p.k].append(time.perf_counter() - t)
+    t_work = sum(float(np.mean(v)) for v in per_k.values())
+    value = len(KS) / t_work
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": ws, "steps": nsteps, "warmup": min(args.warmup, 1),
+        "ms_per_step": 1e3 * t_work / len(KS), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_GRID, "k": list(KS), "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": workers, "kind": "oracle",
+                         "sample": f"{nsteps} oracle solves (exact sine-basis inner solves), k "
+                                   f"rotating over {list(KS)}; value = 4 / sum_k mean time"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2308_11469_gb300 import binding as B
+    from paper_2308_11469_gb300 import build as _build
+    from paper_2308_11469_gb300 import inputs
+    _build.build()
+    B.load()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    problems = [inputs.gaussian_cavity_2d(k) for k in KS]
+    n = N_GRID
+    h = problems[0].h
+    F = [torch.from_numpy(p.f).to(dev) for p in problems]
+    G = [torch.from_numpy(p.g).to(dev) for p in problems]
+    U = [torch.zeros_like(g) for g in G]
+    mixed_plans = [B.helm_plan_create(2, n, h, k, prec=B.HELM_PREC_MIXED) for k in KS]
+    fp64_plans = [B.helm_plan_create(2, n, h, k, prec=B.HELM_PREC_FP64) for k in KS]
+    batch = B.helm_batch_create(120 << 30)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def mixed_step(Fs=F, Gs=G, Us=U):
+        for u in Us:
+            u.zero_()
+        tickets = [B.helm_batch_submit(batch, mixed_plans[i], Fs[i], Gs[i], Us[i], TOL, MAX_OUTER)
+                   for i in range(len(KS))]
+        B.helm_batch_step(batch, 0)
+        out = [B.helm_batch_poll(batch, t, MAX_OUTER) for t in tickets]
+        return out
+
+    def fp64_step():
+        out = []
+        for i in range(len(KS)):
+            U[i].zero_()
+            out.append(B.helm_solve(fp64_plans[i], F[i], G[i], U[i], TOL, MAX_OUTER))
+        return out
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        barrier()
+        times = []
+        last = None
+        for _ in range(steps):
+            flush.fill_(1)                          # evict L2 between timed steps
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record()
+            last = fn()
+            e.record()
+            e.synchronize()
+            times.append(s.elapsed_time(e))
+        barrier()
+        return times, last
+
+    # ---- headline: mixed batch ----
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = B.helm_launch_count()
+    t_mixed, res_mixed = timed(mixed_step, args.steps, args.warmup)
+    launches = (B.helm_launch_count() - l0)
+    clocks = sampler.stop()
+    l1 = B.helm_launch_count()
+    mixed_step()
+    launches_per_step = B.helm_launch_count() - l1
+    total_ms = max_over_ranks(float(np.sum(t_mixed)))
+    value = ws * len(KS) * args.steps / (total_ms / 1e3)
+    mixed_u = [u.cpu().numpy() for u in U]
+    mixed_iters = [r[1] for r in res_mixed]
+    mixed_status = [B.helm_status_str(r[0]) for r in res_mixed]
+
+    # ---- plain FP64, each solve alone ----
+    fp64 = None
+    fp64_u = None
+    if not args.no_fp64:
+        t_fp64, res_fp64 = timed(fp64_step, max(2, args.steps // 2), min(args.warmup, 2))
+        tot64 = max_over_ranks(float(np.sum(t_fp64)))
+        fp64 = {"value": ws * len(KS) * len(t_fp64) / (tot64 / 1e3), "unit": "solves/s",
+                "ms_per_step": tot64 / len(t_fp64),
+                "iters": [r[1] for r in res_fp64],
+                "status": [B.helm_status_str(r[0]) for r in res_fp64]}
+        fp64_u = [u.cpu().numpy() for u in U]
+
+    # ---- end to end through the public API with host buffers ----
+    Fh = [torch.from_numpy(p.f).pin_memory() for p in problems]
+    Gh = [torch.from_numpy(p.g).pin_memory() for p in problems]
+    Uh = [torch.empty(g.shape, dtype=g.dtype).pin_memory() for g in Gh]
+    Fd = [torch.empty_like(f) for f in F]
+    Gd = [torch.empty_like(g) for g in G]
+    Ud = [torch.empty_like(u) for u in U]
+
+    def e2e_step():
+        for i in range(len(KS)):
+            Fd[i].copy_(Fh[i], non_blocking=True)
+            Gd[i].copy_(Gh[i], non_blocking=True)
+        out = mixed_step(Fd, Gd, Ud)
+        for i in range(len(KS)):
+            Uh[i].copy_(Ud[i], non_blocking=True)
+        return out
+
+    t_e2e, _ = timed(e2e_step, max(2, args.steps // 2), 1)
+    tot_e2e = max_over_ranks(float(np.sum(t_e2e)))
+    h2d = sum(f.numel() * 16 + g.numel() * 16 for f, g in zip(Fh, Gh))
+    d2h = sum(u.numel() * 16 for u in Uh)
+    e2e = {"value": ws * len(KS) * len(t_e2e) / (tot_e2e / 1e3), "unit": "solves/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # ---- per-kernel replay of one step (events around every launch) ----
+    for u in U:
+        u.zero_()
+    tickets = [B.helm_batch_submit(batch, mixed_plans[i], F[i], G[i], U[i], TOL, MAX_OUTER)
+               for i in range(len(KS))]
+    prof = B.helm_batch_profile(batch, 0)
+    for t in tickets:
+        B.helm_batch_poll(batch, t, MAX_OUTER)
+    total_kernel_ms = sum(v[1] for v in prof.values())
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, ms, by) = top
+    peak, peak_kind = _peaks()
+    achieved = (by / nl) / ((ms / nl) / 1e3) / 1e9 if nl else 0.0
+    model_bytes = sum(v[2] for v in prof.values())
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (burst)",
+                "traffic": None, "share": ms / total_kernel_ms,
+                "bytes_per_launch": by / nl if nl else 0, "avg_launch_us": 1e3 * ms / nl if nl else 0}
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 4), "GBs": (v[2] / (v[1] / 1e3) / 1e9) if v[1] else 0}
+               for k, v in prof.items() if v[0]}
+    step_ms = total_ms / args.steps
+    stencil_gbs = model_bytes / (step_ms / 1e3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64/c128",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "h": h, "k": list(KS), "tol": TOL,
+                   "solves_per_step": len(KS), "form": "mixed complex64 V(2,2) + FP64 refinement, 4-instance batch",
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "latency_ms": {"p50": float(np.percentile(t_mixed, 50)), "p99": float(np.percentile(t_mixed, 99)),
+                       "per": "step of 4 solves"},
+        "iters": mixed_iters, "status": mixed_status,
+        "fp64_single": fp64,
+        "stencil_GBs": stencil_gbs, "stencil_frac_of_peak": stencil_gbs / peak,
+        "model_bytes_per_step": model_bytes,
+        "roofline": roofline, "kernels": kernels,
+        "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches_per_step * args.steps),
+    }
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        times, iters, exact, workers = cpu_oracle_workload(problems)
+        done = len(times)
+        cpu_val = done / float(np.sum(times))
+        line["cpu_baseline"] = {"value": cpu_val, "unit": "solves/s", "cores": workers, "kind": "oracle",
+                                "sample": f"{done} of the step's {len(KS)} solves, each to relres {TOL} "
+                                          f"with exact sine-basis inner solves (iters {iters})"}
+        acc = {"mixed_rel_l2_vs_exact": [], "fp64_rel_l2_vs_exact": []}
+        for i in range(len(KS)):
+            nrm = np.linalg.norm(exact[i])
+            acc["mixed_rel_l2_vs_exact"].append(float(np.linalg.norm(mixed_u[i] - exact[i]) / nrm))
+            if fp64_u is not None:
+                acc["fp64_rel_l2_vs_exact"].append(float(np.linalg.norm(fp64_u[i] - exact[i]) / nrm))
+        line["accuracy"] = acc
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    B.helm_batch_destroy(batch)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -163,6 +163,17 @@ HELM_API helm_status helm_batch_submit(helm_batch* batch, const helm_plan* plan,
 HELM_API helm_status helm_batch_step(helm_batch* batch, int max_steps);
 HELM_API helm_status helm_batch_poll(helm_batch* batch, uint64_t ticket, int* done, int* status,
                             int* iters, double* res_hist);
+/*
+ * Diagnostic twin of helm_batch_step: the same outer steps, each kernel launched on its
+ * own (no graph) between CUDA events on the batch's stream, accumulating per kernel
+ * kind k (0 smoothing half-sweep, 1 residual + restriction, 2 prolongation + correction,
+ * 3 zeroing, 4 coarse-level tail, 5 Helmholtz residual + update + norm, 6 convergence
+ * check): launches[k], device milliseconds ms[k] and algorithmic bytes bytes[k] (each
+ * datum a launch must read or write, counted once).  nkinds >= 7.
+ */
+HELM_API helm_status helm_batch_profile(helm_batch* batch, int max_steps, uint64_t* launches,
+                                        double* ms, double* bytes, int nkinds);
+
 /* Active (submitted, not yet polled done) solves and the workspace bytes they hold. */
 HELM_API helm_status helm_batch_info(const helm_batch* batch, int* active, size_t* bytes_in_use);
 

@@ -54,7 +54,12 @@ _SIGS = {
     "helm_batch_poll": (C.c_int, [_vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "helm_batch_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_size_t)]),
+    "helm_batch_profile": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_uint64), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), C.c_int]),
 }
+
+KERNEL_KINDS = ["rbgs_half_sweep", "residual_restrict", "prolong_correct", "zero",
+                "coarse_tail", "helmholtz_residual_update", "convergence_check"]
 
 _lib = None
 
@@ -268,3 +273,14 @@ def helm_batch_info(batch: _Batch):
     b = C.c_size_t()
     _check(load().helm_batch_info(batch.handle, C.byref(a), C.byref(b)), "helm_batch_info")
     return a.value, b.value
+
+
+def helm_batch_profile(batch: _Batch, max_steps: int = 0):
+    """Per kernel kind: {name: (launches, device ms, algorithmic bytes)}."""
+    nk = len(KERNEL_KINDS)
+    la = (C.c_uint64 * nk)()
+    ms = (C.c_double * nk)()
+    by = (C.c_double * nk)()
+    _check(load().helm_batch_profile(batch.handle, int(max_steps), la, ms, by, nk),
+           "helm_batch_profile")
+    return {KERNEL_KINDS[i]: (int(la[i]), float(ms[i]), float(by[i])) for i in range(nk)}

