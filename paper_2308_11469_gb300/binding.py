@@ -59,7 +59,8 @@ _SIGS = {
 }
 
 KERNEL_KINDS = ["rbgs_half_sweep", "residual_restrict", "prolong_correct", "zero",
-                "coarse_tail", "helmholtz_residual_update", "convergence_check"]
+                "coarse_tail", "helmholtz_residual_update", "convergence_check",
+                "smooth_restrict_2d", "prolong_smooth_2d"]
 
 _lib = None
 

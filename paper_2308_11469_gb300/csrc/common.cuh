@@ -29,8 +29,9 @@ struct LevelDesc {
     int rows;     // n + 2 rows per z plane
     int pad_;
     double h;     // spacing 2^l h
-    void* e;      // padded iterate of Delta_h e = rhs
+    void* e;      // padded iterate of Delta_h e = rhs (final iterate of a V-cycle)
     void* rhs;    // right-hand side (same indexing as e)
+    void* e2;     // 2D fused path: the pre-smoothed iterate (same indexing as e)
 };
 
 struct InstDesc {
@@ -41,7 +42,8 @@ struct InstDesc {
     double2* u[2];              // u[0] = caller's array, u[1] = library buffer
     const double2* f;
     const double2* g;
-    double* part;               // [2 * nres_blocks]: sum |r|^2 partials, then max |e|
+    double* part;               // [2 * nres_blocks]: sum |r|^2 partials, then max |e|^2
+    unsigned int* count;        // residual tiles finished in the current launch
     double* hist;               // relres_0..relres_max_outer
     double* einf;               // ||e_N||_inf, N = 0..max_outer-1
     LevelDesc lev[HELM_MAXLEV];

@@ -47,7 +47,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool is_pow2m1(int n) { return n >= 1 && ((n + 1) & n) == 0; }
 
-int res_rows_per_tile(int D) { return D == 2 ? 32 : 16; }
+int res_rows_per_tile(int D) { return residual_tile_rows(D); }
 
 // Fill the geometry part of a descriptor and return the workspace bytes it needs (the
 // level arrays, the second iterate buffer and the residual partials).  With base != NULL
@@ -77,14 +77,17 @@ size_t layout(InstDesc& d, int D, int n, double h, double k, int prec, char* bas
         L.pitch = round_up(L.n + 2, 16);
         L.e = nullptr;
         L.rhs = nullptr;
+        L.e2 = nullptr;
         if (l > lt) continue;               // deeper levels live only inside the tail kernel
         const size_t planes = (D == 3) ? (size_t)L.rows : 1;
         const size_t sz = align256((size_t)L.pitch * L.rows * planes * eb);
+        const bool two = (D == 2 && l < lt);  // fused 2D levels keep a second iterate
         if (base) {
             L.e = base + off;
             L.rhs = base + off + sz;
+            if (two) L.e2 = base + off + 2 * sz;
         }
-        off += 2 * sz;
+        off += (two ? 3 : 2) * sz;
     }
     const size_t S = (size_t)n + 2;
     const size_t ubytes = align256(((D == 3) ? S * S * S : S * S) * 16);
@@ -95,6 +98,8 @@ size_t layout(InstDesc& d, int D, int n, double h, double k, int prec, char* bas
     d.nres_blocks = d.res_tx * d.res_ty * ((D == 3) ? n : 1);
     if (base) d.part = (double*)(base + off);
     off += align256((size_t)2 * d.nres_blocks * sizeof(double));
+    if (base) d.count = (unsigned int*)(base + off);
+    off += 256;
     return off;
 }
 
@@ -112,7 +117,7 @@ struct Instance {
 };
 
 struct LaunchRec {
-    enum Kind { RBGS, RESTRICT, PROLONG, ZERO, TAIL, RESID, CHECK, NKINDS } kind;
+    enum Kind { RBGS, RESTRICT, PROLONG, ZERO, TAIL, RESID, CHECK, DOWN, UP, NKINDS } kind;
     int off, cnt, work, color, mode;
     double bytes;   // algorithmic bytes of one launch (each datum it must touch, once)
 };
@@ -135,6 +140,7 @@ struct Engine {
     int nres = 0;
     std::vector<LaunchRec> step;               // one outer step
     std::vector<long> signature;               // geometry of the slots the graph was built for
+    std::vector<MgItem> h_items;               // host copy of the multigrid work items
     std::vector<LaunchRec> vcyc_plain;         // one V-cycle from the current iterate
     int max_tail = 1;
     bool dirty = true;
@@ -170,6 +176,7 @@ struct Engine {
         HELM_CK(cudaMalloc(&d_ctrl, 4 * sizeof(int)));
         HELM_CK(cudaMallocHost(&h_ctrl, 4 * sizeof(int)));
         HELM_CK(setup_tail(D, prec == HELM_PREC_FP64 ? 0 : 1));
+        if (D == 2) HELM_CK(setup_2d(prec == HELM_PREC_FP64 ? 0 : 1));
         return grow(4);
     }
 
@@ -215,12 +222,12 @@ struct Engine {
                 J = std::max(J, slots[i]->d.ltail);
                 max_tail = std::max(max_tail, slots[i]->d.lev[slots[i]->d.ltail].n);
             }
-        struct Ph { int off, cnt, w_rb, w_rs, w_pr, w_z; double b_rb, b_rs, b_pr, b_z; };
+        struct Ph { int off, cnt, w_rb, w_rs, w_pr, w_z; double b_rb, b_rs, b_pr, b_z; int tiles; };
         const double eb = elem_bytes(prec);
         auto pts = [&](int m) { return (D == 3) ? (double)m * m * m : (double)m * m; };
         std::vector<Ph> ph(J);
         for (int j = 0; j < J; ++j) {
-            Ph p{(int)items.size(), 0, 0, 0, 0, 0, 0.0, 0.0, 0.0, 0.0};
+            Ph p{(int)items.size(), 0, 0, 0, 0, 0, 0.0, 0.0, 0.0, 0.0, 0};
             for (int i = 0; i < cap; ++i) {
                 if (!slots[i]) continue;
                 const InstDesc& d = slots[i]->d;
@@ -241,6 +248,7 @@ struct Engine {
                 // prolongation: coarse e in, fine e in and out
                 p.b_pr += (pts(nc) + 2.0 * pts(n)) * eb;
                 p.b_z += pts(n) * eb;
+                if (D == 2) p.tiles = std::max(p.tiles, tiles2d(n));
                 ++p.cnt;
             }
             ph[j] = p;
@@ -286,13 +294,23 @@ struct Engine {
             res_cap = std::max(res.size(), res_cap * 2);
             HELM_CK(cudaMalloc(&d_res, res_cap * sizeof(ResItem)));
         }
+        h_items = items;
         if (!items.empty())
             HELM_CK(cudaMemcpy(d_mg, items.data(), items.size() * sizeof(MgItem), cudaMemcpyHostToDevice));
         if (!res.empty())
             HELM_CK(cudaMemcpy(d_res, res.data(), res.size() * sizeof(ResItem), cudaMemcpyHostToDevice));
         nres = (int)res.size();
 
+        auto vcycle2d = [&](std::vector<LaunchRec>& out, bool zero_start) {
+            for (int j = 0; j < J; ++j)
+                out.push_back({LaunchRec::DOWN, ph[j].off, ph[j].cnt, ph[j].tiles, 0,
+                               zero_start ? 2 : 1, 0.0});
+            out.push_back({LaunchRec::TAIL, tail_off, ntail, 0, 0, zero_start ? 0 : 1, b_tail});
+            for (int j = J - 1; j >= 0; --j)
+                out.push_back({LaunchRec::UP, ph[j].off, ph[j].cnt, ph[j].tiles, 0, 0, 0.0});
+        };
         auto vcycle = [&](std::vector<LaunchRec>& out, bool zero_start) {
+            if (D == 2) { vcycle2d(out, zero_start); return; }
             if (zero_start && nu1 == 0)
                 out.push_back({LaunchRec::ZERO, l0_off, nl0, w_l0, 0, 0, b_l0});
             for (int j = 0; j < J; ++j) {
@@ -321,6 +339,44 @@ struct Engine {
         return HELM_OK;
     }
 
+    // Algorithmic bytes of one launch counting only the instances still iterating
+    // (finished instances' blocks exit at once and move no data).
+    double launch_bytes(const LaunchRec& L, const InstState* st) const
+    {
+        const double eb = elem_bytes(prec);
+        auto pts = [&](int m) { return (D == 3) ? (double)m * m * m : (double)m * m; };
+        double b = 0.0;
+        if (L.kind == LaunchRec::RESID) {
+            for (int i = 0; i < cap; ++i)
+                if (slots[i] && st[i].status == HELM_ST_ACTIVE)
+                    b += pts(slots[i]->d.n) * (16.0 + eb + 16.0 + 16.0 + eb);
+            return b;
+        }
+        if (L.kind == LaunchRec::CHECK) return 0.0;
+        for (int q = L.off; q < L.off + L.cnt; ++q) {
+            const MgItem& it = h_items[q];
+            if (!slots[it.inst] || st[it.inst].status != HELM_ST_ACTIVE) continue;
+            const InstDesc& d = slots[it.inst]->d;
+            const int n = d.lev[it.level].n;
+            const int nc = (it.level + 1 < d.nlev) ? d.lev[it.level + 1].n : 0;
+            switch (L.kind) {
+            case LaunchRec::RBGS: b += 1.5 * pts(n) * eb; break;
+            case LaunchRec::RESTRICT: b += (2.0 * pts(n) + 2.0 * pts(nc)) * eb; break;
+            case LaunchRec::PROLONG: b += (pts(nc) + 2.0 * pts(n)) * eb; break;
+            case LaunchRec::ZERO: b += pts(n) * eb; break;
+            case LaunchRec::TAIL: b += 2.0 * pts(n) * eb; break;
+            case LaunchRec::DOWN: {
+                const bool zero = (L.mode == 2) || (L.mode == 1 && it.level > 0);
+                b += ((zero ? 2.0 : 3.0) * pts(n) + pts(nc)) * eb;   // [e], rhs in; e2, coarse rhs out
+                break;
+            }
+            case LaunchRec::UP: b += (3.0 * pts(n) + pts(nc)) * eb; break;  // e2, rhs, coarse e in; e out
+            default: break;
+            }
+        }
+        return b;
+    }
+
     helm_status enqueue(const std::vector<LaunchRec>& seq, cudaStream_t s, bool use_cond)
     {
         for (const LaunchRec& L : seq) {
@@ -342,11 +398,17 @@ struct Engine {
                 e = launch_tail(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, nu1, nu2, L.mode,
                                 max_tail, s);
                 break;
+            case LaunchRec::DOWN:
+                e = launch_down2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu1, L.mode, s);
+                break;
+            case LaunchRec::UP:
+                e = launch_up2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu2, s);
+                break;
             case LaunchRec::RESID:
                 e = launch_residual(D, prec, d_desc, d_state, d_res + L.off, L.cnt, L.mode, s);
                 break;
             case LaunchRec::CHECK:
-                e = launch_check(d_desc, d_state, L.cnt, L.mode, d_ctrl, use_cond ? 1 : 0,
+                e = launch_check(d_state, L.cnt, d_ctrl, use_cond ? 1 : 0,
                                  (unsigned long long)cond, s);
                 break;
             }
@@ -427,12 +489,11 @@ struct Engine {
         init.status = HELM_ST_ACTIVE;
         HELM_CK(cudaMemcpyAsync(d_desc + slot, &in->d, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
         HELM_CK(cudaMemcpyAsync(d_state + slot, &init, sizeof(InstState), cudaMemcpyHostToDevice, s));
-        HELM_CK(launch_set_ring(D, d_desc, d_state, slot, in->d.n, s));
-        // the instance's own tile list names instance 0: offset the tables to its slot
+        HELM_CK(launch_set_ring(D, d_desc, slot, in->d.n, s));
+        // the instance's own tile list names instance 0: offset the tables to its slot;
+        // the last tile records relres_0 and the initial status
         HELM_CK(launch_residual(D, prec, d_desc + slot, d_state + slot, in->d_res0, in->nres0, 0, s));
-        // the check of the initial residual only touches this slot
-        HELM_CK(launch_check(d_desc + slot, d_state + slot, 1, 0, d_ctrl, 0, 0, s));
-        g_launches += 3;
+        g_launches += 2;
         return HELM_OK;
     }
 
@@ -954,7 +1015,12 @@ helm_status helm_batch_profile(helm_batch* b, int max_steps, uint64_t* launches,
         E->h_ctrl[1] = INT_MAX;
         E->h_ctrl[2] = 1;
         HELM_CK(cudaMemcpyAsync(E->d_ctrl, E->h_ctrl, 3 * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+        HELM_CK(cudaMemcpyAsync(E->h_state, E->d_state, sizeof(InstState) * E->cap,
+                                cudaMemcpyDeviceToHost, b->stream));
+        HELM_CK(cudaStreamSynchronize(b->stream));
         for (int s = 0; (max_steps == 0 || s < max_steps) && s < 1000000; ++s) {
+            std::vector<double> lb(nl);
+            for (size_t i = 0; i < nl; ++i) lb[i] = E->launch_bytes(E->step[i], E->h_state);
             for (size_t i = 0; i < nl; ++i) {
                 HELM_CK(cudaEventRecord(ev[2 * i], b->stream));
                 std::vector<LaunchRec> one{E->step[i]};
@@ -963,6 +1029,8 @@ helm_status helm_batch_profile(helm_batch* b, int max_steps, uint64_t* launches,
                 HELM_CK(cudaEventRecord(ev[2 * i + 1], b->stream));
             }
             HELM_CK(cudaMemcpyAsync(E->h_ctrl, E->d_ctrl, 3 * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+            HELM_CK(cudaMemcpyAsync(E->h_state, E->d_state, sizeof(InstState) * E->cap,
+                                    cudaMemcpyDeviceToHost, b->stream));
             HELM_CK(cudaStreamSynchronize(b->stream));
             for (size_t i = 0; i < nl; ++i) {
                 float t = 0.f;
@@ -970,7 +1038,7 @@ helm_status helm_batch_profile(helm_batch* b, int max_steps, uint64_t* launches,
                 const int k = (int)E->step[i].kind;
                 launches[k] += 1;
                 ms[k] += t;
-                bytes[k] += E->step[i].bytes;
+                bytes[k] += lb[i];
             }
             g_launches += nl;
             if (!E->h_ctrl[2]) break;

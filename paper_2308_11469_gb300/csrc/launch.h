@@ -35,18 +35,30 @@ size_t tail_smem_bytes(int D, int prec, int n);
 // raise the tail kernel's dynamic shared-memory limit (once, before any capture)
 cudaError_t setup_tail(int D, int prec);
 
+// ---- fused 2D multigrid (vcycle2d.cu): two launches per level ----
+// descent: nu1 sweeps + residual + restriction; e (or zero) -> e2, coarse rhs.
+// zero_mode: 2 = every level's iterate is zero, 1 = levels > 0 are zero, 0 = load e.
+cudaError_t launch_down2d(int prec, const InstDesc* insts, const InstState* st, const MgItem* items,
+                          int nitems, int max_tiles, int nu1, int zero_mode, cudaStream_t s);
+// ascent: e2 + prolongation of the coarse e, nu2 sweeps -> e
+cudaError_t launch_up2d(int prec, const InstDesc* insts, const InstState* st, const MgItem* items,
+                        int nitems, int max_tiles, int nu2, cudaStream_t s);
+int tiles2d(int n);
+cudaError_t setup_2d(int prec);
+
 // ---- outer FP64 iteration (outer.cu) ----
 // mode 0: r_0 from u[it&1]; mode 1: u[(it+1)&1] = u[it&1] + e_0, then r from it.
-// Writes r into level-0 rhs (inner precision) and per-tile partials.
-cudaError_t launch_residual(int D, int prec, const InstDesc* insts, const InstState* st,
+// Writes r into level-0 rhs (inner precision) and per-tile partials; the last tile of
+// each instance forms relres, records the history and applies the status rule.
+cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* st,
                             const ResItem* items, int nitems, int mode, cudaStream_t s);
-// Per-instance norms -> relres history, status rule; sets the while-loop condition.
-cudaError_t launch_check(const InstDesc* insts, InstState* st, int ninst, int mode,
-                         int* ctrl, int use_cond, unsigned long long cond_handle,
-                         cudaStream_t s);
+int residual_tile_rows(int D);
+int residual_tile_cols(int D);
+// Any instance still iterating?  Counts the step, sets the while-loop condition.
+cudaError_t launch_check(const InstState* st, int ninst, int* ctrl, int use_cond,
+                         unsigned long long cond_handle, cudaStream_t s);
 // u[0] and u[1] rings := g ring
-cudaError_t launch_set_ring(int D, const InstDesc* insts, const InstState* st, int inst,
-                            int n, cudaStream_t s);
+cudaError_t launch_set_ring(int D, const InstDesc* insts, int inst, int n, cudaStream_t s);
 // interior tight <-> level-0 padded/pitched, inner precision
 cudaError_t launch_pack(int D, int prec, const InstDesc* insts, int inst, int n,
                         const void* src, int which /*0 = e, 1 = rhs*/, cudaStream_t s);

@@ -9,22 +9,21 @@
 // data g enters through the ring of u (the Dirichlet nodes of Section 2.4 that are moved
 // to the right-hand side).
 //
-// k_residual (mode 1) fuses the update with the next residual: it forms
-// u_{N+1} = u_N + e_N at a node and its 2D neighbours (e is zero on the ring), writes
-// u_{N+1} to the other buffer of the ping-pong pair, and writes r_{N+1} (rounded to the
-// inner precision) into the level-0 right-hand side; each tile leaves one partial
-// sum of |r|^2 and one partial max |e| (fixed order => deterministic norms).
+// The residual kernels (mode 1) fuse the update with the next residual: u_{N+1} =
+// u_N + e_N is formed once per node (in shared memory for 2D tiles), written to the
+// other buffer of the ping-pong pair, and r_{N+1} = f - (Delta_h + k^2) u_{N+1} is formed
+// in FP64 and stored, rounded to the inner precision, as the next right-hand side.
+// FP64 work is kept to the update and the stencil (GB300 runs FP64 at a small fraction
+// of its FP32 rate): |e| and |r|^2 are formed in the inner precision (|r|^2 from the
+// stored, rounded r).  Each tile leaves one partial sum of |r|^2 and one partial
+// max |e|^2; the last tile of an instance to finish (atomic ticket) sums the partials in
+// tile order (deterministic), forms relres and applies the status rule.
 #include "launch.h"
 
 namespace helm {
 namespace {
 
-constexpr int RES_BX = 32;
-constexpr int RES_BY = 8;
-
-template <int D> struct ResTile;
-template <> struct ResTile<2> { static constexpr int RY = 4; };   // 32 x 32 nodes
-template <> struct ResTile<3> { static constexpr int RY = 2; };   // 32 x 16 x 1 nodes
+constexpr int NTH = 256;
 
 template <typename R>
 __device__ __forceinline__ typename C2<R>::T to_inner(double2 v) {
@@ -34,19 +33,181 @@ __device__ __forceinline__ typename C2<R>::T to_inner(double2 v) {
     return o;
 }
 
-template <int D, typename R, int MODE>
-__global__ void __launch_bounds__(RES_BX * RES_BY)
-k_residual(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
-           const ResItem* __restrict__ items)
+// Status rule (the paper only reports "converges" / "diverges"; this project's reading):
+// CONVERGED when relres <= tol; DIVERGED when relres > 1e4, or when N >= 20 and relres
+// has not decreased for 10 consecutive steps; NONFINITE on NaN / Inf; MAXITER at max_outer.
+__device__ void finalize(const InstDesc& I, InstState* stp, double norm2, double emax2, int mode)
+{
+    InstState s = *stp;
+    const double norm = sqrt(norm2);
+    double rel;
+    int N;
+    if (mode == 0) {
+        N = 0;
+        s.norm0 = norm;
+        s.run = 0;
+        rel = (norm == 0.0) ? 0.0 : 1.0;
+        if (!isfinite(norm)) rel = norm;
+    } else {
+        s.it += 1;
+        N = s.it;
+        rel = norm / s.norm0;
+        I.einf[N - 1] = sqrt(emax2);
+    }
+    I.hist[N] = rel;
+    int out = HELM_ST_ACTIVE;
+    if (!isfinite(rel)) out = -4;                                   // HELM_ENONFINITE
+    else if (rel <= I.tol || (mode == 0 && norm == 0.0)) out = 0;   // CONVERGED
+    else if (rel > 1e4) out = 2;                                    // DIVERGED
+    else {
+        if (mode != 0) s.run = (rel >= s.prev) ? s.run + 1 : 0;
+        if (N >= 20 && s.run >= 10) out = 2;                        // DIVERGED
+        else if (N >= I.max_outer) out = 1;                         // MAXITER
+    }
+    s.prev = rel;
+    s.status = out;
+    *stp = s;
+}
+
+// Block-wide sums / maxima in a fixed order (xor-shuffle, then warps in order).
+__device__ __forceinline__ void block_reduce(double& a, double& m, double* sa, double* sm)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sa[w] = a;
+        sm[w] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = 0.0;
+        m = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            a += sa[i];
+            m = fmax(m, sm[i]);
+        }
+    }
+}
+
+// Write this tile's partials; the last tile of the instance reduces them all.
+__device__ void tile_done(const InstDesc& I, InstState* stp, int tile, double a, double m, int mode)
+{
+    __shared__ double sa[NTH / 32], sm[NTH / 32];
+    __shared__ int last;
+    block_reduce(a, m, sa, sm);
+    if (threadIdx.x == 0) {
+        I.part[tile] = a;
+        I.part[I.nres_blocks + tile] = m;
+        __threadfence();
+        const unsigned prev = atomicAdd(I.count, 1u);
+        last = (prev == (unsigned)(I.nres_blocks - 1));
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double ta = 0.0, tm = 0.0;
+    for (int b = threadIdx.x; b < I.nres_blocks; b += blockDim.x) {
+        ta += __ldcg(I.part + b);
+        tm = fmax(tm, __ldcg(I.part + I.nres_blocks + b));
+    }
+    __syncthreads();
+    block_reduce(ta, tm, sa, sm);
+    if (threadIdx.x == 0) {
+        finalize(I, stp, ta, tm, mode);
+        *I.count = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2D: 32 x 32 tiles, u_{N+1} staged in shared memory with a 1-node halo
+// ---------------------------------------------------------------------------
+constexpr int T2 = 32;
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(NTH)
+k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
+             const ResItem* __restrict__ items)
 {
     typedef typename C2<R>::T c2;
+    __shared__ double2 U[(T2 + 2) * (T2 + 2)];
     const ResItem item = items[blockIdx.x];
-    const InstState s = st[item.inst];
+    InstState* stp = st + item.inst;
+    const InstState s = *stp;
     if (s.status != HELM_ST_ACTIVE) return;
     const InstDesc& I = insts[item.inst];
     const int n = I.n;
-    const int S = n + 2;                      // tight padded row length of u / g
-    const long SP = (long)S * S;
+    const int S = n + 2;
+    const double2* __restrict__ uin = I.u[s.it & 1];
+    double2* __restrict__ uout = I.u[(s.it + 1) & 1];
+    const double2* __restrict__ f = I.f;
+    const LevelDesc L0 = I.lev[0];
+    const c2* __restrict__ e = (const c2*)L0.e;
+    c2* __restrict__ rhs = (c2*)L0.rhs;
+    const int P = L0.pitch;
+    const int x0 = 1 + item.tx * T2, y0 = 1 + item.ty * T2;
+    R emax2 = 0;
+    for (int q = threadIdx.x; q < (T2 + 2) * (T2 + 2); q += NTH) {
+        const int lx = q % (T2 + 2), ly = q / (T2 + 2);
+        const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+        double2 v = make_double2(0.0, 0.0);
+        if (gx <= n + 1 && gy <= n + 1) {
+            v = uin[gy * S + gx];
+            if (MODE == 1 && gx >= 1 && gx <= n && gy >= 1 && gy <= n) {
+                const c2 ev = e[gy * P + gx];
+                v.x += (double)ev.x;
+                v.y += (double)ev.y;
+                if (lx >= 1 && lx <= T2 && ly >= 1 && ly <= T2)
+                    emax2 = fmax(emax2, ev.x * ev.x + ev.y * ev.y);
+            }
+        }
+        U[q] = v;
+    }
+    __syncthreads();
+    const double ih2 = 1.0 / (I.h * I.h);
+    const double cdiag = I.k2 - 4.0 * ih2;
+    R r2 = 0;
+    const int lx = (threadIdx.x & 31) + 1;
+#pragma unroll
+    for (int k = 0; k < T2 / 8; ++k) {
+        const int ly = (threadIdx.x >> 5) + 8 * k + 1;
+        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        if (gx > n || gy > n) continue;
+        const int o = ly * (T2 + 2) + lx;
+        const double2 c = U[o];
+        const double2 a = U[o - 1], b = U[o + 1], d = U[o - (T2 + 2)], u = U[o + (T2 + 2)];
+        if (MODE == 1) uout[gy * S + gx] = c;
+        const double2 fv = f[(size_t)(gy - 1) * n + (gx - 1)];
+        double2 r;
+        r.x = fv.x - fma(((a.x + b.x) + (d.x + u.x)), ih2, cdiag * c.x);
+        r.y = fv.y - fma(((a.y + b.y) + (d.y + u.y)), ih2, cdiag * c.y);
+        const c2 ri = to_inner<R>(r);
+        rhs[gy * P + gx] = ri;
+        r2 += ri.x * ri.x + ri.y * ri.y;
+    }
+    tile_done(I, stp, item.ty * I.res_tx + item.tx, (double)r2, (double)emax2, MODE);
+}
+
+// ---------------------------------------------------------------------------
+// 3D: 32 x 16 x 1 tiles, direct loads (neighbour reuse through L1)
+// ---------------------------------------------------------------------------
+template <typename R, int MODE>
+__global__ void __launch_bounds__(NTH)
+k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
+             const ResItem* __restrict__ items)
+{
+    typedef typename C2<R>::T c2;
+    const ResItem item = items[blockIdx.x];
+    InstState* stp = st + item.inst;
+    const InstState s = *stp;
+    if (s.status != HELM_ST_ACTIVE) return;
+    const InstDesc& I = insts[item.inst];
+    const int n = I.n;
+    const long S = n + 2;
+    const long SP = S * S;
     const double2* __restrict__ uin = I.u[s.it & 1];
     double2* __restrict__ uout = I.u[(s.it + 1) & 1];
     const double2* __restrict__ f = I.f;
@@ -56,145 +217,62 @@ k_residual(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const long P = L0.pitch;
     const long PL = (long)L0.pitch * L0.rows;
     const double ih2 = 1.0 / (I.h * I.h);
-    const double k2 = I.k2;
-    const double cdiag = k2 - 2.0 * D * ih2;
-
-    const int x = item.tx * RES_BX + threadIdx.x + 1;
-    const int z = (D == 3) ? item.tz + 1 : 0;
-    double r2 = 0.0, emax = 0.0;
-    constexpr int RY = ResTile<D>::RY;
+    const double cdiag = I.k2 - 6.0 * ih2;
+    const int x = item.tx * 32 + (threadIdx.x & 31) + 1;
+    const int z = item.tz + 1;
+    R r2 = 0, emax2 = 0;
 #pragma unroll
-    for (int k = 0; k < RY; ++k) {
-        const int y = item.ty * (RES_BY * RY) + k * RES_BY + threadIdx.y + 1;
+    for (int k = 0; k < 2; ++k) {
+        const int y = item.ty * 16 + k * 8 + (threadIdx.x >> 5) + 1;
         if (x > n || y > n) continue;
-        const long ou = ((D == 3) ? (long)z * SP : 0) + (long)y * S + x;
-        const long oe = ((D == 3) ? (long)z * PL : 0) + (long)y * P + x;
+        const long ou = (long)z * SP + (long)y * S + x;
+        const long oe = (long)z * PL + (long)y * P + x;
         double2 c = uin[ou];
         double2 w = uin[ou - 1], ea = uin[ou + 1], so = uin[ou - S], no = uin[ou + S];
-        double2 dn, up;
-        if (D == 3) { dn = uin[ou - SP]; up = uin[ou + SP]; }
+        double2 dn = uin[ou - SP], up = uin[ou + SP];
         if (MODE == 1) {
             const c2 e0 = e[oe];
             const c2 e1 = e[oe - 1], e2 = e[oe + 1], e3 = e[oe - P], e4 = e[oe + P];
+            const c2 e5 = e[oe - PL], e6 = e[oe + PL];
             c.x += (double)e0.x;  c.y += (double)e0.y;
             w.x += (double)e1.x;  w.y += (double)e1.y;
             ea.x += (double)e2.x; ea.y += (double)e2.y;
             so.x += (double)e3.x; so.y += (double)e3.y;
             no.x += (double)e4.x; no.y += (double)e4.y;
-            if (D == 3) {
-                const c2 e5 = e[oe - PL], e6 = e[oe + PL];
-                dn.x += (double)e5.x; dn.y += (double)e5.y;
-                up.x += (double)e6.x; up.y += (double)e6.y;
-            }
+            dn.x += (double)e5.x; dn.y += (double)e5.y;
+            up.x += (double)e6.x; up.y += (double)e6.y;
             uout[ou] = c;
-            const double ex = (double)e0.x, ey = (double)e0.y;
-            emax = fmax(emax, sqrt(ex * ex + ey * ey));
+            emax2 = fmax(emax2, e0.x * e0.x + e0.y * e0.y);
         }
-        double sx = w.x + ea.x + so.x + no.x;
-        double sy = w.y + ea.y + so.y + no.y;
-        if (D == 3) {
-            sx += dn.x + up.x;
-            sy += dn.y + up.y;
-        }
-        const long of = (D == 3) ? ((long)(z - 1) * n + (y - 1)) * n + (x - 1)
-                                 : (long)(y - 1) * n + (x - 1);
-        const double2 fv = f[of];
+        const double2 fv = f[((long)(z - 1) * n + (y - 1)) * n + (x - 1)];
         double2 r;
-        r.x = fv.x - (sx * ih2 + cdiag * c.x);
-        r.y = fv.y - (sy * ih2 + cdiag * c.y);
-        rhs[oe] = to_inner<R>(r);
-        r2 += r.x * r.x + r.y * r.y;
+        r.x = fv.x - fma(((w.x + ea.x) + (so.x + no.x)) + (dn.x + up.x), ih2, cdiag * c.x);
+        r.y = fv.y - fma(((w.y + ea.y) + (so.y + no.y)) + (dn.y + up.y), ih2, cdiag * c.y);
+        const c2 ri = to_inner<R>(r);
+        rhs[oe] = ri;
+        r2 += ri.x * ri.x + ri.y * ri.y;
     }
-    // deterministic block reduction: xor-shuffle within warps, then warps in order
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-        emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-    }
-    __shared__ double sr[RES_BY], sm[RES_BY];
-    if (threadIdx.x == 0) {
-        sr[threadIdx.y] = r2;
-        sm[threadIdx.y] = emax;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        double a = 0.0, m = 0.0;
-        for (int i = 0; i < RES_BY; ++i) {
-            a += sr[i];
-            m = fmax(m, sm[i]);
-        }
-        const int tid = (D == 3) ? (item.tz * I.res_ty + item.ty) * I.res_tx + item.tx
-                                 : item.ty * I.res_tx + item.tx;
-        I.part[tid] = a;
-        I.part[I.nres_blocks + tid] = m;
-    }
+    const int tile = (item.tz * I.res_ty + item.ty) * I.res_tx + item.tx;
+    tile_done(I, stp, tile, (double)r2, (double)emax2, MODE);
 }
 
-// One CTA; warp w handles instances w, w + 32, ...  Sums the partials in a fixed order,
-// forms relres, applies the status rule, and (graph mode) sets the loop condition.
-__global__ void __launch_bounds__(1024)
-k_check(const InstDesc* __restrict__ insts, InstState* __restrict__ st, int ninst, int mode,
-        int* __restrict__ ctrl, int use_cond, unsigned long long cond_handle)
+// One CTA: is any instance still iterating?  Counts the step and sets the loop condition.
+__global__ void __launch_bounds__(256)
+k_check(const InstState* __restrict__ st, int ninst, int* __restrict__ ctrl, int use_cond,
+        unsigned long long cond_handle)
 {
     __shared__ int any_active;
     if (threadIdx.x == 0) any_active = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    for (int i = warp; i < ninst; i += nwarps) {
-        InstState s = st[i];
-        if (s.status != HELM_ST_ACTIVE) continue;
-        const InstDesc& I = insts[i];
-        double a = 0.0, m = 0.0;
-        for (int b = lane; b < I.nres_blocks; b += 32) {
-            a += I.part[b];
-            m = fmax(m, I.part[I.nres_blocks + b]);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        }
-        if (lane == 0) {
-            const double norm = sqrt(a);
-            double rel;
-            int N;
-            if (mode == 0) {
-                N = 0;
-                s.norm0 = norm;
-                s.run = 0;
-                rel = (norm == 0.0) ? 0.0 : 1.0;
-            } else {
-                s.it += 1;
-                N = s.it;
-                rel = norm / s.norm0;
-                I.einf[N - 1] = m;
-            }
-            I.hist[N] = rel;
-            int out = HELM_ST_ACTIVE;
-            if (!isfinite(rel)) out = -4;                       // HELM_ENONFINITE
-            else if (rel <= I.tol || (mode == 0 && norm == 0.0)) out = 0;   // CONVERGED
-            else if (rel > 1e4) out = 2;                        // DIVERGED
-            else {
-                if (mode != 0) s.run = (rel >= s.prev) ? s.run + 1 : 0;
-                if (N >= 20 && s.run >= 10) out = 2;            // DIVERGED
-                else if (N >= I.max_outer) out = 1;             // MAXITER
-            }
-            s.prev = rel;
-            s.status = out;
-            st[i] = s;
-            if (out == HELM_ST_ACTIVE) atomicOr(&any_active, 1);
-        }
-    }
+    int a = 0;
+    for (int i = threadIdx.x; i < ninst; i += blockDim.x) a |= (st[i].status == HELM_ST_ACTIVE);
+    if (a) atomicOr(&any_active, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
         int go = any_active;
-        if (mode != 0) {
-            const int done = ctrl[0] + 1;
-            ctrl[0] = done;
-            if (done >= ctrl[1]) go = 0;          // step budget of this launch
-        }
+        const int done = ctrl[0] + 1;
+        ctrl[0] = done;
+        if (done >= ctrl[1]) go = 0;          // step budget of this launch
         ctrl[2] = go;
         if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, go ? 1u : 0u);
     }
@@ -269,33 +347,33 @@ inline int blocks_for(long work) {
 
 }  // namespace
 
-cudaError_t launch_residual(int D, int prec, const InstDesc* insts, const InstState* st,
+int residual_tile_rows(int D) { return D == 2 ? T2 : 16; }
+int residual_tile_cols(int D) { return 32; }
+
+cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* st,
                             const ResItem* items, int nitems, int mode, cudaStream_t s)
 {
-    dim3 b(RES_BX, RES_BY);
     if (nitems <= 0) return cudaSuccess;
-#define HELM_RES(DD, RR)                                                             \
-    (mode ? (k_residual<DD, RR, 1><<<nitems, b, 0, s>>>(insts, st, items), 0)          \
-          : (k_residual<DD, RR, 0><<<nitems, b, 0, s>>>(insts, st, items), 0))
-    if (D == 2 && prec == 0) HELM_RES(2, double);
-    else if (D == 2) HELM_RES(2, float);
-    else if (prec == 0) HELM_RES(3, double);
-    else HELM_RES(3, float);
+#define HELM_RES(K, RR)                                                                   \
+    (mode ? (K<RR, 1><<<nitems, NTH, 0, s>>>(insts, st, items), 0)                         \
+          : (K<RR, 0><<<nitems, NTH, 0, s>>>(insts, st, items), 0))
+    if (D == 2 && prec == 0) HELM_RES(k_residual2d, double);
+    else if (D == 2) HELM_RES(k_residual2d, float);
+    else if (prec == 0) HELM_RES(k_residual3d, double);
+    else HELM_RES(k_residual3d, float);
 #undef HELM_RES
     return cudaGetLastError();
 }
 
-cudaError_t launch_check(const InstDesc* insts, InstState* st, int ninst, int mode, int* ctrl,
-                         int use_cond, unsigned long long cond_handle, cudaStream_t s)
+cudaError_t launch_check(const InstState* st, int ninst, int* ctrl, int use_cond,
+                         unsigned long long cond_handle, cudaStream_t s)
 {
-    k_check<<<1, 1024, 0, s>>>(insts, st, ninst, mode, ctrl, use_cond, cond_handle);
+    k_check<<<1, 256, 0, s>>>(st, ninst, ctrl, use_cond, cond_handle);
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_ring(int D, const InstDesc* insts, const InstState* st, int inst, int n,
-                            cudaStream_t s)
+cudaError_t launch_set_ring(int D, const InstDesc* insts, int inst, int n, cudaStream_t s)
 {
-    (void)st;
     const long S = n + 2;
     const long work = (D == 3) ? S * S * S : S * S;
     if (D == 2) k_set_ring<2><<<blocks_for(work), 256, 0, s>>>(insts, inst);
