@@ -82,6 +82,13 @@ HELM_API const char* helm_last_error(void);
  * (graph replays count every kernel node they run).  Used to report launch counts. */
 HELM_API uint64_t helm_launch_count(void);
 
+/* Diagnostic: compares, on `count` seeded random values, the integer-pipe binary64 ->
+ * binary32 (round to nearest even) and binary32 -> binary64 conversions the complex64
+ * residual path uses with the GPU's own conversions; *mismatches = disagreements outside
+ * the binary32 subnormal range (which these conversions flush to zero).  Synchronous;
+ * allocates 8 bytes of device memory for the count. */
+HELM_API helm_status helm_selftest_conversions(int count, uint64_t seed, uint64_t* mismatches);
+
 /*
  * Plan: one cavity geometry (D, n, h), wave number k and precision, with its multigrid
  * hierarchy and workspace allocated on the current CUDA device.

@@ -35,6 +35,7 @@ _SIGS = {
     "helm_status_str": (C.c_char_p, [C.c_int]),
     "helm_last_error": (C.c_char_p, []),
     "helm_launch_count": (C.c_uint64, []),
+    "helm_selftest_conversions": (C.c_int, [C.c_int, C.c_uint64, C.POINTER(C.c_uint64)]),
     "helm_plan_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(C.c_int), C.c_double,
                                    C.c_double, C.c_int, C.c_int, _vp]),
     "helm_plan_destroy": (C.c_int, [_vp]),
@@ -134,6 +135,13 @@ def helm_last_error() -> str:
 
 def helm_launch_count() -> int:
     return int(load().helm_launch_count())
+
+
+def helm_selftest_conversions(count: int = 1 << 20, seed: int = 1) -> int:
+    bad = C.c_uint64()
+    _check(load().helm_selftest_conversions(int(count), C.c_uint64(seed), C.byref(bad)),
+           "helm_selftest_conversions")
+    return int(bad.value)
 
 
 class _Plan:

@@ -39,6 +39,7 @@ struct InstDesc {
     int max_outer, nres_blocks; // residual tiles (one partial sum each)
     int res_tx, res_ty;         // residual tile grid (x tiles, y tiles); z tiles = n (3D)
     double h, k2, tol;
+    double ih2, cdiag;          // 1/h^2 and k^2 - 2D/h^2 (the stencil's diagonal)
     double2* u[2];              // u[0] = caller's array, u[1] = library buffer
     const double2* f;
     const double2* g;

@@ -58,6 +58,8 @@ size_t layout(InstDesc& d, int D, int n, double h, double k, int prec, char* bas
     d.n = n;
     d.h = h;
     d.k2 = k * k;
+    d.ih2 = 1.0 / (h * h);
+    d.cdiag = d.k2 - 2.0 * D * d.ih2;
     int nl = 0, lt = -1;
     for (int m = n; m >= 1 && nl < HELM_MAXLEV; m = (m - 1) / 2) {
         if (lt < 0 && m <= tail_n(D)) lt = nl;
@@ -253,15 +255,25 @@ struct Engine {
             }
             ph[j] = p;
         }
-        const int tail_off = (int)items.size();
-        int ntail = 0;
-        double b_tail = 0.0, b_l0 = 0.0, b_res = 0.0;
+        // tail items grouped by their top size (one launch per size present)
+        struct TailGroup { int off, cnt, n0; double bytes; };
+        std::vector<TailGroup> tails;
+        double b_l0 = 0.0, b_res = 0.0;
+        for (int n0 = 1; n0 <= 63; n0 = 2 * n0 + 1) {
+            TailGroup tg{(int)items.size(), 0, n0, 0.0};
+            for (int i = 0; i < cap; ++i) {
+                if (!slots[i]) continue;
+                const InstDesc& d = slots[i]->d;
+                if (d.lev[d.ltail].n != n0) continue;
+                items.push_back(MgItem{i, d.ltail});
+                ++tg.cnt;
+                tg.bytes += 2.0 * pts(n0) * eb;                      // rhs in, e out
+            }
+            if (tg.cnt) tails.push_back(tg);
+        }
         for (int i = 0; i < cap; ++i)
             if (slots[i]) {
                 const InstDesc& d = slots[i]->d;
-                items.push_back(MgItem{i, d.ltail});
-                ++ntail;
-                b_tail += 2.0 * pts(d.lev[d.ltail].n) * eb;       // rhs in, e out
                 b_l0 += pts(d.n) * eb;
                 // residual + update: u, e, f in; u', r out
                 b_res += pts(d.n) * (16.0 + eb + 16.0 + 16.0 + eb);
@@ -301,16 +313,20 @@ struct Engine {
             HELM_CK(cudaMemcpy(d_res, res.data(), res.size() * sizeof(ResItem), cudaMemcpyHostToDevice));
         nres = (int)res.size();
 
+        auto tail = [&](std::vector<LaunchRec>& out, bool zero_start) {
+            for (const TailGroup& tg : tails)
+                out.push_back({LaunchRec::TAIL, tg.off, tg.cnt, tg.n0, 0, zero_start ? 0 : 1, tg.bytes});
+        };
         auto vcycle2d = [&](std::vector<LaunchRec>& out, bool zero_start) {
             for (int j = 0; j < J; ++j)
                 out.push_back({LaunchRec::DOWN, ph[j].off, ph[j].cnt, ph[j].tiles, 0,
                                zero_start ? 2 : 1, 0.0});
-            out.push_back({LaunchRec::TAIL, tail_off, ntail, 0, 0, zero_start ? 0 : 1, b_tail});
+            tail(out, zero_start);
             for (int j = J - 1; j >= 0; --j)
                 out.push_back({LaunchRec::UP, ph[j].off, ph[j].cnt, ph[j].tiles, 0, 0, 0.0});
         };
         auto vcycle = [&](std::vector<LaunchRec>& out, bool zero_start) {
-            if (D == 2) { vcycle2d(out, zero_start); return; }
+            if (D == 2 && nu1 <= 4 && nu2 <= 4) { vcycle2d(out, zero_start); return; }
             if (zero_start && nu1 == 0)
                 out.push_back({LaunchRec::ZERO, l0_off, nl0, w_l0, 0, 0, b_l0});
             for (int j = 0; j < J; ++j) {
@@ -321,7 +337,7 @@ struct Engine {
                 }
                 out.push_back({LaunchRec::RESTRICT, ph[j].off, ph[j].cnt, ph[j].w_rs, 0, 0, ph[j].b_rs});
             }
-            out.push_back({LaunchRec::TAIL, tail_off, ntail, 0, 0, zero_start ? 0 : 1, b_tail});
+            tail(out, zero_start);
             for (int j = J - 1; j >= 0; --j) {
                 out.push_back({LaunchRec::PROLONG, ph[j].off, ph[j].cnt, ph[j].w_pr, 0, 0, ph[j].b_pr});
                 for (int s = 0; s < nu2; ++s) {
@@ -395,8 +411,8 @@ struct Engine {
                 e = launch_zero(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s);
                 break;
             case LaunchRec::TAIL:
-                e = launch_tail(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, nu1, nu2, L.mode,
-                                max_tail, s);
+                e = launch_tail(D, prec, L.work, d_desc, d_state, d_mg + L.off, L.cnt, nu1, nu2,
+                                L.mode, s);
                 break;
             case LaunchRec::DOWN:
                 e = launch_down2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu1, L.mode, s);
@@ -653,6 +669,15 @@ const char* helm_last_error(void) { return g_errbuf; }
 
 uint64_t helm_launch_count(void) { return g_launches.load(); }
 
+helm_status helm_selftest_conversions(int count, uint64_t seed, uint64_t* mismatches)
+{
+    if (count <= 0 || !mismatches) return HELM_EINVAL;
+    unsigned long long bad = 0;
+    HELM_CK(run_fp_bits_check(count, (unsigned long long)seed, &bad));
+    *mismatches = bad;
+    return HELM_OK;
+}
+
 helm_status helm_plan_create(helm_plan** out, int ndim, const int* n, double h, double k, int bc,
                              int prec, void* cuda_stream)
 {
@@ -743,6 +768,7 @@ helm_status helm_solve_ex(helm_plan* p, const void* f, const void* g, void* u, d
     in.d.tol = tol;
     in.d.max_outer = max_outer;
     in.d.k2 = p->k * p->k;
+    in.d.cdiag = in.d.k2 - 2.0 * p->D * in.d.ih2;
     helm_status st = p->eng.prepare();
     if (st != HELM_OK) return st;
     st = p->eng.start_instance(0, p->stream);

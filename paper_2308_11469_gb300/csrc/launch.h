@@ -26,11 +26,12 @@ cudaError_t launch_prolong(int D, int prec, const InstDesc* insts, const InstSta
 // zero the iterate of the listed levels (ring included)
 cudaError_t launch_zero(int D, int prec, const InstDesc* insts, const InstState* st,
                         const MgItem* items, int nitems, int work, cudaStream_t s);
-// one CTA per item: V(nu1,nu2) on levels item.level..coarsest in shared memory.
-// load_e: start from the level's e in global memory instead of zero.
-cudaError_t launch_tail(int D, int prec, const InstDesc* insts, const InstState* st,
+// tail.cu: one CTA per item runs V(nu1,nu2) on levels item.level..coarsest in shared
+// memory; every item of one launch has top size n0.  load_e: start level 0 from its e in
+// global memory instead of zero.
+cudaError_t launch_tail(int D, int prec, int n0, const InstDesc* insts, const InstState* st,
                         const MgItem* items, int nitems, int nu1, int nu2, int load_e,
-                        int max_tail_n, cudaStream_t s);
+                        cudaStream_t s);
 size_t tail_smem_bytes(int D, int prec, int n);
 // raise the tail kernel's dynamic shared-memory limit (once, before any capture)
 cudaError_t setup_tail(int D, int prec);
@@ -57,6 +58,7 @@ int residual_tile_cols(int D);
 // Any instance still iterating?  Counts the step, sets the while-loop condition.
 cudaError_t launch_check(const InstState* st, int ninst, int* ctrl, int use_cond,
                          unsigned long long cond_handle, cudaStream_t s);
+cudaError_t run_fp_bits_check(int count, unsigned long long seed, unsigned long long* bad_host);
 // u[0] and u[1] rings := g ring
 cudaError_t launch_set_ring(int D, const InstDesc* insts, int inst, int n, cudaStream_t s);
 // interior tight <-> level-0 padded/pitched, inner precision

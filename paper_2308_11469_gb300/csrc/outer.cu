@@ -19,19 +19,25 @@
 // max |e|^2; the last tile of an instance to finish (atomic ticket) sums the partials in
 // tile order (deterministic), forms relres and applies the status rule.
 #include "launch.h"
+#include "fp_bits.cuh"
 
 namespace helm {
 namespace {
 
 constexpr int NTH = 256;
 
-template <typename R>
-__device__ __forceinline__ typename C2<R>::T to_inner(double2 v) {
-    typename C2<R>::T o;
-    o.x = (R)v.x;
-    o.y = (R)v.y;
-    return o;
-}
+// FP64 -> inner precision and back; for complex64 the format changes run on the
+// integer pipes (fp_bits.cuh), leaving the FP64 pipe to the update and the stencil.
+__device__ __forceinline__ float2 to_inner_f(double2 v) { return make_float2(d2f_bits(v.x), d2f_bits(v.y)); }
+template <typename R> struct Inner;
+template <> struct Inner<float> {
+    static __device__ __forceinline__ float2 from(double2 v) { return to_inner_f(v); }
+    static __device__ __forceinline__ double widen(float x) { return f2d_bits(x); }
+};
+template <> struct Inner<double> {
+    static __device__ __forceinline__ double2 from(double2 v) { return v; }
+    static __device__ __forceinline__ double widen(double x) { return x; }
+};
 
 // Status rule (the paper only reports "converges" / "diverges"; this project's reading):
 // CONVERGED when relres <= tol; DIVERGED when relres > 1e4, or when N >= 20 and relres
@@ -158,8 +164,8 @@ k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
             v = uin[gy * S + gx];
             if (MODE == 1 && gx >= 1 && gx <= n && gy >= 1 && gy <= n) {
                 const c2 ev = e[gy * P + gx];
-                v.x += (double)ev.x;
-                v.y += (double)ev.y;
+                v.x += Inner<R>::widen(ev.x);
+                v.y += Inner<R>::widen(ev.y);
                 if (lx >= 1 && lx <= T2 && ly >= 1 && ly <= T2)
                     emax2 = fmax(emax2, ev.x * ev.x + ev.y * ev.y);
             }
@@ -167,8 +173,8 @@ k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
         U[q] = v;
     }
     __syncthreads();
-    const double ih2 = 1.0 / (I.h * I.h);
-    const double cdiag = I.k2 - 4.0 * ih2;
+    const double mih2 = -I.ih2;
+    const double mcdiag = -I.cdiag;
     R r2 = 0;
     const int lx = (threadIdx.x & 31) + 1;
 #pragma unroll
@@ -181,10 +187,11 @@ k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
         const double2 a = U[o - 1], b = U[o + 1], d = U[o - (T2 + 2)], u = U[o + (T2 + 2)];
         if (MODE == 1) uout[gy * S + gx] = c;
         const double2 fv = f[(size_t)(gy - 1) * n + (gx - 1)];
+        // r = f - (Delta_h + k^2) u = f - cdiag u - (sum of the 4 neighbours) / h^2
         double2 r;
-        r.x = fv.x - fma(((a.x + b.x) + (d.x + u.x)), ih2, cdiag * c.x);
-        r.y = fv.y - fma(((a.y + b.y) + (d.y + u.y)), ih2, cdiag * c.y);
-        const c2 ri = to_inner<R>(r);
+        r.x = fma((a.x + b.x) + (d.x + u.x), mih2, fma(c.x, mcdiag, fv.x));
+        r.y = fma((a.y + b.y) + (d.y + u.y), mih2, fma(c.y, mcdiag, fv.y));
+        const c2 ri = Inner<R>::from(r);
         rhs[gy * P + gx] = ri;
         r2 += ri.x * ri.x + ri.y * ri.y;
     }
@@ -216,8 +223,8 @@ k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     c2* __restrict__ rhs = (c2*)L0.rhs;
     const long P = L0.pitch;
     const long PL = (long)L0.pitch * L0.rows;
-    const double ih2 = 1.0 / (I.h * I.h);
-    const double cdiag = I.k2 - 6.0 * ih2;
+    const double mih2 = -I.ih2;
+    const double mcdiag = -I.cdiag;
     const int x = item.tx * 32 + (threadIdx.x & 31) + 1;
     const int z = item.tz + 1;
     R r2 = 0, emax2 = 0;
@@ -234,21 +241,21 @@ k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
             const c2 e0 = e[oe];
             const c2 e1 = e[oe - 1], e2 = e[oe + 1], e3 = e[oe - P], e4 = e[oe + P];
             const c2 e5 = e[oe - PL], e6 = e[oe + PL];
-            c.x += (double)e0.x;  c.y += (double)e0.y;
-            w.x += (double)e1.x;  w.y += (double)e1.y;
-            ea.x += (double)e2.x; ea.y += (double)e2.y;
-            so.x += (double)e3.x; so.y += (double)e3.y;
-            no.x += (double)e4.x; no.y += (double)e4.y;
-            dn.x += (double)e5.x; dn.y += (double)e5.y;
-            up.x += (double)e6.x; up.y += (double)e6.y;
+            c.x += Inner<R>::widen(e0.x);  c.y += Inner<R>::widen(e0.y);
+            w.x += Inner<R>::widen(e1.x);  w.y += Inner<R>::widen(e1.y);
+            ea.x += Inner<R>::widen(e2.x); ea.y += Inner<R>::widen(e2.y);
+            so.x += Inner<R>::widen(e3.x); so.y += Inner<R>::widen(e3.y);
+            no.x += Inner<R>::widen(e4.x); no.y += Inner<R>::widen(e4.y);
+            dn.x += Inner<R>::widen(e5.x); dn.y += Inner<R>::widen(e5.y);
+            up.x += Inner<R>::widen(e6.x); up.y += Inner<R>::widen(e6.y);
             uout[ou] = c;
             emax2 = fmax(emax2, e0.x * e0.x + e0.y * e0.y);
         }
         const double2 fv = f[((long)(z - 1) * n + (y - 1)) * n + (x - 1)];
         double2 r;
-        r.x = fv.x - fma(((w.x + ea.x) + (so.x + no.x)) + (dn.x + up.x), ih2, cdiag * c.x);
-        r.y = fv.y - fma(((w.y + ea.y) + (so.y + no.y)) + (dn.y + up.y), ih2, cdiag * c.y);
-        const c2 ri = to_inner<R>(r);
+        r.x = fma(((w.x + ea.x) + (so.x + no.x)) + (dn.x + up.x), mih2, fma(c.x, mcdiag, fv.x));
+        r.y = fma(((w.y + ea.y) + (so.y + no.y)) + (dn.y + up.y), mih2, fma(c.y, mcdiag, fv.y));
+        const c2 ri = Inner<R>::from(r);
         rhs[oe] = ri;
         r2 += ri.x * ri.x + ri.y * ri.y;
     }
@@ -338,6 +345,48 @@ __global__ void k_unpack(const InstDesc* __restrict__ insts, int inst, void* __r
     }
 }
 
+// Self-test of the integer-pipe conversions against the hardware conversions on random
+// values of the binary32 range, exact ties, and the special values.
+__device__ __forceinline__ unsigned long long splitmix(unsigned long long x)
+{
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+__global__ void k_fp_bits_check(unsigned long long seed, int count, unsigned long long* bad)
+{
+    unsigned long long local = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const unsigned long long r = splitmix(seed + (unsigned long long)i);
+        // binary64 with an exponent inside (or just outside) the binary32 range
+        const unsigned long long ex = 1023ull - 130ull + ((r >> 52) % 261ull);
+        unsigned long long frac = r & 0x000fffffffffffffull;
+        const unsigned kind = (unsigned)(r >> 61);
+        if (kind == 0) frac = (frac & ~0x1fffffffull) | 0x10000000ull;   // exact tie
+        if (kind == 1) frac &= ~0x1fffffffull;                           // exactly representable
+        const unsigned long long bits = ((r >> 51) & 1ull) << 63 | ex << 52 | frac;
+        double d = __longlong_as_double((long long)bits);
+        if (i < 6) {
+            const double sp[6] = {0.0, -0.0, 1.0 / 0.0, -1.0 / 0.0, 0.0 / 0.0, 3.4028235677973366e38};
+            d = sp[i];
+        }
+        const float ref = __double2float_rn(d);
+        const float got = d2f_bits(d);
+        const unsigned rb = __float_as_uint(ref), gb = __float_as_uint(got);
+        const bool sub = (rb & 0x7f800000u) == 0u && (rb & 0x007fffffu) != 0u;
+        if (!sub && !(isnan(ref) && isnan(got)) && rb != gb) ++local;
+        // binary32 -> binary64 (exact) on the normal range and the special values
+        const float f = __uint_as_float((unsigned)(r >> 17));
+        const unsigned fb = __float_as_uint(f);
+        const bool fsub = (fb & 0x7f800000u) == 0u && (fb & 0x007fffffu) != 0u;
+        const double w = f2d_bits(f), wr = (double)f;
+        if (!fsub && !(isnan(w) && isnan(wr)) && __double_as_longlong(w) != __double_as_longlong(wr)) ++local;
+    }
+    if (local) atomicAdd(bad, local);
+}
+
 inline int blocks_for(long work) {
     long b = (work + 255) / 256;
     if (b < 1) b = 1;
@@ -348,6 +397,19 @@ inline int blocks_for(long work) {
 }  // namespace
 
 int residual_tile_rows(int D) { return D == 2 ? T2 : 16; }
+
+cudaError_t run_fp_bits_check(int count, unsigned long long seed, unsigned long long* bad_host)
+{
+    unsigned long long* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(unsigned long long));
+    if (e != cudaSuccess) return e;
+    cudaMemset(d, 0, sizeof(unsigned long long));
+    k_fp_bits_check<<<1216, 256>>>(seed, count, d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(bad_host, d, sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e;
+}
 int residual_tile_cols(int D) { return 32; }
 
 cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* st,

@@ -10,9 +10,7 @@
 //   k_restrict  coarse rhs = full weighting ([1,2,1]/4 per axis) of the fine residual
 //               rhs - Delta_h e, coarse iterate = 0.
 //   k_prolong   e_fine += multilinear interpolation of e_coarse.
-//   k_tail      one CTA per item runs the rest of the V-cycle (levels with n <= 63 in 2D,
-//               n <= 15 in 3D) entirely in shared memory, down to the one-node exact
-//               solve e = -h^2 rhs / (2D).
+// The coarse levels (n <= 63 in 2D, n <= 15 in 3D) run inside one CTA (tail.cu).
 #include "launch.h"
 
 namespace helm {
@@ -210,207 +208,6 @@ k_zero(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
         e[q] = cz<c2>();
 }
 
-// ---------------------------------------------------------------------------
-// Tail: the coarse part of the V-cycle inside one CTA (shared memory)
-// ---------------------------------------------------------------------------
-template <int D>
-__device__ __forceinline__ int sidx(int n, int x, int y, int z) {
-    const int s = n + 2;
-    return ((D == 3) ? (z * s + y) : y) * s + x;
-}
-
-template <int D, typename R>
-__device__ void tail_half_sweep(typename C2<R>::T* e, const typename C2<R>::T* r, int n, R h,
-                                int color)
-{
-    typedef typename C2<R>::T c2;
-    const int half = (n + 1) >> 1;
-    const int rows = (D == 3) ? n * n : n;
-    const int total = rows * half;
-    const int s = n + 2, sp = s * s;
-    const R h2 = h * h;
-    const R inv = (R)1 / (R)(2 * D);
-    for (int q = threadIdx.x; q < total; q += blockDim.x) {
-        const int j = q % half;
-        const int row = q / half;
-        const int y = (D == 3) ? row % n + 1 : row + 1;
-        const int z = (D == 3) ? row / n + 1 : 0;
-        const int xa = 2 * j + 1;
-        const int xc = (((xa + y + z) & 1) == color) ? xa : xa + 1;
-        if (xc > n) continue;
-        const int o = sidx<D>(n, xc, y, z);
-        const c2 a = e[o - 1], b = e[o + 1], c = e[o - s], d = e[o + s];
-        R sx = a.x + b.x + c.x + d.x;
-        R sy = a.y + b.y + c.y + d.y;
-        if (D == 3) {
-            const c2 f = e[o - sp], g = e[o + sp];
-            sx += f.x + g.x;
-            sy += f.y + g.y;
-        }
-        const c2 rr = r[o];
-        c2 v;
-        v.x = (sx - h2 * rr.x) * inv;
-        v.y = (sy - h2 * rr.y) * inv;
-        e[o] = v;
-    }
-}
-
-template <int D, typename R>
-__global__ void __launch_bounds__(512)
-k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
-       const MgItem* __restrict__ items, int nu1, int nu2, int load_e)
-{
-    typedef typename C2<R>::T c2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    c2* base = reinterpret_cast<c2*>(smem_raw);
-    const MgItem item = items[blockIdx.x];
-    if (st[item.inst].status != HELM_ST_ACTIVE) return;
-    const LevelDesc L0 = insts[item.inst].lev[item.level];
-    const int n0 = L0.n;
-    c2* E[8];
-    c2* Rr[8];
-    int N[8];
-    int T = 0;
-    int total = 0;
-    for (int m = n0; m >= 1 && T < 8; m = (m - 1) >> 1) {
-        const int sz = (D == 3) ? (m + 2) * (m + 2) * (m + 2) : (m + 2) * (m + 2);
-        N[T] = m;
-        E[T] = base + total;
-        total += sz;
-        Rr[T] = base + total;
-        total += sz;
-        ++T;
-    }
-    for (int i = threadIdx.x; i < total; i += blockDim.x) base[i] = cz<c2>();
-    __syncthreads();
-    {
-        const c2* gr = (const c2*)L0.rhs;
-        const c2* ge = (const c2*)L0.e;
-        const int tot = (D == 3) ? n0 * n0 * n0 : n0 * n0;
-        for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-            const int x = q % n0 + 1;
-            const int y = (q / n0) % n0 + 1;
-            const int z = (D == 3) ? q / (n0 * n0) + 1 : 0;
-            const size_t g = off<D>(L0, x, y, z);
-            const int s = sidx<D>(n0, x, y, z);
-            Rr[0][s] = gr[g];
-            if (load_e && item.level == 0) E[0][s] = ge[g];
-        }
-    }
-    __syncthreads();
-    R h = (R)L0.h;
-    // descent
-    for (int t = 0; t + 1 < T; ++t) {
-        const int n = N[t];
-        for (int it = 0; it < nu1; ++it) {
-            tail_half_sweep<D, R>(E[t], Rr[t], n, h, 0);
-            __syncthreads();
-            tail_half_sweep<D, R>(E[t], Rr[t], n, h, 1);
-            __syncthreads();
-        }
-        // restriction of the residual into Rr[t+1]
-        const int nc = N[t + 1];
-        const int tot = (D == 3) ? nc * nc * nc : nc * nc;
-        const int s = n + 2, sp = s * s;
-        const R ih2 = (R)1 / (h * h);
-        const R scale = (D == 3) ? (R)(1.0 / 64.0) : (R)(1.0 / 16.0);
-        for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-            const int X = q % nc + 1;
-            const int Y = (q / nc) % nc + 1;
-            const int Z = (D == 3) ? q / (nc * nc) + 1 : 0;
-            R ax = 0, ay = 0;
-            const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
-            for (int dz = zlo; dz <= zhi; ++dz) {
-                const R wz = (D == 3) ? (dz == 0 ? (R)2 : (R)1) : (R)1;
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const R wy = (dy == 0) ? (R)2 : (R)1;
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const R w = wz * wy * ((dx == 0) ? (R)2 : (R)1);
-                        const int o = sidx<D>(n, 2 * X + dx, 2 * Y + dy, 2 * Z + dz);
-                        const c2* e = E[t];
-                        const c2 c = e[o], a = e[o - 1], b = e[o + 1], u = e[o - s], d = e[o + s];
-                        R sx = a.x + b.x + u.x + d.x;
-                        R sy = a.y + b.y + u.y + d.y;
-                        if (D == 3) {
-                            const c2 f = e[o - sp], g = e[o + sp];
-                            sx += f.x + g.x;
-                            sy += f.y + g.y;
-                        }
-                        const c2 rr = Rr[t][o];
-                        ax += w * (rr.x - (sx - (R)(2 * D) * c.x) * ih2);
-                        ay += w * (rr.y - (sy - (R)(2 * D) * c.y) * ih2);
-                    }
-                }
-            }
-            c2 v;
-            v.x = ax * scale;
-            v.y = ay * scale;
-            Rr[t + 1][sidx<D>(nc, X, Y, Z)] = v;
-        }
-        __syncthreads();
-        h = h * (R)2;
-    }
-    // coarsest level: one node, exact
-    if (threadIdx.x == 0) {
-        const int o = sidx<D>(1, 1, 1, 1);
-        const c2 rr = Rr[T - 1][o];
-        const R c = -(h * h) / (R)(2 * D);
-        c2 v;
-        v.x = c * rr.x;
-        v.y = c * rr.y;
-        E[T - 1][o] = v;
-    }
-    __syncthreads();
-    // ascent
-    for (int t = T - 2; t >= 0; --t) {
-        h = h * (R)0.5;
-        const int n = N[t];
-        const int nc = N[t + 1];
-        const int tot = (D == 3) ? n * n * n : n * n;
-        for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-            const int x = q % n + 1;
-            const int y = (q / n) % n + 1;
-            const int z = (D == 3) ? q / (n * n) + 1 : 0;
-            const int x0 = x >> 1, x1 = (x + 1) >> 1;
-            const int y0 = y >> 1, y1 = (y + 1) >> 1;
-            const int z0 = z >> 1, z1 = (z + 1) >> 1;
-            R vx = 0, vy = 0;
-            const int nz = (D == 3) ? 2 : 1;
-            for (int iz = 0; iz < nz; ++iz)
-                for (int iy = 0; iy < 2; ++iy)
-                    for (int ix = 0; ix < 2; ++ix) {
-                        const c2 c = E[t + 1][sidx<D>(nc, ix ? x1 : x0, iy ? y1 : y0,
-                                                      iz ? z1 : z0)];
-                        vx += c.x;
-                        vy += c.y;
-                    }
-            const R w = (D == 3) ? (R)0.125 : (R)0.25;
-            const int o = sidx<D>(n, x, y, z);
-            c2 v = E[t][o];
-            v.x += w * vx;
-            v.y += w * vy;
-            E[t][o] = v;
-        }
-        __syncthreads();
-        for (int it = 0; it < nu2; ++it) {
-            tail_half_sweep<D, R>(E[t], Rr[t], n, h, 0);
-            __syncthreads();
-            tail_half_sweep<D, R>(E[t], Rr[t], n, h, 1);
-            __syncthreads();
-        }
-    }
-    {
-        c2* ge = (c2*)L0.e;
-        const int tot = (D == 3) ? n0 * n0 * n0 : n0 * n0;
-        for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-            const int x = q % n0 + 1;
-            const int y = (q / n0) % n0 + 1;
-            const int z = (D == 3) ? q / (n0 * n0) + 1 : 0;
-            ge[off<D>(L0, x, y, z)] = E[0][sidx<D>(n0, x, y, z)];
-        }
-    }
-}
-
 inline dim3 mg_grid(int work, int nitems) {
     int bx = (work + 255) / 256;
     if (bx < 1) bx = 1;
@@ -463,52 +260,6 @@ cudaError_t launch_zero(int D, int prec, const InstDesc* insts, const InstState*
     else if (prec == 0) k_zero<3, double><<<g, 256, 0, s>>>(insts, st, items);
     else k_zero<3, float><<<g, 256, 0, s>>>(insts, st, items);
     return cudaGetLastError();
-}
-
-size_t tail_smem_bytes(int D, int prec, int n)
-{
-    size_t elem = prec == 0 ? 16 : 8;
-    size_t tot = 0;
-    for (int m = n; m >= 1; m = (m - 1) >> 1) {
-        size_t s = (size_t)(m + 2);
-        tot += 2 * ((D == 3) ? s * s * s : s * s);
-    }
-    return tot * elem;
-}
-
-template <int D, typename R>
-static cudaError_t tail_launch(const InstDesc* insts, const InstState* st, const MgItem* items,
-                               int nitems, int nu1, int nu2, int load_e, int max_n,
-                               cudaStream_t s)
-{
-    const size_t smem = tail_smem_bytes(D, sizeof(R) == 8 ? 0 : 1, max_n);
-    k_tail<D, R><<<nitems, 512, smem, s>>>(insts, st, items, nu1, nu2, load_e);
-    return cudaGetLastError();
-}
-
-template <int D, typename R>
-static cudaError_t tail_attr()
-{
-    const size_t smem = tail_smem_bytes(D, sizeof(R) == 8 ? 0 : 1, D == 2 ? TAIL_N_2D : TAIL_N_3D);
-    return cudaFuncSetAttribute(k_tail<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-cudaError_t setup_tail(int D, int prec)
-{
-    if (D == 2 && prec == 0) return tail_attr<2, double>();
-    if (D == 2) return tail_attr<2, float>();
-    if (prec == 0) return tail_attr<3, double>();
-    return tail_attr<3, float>();
-}
-
-cudaError_t launch_tail(int D, int prec, const InstDesc* insts, const InstState* st,
-                        const MgItem* items, int nitems, int nu1, int nu2, int load_e,
-                        int max_tail_n, cudaStream_t s)
-{
-    if (D == 2 && prec == 0) return tail_launch<2, double>(insts, st, items, nitems, nu1, nu2, load_e, max_tail_n, s);
-    if (D == 2) return tail_launch<2, float>(insts, st, items, nitems, nu1, nu2, load_e, max_tail_n, s);
-    if (prec == 0) return tail_launch<3, double>(insts, st, items, nitems, nu1, nu2, load_e, max_tail_n, s);
-    return tail_launch<3, float>(insts, st, items, nitems, nu1, nu2, load_e, max_tail_n, s);
 }
 
 }  // namespace helm

@@ -276,3 +276,9 @@ def test_repeated_solves_are_deterministic(B):
     assert a[1] == b[1]
     assert np.array_equal(a[2], b[2])
     assert np.array_equal(a[4], b[4])
+
+
+def test_integer_pipe_conversions_match_hardware(B):
+    # the complex64 residual path converts with integer operations; they must agree with
+    # the GPU's own IEEE conversions (round to nearest even) outside the subnormal range
+    assert B.helm_selftest_conversions(1 << 22, 12345) == 0
