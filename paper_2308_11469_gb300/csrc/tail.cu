@@ -14,7 +14,7 @@
 namespace helm {
 namespace {
 
-constexpr int TNT = 512;
+constexpr int TNT = 1024;
 
 template <int D, int N> struct Lv {
     static constexpr int S = N + 2;

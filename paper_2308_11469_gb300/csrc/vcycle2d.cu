@@ -27,7 +27,7 @@ namespace {
 
 constexpr int TX = 64;
 constexpr int TY = 32;
-constexpr int NT = 256;
+constexpr int NT = 512;
 constexpr int NW = NT / 32;
 
 template <typename T> __device__ __forceinline__ T cz() { T v; v.x = 0; v.y = 0; return v; }
