@@ -151,6 +151,28 @@ HELM_API helm_status helm_solve_ex(helm_plan* plan, const void* f, const void* g
 HELM_API helm_status poisson_vcycle(helm_plan* plan, const void* rhs, void* e, int nu1, int nu2);
 
 /*
+ * poisson_vcycle without a plan and without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc -- code
+ * running under another framework's memory manager that has reserved the device memory,
+ * or a latency-critical loop that cannot take the implicit device synchronisation of
+ * cudaMalloc / cudaFree.  It runs the same kernels as poisson_vcycle (same cycle, same
+ * results) on one statically sized device array of 16 MiB that the library keeps on every
+ * device that loads it, until the process exits (enough for 2D n <= 511 in complex64,
+ * 2D n <= 255 in complex128, 3D n <= 63 in either precision).
+ *   ndim, n, h, prec   as helm_plan_create (prec picks complex64 or complex128 arrays).
+ *   rhs, e             as poisson_vcycle (interior n^D, device, 16-byte aligned).
+ *   cuda_stream        stream the work is enqueued on (NULL = legacy default stream).
+ * Returns HELM_EUNSUPPORTED, doing nothing, when the grid's multigrid arrays would not fit
+ * the 16 MiB array.  Asynchronous: the result is in e once the stream reaches it.
+ * The first call on a device (with that device current) looks up the array's device
+ * address and raises the kernels' shared-memory limits; make that first call before any
+ * stream capture.  Every call reuses the same array (it clears what it uses), so calls
+ * that overlap on the GPU -- from two streams or two host threads -- race.
+ */
+HELM_API helm_status poisson_vcycle_noalloc(int ndim, int n, double h, int prec, const void* rhs,
+                                            void* e, int nu1, int nu2, void* cuda_stream);
+
+/*
  * Batch / serving: many independent solves of uneven size, dimension and k advanced
  * together, each outer step of all active instances in one launch per kernel.
  *   hbm_cap_bytes  device-memory cap for the instances' workspace (0 = no cap).

@@ -16,6 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libhelm.so")
 
+HELM_OK = 0
 HELM_CONVERGED = 0
 HELM_MAXITER = 1
 HELM_DIVERGED = 2
@@ -47,6 +48,8 @@ _SIGS = {
     "helm_solve_ex": (C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int),
                                 C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "poisson_vcycle": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int]),
+    "poisson_vcycle_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_int, _vp, _vp, C.c_int,
+                                         C.c_int, _vp]),
     "helm_batch_create": (C.c_int, [C.POINTER(_vp), C.c_size_t, _vp]),
     "helm_batch_destroy": (C.c_int, [_vp]),
     "helm_batch_submit": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_double, C.c_int,
@@ -220,6 +223,22 @@ def poisson_vcycle(plan: _Plan, rhs, e, nu1: int = 2, nu2: int = 2) -> None:
     pr = _ptr(rhs, plan.inner_dtype, (n,) * D, "rhs")
     pe = _ptr(e, plan.inner_dtype, (n,) * D, "e")
     _check(load().poisson_vcycle(plan.handle, pr, pe, int(nu1), int(nu2)), "poisson_vcycle")
+
+
+def poisson_vcycle_noalloc(ndim: int, n: int, h: float, prec: int, rhs, e, nu1: int = 2,
+                           nu2: int = 2, stream=None) -> int:
+    """One V-cycle without a plan or any device allocation (the library's static scratch
+    array); asynchronous on the stream.  Returns the status (HELM_EUNSUPPORTED when the
+    grid does not fit the scratch array)."""
+    import torch
+    dt = torch.complex128 if prec == HELM_PREC_FP64 else torch.complex64
+    pr = _ptr(rhs, dt, (n,) * ndim, "rhs")
+    pe = _ptr(e, dt, (n,) * ndim, "e")
+    st = load().poisson_vcycle_noalloc(int(ndim), int(n), float(h), int(prec), pr, pe, int(nu1),
+                                       int(nu2), _stream_handle(stream))
+    if st != HELM_EUNSUPPORTED:
+        _check(st, "poisson_vcycle_noalloc")
+    return st
 
 
 class _Batch:
