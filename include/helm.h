@@ -57,7 +57,8 @@ typedef enum {
     HELM_CONVERGED = 0,      /* relres <= tol                                        */
     HELM_OK = 0,
     HELM_MAXITER = 1,        /* max_outer steps without convergence                 */
-    HELM_DIVERGED = 2,       /* relres > 1e4, or >= 20 steps and 10 non-decreasing  */
+    HELM_DIVERGED = 2,       /* relres > 1e4, or >= 20 steps, 10 non-decreasing and
+                                at least twice the smallest relres so far            */
     HELM_EINVAL = -1,        /* bad argument (null / misaligned pointer, bad size)  */
     HELM_ENOMEM = -2,        /* device allocation failed / batch memory cap reached */
     HELM_ECUDA = -3,         /* a CUDA runtime call failed                          */

@@ -29,8 +29,10 @@ Bookkeeping used throughout this project (readings of points the paper leaves op
 * The increment sup-norm ||v_n + i w_n||_inf is recorded too: Section 3 proposes
   truncating on the size of successive iterates.
 * Status (the paper only reports "converges" / "diverges"): CONVERGED when relres <= tol;
-  DIVERGED when relres > 1e4, or when N >= 20 and relres has not decreased for 10
-  consecutive steps; NONFINITE on a NaN / Inf; MAXITER when N reaches max_outer.
+  DIVERGED when relres > 1e4, or when N >= 20, relres has not decreased for 10
+  consecutive steps and has grown to at least twice its smallest value so far (so that
+  stagnation at the rounding floor is not taken for divergence); NONFINITE on a NaN /
+  Inf; MAXITER when N reaches max_outer.
 """
 from __future__ import annotations
 
@@ -49,6 +51,7 @@ NONFINITE = -4
 DIVERGE_RELRES = 1e4
 DIVERGE_MIN_STEPS = 20
 DIVERGE_RUN = 10
+DIVERGE_GROWTH = 2.0
 
 
 @dataclass
@@ -69,6 +72,7 @@ class StatusRule:
         self.max_outer = max_outer
         self.prev = None
         self.run = 0
+        self.rmin = math.inf
 
     def __call__(self, N: int, relres: float) -> int | None:
         if not math.isfinite(relres):
@@ -80,7 +84,9 @@ class StatusRule:
         if self.prev is not None:
             self.run = self.run + 1 if relres >= self.prev else 0
         self.prev = relres
-        if N >= DIVERGE_MIN_STEPS and self.run >= DIVERGE_RUN:
+        self.rmin = min(self.rmin, relres)
+        if (N >= DIVERGE_MIN_STEPS and self.run >= DIVERGE_RUN
+                and relres >= DIVERGE_GROWTH * self.rmin):
             return DIVERGED
         if N >= self.max_outer:
             return MAXITER

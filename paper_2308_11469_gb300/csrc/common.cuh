@@ -57,6 +57,7 @@ struct InstState {
     int pad_;
     double norm0;    // ||r_0||_2
     double prev;     // relres of the previous step
+    double rmin;     // smallest relres so far
 };
 
 // Work item of a multigrid launch: one (instance, level) pair; blocks stride over it.

@@ -179,6 +179,8 @@ struct Engine {
         HELM_CK(cudaMallocHost(&h_ctrl, 4 * sizeof(int)));
         HELM_CK(setup_tail(D, prec == HELM_PREC_FP64 ? 0 : 1));
         if (D == 2) HELM_CK(setup_2d(prec == HELM_PREC_FP64 ? 0 : 1));
+        HELM_CK(setup_generic(D, prec == HELM_PREC_FP64 ? 0 : 1));
+        HELM_CK(setup_outer());
         return grow(4);
     }
 

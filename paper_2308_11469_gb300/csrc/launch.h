@@ -35,6 +35,9 @@ cudaError_t launch_tail(int D, int prec, int n0, const InstDesc* insts, const In
 size_t tail_smem_bytes(int D, int prec, int n);
 // raise the tail kernel's dynamic shared-memory limit (once, before any capture)
 cudaError_t setup_tail(int D, int prec);
+// shared-memory carve-out preferences of the generic and outer kernels
+cudaError_t setup_generic(int D, int prec);
+cudaError_t setup_outer();
 
 // ---- fused 2D multigrid (vcycle2d.cu): two launches per level ----
 // descent: nu1 sweeps + residual + restriction; e (or zero) -> e2, coarse rhs.

@@ -19,6 +19,7 @@
 // max |e|^2; the last tile of an instance to finish (atomic ticket) sums the partials in
 // tile order (deterministic), forms relres and applies the status rule.
 #include "launch.h"
+#include "pdl.cuh"
 #include "fp_bits.cuh"
 
 namespace helm {
@@ -40,8 +41,10 @@ template <> struct Inner<double> {
 };
 
 // Status rule (the paper only reports "converges" / "diverges"; this project's reading):
-// CONVERGED when relres <= tol; DIVERGED when relres > 1e4, or when N >= 20 and relres
-// has not decreased for 10 consecutive steps; NONFINITE on NaN / Inf; MAXITER at max_outer.
+// CONVERGED when relres <= tol; DIVERGED when relres > 1e4, or when N >= 20, relres has
+// not decreased for 10 consecutive steps and has grown to at least twice its smallest
+// value so far (stagnation at the rounding floor is not divergence); NONFINITE on NaN /
+// Inf; MAXITER at max_outer.
 __device__ void finalize(const InstDesc& I, InstState* stp, double norm2, double emax2, int mode)
 {
     InstState s = *stp;
@@ -52,6 +55,7 @@ __device__ void finalize(const InstDesc& I, InstState* stp, double norm2, double
         N = 0;
         s.norm0 = norm;
         s.run = 0;
+        s.rmin = 1.0;
         rel = (norm == 0.0) ? 0.0 : 1.0;
         if (!isfinite(norm)) rel = norm;
     } else {
@@ -67,7 +71,8 @@ __device__ void finalize(const InstDesc& I, InstState* stp, double norm2, double
     else if (rel > 1e4) out = 2;                                    // DIVERGED
     else {
         if (mode != 0) s.run = (rel >= s.prev) ? s.run + 1 : 0;
-        if (N >= 20 && s.run >= 10) out = 2;                        // DIVERGED
+        s.rmin = fmin(s.rmin, rel);
+        if (N >= 20 && s.run >= 10 && rel >= 2.0 * s.rmin) out = 2; // DIVERGED
         else if (N >= I.max_outer) out = 1;                         // MAXITER
     }
     s.prev = rel;
@@ -138,6 +143,8 @@ __global__ void __launch_bounds__(NTH)
 k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
              const ResItem* __restrict__ items)
 {
+    pdl_wait();
+    pdl_trigger();
     typedef typename C2<R>::T c2;
     __shared__ double2 U[(T2 + 2) * (T2 + 2)];
     const ResItem item = items[blockIdx.x];
@@ -156,7 +163,12 @@ k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     const int P = L0.pitch;
     const int x0 = 1 + item.tx * T2, y0 = 1 + item.ty * T2;
     R emax2 = 0;
-    for (int q = threadIdx.x; q < (T2 + 2) * (T2 + 2); q += NTH) {
+    constexpr int NSTAGE = ((T2 + 2) * (T2 + 2) + NTH - 1) / NTH;
+    // fixed trip count, fully unrolled: all loads of the tile are issued before their uses
+#pragma unroll
+    for (int it = 0; it < NSTAGE; ++it) {
+        const int q = threadIdx.x + it * NTH;
+        if (q >= (T2 + 2) * (T2 + 2)) break;
         const int lx = q % (T2 + 2), ly = q / (T2 + 2);
         const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
         double2 v = make_double2(0.0, 0.0);
@@ -206,6 +218,8 @@ __global__ void __launch_bounds__(NTH)
 k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
              const ResItem* __restrict__ items)
 {
+    pdl_wait();
+    pdl_trigger();
     typedef typename C2<R>::T c2;
     const ResItem item = items[blockIdx.x];
     InstState* stp = st + item.inst;
@@ -268,6 +282,8 @@ __global__ void __launch_bounds__(256)
 k_check(const InstState* __restrict__ st, int ninst, int* __restrict__ ctrl, int use_cond,
         unsigned long long cond_handle)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int any_active;
     if (threadIdx.x == 0) any_active = 0;
     __syncthreads();
@@ -288,6 +304,8 @@ k_check(const InstState* __restrict__ st, int ninst, int* __restrict__ ctrl, int
 template <int D>
 __global__ void k_set_ring(const InstDesc* __restrict__ insts, int inst)
 {
+    pdl_wait();
+    pdl_trigger();
     const InstDesc& I = insts[inst];
     const int n = I.n, S = n + 2;
     const long total = (D == 3) ? (long)S * S * S : (long)S * S;
@@ -310,6 +328,8 @@ template <int D, typename R>
 __global__ void k_pack(const InstDesc* __restrict__ insts, int inst, const void* __restrict__ src,
                        int which)
 {
+    pdl_wait();
+    pdl_trigger();
     typedef typename C2<R>::T c2;
     const InstDesc& I = insts[inst];
     const LevelDesc L = I.lev[0];
@@ -329,6 +349,8 @@ __global__ void k_pack(const InstDesc* __restrict__ insts, int inst, const void*
 template <int D, typename R>
 __global__ void k_unpack(const InstDesc* __restrict__ insts, int inst, void* __restrict__ dst)
 {
+    pdl_wait();
+    pdl_trigger();
     typedef typename C2<R>::T c2;
     const InstDesc& I = insts[inst];
     const LevelDesc L = I.lev[0];
@@ -417,8 +439,8 @@ cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* s
 {
     if (nitems <= 0) return cudaSuccess;
 #define HELM_RES(K, RR)                                                                   \
-    (mode ? (K<RR, 1><<<nitems, NTH, 0, s>>>(insts, st, items), 0)                         \
-          : (K<RR, 0><<<nitems, NTH, 0, s>>>(insts, st, items), 0))
+    (mode ? launch_k(K<RR, 1>, dim3(nitems), dim3(NTH), 0, s, insts, st, items)             \
+          : launch_k(K<RR, 0>, dim3(nitems), dim3(NTH), 0, s, insts, st, items))
     if (D == 2 && prec == 0) HELM_RES(k_residual2d, double);
     else if (D == 2) HELM_RES(k_residual2d, float);
     else if (prec == 0) HELM_RES(k_residual3d, double);
@@ -427,10 +449,24 @@ cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* s
     return cudaGetLastError();
 }
 
+cudaError_t setup_outer()
+{
+    cudaError_t e;
+    if ((e = max_carveout(k_residual2d<float, 0>)) != cudaSuccess) return e;
+    if ((e = max_carveout(k_residual2d<float, 1>)) != cudaSuccess) return e;
+    if ((e = max_carveout(k_residual2d<double, 0>)) != cudaSuccess) return e;
+    if ((e = max_carveout(k_residual2d<double, 1>)) != cudaSuccess) return e;
+    if ((e = max_carveout(k_residual3d<float, 0>)) != cudaSuccess) return e;
+    if ((e = max_carveout(k_residual3d<float, 1>)) != cudaSuccess) return e;
+    if ((e = max_carveout(k_residual3d<double, 0>)) != cudaSuccess) return e;
+    if ((e = max_carveout(k_residual3d<double, 1>)) != cudaSuccess) return e;
+    return max_carveout(k_check);
+}
+
 cudaError_t launch_check(const InstState* st, int ninst, int* ctrl, int use_cond,
                          unsigned long long cond_handle, cudaStream_t s)
 {
-    k_check<<<1, 256, 0, s>>>(st, ninst, ctrl, use_cond, cond_handle);
+    launch_k(k_check, dim3(1), dim3(256), 0, s, st, ninst, ctrl, use_cond, cond_handle);
     return cudaGetLastError();
 }
 
@@ -438,8 +474,8 @@ cudaError_t launch_set_ring(int D, const InstDesc* insts, int inst, int n, cudaS
 {
     const long S = n + 2;
     const long work = (D == 3) ? S * S * S : S * S;
-    if (D == 2) k_set_ring<2><<<blocks_for(work), 256, 0, s>>>(insts, inst);
-    else k_set_ring<3><<<blocks_for(work), 256, 0, s>>>(insts, inst);
+    if (D == 2) launch_k(k_set_ring<2>, dim3(blocks_for(work)), dim3(256), 0, s, insts, inst);
+    else launch_k(k_set_ring<3>, dim3(blocks_for(work)), dim3(256), 0, s, insts, inst);
     return cudaGetLastError();
 }
 
@@ -448,10 +484,10 @@ cudaError_t launch_pack(int D, int prec, const InstDesc* insts, int inst, int n,
 {
     const long work = (D == 3) ? (long)n * n * n : (long)n * n;
     const int nb = blocks_for(work);
-    if (D == 2 && prec == 0) k_pack<2, double><<<nb, 256, 0, s>>>(insts, inst, src, which);
-    else if (D == 2) k_pack<2, float><<<nb, 256, 0, s>>>(insts, inst, src, which);
-    else if (prec == 0) k_pack<3, double><<<nb, 256, 0, s>>>(insts, inst, src, which);
-    else k_pack<3, float><<<nb, 256, 0, s>>>(insts, inst, src, which);
+    if (D == 2 && prec == 0) launch_k(k_pack<2, double>, dim3(nb), dim3(256), 0, s, insts, inst, src, which);
+    else if (D == 2) launch_k(k_pack<2, float>, dim3(nb), dim3(256), 0, s, insts, inst, src, which);
+    else if (prec == 0) launch_k(k_pack<3, double>, dim3(nb), dim3(256), 0, s, insts, inst, src, which);
+    else launch_k(k_pack<3, float>, dim3(nb), dim3(256), 0, s, insts, inst, src, which);
     return cudaGetLastError();
 }
 
@@ -460,10 +496,10 @@ cudaError_t launch_unpack(int D, int prec, const InstDesc* insts, int inst, int 
 {
     const long work = (D == 3) ? (long)n * n * n : (long)n * n;
     const int nb = blocks_for(work);
-    if (D == 2 && prec == 0) k_unpack<2, double><<<nb, 256, 0, s>>>(insts, inst, dst);
-    else if (D == 2) k_unpack<2, float><<<nb, 256, 0, s>>>(insts, inst, dst);
-    else if (prec == 0) k_unpack<3, double><<<nb, 256, 0, s>>>(insts, inst, dst);
-    else k_unpack<3, float><<<nb, 256, 0, s>>>(insts, inst, dst);
+    if (D == 2 && prec == 0) launch_k(k_unpack<2, double>, dim3(nb), dim3(256), 0, s, insts, inst, dst);
+    else if (D == 2) launch_k(k_unpack<2, float>, dim3(nb), dim3(256), 0, s, insts, inst, dst);
+    else if (prec == 0) launch_k(k_unpack<3, double>, dim3(nb), dim3(256), 0, s, insts, inst, dst);
+    else launch_k(k_unpack<3, float>, dim3(nb), dim3(256), 0, s, insts, inst, dst);
     return cudaGetLastError();
 }
 

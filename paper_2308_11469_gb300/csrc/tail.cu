@@ -10,6 +10,7 @@
 // barrier.  Shared-memory layout: for each level, its iterate then its rhs, padded
 // (n + 2)^D arrays with zero rings.
 #include "launch.h"
+#include "pdl.cuh"
 
 namespace helm {
 namespace {
@@ -206,6 +207,8 @@ __global__ void __launch_bounds__(TNT)
 k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
        const MgItem* __restrict__ items, int nu1, int nu2, int load_e)
 {
+    pdl_wait();
+    pdl_trigger();
     typedef typename C2<R>::T c2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     c2* base = reinterpret_cast<c2*>(smem_raw);
@@ -259,7 +262,7 @@ cudaError_t tl(const InstDesc* insts, const InstState* st, const MgItem* items, 
                int nu1, int nu2, int load_e, cudaStream_t s)
 {
     const size_t sm = (size_t)tail_elems<D, N0>() * sizeof(typename C2<R>::T);
-    k_tail<D, R, N0><<<nitems, TNT, sm, s>>>(insts, st, items, nu1, nu2, load_e);
+    launch_k(k_tail<D, R, N0>, dim3(nitems), dim3(TNT), sm, s, insts, st, items, nu1, nu2, load_e);
     return cudaGetLastError();
 }
 
@@ -267,7 +270,9 @@ template <int D, typename R, int N0>
 cudaError_t ta()
 {
     const size_t sm = (size_t)tail_elems<D, N0>() * sizeof(typename C2<R>::T);
-    return cudaFuncSetAttribute(k_tail<D, R, N0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const cudaError_t e = cudaFuncSetAttribute(k_tail<D, R, N0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    return max_carveout(k_tail<D, R, N0>);
 }
 
 template <int D, typename R>

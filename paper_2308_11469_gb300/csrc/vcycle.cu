@@ -12,6 +12,7 @@
 //   k_prolong   e_fine += multilinear interpolation of e_coarse.
 // The coarse levels (n <= 63 in 2D, n <= 15 in 3D) run inside one CTA (tail.cu).
 #include "launch.h"
+#include "pdl.cuh"
 
 namespace helm {
 namespace {
@@ -31,6 +32,8 @@ __global__ void __launch_bounds__(256)
 k_rbgs(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
        const MgItem* __restrict__ items, int color, int mode)
 {
+    pdl_wait();
+    pdl_trigger();
     typedef typename C2<R>::T c2;
     const MgItem item = items[blockIdx.y];
     if (st[item.inst].status != HELM_ST_ACTIVE) return;
@@ -89,6 +92,8 @@ __global__ void __launch_bounds__(256)
 k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
            const MgItem* __restrict__ items)
 {
+    pdl_wait();
+    pdl_trigger();
     typedef typename C2<R>::T c2;
     const MgItem item = items[blockIdx.y];
     if (st[item.inst].status != HELM_ST_ACTIVE) return;
@@ -149,6 +154,8 @@ __global__ void __launch_bounds__(256)
 k_prolong(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
           const MgItem* __restrict__ items)
 {
+    pdl_wait();
+    pdl_trigger();
     typedef typename C2<R>::T c2;
     const MgItem item = items[blockIdx.y];
     if (st[item.inst].status != HELM_ST_ACTIVE) return;
@@ -197,6 +204,8 @@ __global__ void __launch_bounds__(256)
 k_zero(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
        const MgItem* __restrict__ items)
 {
+    pdl_wait();
+    pdl_trigger();
     typedef typename C2<R>::T c2;
     const MgItem item = items[blockIdx.y];
     if (st[item.inst].status != HELM_ST_ACTIVE) return;
@@ -217,15 +226,31 @@ inline dim3 mg_grid(int work, int nitems) {
 
 }  // namespace
 
+template <int D, typename R>
+static cudaError_t carve()
+{
+    cudaError_t e;
+    if ((e = max_carveout(k_rbgs<D, R>)) != cudaSuccess) return e;
+    if ((e = max_carveout(k_restrict<D, R>)) != cudaSuccess) return e;
+    if ((e = max_carveout(k_prolong<D, R>)) != cudaSuccess) return e;
+    return max_carveout(k_zero<D, R>);
+}
+
+cudaError_t setup_generic(int D, int prec)
+{
+    if (D == 2) return prec == 0 ? carve<2, double>() : carve<2, float>();
+    return prec == 0 ? carve<3, double>() : carve<3, float>();
+}
+
 cudaError_t launch_rbgs(int D, int prec, const InstDesc* insts, const InstState* st,
                         const MgItem* items, int nitems, int work, int color, int mode,
                         cudaStream_t s)
 {
     dim3 g = mg_grid(work, nitems);
-    if (D == 2 && prec == 0) k_rbgs<2, double><<<g, 256, 0, s>>>(insts, st, items, color, mode);
-    else if (D == 2) k_rbgs<2, float><<<g, 256, 0, s>>>(insts, st, items, color, mode);
-    else if (prec == 0) k_rbgs<3, double><<<g, 256, 0, s>>>(insts, st, items, color, mode);
-    else k_rbgs<3, float><<<g, 256, 0, s>>>(insts, st, items, color, mode);
+    if (D == 2 && prec == 0) launch_k(k_rbgs<2, double>, dim3(g), dim3(256), 0, s, insts, st, items, color, mode);
+    else if (D == 2) launch_k(k_rbgs<2, float>, dim3(g), dim3(256), 0, s, insts, st, items, color, mode);
+    else if (prec == 0) launch_k(k_rbgs<3, double>, dim3(g), dim3(256), 0, s, insts, st, items, color, mode);
+    else launch_k(k_rbgs<3, float>, dim3(g), dim3(256), 0, s, insts, st, items, color, mode);
     return cudaGetLastError();
 }
 
@@ -233,10 +258,10 @@ cudaError_t launch_restrict(int D, int prec, const InstDesc* insts, const InstSt
                             const MgItem* items, int nitems, int work, cudaStream_t s)
 {
     dim3 g = mg_grid(work, nitems);
-    if (D == 2 && prec == 0) k_restrict<2, double><<<g, 256, 0, s>>>(insts, st, items);
-    else if (D == 2) k_restrict<2, float><<<g, 256, 0, s>>>(insts, st, items);
-    else if (prec == 0) k_restrict<3, double><<<g, 256, 0, s>>>(insts, st, items);
-    else k_restrict<3, float><<<g, 256, 0, s>>>(insts, st, items);
+    if (D == 2 && prec == 0) launch_k(k_restrict<2, double>, dim3(g), dim3(256), 0, s, insts, st, items);
+    else if (D == 2) launch_k(k_restrict<2, float>, dim3(g), dim3(256), 0, s, insts, st, items);
+    else if (prec == 0) launch_k(k_restrict<3, double>, dim3(g), dim3(256), 0, s, insts, st, items);
+    else launch_k(k_restrict<3, float>, dim3(g), dim3(256), 0, s, insts, st, items);
     return cudaGetLastError();
 }
 
@@ -244,10 +269,10 @@ cudaError_t launch_prolong(int D, int prec, const InstDesc* insts, const InstSta
                            const MgItem* items, int nitems, int work, cudaStream_t s)
 {
     dim3 g = mg_grid(work, nitems);
-    if (D == 2 && prec == 0) k_prolong<2, double><<<g, 256, 0, s>>>(insts, st, items);
-    else if (D == 2) k_prolong<2, float><<<g, 256, 0, s>>>(insts, st, items);
-    else if (prec == 0) k_prolong<3, double><<<g, 256, 0, s>>>(insts, st, items);
-    else k_prolong<3, float><<<g, 256, 0, s>>>(insts, st, items);
+    if (D == 2 && prec == 0) launch_k(k_prolong<2, double>, dim3(g), dim3(256), 0, s, insts, st, items);
+    else if (D == 2) launch_k(k_prolong<2, float>, dim3(g), dim3(256), 0, s, insts, st, items);
+    else if (prec == 0) launch_k(k_prolong<3, double>, dim3(g), dim3(256), 0, s, insts, st, items);
+    else launch_k(k_prolong<3, float>, dim3(g), dim3(256), 0, s, insts, st, items);
     return cudaGetLastError();
 }
 
@@ -255,10 +280,10 @@ cudaError_t launch_zero(int D, int prec, const InstDesc* insts, const InstState*
                         const MgItem* items, int nitems, int work, cudaStream_t s)
 {
     dim3 g = mg_grid(work, nitems);
-    if (D == 2 && prec == 0) k_zero<2, double><<<g, 256, 0, s>>>(insts, st, items);
-    else if (D == 2) k_zero<2, float><<<g, 256, 0, s>>>(insts, st, items);
-    else if (prec == 0) k_zero<3, double><<<g, 256, 0, s>>>(insts, st, items);
-    else k_zero<3, float><<<g, 256, 0, s>>>(insts, st, items);
+    if (D == 2 && prec == 0) launch_k(k_zero<2, double>, dim3(g), dim3(256), 0, s, insts, st, items);
+    else if (D == 2) launch_k(k_zero<2, float>, dim3(g), dim3(256), 0, s, insts, st, items);
+    else if (prec == 0) launch_k(k_zero<3, double>, dim3(g), dim3(256), 0, s, insts, st, items);
+    else launch_k(k_zero<3, float>, dim3(g), dim3(256), 0, s, insts, st, items);
     return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@
 // The node colours, the update formula and the transfer weights are those of the
 // generic kernels (vcycle.cu), so both paths compute the same V-cycle.
 #include "launch.h"
+#include "pdl.cuh"
 
 namespace helm {
 namespace {
@@ -67,6 +68,8 @@ __global__ void __launch_bounds__(NT)
 k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
          const MgItem* __restrict__ items, int zero_mode)
 {
+    pdl_wait();
+    pdl_trigger();
     typedef typename C2<R>::T c2;
     constexpr int H = 2 * NU + 2;
     constexpr int W = TX + 2 * H, HH = TY + 2 * H;
@@ -89,6 +92,8 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const c2* __restrict__ gr = (const c2*)L.rhs;
     const int P = L.pitch;
     const int lane = threadIdx.x & 31;
+    // stage e (or zeros) and rhs with asynchronous copies: every load of the tile is in
+    // flight at once; nodes outside the interior are zero-filled
     for (int ly = threadIdx.x >> 5; ly < HH; ly += NW) {
         const int gy = gy0 + ly;
         const bool yin = gy >= 1 && gy <= n;
@@ -96,11 +101,13 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
         for (int lx = lane; lx < W; lx += 32) {
             const int gx = gx0 + lx;
             const bool in = yin && gx >= 1 && gx <= n;
-            const size_t g = (size_t)gy * P + gx;
-            E[ly * W + lx] = (!zero && in) ? ge[g] : cz<c2>();
-            Rs[ly * W + lx] = in ? gr[g] : cz<c2>();
+            const size_t g = in ? (size_t)gy * P + gx : 0;
+            if (zero) E[ly * W + lx] = cz<c2>();
+            else cp_async_elem<sizeof(c2)>(E + ly * W + lx, ge + g, in);
+            cp_async_elem<sizeof(c2)>(Rs + ly * W + lx, gr + g, in);
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     const R h2 = (R)(L.h * L.h);
     int ring = 2 * NU + 1;
@@ -178,6 +185,8 @@ __global__ void __launch_bounds__(NT)
 k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
        const MgItem* __restrict__ items)
 {
+    pdl_wait();
+    pdl_trigger();
     typedef typename C2<R>::T c2;
     constexpr int H = 2 * NU;
     constexpr int W = TX + 2 * H, HH = TY + 2 * H;
@@ -203,40 +212,49 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const c2* __restrict__ gce = (const c2*)C.e;
     const int PC = C.pitch;
     const int lane = threadIdx.x & 31;
+    const c2* __restrict__ ge2 = (const c2*)L.e2;
+    const c2* __restrict__ gr = (const c2*)L.rhs;
+    const int P = L.pitch;
+    // stage the coarse window, e2 and rhs with asynchronous copies (zero-filled outside)
     for (int cy = threadIdx.x >> 5; cy < CH; cy += NW) {
         const int Y = cy0 + cy;
 #pragma unroll
         for (int cx = lane; cx < CW; cx += 32) {
             const int X = cx0 + cx;
-            Cs[cy * CW + cx] = (X <= nc1 && Y <= nc1) ? gce[(size_t)Y * PC + X] : cz<c2>();
+            const bool in = X <= nc1 && Y <= nc1;
+            cp_async_elem<sizeof(c2)>(Cs + cy * CW + cx, gce + (in ? (size_t)Y * PC + X : 0), in);
         }
     }
-    __syncthreads();
-    const c2* __restrict__ ge2 = (const c2*)L.e2;
-    const c2* __restrict__ gr = (const c2*)L.rhs;
-    const int P = L.pitch;
     for (int ly = threadIdx.x >> 5; ly < HH; ly += NW) {
         const int gy = gy0 + ly;
         const bool yin = gy >= 1 && gy <= n;
-        const int Y0 = (gy >> 1) - cy0, Y1 = ((gy + 1) >> 1) - cy0;
 #pragma unroll
         for (int lx = lane; lx < W; lx += 32) {
             const int gx = gx0 + lx;
             const bool in = yin && gx >= 1 && gx <= n;
-            c2 v = cz<c2>();
-            c2 r = cz<c2>();
-            if (in) {
-                const size_t g = (size_t)gy * P + gx;
-                v = ge2[g];
-                r = gr[g];
-                const int X0 = (gx >> 1) - cx0, X1 = ((gx + 1) >> 1) - cx0;
-                const c2 a = Cs[Y0 * CW + X0], b = Cs[Y0 * CW + X1];
-                const c2 c = Cs[Y1 * CW + X0], d = Cs[Y1 * CW + X1];
-                v.x += (R)0.25 * (((a.x + b.x) + c.x) + d.x);
-                v.y += (R)0.25 * (((a.y + b.y) + c.y) + d.y);
-            }
+            const size_t g = in ? (size_t)gy * P + gx : 0;
+            cp_async_elem<sizeof(c2)>(E + ly * W + lx, ge2 + g, in);
+            cp_async_elem<sizeof(c2)>(Rs + ly * W + lx, gr + g, in);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // correction: e2 + multilinear interpolation of the coarse iterate (interior nodes)
+    for (int ly = threadIdx.x >> 5; ly < HH; ly += NW) {
+        const int gy = gy0 + ly;
+        if (gy < 1 || gy > n) continue;
+        const int Y0 = (gy >> 1) - cy0, Y1 = ((gy + 1) >> 1) - cy0;
+#pragma unroll
+        for (int lx = lane; lx < W; lx += 32) {
+            const int gx = gx0 + lx;
+            if (gx < 1 || gx > n) continue;
+            const int X0 = (gx >> 1) - cx0, X1 = ((gx + 1) >> 1) - cx0;
+            const c2 a = Cs[Y0 * CW + X0], b = Cs[Y0 * CW + X1];
+            const c2 c = Cs[Y1 * CW + X0], d = Cs[Y1 * CW + X1];
+            c2 v = E[ly * W + lx];
+            v.x += (R)0.25 * (((a.x + b.x) + c.x) + d.x);
+            v.y += (R)0.25 * (((a.y + b.y) + c.y) + d.y);
             E[ly * W + lx] = v;
-            Rs[ly * W + lx] = r;
         }
     }
     __syncthreads();
@@ -275,6 +293,8 @@ cudaError_t set_attrs()
     cudaError_t e = cudaFuncSetAttribute(k_down2d<R, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)down_bytes<NU>(sizeof(R) * 2));
     if (e != cudaSuccess) return e;
+    if ((e = max_carveout(k_down2d<R, NU>)) != cudaSuccess) return e;
+    if ((e = max_carveout(k_up2d<R, NU>)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_up2d<R, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)up_bytes<NU>(sizeof(R) * 2));
 }
@@ -296,11 +316,11 @@ cudaError_t down(int nu, dim3 g, const InstDesc* insts, const InstState* st, con
 {
     const size_t eb = sizeof(R) * 2;
     switch (nu) {
-    case 0: k_down2d<R, 0><<<g, NT, down_bytes<0>(eb), s>>>(insts, st, items, zero_mode); break;
-    case 1: k_down2d<R, 1><<<g, NT, down_bytes<1>(eb), s>>>(insts, st, items, zero_mode); break;
-    case 2: k_down2d<R, 2><<<g, NT, down_bytes<2>(eb), s>>>(insts, st, items, zero_mode); break;
-    case 3: k_down2d<R, 3><<<g, NT, down_bytes<3>(eb), s>>>(insts, st, items, zero_mode); break;
-    case 4: k_down2d<R, 4><<<g, NT, down_bytes<4>(eb), s>>>(insts, st, items, zero_mode); break;
+    case 0: launch_k(k_down2d<R, 0>, g, dim3(NT), down_bytes<0>(eb), s, insts, st, items, zero_mode); break;
+    case 1: launch_k(k_down2d<R, 1>, g, dim3(NT), down_bytes<1>(eb), s, insts, st, items, zero_mode); break;
+    case 2: launch_k(k_down2d<R, 2>, g, dim3(NT), down_bytes<2>(eb), s, insts, st, items, zero_mode); break;
+    case 3: launch_k(k_down2d<R, 3>, g, dim3(NT), down_bytes<3>(eb), s, insts, st, items, zero_mode); break;
+    case 4: launch_k(k_down2d<R, 4>, g, dim3(NT), down_bytes<4>(eb), s, insts, st, items, zero_mode); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -312,11 +332,11 @@ cudaError_t up(int nu, dim3 g, const InstDesc* insts, const InstState* st, const
 {
     const size_t eb = sizeof(R) * 2;
     switch (nu) {
-    case 0: k_up2d<R, 0><<<g, NT, up_bytes<0>(eb), s>>>(insts, st, items); break;
-    case 1: k_up2d<R, 1><<<g, NT, up_bytes<1>(eb), s>>>(insts, st, items); break;
-    case 2: k_up2d<R, 2><<<g, NT, up_bytes<2>(eb), s>>>(insts, st, items); break;
-    case 3: k_up2d<R, 3><<<g, NT, up_bytes<3>(eb), s>>>(insts, st, items); break;
-    case 4: k_up2d<R, 4><<<g, NT, up_bytes<4>(eb), s>>>(insts, st, items); break;
+    case 0: launch_k(k_up2d<R, 0>, g, dim3(NT), up_bytes<0>(eb), s, insts, st, items); break;
+    case 1: launch_k(k_up2d<R, 1>, g, dim3(NT), up_bytes<1>(eb), s, insts, st, items); break;
+    case 2: launch_k(k_up2d<R, 2>, g, dim3(NT), up_bytes<2>(eb), s, insts, st, items); break;
+    case 3: launch_k(k_up2d<R, 3>, g, dim3(NT), up_bytes<3>(eb), s, insts, st, items); break;
+    case 4: launch_k(k_up2d<R, 4>, g, dim3(NT), up_bytes<4>(eb), s, insts, st, items); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -173,6 +173,11 @@ def test_status_rule():
     assert out[first] == it.DIVERGED and first == 20
     r = it.StatusRule(1e-8, 3)
     assert [r(N, 0.5 ** N) for N in range(4)] == [None, None, None, it.MAXITER]
+    # stagnation at a floor (non-decreasing, but within 2x of the minimum) is not divergence
+    r = it.StatusRule(1e-12, 100)
+    vals = [1.0, 1e-3, 1e-6, 1e-9] + [1.1e-9 + 1e-12 * N for N in range(4, 101)]
+    out = [r(N, v) for N, v in enumerate(vals)]
+    assert [s for s in out if s is not None] == [it.MAXITER]
 
 
 def test_zero_data_is_converged_immediately():
