@@ -118,6 +118,17 @@ HELM_API helm_status helm_plan_info(const helm_plan* plan, double* lambda_min, d
  * cycles in [1, 16]. */
 HELM_API helm_status helm_plan_set_cycle(helm_plan* plan, int nu1, int nu2, int cycles);
 
+/* Autotuner: solves the given problem (f, g, starting iterate u, tol, max_outer as in
+ * helm_solve) with each candidate inner schedule -- V(1,0), V(0,1), V(1,1), V(2,1),
+ * V(1,2), V(2,2), V(3,3) with one cycle per outer step, V(1,1) with two -- times each
+ * converged solve on the plan's stream (best of two after a warm-up run), keeps the
+ * fastest in the plan and reports it (outputs may be NULL).  u is restored to the
+ * starting iterate.  HELM_DIVERGED if no candidate converged (schedule unchanged).
+ * Allocates one temporary copy of u. */
+HELM_API helm_status helm_plan_autotune(helm_plan* plan, const void* f, const void* g, void* u,
+                                        double tol, int max_outer, int* nu1, int* nu2,
+                                        int* cycles, double* best_ms);
+
 /*
  * Solve (Delta_h + k^2) u = f, u = g on the wall, by the outer Poisson iteration.
  *   f         interior complex128, n^D (device).
@@ -181,7 +192,8 @@ HELM_API helm_status poisson_vcycle_noalloc(int ndim, int n, double h, int prec,
  * reserves workspace; HELM_ENOMEM when the cap would be exceeded (retry after others
  * finish).  f, g, u follow helm_solve and must stay valid until the solve is polled done.
  * helm_batch_step runs up to `max_steps` outer steps (0 = until every active solve has
- * finished).  helm_batch_poll reports a solve; once it returns done = 1 the result is in
+ * finished, as one CUDA-graph launch; a bounded chunk right after admissions or
+ * retirements runs as direct launches, so admitting between chunks costs no re-capture).  helm_batch_poll reports a solve; once it returns done = 1 the result is in
  * u (synchronised), the histories are copied (res_hist may be NULL), and the instance's
  * workspace is released.
  */
@@ -190,7 +202,15 @@ HELM_API helm_status helm_batch_destroy(helm_batch* batch);
 HELM_API helm_status helm_batch_submit(helm_batch* batch, const helm_plan* plan, const void* f,
                               const void* g, void* u, double tol, int max_outer,
                               uint64_t* ticket);
+/* As helm_batch_submit, with the geometry, k and precision given directly (no plan, so
+ * no plan workspace is allocated): for a serving loop admitting many requests. */
+HELM_API helm_status helm_batch_submit_geom(helm_batch* batch, int ndim, int n, double h, double k,
+                                            int prec, const void* f, const void* g, void* u,
+                                            double tol, int max_outer, uint64_t* ticket);
 HELM_API helm_status helm_batch_step(helm_batch* batch, int max_steps);
+/* Inner schedule (as helm_plan_set_cycle) used by every solve of the batch from the next
+ * step on (the batch's solves share their launches, hence one schedule). */
+HELM_API helm_status helm_batch_set_cycle(helm_batch* batch, int nu1, int nu2, int cycles);
 HELM_API helm_status helm_batch_poll(helm_batch* batch, uint64_t ticket, int* done, int* status,
                             int* iters, double* res_hist);
 /*

@@ -55,6 +55,11 @@ _SIGS = {
     "helm_batch_submit": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_double, C.c_int,
                                     C.POINTER(C.c_uint64)]),
     "helm_batch_step": (C.c_int, [_vp, C.c_int]),
+    "helm_batch_submit_geom": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, _vp,
+                                         _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_uint64)]),
+    "helm_batch_set_cycle": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
+    "helm_plan_autotune": (C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int),
+                                     C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "helm_batch_poll": (C.c_int, [_vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "helm_batch_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_size_t)]),
@@ -194,6 +199,20 @@ def helm_plan_set_cycle(plan: _Plan, nu1: int, nu2: int, cycles: int = 1) -> Non
     _check(load().helm_plan_set_cycle(plan.handle, nu1, nu2, cycles), "helm_plan_set_cycle")
 
 
+def helm_plan_autotune(plan: _Plan, f, g, u, tol: float, max_outer: int):
+    """Returns (nu1, nu2, cycles, best ms); the plan keeps the fastest schedule."""
+    import torch
+    D, n = plan.D, plan.n
+    pf = _ptr(f, torch.complex128, (n,) * D, "f")
+    pg = _ptr(g, torch.complex128, (n + 2,) * D, "g")
+    pu = _ptr(u, torch.complex128, (n + 2,) * D, "u")
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    ms = C.c_double()
+    _check(load().helm_plan_autotune(plan.handle, pf, pg, pu, float(tol), int(max_outer), C.byref(a),
+                                     C.byref(b), C.byref(c), C.byref(ms)), "helm_plan_autotune")
+    return a.value, b.value, c.value, ms.value
+
+
 def helm_solve_ex(plan: _Plan, f, g, u, tol: float, max_outer: int):
     """Returns (status, iters, relres history, increment sup-norm history)."""
     import torch
@@ -280,8 +299,28 @@ def helm_batch_submit(batch: _Batch, plan: _Plan, f, g, u, tol: float, max_outer
     return t.value
 
 
+def helm_batch_submit_geom(batch: _Batch, ndim: int, n: int, h: float, k: float, prec: int, f, g, u,
+                           tol: float, max_outer: int):
+    """As helm_batch_submit without a plan.  Returns a ticket, or None over the memory cap."""
+    import torch
+    pf = _ptr(f, torch.complex128, (n,) * ndim, "f")
+    pg = _ptr(g, torch.complex128, (n + 2,) * ndim, "g")
+    pu = _ptr(u, torch.complex128, (n + 2,) * ndim, "u")
+    t = C.c_uint64()
+    st = load().helm_batch_submit_geom(batch.handle, int(ndim), int(n), float(h), float(k), int(prec),
+                                       pf, pg, pu, float(tol), int(max_outer), C.byref(t))
+    if st == HELM_ENOMEM:
+        return None
+    _check(st, "helm_batch_submit_geom")
+    return t.value
+
+
 def helm_batch_step(batch: _Batch, max_steps: int = 0) -> None:
     _check(load().helm_batch_step(batch.handle, int(max_steps)), "helm_batch_step")
+
+
+def helm_batch_set_cycle(batch: _Batch, nu1: int, nu2: int, cycles: int = 1) -> None:
+    _check(load().helm_batch_set_cycle(batch.handle, nu1, nu2, cycles), "helm_batch_set_cycle")
 
 
 def helm_batch_poll(batch: _Batch, ticket: int, max_outer: int):

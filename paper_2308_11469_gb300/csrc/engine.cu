@@ -141,7 +141,8 @@ struct Engine {
     size_t res_cap = 0;
     int nres = 0;
     std::vector<LaunchRec> step;               // one outer step
-    std::vector<long> signature;               // geometry of the slots the graph was built for
+    std::vector<long> plan_sig;                // slot geometry the launch plan was built for
+    std::vector<long> graph_sig;               // slot geometry the graph was captured for
     std::vector<MgItem> h_items;               // host copy of the multigrid work items
     std::vector<LaunchRec> vcyc_plain;         // one V-cycle from the current iterate
     int max_tail = 1;
@@ -471,23 +472,33 @@ struct Engine {
         return sig;
     }
 
-    // Make the launch plan and the graph match the slots.  The graph only depends on the
-    // geometry of the occupied slots (pointers live in the device descriptors), so a
-    // re-admission of same-sized solves into the same slots reuses it.
-    helm_status prepare()
+    // Make the launch plan (work items, launch sequence) match the slots.  The plan only
+    // depends on the geometry of the occupied slots (pointers live in the device
+    // descriptors), so re-admitting same-sized solves into the same slots keeps it.
+    helm_status prepare_plan()
     {
         if (!dirty) return HELM_OK;
         std::vector<long> sig = current_signature();
-        if (exec && sig == signature) {
-            dirty = false;
-            return HELM_OK;
+        if (sig != plan_sig) {
+            helm_status st = rebuild_plan();
+            if (st != HELM_OK) return st;
+            plan_sig = sig;
         }
-        helm_status st = rebuild_plan();
+        dirty = false;
+        return HELM_OK;
+    }
+
+    bool graph_current() const { return exec != nullptr && graph_sig == plan_sig && !plan_sig.empty(); }
+
+    // Plan and the CUDA graph of one outer step (re-captured when the plan changed).
+    helm_status prepare()
+    {
+        helm_status st = prepare_plan();
         if (st != HELM_OK) return st;
+        if (graph_current()) return HELM_OK;
         st = build_graph();
         if (st != HELM_OK) return st;
-        signature = sig;
-        dirty = false;
+        graph_sig = plan_sig;
         return HELM_OK;
     }
 
@@ -632,6 +643,7 @@ struct helm_plan {
 
 struct helm_batch {
     size_t cap_bytes = 0, used = 0;
+    int nu1 = 2, nu2 = 2, cycles = 1;           // inner schedule of every engine
     cudaStream_t stream = nullptr;
     std::map<int, std::unique_ptr<Engine>> engines;   // key = 2 * D + prec
     std::map<int, cudaStream_t> eng_streams;
@@ -801,6 +813,68 @@ helm_status helm_solve(helm_plan* p, const void* f, const void* g, void* u, doub
     return helm_solve_ex(p, f, g, u, tol, max_outer, iters, res_hist, nullptr);
 }
 
+helm_status helm_plan_autotune(helm_plan* p, const void* f, const void* g, void* u, double tol,
+                               int max_outer, int* nu1_out, int* nu2_out, int* cycles_out,
+                               double* best_ms)
+{
+    if (!p) return HELM_EINVAL;
+    if (check_ptr(f) || check_ptr(g) || check_ptr(u)) return HELM_EINVAL;
+    static const int cand[][3] = {{1, 0, 1}, {0, 1, 1}, {1, 1, 1}, {2, 1, 1}, {1, 2, 1},
+                                  {2, 2, 1}, {3, 3, 1}, {1, 1, 2}};
+    const size_t ub = p->padded() * 16;
+    void* saved = nullptr;
+    HELM_CK(cudaMallocAsync(&saved, ub, p->stream));
+    HELM_CK(cudaMemcpyAsync(saved, u, ub, cudaMemcpyDeviceToDevice, p->stream));
+    cudaEvent_t e0, e1;
+    HELM_CK(cudaEventCreate(&e0));
+    HELM_CK(cudaEventCreate(&e1));
+    const int s1 = p->eng.nu1, s2 = p->eng.nu2, sc = p->eng.cycles;
+    int bi = -1;
+    float bms = 0.f;
+    helm_status st = HELM_OK;
+    for (int c = 0; c < (int)(sizeof cand / sizeof cand[0]); ++c) {
+        st = helm_plan_set_cycle(p, cand[c][0], cand[c][1], cand[c][2]);
+        if (st != HELM_OK) break;
+        float best = 0.f;
+        helm_status out = HELM_OK;
+        for (int rep = 0; rep < 3; ++rep) {               // first run builds the graph
+            HELM_CK(cudaMemcpyAsync(u, saved, ub, cudaMemcpyDeviceToDevice, p->stream));
+            HELM_CK(cudaEventRecord(e0, p->stream));
+            out = helm_solve(p, f, g, u, tol, max_outer, nullptr, nullptr);
+            HELM_CK(cudaEventRecord(e1, p->stream));
+            HELM_CK(cudaEventSynchronize(e1));
+            if (out != HELM_CONVERGED) break;
+            float ms = 0.f;
+            HELM_CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0 && (best == 0.f || ms < best)) best = ms;
+        }
+        if (out < 0) { st = out; break; }
+        if (out == HELM_CONVERGED && (bi < 0 || best < bms)) {
+            bi = c;
+            bms = best;
+        }
+    }
+    HELM_CK(cudaMemcpyAsync(u, saved, ub, cudaMemcpyDeviceToDevice, p->stream));
+    HELM_CK(cudaFreeAsync(saved, p->stream));
+    HELM_CK(cudaStreamSynchronize(p->stream));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HELM_OK) {
+        helm_plan_set_cycle(p, s1, s2, sc);
+        return st;
+    }
+    if (bi < 0) {                                          // nothing converged: keep the old schedule
+        helm_plan_set_cycle(p, s1, s2, sc);
+        return HELM_DIVERGED;
+    }
+    helm_plan_set_cycle(p, cand[bi][0], cand[bi][1], cand[bi][2]);
+    if (nu1_out) *nu1_out = cand[bi][0];
+    if (nu2_out) *nu2_out = cand[bi][1];
+    if (cycles_out) *cycles_out = cand[bi][2];
+    if (best_ms) *best_ms = bms;
+    return HELM_OK;
+}
+
 helm_status poisson_vcycle(helm_plan* p, const void* rhs, void* e, int nu1, int nu2)
 {
     if (!p) return HELM_EINVAL;
@@ -818,7 +892,8 @@ helm_status poisson_vcycle(helm_plan* p, const void* rhs, void* e, int nu1, int 
     E.nu2 = s2;
     E.cycles = sc;
     E.dirty = true;
-    E.signature.clear();
+    E.plan_sig.clear();
+    E.graph_sig.clear();
     if (st != HELM_OK) return st;
     InstState act;
     memset(&act, 0, sizeof act);
@@ -884,25 +959,35 @@ helm_status helm_batch_destroy(helm_batch* b)
     return HELM_OK;
 }
 
-helm_status helm_batch_submit(helm_batch* b, const helm_plan* p, const void* f, const void* g,
-                              void* u, double tol, int max_outer, uint64_t* ticket)
+static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, int prec,
+                               const void* f, const void* g, void* u, double tol, int max_outer,
+                               uint64_t* ticket)
 {
-    if (!b || !p || !ticket) return HELM_EINVAL;
+    if (!b || !ticket) return HELM_EINVAL;
+    if (D != 2 && D != 3) return HELM_EINVAL;
+    if (!is_pow2m1(n) || (D == 2 && n > 32767) || (D == 3 && n > 2047)) return HELM_EINVAL;
+    if (!(h > 0.0) || !std::isfinite(h) || !(k >= 0.0) || !std::isfinite(k)) return HELM_EINVAL;
+    if (prec != HELM_PREC_FP64 && prec != HELM_PREC_MIXED) return HELM_EINVAL;
     if (max_outer < 0 || !(tol >= 0.0)) return HELM_EINVAL;
     if (check_ptr(f) || check_ptr(g) || check_ptr(u)) return HELM_EINVAL;
-    const size_t fb = p->points() * 16, ub = p->padded() * 16;
+    const size_t S = (size_t)n + 2;
+    const size_t fb = (D == 3 ? (size_t)n * n * n : (size_t)n * n) * 16;
+    const size_t ub = (D == 3 ? S * S * S : S * S) * 16;
     if (overlap(f, fb, u, ub) || overlap(g, ub, u, ub)) return HELM_EINVAL;
     InstDesc probe{};
-    const size_t need = layout(probe, p->D, p->n, p->h, p->k, p->prec, nullptr) +
+    const size_t need = layout(probe, D, n, h, k, prec, nullptr) +
                         (2 * (size_t)max_outer + 1) * sizeof(double);
     if (b->cap_bytes && b->used + need > b->cap_bytes) return HELM_ENOMEM;
-    const int key = 2 * p->D + p->prec;
+    const int key = 2 * D + prec;
     Engine* E = nullptr;
     auto it = b->engines.find(key);
     if (it == b->engines.end()) {
         std::unique_ptr<Engine> ne(new Engine());
-        helm_status st = ne->init(p->D, p->prec);
+        helm_status st = ne->init(D, prec);
         if (st != HELM_OK) return st;
+        ne->nu1 = b->nu1;
+        ne->nu2 = b->nu2;
+        ne->cycles = b->cycles;
         cudaStream_t es;
         HELM_CK(cudaStreamCreateWithFlags(&es, cudaStreamNonBlocking));
         cudaEvent_t ev;
@@ -923,7 +1008,7 @@ helm_status helm_batch_submit(helm_batch* b, const helm_plan* p, const void* f, 
         if (st != HELM_OK) return st;
     }
     Instance* in = new Instance();
-    helm_status st = alloc_instance(*in, p->D, p->n, p->h, p->k, p->prec, max_outer, b->stream, true);
+    helm_status st = alloc_instance(*in, D, n, h, k, prec, max_outer, b->stream, true);
     if (st != HELM_OK) { free_instance(*in, b->stream); delete in; return st; }
     in->d.u[0] = (double2*)u;
     in->d.f = (const double2*)f;
@@ -945,6 +1030,20 @@ helm_status helm_batch_submit(helm_batch* b, const helm_plan* p, const void* f, 
     b->used += need;
     *ticket = t;
     return HELM_OK;
+}
+
+helm_status helm_batch_submit(helm_batch* b, const helm_plan* p, const void* f, const void* g,
+                              void* u, double tol, int max_outer, uint64_t* ticket)
+{
+    if (!p) return HELM_EINVAL;
+    return submit_impl(b, p->D, p->n, p->h, p->k, p->prec, f, g, u, tol, max_outer, ticket);
+}
+
+helm_status helm_batch_submit_geom(helm_batch* b, int ndim, int n, double h, double k, int prec,
+                                   const void* f, const void* g, void* u, double tol,
+                                   int max_outer, uint64_t* ticket)
+{
+    return submit_impl(b, ndim, n, h, k, prec, f, g, u, tol, max_outer, ticket);
 }
 
 static helm_status retire_finished(helm_batch* b)
@@ -988,6 +1087,24 @@ static helm_status retire_finished(helm_batch* b)
     return HELM_OK;
 }
 
+helm_status helm_batch_set_cycle(helm_batch* b, int nu1, int nu2, int cycles)
+{
+    if (!b) return HELM_EINVAL;
+    if (nu1 < 0 || nu1 > 8 || nu2 < 0 || nu2 > 8 || nu1 + nu2 < 1 || cycles < 1 || cycles > 16)
+        return HELM_EINVAL;
+    b->nu1 = nu1;
+    b->nu2 = nu2;
+    b->cycles = cycles;
+    for (auto& kv : b->engines) {
+        kv.second->nu1 = nu1;
+        kv.second->nu2 = nu2;
+        kv.second->cycles = cycles;
+        kv.second->dirty = true;
+        kv.second->plan_sig.clear();
+    }
+    return HELM_OK;
+}
+
 helm_status helm_batch_step(helm_batch* b, int max_steps)
 {
     if (!b || max_steps < 0) return HELM_EINVAL;
@@ -999,13 +1116,28 @@ helm_status helm_batch_step(helm_batch* b, int max_steps)
         if (E->active_count() == 0) continue;
         cudaStream_t es = b->eng_streams[kv.first];
         HELM_CK(cudaStreamWaitEvent(es, b->fork, 0));
-        helm_status st = E->prepare();
+        helm_status st = E->prepare_plan();
         if (st != HELM_OK) return st;
+        // A bounded chunk after a membership change runs as direct launches (finished
+        // instances' kernels exit at once); the graph is (re)captured only for runs to
+        // completion, so a serving loop that admits between chunks never waits on a capture.
+        const bool direct = max_steps > 0 && max_steps <= 64 && !E->graph_current();
+        if (!direct) {
+            st = E->prepare();
+            if (st != HELM_OK) return st;
+        }
         E->h_ctrl[0] = 0;
         E->h_ctrl[1] = max_steps > 0 ? max_steps : INT_MAX;
         E->h_ctrl[2] = 1;
         HELM_CK(cudaMemcpyAsync(E->d_ctrl, E->h_ctrl, 3 * sizeof(int), cudaMemcpyHostToDevice, es));
-        HELM_CK(cudaGraphLaunch(E->exec, es));
+        if (direct) {
+            for (int k = 0; k < max_steps; ++k) {
+                st = E->enqueue(E->step, es, false);
+                if (st != HELM_OK) return st;
+            }
+        } else {
+            HELM_CK(cudaGraphLaunch(E->exec, es));
+        }
         HELM_CK(cudaMemcpyAsync(E->h_ctrl, E->d_ctrl, 3 * sizeof(int), cudaMemcpyDeviceToHost, es));
         HELM_CK(cudaMemcpyAsync(E->h_state, E->d_state, sizeof(InstState) * E->cap,
                                 cudaMemcpyDeviceToHost, es));
@@ -1034,7 +1166,7 @@ helm_status helm_batch_profile(helm_batch* b, int max_steps, uint64_t* launches,
     for (auto& kv : b->engines) {
         Engine* E = kv.second.get();
         if (E->active_count() == 0) continue;
-        helm_status st = E->prepare();
+        helm_status st = E->prepare_plan();
         if (st != HELM_OK) return st;
         const size_t nl = E->step.size();
         std::vector<cudaEvent_t> ev(2 * nl);

@@ -1,0 +1,198 @@
+"""Continuous-batching server for streams of Helmholtz solves (host scheduling only).
+
+Requests of different dimension, grid size and k arrive over time; the server keeps the
+solves resident on the device in one ``helm_batch`` (one engine per kernel class, its
+plans, multigrid hierarchies and iterates in device memory), admits arrivals whenever
+the batch's device-memory cap allows, advances every active solve together a few outer
+steps at a time, and retires solves as they converge.  A solve admitted while others are
+mid-flight shares their launches from the next chunk on; its arithmetic depends only on
+its own data, so its result is the same alone and in the mix.
+
+Latency of a request = completion time - arrival time, on the host clock.  All
+arithmetic runs in the CUDA library through the C ABI (``binding``); this module only
+orders admissions, steps and polls.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import binding as B
+
+
+@dataclass
+class Job:
+    """One request: a problem (device tensors f, g, u) and its bookkeeping."""
+    rid: int
+    D: int
+    n: int
+    h: float
+    k: float
+    f: object
+    g: object
+    u: object
+    t_arrival: float
+    tol: float = 1e-8
+    max_outer: int = 2000
+    ticket: int | None = None
+    t_admit: float | None = None
+    t_done: float | None = None
+    status: int | None = None
+    iters: int | None = None
+    hist: np.ndarray | None = field(default=None, repr=False)
+
+
+class Server:
+    """Admission queue + batch stepping + retirement.
+
+    hbm_cap_bytes  cap on the workspace the batch may hold (HELM_ENOMEM beyond it:
+                   the request waits in the queue until solves retire).
+    chunk          outer steps per batch launch between admission / retirement checks.
+    prec           inner precision of every solve (HELM_PREC_MIXED by default).
+    """
+
+    def __init__(self, hbm_cap_bytes: int, chunk: int = 4, prec: int = B.HELM_PREC_MIXED,
+                 schedule=None, clock=time.perf_counter):
+        self.batch = B.helm_batch_create(hbm_cap_bytes)
+        if schedule is not None:
+            B.helm_batch_set_cycle(self.batch, *schedule)
+        self.chunk = chunk
+        self.prec = prec
+        self.clock = clock
+        self.queue: deque[Job] = deque()
+        self.active: dict[int, Job] = {}
+        self.done: list[Job] = []
+        self.max_in_use = 0
+
+    def submit(self, job: Job) -> None:
+        self.queue.append(job)
+
+    def admit(self) -> int:
+        """Admit queued jobs in arrival order while the memory cap allows."""
+        n = 0
+        while self.queue:
+            job = self.queue[0]
+            t = B.helm_batch_submit_geom(self.batch, job.D, job.n, job.h, job.k, self.prec,
+                                         job.f, job.g, job.u, job.tol, job.max_outer)
+            if t is None:
+                break                       # over the cap: wait for retirements
+            job.ticket = t
+            job.t_admit = self.clock()
+            self.active[t] = job
+            self.queue.popleft()
+            n += 1
+        a, used = B.helm_batch_info(self.batch)
+        self.max_in_use = max(self.max_in_use, used)
+        return n
+
+    def step(self) -> list[Job]:
+        """Advance every active solve by up to `chunk` outer steps; return the finished."""
+        if not self.active:
+            return []
+        B.helm_batch_step(self.batch, self.chunk)
+        now = self.clock()
+        fin = []
+        for t, job in list(self.active.items()):
+            r = B.helm_batch_poll(self.batch, t, job.max_outer)
+            if r is not None:
+                job.status, job.iters, job.hist = r
+                job.t_done = now
+                fin.append(job)
+                del self.active[t]
+        self.done.extend(fin)
+        return fin
+
+    def run(self, jobs: list[Job], realtime: bool = True) -> list[Job]:
+        """Serve `jobs` (sorted by arrival time, seconds from the start) to completion."""
+        pending = deque(sorted(jobs, key=lambda j: j.t_arrival))
+        t0 = self.clock()
+        if realtime:
+            for j in pending:
+                j.t_arrival += t0
+        while pending or self.queue or self.active:
+            now = self.clock()
+            while pending and (not realtime or pending[0].t_arrival <= now):
+                job = pending.popleft()
+                if not realtime:
+                    job.t_arrival = now
+                self.submit(job)
+            self.admit()
+            if self.active:
+                self.step()
+            elif pending and realtime:
+                time.sleep(max(0.0, min(pending[0].t_arrival - self.clock(), 0.001)))
+        return self.done
+
+    def close(self) -> None:
+        B.helm_batch_destroy(self.batch)
+
+
+def latency_stats(jobs: list[Job]) -> dict:
+    lat = np.array([j.t_done - j.t_arrival for j in jobs if j.t_done is not None])
+    if lat.size == 0:
+        return {"count": 0}
+    span = max(j.t_done for j in jobs) - min(j.t_arrival for j in jobs)
+    return {"count": int(lat.size), "p50_ms": float(1e3 * np.percentile(lat, 50)),
+            "p99_ms": float(1e3 * np.percentile(lat, 99)), "mean_ms": float(1e3 * lat.mean()),
+            "solves_per_s": float(lat.size / span) if span > 0 else None}
+
+
+def _pool_key(req):
+    p = req.problem
+    return (p.D, p.n, p.meta["kind"])
+
+
+def main(argv=None) -> int:
+    """Serve a seeded stream of mixed 2D / 3D requests and print latency / throughput."""
+    import argparse
+    import json
+
+    import torch
+
+    from . import build, inputs
+
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--rate", type=float, default=100.0, help="mean arrivals per second")
+    ap.add_argument("--count", type=int, default=200)
+    ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--cap-gb", type=float, default=120.0)
+    ap.add_argument("--chunk", type=int, default=4)
+    ap.add_argument("--sizes-2d", default="127,255,511,1023,2047")
+    ap.add_argument("--sizes-3d", default="63,127,255")
+    args = ap.parse_args(argv)
+    build.build()
+    B.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    reqs = inputs.served_stream(args.rate, args.count, seed=args.seed,
+                                sizes_2d=tuple(int(x) for x in args.sizes_2d.split(",")),
+                                sizes_3d=tuple(int(x) for x in args.sizes_3d.split(",")),
+                                materialise=False)
+    # device data: one materialised source / wall-data pair per (D, n, kind); each request
+    # keeps its own k and its own solution buffer
+    pool = {}
+    jobs = []
+    for i, r in enumerate(reqs):
+        key = _pool_key(r)
+        if key not in pool:
+            p = inputs.materialise(r.problem)
+            pool[key] = (torch.from_numpy(p.f).to(dev), torch.from_numpy(p.g).to(dev))
+        f, g = pool[key]
+        p = r.problem
+        jobs.append(Job(i, p.D, p.n, p.h, p.k, f, g, torch.zeros_like(g), r.t_arrival))
+    torch.cuda.synchronize()
+    srv = Server(int(args.cap_gb * (1 << 30)), chunk=args.chunk)
+    done = srv.run(jobs, realtime=True)
+    stats = latency_stats(done)
+    stats.update({"rate": args.rate, "requests": args.count, "chunk": args.chunk,
+                  "converged": sum(j.status == B.HELM_CONVERGED for j in done),
+                  "max_workspace_gb": srv.max_in_use / (1 << 30)})
+    srv.close()
+    print(json.dumps(stats))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -282,3 +282,22 @@ def test_integer_pipe_conversions_match_hardware(B):
     # the complex64 residual path converts with integer operations; they must agree with
     # the GPU's own IEEE conversions (round to nearest even) outside the subnormal range
     assert B.helm_selftest_conversions(1 << 22, 12345) == 0
+
+
+def test_autotuner_picks_a_converging_schedule_and_restores_u(B):
+    p = inputs.gaussian_cavity_2d(3.0, n=255)
+    plan = B.helm_plan_create(2, p.n, p.h, p.k, prec=1)
+    f = _t(p.f)
+    g = _t(p.g)
+    u0 = _t(np.random.default_rng(3).standard_normal((p.n + 2, p.n + 2)) * 0.0 + 0j)
+    u = u0.clone()
+    nu1, nu2, cyc, ms = B.helm_plan_autotune(plan, f, g, u, 1e-8, 2000)
+    assert (nu1, nu2, cyc) in [(1, 0, 1), (0, 1, 1), (1, 1, 1), (2, 1, 1), (1, 2, 1), (2, 2, 1),
+                               (3, 3, 1), (1, 1, 2)]
+    assert ms > 0
+    assert torch.equal(u, u0)
+    st, iters, hist = B.helm_solve(plan, f, g, u, 1e-8, 2000)
+    assert st == B.HELM_CONVERGED
+    exact = fd.solve_exact_dst(p.f, p.g, p.h, p.k)
+    assert _relerr(u.cpu().numpy(), exact) <= 1e-6
+    B.helm_plan_destroy(plan)

@@ -1,0 +1,59 @@
+"""Served stream on the GPU: Poisson arrivals of mixed 2D / 3D solves through the
+continuous-batching server; every result is the same alone and in the mix, admission
+respects the memory cap, every solve converges to its exact discrete solution."""
+import numpy as np
+import pytest
+
+from oracle import fd
+from paper_2308_11469_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_11469_gb300 import binding, build
+    build.build()
+    binding.load()
+    return binding
+
+
+def test_served_stream_equals_solo(B):
+    from paper_2308_11469_gb300 import serve
+    reqs = inputs.served_stream(rate=400.0, count=24, seed=11, sizes_2d=(31, 63, 127, 255),
+                                sizes_3d=(15, 31))
+    jobs = []
+    for i, r in enumerate(reqs):
+        p = r.problem
+        f = torch.from_numpy(p.f).to(DEV)
+        g = torch.from_numpy(p.g).to(DEV)
+        jobs.append(serve.Job(i, p.D, p.n, p.h, p.k, f, g, torch.zeros_like(g), r.t_arrival))
+    cap = 48 << 20                       # small cap: admissions must wait for retirements
+    srv = serve.Server(cap, chunk=3)
+    done = srv.run(jobs, realtime=True)
+    assert len(done) == len(jobs)
+    assert srv.max_in_use <= cap
+    stats = serve.latency_stats(done)
+    assert stats["count"] == len(jobs) and stats["p99_ms"] >= stats["p50_ms"] > 0
+    srv.close()
+    for j in done:
+        p = reqs[j.rid].problem
+        assert j.status == B.HELM_CONVERGED
+        plan = B.helm_plan_create(p.D, p.n, p.h, p.k, prec=B.HELM_PREC_MIXED)
+        u = torch.zeros_like(j.g)
+        st, iters, hist = B.helm_solve(plan, j.f, j.g, u, 1e-8, 2000)
+        B.helm_plan_destroy(plan)
+        assert st == j.status and iters == j.iters
+        assert np.array_equal(hist, j.hist)
+        assert torch.equal(u, j.u)
+        exact = fd.solve_exact_dst(p.f, p.g, p.h, p.k)
+        ref = np.linalg.norm(exact)
+        # relres 1e-8 against ||b|| bounds the error by ||r|| / (lambda_min - k^2)
+        lam = fd.lambda_min(p.D, p.n, p.h)
+        bound = max(1e-6, 2 * hist[-1] * np.linalg.norm(fd.lifted_rhs(p.f, p.g, p.h)) / (lam - p.k ** 2) / ref)
+        assert np.linalg.norm(j.u.cpu().numpy() - exact) / ref <= bound
