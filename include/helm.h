@@ -136,11 +136,16 @@ HELM_API helm_status helm_plan_autotune(helm_plan* plan, const void* f, const vo
  *   u         padded complex128, (n+2)^D (device).  In: the interior is the starting
  *             iterate u_0 (zeros = the paper's start).  Out: the last iterate u_iters,
  *             its wall ring overwritten with g.
- *   tol       stop when relres_N = ||r_N||_2 / ||r_0||_2 <= tol (interior 2-norms).
+ *   tol       stop when relres_N = ||r_N||_2 / ||b||_2 <= tol (interior 2-norms), where
+ *             r_N = f - (Delta_h + k^2) u_N and b = f minus the wall values' share of the
+ *             stencil (the right-hand side with the Dirichlet nodes eliminated, Section
+ *             2.4).  With a zero starting interior r_0 = b and relres_0 = 1; a starting
+ *             iterate from an earlier solve (resume) starts at its own, smaller relres.
+ *             If b = 0 the denominator is ||r_0||.
  *   max_outer >= 0 outer steps at most.
  *   iters     (host, may be NULL) number of outer steps performed.
  *   res_hist  (host, may be NULL) relres_0 .. relres_iters (iters + 1 doubles; the
- *             caller provides max_outer + 1).  relres_0 = 1 unless r_0 = 0.
+ *             caller provides max_outer + 1).
  * Returns HELM_CONVERGED / HELM_MAXITER / HELM_DIVERGED / HELM_ENONFINITE, or an error.
  * Synchronous: returns after the stream has finished the solve.
  */

@@ -45,7 +45,11 @@ template <> struct Inner<double> {
 // not decreased for 10 consecutive steps and has grown to at least twice its smallest
 // value so far (stagnation at the rounding floor is not divergence); NONFINITE on NaN /
 // Inf; MAXITER at max_outer.
-__device__ void finalize(const InstDesc& I, InstState* stp, double norm2, double emax2, int mode)
+// relres_N = ||r_N|| / ||b||, b the lifted right-hand side (f minus the wall values'
+// contribution to the stencil): with the paper's zero start r_0 = b and relres_0 = 1; a
+// starting iterate that already solves the system well starts with a small relres.
+// mode 0: `second` is ||b||^2; mode 1: it is max |e|^2.
+__device__ void finalize(const InstDesc& I, InstState* stp, double norm2, double second, int mode)
 {
     InstState s = *stp;
     const double norm = sqrt(norm2);
@@ -53,16 +57,17 @@ __device__ void finalize(const InstDesc& I, InstState* stp, double norm2, double
     int N;
     if (mode == 0) {
         N = 0;
-        s.norm0 = norm;
+        const double nb = sqrt(second);
+        s.norm0 = (nb > 0.0) ? nb : norm;      // zero data: measure against r_0 itself
         s.run = 0;
-        s.rmin = 1.0;
-        rel = (norm == 0.0) ? 0.0 : 1.0;
-        if (!isfinite(norm)) rel = norm;
+        rel = (norm == 0.0) ? 0.0 : norm / s.norm0;
+        if (!isfinite(norm) || !isfinite(nb)) rel = norm + nb;
+        s.rmin = rel;
     } else {
         s.it += 1;
         N = s.it;
         rel = norm / s.norm0;
-        I.einf[N - 1] = sqrt(emax2);
+        I.einf[N - 1] = sqrt(second);
     }
     I.hist[N] = rel;
     int out = HELM_ST_ACTIVE;
@@ -81,12 +86,14 @@ __device__ void finalize(const InstDesc& I, InstState* stp, double norm2, double
 }
 
 // Block-wide sums / maxima in a fixed order (xor-shuffle, then warps in order).
-__device__ __forceinline__ void block_reduce(double& a, double& m, double* sa, double* sm)
+// `sum2`: the second channel is summed (mode 0, ||b||^2) instead of maximised (max |e|^2).
+__device__ __forceinline__ void block_reduce(double& a, double& m, double* sa, double* sm, bool sum2)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
-        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const double mo = __shfl_xor_sync(0xffffffffu, m, o);
+        m = sum2 ? m + mo : fmax(m, mo);
     }
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
@@ -99,7 +106,7 @@ __device__ __forceinline__ void block_reduce(double& a, double& m, double* sa, d
         m = 0.0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
             a += sa[i];
-            m = fmax(m, sm[i]);
+            m = sum2 ? m + sm[i] : fmax(m, sm[i]);
         }
     }
 }
@@ -109,7 +116,7 @@ __device__ void tile_done(const InstDesc& I, InstState* stp, int tile, double a,
 {
     __shared__ double sa[NTH / 32], sm[NTH / 32];
     __shared__ int last;
-    block_reduce(a, m, sa, sm);
+    block_reduce(a, m, sa, sm, mode == 0);
     if (threadIdx.x == 0) {
         I.part[tile] = a;
         I.part[I.nres_blocks + tile] = m;
@@ -123,10 +130,11 @@ __device__ void tile_done(const InstDesc& I, InstState* stp, int tile, double a,
     double ta = 0.0, tm = 0.0;
     for (int b = threadIdx.x; b < I.nres_blocks; b += blockDim.x) {
         ta += __ldcg(I.part + b);
-        tm = fmax(tm, __ldcg(I.part + I.nres_blocks + b));
+        const double v = __ldcg(I.part + I.nres_blocks + b);
+        tm = (mode == 0) ? tm + v : fmax(tm, v);
     }
     __syncthreads();
-    block_reduce(ta, tm, sa, sm);
+    block_reduce(ta, tm, sa, sm, mode == 0);
     if (threadIdx.x == 0) {
         finalize(I, stp, ta, tm, mode);
         *I.count = 0u;
@@ -188,6 +196,7 @@ k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     const double mih2 = -I.ih2;
     const double mcdiag = -I.cdiag;
     R r2 = 0;
+    double r2d = 0.0, b2 = 0.0;
     const int lx = (threadIdx.x & 31) + 1;
 #pragma unroll
     for (int k = 0; k < T2 / 8; ++k) {
@@ -205,9 +214,22 @@ k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
         r.y = fma((a.y + b.y) + (d.y + u.y), mih2, fma(c.y, mcdiag, fv.y));
         const c2 ri = Inner<R>::from(r);
         rhs[gy * P + gx] = ri;
-        r2 += ri.x * ri.x + ri.y * ri.y;
+        if (MODE == 1) {
+            r2 += ri.x * ri.x + ri.y * ri.y;
+        } else {
+            // once per solve, in FP64: ||r_0||^2 and ||b||^2, b = f - (wall neighbours)/h^2
+            // formed with the same operations as r (so r_0 = b bit for bit from a zero start)
+            r2d += r.x * r.x + r.y * r.y;
+            const double2 z = make_double2(0.0, 0.0);
+            const double2 aw = (gx == 1) ? a : z, bw = (gx == n) ? b : z;
+            const double2 dw = (gy == 1) ? d : z, uw = (gy == n) ? u : z;
+            const double bx = fma((aw.x + bw.x) + (dw.x + uw.x), mih2, fma(0.0, mcdiag, fv.x));
+            const double by = fma((aw.y + bw.y) + (dw.y + uw.y), mih2, fma(0.0, mcdiag, fv.y));
+            b2 += bx * bx + by * by;
+        }
     }
-    tile_done(I, stp, item.ty * I.res_tx + item.tx, (double)r2, (double)emax2, MODE);
+    tile_done(I, stp, item.ty * I.res_tx + item.tx, MODE == 0 ? r2d : (double)r2,
+              MODE == 0 ? b2 : (double)emax2, MODE);
 }
 
 // ---------------------------------------------------------------------------
@@ -242,6 +264,7 @@ k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     const int x = item.tx * 32 + (threadIdx.x & 31) + 1;
     const int z = item.tz + 1;
     R r2 = 0, emax2 = 0;
+    double r2d = 0.0, b2 = 0.0;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int y = item.ty * 16 + k * 8 + (threadIdx.x >> 5) + 1;
@@ -271,10 +294,21 @@ k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
         r.y = fma(((w.y + ea.y) + (so.y + no.y)) + (dn.y + up.y), mih2, fma(c.y, mcdiag, fv.y));
         const c2 ri = Inner<R>::from(r);
         rhs[oe] = ri;
-        r2 += ri.x * ri.x + ri.y * ri.y;
+        if (MODE == 1) {
+            r2 += ri.x * ri.x + ri.y * ri.y;
+        } else {
+            r2d += r.x * r.x + r.y * r.y;
+            const double2 zz = make_double2(0.0, 0.0);
+            const double2 w1 = (x == 1) ? w : zz, w2 = (x == n) ? ea : zz;
+            const double2 w3 = (y == 1) ? so : zz, w4 = (y == n) ? no : zz;
+            const double2 w5 = (z == 1) ? dn : zz, w6 = (z == n) ? up : zz;
+            const double bx = fma(((w1.x + w2.x) + (w3.x + w4.x)) + (w5.x + w6.x), mih2, fma(0.0, mcdiag, fv.x));
+            const double by = fma(((w1.y + w2.y) + (w3.y + w4.y)) + (w5.y + w6.y), mih2, fma(0.0, mcdiag, fv.y));
+            b2 += bx * bx + by * by;
+        }
     }
     const int tile = (item.tz * I.res_ty + item.ty) * I.res_tx + item.tx;
-    tile_done(I, stp, tile, (double)r2, (double)emax2, MODE);
+    tile_done(I, stp, tile, MODE == 0 ? r2d : (double)r2, MODE == 0 ? b2 : (double)emax2, MODE);
 }
 
 // One CTA: is any instance still iterating?  Counts the step and sets the loop condition.

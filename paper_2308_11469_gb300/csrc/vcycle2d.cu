@@ -33,32 +33,50 @@ constexpr int NW = NT / 32;
 
 template <typename T> __device__ __forceinline__ T cz() { T v; v.x = 0; v.y = 0; return v; }
 
+// Shared-memory tiles are stored as two colour planes: node (lx, ly) of the staged
+// window, whose global colour is (gx + gy) & 1, lives in plane[colour] at row ly, column
+// lx >> 1 (row stride W/2).  A warp that updates 32 nodes of one colour in a row then
+// reads its west / east / north / south neighbours (the other colour) and its own rhs as
+// contiguous runs: no shared-memory bank conflicts.
+template <int W>
+struct Planes {
+    static constexpr int WH = W / 2;
+    __device__ __forceinline__ static int at(int lx, int ly) { return ly * WH + (lx >> 1); }
+};
+
 // One half-sweep over the nodes of colour `color` within Chebyshev distance `ring` of
-// the tile, clipped to the interior.  E, Rh: shared arrays of row stride W whose
+// the tile, clipped to the interior.  E0/E1, R0/R1: colour planes of the window whose
 // element (0, 0) is global node (gx0, gy0).
 template <typename R, int W>
-__device__ __forceinline__ void half_sweep(typename C2<R>::T* E, const typename C2<R>::T* Rh,
-                                           int gx0, int gy0, int x0, int y0, int ring, int n,
-                                           R h2, int color)
+__device__ __forceinline__ void half_sweep(typename C2<R>::T* E0, typename C2<R>::T* E1,
+                                           const typename C2<R>::T* R0,
+                                           const typename C2<R>::T* R1, int gx0, int gy0,
+                                           int x0, int y0, int ring, int n, R h2, int color)
 {
     typedef typename C2<R>::T c2;
+    typedef Planes<W> PL;
     const int xa = max(x0 - ring, 1), xb = min(x0 + TX - 1 + ring, n);
     const int ya = max(y0 - ring, 1), yb = min(y0 + TY - 1 + ring, n);
     const int lane = threadIdx.x & 31;
+    c2* __restrict__ Ec = color ? E1 : E0;
+    const c2* __restrict__ Eo = color ? E0 : E1;
+    const c2* __restrict__ Rc = color ? R1 : R0;
     for (int gy = ya + (int)(threadIdx.x >> 5); gy <= yb; gy += NW) {
         const int xs = xa + (((xa + gy) & 1) ^ color);
-        const int row = (gy - gy0) * W - gx0;
+        const int ly = gy - gy0;
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const int gx = xs + 2 * (lane + 32 * j);
             if (gx > xb) break;
-            const int o = row + gx;
-            const c2 a = E[o - 1], b = E[o + 1], c = E[o - W], d = E[o + W];
-            const c2 rr = Rh[o];
+            const int lx = gx - gx0;
+            const int o = PL::at(lx, ly);
+            const c2 a = Eo[PL::at(lx - 1, ly)], b = Eo[PL::at(lx + 1, ly)];
+            const c2 c = Eo[PL::at(lx, ly - 1)], d = Eo[PL::at(lx, ly + 1)];
+            const c2 rr = Rc[o];
             c2 v;
             v.x = ((a.x + b.x + c.x + d.x) - h2 * rr.x) * (R)0.25;
             v.y = ((a.y + b.y + c.y + d.y) - h2 * rr.y) * (R)0.25;
-            E[o] = v;
+            Ec[o] = v;
         }
     }
 }
@@ -73,6 +91,7 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     typedef typename C2<R>::T c2;
     constexpr int H = 2 * NU + 2;
     constexpr int W = TX + 2 * H, HH = TY + 2 * H;
+    typedef Planes<W> PL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const MgItem item = items[blockIdx.y];
     if (st[item.inst].status != HELM_ST_ACTIVE) return;
@@ -84,9 +103,14 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     if ((int)blockIdx.x >= ntx * nty) return;
     const int x0 = 1 + (blockIdx.x % ntx) * TX;
     const int y0 = 1 + (blockIdx.x / ntx) * TY;
-    c2* E = reinterpret_cast<c2*>(smem_raw);
-    c2* Rs = E + W * HH;
+    c2* base = reinterpret_cast<c2*>(smem_raw);
+    constexpr int PS = HH * PL::WH;                 // one colour plane
+    c2* const E0 = base;
+    c2* const E1 = base + PS;
+    c2* const R0 = base + 2 * PS;
+    c2* const R1 = base + 3 * PS;
     const int gx0 = x0 - H, gy0 = y0 - H;
+    const int cpar = (gx0 + gy0) & 1;
     const bool zero = (zero_mode == 2) || (zero_mode == 1 && item.level > 0);
     const c2* __restrict__ ge = (const c2*)L.e;
     const c2* __restrict__ gr = (const c2*)L.rhs;
@@ -102,9 +126,11 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
             const int gx = gx0 + lx;
             const bool in = yin && gx >= 1 && gx <= n;
             const size_t g = in ? (size_t)gy * P + gx : 0;
-            if (zero) E[ly * W + lx] = cz<c2>();
-            else cp_async_elem<sizeof(c2)>(E + ly * W + lx, ge + g, in);
-            cp_async_elem<sizeof(c2)>(Rs + ly * W + lx, gr + g, in);
+            const int c = (lx + ly + cpar) & 1;
+            const int o = PL::at(lx, ly);
+            if (zero) (c ? E1 : E0)[o] = cz<c2>();
+            else cp_async_elem<sizeof(c2)>((c ? E1 : E0) + o, ge + g, in);
+            cp_async_elem<sizeof(c2)>((c ? R1 : R0) + o, gr + g, in);
         }
     }
     cp_async_wait_all();
@@ -113,9 +139,9 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     int ring = 2 * NU + 1;
 #pragma unroll 1
     for (int s = 0; s < NU; ++s) {
-        half_sweep<R, W>(E, Rs, gx0, gy0, x0, y0, ring--, n, h2, 0);
+        half_sweep<R, W>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 0);
         __syncthreads();
-        half_sweep<R, W>(E, Rs, gx0, gy0, x0, y0, ring--, n, h2, 1);
+        half_sweep<R, W>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 1);
         __syncthreads();
     }
     // smoothed iterate of the tile -> e2
@@ -126,27 +152,38 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
 #pragma unroll
         for (int tx = lane; tx < TX; tx += 32) {
             const int gx = x0 + tx;
-            if (gx <= n) ge2[(size_t)gy * P + gx] = E[(ty + H) * W + tx + H];
+            const int lx = tx + H, ly = ty + H;
+            if (gx <= n) ge2[(size_t)gy * P + gx] = (((lx + ly + cpar) & 1) ? E1 : E0)[PL::at(lx, ly)];
         }
     }
-    // residual on the tile plus a 1-node ring, in place of rhs
+    // residual on the tile plus a 1-node ring, in place of rhs (one colour at a time)
     const R ih2 = (R)1 / h2;
     {
         const int xa = max(x0 - 1, 1), xb = min(x0 + TX, n);
         const int ya = max(y0 - 1, 1), yb = min(y0 + TY, n);
-        for (int gy = ya + (int)(threadIdx.x >> 5); gy <= yb; gy += NW) {
-            const int row = (gy - gy0) * W - gx0;
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const int gx = xa + lane + 32 * j;
-                if (gx > xb) break;
-                const int o = row + gx;
-                const c2 c = E[o], a = E[o - 1], b = E[o + 1], u = E[o - W], d = E[o + W];
-                const c2 rr = Rs[o];
-                c2 v;
-                v.x = rr.x - ((a.x + b.x + u.x + d.x) - (R)4 * c.x) * ih2;
-                v.y = rr.y - ((a.y + b.y + u.y + d.y) - (R)4 * c.y) * ih2;
-                Rs[o] = v;
+        for (int color = 0; color < 2; ++color) {
+            const c2* __restrict__ Ec = color ? E1 : E0;
+            const c2* __restrict__ Eo = color ? E0 : E1;
+            c2* __restrict__ Rc = color ? R1 : R0;
+            for (int gy = ya + (int)(threadIdx.x >> 5); gy <= yb; gy += NW) {
+                const int xs = xa + (((xa + gy) & 1) ^ color);
+                const int ly = gy - gy0;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int gx = xs + 2 * (lane + 32 * j);
+                    if (gx > xb) break;
+                    const int lx = gx - gx0;
+                    const int o = PL::at(lx, ly);
+                    const c2 c = Ec[o];
+                    const c2 a = Eo[PL::at(lx - 1, ly)], b = Eo[PL::at(lx + 1, ly)];
+                    const c2 u = Eo[PL::at(lx, ly - 1)], d = Eo[PL::at(lx, ly + 1)];
+                    const c2 rr = Rc[o];
+                    c2 v;
+                    v.x = rr.x - ((a.x + b.x + u.x + d.x) - (R)4 * c.x) * ih2;
+                    v.y = rr.y - ((a.y + b.y + u.y + d.y) - (R)4 * c.y) * ih2;
+                    Rc[o] = v;
+                }
             }
         }
     }
@@ -160,7 +197,7 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
         const int Y = Ya + cy;
         const int X = Xa + lane;
         if (Y > nc || X > nc) continue;
-        const int o = (2 * Y - gy0) * W + (2 * X - gx0);
+        const int lx = 2 * X - gx0, ly = 2 * Y - gy0;
         R ax = 0, ay = 0;
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
@@ -168,7 +205,7 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
 #pragma unroll
             for (int dx = -1; dx <= 1; ++dx) {
                 const R wgt = wy * ((dx == 0) ? (R)2 : (R)1);
-                const c2 r = Rs[o + dy * W + dx];
+                const c2 r = (((lx + dx + ly + dy + cpar) & 1) ? R1 : R0)[PL::at(lx + dx, ly + dy)];
                 ax += wgt * r.x;
                 ay += wgt * r.y;
             }
@@ -191,6 +228,7 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     constexpr int H = 2 * NU;
     constexpr int W = TX + 2 * H, HH = TY + 2 * H;
     constexpr int CW = W / 2 + 2, CH = HH / 2 + 2;
+    typedef Planes<W> PL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const MgItem item = items[blockIdx.y];
     if (st[item.inst].status != HELM_ST_ACTIVE) return;
@@ -202,10 +240,15 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     if ((int)blockIdx.x >= ntx * nty) return;
     const int x0 = 1 + (blockIdx.x % ntx) * TX;
     const int y0 = 1 + (blockIdx.x / ntx) * TY;
-    c2* E = reinterpret_cast<c2*>(smem_raw);
-    c2* Rs = E + W * HH;
-    c2* Cs = Rs + W * HH;
+    c2* base = reinterpret_cast<c2*>(smem_raw);
+    constexpr int PS = HH * PL::WH;
+    c2* const E0 = base;
+    c2* const E1 = base + PS;
+    c2* const R0 = base + 2 * PS;
+    c2* const R1 = base + 3 * PS;
+    c2* Cs = base + 4 * PS;
     const int gx0 = x0 - H, gy0 = y0 - H;
+    const int cpar = (gx0 + gy0) & 1;
     // coarse window: X in [cx0, cx0 + CW), clipped to the padded coarse grid
     const int cx0 = max(gx0, 0) >> 1, cy0 = max(gy0, 0) >> 1;
     const int nc1 = C.n + 1;
@@ -233,8 +276,10 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
             const int gx = gx0 + lx;
             const bool in = yin && gx >= 1 && gx <= n;
             const size_t g = in ? (size_t)gy * P + gx : 0;
-            cp_async_elem<sizeof(c2)>(E + ly * W + lx, ge2 + g, in);
-            cp_async_elem<sizeof(c2)>(Rs + ly * W + lx, gr + g, in);
+            const int c = (lx + ly + cpar) & 1;
+            const int o = PL::at(lx, ly);
+            cp_async_elem<sizeof(c2)>((c ? E1 : E0) + o, ge2 + g, in);
+            cp_async_elem<sizeof(c2)>((c ? R1 : R0) + o, gr + g, in);
         }
     }
     cp_async_wait_all();
@@ -251,10 +296,11 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
             const int X0 = (gx >> 1) - cx0, X1 = ((gx + 1) >> 1) - cx0;
             const c2 a = Cs[Y0 * CW + X0], b = Cs[Y0 * CW + X1];
             const c2 c = Cs[Y1 * CW + X0], d = Cs[Y1 * CW + X1];
-            c2 v = E[ly * W + lx];
+            c2* Ep = (((lx + ly + cpar) & 1) ? E1 : E0) + PL::at(lx, ly);
+            c2 v = *Ep;
             v.x += (R)0.25 * (((a.x + b.x) + c.x) + d.x);
             v.y += (R)0.25 * (((a.y + b.y) + c.y) + d.y);
-            E[ly * W + lx] = v;
+            *Ep = v;
         }
     }
     __syncthreads();
@@ -262,9 +308,9 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     int ring = 2 * NU - 1;
 #pragma unroll 1
     for (int s = 0; s < NU; ++s) {
-        half_sweep<R, W>(E, Rs, gx0, gy0, x0, y0, ring--, n, h2, 0);
+        half_sweep<R, W>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 0);
         __syncthreads();
-        half_sweep<R, W>(E, Rs, gx0, gy0, x0, y0, ring--, n, h2, 1);
+        half_sweep<R, W>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 1);
         __syncthreads();
     }
     c2* __restrict__ ge = (c2*)L.e;
@@ -274,7 +320,8 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
 #pragma unroll
         for (int tx = lane; tx < TX; tx += 32) {
             const int gx = x0 + tx;
-            if (gx <= n) ge[(size_t)gy * P + gx] = E[(ty + H) * W + tx + H];
+            const int lx = tx + H, ly = ty + H;
+            if (gx <= n) ge[(size_t)gy * P + gx] = (((lx + ly + cpar) & 1) ? E1 : E0)[PL::at(lx, ly)];
         }
     }
 }

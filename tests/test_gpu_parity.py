@@ -301,3 +301,26 @@ def test_autotuner_picks_a_converging_schedule_and_restores_u(B):
     exact = fd.solve_exact_dst(p.f, p.g, p.h, p.k)
     assert _relerr(u.cpu().numpy(), exact) <= 1e-6
     B.helm_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_resume_from_a_saved_iterate(B, prec):
+    # relres is measured against ||b||: resuming from an interrupted solve continues where
+    # it stopped, and resuming from a converged solve stops at once
+    p = inputs.gaussian_cavity_2d(3.0, n=127)
+    plan = B.helm_plan_create(2, p.n, p.h, p.k, prec=prec)
+    f = _t(p.f)
+    g = _t(p.g)
+    u = torch.zeros_like(g)
+    st, it_full, h_full = B.helm_solve(plan, f, g, u, 1e-8, 500)
+    assert st == B.HELM_CONVERGED
+    st, it0, h0 = B.helm_solve(plan, f, g, u, 1e-8, 500)
+    assert st == B.HELM_CONVERGED and it0 == 0 and h0[0] <= 1e-8
+    u.zero_()
+    st, it_a, h_a = B.helm_solve(plan, f, g, u, 1e-8, 6)
+    assert st == B.HELM_MAXITER and it_a == 6
+    st, it_b, h_b = B.helm_solve(plan, f, g, u, 1e-8, 500)
+    assert st == B.HELM_CONVERGED
+    assert abs(h_b[0] - h_a[-1]) <= 1e-6 * h_a[-1]
+    assert it_a + it_b <= it_full + 1
+    B.helm_plan_destroy(plan)
