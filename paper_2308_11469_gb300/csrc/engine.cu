@@ -227,12 +227,12 @@ struct Engine {
                 J = std::max(J, slots[i]->d.ltail);
                 max_tail = std::max(max_tail, slots[i]->d.lev[slots[i]->d.ltail].n);
             }
-        struct Ph { int off, cnt, w_rb, w_rs, w_pr, w_z; double b_rb, b_rs, b_pr, b_z; int tiles; };
+        struct Ph { int off, cnt, w_rb, w_rs, w_pr, w_z; double b_rb, b_rs, b_pr, b_z; int tiles, shape, nmax; };
         const double eb = elem_bytes(prec);
         auto pts = [&](int m) { return (D == 3) ? (double)m * m * m : (double)m * m; };
         std::vector<Ph> ph(J);
         for (int j = 0; j < J; ++j) {
-            Ph p{(int)items.size(), 0, 0, 0, 0, 0, 0.0, 0.0, 0.0, 0.0, 0};
+            Ph p{(int)items.size(), 0, 0, 0, 0, 0, 0.0, 0.0, 0.0, 0.0, 0, 0, 0};
             for (int i = 0; i < cap; ++i) {
                 if (!slots[i]) continue;
                 const InstDesc& d = slots[i]->d;
@@ -253,8 +253,15 @@ struct Engine {
                 // prolongation: coarse e in, fine e in and out
                 p.b_pr += (pts(nc) + 2.0 * pts(n)) * eb;
                 p.b_z += pts(n) * eb;
-                if (D == 2) p.tiles = std::max(p.tiles, tiles2d(n));
+                p.nmax = std::max(p.nmax, n);
                 ++p.cnt;
+            }
+            // one tile shape per launch (that of its largest level) and the matching grid
+            if (D == 2) {
+                // small tiles only where the large ones would leave the GPU under-filled
+                p.shape = (tile_shape2d(p.nmax) == 1 && p.cnt * tiles2d_for(p.nmax, 0) < 2 * 152) ? 1 : 0;
+                for (int q = p.off; q < p.off + p.cnt; ++q)
+                    p.tiles = std::max(p.tiles, tiles2d_for(slots[items[q].inst]->d.lev[items[q].level].n, p.shape));
             }
             ph[j] = p;
         }
@@ -322,11 +329,11 @@ struct Engine {
         };
         auto vcycle2d = [&](std::vector<LaunchRec>& out, bool zero_start) {
             for (int j = 0; j < J; ++j)
-                out.push_back({LaunchRec::DOWN, ph[j].off, ph[j].cnt, ph[j].tiles, 0,
+                out.push_back({LaunchRec::DOWN, ph[j].off, ph[j].cnt, ph[j].tiles, ph[j].shape,
                                zero_start ? 2 : 1, 0.0});
             tail(out, zero_start);
             for (int j = J - 1; j >= 0; --j)
-                out.push_back({LaunchRec::UP, ph[j].off, ph[j].cnt, ph[j].tiles, 0, 0, 0.0});
+                out.push_back({LaunchRec::UP, ph[j].off, ph[j].cnt, ph[j].tiles, ph[j].shape, 0, 0.0});
         };
         auto vcycle = [&](std::vector<LaunchRec>& out, bool zero_start) {
             if (D == 2 && nu1 <= 4 && nu2 <= 4) { vcycle2d(out, zero_start); return; }
@@ -418,10 +425,10 @@ struct Engine {
                                 L.mode, s);
                 break;
             case LaunchRec::DOWN:
-                e = launch_down2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu1, L.mode, s);
+                e = launch_down2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu1, L.mode, L.color, s);
                 break;
             case LaunchRec::UP:
-                e = launch_up2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu2, s);
+                e = launch_up2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu2, L.color, s);
                 break;
             case LaunchRec::RESID:
                 e = launch_residual(D, prec, d_desc, d_state, d_res + L.off, L.cnt, L.mode, s);

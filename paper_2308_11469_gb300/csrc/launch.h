@@ -43,11 +43,15 @@ cudaError_t setup_outer();
 // descent: nu1 sweeps + residual + restriction; e (or zero) -> e2, coarse rhs.
 // zero_mode: 2 = every level's iterate is zero, 1 = levels > 0 are zero, 0 = load e.
 cudaError_t launch_down2d(int prec, const InstDesc* insts, const InstState* st, const MgItem* items,
-                          int nitems, int max_tiles, int nu1, int zero_mode, cudaStream_t s);
+                          int nitems, int max_tiles, int nu1, int zero_mode, int shape,
+                          cudaStream_t s);
 // ascent: e2 + prolongation of the coarse e, nu2 sweeps -> e
 cudaError_t launch_up2d(int prec, const InstDesc* insts, const InstState* st, const MgItem* items,
-                        int nitems, int max_tiles, int nu2, cudaStream_t s);
+                        int nitems, int max_tiles, int nu2, int shape, cudaStream_t s);
+// tile shape of a level (0 = 64 x 32, 1 = 32 x 16 for n <= 511) and its tile count
+int tile_shape2d(int n);
 int tiles2d(int n);
+int tiles2d_for(int n, int shape);
 cudaError_t setup_2d(int prec);
 
 // ---- outer FP64 iteration (outer.cu) ----

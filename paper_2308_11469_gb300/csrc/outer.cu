@@ -151,21 +151,24 @@ __global__ void __launch_bounds__(NTH)
 k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
              const ResItem* __restrict__ items)
 {
-    pdl_wait();
-    pdl_trigger();
     typedef typename C2<R>::T c2;
     __shared__ double2 U[(T2 + 2) * (T2 + 2)];
+    // descriptors are host-written: read them before waiting for the predecessor kernel
     const ResItem item = items[blockIdx.x];
-    InstState* stp = st + item.inst;
-    const InstState s = *stp;
-    if (s.status != HELM_ST_ACTIVE) return;
     const InstDesc& I = insts[item.inst];
     const int n = I.n;
     const int S = n + 2;
-    const double2* __restrict__ uin = I.u[s.it & 1];
-    double2* __restrict__ uout = I.u[(s.it + 1) & 1];
+    const double2* u0 = I.u[0];
+    const double2* u1 = I.u[1];
     const double2* __restrict__ f = I.f;
     const LevelDesc L0 = I.lev[0];
+    pdl_wait();
+    pdl_trigger();
+    InstState* stp = st + item.inst;
+    const InstState s = *stp;
+    if (s.status != HELM_ST_ACTIVE) return;
+    const double2* __restrict__ uin = (s.it & 1) ? u1 : u0;
+    double2* __restrict__ uout = (double2*)((s.it & 1) ? u0 : u1);
     const c2* __restrict__ e = (const c2*)L0.e;
     c2* __restrict__ rhs = (c2*)L0.rhs;
     const int P = L0.pitch;

@@ -207,14 +207,14 @@ __global__ void __launch_bounds__(TNT)
 k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
        const MgItem* __restrict__ items, int nu1, int nu2, int load_e)
 {
-    pdl_wait();
-    pdl_trigger();
     typedef typename C2<R>::T c2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     c2* base = reinterpret_cast<c2*>(smem_raw);
     const MgItem item = items[blockIdx.x];
+    const LevelDesc L0 = insts[item.inst].lev[item.level];   // host-written: read before the wait
+    pdl_wait();
+    pdl_trigger();
     if (st[item.inst].status != HELM_ST_ACTIVE) return;
-    const LevelDesc L0 = insts[item.inst].lev[item.level];
     if (L0.n != N0) return;                       // launched for another tail size
     constexpr int TOT = tail_elems<D, N0>();
     for (int i = threadIdx.x; i < TOT; i += TNT) base[i] = cz<c2>();

@@ -26,8 +26,6 @@
 namespace helm {
 namespace {
 
-constexpr int TX = 64;
-constexpr int TY = 32;
 constexpr int NT = 512;
 constexpr int NW = NT / 32;
 
@@ -47,7 +45,7 @@ struct Planes {
 // One half-sweep over the nodes of colour `color` within Chebyshev distance `ring` of
 // the tile, clipped to the interior.  E0/E1, R0/R1: colour planes of the window whose
 // element (0, 0) is global node (gx0, gy0).
-template <typename R, int W>
+template <typename R, int W, int TX, int TY>
 __device__ __forceinline__ void half_sweep(typename C2<R>::T* E0, typename C2<R>::T* E1,
                                            const typename C2<R>::T* R0,
                                            const typename C2<R>::T* R1, int gx0, int gy0,
@@ -81,22 +79,24 @@ __device__ __forceinline__ void half_sweep(typename C2<R>::T* E0, typename C2<R>
     }
 }
 
-template <typename R, int NU>
+template <typename R, int NU, int TX, int TY>
 __global__ void __launch_bounds__(NT)
 k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
          const MgItem* __restrict__ items, int zero_mode)
 {
-    pdl_wait();
-    pdl_trigger();
     typedef typename C2<R>::T c2;
     constexpr int H = 2 * NU + 2;
     constexpr int W = TX + 2 * H, HH = TY + 2 * H;
     typedef Planes<W> PL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // work item and level descriptors are written by the host before the launch: read them
+    // before waiting for the predecessor kernel (overlaps its drain)
     const MgItem item = items[blockIdx.y];
-    if (st[item.inst].status != HELM_ST_ACTIVE) return;
     const LevelDesc L = insts[item.inst].lev[item.level];
     const LevelDesc C = insts[item.inst].lev[item.level + 1];
+    pdl_wait();
+    pdl_trigger();
+    if (st[item.inst].status != HELM_ST_ACTIVE) return;
     const int n = L.n;
     const int ntx = (n + TX - 1) / TX;
     const int nty = (n + TY - 1) / TY;
@@ -139,9 +139,9 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     int ring = 2 * NU + 1;
 #pragma unroll 1
     for (int s = 0; s < NU; ++s) {
-        half_sweep<R, W>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 0);
+        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 0);
         __syncthreads();
-        half_sweep<R, W>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 1);
+        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 1);
         __syncthreads();
     }
     // smoothed iterate of the tile -> e2
@@ -188,7 +188,7 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
         }
     }
     __syncthreads();
-    // full weighting at the coarse nodes owned by this tile (32 x 16 of them)
+    // full weighting at the coarse nodes owned by this tile (TX/2 x TY/2 of them)
     c2* __restrict__ cr = (c2*)C.rhs;
     const int nc = C.n;
     const int Xa = (x0 + 1) >> 1, Ya = (y0 + 1) >> 1;
@@ -196,7 +196,7 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     for (int cy = threadIdx.x >> 5; cy < TY / 2; cy += NW) {
         const int Y = Ya + cy;
         const int X = Xa + lane;
-        if (Y > nc || X > nc) continue;
+        if (lane >= TX / 2 || Y > nc || X > nc) continue;
         const int lx = 2 * X - gx0, ly = 2 * Y - gy0;
         R ax = 0, ay = 0;
 #pragma unroll
@@ -217,23 +217,25 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     }
 }
 
-template <typename R, int NU>
+template <typename R, int NU, int TX, int TY>
 __global__ void __launch_bounds__(NT)
 k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
        const MgItem* __restrict__ items)
 {
-    pdl_wait();
-    pdl_trigger();
     typedef typename C2<R>::T c2;
     constexpr int H = 2 * NU;
     constexpr int W = TX + 2 * H, HH = TY + 2 * H;
     constexpr int CW = W / 2 + 2, CH = HH / 2 + 2;
     typedef Planes<W> PL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // work item and level descriptors are written by the host before the launch: read them
+    // before waiting for the predecessor kernel (overlaps its drain)
     const MgItem item = items[blockIdx.y];
-    if (st[item.inst].status != HELM_ST_ACTIVE) return;
     const LevelDesc L = insts[item.inst].lev[item.level];
     const LevelDesc C = insts[item.inst].lev[item.level + 1];
+    pdl_wait();
+    pdl_trigger();
+    if (st[item.inst].status != HELM_ST_ACTIVE) return;
     const int n = L.n;
     const int ntx = (n + TX - 1) / TX;
     const int nty = (n + TY - 1) / TY;
@@ -308,9 +310,9 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     int ring = 2 * NU - 1;
 #pragma unroll 1
     for (int s = 0; s < NU; ++s) {
-        half_sweep<R, W>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 0);
+        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 0);
         __syncthreads();
-        half_sweep<R, W>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 1);
+        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 1);
         __syncthreads();
     }
     c2* __restrict__ ge = (c2*)L.e;
@@ -326,24 +328,39 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     }
 }
 
-template <int NU> constexpr size_t down_bytes(size_t eb) {
+template <int NU, int TX, int TY> constexpr size_t down_bytes(size_t eb) {
     return 2 * (size_t)(TX + 2 * (2 * NU + 2)) * (TY + 2 * (2 * NU + 2)) * eb;
 }
-template <int NU> constexpr size_t up_bytes(size_t eb) {
+template <int NU, int TX, int TY> constexpr size_t up_bytes(size_t eb) {
     return ((size_t)2 * (TX + 4 * NU) * (TY + 4 * NU) +
             (size_t)((TX + 4 * NU) / 2 + 2) * ((TY + 4 * NU) / 2 + 2)) * eb;
+}
+
+// tile shapes: 0 = 64 x 32, 1 = 32 x 16 (levels <= 511 whose launch would otherwise leave
+// the GPU under-filled: a lone instance's coarser levels still spread over many SMs)
+template <int S> struct Shape;
+template <> struct Shape<0> { static constexpr int X = 64, Y = 32; };
+template <> struct Shape<1> { static constexpr int X = 32, Y = 16; };
+
+template <typename R, int NU, int S>
+cudaError_t set_attrs_s()
+{
+    constexpr int X = Shape<S>::X, Y = Shape<S>::Y;
+    cudaError_t e = cudaFuncSetAttribute(k_down2d<R, NU, X, Y>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)down_bytes<NU, X, Y>(sizeof(R) * 2));
+    if (e != cudaSuccess) return e;
+    if ((e = max_carveout(k_down2d<R, NU, X, Y>)) != cudaSuccess) return e;
+    if ((e = max_carveout(k_up2d<R, NU, X, Y>)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_up2d<R, NU, X, Y>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)up_bytes<NU, X, Y>(sizeof(R) * 2));
 }
 
 template <typename R, int NU>
 cudaError_t set_attrs()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_down2d<R, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)down_bytes<NU>(sizeof(R) * 2));
+    cudaError_t e = set_attrs_s<R, NU, 0>();
     if (e != cudaSuccess) return e;
-    if ((e = max_carveout(k_down2d<R, NU>)) != cudaSuccess) return e;
-    if ((e = max_carveout(k_up2d<R, NU>)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_up2d<R, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)up_bytes<NU>(sizeof(R) * 2));
+    return set_attrs_s<R, NU, 1>();
 }
 
 template <typename R>
@@ -357,33 +374,47 @@ cudaError_t set_all()
     return set_attrs<R, 4>();
 }
 
-template <typename R>
+template <typename R, int NU, int S>
+void down_s(dim3 g, const InstDesc* insts, const InstState* st, const MgItem* items, int zero_mode,
+            cudaStream_t s)
+{
+    constexpr int X = Shape<S>::X, Y = Shape<S>::Y;
+    launch_k(k_down2d<R, NU, X, Y>, g, dim3(NT), down_bytes<NU, X, Y>(sizeof(R) * 2), s, insts, st,
+             items, zero_mode);
+}
+
+template <typename R, int NU, int S>
+void up_s(dim3 g, const InstDesc* insts, const InstState* st, const MgItem* items, cudaStream_t s)
+{
+    constexpr int X = Shape<S>::X, Y = Shape<S>::Y;
+    launch_k(k_up2d<R, NU, X, Y>, g, dim3(NT), up_bytes<NU, X, Y>(sizeof(R) * 2), s, insts, st, items);
+}
+
+template <typename R, int S>
 cudaError_t down(int nu, dim3 g, const InstDesc* insts, const InstState* st, const MgItem* items,
                  int zero_mode, cudaStream_t s)
 {
-    const size_t eb = sizeof(R) * 2;
     switch (nu) {
-    case 0: launch_k(k_down2d<R, 0>, g, dim3(NT), down_bytes<0>(eb), s, insts, st, items, zero_mode); break;
-    case 1: launch_k(k_down2d<R, 1>, g, dim3(NT), down_bytes<1>(eb), s, insts, st, items, zero_mode); break;
-    case 2: launch_k(k_down2d<R, 2>, g, dim3(NT), down_bytes<2>(eb), s, insts, st, items, zero_mode); break;
-    case 3: launch_k(k_down2d<R, 3>, g, dim3(NT), down_bytes<3>(eb), s, insts, st, items, zero_mode); break;
-    case 4: launch_k(k_down2d<R, 4>, g, dim3(NT), down_bytes<4>(eb), s, insts, st, items, zero_mode); break;
+    case 0: down_s<R, 0, S>(g, insts, st, items, zero_mode, s); break;
+    case 1: down_s<R, 1, S>(g, insts, st, items, zero_mode, s); break;
+    case 2: down_s<R, 2, S>(g, insts, st, items, zero_mode, s); break;
+    case 3: down_s<R, 3, S>(g, insts, st, items, zero_mode, s); break;
+    case 4: down_s<R, 4, S>(g, insts, st, items, zero_mode, s); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template <typename R>
+template <typename R, int S>
 cudaError_t up(int nu, dim3 g, const InstDesc* insts, const InstState* st, const MgItem* items,
                cudaStream_t s)
 {
-    const size_t eb = sizeof(R) * 2;
     switch (nu) {
-    case 0: launch_k(k_up2d<R, 0>, g, dim3(NT), up_bytes<0>(eb), s, insts, st, items); break;
-    case 1: launch_k(k_up2d<R, 1>, g, dim3(NT), up_bytes<1>(eb), s, insts, st, items); break;
-    case 2: launch_k(k_up2d<R, 2>, g, dim3(NT), up_bytes<2>(eb), s, insts, st, items); break;
-    case 3: launch_k(k_up2d<R, 3>, g, dim3(NT), up_bytes<3>(eb), s, insts, st, items); break;
-    case 4: launch_k(k_up2d<R, 4>, g, dim3(NT), up_bytes<4>(eb), s, insts, st, items); break;
+    case 0: up_s<R, 0, S>(g, insts, st, items, s); break;
+    case 1: up_s<R, 1, S>(g, insts, st, items, s); break;
+    case 2: up_s<R, 2, S>(g, insts, st, items, s); break;
+    case 3: up_s<R, 3, S>(g, insts, st, items, s); break;
+    case 4: up_s<R, 4, S>(g, insts, st, items, s); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -391,23 +422,37 @@ cudaError_t up(int nu, dim3 g, const InstDesc* insts, const InstState* st, const
 
 }  // namespace
 
-int tiles2d(int n) { return ((n + TX - 1) / TX) * ((n + TY - 1) / TY); }
+int tile_shape2d(int n) { return n <= 511 ? 1 : 0; }
+
+int tiles2d_for(int n, int shape)
+{
+    const int X = shape ? Shape<1>::X : Shape<0>::X;
+    const int Y = shape ? Shape<1>::Y : Shape<0>::Y;
+    return ((n + X - 1) / X) * ((n + Y - 1) / Y);
+}
+
+int tiles2d(int n) { return tiles2d_for(n, tile_shape2d(n)); }
 
 cudaError_t setup_2d(int prec) { return prec == 0 ? set_all<double>() : set_all<float>(); }
 
+// shape: the tile shape of every item of the launch (tile_shape2d of the largest level)
 cudaError_t launch_down2d(int prec, const InstDesc* insts, const InstState* st, const MgItem* items,
-                          int nitems, int max_tiles, int nu1, int zero_mode, cudaStream_t s)
+                          int nitems, int max_tiles, int nu1, int zero_mode, int shape, cudaStream_t s)
 {
     dim3 g(max_tiles, nitems);
-    return prec == 0 ? down<double>(nu1, g, insts, st, items, zero_mode, s)
-                     : down<float>(nu1, g, insts, st, items, zero_mode, s);
+    if (shape) return prec == 0 ? down<double, 1>(nu1, g, insts, st, items, zero_mode, s)
+                                : down<float, 1>(nu1, g, insts, st, items, zero_mode, s);
+    return prec == 0 ? down<double, 0>(nu1, g, insts, st, items, zero_mode, s)
+                     : down<float, 0>(nu1, g, insts, st, items, zero_mode, s);
 }
 
 cudaError_t launch_up2d(int prec, const InstDesc* insts, const InstState* st, const MgItem* items,
-                        int nitems, int max_tiles, int nu2, cudaStream_t s)
+                        int nitems, int max_tiles, int nu2, int shape, cudaStream_t s)
 {
     dim3 g(max_tiles, nitems);
-    return prec == 0 ? up<double>(nu2, g, insts, st, items, s) : up<float>(nu2, g, insts, st, items, s);
+    if (shape) return prec == 0 ? up<double, 1>(nu2, g, insts, st, items, s)
+                                : up<float, 1>(nu2, g, insts, st, items, s);
+    return prec == 0 ? up<double, 0>(nu2, g, insts, st, items, s) : up<float, 0>(nu2, g, insts, st, items, s);
 }
 
 }  // namespace helm
