@@ -41,13 +41,15 @@ thread_local char g_errbuf[256] = "";
         }                                                                                 \
     } while (0)
 
-int tail_n(int D) { return D == 2 ? TAIL_N_2D : TAIL_N_3D; }
+int tail_n(int D, int prec) { return tail_top(D, prec == HELM_PREC_FP64); }
 int elem_bytes(int prec) { return prec == HELM_PREC_FP64 ? 16 : 8; }
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool is_pow2m1(int n) { return n >= 1 && ((n + 1) & n) == 0; }
 
 int res_rows_per_tile(int D) { return residual_tile_rows(D); }
+// residual tiles along z: 3D tiles march over residual_tile_planes(3) planes; 2D has one
+int res_tz(int D, int n) { return D == 3 ? (n + residual_tile_planes(3) - 1) / residual_tile_planes(3) : 1; }
 
 // Fill the geometry part of a descriptor and return the workspace bytes it needs (the
 // level arrays, the second iterate buffer and the residual partials).  With base != NULL
@@ -62,7 +64,7 @@ size_t layout(InstDesc& d, int D, int n, double h, double k, int prec, char* bas
     d.cdiag = d.k2 - 2.0 * D * d.ih2;
     int nl = 0, lt = -1;
     for (int m = n; m >= 1 && nl < HELM_MAXLEV; m = (m - 1) / 2) {
-        if (lt < 0 && m <= tail_n(D)) lt = nl;
+        if (lt < 0 && m <= tail_n(D, prec)) lt = nl;
         d.lev[nl].n = m;
         ++nl;
     }
@@ -97,7 +99,7 @@ size_t layout(InstDesc& d, int D, int n, double h, double k, int prec, char* bas
     off += ubytes;
     d.res_tx = (n + 31) / 32;
     d.res_ty = (n + res_rows_per_tile(D) - 1) / res_rows_per_tile(D);
-    d.nres_blocks = d.res_tx * d.res_ty * ((D == 3) ? n : 1);
+    d.nres_blocks = d.res_tx * d.res_ty * res_tz(D, n);
     if (base) d.part = (double*)(base + off);
     off += align256((size_t)2 * d.nres_blocks * sizeof(double));
     if (base) d.count = (unsigned int*)(base + off);
@@ -301,7 +303,7 @@ struct Engine {
         for (int i = 0; i < cap; ++i) {
             if (!slots[i]) continue;
             const InstDesc& d = slots[i]->d;
-            const int tz = (D == 3) ? d.n : 1;
+            const int tz = res_tz(D, d.n);
             for (int z = 0; z < tz; ++z)
                 for (int y = 0; y < d.res_ty; ++y)
                     for (int x = 0; x < d.res_tx; ++x) res.push_back(ResItem{i, x, y, z});
@@ -574,7 +576,7 @@ helm_status alloc_instance(Instance& in, int D, int n, double h, double k, int p
     HELM_CK(cudaMemsetAsync(in.ws, 0, in.ws_bytes, s));
     // residual tiles of this instance (for its initial residual)
     std::vector<ResItem> r;
-    const int tz = (D == 3) ? n : 1;
+    const int tz = res_tz(D, n);
     for (int z = 0; z < tz; ++z)
         for (int y = 0; y < in.d.res_ty; ++y)
             for (int x = 0; x < in.d.res_tx; ++x) r.push_back(ResItem{0, x, y, z});

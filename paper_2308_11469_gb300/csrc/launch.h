@@ -9,6 +9,13 @@ namespace helm {
 // Tail-level bounds: levels with n <= these are solved inside one CTA in shared memory.
 constexpr int TAIL_N_2D = 63;
 constexpr int TAIL_N_3D = 15;
+// FP64 keeps fewer levels in the one-CTA tail: on GB300 the FP64 rate of a single SM is
+// small, so FP64 coarse levels run faster spread over the GPU.
+inline int tail_top(int D, int prec_is_fp64)
+{
+    if (prec_is_fp64) return D == 2 ? 31 : 7;
+    return D == 2 ? TAIL_N_2D : TAIL_N_3D;
+}
 
 // ---- multigrid (vcycle.cu); prec: 0 = double, 1 = float ----
 // mode 0: plain half-sweep; modes 1/2: first half-sweep of a pre-smoothing whose
@@ -61,6 +68,7 @@ cudaError_t setup_2d(int prec);
 cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* st,
                             const ResItem* items, int nitems, int mode, cudaStream_t s);
 int residual_tile_rows(int D);
+int residual_tile_planes(int D);
 int residual_tile_cols(int D);
 // Any instance still iterating?  Counts the step, sets the while-loop condition.
 cudaError_t launch_check(const InstState* st, int ninst, int* ctrl, int use_cond,

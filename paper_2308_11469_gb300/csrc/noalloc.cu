@@ -95,7 +95,7 @@ extern "C" helm_status poisson_vcycle_noalloc(int ndim, int n, double h, int pre
     const int D = ndim;
     const int pr = (prec == HELM_PREC_FP64) ? 0 : 1;
     const size_t eb = pr == 0 ? 16 : 8;
-    const int tail_top = D == 2 ? TAIL_N_2D : TAIL_N_3D;
+    const int ttop = tail_top(D, pr == 0);
     const bool fused = (D == 2 && nu1 <= 4 && nu2 <= 4);
 
     InstDesc d;
@@ -105,7 +105,7 @@ extern "C" helm_status poisson_vcycle_noalloc(int ndim, int n, double h, int pre
     d.h = h;
     int nl = 0, lt = -1;
     for (int m = n; m >= 1 && nl < HELM_MAXLEV; m = (m - 1) / 2) {
-        if (lt < 0 && m <= tail_top) lt = nl;
+        if (lt < 0 && m <= ttop) lt = nl;
         d.lev[nl].n = m;
         ++nl;
     }

@@ -147,28 +147,21 @@ __device__ void tile_done(const InstDesc& I, InstState* stp, int tile, double a,
 constexpr int T2 = 32;
 
 template <typename R, int MODE>
-__global__ void __launch_bounds__(NTH)
-k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
-             const ResItem* __restrict__ items)
+__device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ insts,
+                                                InstState* __restrict__ st, const ResItem item,
+                                                double2* U)
 {
     typedef typename C2<R>::T c2;
-    __shared__ double2 U[(T2 + 2) * (T2 + 2)];
-    // descriptors are host-written: read them before waiting for the predecessor kernel
-    const ResItem item = items[blockIdx.x];
     const InstDesc& I = insts[item.inst];
-    const int n = I.n;
-    const int S = n + 2;
-    const double2* u0 = I.u[0];
-    const double2* u1 = I.u[1];
-    const double2* __restrict__ f = I.f;
-    const LevelDesc L0 = I.lev[0];
-    pdl_wait();
-    pdl_trigger();
     InstState* stp = st + item.inst;
     const InstState s = *stp;
-    if (s.status != HELM_ST_ACTIVE) return;
-    const double2* __restrict__ uin = (s.it & 1) ? u1 : u0;
-    double2* __restrict__ uout = (double2*)((s.it & 1) ? u0 : u1);
+    if (s.status != HELM_ST_ACTIVE) return;     // uniform over the CTA
+    const int n = I.n;
+    const int S = n + 2;
+    const double2* __restrict__ uin = I.u[s.it & 1];
+    double2* __restrict__ uout = I.u[(s.it + 1) & 1];
+    const double2* __restrict__ f = I.f;
+    const LevelDesc L0 = I.lev[0];
     const c2* __restrict__ e = (const c2*)L0.e;
     c2* __restrict__ rhs = (c2*)L0.rhs;
     const int P = L0.pitch;
@@ -235,83 +228,149 @@ k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
               MODE == 0 ? b2 : (double)emax2, MODE);
 }
 
-// ---------------------------------------------------------------------------
-// 3D: 32 x 16 x 1 tiles, direct loads (neighbour reuse through L1)
-// ---------------------------------------------------------------------------
+// Grid-stride over the tiles of every instance (one tile per CTA when the grid covers
+// them all).
 template <typename R, int MODE>
 __global__ void __launch_bounds__(NTH)
-k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
-             const ResItem* __restrict__ items)
+k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
+             const ResItem* __restrict__ items, int nitems)
 {
+    __shared__ double2 U[(T2 + 2) * (T2 + 2)];
     pdl_wait();
     pdl_trigger();
+    for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
+        residual2d_tile<R, MODE>(insts, st, items[t], U);
+        __syncthreads();                          // U is restaged by the next tile
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3D: 32 x 8 columns marching over 16 z-planes; u_{N+1} staged once per node in a
+// three-plane ring of shared memory (1-node halo in x and y)
+// ---------------------------------------------------------------------------
+constexpr int T3X = 32, T3Y = 8, T3Z = 16;
+constexpr int P3 = (T3X + 2) * (T3Y + 2);
+
+template <typename R, int MODE>
+__device__ __forceinline__ R stage_plane3d(double2* Up, const double2* __restrict__ uin,
+                                           const typename C2<R>::T* __restrict__ e, int n, long S,
+                                           long SP, long P, long PL, int x0, int y0, int gz,
+                                           bool own)
+{
     typedef typename C2<R>::T c2;
-    const ResItem item = items[blockIdx.x];
-    InstState* stp = st + item.inst;
-    const InstState s = *stp;
-    if (s.status != HELM_ST_ACTIVE) return;
+    R emax2 = 0;
+#pragma unroll
+    for (int it = 0; it < (P3 + NTH - 1) / NTH; ++it) {
+        const int q = threadIdx.x + it * NTH;
+        if (q >= P3) break;
+        const int lx = q % (T3X + 2), ly = q / (T3X + 2);
+        const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+        double2 v = make_double2(0.0, 0.0);
+        if (gx <= n + 1 && gy <= n + 1) {
+            v = uin[(long)gz * SP + (long)gy * S + gx];
+            if (MODE == 1 && gx >= 1 && gx <= n && gy >= 1 && gy <= n && gz >= 1 && gz <= n) {
+                const c2 ev = e[(long)gz * PL + (long)gy * P + gx];
+                v.x += Inner<R>::widen(ev.x);
+                v.y += Inner<R>::widen(ev.y);
+                if (own && lx >= 1 && lx <= T3X && ly >= 1 && ly <= T3Y)
+                    emax2 = fmax(emax2, ev.x * ev.x + ev.y * ev.y);
+            }
+        }
+        Up[q] = v;
+    }
+    return emax2;
+}
+
+template <typename R, int MODE>
+__device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ insts,
+                                                InstState* __restrict__ st, const ResItem item,
+                                                double2 (*U)[P3])
+{
+    typedef typename C2<R>::T c2;
     const InstDesc& I = insts[item.inst];
     const int n = I.n;
     const long S = n + 2;
     const long SP = S * S;
-    const double2* __restrict__ uin = I.u[s.it & 1];
-    double2* __restrict__ uout = I.u[(s.it + 1) & 1];
+    const double2* u0 = I.u[0];
+    const double2* u1 = I.u[1];
     const double2* __restrict__ f = I.f;
     const LevelDesc L0 = I.lev[0];
+    InstState* stp = st + item.inst;
+    const InstState s = *stp;
+    if (s.status != HELM_ST_ACTIVE) return;
+    const double2* __restrict__ uin = (s.it & 1) ? u1 : u0;
+    double2* __restrict__ uout = (double2*)((s.it & 1) ? u0 : u1);
     const c2* __restrict__ e = (const c2*)L0.e;
     c2* __restrict__ rhs = (c2*)L0.rhs;
     const long P = L0.pitch;
     const long PL = (long)L0.pitch * L0.rows;
     const double mih2 = -I.ih2;
     const double mcdiag = -I.cdiag;
-    const int x = item.tx * 32 + (threadIdx.x & 31) + 1;
-    const int z = item.tz + 1;
+    const int x0 = 1 + item.tx * T3X, y0 = 1 + item.ty * T3Y, z0 = 1 + item.tz * T3Z;
+    const int z1 = min(z0 + T3Z - 1, n);
+    const int lx = (threadIdx.x & 31) + 1, ly = (threadIdx.x >> 5) + 1;
+    const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+    const bool live = gx <= n && gy <= n;
+    const int o = ly * (T3X + 2) + lx;
     R r2 = 0, emax2 = 0;
     double r2d = 0.0, b2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int y = item.ty * 16 + k * 8 + (threadIdx.x >> 5) + 1;
-        if (x > n || y > n) continue;
-        const long ou = (long)z * SP + (long)y * S + x;
-        const long oe = (long)z * PL + (long)y * P + x;
-        double2 c = uin[ou];
-        double2 w = uin[ou - 1], ea = uin[ou + 1], so = uin[ou - S], no = uin[ou + S];
-        double2 dn = uin[ou - SP], up = uin[ou + SP];
-        if (MODE == 1) {
-            const c2 e0 = e[oe];
-            const c2 e1 = e[oe - 1], e2 = e[oe + 1], e3 = e[oe - P], e4 = e[oe + P];
-            const c2 e5 = e[oe - PL], e6 = e[oe + PL];
-            c.x += Inner<R>::widen(e0.x);  c.y += Inner<R>::widen(e0.y);
-            w.x += Inner<R>::widen(e1.x);  w.y += Inner<R>::widen(e1.y);
-            ea.x += Inner<R>::widen(e2.x); ea.y += Inner<R>::widen(e2.y);
-            so.x += Inner<R>::widen(e3.x); so.y += Inner<R>::widen(e3.y);
-            no.x += Inner<R>::widen(e4.x); no.y += Inner<R>::widen(e4.y);
-            dn.x += Inner<R>::widen(e5.x); dn.y += Inner<R>::widen(e5.y);
-            up.x += Inner<R>::widen(e6.x); up.y += Inner<R>::widen(e6.y);
-            uout[ou] = c;
-            emax2 = fmax(emax2, e0.x * e0.x + e0.y * e0.y);
+    stage_plane3d<R, MODE>(U[0], uin, e, n, S, SP, P, PL, x0, y0, z0 - 1, false);
+    emax2 = fmax(emax2, stage_plane3d<R, MODE>(U[1], uin, e, n, S, SP, P, PL, x0, y0, z0, true));
+    int sp = 0, sc = 1, sn = 2;                 // ring slots of planes z-1, z, z+1
+    for (int z = z0; z <= z1; ++z) {
+        const R em = stage_plane3d<R, MODE>(U[sn], uin, e, n, S, SP, P, PL, x0, y0, z + 1, z + 1 <= z1);
+        emax2 = fmax(emax2, em);
+        __syncthreads();
+        if (live) {
+            const double2* Uc = U[sc];
+            const double2 c = Uc[o];
+            const double2 w = Uc[o - 1], ea = Uc[o + 1], so = Uc[o - (T3X + 2)], no = Uc[o + (T3X + 2)];
+            const double2 dn = U[sp][o], up = U[sn][o];
+            const long ou = (long)z * SP + (long)gy * S + gx;
+            const long oe = (long)z * PL + (long)gy * P + gx;
+            if (MODE == 1) uout[ou] = c;
+            const double2 fv = f[((long)(z - 1) * n + (gy - 1)) * n + (gx - 1)];
+            double2 r;
+            r.x = fma(((w.x + ea.x) + (so.x + no.x)) + (dn.x + up.x), mih2, fma(c.x, mcdiag, fv.x));
+            r.y = fma(((w.y + ea.y) + (so.y + no.y)) + (dn.y + up.y), mih2, fma(c.y, mcdiag, fv.y));
+            const c2 ri = Inner<R>::from(r);
+            rhs[oe] = ri;
+            if (MODE == 1) {
+                r2 += ri.x * ri.x + ri.y * ri.y;
+            } else {
+                // once per solve, in FP64: ||r_0||^2 and ||b||^2 (same operations as r)
+                r2d += r.x * r.x + r.y * r.y;
+                const double2 zz = make_double2(0.0, 0.0);
+                const double2 w1 = (gx == 1) ? w : zz, w2 = (gx == n) ? ea : zz;
+                const double2 w3 = (gy == 1) ? so : zz, w4 = (gy == n) ? no : zz;
+                const double2 w5 = (z == 1) ? dn : zz, w6 = (z == n) ? up : zz;
+                const double bx = fma(((w1.x + w2.x) + (w3.x + w4.x)) + (w5.x + w6.x), mih2, fma(0.0, mcdiag, fv.x));
+                const double by = fma(((w1.y + w2.y) + (w3.y + w4.y)) + (w5.y + w6.y), mih2, fma(0.0, mcdiag, fv.y));
+                b2 += bx * bx + by * by;
+            }
         }
-        const double2 fv = f[((long)(z - 1) * n + (y - 1)) * n + (x - 1)];
-        double2 r;
-        r.x = fma(((w.x + ea.x) + (so.x + no.x)) + (dn.x + up.x), mih2, fma(c.x, mcdiag, fv.x));
-        r.y = fma(((w.y + ea.y) + (so.y + no.y)) + (dn.y + up.y), mih2, fma(c.y, mcdiag, fv.y));
-        const c2 ri = Inner<R>::from(r);
-        rhs[oe] = ri;
-        if (MODE == 1) {
-            r2 += ri.x * ri.x + ri.y * ri.y;
-        } else {
-            r2d += r.x * r.x + r.y * r.y;
-            const double2 zz = make_double2(0.0, 0.0);
-            const double2 w1 = (x == 1) ? w : zz, w2 = (x == n) ? ea : zz;
-            const double2 w3 = (y == 1) ? so : zz, w4 = (y == n) ? no : zz;
-            const double2 w5 = (z == 1) ? dn : zz, w6 = (z == n) ? up : zz;
-            const double bx = fma(((w1.x + w2.x) + (w3.x + w4.x)) + (w5.x + w6.x), mih2, fma(0.0, mcdiag, fv.x));
-            const double by = fma(((w1.y + w2.y) + (w3.y + w4.y)) + (w5.y + w6.y), mih2, fma(0.0, mcdiag, fv.y));
-            b2 += bx * bx + by * by;
-        }
+        __syncthreads();                        // the oldest plane is overwritten next
+        const int t = sp;
+        sp = sc;
+        sc = sn;
+        sn = t;
     }
     const int tile = (item.tz * I.res_ty + item.ty) * I.res_tx + item.tx;
     tile_done(I, stp, tile, MODE == 0 ? r2d : (double)r2, MODE == 0 ? b2 : (double)emax2, MODE);
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(NTH)
+k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
+             const ResItem* __restrict__ items, int nitems)
+{
+    __shared__ double2 U[3][P3];
+    pdl_wait();
+    pdl_trigger();
+    for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
+        residual3d_tile<R, MODE>(insts, st, items[t], U);
+        __syncthreads();
+    }
 }
 
 // One CTA: is any instance still iterating?  Counts the step and sets the loop condition.
@@ -455,7 +514,8 @@ inline int blocks_for(long work) {
 
 }  // namespace
 
-int residual_tile_rows(int D) { return D == 2 ? T2 : 16; }
+int residual_tile_rows(int D) { return D == 2 ? T2 : T3Y; }
+int residual_tile_planes(int D) { return D == 2 ? 1 : T3Z; }
 
 cudaError_t run_fp_bits_check(int count, unsigned long long seed, unsigned long long* bad_host)
 {
@@ -471,13 +531,19 @@ cudaError_t run_fp_bits_check(int count, unsigned long long seed, unsigned long 
 }
 int residual_tile_cols(int D) { return 32; }
 
+static int g_res_grid = 152 * 5;               // SMs x resident residual CTAs (set up below)
+
 cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* st,
                             const ResItem* items, int nitems, int mode, cudaStream_t s)
 {
     if (nitems <= 0) return cudaSuccess;
-#define HELM_RES(K, RR)                                                                   \
-    (mode ? launch_k(K<RR, 1>, dim3(nitems), dim3(NTH), 0, s, insts, st, items)             \
-          : launch_k(K<RR, 0>, dim3(nitems), dim3(NTH), 0, s, insts, st, items))
+    // one CTA per tile: measured faster than a persistent grid (SMs x resident CTAs
+    // striding over the tiles) for both the 2D tiles and the 3D columns
+    const int grid = nitems;
+    (void)g_res_grid;
+#define HELM_RES(K, RR)                                                                        \
+    (mode ? launch_k(K<RR, 1>, dim3(grid), dim3(NTH), 0, s, insts, st, items, nitems)           \
+          : launch_k(K<RR, 0>, dim3(grid), dim3(NTH), 0, s, insts, st, items, nitems))
     if (D == 2 && prec == 0) HELM_RES(k_residual2d, double);
     else if (D == 2) HELM_RES(k_residual2d, float);
     else if (prec == 0) HELM_RES(k_residual3d, double);
@@ -489,6 +555,12 @@ cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* s
 cudaError_t setup_outer()
 {
     cudaError_t e;
+    int dev = 0, sms = 0, per = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_residual2d<float, 1>, NTH, 0)) != cudaSuccess)
+        return e;
+    if (sms > 0 && per > 0) g_res_grid = sms * per;
     if ((e = max_carveout(k_residual2d<float, 0>)) != cudaSuccess) return e;
     if ((e = max_carveout(k_residual2d<float, 1>)) != cudaSuccess) return e;
     if ((e = max_carveout(k_residual2d<double, 0>)) != cudaSuccess) return e;
