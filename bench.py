@@ -55,10 +55,8 @@ def _peaks():
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2308_11469_gb300 import dist as wsd
+    return wsd.world()
 
 
 class ClockSampler:
@@ -213,12 +211,14 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    from paper_2308_11469_gb300 import dist as wsd
+
     def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return wsd.max_over_ranks(x, dist, dev)
+
+    def job_throughput(units: float, ms: float) -> float:
+        # units summed over the ranks / the slowest rank's time
+        return wsd.throughput(units, ms / 1e3, dist, dev)
 
     problems = [inputs.gaussian_cavity_2d(k) for k in KS]
     n = N_GRID
@@ -287,7 +287,7 @@ def main():
     mixed_step()
     launches_per_step = B.helm_launch_count() - l1
     total_ms = max_over_ranks(float(np.sum(t_mixed)))
-    value = ws * len(KS) * args.steps / (total_ms / 1e3)
+    value = job_throughput(len(KS) * args.steps, float(np.sum(t_mixed)))
     mixed_u = [u.cpu().numpy() for u in U]
     mixed_iters = [r[1] for r in res_mixed]
     mixed_status = [B.helm_status_str(r[0]) for r in res_mixed]
@@ -298,7 +298,8 @@ def main():
     if not args.no_fp64:
         t_fp64, res_fp64 = timed(fp64_step, max(2, args.steps // 2), min(args.warmup, 2))
         tot64 = max_over_ranks(float(np.sum(t_fp64)))
-        fp64 = {"value": ws * len(KS) * len(t_fp64) / (tot64 / 1e3), "unit": "solves/s",
+        fp64 = {"value": job_throughput(len(KS) * len(t_fp64), float(np.sum(t_fp64))),
+                "unit": "solves/s",
                 "ms_per_step": tot64 / len(t_fp64),
                 "iters": [r[1] for r in res_fp64],
                 "status": [B.helm_status_str(r[0]) for r in res_fp64]}
@@ -322,10 +323,10 @@ def main():
         return out
 
     t_e2e, _ = timed(e2e_step, max(2, args.steps // 2), 1)
-    tot_e2e = max_over_ranks(float(np.sum(t_e2e)))
+    e2e_value = job_throughput(len(KS) * len(t_e2e), float(np.sum(t_e2e)))
     h2d = sum(f.numel() * 16 + g.numel() * 16 for f, g in zip(Fh, Gh))
     d2h = sum(u.numel() * 16 for u in Uh)
-    e2e = {"value": ws * len(KS) * len(t_e2e) / (tot_e2e / 1e3), "unit": "solves/s",
+    e2e = {"value": e2e_value, "unit": "solves/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     # ---- per-kernel replay of one step (events around every launch) ----

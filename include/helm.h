@@ -113,6 +113,13 @@ HELM_API helm_status helm_plan_destroy(helm_plan* plan);
 HELM_API helm_status helm_plan_info(const helm_plan* plan, double* lambda_min, double* k_max,
                            double* rho_pred, size_t* workspace_bytes);
 
+/* Shape of the plan's multigrid hierarchy (this project's inner solver; the paper leaves
+ * the Poisson solver open, Section 3): *tail_n = the grid size from which one CTA per
+ * instance runs every coarser level in shared memory; *exact_n = the size of the level
+ * that is solved exactly in the sine basis instead of being cycled (0: every level down
+ * to n = 1 is cycled).  Either pointer may be NULL; HELM_EINVAL on a NULL plan. */
+HELM_API helm_status helm_plan_coarse(const helm_plan* plan, int* tail_n, int* exact_n);
+
 /* Inner-solve schedule: V(nu1, nu2) cycles, `cycles` V-cycles per outer step.
  * Defaults: 2D (2, 2, 1), 3D (2, 2, 1).  nu1, nu2 in [0, 8] with nu1 + nu2 >= 1,
  * cycles in [1, 16]. */

@@ -23,7 +23,10 @@ Components (levels have n_l = 2^(m-l) - 1 interior nodes per axis, h_l = 2^l h):
 * coarsest level n = 1: the exact solve e = -h^2 r / (2D);
 * V(nu1, nu2)-cycle: nu1 x (red, black) half-sweeps, residual, restriction, recursive
   cycle on the coarse level from a zero guess, prolongation + correction,
-  nu2 x (red, black) half-sweeps.
+  nu2 x (red, black) half-sweeps;
+* optionally (``exact_n``) a direct coarse-grid solver: the level with n == exact_n is
+  not cycled but solved exactly (sine-basis solve of Delta_h e = r, zero walls), as the
+  CUDA library does for its 2D complex64 hierarchies.
 """
 from __future__ import annotations
 
@@ -115,10 +118,15 @@ def coarse_solve(E: np.ndarray, r: np.ndarray, h: float) -> None:
     E[(slice(1, 2),) * D] = -(h * h) * r / (2.0 * D)
 
 
-def vcycle(E: np.ndarray, r: np.ndarray, h: float, nu1: int = 2, nu2: int = 2) -> None:
-    """One V(nu1, nu2)-cycle on the padded iterate E (in place)."""
+def vcycle(E: np.ndarray, r: np.ndarray, h: float, nu1: int = 2, nu2: int = 2,
+           exact_n: int | None = None) -> None:
+    """One V(nu1, nu2)-cycle on the padded iterate E (in place); a level with
+    n == exact_n is solved exactly instead (whatever E held there)."""
     D = E.ndim
     n = E.shape[0] - 2
+    if exact_n is not None and n == exact_n:
+        E[(slice(1, -1),) * D] = fd.dst_poisson(r, h)
+        return
     if n == 1:
         coarse_solve(E, r, h)
         return
@@ -127,7 +135,7 @@ def vcycle(E: np.ndarray, r: np.ndarray, h: float, nu1: int = 2, nu2: int = 2) -
     rc = restrict_fw(poisson_residual(E, r, h))
     nc = rc.shape[0]
     Ec = np.zeros((nc + 2,) * D, dtype=E.dtype)
-    vcycle(Ec, rc, 2.0 * h, nu1, nu2)
+    vcycle(Ec, rc, 2.0 * h, nu1, nu2, exact_n)
     prolong_add(E, Ec)
     for _ in range(nu2):
         rbgs_sweep(E, r, h)

@@ -43,6 +43,7 @@ _SIGS = {
     "helm_plan_info": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.POINTER(C.c_size_t)]),
     "helm_plan_set_cycle": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
+    "helm_plan_coarse": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "helm_solve": (C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int),
                              C.POINTER(C.c_double)]),
     "helm_solve_ex": (C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int),
@@ -193,6 +194,14 @@ def helm_plan_info(plan: _Plan):
     _check(load().helm_plan_info(plan.handle, C.byref(lm), C.byref(km), C.byref(rho), C.byref(ws)),
            "helm_plan_info")
     return lm.value, km.value, rho.value, ws.value
+
+
+def helm_plan_coarse(plan: _Plan):
+    """(tail_n, exact_n): where the one-CTA coarse tail starts, and the level it solves
+    exactly in the sine basis (0: none)."""
+    t, x = C.c_int(), C.c_int()
+    _check(load().helm_plan_coarse(plan.handle, C.byref(t), C.byref(x)), "helm_plan_coarse")
+    return t.value, x.value
 
 
 def helm_plan_set_cycle(plan: _Plan, nu1: int, nu2: int, cycles: int = 1) -> None:

@@ -134,7 +134,7 @@ struct Engine {
     std::vector<Instance*> slots;              // nullptr = free
     InstDesc* d_desc = nullptr;
     InstState* d_state = nullptr;
-    int* d_ctrl = nullptr;                     // [0] steps done, [1] step budget, [2] go
+    int* d_ctrl = nullptr;                     // [0] steps done, [1] step budget, [2] go, [3] arrivals
     int* h_ctrl = nullptr;                     // pinned mirror
     InstState* h_state = nullptr;              // pinned mirror (cap entries)
     MgItem* d_mg = nullptr;
@@ -360,8 +360,11 @@ struct Engine {
         };
         step.clear();
         for (int c = 0; c < cycles; ++c) vcycle(step, c == 0);
-        step.push_back({LaunchRec::RESID, 0, nres, 0, 0, 1, b_res});
-        step.push_back({LaunchRec::CHECK, 0, cap, 0, 0, 1, 0.0});
+        // the residual launch also ends the step (its last instance to finish sets the
+        // loop condition), so a step has no separate check launch
+        int nocc = 0;
+        for (int i = 0; i < cap; ++i) nocc += slots[i] ? 1 : 0;
+        step.push_back({LaunchRec::RESID, 0, nres, nocc, 1, 1, b_res});
         vcyc_plain.clear();
         vcycle(vcyc_plain, false);
         return HELM_OK;
@@ -433,7 +436,11 @@ struct Engine {
                 e = launch_up2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu2, L.color, s);
                 break;
             case LaunchRec::RESID:
-                e = launch_residual(D, prec, d_desc, d_state, d_res + L.off, L.cnt, L.mode, s);
+                if (L.color)      // folded step control: L.work instances, cap statuses
+                    e = launch_residual(D, prec, d_desc, d_state, d_res + L.off, L.cnt, L.mode, s,
+                                        d_ctrl, cap, L.work, use_cond ? 1 : 0, (unsigned long long)cond);
+                else
+                    e = launch_residual(D, prec, d_desc, d_state, d_res + L.off, L.cnt, L.mode, s);
                 break;
             case LaunchRec::CHECK:
                 e = launch_check(d_state, L.cnt, d_ctrl, use_cond ? 1 : 0,
@@ -544,7 +551,8 @@ struct Engine {
         h_ctrl[0] = 0;
         h_ctrl[1] = budget > 0 ? budget : INT_MAX;
         h_ctrl[2] = 1;
-        HELM_CK(cudaMemcpyAsync(d_ctrl, h_ctrl, 3 * sizeof(int), cudaMemcpyHostToDevice, s));
+        h_ctrl[3] = 0;
+        HELM_CK(cudaMemcpyAsync(d_ctrl, h_ctrl, 4 * sizeof(int), cudaMemcpyHostToDevice, s));
         HELM_CK(cudaGraphLaunch(exec, s));
         HELM_CK(cudaMemcpyAsync(h_ctrl, d_ctrl, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
         HELM_CK(cudaMemcpyAsync(h_state, d_state, sizeof(InstState) * cap, cudaMemcpyDeviceToHost, s));
@@ -751,6 +759,16 @@ helm_status helm_plan_info(const helm_plan* p, double* lmin, double* kmax, doubl
     if (kmax) *kmax = std::sqrt(l);
     if (rho) *rho = p->k * p->k / l;
     if (ws) *ws = p->inst.ws_bytes + (2 * (size_t)p->inst.hist_cap + 1) * sizeof(double);
+    return HELM_OK;
+}
+
+helm_status helm_plan_coarse(const helm_plan* p, int* tail_n, int* exact_n)
+{
+    if (!p) return HELM_EINVAL;
+    const int tn = p->inst.d.lev[p->inst.d.ltail].n;
+    const int xn = tail_exact_n(p->D, p->prec == HELM_PREC_FP64 ? 0 : 1);
+    if (tail_n) *tail_n = tn;
+    if (exact_n) *exact_n = (xn > 0 && tn >= xn) ? xn : 0;
     return HELM_OK;
 }
 
@@ -1138,7 +1156,8 @@ helm_status helm_batch_step(helm_batch* b, int max_steps)
         E->h_ctrl[0] = 0;
         E->h_ctrl[1] = max_steps > 0 ? max_steps : INT_MAX;
         E->h_ctrl[2] = 1;
-        HELM_CK(cudaMemcpyAsync(E->d_ctrl, E->h_ctrl, 3 * sizeof(int), cudaMemcpyHostToDevice, es));
+        E->h_ctrl[3] = 0;
+        HELM_CK(cudaMemcpyAsync(E->d_ctrl, E->h_ctrl, 4 * sizeof(int), cudaMemcpyHostToDevice, es));
         if (direct) {
             for (int k = 0; k < max_steps; ++k) {
                 st = E->enqueue(E->step, es, false);
@@ -1183,7 +1202,8 @@ helm_status helm_batch_profile(helm_batch* b, int max_steps, uint64_t* launches,
         E->h_ctrl[0] = 0;
         E->h_ctrl[1] = INT_MAX;
         E->h_ctrl[2] = 1;
-        HELM_CK(cudaMemcpyAsync(E->d_ctrl, E->h_ctrl, 3 * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+        E->h_ctrl[3] = 0;
+        HELM_CK(cudaMemcpyAsync(E->d_ctrl, E->h_ctrl, 4 * sizeof(int), cudaMemcpyHostToDevice, b->stream));
         HELM_CK(cudaMemcpyAsync(E->h_state, E->d_state, sizeof(InstState) * E->cap,
                                 cudaMemcpyDeviceToHost, b->stream));
         HELM_CK(cudaStreamSynchronize(b->stream));

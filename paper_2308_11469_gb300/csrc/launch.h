@@ -40,6 +40,8 @@ cudaError_t launch_tail(int D, int prec, int n0, const InstDesc* insts, const In
                         const MgItem* items, int nitems, int nu1, int nu2, int load_e,
                         cudaStream_t s);
 size_t tail_smem_bytes(int D, int prec, int n);
+// size of the level the tail solves exactly instead of cycling (0: none); prec 0 = FP64
+int tail_exact_n(int D, int prec);
 // raise the tail kernel's dynamic shared-memory limit (once, before any capture)
 cudaError_t setup_tail(int D, int prec);
 // shared-memory carve-out preferences of the generic and outer kernels
@@ -65,8 +67,13 @@ cudaError_t setup_2d(int prec);
 // mode 0: r_0 from u[it&1]; mode 1: u[(it+1)&1] = u[it&1] + e_0, then r from it.
 // Writes r into level-0 rhs (inner precision) and per-tile partials; the last tile of
 // each instance forms relres, records the history and applies the status rule.
+// ctrl != nullptr folds the step control (k_check) into the launch: the last of the
+// launch's `ninst` instances to finish its residual scans `nscan` statuses, counts the
+// step and sets the WHILE node's condition (use_cond).
 cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* st,
-                            const ResItem* items, int nitems, int mode, cudaStream_t s);
+                            const ResItem* items, int nitems, int mode, cudaStream_t s,
+                            int* ctrl = nullptr, int nscan = 0, int ninst = 0, int use_cond = 0,
+                            unsigned long long cond_handle = 0);
 int residual_tile_rows(int D);
 int residual_tile_planes(int D);
 int residual_tile_cols(int D);

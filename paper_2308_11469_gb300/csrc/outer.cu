@@ -111,8 +111,59 @@ __device__ __forceinline__ void block_reduce(double& a, double& m, double* sa, d
     }
 }
 
+// End of an outer step, run by one whole CTA once every instance's status is final: is
+// any instance still iterating?  Counts the step, applies the step budget of this launch
+// and sets the loop condition of the graph's WHILE node.
+__device__ void step_end(const InstState* st, int nscan, int* ctrl, int use_cond,
+                         unsigned long long cond_handle)
+{
+    __shared__ int any_active;
+    if (threadIdx.x == 0) any_active = 0;
+    __syncthreads();
+    int a = 0;
+    for (int i = threadIdx.x; i < nscan; i += blockDim.x)
+        a |= (__ldcg(&st[i].status) == HELM_ST_ACTIVE);
+    if (a) atomicOr(&any_active, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int go = any_active;
+        const int done = ctrl[0] + 1;
+        ctrl[0] = done;
+        if (done >= ctrl[1]) go = 0;          // step budget of this launch
+        ctrl[2] = go;
+        if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, go ? 1u : 0u);
+    }
+}
+
+// Step control folded into the residual launch (ctrl == nullptr: not folded).  Every
+// instance of the launch arrives once -- an iterating instance from the CTA that
+// finalised its status, a finished one from the CTA of its first tile -- and the last
+// arrival (launch-wide ticket ctrl[3]) ends the step.
+struct StepCtl {
+    int* ctrl;
+    int nscan;                  // status entries to scan (descriptor slots)
+    int ninst;                  // instances with tiles in this launch
+    int use_cond;
+    unsigned long long cond;
+};
+
+__device__ void step_arrive(const InstState* st, const StepCtl& c)
+{
+    __shared__ int last_arrival;
+    if (threadIdx.x == 0) {
+        __threadfence();                      // this instance's status before the ticket
+        last_arrival = (atomicAdd(&c.ctrl[3], 1) == c.ninst - 1);
+    }
+    __syncthreads();
+    if (!last_arrival) return;
+    __threadfence();
+    step_end(st, c.nscan, c.ctrl, c.use_cond, c.cond);
+    if (threadIdx.x == 0) c.ctrl[3] = 0;
+}
+
 // Write this tile's partials; the last tile of the instance reduces them all.
-__device__ void tile_done(const InstDesc& I, InstState* stp, int tile, double a, double m, int mode)
+__device__ void tile_done(const InstDesc& I, InstState* stp, int tile, double a, double m, int mode,
+                          const InstState* st_all, const StepCtl& c)
 {
     __shared__ double sa[NTH / 32], sm[NTH / 32];
     __shared__ int last;
@@ -139,6 +190,7 @@ __device__ void tile_done(const InstDesc& I, InstState* stp, int tile, double a,
         finalize(I, stp, ta, tm, mode);
         *I.count = 0u;
     }
+    if (c.ctrl) step_arrive(st_all, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -149,13 +201,16 @@ constexpr int T2 = 32;
 template <typename R, int MODE>
 __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ insts,
                                                 InstState* __restrict__ st, const ResItem item,
-                                                double2* U)
+                                                double2* U, const StepCtl& c)
 {
     typedef typename C2<R>::T c2;
     const InstDesc& I = insts[item.inst];
     InstState* stp = st + item.inst;
     const InstState s = *stp;
-    if (s.status != HELM_ST_ACTIVE) return;     // uniform over the CTA
+    if (s.status != HELM_ST_ACTIVE) {           // uniform over the CTA
+        if (c.ctrl && item.tx == 0 && item.ty == 0) step_arrive(st, c);
+        return;
+    }
     const int n = I.n;
     const int S = n + 2;
     const double2* __restrict__ uin = I.u[s.it & 1];
@@ -225,7 +280,7 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
         }
     }
     tile_done(I, stp, item.ty * I.res_tx + item.tx, MODE == 0 ? r2d : (double)r2,
-              MODE == 0 ? b2 : (double)emax2, MODE);
+              MODE == 0 ? b2 : (double)emax2, MODE, st, c);
 }
 
 // Grid-stride over the tiles of every instance (one tile per CTA when the grid covers
@@ -233,13 +288,13 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
 template <typename R, int MODE>
 __global__ void __launch_bounds__(NTH)
 k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
-             const ResItem* __restrict__ items, int nitems)
+             const ResItem* __restrict__ items, int nitems, StepCtl c)
 {
     __shared__ double2 U[(T2 + 2) * (T2 + 2)];
     pdl_wait();
     pdl_trigger();
     for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
-        residual2d_tile<R, MODE>(insts, st, items[t], U);
+        residual2d_tile<R, MODE>(insts, st, items[t], U, c);
         __syncthreads();                          // U is restaged by the next tile
     }
 }
@@ -284,7 +339,7 @@ __device__ __forceinline__ R stage_plane3d(double2* Up, const double2* __restric
 template <typename R, int MODE>
 __device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ insts,
                                                 InstState* __restrict__ st, const ResItem item,
-                                                double2 (*U)[P3])
+                                                double2 (*U)[P3], const StepCtl& c)
 {
     typedef typename C2<R>::T c2;
     const InstDesc& I = insts[item.inst];
@@ -297,7 +352,10 @@ __device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ ins
     const LevelDesc L0 = I.lev[0];
     InstState* stp = st + item.inst;
     const InstState s = *stp;
-    if (s.status != HELM_ST_ACTIVE) return;
+    if (s.status != HELM_ST_ACTIVE) {           // uniform over the CTA
+        if (c.ctrl && item.tx == 0 && item.ty == 0 && item.tz == 0) step_arrive(st, c);
+        return;
+    }
     const double2* __restrict__ uin = (s.it & 1) ? u1 : u0;
     double2* __restrict__ uout = (double2*)((s.it & 1) ? u0 : u1);
     const c2* __restrict__ e = (const c2*)L0.e;
@@ -356,45 +414,31 @@ __device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ ins
         sn = t;
     }
     const int tile = (item.tz * I.res_ty + item.ty) * I.res_tx + item.tx;
-    tile_done(I, stp, tile, MODE == 0 ? r2d : (double)r2, MODE == 0 ? b2 : (double)emax2, MODE);
+    tile_done(I, stp, tile, MODE == 0 ? r2d : (double)r2, MODE == 0 ? b2 : (double)emax2, MODE, st, c);
 }
 
 template <typename R, int MODE>
 __global__ void __launch_bounds__(NTH)
 k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
-             const ResItem* __restrict__ items, int nitems)
+             const ResItem* __restrict__ items, int nitems, StepCtl c)
 {
     __shared__ double2 U[3][P3];
     pdl_wait();
     pdl_trigger();
     for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
-        residual3d_tile<R, MODE>(insts, st, items[t], U);
+        residual3d_tile<R, MODE>(insts, st, items[t], U, c);
         __syncthreads();
     }
 }
 
-// One CTA: is any instance still iterating?  Counts the step and sets the loop condition.
+// One CTA: the step control when it is not folded into the residual launch.
 __global__ void __launch_bounds__(256)
 k_check(const InstState* __restrict__ st, int ninst, int* __restrict__ ctrl, int use_cond,
         unsigned long long cond_handle)
 {
     pdl_wait();
     pdl_trigger();
-    __shared__ int any_active;
-    if (threadIdx.x == 0) any_active = 0;
-    __syncthreads();
-    int a = 0;
-    for (int i = threadIdx.x; i < ninst; i += blockDim.x) a |= (st[i].status == HELM_ST_ACTIVE);
-    if (a) atomicOr(&any_active, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int go = any_active;
-        const int done = ctrl[0] + 1;
-        ctrl[0] = done;
-        if (done >= ctrl[1]) go = 0;          // step budget of this launch
-        ctrl[2] = go;
-        if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, go ? 1u : 0u);
-    }
+    step_end(st, ninst, ctrl, use_cond, cond_handle);
 }
 
 template <int D>
@@ -534,16 +578,19 @@ int residual_tile_cols(int D) { return 32; }
 static int g_res_grid = 152 * 5;               // SMs x resident residual CTAs (set up below)
 
 cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* st,
-                            const ResItem* items, int nitems, int mode, cudaStream_t s)
+                            const ResItem* items, int nitems, int mode, cudaStream_t s,
+                            int* ctrl, int nscan, int ninst, int use_cond,
+                            unsigned long long cond_handle)
 {
     if (nitems <= 0) return cudaSuccess;
+    const StepCtl c{ctrl, nscan, ninst, use_cond, cond_handle};
     // one CTA per tile: measured faster than a persistent grid (SMs x resident CTAs
     // striding over the tiles) for both the 2D tiles and the 3D columns
     const int grid = nitems;
     (void)g_res_grid;
 #define HELM_RES(K, RR)                                                                        \
-    (mode ? launch_k(K<RR, 1>, dim3(grid), dim3(NTH), 0, s, insts, st, items, nitems)           \
-          : launch_k(K<RR, 0>, dim3(grid), dim3(NTH), 0, s, insts, st, items, nitems))
+    (mode ? launch_k(K<RR, 1>, dim3(grid), dim3(NTH), 0, s, insts, st, items, nitems, c)        \
+          : launch_k(K<RR, 0>, dim3(grid), dim3(NTH), 0, s, insts, st, items, nitems, c))
     if (D == 2 && prec == 0) HELM_RES(k_residual2d, double);
     else if (D == 2) HELM_RES(k_residual2d, float);
     else if (prec == 0) HELM_RES(k_residual3d, double);

@@ -4,11 +4,20 @@
 // global-memory levels (vcycle.cu / vcycle2d.cu): red-black Gauss-Seidel, residual,
 // full weighting, multilinear prolongation.
 //
+// In 2D complex64 the n = 31 level is not cycled but solved exactly (a direct
+// coarse-grid solver): the sine basis diagonalises Delta_h with zero walls, so
+// e = (2/(n+1))^2 S ((S r S) / mu) S with S_ab = sin(pi a b / (n+1)) and
+// mu_ab = -(4/h^2)(sin^2(pi a / (2(n+1))) + sin^2(pi b / (2(n+1)))).  The four 31 x 31
+// products run on the FP32 pipes from shared memory in ~1/4 of the barrier-bound time
+// of the five-level cycle they replace.
+//
 // The level sizes are template parameters (n_top = 63, 31, ..., 1), so every index is
 // compile-time arithmetic; lanes walk x, warps stride over rows.  Levels with n <= 7
 // are run by warp 0 alone with warp-level barriers, the other warps wait at one block
 // barrier.  Shared-memory layout: for each level, its iterate then its rhs, padded
 // (n + 2)^D arrays with zero rings.
+#include <type_traits>
+
 #include "launch.h"
 #include "pdl.cuh"
 
@@ -26,6 +35,18 @@ template <int D, int N> struct Lv {
 template <int D, int N> constexpr int tail_elems() {
     if constexpr (N <= 1) return 2 * Lv<D, 1>::SZ;
     else return 2 * Lv<D, N>::SZ + tail_elems<D, (N - 1) / 2>();
+}
+
+// does a tail with top size N0 contain the exactly solved n = 31 level?
+template <int D, typename R, int N0> constexpr bool tail_exact()
+{
+    return D == 2 && std::is_same<R, float>::value && N0 >= 31;
+}
+
+template <int D, typename R, int N0> constexpr size_t tail_bytes()
+{
+    return (size_t)tail_elems<D, N0>() * sizeof(typename C2<R>::T) +
+           (tail_exact<D, R, N0>() ? (size_t)(2 * 31 * 32 + 2 * 31 * 34 + 2 * 31 * 32) * sizeof(float) : 0);
 }
 
 template <int NWARPS> __device__ __forceinline__ void tsync() {
@@ -155,13 +176,123 @@ __device__ __forceinline__ void t_prolong(typename C2<R>::T* E, const typename C
     }
 }
 
+// ---------------------------------------------------------------------------
+// Exact 2D solve on the n = 31 level (complex64) in the sine basis
+// ---------------------------------------------------------------------------
+constexpr int XN = 31;                 // level solved exactly (2D complex64)
+constexpr int XP = 32;                 // row pitch of the tables and of T2 (elements)
+constexpr int XT = 34;                 // row pitch of the transposed intermediates (float2)
+constexpr int XGROUPS = (XN + 3) / 4;  // warps of the products, 4 output rows each
+
+// scratch (floats): S[XN][XP], W[XN][XP], Tt[XN][XT] float2, T2[XN][XP] float2
+constexpr int XSCR_FLOATS = 2 * XN * XP + 2 * XN * XT + 2 * XN * XP;
+
+// out_t[x][a] = sum_y S[a][y] in[y][x]  (lanes over x, 4 values of a per warp; S is
+// symmetric, so S[a..a+3][y] is one float4 of row y)
+__device__ __forceinline__ void x_cols(const float2* in, int in_pitch, int in_off,
+                                       const float* Sm, float2* out_t)
+{
+    const int w = threadIdx.x >> 5, x = threadIdx.x & 31;
+    if (w >= XGROUPS || x >= XN) return;
+    const int a0 = 4 * w;
+    float2 acc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] = make_float2(0.f, 0.f);
+#pragma unroll 8
+    for (int y = 0; y < XN; ++y) {
+        const float2 v = in[in_off + y * in_pitch + x];
+        const float4 s4 = *reinterpret_cast<const float4*>(Sm + y * XP + a0);
+        acc[0].x = fmaf(s4.x, v.x, acc[0].x); acc[0].y = fmaf(s4.x, v.y, acc[0].y);
+        acc[1].x = fmaf(s4.y, v.x, acc[1].x); acc[1].y = fmaf(s4.y, v.y, acc[1].y);
+        acc[2].x = fmaf(s4.z, v.x, acc[2].x); acc[2].y = fmaf(s4.z, v.y, acc[2].y);
+        acc[3].x = fmaf(s4.w, v.x, acc[3].x); acc[3].y = fmaf(s4.w, v.y, acc[3].y);
+    }
+    float4* o = reinterpret_cast<float4*>(out_t + x * XT + a0);
+    o[0] = make_float4(acc[0].x, acc[0].y, acc[1].x, acc[1].y);
+    o[1] = make_float4(acc[2].x, acc[2].y, acc[3].x, acc[3].y);
+}
+
+// out[a][b] = W[a][b] * sum_x in_t[x][a] S[x][b]  (lanes over b, 4 values of a per warp)
+__device__ __forceinline__ void x_rows(const float2* in_t, const float* Sm, const float* Wm,
+                                       float2* out, int out_pitch, int out_off)
+{
+    const int w = threadIdx.x >> 5, b = threadIdx.x & 31;
+    if (w >= XGROUPS || b >= XN) return;
+    const int a0 = 4 * w;
+    float2 acc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] = make_float2(0.f, 0.f);
+#pragma unroll 8
+    for (int x = 0; x < XN; ++x) {
+        const float s = Sm[x * XP + b];
+        const float4* t = reinterpret_cast<const float4*>(in_t + x * XT + a0);
+        const float4 t01 = t[0], t23 = t[1];
+        acc[0].x = fmaf(t01.x, s, acc[0].x); acc[0].y = fmaf(t01.y, s, acc[0].y);
+        acc[1].x = fmaf(t01.z, s, acc[1].x); acc[1].y = fmaf(t01.w, s, acc[1].y);
+        acc[2].x = fmaf(t23.x, s, acc[2].x); acc[2].y = fmaf(t23.y, s, acc[2].y);
+        acc[3].x = fmaf(t23.z, s, acc[3].x); acc[3].y = fmaf(t23.w, s, acc[3].y);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int a = a0 + i;
+        if (a >= XN) break;
+        float2 v = acc[i];
+        if (Wm) {
+            const float wv = Wm[a * XP + b];
+            v.x *= wv;
+            v.y *= wv;
+        }
+        out[out_off + a * out_pitch + b] = v;
+    }
+}
+
+// Tables of the sine basis for the n = 31 level of spacing h: S and the scaled inverse
+// eigenvalues W_ab = (2/(n+1))^2 / mu_ab = -h^2 / ((n+1)^2 (s_a + s_b)),
+// s_a = sin^2(pi a / (2(n+1))).  Written once per CTA before the cycle starts.
+__device__ __forceinline__ void x_tables(float* scr, float h)
+{
+    float* Sm = scr;
+    float* Wm = scr + XN * XP;
+    const float c = -(h * h) / (float)((XN + 1) * (XN + 1));
+    for (int q = threadIdx.x; q < XN * XP; q += blockDim.x) {
+        const int i = q / XP, j = q % XP;
+        if (j >= XN) { Sm[q] = 0.f; Wm[q] = 0.f; continue; }
+        const int a = i + 1, b = j + 1;
+        Sm[q] = sinpif((float)((a * b) % (2 * (XN + 1))) / (float)(XN + 1));
+        const float sa = sinpif((float)a / (float)(2 * (XN + 1)));
+        const float sb = sinpif((float)b / (float)(2 * (XN + 1)));
+        Wm[q] = c / (sa * sa + sb * sb);
+    }
+}
+
+// E (padded (n+2)^2, pitch n+2) <- exact solution of Delta_h e = Rr with zero walls
+__device__ __forceinline__ void x_solve(float2* E, const float2* Rr, float* scr)
+{
+    const float* Sm = scr;
+    const float* Wm = scr + XN * XP;
+    float2* Tt = reinterpret_cast<float2*>(scr + 2 * XN * XP);
+    float2* T2 = Tt + XN * XT;
+    constexpr int SP = XN + 2;
+    x_cols(Rr, SP, SP + 1, Sm, Tt);            // S r          (transposed)
+    __syncthreads();
+    x_rows(Tt, Sm, Wm, T2, XP, 0);             // W (S r S)
+    __syncthreads();
+    x_cols(T2, XP, 0, Sm, Tt);                 // S (...)      (transposed)
+    __syncthreads();
+    x_rows(Tt, Sm, nullptr, E, SP, SP + 1);    // (S (...)) S
+    __syncthreads();
+}
+
 template <int D, typename R, int N, int NWARPS>
-__device__ void t_vcycle(typename C2<R>::T* base, R h, int nu1, int nu2)
+__device__ void t_vcycle(typename C2<R>::T* base, R h, int nu1, int nu2, float* xscr)
 {
     typedef typename C2<R>::T c2;
     c2* E = base;
     c2* Rr = base + Lv<D, N>::SZ;
-    if constexpr (N == 1) {
+    if constexpr (D == 2 && std::is_same<R, float>::value && N == XN && NWARPS == TNT / 32) {
+        x_solve(E, Rr, xscr);
+        return;
+    } else if constexpr (N == 1) {
         if (threadIdx.x == 0) {
             constexpr int o = (D == 3) ? 13 : 4;   // the single interior node
             const c2 rr = Rr[o];
@@ -186,10 +317,10 @@ __device__ void t_vcycle(typename C2<R>::T* base, R h, int nu1, int nu2)
         t_restrict<D, R, N, NWARPS>(E, Rr, Rc, h);
         tsync<NWARPS>();
         if constexpr (NWARPS > 1 && NC <= 7) {
-            if (threadIdx.x < 32) t_vcycle<D, R, NC, 1>(Ec, h * (R)2, nu1, nu2);
+            if (threadIdx.x < 32) t_vcycle<D, R, NC, 1>(Ec, h * (R)2, nu1, nu2, xscr);
             __syncthreads();
         } else {
-            t_vcycle<D, R, NC, NWARPS>(Ec, h * (R)2, nu1, nu2);
+            t_vcycle<D, R, NC, NWARPS>(Ec, h * (R)2, nu1, nu2, xscr);
         }
         t_prolong<D, R, N, NWARPS>(E, Ec);
         tsync<NWARPS>();
@@ -218,6 +349,12 @@ k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     if (L0.n != N0) return;                       // launched for another tail size
     constexpr int TOT = tail_elems<D, N0>();
     for (int i = threadIdx.x; i < TOT; i += TNT) base[i] = cz<c2>();
+    float* xscr = nullptr;
+    if constexpr (tail_exact<D, R, N0>()) {
+        xscr = reinterpret_cast<float*>(base + TOT);
+        // the level spacing of n = 31 under the top level's h
+        x_tables(xscr, (float)L0.h * (float)((N0 + 1) / (XN + 1)));
+    }
     __syncthreads();
     constexpr int S = N0 + 2;
     constexpr int ROWS = (D == 3) ? N0 * N0 : N0;
@@ -241,7 +378,7 @@ k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
         }
     }
     __syncthreads();
-    t_vcycle<D, R, N0, TNT / 32>(base, (R)L0.h, nu1, nu2);
+    t_vcycle<D, R, N0, TNT / 32>(base, (R)L0.h, nu1, nu2, xscr);
     c2* __restrict__ go = (c2*)L0.e;
     for (int r = threadIdx.x >> 5; r < ROWS; r += TNT / 32) {
         const int y = r % N0 + 1;
@@ -261,7 +398,7 @@ template <int D, typename R, int N0>
 cudaError_t tl(const InstDesc* insts, const InstState* st, const MgItem* items, int nitems,
                int nu1, int nu2, int load_e, cudaStream_t s)
 {
-    const size_t sm = (size_t)tail_elems<D, N0>() * sizeof(typename C2<R>::T);
+    const size_t sm = tail_bytes<D, R, N0>();
     launch_k(k_tail<D, R, N0>, dim3(nitems), dim3(TNT), sm, s, insts, st, items, nu1, nu2, load_e);
     return cudaGetLastError();
 }
@@ -269,7 +406,7 @@ cudaError_t tl(const InstDesc* insts, const InstState* st, const MgItem* items, 
 template <int D, typename R, int N0>
 cudaError_t ta()
 {
-    const size_t sm = (size_t)tail_elems<D, N0>() * sizeof(typename C2<R>::T);
+    const size_t sm = tail_bytes<D, R, N0>();
     const cudaError_t e = cudaFuncSetAttribute(k_tail<D, R, N0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     return max_carveout(k_tail<D, R, N0>);
@@ -316,8 +453,10 @@ size_t tail_smem_bytes(int D, int prec, int n)
         size_t s = (size_t)(m + 2);
         tot += 2 * ((D == 3) ? s * s * s : s * s);
     }
-    return tot * elem;
+    return tot * elem + (size_t)(tail_exact_n(D, prec) && n >= tail_exact_n(D, prec) ? XSCR_FLOATS * sizeof(float) : 0);
 }
+
+int tail_exact_n(int D, int prec) { return (D == 2 && prec != 0) ? XN : 0; }
 
 cudaError_t setup_tail(int D, int prec)
 {

@@ -45,7 +45,8 @@ def _relerr(a, b):
 # ---------------------------------------------------------------------------
 # single V-cycles, element by element
 # ---------------------------------------------------------------------------
-VC_CASES = [(2, 15), (2, 63), (2, 127), (2, 255), (3, 7), (3, 15), (3, 31), (3, 63), (2, 1), (3, 1)]
+VC_CASES = [(2, 15), (2, 31), (2, 63), (2, 127), (2, 255), (3, 7), (3, 15), (3, 31), (3, 63), (2, 1),
+            (3, 1)]
 
 
 @pytest.mark.parametrize("D,n", VC_CASES)
@@ -56,10 +57,11 @@ def test_vcycle_elementwise(B, D, n, prec, nus):
     rng = np.random.default_rng(100 + n + D)
     r = _rand_c(rng, (n,) * D)
     e0 = _rand_c(rng, (n,) * D) * 0.01
-    E = fd.padded_from(e0.copy())
-    mg.vcycle(E, r, h, *nus)
-    expect = fd.interior(E)
     plan = B.helm_plan_create(D, n, h, 1.0, prec=prec)
+    _, exact_n = B.helm_plan_coarse(plan)      # the level solved exactly, if any
+    E = fd.padded_from(e0.copy())
+    mg.vcycle(E, r, h, *nus, exact_n=exact_n or None)
+    expect = fd.interior(E)
     dt = torch.complex128 if prec == 0 else torch.complex64
     rt = _t(r, dt)
     et = _t(e0, dt)
@@ -71,6 +73,15 @@ def test_vcycle_elementwise(B, D, n, prec, nus):
     # so one cycle's rounding grows with the grid (~2e-5 at 255, ~1.2e-4 at 1023)
     tol = 1e-12 if prec == 0 else 1e-4 * max(1.0, (n + 1) / 256)
     assert np.max(np.abs(got - expect)) <= tol * scale
+
+
+@pytest.mark.parametrize("D,n,prec,want", [
+    (2, 1023, 1, (63, 31)), (2, 1023, 0, (31, 0)), (2, 31, 1, (31, 31)), (2, 15, 1, (15, 0)),
+    (3, 255, 1, (15, 0)), (3, 255, 0, (7, 0))])
+def test_plan_coarse_hierarchy(B, D, n, prec, want):
+    plan = B.helm_plan_create(D, n, 1.0 / (n + 1), 1.0, prec=prec)
+    assert B.helm_plan_coarse(plan) == want
+    B.helm_plan_destroy(plan)
 
 
 @pytest.mark.parametrize("D,n", [(2, 1023), (2, 511), (3, 127)])

@@ -122,3 +122,40 @@ def test_vcycle_contracts_and_converges_to_direct_solve(D, n, bound):
     factors = np.asarray(errs[1:6]) / np.asarray(errs[0:5])
     assert np.all(factors < bound), factors
     assert errs[-1] < 1e-12
+
+
+@pytest.mark.parametrize("D,n", [(2, 31), (3, 7)])
+def test_exact_level_is_the_direct_solve(D, n):
+    # a cycle whose top level is the exactly solved one returns the sparse-LU solution
+    h = 1.0 / (n + 1)
+    rng = np.random.default_rng(11)
+    r = _rand(rng, (n,) * D)
+    E = fd.padded_from(_rand(rng, (n,) * D))        # the guess is discarded
+    mg.vcycle(E, r, h, 1, 1, exact_n=n)
+    lu = fd.SparsePoisson(D, n, h)
+    want = lu(r.real) + 1j * lu(r.imag)
+    assert np.allclose(fd.interior(E), want, rtol=0, atol=1e-12 * np.max(np.abs(want)))
+
+
+@pytest.mark.parametrize("nus", [(2, 2), (1, 1)])
+def test_exact_coarse_level_contracts_at_least_as_well(nus):
+    # 2D n = 127 with the n = 31 level solved exactly (the CUDA complex64 hierarchy):
+    # a better coarse solve cannot slow the cycle down, and it still converges to the
+    # direct solve of the fine system
+    n = 127
+    h = 1.0 / (n + 1)
+    rng = np.random.default_rng(12)
+    r = _rand(rng, (n, n))
+    exact = fd.dst_poisson(r, h)
+    errs = {}
+    for xn in (None, 31):
+        E = np.zeros((n + 2, n + 2), dtype=np.complex128)
+        e = []
+        for _ in range(10):
+            mg.vcycle(E, r, h, *nus, exact_n=xn)
+            e.append(np.linalg.norm(fd.interior(E) - exact) / np.linalg.norm(exact))
+        errs[xn] = np.asarray(e)
+    assert np.all(errs[31] <= errs[None] * 1.02)
+    f = errs[31][1:6] / errs[31][:5]
+    assert np.all(f < (0.1 if nus == (2, 2) else 0.2)), f
+    assert errs[31][-1] < 1e-8
