@@ -85,28 +85,32 @@ __device__ void finalize(const InstDesc& I, InstState* stp, double norm2, double
     *stp = s;
 }
 
-// Block-wide sums / maxima in a fixed order (xor-shuffle, then warps in order).
-// `sum2`: the second channel is summed (mode 0, ||b||^2) instead of maximised (max |e|^2).
-__device__ __forceinline__ void block_reduce(double& a, double& m, double* sa, double* sm, bool sum2)
+// Block-wide sums / maxima in a fixed order (xor-shuffle in T, then the warps' values in
+// order, in FP64).  `sum2`: the second channel is summed (mode 0, ||b||^2) instead of
+// maximised (max |e|^2).  Mode 1 reduces its complex64-derived values in FP32, keeping the
+// shuffle tree off the FP64 pipe; the result (thread 0) is FP64 either way.
+template <typename T>
+__device__ __forceinline__ void block_reduce(T a, T m, double& ra, double& rm, double* sa, double* sm,
+                                             bool sum2)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
-        const double mo = __shfl_xor_sync(0xffffffffu, m, o);
-        m = sum2 ? m + mo : fmax(m, mo);
+        const T mo = __shfl_xor_sync(0xffffffffu, m, o);
+        m = sum2 ? m + mo : (m > mo ? m : mo);
     }
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
-        sa[w] = a;
-        sm[w] = m;
+        sa[w] = (double)a;
+        sm[w] = (double)m;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        a = 0.0;
-        m = 0.0;
+        ra = 0.0;
+        rm = 0.0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-            a += sa[i];
-            m = sum2 ? m + sm[i] : fmax(m, sm[i]);
+            ra += sa[i];
+            rm = sum2 ? rm + sm[i] : fmax(rm, sm[i]);
         }
     }
 }
@@ -162,12 +166,14 @@ __device__ void step_arrive(const InstState* st, const StepCtl& c)
 }
 
 // Write this tile's partials; the last tile of the instance reduces them all.
-__device__ void tile_done(const InstDesc& I, InstState* stp, int tile, double a, double m, int mode,
+template <typename T>
+__device__ void tile_done(const InstDesc& I, InstState* stp, int tile, T ta0, T tm0, int mode,
                           const InstState* st_all, const StepCtl& c)
 {
     __shared__ double sa[NTH / 32], sm[NTH / 32];
     __shared__ int last;
-    block_reduce(a, m, sa, sm, mode == 0);
+    double a = 0.0, m = 0.0;
+    block_reduce<T>(ta0, tm0, a, m, sa, sm, mode == 0);
     if (threadIdx.x == 0) {
         I.part[tile] = a;
         I.part[I.nres_blocks + tile] = m;
@@ -185,9 +191,10 @@ __device__ void tile_done(const InstDesc& I, InstState* stp, int tile, double a,
         tm = (mode == 0) ? tm + v : fmax(tm, v);
     }
     __syncthreads();
-    block_reduce(ta, tm, sa, sm, mode == 0);
+    double fa = 0.0, fm = 0.0;
+    block_reduce<double>(ta, tm, fa, fm, sa, sm, mode == 0);
     if (threadIdx.x == 0) {
-        finalize(I, stp, ta, tm, mode);
+        finalize(I, stp, fa, fm, mode);
         *I.count = 0u;
     }
     if (c.ctrl) step_arrive(st_all, c);
@@ -279,14 +286,17 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
             b2 += bx * bx + by * by;
         }
     }
-    tile_done(I, stp, item.ty * I.res_tx + item.tx, MODE == 0 ? r2d : (double)r2,
-              MODE == 0 ? b2 : (double)emax2, MODE, st, c);
+    if constexpr (MODE == 0)
+        tile_done<double>(I, stp, item.ty * I.res_tx + item.tx, r2d, b2, MODE, st, c);
+    else
+        tile_done<R>(I, stp, item.ty * I.res_tx + item.tx, r2, emax2, MODE, st, c);
 }
 
 // Grid-stride over the tiles of every instance (one tile per CTA when the grid covers
 // them all).
 template <typename R, int MODE>
-__global__ void __launch_bounds__(NTH)
+// 5 resident CTAs per SM (48 registers, no spills) keep more FP64 work in flight
+__global__ void __launch_bounds__(NTH, 5)
 k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
              const ResItem* __restrict__ items, int nitems, StepCtl c)
 {
@@ -414,11 +424,12 @@ __device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ ins
         sn = t;
     }
     const int tile = (item.tz * I.res_ty + item.ty) * I.res_tx + item.tx;
-    tile_done(I, stp, tile, MODE == 0 ? r2d : (double)r2, MODE == 0 ? b2 : (double)emax2, MODE, st, c);
+    if constexpr (MODE == 0) tile_done<double>(I, stp, tile, r2d, b2, MODE, st, c);
+    else tile_done<R>(I, stp, tile, r2, emax2, MODE, st, c);
 }
 
 template <typename R, int MODE>
-__global__ void __launch_bounds__(NTH)
+__global__ void __launch_bounds__(NTH, 4)
 k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
              const ResItem* __restrict__ items, int nitems, StepCtl c)
 {
