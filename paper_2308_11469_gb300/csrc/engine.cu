@@ -334,8 +334,10 @@ struct Engine {
                 out.push_back({LaunchRec::DOWN, ph[j].off, ph[j].cnt, ph[j].tiles, ph[j].shape,
                                zero_start ? 2 : 1, 0.0});
             tail(out, zero_start);
+            // without pre-smoothing the descent leaves e2 unwritten where the iterate was zero
+            const int e2_mode = (nu1 == 0) ? (zero_start ? 2 : 1) : 0;
             for (int j = J - 1; j >= 0; --j)
-                out.push_back({LaunchRec::UP, ph[j].off, ph[j].cnt, ph[j].tiles, ph[j].shape, 0, 0.0});
+                out.push_back({LaunchRec::UP, ph[j].off, ph[j].cnt, ph[j].tiles, ph[j].shape, e2_mode, 0.0});
         };
         auto vcycle = [&](std::vector<LaunchRec>& out, bool zero_start) {
             if (D == 2 && nu1 <= 4 && nu2 <= 4) { vcycle2d(out, zero_start); return; }
@@ -433,7 +435,7 @@ struct Engine {
                 e = launch_down2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu1, L.mode, L.color, s);
                 break;
             case LaunchRec::UP:
-                e = launch_up2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu2, L.color, s);
+                e = launch_up2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu2, L.color, L.mode, s);
                 break;
             case LaunchRec::RESID:
                 if (L.color)      // folded step control: L.work instances, cap statuses

@@ -55,8 +55,10 @@ cudaError_t launch_down2d(int prec, const InstDesc* insts, const InstState* st, 
                           int nitems, int max_tiles, int nu1, int zero_mode, int shape,
                           cudaStream_t s);
 // ascent: e2 + prolongation of the coarse e, nu2 sweeps -> e
+// e2_mode: 0 = read e2; 2 = e2 is zero on every level, 1 = below the finest level (no
+// pre-smoothing from a zero iterate: the descent did not write it)
 cudaError_t launch_up2d(int prec, const InstDesc* insts, const InstState* st, const MgItem* items,
-                        int nitems, int max_tiles, int nu2, int shape, cudaStream_t s);
+                        int nitems, int max_tiles, int nu2, int shape, int e2_mode, cudaStream_t s);
 // tile shape of a level (0 = 64 x 32, 1 = 32 x 16 for n <= 511) and its tile count
 int tile_shape2d(int n);
 int tiles2d(int n);

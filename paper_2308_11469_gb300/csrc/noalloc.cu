@@ -169,7 +169,8 @@ extern "C" helm_status poisson_vcycle_noalloc(int ndim, int n, double h, int pre
                                 tile_shape2d(d.lev[l].n), sm));
         NA_CK(launch_tail(D, pr, d.lev[lt].n, dd, ds, di + lt, 1, nu1, nu2, 1, sm));
         for (int l = lt - 1; l >= 0; --l)
-            NA_CK(launch_up2d(pr, dd, ds, di + l, 1, tiles2d(d.lev[l].n), nu2, tile_shape2d(d.lev[l].n), sm));
+            NA_CK(launch_up2d(pr, dd, ds, di + l, 1, tiles2d(d.lev[l].n), nu2, tile_shape2d(d.lev[l].n),
+                              nu1 == 0 ? 1 : 0, sm));
     } else {
         for (int l = 0; l < lt; ++l) {
             const int m = d.lev[l].n;

@@ -8,14 +8,16 @@
 // coarse-grid solver): the sine basis diagonalises Delta_h with zero walls, so
 // e = (2/(n+1))^2 S ((S r S) / mu) S with S_ab = sin(pi a b / (n+1)) and
 // mu_ab = -(4/h^2)(sin^2(pi a / (2(n+1))) + sin^2(pi b / (2(n+1)))).  The four 31 x 31
-// products run on the FP32 pipes from shared memory in ~1/4 of the barrier-bound time
-// of the five-level cycle they replace.
+// products run on the FP32 pipes from shared memory.
 //
 // The level sizes are template parameters (n_top = 63, 31, ..., 1), so every index is
 // compile-time arithmetic; lanes walk x, warps stride over rows.  Levels with n <= 7
 // are run by warp 0 alone with warp-level barriers, the other warps wait at one block
 // barrier.  Shared-memory layout: for each level, its iterate then its rhs, padded
-// (n + 2)^D arrays with zero rings.
+// (n + 2)^D arrays with zero rings, each x-row stored with its even-x entries first and
+// its odd-x entries after them, so that the lanes of a red-black half-sweep (one colour:
+// x of one parity) and of the restriction read consecutive words (no bank conflicts).
+#include <cmath>
 #include <type_traits>
 
 #include "launch.h"
@@ -26,11 +28,32 @@ namespace {
 
 constexpr int TNT = 1024;
 
+// Exact 2D solve of the n = 31 level (complex64)
+constexpr int XN = 31;                 // level solved exactly
+constexpr int XP = 32;                 // row pitch of the tables and of T2 (elements)
+constexpr int XT = 34;                 // row pitch of the transposed intermediate (float2)
+constexpr int XA = 4;                  // output rows per warp in the products
+constexpr int XG = (XN + XA - 1) / XA; // warps of the products (8)
+// scratch (floats): S[XN][XP], U[XN][XP] (tables), Tt [XN][XT] float2, T2 [XN][XP] float2
+constexpr int XTAB_FLOATS = 2 * XN * XP;
+constexpr int XSCR_FLOATS = XTAB_FLOATS + 2 * XN * XT + 2 * XN * XP;
+
+// S_ab = sin(pi a b / 32) and U_ab = 1 / (s_a + s_b), s_a = sin^2(pi a / 64), written by
+// setup_tail (host, double precision, rounded once)
+__device__ float g_xtab[XTAB_FLOATS];
+
 template <int D, int N> struct Lv {
-    static constexpr int S = N + 2;
+    static constexpr int S = N + 2;              // padded row length (odd)
+    static constexpr int HE = (S + 1) / 2;       // even-x entries of a row, stored first
     static constexpr int SZ = (D == 3) ? S * S * S : S * S;
     static constexpr int NC = (N - 1) / 2;
 };
+
+// position of padded x within a row of a level with n = N
+template <int N> __device__ __forceinline__ int ix(int x)
+{
+    return (x & 1) ? Lv<2, N>::HE + (x >> 1) : (x >> 1);
+}
 
 template <int D, int N> constexpr int tail_elems() {
     if constexpr (N <= 1) return 2 * Lv<D, 1>::SZ;
@@ -40,13 +63,13 @@ template <int D, int N> constexpr int tail_elems() {
 // does a tail with top size N0 contain the exactly solved n = 31 level?
 template <int D, typename R, int N0> constexpr bool tail_exact()
 {
-    return D == 2 && std::is_same<R, float>::value && N0 >= 31;
+    return D == 2 && std::is_same<R, float>::value && N0 >= XN;
 }
 
 template <int D, typename R, int N0> constexpr size_t tail_bytes()
 {
     return (size_t)tail_elems<D, N0>() * sizeof(typename C2<R>::T) +
-           (tail_exact<D, R, N0>() ? (size_t)(2 * 31 * 32 + 2 * 31 * 34 + 2 * 31 * 32) * sizeof(float) : 0);
+           (tail_exact<D, R, N0>() ? (size_t)XSCR_FLOATS * sizeof(float) : 0);
 }
 
 template <int NWARPS> __device__ __forceinline__ void tsync() {
@@ -70,8 +93,12 @@ __device__ __forceinline__ void t_sweep(typename C2<R>::T* E, const typename C2<
         const int xs = 1 + (((1 + y + z) & 1) ^ color);
         const int x = xs + 2 * lane;          // N <= 63: one pass of 32 lanes covers the row
         if (x > N) continue;
-        const int o = ((D == 3) ? (z * S + y) : y) * S + x;
-        const c2 a = E[o - 1], b = E[o + 1], c = E[o - S], d = E[o + S];
+        const int row = ((D == 3) ? (z * S + y) : y) * S;
+        // x has the row's colour parity p; its west / east neighbours the other one
+        constexpr int HE = Lv<D, N>::HE;
+        const int p = xs & 1, m = row + (x >> 1);
+        const int o = m + (p ? HE : 0);
+        const c2 a = E[m + (p ? 0 : HE - 1)], b = E[m + (p ? 1 : HE)], c = E[o - S], d = E[o + S];
         R sx = a.x + b.x + c.x + d.x;
         R sy = a.y + b.y + c.y + d.y;
         if (D == 3) {
@@ -87,7 +114,10 @@ __device__ __forceinline__ void t_sweep(typename C2<R>::T* E, const typename C2<
     }
 }
 
-template <int D, typename R, int N, int NWARPS>
+// Full weighting of the residual rhs - Delta_h e; EZ: the iterate is known to be zero
+// (no pre-smoothing from a zero guess), so the residual is rhs itself (the same values
+// the general form yields with e = 0).
+template <int D, typename R, int N, int NWARPS, bool EZ>
 __device__ __forceinline__ void t_restrict(const typename C2<R>::T* E, const typename C2<R>::T* Rr,
                                            typename C2<R>::T* Rc, R h)
 {
@@ -113,28 +143,39 @@ __device__ __forceinline__ void t_restrict(const typename C2<R>::T* E, const typ
 #pragma unroll
                 for (int dx = -1; dx <= 1; ++dx) {
                     const R w = wz * wy * ((dx == 0) ? (R)2 : (R)1);
-                    const int o = ((D == 3) ? ((2 * Z + dz) * S + 2 * Y + dy) : (2 * Y + dy)) * S + 2 * X + dx;
-                    const c2 c = E[o], a = E[o - 1], b = E[o + 1], u = E[o - S], d = E[o + S];
-                    R sx = a.x + b.x + u.x + d.x;
-                    R sy = a.y + b.y + u.y + d.y;
-                    if (D == 3) {
-                        const c2 f = E[o - S * S], g = E[o + S * S];
-                        sx += f.x + g.x;
-                        sy += f.y + g.y;
-                    }
+                    const int row = ((D == 3) ? ((2 * Z + dz) * S + 2 * Y + dy) : (2 * Y + dy)) * S;
+                    const int x = 2 * X + dx;
+                    const int o = row + ix<N>(x);
                     const c2 rr = Rr[o];
-                    ax += w * (rr.x - (sx - (R)(2 * D) * c.x) * ih2);
-                    ay += w * (rr.y - (sy - (R)(2 * D) * c.y) * ih2);
+                    if constexpr (EZ) {
+                        ax += w * rr.x;
+                        ay += w * rr.y;
+                    } else {
+                        const c2 c = E[o], a = E[row + ix<N>(x - 1)], b = E[row + ix<N>(x + 1)];
+                        const c2 u = E[o - S], d = E[o + S];
+                        R sx = a.x + b.x + u.x + d.x;
+                        R sy = a.y + b.y + u.y + d.y;
+                        if (D == 3) {
+                            const c2 f = E[o - S * S], g = E[o + S * S];
+                            sx += f.x + g.x;
+                            sy += f.y + g.y;
+                        }
+                        ax += w * (rr.x - (sx - (R)(2 * D) * c.x) * ih2);
+                        ay += w * (rr.y - (sy - (R)(2 * D) * c.y) * ih2);
+                    }
                 }
             }
         }
         c2 v;
         v.x = ax * scale;
         v.y = ay * scale;
-        Rc[((D == 3) ? (Z * SC + Y) : Y) * SC + X] = v;
+        Rc[((D == 3) ? (Z * SC + Y) : Y) * SC + ix<NC>(X)] = v;
     }
 }
 
+// e += multilinear interpolation of the coarse iterate.  Each row is walked by storage
+// half: even x = 2q (coarse column q) then odd x = 2q + 1 (coarse columns q, q + 1), so
+// lanes touch consecutive words.
 template <int D, typename R, int N, int NWARPS>
 __device__ __forceinline__ void t_prolong(typename C2<R>::T* E, const typename C2<R>::T* Ec)
 {
@@ -142,32 +183,35 @@ __device__ __forceinline__ void t_prolong(typename C2<R>::T* E, const typename C
     constexpr int S = N + 2;
     constexpr int NC = (N - 1) / 2;
     constexpr int SC = NC + 2;
+    constexpr int HE = Lv<D, N>::HE;
     constexpr int ROWS = (D == 3) ? N * N : N;
     const int lane = threadIdx.x & 31;
+    const R w = (D == 3) ? (R)0.125 : (R)0.25;
     for (int r = threadIdx.x >> 5; r < ROWS; r += NWARPS) {
         const int y = r % N + 1;
         const int z = (D == 3) ? r / N + 1 : 0;
+        const int row = ((D == 3) ? (z * S + y) : y) * S;
         const int y0 = y >> 1, y1 = (y + 1) >> 1;
         const int z0 = z >> 1, z1 = (z + 1) >> 1;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int x = lane + 32 * j + 1;
-            if (x > N) break;
-            const int x0 = x >> 1, x1 = (x + 1) >> 1;
+        for (int par = 0; par < 2; ++par) {
+            const int q = lane + (par ? 0 : 1);
+            if (2 * q + par > N) continue;
+            const int c0 = ix<NC>(q), c1 = par ? ix<NC>(q + 1) : c0;
             R vx = 0, vy = 0;
 #pragma unroll
             for (int iz = 0; iz < (D == 3 ? 2 : 1); ++iz)
 #pragma unroll
-                for (int iy = 0; iy < 2; ++iy)
-#pragma unroll
-                    for (int ix = 0; ix < 2; ++ix) {
-                        const int Z = iz ? z1 : z0, Y = iy ? y1 : y0, XX = ix ? x1 : x0;
-                        const c2 c = Ec[((D == 3) ? (Z * SC + Y) : Y) * SC + XX];
-                        vx += c.x;
-                        vy += c.y;
-                    }
-            const R w = (D == 3) ? (R)0.125 : (R)0.25;
-            const int o = ((D == 3) ? (z * S + y) : y) * S + x;
+                for (int iy = 0; iy < 2; ++iy) {
+                    const int Z = iz ? z1 : z0, Y = iy ? y1 : y0;
+                    const int crow = ((D == 3) ? (Z * SC + Y) : Y) * SC;
+                    const c2 a = Ec[crow + c0], b = Ec[crow + c1];
+                    vx += a.x;
+                    vy += a.y;
+                    vx += b.x;
+                    vy += b.y;
+                }
+            const int o = row + (par ? HE : 0) + q;
             c2 v = E[o];
             v.x += w * vx;
             v.y += w * vy;
@@ -176,31 +220,42 @@ __device__ __forceinline__ void t_prolong(typename C2<R>::T* E, const typename C
     }
 }
 
-// ---------------------------------------------------------------------------
-// Exact 2D solve on the n = 31 level (complex64) in the sine basis
-// ---------------------------------------------------------------------------
-constexpr int XN = 31;                 // level solved exactly (2D complex64)
-constexpr int XP = 32;                 // row pitch of the tables and of T2 (elements)
-constexpr int XT = 34;                 // row pitch of the transposed intermediates (float2)
-constexpr int XGROUPS = (XN + 3) / 4;  // warps of the products, 4 output rows each
+// Clear the iterates of the levels the cycle will use (their rings must be zero and the
+// coarse ones start from zero); the rhs arrays are written before they are read.
+template <int D, typename R, int N>
+__device__ __forceinline__ void t_clear(typename C2<R>::T* base)
+{
+    typedef typename C2<R>::T c2;
+    for (int i = threadIdx.x; i < Lv<D, N>::SZ; i += TNT) base[i] = cz<c2>();
+    constexpr bool exact_here = D == 2 && std::is_same<R, float>::value && N == XN;
+    if constexpr (N > 1 && !exact_here) t_clear<D, R, (N - 1) / 2>(base + 2 * Lv<D, N>::SZ);
+}
 
-// scratch (floats): S[XN][XP], W[XN][XP], Tt[XN][XT] float2, T2[XN][XP] float2
-constexpr int XSCR_FLOATS = 2 * XN * XP + 2 * XN * XT + 2 * XN * XP;
+// ---------------------------------------------------------------------------
+// Exact 2D solve of the n = 31 level (complex64) in the sine basis
+// ---------------------------------------------------------------------------
+// element (y, x) (0-based interior indices) of a level array, or of a plain scratch
+// matrix of pitch XP
+template <bool LEVEL> __device__ __forceinline__ int x_at(int y, int x)
+{
+    if constexpr (LEVEL) return (y + 1) * (XN + 2) + ix<XN>(x + 1);
+    else return y * XP + x;
+}
 
-// out_t[x][a] = sum_y S[a][y] in[y][x]  (lanes over x, 4 values of a per warp; S is
-// symmetric, so S[a..a+3][y] is one float4 of row y)
-__device__ __forceinline__ void x_cols(const float2* in, int in_pitch, int in_off,
-                                       const float* Sm, float2* out_t)
+// out_t[x][a] = sum_y S[a][y] in[y][x]: lanes over x, XA values of a per warp (S is
+// symmetric, so S[a0..a0+3][y] is one float4 of row y)
+template <bool LEVEL_IN>
+__device__ __forceinline__ void x_cols(const float2* in, const float* Sm, float2* out_t)
 {
     const int w = threadIdx.x >> 5, x = threadIdx.x & 31;
-    if (w >= XGROUPS || x >= XN) return;
-    const int a0 = 4 * w;
-    float2 acc[4];
+    if (w >= XG || x >= XN) return;
+    const int a0 = XA * w;
+    float2 acc[XA];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < XA; ++i) acc[i] = make_float2(0.f, 0.f);
 #pragma unroll 8
     for (int y = 0; y < XN; ++y) {
-        const float2 v = in[in_off + y * in_pitch + x];
+        const float2 v = in[x_at<LEVEL_IN>(y, x)];
         const float4 s4 = *reinterpret_cast<const float4*>(Sm + y * XP + a0);
         acc[0].x = fmaf(s4.x, v.x, acc[0].x); acc[0].y = fmaf(s4.x, v.y, acc[0].y);
         acc[1].x = fmaf(s4.y, v.x, acc[1].x); acc[1].y = fmaf(s4.y, v.y, acc[1].y);
@@ -212,16 +267,18 @@ __device__ __forceinline__ void x_cols(const float2* in, int in_pitch, int in_of
     o[1] = make_float4(acc[2].x, acc[2].y, acc[3].x, acc[3].y);
 }
 
-// out[a][b] = W[a][b] * sum_x in_t[x][a] S[x][b]  (lanes over b, 4 values of a per warp)
-__device__ __forceinline__ void x_rows(const float2* in_t, const float* Sm, const float* Wm,
-                                       float2* out, int out_pitch, int out_off)
+// out[a][b] = scale_ab * sum_x in_t[x][a] S[x][b] (scale_ab = c U_ab, or 1): lanes over
+// b, XA values of a per warp
+template <bool LEVEL_OUT>
+__device__ __forceinline__ void x_rows(const float2* in_t, const float* Sm, const float* Um, float c,
+                                       float2* out)
 {
     const int w = threadIdx.x >> 5, b = threadIdx.x & 31;
-    if (w >= XGROUPS || b >= XN) return;
-    const int a0 = 4 * w;
-    float2 acc[4];
+    if (w >= XG || b >= XN) return;
+    const int a0 = XA * w;
+    float2 acc[XA];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < XA; ++i) acc[i] = make_float2(0.f, 0.f);
 #pragma unroll 8
     for (int x = 0; x < XN; ++x) {
         const float s = Sm[x * XP + b];
@@ -233,68 +290,53 @@ __device__ __forceinline__ void x_rows(const float2* in_t, const float* Sm, cons
         acc[3].x = fmaf(t23.z, s, acc[3].x); acc[3].y = fmaf(t23.w, s, acc[3].y);
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < XA; ++i) {
         const int a = a0 + i;
         if (a >= XN) break;
         float2 v = acc[i];
-        if (Wm) {
-            const float wv = Wm[a * XP + b];
+        if (Um) {
+            const float wv = c * Um[a * XP + b];
             v.x *= wv;
             v.y *= wv;
         }
-        out[out_off + a * out_pitch + b] = v;
+        out[x_at<LEVEL_OUT>(a, b)] = v;
     }
 }
 
-// Tables of the sine basis for the n = 31 level of spacing h: S and the scaled inverse
-// eigenvalues W_ab = (2/(n+1))^2 / mu_ab = -h^2 / ((n+1)^2 (s_a + s_b)),
-// s_a = sin^2(pi a / (2(n+1))).  Written once per CTA before the cycle starts.
-__device__ __forceinline__ void x_tables(float* scr, float h)
-{
-    float* Sm = scr;
-    float* Wm = scr + XN * XP;
-    const float c = -(h * h) / (float)((XN + 1) * (XN + 1));
-    for (int q = threadIdx.x; q < XN * XP; q += blockDim.x) {
-        const int i = q / XP, j = q % XP;
-        if (j >= XN) { Sm[q] = 0.f; Wm[q] = 0.f; continue; }
-        const int a = i + 1, b = j + 1;
-        Sm[q] = sinpif((float)((a * b) % (2 * (XN + 1))) / (float)(XN + 1));
-        const float sa = sinpif((float)a / (float)(2 * (XN + 1)));
-        const float sb = sinpif((float)b / (float)(2 * (XN + 1)));
-        Wm[q] = c / (sa * sa + sb * sb);
-    }
-}
-
-// E (padded (n+2)^2, pitch n+2) <- exact solution of Delta_h e = Rr with zero walls
-__device__ __forceinline__ void x_solve(float2* E, const float2* Rr, float* scr)
+// E (level array of n = 31) <- exact solution of Delta_h e = Rr with zero walls, h the
+// level's spacing:  e = c S (U o (S r S)) S, c = -h^2 / (n+1)^2
+__device__ __forceinline__ void x_solve(float2* E, const float2* Rr, float* scr, float h)
 {
     const float* Sm = scr;
-    const float* Wm = scr + XN * XP;
-    float2* Tt = reinterpret_cast<float2*>(scr + 2 * XN * XP);
+    const float* Um = scr + XN * XP;
+    float2* Tt = reinterpret_cast<float2*>(scr + XTAB_FLOATS);
     float2* T2 = Tt + XN * XT;
-    constexpr int SP = XN + 2;
-    x_cols(Rr, SP, SP + 1, Sm, Tt);            // S r          (transposed)
+    const float c = -(h * h) / (float)((XN + 1) * (XN + 1));
+    x_cols<true>(Rr, Sm, Tt);                  // S r          (transposed)
     __syncthreads();
-    x_rows(Tt, Sm, Wm, T2, XP, 0);             // W (S r S)
+    x_rows<false>(Tt, Sm, Um, c, T2);          // c U o (S r S)
     __syncthreads();
-    x_cols(T2, XP, 0, Sm, Tt);                 // S (...)      (transposed)
+    x_cols<false>(T2, Sm, Tt);                 // S (...)      (transposed)
     __syncthreads();
-    x_rows(Tt, Sm, nullptr, E, SP, SP + 1);    // (S (...)) S
+    x_rows<true>(Tt, Sm, nullptr, 1.f, E);     // (S (...)) S
     __syncthreads();
 }
 
+// One V(nu1, nu2)-cycle on the level of size N held at `base` (iterate, then rhs).
+// ez: the iterate is zero on entry (a coarse level, or a top level started from zero).
 template <int D, typename R, int N, int NWARPS>
-__device__ void t_vcycle(typename C2<R>::T* base, R h, int nu1, int nu2, float* xscr)
+__device__ void t_vcycle(typename C2<R>::T* base, R h, int nu1, int nu2, float* xscr, bool ez)
 {
     typedef typename C2<R>::T c2;
     c2* E = base;
     c2* Rr = base + Lv<D, N>::SZ;
     if constexpr (D == 2 && std::is_same<R, float>::value && N == XN && NWARPS == TNT / 32) {
-        x_solve(E, Rr, xscr);
+        x_solve(E, Rr, xscr, (float)h);
         return;
     } else if constexpr (N == 1) {
         if (threadIdx.x == 0) {
-            constexpr int o = (D == 3) ? 13 : 4;   // the single interior node
+            constexpr int S = 3;
+            constexpr int o = ((D == 3) ? (S + 1) : 1) * S + Lv<D, 1>::HE;  // the single node
             const c2 rr = Rr[o];
             const R c = -(h * h) / (R)(2 * D);
             c2 v;
@@ -314,13 +356,14 @@ __device__ void t_vcycle(typename C2<R>::T* base, R h, int nu1, int nu2, float* 
             t_sweep<D, R, N, NWARPS>(E, Rr, h2, 1);
             tsync<NWARPS>();
         }
-        t_restrict<D, R, N, NWARPS>(E, Rr, Rc, h);
+        if (ez && nu1 == 0) t_restrict<D, R, N, NWARPS, true>(E, Rr, Rc, h);
+        else t_restrict<D, R, N, NWARPS, false>(E, Rr, Rc, h);
         tsync<NWARPS>();
         if constexpr (NWARPS > 1 && NC <= 7) {
-            if (threadIdx.x < 32) t_vcycle<D, R, NC, 1>(Ec, h * (R)2, nu1, nu2, xscr);
+            if (threadIdx.x < 32) t_vcycle<D, R, NC, 1>(Ec, h * (R)2, nu1, nu2, xscr, true);
             __syncthreads();
         } else {
-            t_vcycle<D, R, NC, NWARPS>(Ec, h * (R)2, nu1, nu2, xscr);
+            t_vcycle<D, R, NC, NWARPS>(Ec, h * (R)2, nu1, nu2, xscr, true);
         }
         t_prolong<D, R, N, NWARPS>(E, Ec);
         tsync<NWARPS>();
@@ -348,48 +391,85 @@ k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     if (st[item.inst].status != HELM_ST_ACTIVE) return;
     if (L0.n != N0) return;                       // launched for another tail size
     constexpr int TOT = tail_elems<D, N0>();
-    for (int i = threadIdx.x; i < TOT; i += TNT) base[i] = cz<c2>();
-    float* xscr = nullptr;
-    if constexpr (tail_exact<D, R, N0>()) {
-        xscr = reinterpret_cast<float*>(base + TOT);
-        // the level spacing of n = 31 under the top level's h
-        x_tables(xscr, (float)L0.h * (float)((N0 + 1) / (XN + 1)));
-    }
-    __syncthreads();
     constexpr int S = N0 + 2;
     constexpr int ROWS = (D == 3) ? N0 * N0 : N0;
     const c2* __restrict__ gr = (const c2*)L0.rhs;
     const c2* __restrict__ ge = (const c2*)L0.e;
-    const bool le = load_e && item.level == 0;
-    const int lane = threadIdx.x & 31;
+    // the starting iterate is read unless the top level is the exactly solved one (which
+    // discards it)
+    const bool le = load_e && item.level == 0 && !(tail_exact<D, R, N0>() && N0 == XN);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     c2* E = base;
     c2* Rr = base + Lv<D, N0>::SZ;
-    for (int r = threadIdx.x >> 5; r < ROWS; r += TNT / 32) {
-        const int y = r % N0 + 1;
-        const int z = (D == 3) ? r / N0 + 1 : 0;
-        const size_t grow = ((D == 3) ? ((size_t)z * L0.rows + y) : (size_t)y) * L0.pitch;
-        const int srow = ((D == 3) ? (z * S + y) : y) * S;
+    // 2D: the top level's global loads go out first, their latency overlapping the
+    // clearing of shared memory (3D: loaded after it, to bound the registers held)
+    constexpr int RPW = (D == 2) ? (ROWS + 31) / 32 : 1;      // rows per warp
+    constexpr int XJ = (N0 + 31) / 32;                         // 32-wide chunks of a row
+    c2 vr[RPW][XJ], ve[RPW][XJ];
+    if constexpr (D == 2) {
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int x = lane + 32 * j + 1;
-            if (x > N0) break;
-            Rr[srow + x] = gr[grow + x];
-            if (le) E[srow + x] = ge[grow + x];
+        for (int i = 0; i < RPW; ++i) {
+            const int y = warp + 32 * i + 1;
+#pragma unroll
+            for (int j = 0; j < XJ; ++j) {
+                const int x = lane + 32 * j + 1;
+                if (y <= N0 && x <= N0) {
+                    vr[i][j] = gr[(size_t)y * L0.pitch + x];
+                    if (le) ve[i][j] = ge[(size_t)y * L0.pitch + x];
+                }
+            }
+        }
+    }
+    float* xscr = nullptr;
+    if constexpr (tail_exact<D, R, N0>()) {
+        // sine tables of the exact level (host-computed)
+        xscr = reinterpret_cast<float*>(base + TOT);
+        for (int i = threadIdx.x; i < XTAB_FLOATS / 4; i += TNT)
+            reinterpret_cast<float4*>(xscr)[i] = reinterpret_cast<const float4*>(g_xtab)[i];
+    }
+    t_clear<D, R, N0>(base);
+    __syncthreads();
+    if constexpr (D == 2) {
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+            const int y = warp + 32 * i + 1;
+#pragma unroll
+            for (int j = 0; j < XJ; ++j) {
+                const int x = lane + 32 * j + 1;
+                if (y <= N0 && x <= N0) {
+                    Rr[y * S + ix<N0>(x)] = vr[i][j];
+                    if (le) E[y * S + ix<N0>(x)] = ve[i][j];
+                }
+            }
+        }
+    } else {
+        for (int r = warp; r < ROWS; r += TNT / 32) {
+            const int y = r % N0 + 1;
+            const int z = r / N0 + 1;
+            const size_t grow = ((size_t)z * L0.rows + y) * L0.pitch;
+            const int srow = (z * S + y) * S;
+#pragma unroll
+            for (int j = 0; j < XJ; ++j) {
+                const int x = lane + 32 * j + 1;
+                if (x > N0) break;
+                Rr[srow + ix<N0>(x)] = gr[grow + x];
+                if (le) E[srow + ix<N0>(x)] = ge[grow + x];
+            }
         }
     }
     __syncthreads();
-    t_vcycle<D, R, N0, TNT / 32>(base, (R)L0.h, nu1, nu2, xscr);
+    t_vcycle<D, R, N0, TNT / 32>(base, (R)L0.h, nu1, nu2, xscr, !le);
     c2* __restrict__ go = (c2*)L0.e;
-    for (int r = threadIdx.x >> 5; r < ROWS; r += TNT / 32) {
+    for (int r = warp; r < ROWS; r += TNT / 32) {
         const int y = r % N0 + 1;
         const int z = (D == 3) ? r / N0 + 1 : 0;
         const size_t grow = ((D == 3) ? ((size_t)z * L0.rows + y) : (size_t)y) * L0.pitch;
         const int srow = ((D == 3) ? (z * S + y) : y) * S;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < XJ; ++j) {
             const int x = lane + 32 * j + 1;
             if (x > N0) break;
-            go[grow + x] = E[srow + x];
+            go[grow + x] = E[srow + ix<N0>(x)];
         }
     }
 }
@@ -460,6 +540,21 @@ int tail_exact_n(int D, int prec) { return (D == 2 && prec != 0) ? XN : 0; }
 
 cudaError_t setup_tail(int D, int prec)
 {
+    if (D == 2 && prec != 0) {
+        static float tab[XTAB_FLOATS];
+        const double pi = 3.14159265358979323846;
+        for (int i = 0; i < XN; ++i)
+            for (int j = 0; j < XP; ++j) {
+                const int a = i + 1, b = j + 1;
+                const double sa = std::sin(pi * a / (2.0 * (XN + 1)));
+                const double sb = std::sin(pi * b / (2.0 * (XN + 1)));
+                const bool in = j < XN;
+                tab[i * XP + j] = in ? (float)std::sin(pi * a * b / (XN + 1)) : 0.f;
+                tab[XN * XP + i * XP + j] = in ? (float)(1.0 / (sa * sa + sb * sb)) : 0.f;
+            }
+        const cudaError_t e = cudaMemcpyToSymbol(g_xtab, tab, sizeof tab);
+        if (e != cudaSuccess) return e;
+    }
     if (D == 2) return prec == 0 ? tail_attrs<2, double>() : tail_attrs<2, float>();
     return prec == 0 ? tail_attrs<3, double>() : tail_attrs<3, float>();
 }

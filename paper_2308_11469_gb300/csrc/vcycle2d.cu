@@ -144,9 +144,12 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
         half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 1);
         __syncthreads();
     }
+    // no pre-smoothing from a zero iterate: e2 stays zero (the ascent kernel knows it and
+    // does not read it) and the residual is rhs itself
+    const bool skip = (NU == 0) && zero;
     // smoothed iterate of the tile -> e2
     c2* __restrict__ ge2 = (c2*)L.e2;
-    for (int ty = threadIdx.x >> 5; ty < TY; ty += NW) {
+    for (int ty = threadIdx.x >> 5; ty < TY && !skip; ty += NW) {
         const int gy = y0 + ty;
         if (gy > n) break;
 #pragma unroll
@@ -158,7 +161,7 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     }
     // residual on the tile plus a 1-node ring, in place of rhs (one colour at a time)
     const R ih2 = (R)1 / h2;
-    {
+    if (!skip) {
         const int xa = max(x0 - 1, 1), xb = min(x0 + TX, n);
         const int ya = max(y0 - 1, 1), yb = min(y0 + TY, n);
 #pragma unroll
@@ -220,7 +223,7 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
 template <typename R, int NU, int TX, int TY>
 __global__ void __launch_bounds__(NT)
 k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
-       const MgItem* __restrict__ items)
+       const MgItem* __restrict__ items, int e2_mode)
 {
     typedef typename C2<R>::T c2;
     constexpr int H = 2 * NU;
@@ -260,6 +263,9 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const c2* __restrict__ ge2 = (const c2*)L.e2;
     const c2* __restrict__ gr = (const c2*)L.rhs;
     const int P = L.pitch;
+    // e2 is zero (not written by the descent) when the cycle has no pre-smoothing and the
+    // level started from zero: e2_mode 2 = every level, 1 = the levels below the finest
+    const bool e2z = (e2_mode == 2) || (e2_mode == 1 && item.level > 0);
     // stage the coarse window, e2 and rhs with asynchronous copies (zero-filled outside)
     for (int cy = threadIdx.x >> 5; cy < CH; cy += NW) {
         const int Y = cy0 + cy;
@@ -280,7 +286,8 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
             const size_t g = in ? (size_t)gy * P + gx : 0;
             const int c = (lx + ly + cpar) & 1;
             const int o = PL::at(lx, ly);
-            cp_async_elem<sizeof(c2)>((c ? E1 : E0) + o, ge2 + g, in);
+            if (e2z) (c ? E1 : E0)[o] = cz<c2>();
+            else cp_async_elem<sizeof(c2)>((c ? E1 : E0) + o, ge2 + g, in);
             cp_async_elem<sizeof(c2)>((c ? R1 : R0) + o, gr + g, in);
         }
     }
@@ -384,10 +391,12 @@ void down_s(dim3 g, const InstDesc* insts, const InstState* st, const MgItem* it
 }
 
 template <typename R, int NU, int S>
-void up_s(dim3 g, const InstDesc* insts, const InstState* st, const MgItem* items, cudaStream_t s)
+void up_s(dim3 g, const InstDesc* insts, const InstState* st, const MgItem* items, int e2_mode,
+          cudaStream_t s)
 {
     constexpr int X = Shape<S>::X, Y = Shape<S>::Y;
-    launch_k(k_up2d<R, NU, X, Y>, g, dim3(NT), up_bytes<NU, X, Y>(sizeof(R) * 2), s, insts, st, items);
+    launch_k(k_up2d<R, NU, X, Y>, g, dim3(NT), up_bytes<NU, X, Y>(sizeof(R) * 2), s, insts, st, items,
+             e2_mode);
 }
 
 template <typename R, int S>
@@ -407,14 +416,14 @@ cudaError_t down(int nu, dim3 g, const InstDesc* insts, const InstState* st, con
 
 template <typename R, int S>
 cudaError_t up(int nu, dim3 g, const InstDesc* insts, const InstState* st, const MgItem* items,
-               cudaStream_t s)
+               int e2_mode, cudaStream_t s)
 {
     switch (nu) {
-    case 0: up_s<R, 0, S>(g, insts, st, items, s); break;
-    case 1: up_s<R, 1, S>(g, insts, st, items, s); break;
-    case 2: up_s<R, 2, S>(g, insts, st, items, s); break;
-    case 3: up_s<R, 3, S>(g, insts, st, items, s); break;
-    case 4: up_s<R, 4, S>(g, insts, st, items, s); break;
+    case 0: up_s<R, 0, S>(g, insts, st, items, e2_mode, s); break;
+    case 1: up_s<R, 1, S>(g, insts, st, items, e2_mode, s); break;
+    case 2: up_s<R, 2, S>(g, insts, st, items, e2_mode, s); break;
+    case 3: up_s<R, 3, S>(g, insts, st, items, e2_mode, s); break;
+    case 4: up_s<R, 4, S>(g, insts, st, items, e2_mode, s); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -447,12 +456,13 @@ cudaError_t launch_down2d(int prec, const InstDesc* insts, const InstState* st, 
 }
 
 cudaError_t launch_up2d(int prec, const InstDesc* insts, const InstState* st, const MgItem* items,
-                        int nitems, int max_tiles, int nu2, int shape, cudaStream_t s)
+                        int nitems, int max_tiles, int nu2, int shape, int e2_mode, cudaStream_t s)
 {
     dim3 g(max_tiles, nitems);
-    if (shape) return prec == 0 ? up<double, 1>(nu2, g, insts, st, items, s)
-                                : up<float, 1>(nu2, g, insts, st, items, s);
-    return prec == 0 ? up<double, 0>(nu2, g, insts, st, items, s) : up<float, 0>(nu2, g, insts, st, items, s);
+    if (shape) return prec == 0 ? up<double, 1>(nu2, g, insts, st, items, e2_mode, s)
+                                : up<float, 1>(nu2, g, insts, st, items, e2_mode, s);
+    return prec == 0 ? up<double, 0>(nu2, g, insts, st, items, e2_mode, s)
+                     : up<float, 0>(nu2, g, insts, st, items, e2_mode, s);
 }
 
 }  // namespace helm
