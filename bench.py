@@ -42,6 +42,10 @@ MAX_OUTER = 2000
 METRIC = "solves/s & stencil HBM GB/s (%peak) at relres 1e-8, mixed vs FP64; p50/p99"
 WORKLOAD = "gaussian_cavity_2d_1023_k1234"
 FP64_PEAK_TFLOPS = 1.25          # GB300 nominal FP64 rate (FMA = 2 flops)
+# DRAM bytes (read + write) per point of the residual kernel: one ncu capture of a
+# 4-instance 1023^2 launch (dram__bytes_read.sum + dram__bytes_write.sum = 168.07 + 67.24 MB
+# over 4 x 1023^2 points), scaled below to the points of an average launch
+RESIDUAL_DRAM_BYTES_PER_POINT = (168.065024e6 + 67.244032e6) / (4 * 1023 ** 2)
 
 
 def _peaks():
@@ -60,7 +64,7 @@ def _dist():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms while running."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -76,13 +80,16 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        t0 = time.time()                      # sampling is live before the timed region
+        while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -179,7 +186,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -361,12 +368,19 @@ def main():
         pts = by / (48 + 2 * eb)
         flops = 16.0 * pts
         ach = (flops / nl) / ((ms / nl) / 1e3) / 1e12
+        traffic = RESIDUAL_DRAM_BYTES_PER_POINT * pts / nl
+        hv = hbm_line(name, (nl, ms, by))
+        hv["traffic"] = traffic
         roofline = {"bound": "alu", "kernel": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                    "peak_kind": "nominal FP64 rate (no measured FP64 figure)",
-                    "traffic": None, "share": ms / total_kernel_ms,
+                    "peak_kind": "nominal FP64 rate (2 FP64 FMA per SM per clock x 152 SMs x "
+                                 "2.07 GHz = 1.26 TFLOP/s; no measured FP64 figure)",
+                    "traffic": traffic,
+                    "traffic_source": "ncu DRAM bytes per point of a 4-instance launch x the "
+                                      "average launch's points",
+                    "share": ms / total_kernel_ms,
                     "flops_per_launch": flops / nl, "avg_launch_us": 1e3 * ms / nl,
-                    "hbm_view": hbm_line(name, (nl, ms, by))}
+                    "hbm_view": hv}
     else:
         roofline = hbm_line(name, (nl, ms, by))
     mg = {k: v for k, v in prof.items() if k in ("smooth_restrict_2d", "prolong_smooth_2d") and v[0]}

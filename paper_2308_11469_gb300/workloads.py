@@ -1,0 +1,199 @@
+"""Timings of the method's other workloads on one GPU (one JSON line each).
+
+    python -m paper_2308_11469_gb300.workloads [--only cavity63,cube255,batch512]
+    python -m paper_2308_11469_gb300.workloads --replay cube255|cavity1023 [--steps 4] [--fp64]
+
+* cavity63  63x63 unit-square cavity, plane-wave wall data (theta = pi/6), f = 0:
+            k = 2 to relres 1e-10 and k = 5 (above k_max: the iteration diverges), mixed
+            and FP64 single solves; device ms per solve.
+* cube255   255^3 cube, plane-wave wall data + sine source, k = 4, relres 1e-8, mixed and
+            FP64 single solves with autotuned inner schedules; solves/s.
+* batch512  512 2D cavities, n in {63, 127, 255, 511}, k ~ U[0.5, 0.9 k_max], relres 1e-8:
+            one mixed batch (graph run to completion) against the plain FP64 form solving
+            the first 64 alone (per-solve rate).
+
+Device time comes from CUDA events on the current stream around each call.  The inputs
+are the seeded generators of ``inputs``; result accuracy against exact discrete
+solutions is checked by the GPU test-suite, not here.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+from . import binding as B
+from . import inputs
+
+
+def _dev_ms(fn, reps: int = 3):
+    import torch
+    best, out = None, None
+    for _ in range(reps):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        out = fn()
+        e.record()
+        e.synchronize()
+        t = s.elapsed_time(e)
+        best = t if best is None else min(best, t)
+    return best, out
+
+
+def cavity63(dev):
+    import torch
+    rows = []
+    for k, tol in ((2.0, 1e-10), (5.0, 1e-10)):
+        p = inputs.plane_wave_cavity_2d(k)
+        f = torch.from_numpy(p.f).to(dev)
+        g = torch.from_numpy(p.g).to(dev)
+        u = torch.zeros_like(g)
+        for prec, name in ((B.HELM_PREC_MIXED, "mixed"), (B.HELM_PREC_FP64, "fp64")):
+            plan = B.helm_plan_create(2, p.n, p.h, k, prec=prec)
+
+            def run():
+                u.zero_()
+                return B.helm_solve(plan, f, g, u, tol, 400)
+            run()
+            ms, (st, it, hist) = _dev_ms(run, 5)
+            rows.append({"workload": "cavity63", "k": k, "form": name, "tol": tol,
+                         "status": B.helm_status_str(st), "iters": it, "ms_per_solve": ms,
+                         "rho_pred": B.helm_plan_info(plan)[2]})
+            B.helm_plan_destroy(plan)
+    return rows
+
+
+def cube255(dev):
+    import torch
+    rows = []
+    p = inputs.plane_wave_sine_cube(4.0, seed=3, n=255)
+    f = torch.from_numpy(p.f).to(dev)
+    g = torch.from_numpy(p.g).to(dev)
+    u = torch.zeros_like(g)
+    for prec, name in ((B.HELM_PREC_MIXED, "mixed"), (B.HELM_PREC_FP64, "fp64")):
+        plan = B.helm_plan_create(3, p.n, p.h, p.k, prec=prec)
+        sched = B.helm_plan_autotune(plan, f, g, u, 1e-8, 2000)
+
+        def run():
+            u.zero_()
+            return B.helm_solve(plan, f, g, u, 1e-8, 2000)
+        ms, (st, it, hist) = _dev_ms(run, 3)
+        rows.append({"workload": "cube255", "k": p.k, "form": name, "status": B.helm_status_str(st),
+                     "iters": it, "ms_per_solve": ms, "solves_per_s": 1e3 / ms,
+                     "schedule": {"nu1": sched[0], "nu2": sched[1], "cycles": sched[2]}})
+        B.helm_plan_destroy(plan)
+    return rows
+
+
+def batch512(dev):
+    import torch
+    probs = inputs.batched_instances(count=512, seed=4)
+    F = [torch.from_numpy(q.f).to(dev) for q in probs]
+    G = [torch.from_numpy(q.g).to(dev) for q in probs]
+    U = [torch.zeros_like(x) for x in G]
+    # inner schedules tuned on the largest instance of the set
+    big = max(range(len(probs)), key=lambda i: (probs[i].n, probs[i].k))
+    q = probs[big]
+    scheds = {}
+    for prec in (B.HELM_PREC_MIXED, B.HELM_PREC_FP64):
+        pl = B.helm_plan_create(2, q.n, q.h, q.k, prec=prec)
+        scheds[prec] = B.helm_plan_autotune(pl, F[big], G[big], U[big], 1e-8, 3000)[:3]
+        B.helm_plan_destroy(pl)
+    batch = B.helm_batch_create(120 << 30)
+    B.helm_batch_set_cycle(batch, *scheds[B.HELM_PREC_MIXED])
+
+    def run_batch():
+        for x in U:
+            x.zero_()
+        ts = [B.helm_batch_submit_geom(batch, 2, q.n, q.h, q.k, B.HELM_PREC_MIXED, F[i], G[i], U[i],
+                                       1e-8, 3000) for i, q in enumerate(probs)]
+        B.helm_batch_step(batch, 0)
+        return [B.helm_batch_poll(batch, t, 3000) for t in ts]
+    run_batch()
+    ms, res = _dev_ms(run_batch, 3)
+    B.helm_batch_destroy(batch)
+    its = [r[1] for r in res]
+    rows = [{"workload": "batch512", "form": "mixed batch", "ms_per_batch": ms,
+             "solves_per_s": 512 * 1e3 / ms, "converged": int(sum(r[0] == B.HELM_CONVERGED for r in res)),
+             "iters_mean": float(np.mean(its)), "iters_max": int(max(its)),
+             "schedule": dict(zip(("nu1", "nu2", "cycles"), scheds[B.HELM_PREC_MIXED]))}]
+    tot, cnt = 0.0, 64
+    for i in range(cnt):
+        q = probs[i]
+        pl = B.helm_plan_create(2, q.n, q.h, q.k, prec=B.HELM_PREC_FP64)
+        B.helm_plan_set_cycle(pl, *scheds[B.HELM_PREC_FP64])
+
+        def one():
+            U[i].zero_()
+            return B.helm_solve(pl, F[i], G[i], U[i], 1e-8, 3000)
+        one()
+        t, _ = _dev_ms(one, 1)
+        tot += t
+        B.helm_plan_destroy(pl)
+    rows.append({"workload": "batch512", "form": "fp64 single (first 64 instances)",
+                 "solves_per_s": cnt * 1e3 / tot,
+                 "schedule": dict(zip(("nu1", "nu2", "cycles"), scheds[B.HELM_PREC_FP64]))})
+    return rows
+
+
+def replay(dev, which: str, steps: int, prec: int = B.HELM_PREC_MIXED):
+    """Per-kernel device time of `steps` outer steps of one solve, every launch made
+    directly between CUDA events (so a profiler sees each kernel; the graph's
+    conditional loop hides them): the 255^3 cube or the 1023^2 Gaussian cavity (k = 4)."""
+    import torch
+    p = (inputs.plane_wave_sine_cube(4.0, seed=3, n=255) if which == "cube255"
+         else inputs.gaussian_cavity_2d(4.0))
+    f = torch.from_numpy(p.f).to(dev)
+    g = torch.from_numpy(p.g).to(dev)
+    u = torch.zeros_like(g)
+    plan = B.helm_plan_create(p.D, p.n, p.h, p.k, prec=prec)
+    sched = B.helm_plan_autotune(plan, f, g, u, 1e-8, 2000)[:3]
+    batch = B.helm_batch_create(0)
+    B.helm_batch_set_cycle(batch, *sched)
+    u.zero_()
+    B.helm_batch_submit(batch, plan, f, g, u, 1e-8, 2000)
+    prof = B.helm_batch_profile(batch, steps)
+    B.helm_batch_destroy(batch)
+    B.helm_plan_destroy(plan)
+    rows = []
+    for kind, (nl, ms, by) in prof.items():
+        if nl:
+            rows.append({"workload": f"replay_{which}", "prec": "mixed" if prec else "fp64",
+                         "schedule": dict(zip(("nu1", "nu2", "cycles"), sched)), "kernel": kind,
+                         "launches": nl, "us_per_launch": 1e3 * ms / nl,
+                         "model_GBs": by / (ms / 1e3) / 1e9})
+    return rows
+
+
+WORKLOADS = {"cavity63": cavity63, "cube255": cube255, "batch512": batch512}
+
+
+def main(argv=None) -> int:
+    import torch
+
+    from . import build
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--only", default=",".join(WORKLOADS))
+    ap.add_argument("--replay", default=None, choices=["cube255", "cavity1023"],
+                    help="per-kernel replay of a few outer steps of one solve instead")
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--fp64", action="store_true", help="replay the plain FP64 form")
+    args = ap.parse_args(argv)
+    build.build()
+    B.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if args.replay:
+        for row in replay(dev, args.replay, args.steps,
+                          B.HELM_PREC_FP64 if args.fp64 else B.HELM_PREC_MIXED):
+            print(json.dumps(row), flush=True)
+        return 0
+    for name in args.only.split(","):
+        for row in WORKLOADS[name](dev):
+            print(json.dumps(row), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
