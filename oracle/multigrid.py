@@ -27,6 +27,11 @@ Components (levels have n_l = 2^(m-l) - 1 interior nodes per axis, h_l = 2^l h):
 * optionally (``exact_n``) a direct coarse-grid solver: the level with n == exact_n is
   not cycled but solved exactly (sine-basis solve of Delta_h e = r, zero walls), as the
   CUDA library does for its 2D complex64 hierarchies.
+
+``sigma`` >= 0 selects the shifted operator Delta_h - sigma of the general cavity
+iteration (Section 2.2, sigma = alpha - k^2; see ``general``) on every level: the local
+solve becomes e = (sum of neighbours - h^2 r) / (2D + sigma h^2), the residual
+r - (Delta_h - sigma) e, the one-node solve e = -h^2 r / (2D + sigma h^2).
 """
 from __future__ import annotations
 
@@ -46,26 +51,28 @@ def color_mask(D: int, n: int, color: int) -> np.ndarray:
     return (s % 2) == color
 
 
-def rbgs_half_sweep(E: np.ndarray, r: np.ndarray, h: float, color: int) -> None:
+def rbgs_half_sweep(E: np.ndarray, r: np.ndarray, h: float, color: int,
+                    sigma: float = 0.0) -> None:
     """In-place half-sweep on the padded iterate E for the interior right-hand side r."""
     D = E.ndim
     n = E.shape[0] - 2
     nbr = np.zeros(r.shape, dtype=E.dtype)
     for a in range(D):
         nbr = nbr + fd._shift(E, a, +1) + fd._shift(E, a, -1)
-    new = (nbr - (h * h) * r) / (2.0 * D)
+    new = (nbr - (h * h) * r) / (2.0 * D + sigma * h * h)
     mask = color_mask(D, n, color)
     inner = E[(slice(1, -1),) * D]
     inner[mask] = new[mask]
 
 
-def rbgs_sweep(E: np.ndarray, r: np.ndarray, h: float) -> None:
-    rbgs_half_sweep(E, r, h, 0)
-    rbgs_half_sweep(E, r, h, 1)
+def rbgs_sweep(E: np.ndarray, r: np.ndarray, h: float, sigma: float = 0.0) -> None:
+    rbgs_half_sweep(E, r, h, 0, sigma)
+    rbgs_half_sweep(E, r, h, 1, sigma)
 
 
-def poisson_residual(E: np.ndarray, r: np.ndarray, h: float) -> np.ndarray:
-    return r - fd.apply_laplacian(E, h)
+def poisson_residual(E: np.ndarray, r: np.ndarray, h: float, sigma: float = 0.0) -> np.ndarray:
+    """r - (Delta_h - sigma) E on the interior."""
+    return r - (fd.apply_laplacian(E, h) - sigma * fd.interior(E))
 
 
 def restrict_fw(rf: np.ndarray) -> np.ndarray:
@@ -112,30 +119,34 @@ def prolong_add(Ef: np.ndarray, Ec: np.ndarray) -> None:
     Ef[(slice(1, -1),) * D] += Q[(slice(1, -1),) * D]
 
 
-def coarse_solve(E: np.ndarray, r: np.ndarray, h: float) -> None:
-    """Exact solve on a single interior node (n = 1): -2D e / h^2 = r."""
+def coarse_solve(E: np.ndarray, r: np.ndarray, h: float, sigma: float = 0.0) -> None:
+    """Exact solve on a single interior node (n = 1): -(2D / h^2 + sigma) e = r."""
     D = E.ndim
-    E[(slice(1, 2),) * D] = -(h * h) * r / (2.0 * D)
+    E[(slice(1, 2),) * D] = -(h * h) * r / (2.0 * D + sigma * h * h)
 
 
 def vcycle(E: np.ndarray, r: np.ndarray, h: float, nu1: int = 2, nu2: int = 2,
-           exact_n: int | None = None) -> None:
+           exact_n: int | None = None, sigma: float = 0.0) -> None:
     """One V(nu1, nu2)-cycle on the padded iterate E (in place); a level with
     n == exact_n is solved exactly instead (whatever E held there)."""
     D = E.ndim
     n = E.shape[0] - 2
     if exact_n is not None and n == exact_n:
-        E[(slice(1, -1),) * D] = fd.dst_poisson(r, h)
+        if sigma == 0.0:
+            E[(slice(1, -1),) * D] = fd.dst_poisson(r, h)
+        else:
+            from .general import dst_shifted_poisson
+            E[(slice(1, -1),) * D] = dst_shifted_poisson(r, h, sigma)
         return
     if n == 1:
-        coarse_solve(E, r, h)
+        coarse_solve(E, r, h, sigma)
         return
     for _ in range(nu1):
-        rbgs_sweep(E, r, h)
-    rc = restrict_fw(poisson_residual(E, r, h))
+        rbgs_sweep(E, r, h, sigma)
+    rc = restrict_fw(poisson_residual(E, r, h, sigma))
     nc = rc.shape[0]
     Ec = np.zeros((nc + 2,) * D, dtype=E.dtype)
-    vcycle(Ec, rc, 2.0 * h, nu1, nu2, exact_n)
+    vcycle(Ec, rc, 2.0 * h, nu1, nu2, exact_n, sigma)
     prolong_add(E, Ec)
     for _ in range(nu2):
-        rbgs_sweep(E, r, h)
+        rbgs_sweep(E, r, h, sigma)

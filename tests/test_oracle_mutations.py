@@ -9,7 +9,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import fd, iteration as it, multigrid as mg
+from oracle import fd, general as gen, iteration as it, multigrid as mg
 from paper_2308_11469_gb300 import inputs
 
 
@@ -101,8 +101,40 @@ def pin_kmax():
     return abs(fd.k_max(2, 2 ** 12 - 1, 2.0 ** -12) - math.pi * math.sqrt(2)) < 1e-6
 
 
+def pin_general_hand():
+    # one interior node, alpha = 3, p = 2, k = 1, h = 1/2 (worked by hand):
+    # u^(1) = (6 + 5i)/18, relres_N = (sqrt(13)/18)^N, rho = sqrt(13)/18
+    f = np.full((1, 1), 2 - 1j)
+    g = np.full((3, 3), 0.5 + 0.25j)
+    res = gen.general_iteration(f, g, 0.5, 1.0, 3.0, 2.0, tol=1e-300, max_outer=3, keep_iterates=True)
+    q = math.sqrt(13) / 18
+    return (abs(res.iterates[1][1, 1] - (6 + 5j) / 18) < 1e-15
+            and np.allclose(res.relres, [1, q, q * q, q ** 3], rtol=1e-13, atol=0)
+            and abs(gen.rho_pred(2, 1, 0.5, 1.0, 3.0, 2.0) - q) < 1e-15)
+
+
+def pin_general_series():
+    # partial sums of G = -(alpha + i p)(Delta_h - sigma)^{-1}, matrices built here
+    n, h, k, alpha, p = 4, 0.2, 1.0, 4.0, 3.0
+    rng = np.random.default_rng(6)
+    f = _rand_c(rng, (n, n))
+    g = fd.padded_from(np.zeros((n, n), complex), _rand_c(rng, (n + 2, n + 2)))
+    T = (np.diag(-2.0 * np.ones(n)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)) / h ** 2
+    M = np.kron(np.eye(n), T) + np.kron(T, np.eye(n)) - (alpha - k * k) * np.eye(n * n)
+    Minv = np.linalg.inv(M)
+    b = fd.lifted_rhs(f, g, h).reshape(-1)
+    res = gen.general_iteration(f, g, h, k, alpha, p, tol=1e-300, max_outer=5, keep_iterates=True)
+    term, acc = Minv @ b, 0
+    for N in range(1, 6):
+        acc = acc + term
+        term = -(alpha + 1j * p) * (Minv @ term)
+        if np.linalg.norm(fd.interior(res.iterates[N]).reshape(-1) - acc) > 1e-12 * np.linalg.norm(acc):
+            return False
+    return True
+
+
 PINS = [pin_quadratic, pin_plane_wave, pin_hand_relres, pin_partial_sums, pin_sine_eigen,
-        pin_vcycle, pin_kmax]
+        pin_vcycle, pin_kmax, pin_general_hand, pin_general_series]
 
 
 def test_pins_pass_on_the_oracle():
@@ -147,18 +179,33 @@ def _restrict_unweighted(rf):
     return rf[(slice(1, None, 2),) * D].copy()
 
 
-def _half_sweep_wrong_h(E, r, h, color):
+def _half_sweep_wrong_h(E, r, h, color, sigma=0.0):
     D = E.ndim
     n = E.shape[0] - 2
     nbr = np.zeros(r.shape, dtype=E.dtype)
     for a in range(D):
         nbr = nbr + fd._shift(E, a, +1) + fd._shift(E, a, -1)
-    new = (nbr - h * r) / (2.0 * D)
+    new = (nbr - h * r) / (2.0 * D + sigma * h * h)
     mask = mg.color_mask(D, n, color)
     E[(slice(1, -1),) * D][mask] = new[mask]
 
 
+def _damping_wrong_sign(U, h, k, p):
+    return fd.apply_laplacian(U, h) + (k * k - 1j * p) * fd.interior(U)
+
+
+def _shift_dropped(D, n, h, sigma):
+    return fd.laplacian_matrix(D, n, h)
+
+
+def _rho_without_hypot(D, n, h, k, alpha, p):
+    return (alpha + p) / (fd.lambda_min(D, n, h) + alpha - k * k)
+
+
 MUTATIONS = [
+    (gen, "apply_damped_helmholtz", _damping_wrong_sign),
+    (gen, "shifted_laplacian_matrix", _shift_dropped),
+    (gen, "rho_pred", _rho_without_hypot),
     (fd, "apply_laplacian", _laplacian_no_minus_two),
     (fd, "apply_laplacian", _laplacian_one_axis_dropped),
     (fd, "apply_helmholtz", _helmholtz_wrong_sign),
