@@ -107,11 +107,24 @@ HELM_API helm_status helm_plan_create(helm_plan** out, int ndim, const int* n, d
                              int bc, int prec, void* cuda_stream);
 HELM_API helm_status helm_plan_destroy(helm_plan* plan);
 
-/* Closed forms of the plan (Section 2.4, Dirichlet case): lambda_min of -Delta_h,
- * k_max = sqrt(lambda_min), rho = k^2 / lambda_min; and the workspace bytes owned.
+/* Closed forms of the plan (Section 2.4, Dirichlet case): lambda_min of -Delta_h; the
+ * spectral radius rho of the iteration matrix G = -(alpha + i p)(Delta_h - sigma)^{-1},
+ * sigma = alpha - k^2: rho = sqrt(alpha^2 + p^2) / (lambda_min + sigma) (= k^2 / lambda_min
+ * for the default alpha = k^2, p = 0); k_max = the supremum of the k with rho < 1 at the
+ * plan's alpha and p: sqrt(lambda_min + alpha - sqrt(alpha^2 + p^2)), which is
+ * sqrt(lambda_min) when p = 0 (0 when no k qualifies); and the workspace bytes owned.
  * Any output pointer may be NULL. */
 HELM_API helm_status helm_plan_info(const helm_plan* plan, double* lambda_min, double* k_max,
                            double* rho_pred, size_t* workspace_bytes);
+
+/* General cavity iteration (Section 2.2, Eq. (2.4)-(2.8), Dirichlet wall): solve
+ * Delta u + (i p + k^2) u = f with the shift alpha >= k^2 and damping p >= 0, i.e. every
+ * outer step solves (Delta_h - sigma) e = r_N, sigma = alpha - k^2, with
+ * r_N = f - (Delta_h + k^2 + i p) u_N.  A new plan has alpha = k^2, p = 0.  Applies to
+ * the plan's later helm_solve / poisson_vcycle / helm_batch_submit calls (the V-cycle
+ * then solves (Delta_h - sigma) e = rhs).  HELM_EINVAL for a NULL plan, a non-finite
+ * value, p < 0 or alpha < k^2. */
+HELM_API helm_status helm_plan_set_cavity(helm_plan* plan, double alpha, double p);
 
 /* Shape of the plan's multigrid hierarchy (this project's inner solver; the paper leaves
  * the Poisson solver open, Section 3): *tail_n = the grid size from which one CTA per
@@ -137,7 +150,8 @@ HELM_API helm_status helm_plan_autotune(helm_plan* plan, const void* f, const vo
                                         int* cycles, double* best_ms);
 
 /*
- * Solve (Delta_h + k^2) u = f, u = g on the wall, by the outer Poisson iteration.
+ * Solve (Delta_h + k^2) u = f, u = g on the wall, by the outer Poisson iteration
+ * (with helm_plan_set_cavity: (Delta_h + k^2 + i p) u = f, inner operator Delta_h - sigma).
  *   f         interior complex128, n^D (device).
  *   g         padded complex128, (n+2)^D (device); only its wall ring is read.
  *   u         padded complex128, (n+2)^D (device).  In: the interior is the starting

@@ -44,6 +44,7 @@ _SIGS = {
                                  C.POINTER(C.c_double), C.POINTER(C.c_size_t)]),
     "helm_plan_set_cycle": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
     "helm_plan_coarse": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "helm_plan_set_cavity": (C.c_int, [_vp, C.c_double, C.c_double]),
     "helm_solve": (C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int),
                              C.POINTER(C.c_double)]),
     "helm_solve_ex": (C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int),
@@ -202,6 +203,11 @@ def helm_plan_coarse(plan: _Plan):
     t, x = C.c_int(), C.c_int()
     _check(load().helm_plan_coarse(plan.handle, C.byref(t), C.byref(x)), "helm_plan_coarse")
     return t.value, x.value
+
+
+def helm_plan_set_cavity(plan: _Plan, alpha: float, p: float) -> None:
+    """General cavity iteration: shift alpha >= k^2 and damping p >= 0."""
+    _check(load().helm_plan_set_cavity(plan.handle, float(alpha), float(p)), "helm_plan_set_cavity")
 
 
 def helm_plan_set_cycle(plan: _Plan, nu1: int, nu2: int, cycles: int = 1) -> None:

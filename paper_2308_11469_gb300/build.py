@@ -18,7 +18,10 @@ OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libhelm.so")
 SOURCES = ["engine.cu", "outer.cu", "vcycle.cu", "vcycle2d.cu", "tail.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code: no contraction of a*b+c into FMAs, so host arithmetic (descriptor constants,
+# closed forms) rounds the same on x86 and Arm hosts
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+         "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 

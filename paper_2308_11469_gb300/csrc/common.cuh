@@ -29,7 +29,8 @@ struct LevelDesc {
     int rows;     // n + 2 rows per z plane
     int pad_;
     double h;     // spacing 2^l h
-    void* e;      // padded iterate of Delta_h e = rhs (final iterate of a V-cycle)
+    double dinv;  // 1 / (2D + sigma h^2): the local solve's factor (host-computed)
+    void* e;      // padded iterate of (Delta_h - sigma) e = rhs (final iterate of a V-cycle)
     void* rhs;    // right-hand side (same indexing as e)
     void* e2;     // 2D fused path: the pre-smoothed iterate (same indexing as e)
 };
@@ -40,6 +41,8 @@ struct InstDesc {
     int res_tx, res_ty;         // residual tile grid (x tiles, y tiles); z tiles = n (3D)
     double h, k2, tol;
     double ih2, cdiag;          // 1/h^2 and k^2 - 2D/h^2 (the stencil's diagonal)
+    double sigma;               // alpha - k^2 >= 0: inner operator Delta_h - sigma
+    double damp;                // p >= 0: damping term i p u of Delta u + (i p + k^2) u = f
     double2* u[2];              // u[0] = caller's array, u[1] = library buffer
     const double2* f;
     const double2* g;

@@ -62,6 +62,7 @@ size_t layout(InstDesc& d, int D, int n, double h, double k, int prec, char* bas
     d.k2 = k * k;
     d.ih2 = 1.0 / (h * h);
     d.cdiag = d.k2 - 2.0 * D * d.ih2;
+    d.damp = 0.0;
     int nl = 0, lt = -1;
     for (int m = n; m >= 1 && nl < HELM_MAXLEV; m = (m - 1) / 2) {
         if (lt < 0 && m <= tail_n(D, prec)) lt = nl;
@@ -104,6 +105,7 @@ size_t layout(InstDesc& d, int D, int n, double h, double k, int prec, char* bas
     off += align256((size_t)2 * d.nres_blocks * sizeof(double));
     if (base) d.count = (unsigned int*)(base + off);
     off += 256;
+    set_shift(d, 0.0);
     return off;
 }
 
@@ -148,6 +150,7 @@ struct Engine {
     std::vector<MgItem> h_items;               // host copy of the multigrid work items
     std::vector<LaunchRec> vcyc_plain;         // one V-cycle from the current iterate
     int max_tail = 1;
+    int damp_any = 0;                          // some slot's instance has p != 0
     bool dirty = true;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -365,7 +368,11 @@ struct Engine {
         // the residual launch also ends the step (its last instance to finish sets the
         // loop condition), so a step has no separate check launch
         int nocc = 0;
-        for (int i = 0; i < cap; ++i) nocc += slots[i] ? 1 : 0;
+        damp_any = 0;
+        for (int i = 0; i < cap; ++i) {
+            nocc += slots[i] ? 1 : 0;
+            if (slots[i] && slots[i]->d.damp != 0.0) damp_any = 1;
+        }
         step.push_back({LaunchRec::RESID, 0, nres, nocc, 1, 1, b_res});
         vcyc_plain.clear();
         vcycle(vcyc_plain, false);
@@ -440,9 +447,11 @@ struct Engine {
             case LaunchRec::RESID:
                 if (L.color)      // folded step control: L.work instances, cap statuses
                     e = launch_residual(D, prec, d_desc, d_state, d_res + L.off, L.cnt, L.mode, s,
-                                        d_ctrl, cap, L.work, use_cond ? 1 : 0, (unsigned long long)cond);
+                                        d_ctrl, cap, L.work, use_cond ? 1 : 0, (unsigned long long)cond,
+                                        damp_any);
                 else
-                    e = launch_residual(D, prec, d_desc, d_state, d_res + L.off, L.cnt, L.mode, s);
+                    e = launch_residual(D, prec, d_desc, d_state, d_res + L.off, L.cnt, L.mode, s,
+                                        nullptr, 0, 0, 0, 0, damp_any);
                 break;
             case LaunchRec::CHECK:
                 e = launch_check(d_state, L.cnt, d_ctrl, use_cond ? 1 : 0,
@@ -539,7 +548,8 @@ struct Engine {
         HELM_CK(launch_set_ring(D, d_desc, slot, in->d.n, s));
         // the instance's own tile list names instance 0: offset the tables to its slot;
         // the last tile records relres_0 and the initial status
-        HELM_CK(launch_residual(D, prec, d_desc + slot, d_state + slot, in->d_res0, in->nres0, 0, s));
+        HELM_CK(launch_residual(D, prec, d_desc + slot, d_state + slot, in->d_res0, in->nres0, 0, s,
+                                nullptr, 0, 0, 0, 0, in->d.damp != 0.0 ? 1 : 0));
         g_launches += 2;
         return HELM_OK;
     }
@@ -653,6 +663,8 @@ double lambda_min_of(int D, int n, double h)
 struct helm_plan {
     int D, n, prec;
     double h, k;
+    double alpha, damp;        // general cavity (Section 2.2): alpha >= k^2, p >= 0
+    double sigma;              // alpha - k^2, computed once (0 exactly for alpha = k^2)
     cudaStream_t stream;
     Engine eng;
     Instance inst;
@@ -731,6 +743,9 @@ helm_status helm_plan_create(helm_plan** out, int ndim, const int* n, double h, 
     p->prec = prec;
     p->h = h;
     p->k = k;
+    p->alpha = k * k;
+    p->damp = 0.0;
+    p->sigma = 0.0;
     p->stream = (cudaStream_t)cuda_stream;
     helm_status st = p->eng.init(ndim, prec);
     if (st != HELM_OK) return st;
@@ -757,10 +772,29 @@ helm_status helm_plan_info(const helm_plan* p, double* lmin, double* kmax, doubl
 {
     if (!p) return HELM_EINVAL;
     const double l = lambda_min_of(p->D, p->n, p->h);
+    // G = -(alpha + i p)(Delta_h - sigma)^{-1}: rho = |alpha + i p| / (lambda_min + sigma);
+    // the iteration converges iff k^2 < lambda_min + alpha - |alpha + i p| (= lambda_min
+    // when p = 0, whatever alpha)
+    const double mod = std::hypot(p->alpha, p->damp);
+    const double q = l + p->alpha - mod;
     if (lmin) *lmin = l;
-    if (kmax) *kmax = std::sqrt(l);
-    if (rho) *rho = p->k * p->k / l;
+    if (kmax) *kmax = p->damp == 0.0 ? std::sqrt(l) : (q > 0.0 ? std::sqrt(q) : 0.0);
+    if (rho) *rho = mod / (l + p->sigma);
     if (ws) *ws = p->inst.ws_bytes + (2 * (size_t)p->inst.hist_cap + 1) * sizeof(double);
+    return HELM_OK;
+}
+
+helm_status helm_plan_set_cavity(helm_plan* p, double alpha, double damp)
+{
+    if (!p) return HELM_EINVAL;
+    if (!std::isfinite(alpha) || !std::isfinite(damp) || damp < 0.0) return HELM_EINVAL;
+    if (alpha < p->k * p->k) return HELM_EINVAL;          // Section 2.2: alpha >= k^2
+    const double k2 = p->k * p->k;
+    p->alpha = alpha;
+    p->damp = damp;
+    p->sigma = (alpha == k2) ? 0.0 : alpha - k2;
+    set_shift(p->inst.d, p->sigma);
+    p->inst.d.damp = damp;
     return HELM_OK;
 }
 
@@ -812,6 +846,8 @@ helm_status helm_solve_ex(helm_plan* p, const void* f, const void* g, void* u, d
     in.d.max_outer = max_outer;
     in.d.k2 = p->k * p->k;
     in.d.cdiag = in.d.k2 - 2.0 * p->D * in.d.ih2;
+    set_shift(in.d, p->sigma);
+    in.d.damp = p->damp;
     helm_status st = p->eng.prepare();
     if (st != HELM_OK) return st;
     st = p->eng.start_instance(0, p->stream);
@@ -990,7 +1026,7 @@ helm_status helm_batch_destroy(helm_batch* b)
 
 static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, int prec,
                                const void* f, const void* g, void* u, double tol, int max_outer,
-                               uint64_t* ticket)
+                               uint64_t* ticket, double sigma = 0.0, double damp = 0.0)
 {
     if (!b || !ticket) return HELM_EINVAL;
     if (D != 2 && D != 3) return HELM_EINVAL;
@@ -1044,6 +1080,8 @@ static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, 
     in->d.g = (const double2*)g;
     in->d.tol = tol;
     in->d.max_outer = max_outer;
+    set_shift(in->d, sigma);
+    in->d.damp = damp;
     E->slots[slot] = in;
     E->dirty = true;
     st = E->start_instance(slot, b->stream);
@@ -1065,7 +1103,8 @@ helm_status helm_batch_submit(helm_batch* b, const helm_plan* p, const void* f, 
                               void* u, double tol, int max_outer, uint64_t* ticket)
 {
     if (!p) return HELM_EINVAL;
-    return submit_impl(b, p->D, p->n, p->h, p->k, p->prec, f, g, u, tol, max_outer, ticket);
+    return submit_impl(b, p->D, p->n, p->h, p->k, p->prec, f, g, u, tol, max_outer, ticket,
+                       p->sigma, p->damp);
 }
 
 helm_status helm_batch_submit_geom(helm_batch* b, int ndim, int n, double h, double k, int prec,

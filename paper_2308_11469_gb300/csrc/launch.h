@@ -11,6 +11,15 @@ constexpr int TAIL_N_2D = 63;
 constexpr int TAIL_N_3D = 15;
 // FP64 keeps fewer levels in the one-CTA tail: on GB300 the FP64 rate of a single SM is
 // small, so FP64 coarse levels run faster spread over the GPU.
+// Set the inner operator's shift sigma (= alpha - k^2) of a descriptor and every level's
+// local-solve factor 1 / (2D + sigma h_l^2) (computed here once, in FP64, so that no
+// kernel thread divides).
+inline void set_shift(InstDesc& d, double sigma)
+{
+    d.sigma = sigma;
+    for (int l = 0; l < d.nlev; ++l) d.lev[l].dinv = 1.0 / (2.0 * d.D + sigma * d.lev[l].h * d.lev[l].h);
+}
+
 inline int tail_top(int D, int prec_is_fp64)
 {
     if (prec_is_fp64) return D == 2 ? 31 : 7;
@@ -71,11 +80,12 @@ cudaError_t setup_2d(int prec);
 // each instance forms relres, records the history and applies the status rule.
 // ctrl != nullptr folds the step control (k_check) into the launch: the last of the
 // launch's `ninst` instances to finish its residual scans `nscan` statuses, counts the
-// step and sets the WHILE node's condition (use_cond).
+// step and sets the WHILE node's condition (use_cond).  damp != 0: some instance has a
+// damping term p (the kernel variant that forms it).
 cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* st,
                             const ResItem* items, int nitems, int mode, cudaStream_t s,
                             int* ctrl = nullptr, int nscan = 0, int ninst = 0, int use_cond = 0,
-                            unsigned long long cond_handle = 0);
+                            unsigned long long cond_handle = 0, int damp = 0);
 int residual_tile_rows(int D);
 int residual_tile_planes(int D);
 int residual_tile_cols(int D);

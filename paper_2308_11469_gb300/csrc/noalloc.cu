@@ -128,6 +128,7 @@ extern "C" helm_status poisson_vcycle_noalloc(int ndim, int n, double h, int pre
         if (two) L.e2 = (void*)(off + 2 * sz);
         off += (two ? 3 : 2) * sz;
     }
+    set_shift(d, 0.0);                         // the alpha = k^2 cavity: Delta_h itself
     if (off > NOALLOC_BYTES) return fail(HELM_EUNSUPPORTED, "grid too large for the scratch array");
     unsigned char* base = nullptr;
     helm_status st = device_scratch(&base);

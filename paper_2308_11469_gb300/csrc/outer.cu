@@ -1,11 +1,13 @@
 // Outer (FP64) part of the Poisson iteration: the Helmholtz residual, the iterate
 // update, the norms and the convergence test.
 //
-// One outer step of Section 2.2's iteration (alpha = k^2, p = 0) in residual form:
-//   r_N = f - (Delta_h + k^2) u_N          (FP64, from the FP64 iterate)
-//   Delta_h e_N = r_N, e_N = 0 on the wall (multigrid, inner precision)
+// One outer step of Section 2.2's iteration in residual form:
+//   r_N = f - (Delta_h + k^2 + i p) u_N    (FP64, from the FP64 iterate)
+//   (Delta_h - sigma) e_N = r_N, e_N = 0 on the wall, sigma = alpha - k^2
+//                                          (multigrid, inner precision)
 //   u_{N+1} = u_N + e_N                    (FP64)
-// i.e. Delta_h u_{N+1} = f - k^2 u_N; with exact solves e_N = v_N + i w_N.  The wall
+// i.e. (Delta_h - sigma) u_{N+1} = f - (alpha + i p) u_N, Eq. (2.6) summed; with exact
+// solves e_N = v_N + i w_N.  alpha = k^2, p = 0 is the default.  The wall
 // data g enters through the ring of u (the Dirichlet nodes of Section 2.4 that are moved
 // to the right-hand side).
 //
@@ -205,7 +207,8 @@ __device__ void tile_done(const InstDesc& I, InstState* stp, int tile, T ta0, T 
 // ---------------------------------------------------------------------------
 constexpr int T2 = 32;
 
-template <typename R, int MODE>
+// DAMP: the instance has p != 0 (decided once per tile, outside the point loop)
+template <typename R, int MODE, bool DAMP>
 __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ insts,
                                                 InstState* __restrict__ st, const ResItem item,
                                                 double2* U, const StepCtl& c)
@@ -253,6 +256,7 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
     __syncthreads();
     const double mih2 = -I.ih2;
     const double mcdiag = -I.cdiag;
+    const double damp = I.damp;
     R r2 = 0;
     double r2d = 0.0, b2 = 0.0;
     const int lx = (threadIdx.x & 31) + 1;
@@ -270,6 +274,10 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
         double2 r;
         r.x = fma((a.x + b.x) + (d.x + u.x), mih2, fma(c.x, mcdiag, fv.x));
         r.y = fma((a.y + b.y) + (d.y + u.y), mih2, fma(c.y, mcdiag, fv.y));
+        if constexpr (DAMP) {                   // - i p u: the damping couples the lanes
+            r.x = fma(c.y, damp, r.x);
+            r.y = fma(c.x, -damp, r.y);
+        }
         const c2 ri = Inner<R>::from(r);
         rhs[gy * P + gx] = ri;
         if (MODE == 1) {
@@ -293,9 +301,9 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
 }
 
 // Grid-stride over the tiles of every instance (one tile per CTA when the grid covers
-// them all).
-template <typename R, int MODE>
-// 5 resident CTAs per SM (48 registers, no spills) keep more FP64 work in flight
+// them all).  DAMP: some instance of the launch has p != 0 (the others add p = 0).
+// 5 resident CTAs per SM (48 registers, no spills) keep more FP64 work in flight.
+template <typename R, int MODE, bool DAMP>
 __global__ void __launch_bounds__(NTH, 5)
 k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
              const ResItem* __restrict__ items, int nitems, StepCtl c)
@@ -304,7 +312,7 @@ k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     pdl_wait();
     pdl_trigger();
     for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
-        residual2d_tile<R, MODE>(insts, st, items[t], U, c);
+        residual2d_tile<R, MODE, DAMP>(insts, st, items[t], U, c);
         __syncthreads();                          // U is restaged by the next tile
     }
 }
@@ -346,7 +354,7 @@ __device__ __forceinline__ R stage_plane3d(double2* Up, const double2* __restric
     return emax2;
 }
 
-template <typename R, int MODE>
+template <typename R, int MODE, bool DAMP>
 __device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ insts,
                                                 InstState* __restrict__ st, const ResItem item,
                                                 double2 (*U)[P3], const StepCtl& c)
@@ -374,6 +382,7 @@ __device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ ins
     const long PL = (long)L0.pitch * L0.rows;
     const double mih2 = -I.ih2;
     const double mcdiag = -I.cdiag;
+    const double damp = I.damp;
     const int x0 = 1 + item.tx * T3X, y0 = 1 + item.ty * T3Y, z0 = 1 + item.tz * T3Z;
     const int z1 = min(z0 + T3Z - 1, n);
     const int lx = (threadIdx.x & 31) + 1, ly = (threadIdx.x >> 5) + 1;
@@ -401,6 +410,10 @@ __device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ ins
             double2 r;
             r.x = fma(((w.x + ea.x) + (so.x + no.x)) + (dn.x + up.x), mih2, fma(c.x, mcdiag, fv.x));
             r.y = fma(((w.y + ea.y) + (so.y + no.y)) + (dn.y + up.y), mih2, fma(c.y, mcdiag, fv.y));
+            if constexpr (DAMP) {               // - i p u: the damping couples the lanes
+                r.x = fma(c.y, damp, r.x);
+                r.y = fma(c.x, -damp, r.y);
+            }
             const c2 ri = Inner<R>::from(r);
             rhs[oe] = ri;
             if (MODE == 1) {
@@ -428,7 +441,7 @@ __device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ ins
     else tile_done<R>(I, stp, tile, r2, emax2, MODE, st, c);
 }
 
-template <typename R, int MODE>
+template <typename R, int MODE, bool DAMP>
 __global__ void __launch_bounds__(NTH, 4)
 k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
              const ResItem* __restrict__ items, int nitems, StepCtl c)
@@ -437,7 +450,7 @@ k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     pdl_wait();
     pdl_trigger();
     for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
-        residual3d_tile<R, MODE>(insts, st, items[t], U, c);
+        residual3d_tile<R, MODE, DAMP>(insts, st, items[t], U, c);
         __syncthreads();
     }
 }
@@ -591,7 +604,7 @@ static int g_res_grid = 152 * 5;               // SMs x resident residual CTAs (
 cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* st,
                             const ResItem* items, int nitems, int mode, cudaStream_t s,
                             int* ctrl, int nscan, int ninst, int use_cond,
-                            unsigned long long cond_handle)
+                            unsigned long long cond_handle, int damp)
 {
     if (nitems <= 0) return cudaSuccess;
     const StepCtl c{ctrl, nscan, ninst, use_cond, cond_handle};
@@ -600,8 +613,10 @@ cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* s
     const int grid = nitems;
     (void)g_res_grid;
 #define HELM_RES(K, RR)                                                                        \
-    (mode ? launch_k(K<RR, 1>, dim3(grid), dim3(NTH), 0, s, insts, st, items, nitems, c)        \
-          : launch_k(K<RR, 0>, dim3(grid), dim3(NTH), 0, s, insts, st, items, nitems, c))
+    (damp ? (mode ? launch_k(K<RR, 1, true>, dim3(grid), dim3(NTH), 0, s, insts, st, items, nitems, c)  \
+                  : launch_k(K<RR, 0, true>, dim3(grid), dim3(NTH), 0, s, insts, st, items, nitems, c)) \
+          : (mode ? launch_k(K<RR, 1, false>, dim3(grid), dim3(NTH), 0, s, insts, st, items, nitems, c) \
+                  : launch_k(K<RR, 0, false>, dim3(grid), dim3(NTH), 0, s, insts, st, items, nitems, c)))
     if (D == 2 && prec == 0) HELM_RES(k_residual2d, double);
     else if (D == 2) HELM_RES(k_residual2d, float);
     else if (prec == 0) HELM_RES(k_residual3d, double);
@@ -616,17 +631,21 @@ cudaError_t setup_outer()
     int dev = 0, sms = 0, per = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_residual2d<float, 1>, NTH, 0)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_residual2d<float, 1, false>, NTH, 0)) != cudaSuccess)
         return e;
     if (sms > 0 && per > 0) g_res_grid = sms * per;
-    if ((e = max_carveout(k_residual2d<float, 0>)) != cudaSuccess) return e;
-    if ((e = max_carveout(k_residual2d<float, 1>)) != cudaSuccess) return e;
-    if ((e = max_carveout(k_residual2d<double, 0>)) != cudaSuccess) return e;
-    if ((e = max_carveout(k_residual2d<double, 1>)) != cudaSuccess) return e;
-    if ((e = max_carveout(k_residual3d<float, 0>)) != cudaSuccess) return e;
-    if ((e = max_carveout(k_residual3d<float, 1>)) != cudaSuccess) return e;
-    if ((e = max_carveout(k_residual3d<double, 0>)) != cudaSuccess) return e;
-    if ((e = max_carveout(k_residual3d<double, 1>)) != cudaSuccess) return e;
+#define HELM_CO(K)                                                                   \
+    if ((e = max_carveout(K<float, 0, false>)) != cudaSuccess) return e;             \
+    if ((e = max_carveout(K<float, 1, false>)) != cudaSuccess) return e;             \
+    if ((e = max_carveout(K<double, 0, false>)) != cudaSuccess) return e;            \
+    if ((e = max_carveout(K<double, 1, false>)) != cudaSuccess) return e;            \
+    if ((e = max_carveout(K<float, 0, true>)) != cudaSuccess) return e;              \
+    if ((e = max_carveout(K<float, 1, true>)) != cudaSuccess) return e;              \
+    if ((e = max_carveout(K<double, 0, true>)) != cudaSuccess) return e;             \
+    if ((e = max_carveout(K<double, 1, true>)) != cudaSuccess) return e;
+    HELM_CO(k_residual2d)
+    HELM_CO(k_residual3d)
+#undef HELM_CO
     return max_carveout(k_check);
 }
 

@@ -34,11 +34,12 @@ constexpr int XP = 32;                 // row pitch of the tables and of T2 (ele
 constexpr int XT = 34;                 // row pitch of the transposed intermediate (float2)
 constexpr int XA = 4;                  // output rows per warp in the products
 constexpr int XG = (XN + XA - 1) / XA; // warps of the products (8)
-// scratch (floats): S[XN][XP], U[XN][XP] (tables), Tt [XN][XT] float2, T2 [XN][XP] float2
-constexpr int XTAB_FLOATS = 2 * XN * XP;
+// scratch (floats): S[XN][XP], U[XN][XP], s[XP] (tables), Tt [XN][XT] float2,
+// T2 [XN][XP] float2
+constexpr int XTAB_FLOATS = 2 * XN * XP + XP;
 constexpr int XSCR_FLOATS = XTAB_FLOATS + 2 * XN * XT + 2 * XN * XP;
 
-// S_ab = sin(pi a b / 32) and U_ab = 1 / (s_a + s_b), s_a = sin^2(pi a / 64), written by
+// S_ab = sin(pi a b / 32), U_ab = 1 / (s_a + s_b) and s_a = sin^2(pi a / 64), written by
 // setup_tail (host, double precision, rounded once)
 __device__ float g_xtab[XTAB_FLOATS];
 
@@ -81,7 +82,7 @@ template <typename T> __device__ __forceinline__ T cz() { T v; v.x = 0; v.y = 0;
 
 template <int D, typename R, int N, int NWARPS>
 __device__ __forceinline__ void t_sweep(typename C2<R>::T* E, const typename C2<R>::T* Rr, R h2,
-                                        int color)
+                                        R dinv, int color)
 {
     typedef typename C2<R>::T c2;
     constexpr int S = N + 2;
@@ -108,8 +109,8 @@ __device__ __forceinline__ void t_sweep(typename C2<R>::T* E, const typename C2<
         }
         const c2 rr = Rr[o];
         c2 v;
-        v.x = (sx - h2 * rr.x) * ((R)1 / (R)(2 * D));
-        v.y = (sy - h2 * rr.y) * ((R)1 / (R)(2 * D));
+        v.x = (sx - h2 * rr.x) * dinv;
+        v.y = (sy - h2 * rr.y) * dinv;
         E[o] = v;
     }
 }
@@ -119,7 +120,7 @@ __device__ __forceinline__ void t_sweep(typename C2<R>::T* E, const typename C2<
 // the general form yields with e = 0).
 template <int D, typename R, int N, int NWARPS, bool EZ>
 __device__ __forceinline__ void t_restrict(const typename C2<R>::T* E, const typename C2<R>::T* Rr,
-                                           typename C2<R>::T* Rc, R h)
+                                           typename C2<R>::T* Rc, R h, R sig)
 {
     typedef typename C2<R>::T c2;
     constexpr int S = N + 2;
@@ -160,8 +161,8 @@ __device__ __forceinline__ void t_restrict(const typename C2<R>::T* E, const typ
                             sx += f.x + g.x;
                             sy += f.y + g.y;
                         }
-                        ax += w * (rr.x - (sx - (R)(2 * D) * c.x) * ih2);
-                        ay += w * (rr.y - (sy - (R)(2 * D) * c.y) * ih2);
+                        ax += w * ((rr.x - (sx - (R)(2 * D) * c.x) * ih2) + sig * c.x);
+                        ay += w * ((rr.y - (sy - (R)(2 * D) * c.y) * ih2) + sig * c.y);
                     }
                 }
             }
@@ -268,10 +269,11 @@ __device__ __forceinline__ void x_cols(const float2* in, const float* Sm, float2
 }
 
 // out[a][b] = scale_ab * sum_x in_t[x][a] S[x][b] (scale_ab = c U_ab, or 1): lanes over
-// b, XA values of a per warp
+// b, XA values of a per warp.  With a shift (tau = sigma h^2 / 4 > 0) the scale is
+// c / (s_a + s_b + tau) instead of c U_ab.
 template <bool LEVEL_OUT>
 __device__ __forceinline__ void x_rows(const float2* in_t, const float* Sm, const float* Um, float c,
-                                       float2* out)
+                                       float tau, float2* out)
 {
     const int w = threadIdx.x >> 5, b = threadIdx.x & 31;
     if (w >= XG || b >= XN) return;
@@ -295,7 +297,8 @@ __device__ __forceinline__ void x_rows(const float2* in_t, const float* Sm, cons
         if (a >= XN) break;
         float2 v = acc[i];
         if (Um) {
-            const float wv = c * Um[a * XP + b];
+            const float* sv = Um + XN * XP;          // s_a follows the U table
+            const float wv = (tau == 0.f) ? c * Um[a * XP + b] : c / (sv[a] + sv[b] + tau);
             v.x *= wv;
             v.y *= wv;
         }
@@ -303,42 +306,46 @@ __device__ __forceinline__ void x_rows(const float2* in_t, const float* Sm, cons
     }
 }
 
-// E (level array of n = 31) <- exact solution of Delta_h e = Rr with zero walls, h the
-// level's spacing:  e = c S (U o (S r S)) S, c = -h^2 / (n+1)^2
-__device__ __forceinline__ void x_solve(float2* E, const float2* Rr, float* scr, float h)
+// E (level array of n = 31) <- exact solution of (Delta_h - sigma) e = Rr with zero walls,
+// h the level's spacing:  e = c S (U o (S r S)) S, c = -h^2 / (n+1)^2, with
+// U_ab = 1 / (s_a + s_b + sigma h^2 / 4)
+__device__ __forceinline__ void x_solve(float2* E, const float2* Rr, float* scr, float h, float sigma)
 {
     const float* Sm = scr;
     const float* Um = scr + XN * XP;
     float2* Tt = reinterpret_cast<float2*>(scr + XTAB_FLOATS);
     float2* T2 = Tt + XN * XT;
     const float c = -(h * h) / (float)((XN + 1) * (XN + 1));
+    const float tau = 0.25f * sigma * h * h;
     x_cols<true>(Rr, Sm, Tt);                  // S r          (transposed)
     __syncthreads();
-    x_rows<false>(Tt, Sm, Um, c, T2);          // c U o (S r S)
+    x_rows<false>(Tt, Sm, Um, c, tau, T2);     // c U o (S r S)
     __syncthreads();
     x_cols<false>(T2, Sm, Tt);                 // S (...)      (transposed)
     __syncthreads();
-    x_rows<true>(Tt, Sm, nullptr, 1.f, E);     // (S (...)) S
+    x_rows<true>(Tt, Sm, nullptr, 1.f, 0.f, E);  // (S (...)) S
     __syncthreads();
 }
 
 // One V(nu1, nu2)-cycle on the level of size N held at `base` (iterate, then rhs).
 // ez: the iterate is zero on entry (a coarse level, or a top level started from zero).
+// lv: this level's descriptor (its dinv); the next coarser level's follows it.
 template <int D, typename R, int N, int NWARPS>
-__device__ void t_vcycle(typename C2<R>::T* base, R h, int nu1, int nu2, float* xscr, bool ez)
+__device__ void t_vcycle(typename C2<R>::T* base, R h, R sig, const LevelDesc* lv, int nu1, int nu2,
+                         float* xscr, bool ez)
 {
     typedef typename C2<R>::T c2;
     c2* E = base;
     c2* Rr = base + Lv<D, N>::SZ;
     if constexpr (D == 2 && std::is_same<R, float>::value && N == XN && NWARPS == TNT / 32) {
-        x_solve(E, Rr, xscr, (float)h);
+        x_solve(E, Rr, xscr, (float)h, (float)sig);
         return;
     } else if constexpr (N == 1) {
         if (threadIdx.x == 0) {
             constexpr int S = 3;
             constexpr int o = ((D == 3) ? (S + 1) : 1) * S + Lv<D, 1>::HE;  // the single node
             const c2 rr = Rr[o];
-            const R c = -(h * h) / (R)(2 * D);
+            const R c = -(h * h) * (R)lv->dinv;      // -h^2 / (2D + sigma h^2)
             c2 v;
             v.x = c * rr.x;
             v.y = c * rr.y;
@@ -350,27 +357,28 @@ __device__ void t_vcycle(typename C2<R>::T* base, R h, int nu1, int nu2, float* 
         c2* Ec = base + 2 * Lv<D, N>::SZ;
         c2* Rc = Ec + Lv<D, NC>::SZ;
         const R h2 = h * h;
+        const R dinv = (R)lv->dinv;                     // 1 / (2D + sigma h^2)
         for (int s = 0; s < nu1; ++s) {
-            t_sweep<D, R, N, NWARPS>(E, Rr, h2, 0);
+            t_sweep<D, R, N, NWARPS>(E, Rr, h2, dinv, 0);
             tsync<NWARPS>();
-            t_sweep<D, R, N, NWARPS>(E, Rr, h2, 1);
+            t_sweep<D, R, N, NWARPS>(E, Rr, h2, dinv, 1);
             tsync<NWARPS>();
         }
-        if (ez && nu1 == 0) t_restrict<D, R, N, NWARPS, true>(E, Rr, Rc, h);
-        else t_restrict<D, R, N, NWARPS, false>(E, Rr, Rc, h);
+        if (ez && nu1 == 0) t_restrict<D, R, N, NWARPS, true>(E, Rr, Rc, h, sig);
+        else t_restrict<D, R, N, NWARPS, false>(E, Rr, Rc, h, sig);
         tsync<NWARPS>();
         if constexpr (NWARPS > 1 && NC <= 7) {
-            if (threadIdx.x < 32) t_vcycle<D, R, NC, 1>(Ec, h * (R)2, nu1, nu2, xscr, true);
+            if (threadIdx.x < 32) t_vcycle<D, R, NC, 1>(Ec, h * (R)2, sig, lv + 1, nu1, nu2, xscr, true);
             __syncthreads();
         } else {
-            t_vcycle<D, R, NC, NWARPS>(Ec, h * (R)2, nu1, nu2, xscr, true);
+            t_vcycle<D, R, NC, NWARPS>(Ec, h * (R)2, sig, lv + 1, nu1, nu2, xscr, true);
         }
         t_prolong<D, R, N, NWARPS>(E, Ec);
         tsync<NWARPS>();
         for (int s = 0; s < nu2; ++s) {
-            t_sweep<D, R, N, NWARPS>(E, Rr, h2, 0);
+            t_sweep<D, R, N, NWARPS>(E, Rr, h2, dinv, 0);
             tsync<NWARPS>();
-            t_sweep<D, R, N, NWARPS>(E, Rr, h2, 1);
+            t_sweep<D, R, N, NWARPS>(E, Rr, h2, dinv, 1);
             tsync<NWARPS>();
         }
     }
@@ -386,6 +394,7 @@ k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     c2* base = reinterpret_cast<c2*>(smem_raw);
     const MgItem item = items[blockIdx.x];
     const LevelDesc L0 = insts[item.inst].lev[item.level];   // host-written: read before the wait
+    const double sigma = insts[item.inst].sigma;
     pdl_wait();
     pdl_trigger();
     if (st[item.inst].status != HELM_ST_ACTIVE) return;
@@ -458,7 +467,8 @@ k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
         }
     }
     __syncthreads();
-    t_vcycle<D, R, N0, TNT / 32>(base, (R)L0.h, nu1, nu2, xscr, !le);
+    t_vcycle<D, R, N0, TNT / 32>(base, (R)L0.h, (R)sigma, &insts[item.inst].lev[item.level], nu1, nu2,
+                                 xscr, !le);
     c2* __restrict__ go = (c2*)L0.e;
     for (int r = warp; r < ROWS; r += TNT / 32) {
         const int y = r % N0 + 1;
@@ -552,6 +562,10 @@ cudaError_t setup_tail(int D, int prec)
                 tab[i * XP + j] = in ? (float)std::sin(pi * a * b / (XN + 1)) : 0.f;
                 tab[XN * XP + i * XP + j] = in ? (float)(1.0 / (sa * sa + sb * sb)) : 0.f;
             }
+        for (int i = 0; i < XP; ++i) {
+            const double si = std::sin(pi * (i + 1) / (2.0 * (XN + 1)));
+            tab[2 * XN * XP + i] = i < XN ? (float)(si * si) : 0.f;
+        }
         const cudaError_t e = cudaMemcpyToSymbol(g_xtab, tab, sizeof tab);
         if (e != cudaSuccess) return e;
     }

@@ -1,7 +1,8 @@
-// Geometric-multigrid kernels for the inner Poisson problem Delta_h e = rhs, e = 0 on
-// the wall: every outer step of the paper's iteration (Section 2.2, Eq. (2.6) with
-// alpha = k^2) is one such real Poisson problem per real/imaginary lane.  The paper
-// prescribes no inner solver; this file is the library's choice (see the header).
+// Geometric-multigrid kernels for the inner problem (Delta_h - sigma) e = rhs, e = 0 on
+// the wall: every outer step of the paper's iteration (Section 2.2, Eq. (2.6);
+// sigma = alpha - k^2, 0 for alpha = k^2) is one such real problem per real/imaginary
+// lane.  The paper prescribes no inner solver; this file is the library's choice (see
+// the header).  sigma enters the local solve (diagonal 2D/h^2 + sigma) and the residual.
 //
 // Generic (any D in {2, 3}, float or double) kernels over lists of (instance, level)
 // work items, blocks striding over each item's nodes:
@@ -46,7 +47,7 @@ k_rbgs(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const long P = L.pitch;
     const long PL = (long)L.pitch * L.rows;
     const R h2 = (R)(L.h * L.h);
-    const R inv = (R)1 / (R)(2 * D);
+    const R inv = (R)L.dinv;                       // 1 / (2D + sigma h^2)
     // mode 2: the iterate of every level is zero; mode 1: only levels > 0 are (their
     // iterate was cleared by the restriction); mode 0: plain half-sweep.
     const bool zi = (mode == 2) || (mode == 1 && item.level > 0);
@@ -108,6 +109,7 @@ k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const long P = F.pitch;
     const long PL = (long)F.pitch * F.rows;
     const R ih2 = (R)(1.0 / (F.h * F.h));
+    const R sig = (R)insts[item.inst].sigma;
     const R scale = (D == 3) ? (R)(1.0 / 64.0) : (R)(1.0 / 16.0);
     for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
          q += (long)gridDim.x * blockDim.x) {
@@ -132,8 +134,8 @@ k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
                         sy += f.y + g.y;
                     }
                     const c2 rr = r[o];
-                    ax += w * (rr.x - (sx - (R)(2 * D) * c.x) * ih2);
-                    ay += w * (rr.y - (sy - (R)(2 * D) * c.y) * ih2);
+                    ax += w * ((rr.x - (sx - (R)(2 * D) * c.x) * ih2) + sig * c.x);
+                    ay += w * ((rr.y - (sy - (R)(2 * D) * c.y) * ih2) + sig * c.y);
                 }
             }
         }

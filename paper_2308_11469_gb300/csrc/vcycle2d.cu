@@ -19,7 +19,8 @@
 // constant; a warp walks a row (lanes along x), the 8 warps stride over rows.
 //
 // The node colours, the update formula and the transfer weights are those of the
-// generic kernels (vcycle.cu), so both paths compute the same V-cycle.
+// generic kernels (vcycle.cu), so both paths compute the same V-cycle; the shift sigma
+// of the general cavity enters the local solve (diagonal 4 + sigma h^2) and the residual.
 #include "launch.h"
 #include "pdl.cuh"
 
@@ -49,7 +50,7 @@ template <typename R, int W, int TX, int TY>
 __device__ __forceinline__ void half_sweep(typename C2<R>::T* E0, typename C2<R>::T* E1,
                                            const typename C2<R>::T* R0,
                                            const typename C2<R>::T* R1, int gx0, int gy0,
-                                           int x0, int y0, int ring, int n, R h2, int color)
+                                           int x0, int y0, int ring, int n, R h2, R dinv, int color)
 {
     typedef typename C2<R>::T c2;
     typedef Planes<W> PL;
@@ -72,8 +73,8 @@ __device__ __forceinline__ void half_sweep(typename C2<R>::T* E0, typename C2<R>
             const c2 c = Eo[PL::at(lx, ly - 1)], d = Eo[PL::at(lx, ly + 1)];
             const c2 rr = Rc[o];
             c2 v;
-            v.x = ((a.x + b.x + c.x + d.x) - h2 * rr.x) * (R)0.25;
-            v.y = ((a.y + b.y + c.y + d.y) - h2 * rr.y) * (R)0.25;
+            v.x = ((a.x + b.x + c.x + d.x) - h2 * rr.x) * dinv;
+            v.y = ((a.y + b.y + c.y + d.y) - h2 * rr.y) * dinv;
             Ec[o] = v;
         }
     }
@@ -94,6 +95,7 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const MgItem item = items[blockIdx.y];
     const LevelDesc L = insts[item.inst].lev[item.level];
     const LevelDesc C = insts[item.inst].lev[item.level + 1];
+    const double sigma = insts[item.inst].sigma;
     pdl_wait();
     pdl_trigger();
     if (st[item.inst].status != HELM_ST_ACTIVE) return;
@@ -136,12 +138,14 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     cp_async_wait_all();
     __syncthreads();
     const R h2 = (R)(L.h * L.h);
+    const R dinv = (R)L.dinv;                      // 1 / (4 + sigma h^2)
+    const R sig = (R)sigma;
     int ring = 2 * NU + 1;
 #pragma unroll 1
     for (int s = 0; s < NU; ++s) {
-        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 0);
+        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, dinv, 0);
         __syncthreads();
-        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 1);
+        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, dinv, 1);
         __syncthreads();
     }
     // no pre-smoothing from a zero iterate: e2 stays zero (the ascent kernel knows it and
@@ -183,8 +187,8 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
                     const c2 u = Eo[PL::at(lx, ly - 1)], d = Eo[PL::at(lx, ly + 1)];
                     const c2 rr = Rc[o];
                     c2 v;
-                    v.x = rr.x - ((a.x + b.x + u.x + d.x) - (R)4 * c.x) * ih2;
-                    v.y = rr.y - ((a.y + b.y + u.y + d.y) - (R)4 * c.y) * ih2;
+                    v.x = (rr.x - ((a.x + b.x + u.x + d.x) - (R)4 * c.x) * ih2) + sig * c.x;
+                    v.y = (rr.y - ((a.y + b.y + u.y + d.y) - (R)4 * c.y) * ih2) + sig * c.y;
                     Rc[o] = v;
                 }
             }
@@ -314,12 +318,13 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     }
     __syncthreads();
     const R h2 = (R)(L.h * L.h);
+    const R dinv = (R)L.dinv;
     int ring = 2 * NU - 1;
 #pragma unroll 1
     for (int s = 0; s < NU; ++s) {
-        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 0);
+        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, dinv, 0);
         __syncthreads();
-        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, 1);
+        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, dinv, 1);
         __syncthreads();
     }
     c2* __restrict__ ge = (c2*)L.e;

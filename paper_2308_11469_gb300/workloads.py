@@ -1,6 +1,6 @@
 """Timings of the method's other workloads on one GPU (one JSON line each).
 
-    python -m paper_2308_11469_gb300.workloads [--only cavity63,cube255,batch512]
+    python -m paper_2308_11469_gb300.workloads [--only cavity63,cube255,batch512,damped1023]
     python -m paper_2308_11469_gb300.workloads --replay cube255|cavity1023 [--steps 4] [--fp64]
 
 * cavity63  63x63 unit-square cavity, plane-wave wall data (theta = pi/6), f = 0:
@@ -11,6 +11,8 @@
 * batch512  512 2D cavities, n in {63, 127, 255, 511}, k ~ U[0.5, 0.9 k_max], relres 1e-8:
             one mixed batch (graph run to completion) against the plain FP64 form solving
             the first 64 alone (per-solve rate).
+* damped1023  the 1023^2 Gaussian cavity at k = 4 with damping p in {0, 4, 8} (general
+            cavity iteration, alpha = k^2 and the rho-minimising alpha), mixed.
 
 Device time comes from CUDA events on the current stream around each call.  The inputs
 are the seeded generators of ``inputs``; result accuracy against exact discrete
@@ -167,7 +169,37 @@ def replay(dev, which: str, steps: int, prec: int = B.HELM_PREC_MIXED):
     return rows
 
 
-WORKLOADS = {"cavity63": cavity63, "cube255": cube255, "batch512": batch512}
+def damped1023(dev):
+    """The 1023^2 Gaussian cavity, k = 4, with damping p (Eq. (2.4)) and alpha = k^2 or the
+    alpha minimising rho, max(k^2, p^2 / (lambda_min - k^2)) (Section 2.2 allows any
+    alpha >= k^2): mixed single solves, autotuned schedule."""
+    import torch
+    q = inputs.gaussian_cavity_2d(4.0)
+    f = torch.from_numpy(q.f).to(dev)
+    g = torch.from_numpy(q.g).to(dev)
+    u = torch.zeros_like(g)
+    rows = []
+    for p in (0.0, 4.0, 8.0):
+        plan = B.helm_plan_create(2, q.n, q.h, q.k, prec=B.HELM_PREC_MIXED)
+        lam = B.helm_plan_info(plan)[0]
+        for alpha in sorted({q.k ** 2, max(q.k ** 2, p * p / (lam - q.k ** 2))}):
+            B.helm_plan_set_cavity(plan, alpha, p)
+            sched = B.helm_plan_autotune(plan, f, g, u, 1e-8, 3000)
+
+            def run():
+                u.zero_()
+                return B.helm_solve(plan, f, g, u, 1e-8, 3000)
+            ms, (st, it, hist) = _dev_ms(run, 3)
+            rows.append({"workload": "damped1023", "k": q.k, "p": p, "alpha": alpha, "form": "mixed",
+                         "status": B.helm_status_str(st), "iters": it, "ms_per_solve": ms,
+                         "solves_per_s": 1e3 / ms, "rho_pred": B.helm_plan_info(plan)[2],
+                         "schedule": {"nu1": sched[0], "nu2": sched[1], "cycles": sched[2]}})
+        B.helm_plan_destroy(plan)
+    return rows
+
+
+WORKLOADS = {"cavity63": cavity63, "cube255": cube255, "batch512": batch512,
+             "damped1023": damped1023}
 
 
 def main(argv=None) -> int:
