@@ -9,7 +9,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import fd, general as gen, iteration as it, multigrid as mg
+from oracle import exit_time as ex, fd, general as gen, iteration as it, multigrid as mg
 from paper_2308_11469_gb300 import inputs
 
 
@@ -133,8 +133,18 @@ def pin_general_series():
     return True
 
 
+def pin_exit_time():
+    # one node by hand (E = h^2/4 = 1/16 -> k_*^C = 4) and the square's continuum maximum
+    # 0.0736713... (torsion series, written out here) approached at O(h^2)
+    s = 0.125 - sum(4.0 * (-1) ** j / (math.pi ** 3 * (2 * j + 1) ** 3 * math.cosh((2 * j + 1) * math.pi / 2))
+                    for j in range(20))
+    e1 = abs(ex.max_exit_time(2, 63, 1 / 64) - s)
+    e2 = abs(ex.max_exit_time(2, 127, 1 / 128) - s)
+    return (abs(ex.k_star_c(2, 1, 0.5) - 4.0) < 1e-14 and 3.5 < e1 / e2 < 4.5 and e2 < 5e-6)
+
+
 PINS = [pin_quadratic, pin_plane_wave, pin_hand_relres, pin_partial_sums, pin_sine_eigen,
-        pin_vcycle, pin_kmax, pin_general_hand, pin_general_series]
+        pin_vcycle, pin_kmax, pin_general_hand, pin_general_series, pin_exit_time]
 
 
 def test_pins_pass_on_the_oracle():
@@ -202,7 +212,18 @@ def _rho_without_hypot(D, n, h, k, alpha, p):
     return (alpha + p) / (fd.lambda_min(D, n, h) + alpha - k * k)
 
 
+def _exit_time_wrong_source(D, n, h):
+    return np.real(fd.dst_poisson(-2.0 * np.ones((n,) * D), h))
+
+
+def _k_star_without_inverse(D, n, h, p=0.0):
+    q = ex.max_exit_time(D, n, h) - p
+    return math.sqrt(q) if q > 0 else 0.0
+
+
 MUTATIONS = [
+    (ex, "exit_time", _exit_time_wrong_source),
+    (ex, "k_star_c", _k_star_without_inverse),
     (gen, "apply_damped_helmholtz", _damping_wrong_sign),
     (gen, "shifted_laplacian_matrix", _shift_dropped),
     (gen, "rho_pred", _rho_without_hypot),
