@@ -126,6 +126,20 @@ HELM_API helm_status helm_plan_info(const helm_plan* plan, double* lambda_min, d
  * value, p < 0 or alpha < k^2. */
 HELM_API helm_status helm_plan_set_cavity(helm_plan* plan, double alpha, double p);
 
+/* Mean exit time and the sufficient bound of the cavity iteration (Section 2.2): E solves
+ * Delta_h E = -1 with E = 0 on the wall (Eq. (2.10), discretised as in Section 2.4; the
+ * plan's geometry and precision, solved by the outer iteration with k = 0 to
+ * relres <= tol in at most max_outer steps); k_*^C = sqrt(1 / max E - p) (Eq. (2.9), p the
+ * plan's damping; 0 when 1 / max E <= p).  No alpha >= k^2 satisfies the convergence
+ * condition of Section 2.2 above k_*^C.
+ *   E_out   padded (n+2)^D complex128 (device, 16-byte aligned) or NULL: receives E
+ *           (imaginary part 0, wall ring 0).
+ *   e_max, k_star   (host, may be NULL).
+ * Allocates a k = 0 plan and three (n+2)^D-sized buffers for the call; synchronous.
+ * Returns the solve's status (HELM_CONVERGED when tol was reached) or an error. */
+HELM_API helm_status helm_exit_time(helm_plan* plan, double tol, int max_outer, void* E_out,
+                                    double* e_max, double* k_star);
+
 /* Shape of the plan's multigrid hierarchy (this project's inner solver; the paper leaves
  * the Poisson solver open, Section 3): *tail_n = the grid size from which one CTA per
  * instance runs every coarser level in shared memory; *exact_n = the size of the level

@@ -45,6 +45,8 @@ _SIGS = {
     "helm_plan_set_cycle": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
     "helm_plan_coarse": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "helm_plan_set_cavity": (C.c_int, [_vp, C.c_double, C.c_double]),
+    "helm_exit_time": (C.c_int, [_vp, C.c_double, C.c_int, _vp, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double)]),
     "helm_solve": (C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int),
                              C.POINTER(C.c_double)]),
     "helm_solve_ex": (C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int),
@@ -208,6 +210,19 @@ def helm_plan_coarse(plan: _Plan):
 def helm_plan_set_cavity(plan: _Plan, alpha: float, p: float) -> None:
     """General cavity iteration: shift alpha >= k^2 and damping p >= 0."""
     _check(load().helm_plan_set_cavity(plan.handle, float(alpha), float(p)), "helm_plan_set_cavity")
+
+
+def helm_exit_time(plan: _Plan, tol: float = 1e-10, max_outer: int = 200, E_out=None):
+    """Mean exit time (Delta_h E = -1, E = 0 on the wall) and k_*^C = sqrt(1/max E - p).
+    E_out: optional padded complex128 device tensor receiving E.  Returns
+    (status, max E, k_*^C)."""
+    import torch
+    D, n = plan.D, plan.n
+    pe = None if E_out is None else _ptr(E_out, torch.complex128, (n + 2,) * D, "E_out")
+    em, ks = C.c_double(), C.c_double()
+    st = _check(load().helm_exit_time(plan.handle, float(tol), int(max_outer), pe, C.byref(em),
+                                      C.byref(ks)), "helm_exit_time")
+    return st, em.value, ks.value
 
 
 def helm_plan_set_cycle(plan: _Plan, nu1: int, nu2: int, cycles: int = 1) -> None:

@@ -808,6 +808,56 @@ helm_status helm_plan_coarse(const helm_plan* p, int* tail_n, int* exact_n)
     return HELM_OK;
 }
 
+helm_status helm_exit_time(helm_plan* p, double tol, int max_outer, void* E_out, double* emax,
+                           double* kstar)
+{
+    if (!p || !(tol >= 0.0) || max_outer < 1) return HELM_EINVAL;
+    if (E_out && check_ptr(E_out)) return HELM_EINVAL;
+    // Delta_h E = -1, E = 0 on the wall: the outer iteration with k = 0 (its steps are
+    // multigrid cycles refined in FP64), on a plan of the same geometry and precision
+    helm_plan* q = nullptr;
+    const int nn[3] = {p->n, p->n, p->n};
+    helm_status st = helm_plan_create(&q, p->D, nn, p->h, 0.0, HELM_BC_DIRICHLET, p->prec, p->stream);
+    if (st != HELM_OK) return st;
+    q->eng.nu1 = p->eng.nu1;
+    q->eng.nu2 = p->eng.nu2;
+    q->eng.cycles = p->eng.cycles;
+    const size_t fb = p->points() * 16, ub = p->padded() * 16;
+    char* buf = nullptr;
+    if (cudaMalloc((void**)&buf, fb + 2 * ub + 256) != cudaSuccess) {
+        cudaGetLastError();
+        helm_plan_destroy(q);
+        return HELM_ENOMEM;
+    }
+    void* f = buf;
+    void* g = buf + fb;
+    void* u = buf + fb + ub;
+    unsigned long long* dmax = (unsigned long long*)(buf + fb + 2 * ub);
+    auto done = [&](helm_status s) { cudaFree(buf); helm_plan_destroy(q); return s; };
+    if (launch_fill_c128(f, (long)p->points(), -1.0, 0.0, p->stream) != cudaSuccess ||
+        cudaMemsetAsync(g, 0, 2 * ub + 256, p->stream) != cudaSuccess)
+        return done(HELM_ECUDA);
+    int iters = 0;
+    st = helm_solve(q, f, g, u, tol, max_outer, &iters, nullptr);
+    if (st < 0) return done(st);
+    unsigned long long bits = 0;
+    if (launch_max_re(p->D, p->n, u, dmax, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&bits, dmax, sizeof bits, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
+        return done(HELM_ECUDA);
+    if (E_out && cudaMemcpyAsync(E_out, u, ub, cudaMemcpyDeviceToDevice, p->stream) != cudaSuccess)
+        return done(HELM_ECUDA);
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return done(HELM_ECUDA);
+    g_launches += 2;
+    double m;
+    memcpy(&m, &bits, sizeof m);
+    if (emax) *emax = m;
+    if (kstar) {
+        const double r = (m > 0.0) ? 1.0 / m - p->damp : -1.0;
+        *kstar = r > 0.0 ? std::sqrt(r) : 0.0;
+    }
+    return done(st);
+}
+
 helm_status helm_plan_set_cycle(helm_plan* p, int nu1, int nu2, int cycles)
 {
     if (!p) return HELM_EINVAL;

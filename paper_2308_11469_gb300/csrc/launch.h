@@ -92,6 +92,9 @@ int residual_tile_cols(int D);
 // Any instance still iterating?  Counts the step, sets the while-loop condition.
 cudaError_t launch_check(const InstState* st, int ninst, int* ctrl, int use_cond,
                          unsigned long long cond_handle, cudaStream_t s);
+// constant fill of a complex128 array; max Re over a padded array's interior (>= 0)
+cudaError_t launch_fill_c128(void* p, long count, double re, double im, cudaStream_t s);
+cudaError_t launch_max_re(int D, int n, const void* u, unsigned long long* out, cudaStream_t s);
 cudaError_t run_fp_bits_check(int count, unsigned long long seed, unsigned long long* bad_host);
 // u[0] and u[1] rings := g ring
 cudaError_t launch_set_ring(int D, const InstDesc* insts, int inst, int n, cudaStream_t s);

@@ -531,6 +531,43 @@ __global__ void k_unpack(const InstDesc* __restrict__ insts, int inst, void* __r
     }
 }
 
+// Mean exit time support (Eq. (2.10)): the constant source, and max Re(u) over the interior
+// of a padded array, clamped at 0 (E >= 0): block maxima, then an atomic maximum on the bit
+// patterns (non-negative doubles order as their bits), so the result is exact and order-free.
+__global__ void k_fill_c128(double2* __restrict__ p, long count, double re, double im)
+{
+    pdl_wait();
+    pdl_trigger();
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < count; q += (long)gridDim.x * blockDim.x)
+        p[q] = make_double2(re, im);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256)
+k_max_re(const double2* __restrict__ u, int n, unsigned long long* __restrict__ out)
+{
+    pdl_wait();
+    pdl_trigger();
+    const long S = n + 2;
+    const long total = (D == 3) ? (long)n * n * n : (long)n * n;
+    double m = 0.0;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
+        const long x = q % n + 1, y = (q / n) % n + 1, z = (D == 3) ? q / ((long)n * n) + 1 : 0;
+        const double v = u[((D == 3) ? (z * S + y) : y) * S + x].x;
+        m = fmax(m, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ double sw[8];
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b = fmax(b, sw[i]);
+        atomicMax(out, (unsigned long long)__double_as_longlong(b));
+    }
+}
+
 // Self-test of the integer-pipe conversions against the hardware conversions on random
 // values of the binary32 range, exact ties, and the special values.
 __device__ __forceinline__ unsigned long long splitmix(unsigned long long x)
@@ -653,6 +690,20 @@ cudaError_t launch_check(const InstState* st, int ninst, int* ctrl, int use_cond
                          unsigned long long cond_handle, cudaStream_t s)
 {
     launch_k(k_check, dim3(1), dim3(256), 0, s, st, ninst, ctrl, use_cond, cond_handle);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_c128(void* p, long count, double re, double im, cudaStream_t s)
+{
+    launch_k(k_fill_c128, dim3(blocks_for(count)), dim3(256), 0, s, (double2*)p, count, re, im);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_re(int D, int n, const void* u, unsigned long long* out, cudaStream_t s)
+{
+    const long work = (D == 3) ? (long)n * n * n : (long)n * n;
+    if (D == 2) launch_k(k_max_re<2>, dim3(blocks_for(work)), dim3(256), 0, s, (const double2*)u, n, out);
+    else launch_k(k_max_re<3>, dim3(blocks_for(work)), dim3(256), 0, s, (const double2*)u, n, out);
     return cudaGetLastError();
 }
 

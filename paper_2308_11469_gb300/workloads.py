@@ -1,6 +1,6 @@
 """Timings of the method's other workloads on one GPU (one JSON line each).
 
-    python -m paper_2308_11469_gb300.workloads [--only cavity63,cube255,batch512,damped1023]
+    python -m paper_2308_11469_gb300.workloads [--only cavity63,cube255,batch512,damped1023,exit1023]
     python -m paper_2308_11469_gb300.workloads --replay cube255|cavity1023 [--steps 4] [--fp64]
 
 * cavity63  63x63 unit-square cavity, plane-wave wall data (theta = pi/6), f = 0:
@@ -13,6 +13,7 @@
             the first 64 alone (per-solve rate).
 * damped1023  the 1023^2 Gaussian cavity at k = 4 with damping p in {0, 4, 8} (general
             cavity iteration, alpha = k^2 and the rho-minimising alpha), mixed.
+* exit1023  mean exit time and k_*^C of the 1023^2 square and the 255^3 cube.
 
 Device time comes from CUDA events on the current stream around each call.  The inputs
 are the seeded generators of ``inputs``; result accuracy against exact discrete
@@ -198,8 +199,24 @@ def damped1023(dev):
     return rows
 
 
+def exit1023(dev):
+    """Mean exit time of the 1023^2 square and 255^3 cube (Delta_h E = -1) and k_*^C."""
+    import torch  # noqa: F401  (device context)
+    rows = []
+    for D, n in ((2, 1023), (3, 255)):
+        for prec, name, tol in ((B.HELM_PREC_MIXED, "mixed", 1e-8), (B.HELM_PREC_FP64, "fp64", 1e-10)):
+            plan = B.helm_plan_create(D, n, 1.0 / (n + 1), 1.0, prec=prec)
+            B.helm_exit_time(plan, tol, 200)
+            ms, (st, emax, kstar) = _dev_ms(lambda: B.helm_exit_time(plan, tol, 200), 3)
+            rows.append({"workload": "exit_time", "D": D, "n": n, "form": name, "tol": tol,
+                         "status": B.helm_status_str(st), "max_E": emax, "k_star_C": kstar,
+                         "ms": ms})
+            B.helm_plan_destroy(plan)
+    return rows
+
+
 WORKLOADS = {"cavity63": cavity63, "cube255": cube255, "batch512": batch512,
-             "damped1023": damped1023}
+             "damped1023": damped1023, "exit1023": exit1023}
 
 
 def main(argv=None) -> int:
