@@ -140,6 +140,19 @@ HELM_API helm_status helm_plan_set_cavity(helm_plan* plan, double alpha, double 
 HELM_API helm_status helm_exit_time(helm_plan* plan, double tol, int max_outer, void* E_out,
                                     double* e_max, double* k_star);
 
+/* Spectral radius of the iteration matrix G = -(alpha + i p)(Delta_h - sigma)^{-1}
+ * (Section 2.4: the partial sums converge iff rho(G) < 1), measured by power iteration on
+ * the GPU: v <- M^{-1} v / ||M^{-1} v|| with M = Delta_h - sigma (zero walls) applied as
+ * `cycles` multigrid cycles of the plan's schedule from zero, in the plan's inner
+ * precision, starting from the constant vector; rho = |alpha + i p| ||M^{-1} v||.
+ * Stops when successive estimates agree to tol (relative) or after max_iters.
+ *   rho, iters_done   (host, may be NULL).
+ * Returns HELM_OK when converged, HELM_MAXITER otherwise, or an error.  Synchronous;
+ * allocates a small reduction buffer.  (For this Dirichlet cavity rho has the closed form
+ * of helm_plan_info; the measurement checks the operator the solver actually applies.) */
+HELM_API helm_status helm_spectral_radius(helm_plan* plan, int max_iters, double tol, int cycles,
+                                          double* rho, int* iters_done);
+
 /* Shape of the plan's multigrid hierarchy (this project's inner solver; the paper leaves
  * the Poisson solver open, Section 3): *tail_n = the grid size from which one CTA per
  * instance runs every coarser level in shared memory; *exact_n = the size of the level

@@ -47,6 +47,8 @@ _SIGS = {
     "helm_plan_set_cavity": (C.c_int, [_vp, C.c_double, C.c_double]),
     "helm_exit_time": (C.c_int, [_vp, C.c_double, C.c_int, _vp, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
+    "helm_spectral_radius": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_int)]),
     "helm_solve": (C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int),
                              C.POINTER(C.c_double)]),
     "helm_solve_ex": (C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int),
@@ -223,6 +225,14 @@ def helm_exit_time(plan: _Plan, tol: float = 1e-10, max_outer: int = 200, E_out=
     st = _check(load().helm_exit_time(plan.handle, float(tol), int(max_outer), pe, C.byref(em),
                                       C.byref(ks)), "helm_exit_time")
     return st, em.value, ks.value
+
+
+def helm_spectral_radius(plan: _Plan, max_iters: int = 200, tol: float = 1e-10, cycles: int = 8):
+    """rho(G) by GPU power iteration; returns (status, rho, iterations)."""
+    r, n = C.c_double(), C.c_int()
+    st = _check(load().helm_spectral_radius(plan.handle, int(max_iters), float(tol), int(cycles),
+                                            C.byref(r), C.byref(n)), "helm_spectral_radius")
+    return st, r.value, n.value
 
 
 def helm_plan_set_cycle(plan: _Plan, nu1: int, nu2: int, cycles: int = 1) -> None:

@@ -990,6 +990,67 @@ helm_status helm_plan_autotune(helm_plan* p, const void* f, const void* g, void*
     return HELM_OK;
 }
 
+helm_status helm_spectral_radius(helm_plan* p, int max_iters, double tol, int cycles, double* rho,
+                                 int* iters_done)
+{
+    if (!p || max_iters < 1 || !(tol >= 0.0) || cycles < 1 || cycles > 64) return HELM_EINVAL;
+    Engine& E = p->eng;
+    const int pr = p->prec == HELM_PREC_FP64 ? 0 : 1;
+    // one V-cycle of the plan's schedule from the current iterate, on instance 0
+    const int sc = E.cycles;
+    E.cycles = 1;
+    helm_status st = E.rebuild_plan();
+    E.cycles = sc;
+    E.dirty = true;
+    E.plan_sig.clear();
+    E.graph_sig.clear();
+    if (st != HELM_OK) return st;
+    double* buf = nullptr;
+    const int nb = power_iteration_blocks();
+    if (cudaMalloc((void**)&buf, (nb + 1) * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return HELM_ENOMEM; }
+    InstState act;
+    memset(&act, 0, sizeof act);
+    act.status = HELM_ST_ACTIVE;
+    const double npts = (double)p->points();
+    double mu = 0.0, prev = -1.0;
+    int it = 0;
+    auto fail = [&](helm_status s) { cudaFree(buf); return s; };
+    if (cudaMemcpyAsync(E.d_desc, &p->inst.d, sizeof(InstDesc), cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(E.d_state, &act, sizeof act, cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+        launch_lev_fill(p->D, pr, E.d_desc, 1, 1.0 / std::sqrt(npts), p->stream) != cudaSuccess)
+        return fail(HELM_ECUDA);
+    while (it < max_iters) {
+        ++it;
+        // w = M^{-1} v by `cycles` cycles from zero (M = Delta_h - sigma, zero walls)
+        if (launch_lev_fill(p->D, pr, E.d_desc, 0, 0.0, p->stream) != cudaSuccess) return fail(HELM_ECUDA);
+        for (int c = 0; c < cycles; ++c) {
+            st = E.enqueue(E.vcyc_plain, p->stream, false);
+            if (st != HELM_OK) return fail(st);
+        }
+        double s2 = 0.0;
+        if (launch_lev_sumsq(p->D, pr, E.d_desc, buf, buf + nb, p->stream) != cudaSuccess ||
+            cudaMemcpyAsync(&s2, buf + nb, sizeof s2, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+            cudaStreamSynchronize(p->stream) != cudaSuccess)
+            return fail(HELM_ECUDA);
+        g_launches += (uint64_t)cycles * E.vcyc_plain.size() + 3;
+        mu = std::sqrt(s2);                     // ||M^{-1} v|| with ||v|| = 1
+        if (!(mu > 0.0) || !std::isfinite(mu)) return fail(HELM_ENONFINITE);
+        if (launch_lev_scale(p->D, pr, E.d_desc, 1.0 / mu, p->stream) != cudaSuccess) return fail(HELM_ECUDA);
+        if (prev > 0.0 && std::fabs(mu - prev) <= tol * mu) break;
+        prev = mu;
+    }
+    InstState idle;
+    memset(&idle, 0, sizeof idle);
+    idle.status = HELM_ST_IDLE;
+    cudaMemcpyAsync(E.d_state, &idle, sizeof idle, cudaMemcpyHostToDevice, p->stream);
+    cudaStreamSynchronize(p->stream);
+    cudaFree(buf);
+    // G = -(alpha + i p) M^{-1}: |eigenvalue| = |alpha + i p| / (lambda_m + sigma)
+    if (rho) *rho = std::hypot(p->alpha, p->damp) * mu;
+    if (iters_done) *iters_done = it;
+    return (prev > 0.0 && std::fabs(mu - prev) <= tol * mu) ? HELM_OK : HELM_MAXITER;
+}
+
 helm_status poisson_vcycle(helm_plan* p, const void* rhs, void* e, int nu1, int nu2)
 {
     if (!p) return HELM_EINVAL;

@@ -95,6 +95,14 @@ cudaError_t launch_check(const InstState* st, int ninst, int* ctrl, int use_cond
 // constant fill of a complex128 array; max Re over a padded array's interior (>= 0)
 cudaError_t launch_fill_c128(void* p, long count, double re, double im, cudaStream_t s);
 cudaError_t launch_max_re(int D, int n, const void* u, unsigned long long* out, cudaStream_t s);
+// power iteration on the finest level of instance 0 (interior nodes): fill e (which = 0)
+// or rhs (1) with a real constant; out = sum |e|^2 (partial: power_iteration_blocks()
+// doubles); rhs = sc * e
+cudaError_t launch_lev_fill(int D, int prec, const InstDesc* insts, int which, double value, cudaStream_t s);
+cudaError_t launch_lev_sumsq(int D, int prec, const InstDesc* insts, double* partial, double* out,
+                             cudaStream_t s);
+cudaError_t launch_lev_scale(int D, int prec, const InstDesc* insts, double sc, cudaStream_t s);
+int power_iteration_blocks();
 cudaError_t run_fp_bits_check(int count, unsigned long long seed, unsigned long long* bad_host);
 // u[0] and u[1] rings := g ring
 cudaError_t launch_set_ring(int D, const InstDesc* insts, int inst, int n, cudaStream_t s);

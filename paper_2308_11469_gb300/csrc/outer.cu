@@ -568,6 +568,87 @@ k_max_re(const double2* __restrict__ u, int n, unsigned long long* __restrict__ 
     }
 }
 
+// Power iteration support on the finest level's arrays (interior nodes only; the rings
+// stay zero): fill, sum of squares (fixed-order block partials, then one block in order),
+// rhs = s * e.
+constexpr int PI_BLOCKS = 512;
+
+template <int D>
+__device__ __forceinline__ long lev_off(const LevelDesc& L, long q)
+{
+    const int n = L.n;
+    const long x = q % n + 1, y = (q / n) % n + 1, z = (D == 3) ? q / ((long)n * n) + 1 : 0;
+    return ((D == 3) ? (z * L.rows + y) : y) * (long)L.pitch + x;
+}
+
+template <int D, typename R>
+__global__ void k_lev_fill(const InstDesc* __restrict__ insts, int which, double re)
+{
+    pdl_wait();
+    pdl_trigger();
+    typedef typename C2<R>::T c2;
+    const LevelDesc L = insts[0].lev[0];
+    c2* a = (c2*)(which ? L.rhs : L.e);
+    const long total = (D == 3) ? (long)L.n * L.n * L.n : (long)L.n * L.n;
+    c2 v;
+    v.x = (R)re;
+    v.y = (R)0;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x)
+        a[lev_off<D>(L, q)] = v;
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(256)
+k_lev_sumsq(const InstDesc* __restrict__ insts, double* __restrict__ partial)
+{
+    pdl_wait();
+    pdl_trigger();
+    typedef typename C2<R>::T c2;
+    const LevelDesc L = insts[0].lev[0];
+    const c2* a = (const c2*)L.e;
+    const long total = (D == 3) ? (long)L.n * L.n * L.n : (long)L.n * L.n;
+    double acc = 0.0;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
+        const c2 v = a[lev_off<D>(L, q)];
+        acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    }
+    __shared__ double sa[8], sm[8];
+    double m = 0.0, ra = 0.0, rm = 0.0;
+    block_reduce<double>(acc, m, ra, rm, sa, sm, true);
+    if (threadIdx.x == 0) partial[blockIdx.x] = ra;
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partial, int nb, double* __restrict__ out)
+{
+    pdl_wait();
+    pdl_trigger();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nb; ++i) s += partial[i];
+        *out = s;
+    }
+}
+
+template <int D, typename R>
+__global__ void k_lev_scale(const InstDesc* __restrict__ insts, double sc)
+{
+    pdl_wait();
+    pdl_trigger();
+    typedef typename C2<R>::T c2;
+    const LevelDesc L = insts[0].lev[0];
+    const c2* e = (const c2*)L.e;
+    c2* r = (c2*)L.rhs;
+    const long total = (D == 3) ? (long)L.n * L.n * L.n : (long)L.n * L.n;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
+        const long o = lev_off<D>(L, q);
+        const c2 v = e[o];
+        c2 w;
+        w.x = (R)((double)v.x * sc);
+        w.y = (R)((double)v.y * sc);
+        r[o] = w;
+    }
+}
+
 // Self-test of the integer-pipe conversions against the hardware conversions on random
 // values of the binary32 range, exact ties, and the special values.
 __device__ __forceinline__ unsigned long long splitmix(unsigned long long x)
@@ -706,6 +787,33 @@ cudaError_t launch_max_re(int D, int n, const void* u, unsigned long long* out, 
     else launch_k(k_max_re<3>, dim3(blocks_for(work)), dim3(256), 0, s, (const double2*)u, n, out);
     return cudaGetLastError();
 }
+
+#define HELM_DPR(K, ...)                                                                   \
+    (D == 2 ? (prec == 0 ? launch_k(K<2, double>, __VA_ARGS__) : launch_k(K<2, float>, __VA_ARGS__)) \
+            : (prec == 0 ? launch_k(K<3, double>, __VA_ARGS__) : launch_k(K<3, float>, __VA_ARGS__)))
+
+cudaError_t launch_lev_fill(int D, int prec, const InstDesc* insts, int which, double value, cudaStream_t s)
+{
+    HELM_DPR(k_lev_fill, dim3(1216), dim3(256), 0, s, insts, which, value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lev_sumsq(int D, int prec, const InstDesc* insts, double* partial, double* out,
+                             cudaStream_t s)
+{
+    HELM_DPR(k_lev_sumsq, dim3(PI_BLOCKS), dim3(256), 0, s, insts, partial);
+    launch_k(k_sum_partials, dim3(1), dim3(32), 0, s, (const double*)partial, PI_BLOCKS, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lev_scale(int D, int prec, const InstDesc* insts, double sc, cudaStream_t s)
+{
+    HELM_DPR(k_lev_scale, dim3(1216), dim3(256), 0, s, insts, sc);
+    return cudaGetLastError();
+}
+#undef HELM_DPR
+
+int power_iteration_blocks() { return PI_BLOCKS; }
 
 cudaError_t launch_set_ring(int D, const InstDesc* insts, int inst, int n, cudaStream_t s)
 {

@@ -1,6 +1,6 @@
 """Timings of the method's other workloads on one GPU (one JSON line each).
 
-    python -m paper_2308_11469_gb300.workloads [--only cavity63,cube255,batch512,damped1023,exit1023]
+    python -m paper_2308_11469_gb300.workloads [--only cavity63,cube255,batch512,damped1023,exit1023,spectral1023]
     python -m paper_2308_11469_gb300.workloads --replay cube255|cavity1023 [--steps 4] [--fp64]
 
 * cavity63  63x63 unit-square cavity, plane-wave wall data (theta = pi/6), f = 0:
@@ -14,6 +14,7 @@
 * damped1023  the 1023^2 Gaussian cavity at k = 4 with damping p in {0, 4, 8} (general
             cavity iteration, alpha = k^2 and the rho-minimising alpha), mixed.
 * exit1023  mean exit time and k_*^C of the 1023^2 square and the 255^3 cube.
+* spectral1023  rho(G) against k by GPU power iteration on the 1023^2 cavity.
 
 Device time comes from CUDA events on the current stream around each call.  The inputs
 are the seeded generators of ``inputs``; result accuracy against exact discrete
@@ -215,8 +216,30 @@ def exit1023(dev):
     return rows
 
 
+def spectral1023(dev):
+    """rho(G) against k by GPU power iteration on the 1023^2 cavity (mixed, V(2,2) x 8 per
+    application of M^{-1}), beside the closed form k^2 / lambda_min."""
+    import torch  # noqa: F401
+    rows = []
+    n = 1023
+    h = 1.0 / (n + 1)
+    plan0 = B.helm_plan_create(2, n, h, 1.0, prec=B.HELM_PREC_MIXED)
+    km = B.helm_plan_info(plan0)[1]
+    B.helm_plan_destroy(plan0)
+    for frac in (0.25, 0.5, 0.75, 0.9, 1.0, 1.1):
+        k = frac * km
+        plan = B.helm_plan_create(2, n, h, k, prec=B.HELM_PREC_MIXED)
+        B.helm_plan_set_cycle(plan, 2, 2, 1)
+        ms, (st, rho, its) = _dev_ms(lambda: B.helm_spectral_radius(plan, 100, 1e-7, 8), 1)
+        rows.append({"workload": "spectral_radius", "n": n, "k": k, "k_over_kmax": frac,
+                     "rho_power_iteration": rho, "rho_closed_form": B.helm_plan_info(plan)[2],
+                     "iterations": its, "status": B.helm_status_str(st), "ms": ms})
+        B.helm_plan_destroy(plan)
+    return rows
+
+
 WORKLOADS = {"cavity63": cavity63, "cube255": cube255, "batch512": batch512,
-             "damped1023": damped1023, "exit1023": exit1023}
+             "damped1023": damped1023, "exit1023": exit1023, "spectral1023": spectral1023}
 
 
 def main(argv=None) -> int:
