@@ -126,6 +126,7 @@ struct LaunchRec {
     enum Kind { RBGS, RESTRICT, PROLONG, ZERO, TAIL, RESID, CHECK, DOWN, UP, NKINDS } kind;
     int off, cnt, work, color, mode;
     double bytes;   // algorithmic bytes of one launch (each datum it must touch, once)
+    int nmax = 0;   // DOWN: the largest level of the launch
 };
 
 struct Engine {
@@ -335,7 +336,7 @@ struct Engine {
         auto vcycle2d = [&](std::vector<LaunchRec>& out, bool zero_start) {
             for (int j = 0; j < J; ++j)
                 out.push_back({LaunchRec::DOWN, ph[j].off, ph[j].cnt, ph[j].tiles, ph[j].shape,
-                               zero_start ? 2 : 1, 0.0});
+                               zero_start ? 2 : 1, 0.0, ph[j].nmax});
             tail(out, zero_start);
             // without pre-smoothing the descent leaves e2 unwritten where the iterate was zero
             const int e2_mode = (nu1 == 0) ? (zero_start ? 2 : 1) : 0;
@@ -407,10 +408,15 @@ struct Engine {
             case LaunchRec::TAIL: b += 2.0 * pts(n) * eb; break;
             case LaunchRec::DOWN: {
                 const bool zero = (L.mode == 2) || (L.mode == 1 && it.level > 0);
-                b += ((zero ? 2.0 : 3.0) * pts(n) + pts(nc)) * eb;   // [e], rhs in; e2, coarse rhs out
+                if (zero && nu1 == 0) b += (pts(n) + pts(nc)) * eb;      // rhs in, coarse rhs out
+                else b += ((zero ? 2.0 : 3.0) * pts(n) + pts(nc)) * eb;  // [e], rhs in; e2, coarse rhs out
                 break;
             }
-            case LaunchRec::UP: b += (3.0 * pts(n) + pts(nc)) * eb; break;  // e2, rhs, coarse e in; e out
+            case LaunchRec::UP: {
+                const bool e2z = (L.mode == 2) || (L.mode == 1 && it.level > 0);
+                b += ((e2z ? 2.0 : 3.0) * pts(n) + pts(nc)) * eb;         // [e2], rhs, coarse e in; e out
+                break;
+            }
             default: break;
             }
         }
@@ -439,7 +445,8 @@ struct Engine {
                                 L.mode, s);
                 break;
             case LaunchRec::DOWN:
-                e = launch_down2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu1, L.mode, L.color, s);
+                e = launch_down2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu1, L.mode, L.color, s,
+                                  L.nmax);
                 break;
             case LaunchRec::UP:
                 e = launch_up2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu2, L.color, L.mode, s);

@@ -60,9 +60,12 @@ cudaError_t setup_outer();
 // ---- fused 2D multigrid (vcycle2d.cu): two launches per level ----
 // descent: nu1 sweeps + residual + restriction; e (or zero) -> e2, coarse rhs.
 // zero_mode: 2 = every level's iterate is zero, 1 = levels > 0 are zero, 0 = load e.
+// nmax: the largest level of the launch; with nu1 = 0 and zero_mode = 2 (every iterate
+// zero) the descent is the restriction of rhs alone (k_restrict_rhs2d)
 cudaError_t launch_down2d(int prec, const InstDesc* insts, const InstState* st, const MgItem* items,
                           int nitems, int max_tiles, int nu1, int zero_mode, int shape,
-                          cudaStream_t s);
+                          cudaStream_t s,
+                          int nmax = 0);
 // ascent: e2 + prolongation of the coarse e, nu2 sweeps -> e
 // e2_mode: 0 = read e2; 2 = e2 is zero on every level, 1 = below the finest level (no
 // pre-smoothing from a zero iterate: the descent did not write it)

@@ -340,6 +340,51 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     }
 }
 
+// Descent step of a cycle without pre-smoothing from a zero iterate: the residual is rhs
+// itself, so the coarse rhs is the full weighting of rhs -- no staging, no iterate.  One
+// thread per coarse node (32 x 8 per CTA), its nine fine values read through L1; the
+// weights and their order are those of k_down2d's restriction.
+constexpr int RX = 32, RY = 8;
+
+template <typename R>
+__global__ void __launch_bounds__(RX * RY)
+k_restrict_rhs2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
+                 const MgItem* __restrict__ items)
+{
+    typedef typename C2<R>::T c2;
+    const MgItem item = items[blockIdx.y];
+    const LevelDesc L = insts[item.inst].lev[item.level];
+    const LevelDesc C = insts[item.inst].lev[item.level + 1];
+    pdl_wait();
+    pdl_trigger();
+    if (st[item.inst].status != HELM_ST_ACTIVE) return;
+    const int nc = C.n;
+    const int ntx = (nc + RX - 1) / RX;
+    if ((int)blockIdx.x >= ntx * ((nc + RY - 1) / RY)) return;
+    const int X = 1 + (blockIdx.x % ntx) * RX + (threadIdx.x % RX);
+    const int Y = 1 + (blockIdx.x / ntx) * RY + (threadIdx.x / RX);
+    if (X > nc || Y > nc) return;
+    const c2* __restrict__ gr = (const c2*)L.rhs;
+    const size_t P = L.pitch;
+    const size_t o = (size_t)(2 * Y) * P + 2 * X;
+    R ax = 0, ay = 0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+        const R wy = (dy == 0) ? (R)2 : (R)1;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const R wgt = wy * ((dx == 0) ? (R)2 : (R)1);
+            const c2 r = __ldg(gr + (o + (ptrdiff_t)dy * (ptrdiff_t)P + dx));
+            ax += wgt * r.x;
+            ay += wgt * r.y;
+        }
+    }
+    c2 v;
+    v.x = ax * (R)(1.0 / 16.0);
+    v.y = ay * (R)(1.0 / 16.0);
+    ((c2*)C.rhs)[(size_t)Y * C.pitch + X] = v;
+}
+
 template <int NU, int TX, int TY> constexpr size_t down_bytes(size_t eb) {
     return 2 * (size_t)(TX + 2 * (2 * NU + 2)) * (TY + 2 * (2 * NU + 2)) * eb;
 }
@@ -379,6 +424,7 @@ template <typename R>
 cudaError_t set_all()
 {
     cudaError_t e;
+    if ((e = max_carveout(k_restrict_rhs2d<R>)) != cudaSuccess) return e;
     if ((e = set_attrs<R, 0>()) != cudaSuccess) return e;
     if ((e = set_attrs<R, 1>()) != cudaSuccess) return e;
     if ((e = set_attrs<R, 2>()) != cudaSuccess) return e;
@@ -451,8 +497,17 @@ cudaError_t setup_2d(int prec) { return prec == 0 ? set_all<double>() : set_all<
 
 // shape: the tile shape of every item of the launch (tile_shape2d of the largest level)
 cudaError_t launch_down2d(int prec, const InstDesc* insts, const InstState* st, const MgItem* items,
-                          int nitems, int max_tiles, int nu1, int zero_mode, int shape, cudaStream_t s)
+                          int nitems, int max_tiles, int nu1, int zero_mode, int shape, cudaStream_t s,
+                          int nmax)
 {
+    if (nu1 == 0 && zero_mode == 2 && nmax > 0) {
+        // every iterate of the launch is zero: restriction of rhs alone
+        const int nc = (nmax - 1) / 2;
+        dim3 gr(((nc + RX - 1) / RX) * ((nc + RY - 1) / RY), nitems);
+        if (prec == 0) launch_k(k_restrict_rhs2d<double>, gr, dim3(RX * RY), 0, s, insts, st, items);
+        else launch_k(k_restrict_rhs2d<float>, gr, dim3(RX * RY), 0, s, insts, st, items);
+        return cudaGetLastError();
+    }
     dim3 g(max_tiles, nitems);
     if (shape) return prec == 0 ? down<double, 1>(nu1, g, insts, st, items, zero_mode, s)
                                 : down<float, 1>(nu1, g, insts, st, items, zero_mode, s);
