@@ -345,19 +345,21 @@ struct Engine {
         };
         auto vcycle = [&](std::vector<LaunchRec>& out, bool zero_start) {
             if (D == 2 && nu1 <= 4 && nu2 <= 4) { vcycle2d(out, zero_start); return; }
-            if (zero_start && nu1 == 0)
-                out.push_back({LaunchRec::ZERO, l0_off, nl0, w_l0, 0, 0, b_l0});
+            // without pre-smoothing the iterates are zero on the way down (every level from a
+            // zero start, the coarse ones otherwise): the restriction takes rhs alone and the
+            // prolongation assigns
+            const int zmode = (nu1 == 0) ? (zero_start ? 2 : 1) : 0;
             for (int j = 0; j < J; ++j) {
                 for (int s = 0; s < nu1; ++s) {
                     const int mode = (s == 0) ? (zero_start ? 2 : 1) : 0;
                     out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 0, mode, ph[j].b_rb});
                     out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 1, 0, ph[j].b_rb});
                 }
-                out.push_back({LaunchRec::RESTRICT, ph[j].off, ph[j].cnt, ph[j].w_rs, 0, 0, ph[j].b_rs});
+                out.push_back({LaunchRec::RESTRICT, ph[j].off, ph[j].cnt, ph[j].w_rs, 0, zmode, ph[j].b_rs});
             }
             tail(out, zero_start);
             for (int j = J - 1; j >= 0; --j) {
-                out.push_back({LaunchRec::PROLONG, ph[j].off, ph[j].cnt, ph[j].w_pr, 0, 0, ph[j].b_pr});
+                out.push_back({LaunchRec::PROLONG, ph[j].off, ph[j].cnt, ph[j].w_pr, 0, zmode, ph[j].b_pr});
                 for (int s = 0; s < nu2; ++s) {
                     out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 0, 0, ph[j].b_rb});
                     out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 1, 0, ph[j].b_rb});
@@ -402,8 +404,16 @@ struct Engine {
             const int nc = (it.level + 1 < d.nlev) ? d.lev[it.level + 1].n : 0;
             switch (L.kind) {
             case LaunchRec::RBGS: b += 1.5 * pts(n) * eb; break;
-            case LaunchRec::RESTRICT: b += (2.0 * pts(n) + 2.0 * pts(nc)) * eb; break;
-            case LaunchRec::PROLONG: b += (pts(nc) + 2.0 * pts(n)) * eb; break;
+            case LaunchRec::RESTRICT: {
+                const bool z = (L.mode == 2) || (L.mode == 1 && it.level > 0);
+                b += (z ? (pts(n) + pts(nc)) : (2.0 * pts(n) + 2.0 * pts(nc))) * eb;
+                break;
+            }
+            case LaunchRec::PROLONG: {
+                const bool z = (L.mode == 2) || (L.mode == 1 && it.level > 0);
+                b += (pts(nc) + (z ? 1.0 : 2.0) * pts(n)) * eb;
+                break;
+            }
             case LaunchRec::ZERO: b += pts(n) * eb; break;
             case LaunchRec::TAIL: b += 2.0 * pts(n) * eb; break;
             case LaunchRec::DOWN: {
@@ -432,10 +442,10 @@ struct Engine {
                 e = launch_rbgs(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, L.color, L.mode, s);
                 break;
             case LaunchRec::RESTRICT:
-                e = launch_restrict(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s);
+                e = launch_restrict(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s, L.mode);
                 break;
             case LaunchRec::PROLONG:
-                e = launch_prolong(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s);
+                e = launch_prolong(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s, L.mode);
                 break;
             case LaunchRec::ZERO:
                 e = launch_zero(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s);

@@ -33,12 +33,14 @@ inline int tail_top(int D, int prec_is_fp64)
 cudaError_t launch_rbgs(int D, int prec, const InstDesc* insts, const InstState* st,
                         const MgItem* items, int nitems, int work, int color, int mode,
                         cudaStream_t s);
-// coarse rhs := full weighting of (rhs - Delta_h e) on level l, coarse e := 0
+// coarse rhs := full weighting of (rhs - (Delta_h - sigma) e) on level l, coarse e := 0;
+// mode 2 / 1 (no pre-smoothing): the iterate is zero on every level / levels > 0, the
+// residual is rhs and the coarse iterate is left to the prolongation
 cudaError_t launch_restrict(int D, int prec, const InstDesc* insts, const InstState* st,
-                            const MgItem* items, int nitems, int work, cudaStream_t s);
-// e_l += prolongation of e_{l+1}
+                            const MgItem* items, int nitems, int work, cudaStream_t s, int mode = 0);
+// e_l += prolongation of e_{l+1}; mode 2 / 1: e_l := prolongation where e_l is zero
 cudaError_t launch_prolong(int D, int prec, const InstDesc* insts, const InstState* st,
-                           const MgItem* items, int nitems, int work, cudaStream_t s);
+                           const MgItem* items, int nitems, int work, cudaStream_t s, int mode = 0);
 // zero the iterate of the listed levels (ring included)
 cudaError_t launch_zero(int D, int prec, const InstDesc* insts, const InstState* st,
                         const MgItem* items, int nitems, int work, cudaStream_t s);

@@ -4,8 +4,8 @@
 // global-memory levels (vcycle.cu / vcycle2d.cu): red-black Gauss-Seidel, residual,
 // full weighting, multilinear prolongation.
 //
-// In 2D complex64 the n = 31 level is not cycled but solved exactly (a direct
-// coarse-grid solver): the sine basis diagonalises Delta_h with zero walls, so
+// In complex64 the n = 31 level (2D) / n = 15 level (3D) is not cycled but solved exactly
+// (a direct coarse-grid solver): the sine basis diagonalises Delta_h with zero walls, so
 // e = (2/(n+1))^2 S ((S r S) / mu) S with S_ab = sin(pi a b / (n+1)) and
 // mu_ab = -(4/h^2)(sin^2(pi a / (2(n+1))) + sin^2(pi b / (2(n+1)))).  The four 31 x 31
 // products run on the FP32 pipes from shared memory.
@@ -43,6 +43,16 @@ constexpr int XSCR_FLOATS = XTAB_FLOATS + 2 * XN * XT + 2 * XN * XP;
 // setup_tail (host, double precision, rounded once)
 __device__ float g_xtab[XTAB_FLOATS];
 
+// Exact 3D solve of the n = 15 level (complex64): a sine transform along each axis, the
+// diagonal scaling, and the transforms back.  Table: S[15][16] (S_ab = sin(pi a b / 16)),
+// then s[16] (s_a = sin^2(pi a / 32)); scratch: two dense 15^3 complex buffers.
+constexpr int YN = 15;
+constexpr int YP = 16;
+constexpr int YV = YN * YN * YN;
+constexpr int YTAB_FLOATS = YN * YP + YP;
+constexpr int YSCR_FLOATS = YTAB_FLOATS + 2 * 2 * YV;
+__device__ float g_ytab[YTAB_FLOATS];
+
 template <int D, int N> struct Lv {
     static constexpr int S = N + 2;              // padded row length (odd)
     static constexpr int HE = (S + 1) / 2;       // even-x entries of a row, stored first
@@ -61,16 +71,22 @@ template <int D, int N> constexpr int tail_elems() {
     else return 2 * Lv<D, N>::SZ + tail_elems<D, (N - 1) / 2>();
 }
 
-// does a tail with top size N0 contain the exactly solved n = 31 level?
+// the level each complex64 tail solves exactly (2D: 31, 3D: 15; none in FP64)
+template <int D, typename R> constexpr int exact_n()
+{
+    return std::is_same<R, float>::value ? (D == 2 ? XN : YN) : 0;
+}
+
+// does a tail with top size N0 contain its exactly solved level?
 template <int D, typename R, int N0> constexpr bool tail_exact()
 {
-    return D == 2 && std::is_same<R, float>::value && N0 >= XN;
+    return exact_n<D, R>() > 0 && N0 >= exact_n<D, R>();
 }
 
 template <int D, typename R, int N0> constexpr size_t tail_bytes()
 {
     return (size_t)tail_elems<D, N0>() * sizeof(typename C2<R>::T) +
-           (tail_exact<D, R, N0>() ? (size_t)XSCR_FLOATS * sizeof(float) : 0);
+           (tail_exact<D, R, N0>() ? (size_t)(D == 2 ? XSCR_FLOATS : YSCR_FLOATS) * sizeof(float) : 0);
 }
 
 template <int NWARPS> __device__ __forceinline__ void tsync() {
@@ -228,7 +244,7 @@ __device__ __forceinline__ void t_clear(typename C2<R>::T* base)
 {
     typedef typename C2<R>::T c2;
     for (int i = threadIdx.x; i < Lv<D, N>::SZ; i += TNT) base[i] = cz<c2>();
-    constexpr bool exact_here = D == 2 && std::is_same<R, float>::value && N == XN;
+    constexpr bool exact_here = exact_n<D, R>() > 0 && N == exact_n<D, R>();
     if constexpr (N > 1 && !exact_here) t_clear<D, R, (N - 1) / 2>(base + 2 * Lv<D, N>::SZ);
 }
 
@@ -327,6 +343,73 @@ __device__ __forceinline__ void x_solve(float2* E, const float2* Rr, float* scr,
     __syncthreads();
 }
 
+// 3D: element (z, y, x) (0-based interior) of the n = 15 level array, or of a dense buffer
+template <bool LEVEL> __device__ __forceinline__ int y_at(int z, int y, int x)
+{
+    constexpr int S = YN + 2;
+    if constexpr (LEVEL) return ((z + 1) * S + (y + 1)) * S + ix<YN>(x + 1);
+    else return (z * YN + y) * YN + x;
+}
+
+// One sine transform along `axis` (0 = x, 1 = y, 2 = z) of the 15^3 complex array:
+// out[.., a, ..] = sum_j S[a][j] in[.., j, ..] (optionally scaled at the end); every thread
+// forms whole outputs, the transformed index fastest for x, the x index fastest otherwise.
+template <int AXIS, bool LEVEL_IN, bool LEVEL_OUT>
+__device__ __forceinline__ void y_pass(const float2* in, float2* out, const float* Sm)
+{
+    for (int t = threadIdx.x; t < YV; t += TNT) {
+        const int i0 = t % YN, i1 = (t / YN) % YN, i2 = t / (YN * YN);
+        // (z, y, x) of the output; `a` is the transformed coordinate
+        int z, y, x, a;
+        if constexpr (AXIS == 0) { a = i0; y = i1; z = i2; x = 0; }
+        else if constexpr (AXIS == 1) { x = i0; a = i1; z = i2; y = 0; }
+        else { x = i0; y = i1; a = i2; z = 0; }
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 5
+        for (int j = 0; j < YN; ++j) {
+            const float sv = Sm[j * YP + a];          // S is symmetric: lanes read along a row
+            const float2 v = (AXIS == 0) ? in[y_at<LEVEL_IN>(z, y, j)]
+                           : (AXIS == 1) ? in[y_at<LEVEL_IN>(z, j, x)] : in[y_at<LEVEL_IN>(j, y, x)];
+            acc.x = fmaf(sv, v.x, acc.x);
+            acc.y = fmaf(sv, v.y, acc.y);
+        }
+        if constexpr (AXIS == 0) out[y_at<LEVEL_OUT>(z, y, a)] = acc;
+        else if constexpr (AXIS == 1) out[y_at<LEVEL_OUT>(z, a, x)] = acc;
+        else out[y_at<LEVEL_OUT>(a, y, x)] = acc;
+    }
+}
+
+// E (level array of n = 15, 3D) <- exact solution of (Delta_h - sigma) e = Rr, zero walls:
+// e = c S S S ((S S S r) / (s_a + s_b + s_c + sigma h^2 / 4)), c = -2 h^2 / (n+1)^3
+__device__ __forceinline__ void y_solve(float2* E, const float2* Rr, float* scr, float h, float sigma)
+{
+    const float* Sm = scr;
+    const float* sv = scr + YN * YP;
+    float2* T1 = reinterpret_cast<float2*>(scr + YTAB_FLOATS);
+    float2* T2 = T1 + YV;
+    const float c = -2.f * h * h / (float)((YN + 1) * (YN + 1) * (YN + 1));
+    const float tau = 0.25f * sigma * h * h;
+    y_pass<0, true, false>(Rr, T1, Sm);
+    __syncthreads();
+    y_pass<1, false, false>(T1, T2, Sm);
+    __syncthreads();
+    y_pass<2, false, false>(T2, T1, Sm);
+    __syncthreads();
+    for (int t = threadIdx.x; t < YV; t += TNT) {
+        const int a = t % YN, b = (t / YN) % YN, cc = t / (YN * YN);
+        const float w = c / (sv[a] + sv[b] + sv[cc] + tau);
+        T1[t].x *= w;
+        T1[t].y *= w;
+    }
+    __syncthreads();
+    y_pass<2, false, false>(T1, T2, Sm);
+    __syncthreads();
+    y_pass<1, false, false>(T2, T1, Sm);
+    __syncthreads();
+    y_pass<0, false, true>(T1, E, Sm);
+    __syncthreads();
+}
+
 // One V(nu1, nu2)-cycle on the level of size N held at `base` (iterate, then rhs).
 // ez: the iterate is zero on entry (a coarse level, or a top level started from zero).
 // lv: this level's descriptor (its dinv); the next coarser level's follows it.
@@ -339,6 +422,9 @@ __device__ void t_vcycle(typename C2<R>::T* base, R h, R sig, const LevelDesc* l
     c2* Rr = base + Lv<D, N>::SZ;
     if constexpr (D == 2 && std::is_same<R, float>::value && N == XN && NWARPS == TNT / 32) {
         x_solve(E, Rr, xscr, (float)h, (float)sig);
+        return;
+    } else if constexpr (D == 3 && std::is_same<R, float>::value && N == YN && NWARPS == TNT / 32) {
+        y_solve(E, Rr, xscr, (float)h, (float)sig);
         return;
     } else if constexpr (N == 1) {
         if (threadIdx.x == 0) {
@@ -406,7 +492,7 @@ k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const c2* __restrict__ ge = (const c2*)L0.e;
     // the starting iterate is read unless the top level is the exactly solved one (which
     // discards it)
-    const bool le = load_e && item.level == 0 && !(tail_exact<D, R, N0>() && N0 == XN);
+    const bool le = load_e && item.level == 0 && !(tail_exact<D, R, N0>() && N0 == exact_n<D, R>());
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     c2* E = base;
     c2* Rr = base + Lv<D, N0>::SZ;
@@ -433,8 +519,9 @@ k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     if constexpr (tail_exact<D, R, N0>()) {
         // sine tables of the exact level (host-computed)
         xscr = reinterpret_cast<float*>(base + TOT);
-        for (int i = threadIdx.x; i < XTAB_FLOATS / 4; i += TNT)
-            reinterpret_cast<float4*>(xscr)[i] = reinterpret_cast<const float4*>(g_xtab)[i];
+        constexpr int NT4 = (D == 2 ? XTAB_FLOATS : YTAB_FLOATS) / 4;
+        const float4* tab = reinterpret_cast<const float4*>(D == 2 ? g_xtab : g_ytab);
+        for (int i = threadIdx.x; i < NT4; i += TNT) reinterpret_cast<float4*>(xscr)[i] = tab[i];
     }
     t_clear<D, R, N0>(base);
     __syncthreads();
@@ -543,10 +630,11 @@ size_t tail_smem_bytes(int D, int prec, int n)
         size_t s = (size_t)(m + 2);
         tot += 2 * ((D == 3) ? s * s * s : s * s);
     }
-    return tot * elem + (size_t)(tail_exact_n(D, prec) && n >= tail_exact_n(D, prec) ? XSCR_FLOATS * sizeof(float) : 0);
+    return tot * elem + (size_t)(tail_exact_n(D, prec) && n >= tail_exact_n(D, prec)
+                                     ? (D == 2 ? XSCR_FLOATS : YSCR_FLOATS) * sizeof(float) : 0);
 }
 
-int tail_exact_n(int D, int prec) { return (D == 2 && prec != 0) ? XN : 0; }
+int tail_exact_n(int D, int prec) { return prec == 0 ? 0 : (D == 2 ? XN : YN); }
 
 cudaError_t setup_tail(int D, int prec)
 {
@@ -567,6 +655,19 @@ cudaError_t setup_tail(int D, int prec)
             tab[2 * XN * XP + i] = i < XN ? (float)(si * si) : 0.f;
         }
         const cudaError_t e = cudaMemcpyToSymbol(g_xtab, tab, sizeof tab);
+        if (e != cudaSuccess) return e;
+    }
+    if (D == 3 && prec != 0) {
+        static float tab[YTAB_FLOATS];
+        const double pi = 3.14159265358979323846;
+        for (int i = 0; i < YN; ++i)
+            for (int j = 0; j < YP; ++j)
+                tab[i * YP + j] = j < YN ? (float)std::sin(pi * (i + 1) * (j + 1) / (YN + 1)) : 0.f;
+        for (int i = 0; i < YP; ++i) {
+            const double si = std::sin(pi * (i + 1) / (2.0 * (YN + 1)));
+            tab[YN * YP + i] = i < YN ? (float)(si * si) : 0.f;
+        }
+        const cudaError_t e = cudaMemcpyToSymbol(g_ytab, tab, sizeof tab);
         if (e != cudaSuccess) return e;
     }
     if (D == 2) return prec == 0 ? tail_attrs<2, double>() : tail_attrs<2, float>();

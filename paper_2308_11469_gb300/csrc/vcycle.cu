@@ -88,10 +88,13 @@ k_rbgs(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
 // ---------------------------------------------------------------------------
 // Residual + full-weighting restriction
 // ---------------------------------------------------------------------------
+// mode 2 / 1: the fine iterate is zero on every level / on levels > 0 (no pre-smoothing
+// from a zero iterate): the residual is rhs itself (the same values the general form gives
+// with e = 0) and the coarse iterate is left for the prolongation to assign.
 template <int D, typename R>
 __global__ void __launch_bounds__(256)
 k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
-           const MgItem* __restrict__ items)
+           const MgItem* __restrict__ items, int mode)
 {
     pdl_wait();
     pdl_trigger();
@@ -111,6 +114,7 @@ k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const R ih2 = (R)(1.0 / (F.h * F.h));
     const R sig = (R)insts[item.inst].sigma;
     const R scale = (D == 3) ? (R)(1.0 / 64.0) : (R)(1.0 / 16.0);
+    const bool ez = (mode == 2) || (mode == 1 && item.level > 0);
     for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
          q += (long)gridDim.x * blockDim.x) {
         const int X = (int)(q % nc) + 1;
@@ -118,6 +122,26 @@ k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
         const int Z = (D == 3) ? (int)(q / ((long)nc * nc)) + 1 : 0;
         R ax = 0, ay = 0;
         const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
+        if (ez) {
+            for (int dz = zlo; dz <= zhi; ++dz) {
+                const R wz = (D == 3) ? (dz == 0 ? (R)2 : (R)1) : (R)1;
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const R wy = (dy == 0) ? (R)2 : (R)1;
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const R w = wz * wy * ((dx == 0) ? (R)2 : (R)1);
+                        const c2 rr = r[(long)off<D>(F, 2 * X + dx, 2 * Y + dy, 2 * Z + dz)];
+                        ax += w * rr.x;
+                        ay += w * rr.y;
+                    }
+                }
+            }
+            const size_t oc = off<D>(C, X, Y, Z);
+            c2 v;
+            v.x = ax * scale;
+            v.y = ay * scale;
+            cr[oc] = v;
+            continue;
+        }
         for (int dz = zlo; dz <= zhi; ++dz) {
             const R wz = (D == 3) ? (dz == 0 ? (R)2 : (R)1) : (R)1;
             for (int dy = -1; dy <= 1; ++dy) {
@@ -151,10 +175,12 @@ k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
 // ---------------------------------------------------------------------------
 // Multilinear prolongation + correction
 // ---------------------------------------------------------------------------
+// mode 2 / 1: the fine iterate is zero on every level / on levels > 0 (no pre-smoothing
+// from a zero iterate): e := interpolation instead of e += interpolation.
 template <int D, typename R>
 __global__ void __launch_bounds__(256)
 k_prolong(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
-          const MgItem* __restrict__ items)
+          const MgItem* __restrict__ items, int mode)
 {
     pdl_wait();
     pdl_trigger();
@@ -167,6 +193,7 @@ k_prolong(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const long total = (D == 3) ? (long)n * n * n : (long)n * n;
     c2* __restrict__ e = (c2*)F.e;
     const c2* __restrict__ ce = (const c2*)C.e;
+    const bool ez = (mode == 2) || (mode == 1 && item.level > 0);
     for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
          q += (long)gridDim.x * blockDim.x) {
         const int x = (int)(q % n) + 1;
@@ -194,9 +221,15 @@ k_prolong(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
         // are read twice, which gives the weight 1 of an even fine index.
         const R w = (D == 3) ? (R)0.125 : (R)0.25;
         const long o = (long)off<D>(F, x, y, z);
-        c2 v = e[o];
-        v.x += w * vx;
-        v.y += w * vy;
+        c2 v;
+        if (ez) {
+            v.x = w * vx;
+            v.y = w * vy;
+        } else {
+            v = e[o];
+            v.x += w * vx;
+            v.y += w * vy;
+        }
         e[o] = v;
     }
 }
@@ -257,24 +290,24 @@ cudaError_t launch_rbgs(int D, int prec, const InstDesc* insts, const InstState*
 }
 
 cudaError_t launch_restrict(int D, int prec, const InstDesc* insts, const InstState* st,
-                            const MgItem* items, int nitems, int work, cudaStream_t s)
+                            const MgItem* items, int nitems, int work, cudaStream_t s, int mode)
 {
     dim3 g = mg_grid(work, nitems);
-    if (D == 2 && prec == 0) launch_k(k_restrict<2, double>, dim3(g), dim3(256), 0, s, insts, st, items);
-    else if (D == 2) launch_k(k_restrict<2, float>, dim3(g), dim3(256), 0, s, insts, st, items);
-    else if (prec == 0) launch_k(k_restrict<3, double>, dim3(g), dim3(256), 0, s, insts, st, items);
-    else launch_k(k_restrict<3, float>, dim3(g), dim3(256), 0, s, insts, st, items);
+    if (D == 2 && prec == 0) launch_k(k_restrict<2, double>, dim3(g), dim3(256), 0, s, insts, st, items, mode);
+    else if (D == 2) launch_k(k_restrict<2, float>, dim3(g), dim3(256), 0, s, insts, st, items, mode);
+    else if (prec == 0) launch_k(k_restrict<3, double>, dim3(g), dim3(256), 0, s, insts, st, items, mode);
+    else launch_k(k_restrict<3, float>, dim3(g), dim3(256), 0, s, insts, st, items, mode);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prolong(int D, int prec, const InstDesc* insts, const InstState* st,
-                           const MgItem* items, int nitems, int work, cudaStream_t s)
+                           const MgItem* items, int nitems, int work, cudaStream_t s, int mode)
 {
     dim3 g = mg_grid(work, nitems);
-    if (D == 2 && prec == 0) launch_k(k_prolong<2, double>, dim3(g), dim3(256), 0, s, insts, st, items);
-    else if (D == 2) launch_k(k_prolong<2, float>, dim3(g), dim3(256), 0, s, insts, st, items);
-    else if (prec == 0) launch_k(k_prolong<3, double>, dim3(g), dim3(256), 0, s, insts, st, items);
-    else launch_k(k_prolong<3, float>, dim3(g), dim3(256), 0, s, insts, st, items);
+    if (D == 2 && prec == 0) launch_k(k_prolong<2, double>, dim3(g), dim3(256), 0, s, insts, st, items, mode);
+    else if (D == 2) launch_k(k_prolong<2, float>, dim3(g), dim3(256), 0, s, insts, st, items, mode);
+    else if (prec == 0) launch_k(k_prolong<3, double>, dim3(g), dim3(256), 0, s, insts, st, items, mode);
+    else launch_k(k_prolong<3, float>, dim3(g), dim3(256), 0, s, insts, st, items, mode);
     return cudaGetLastError();
 }
 
