@@ -33,7 +33,16 @@ struct LevelDesc {
     void* e;      // padded iterate of (Delta_h - sigma) e = rhs (final iterate of a V-cycle)
     void* rhs;    // right-hand side (same indexing as e)
     void* e2;     // 2D fused path: the pre-smoothed iterate (same indexing as e)
+    void* rhs2;   // 2D level 0 only (else null): the right-hand side of odd outer steps
 };
+
+// Right-hand side of level `level` during outer step `it`.  Level 0 of a 2D instance with
+// fused levels keeps two buffers, so that the kernel forming r_{N+1} never writes the
+// array other tiles are still reading r_N from: step N uses rhs for even N, rhs2 for odd.
+__host__ __device__ inline void* lev_rhs(const LevelDesc& L, int level, int it)
+{
+    return (level == 0 && L.rhs2 && (it & 1)) ? L.rhs2 : L.rhs;
+}
 
 struct InstDesc {
     int D, n, nlev, ltail;      // ltail: first level solved inside the one-CTA tail kernel

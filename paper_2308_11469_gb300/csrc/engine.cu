@@ -83,16 +83,19 @@ size_t layout(InstDesc& d, int D, int n, double h, double k, int prec, char* bas
         L.e = nullptr;
         L.rhs = nullptr;
         L.e2 = nullptr;
+        L.rhs2 = nullptr;
         if (l > lt) continue;               // deeper levels live only inside the tail kernel
         const size_t planes = (D == 3) ? (size_t)L.rows : 1;
         const size_t sz = align256((size_t)L.pitch * L.rows * planes * eb);
         const bool two = (D == 2 && l < lt);  // fused 2D levels keep a second iterate
+        const bool r2 = two && l == 0;        // ... and level 0 a second right-hand side
         if (base) {
             L.e = base + off;
             L.rhs = base + off + sz;
             if (two) L.e2 = base + off + 2 * sz;
+            if (r2) L.rhs2 = base + off + 3 * sz;
         }
-        off += (two ? 3 : 2) * sz;
+        off += (two ? (r2 ? 4 : 3) : 2) * sz;
     }
     const size_t S = (size_t)n + 2;
     const size_t ubytes = align256(((D == 3) ? S * S * S : S * S) * 16);

@@ -228,7 +228,7 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
     const double2* __restrict__ f = I.f;
     const LevelDesc L0 = I.lev[0];
     const c2* __restrict__ e = (const c2*)L0.e;
-    c2* __restrict__ rhs = (c2*)L0.rhs;
+    c2* __restrict__ rhs = (c2*)lev_rhs(L0, 0, MODE == 1 ? s.it + 1 : s.it);   // r_{N+1} / r_0
     const int P = L0.pitch;
     const int x0 = 1 + item.tx * T2, y0 = 1 + item.ty * T2;
     R emax2 = 0;
@@ -286,11 +286,15 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
             // once per solve, in FP64: ||r_0||^2 and ||b||^2, b = f - (wall neighbours)/h^2
             // formed with the same operations as r (so r_0 = b bit for bit from a zero start)
             r2d += r.x * r.x + r.y * r.y;
-            const double2 z = make_double2(0.0, 0.0);
-            const double2 aw = (gx == 1) ? a : z, bw = (gx == n) ? b : z;
-            const double2 dw = (gy == 1) ? d : z, uw = (gy == n) ? u : z;
-            const double bx = fma((aw.x + bw.x) + (dw.x + uw.x), mih2, fma(0.0, mcdiag, fv.x));
-            const double by = fma((aw.y + bw.y) + (dw.y + uw.y), mih2, fma(0.0, mcdiag, fv.y));
+            // b = f away from the wall (the same value the general form gives there)
+            double bx = fv.x, by = fv.y;
+            if (gx == 1 || gx == n || gy == 1 || gy == n) {
+                const double2 z = make_double2(0.0, 0.0);
+                const double2 aw = (gx == 1) ? a : z, bw = (gx == n) ? b : z;
+                const double2 dw = (gy == 1) ? d : z, uw = (gy == n) ? u : z;
+                bx = fma((aw.x + bw.x) + (dw.x + uw.x), mih2, fma(0.0, mcdiag, fv.x));
+                by = fma((aw.y + bw.y) + (dw.y + uw.y), mih2, fma(0.0, mcdiag, fv.y));
+            }
             b2 += bx * bx + by * by;
         }
     }
@@ -377,7 +381,7 @@ __device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ ins
     const double2* __restrict__ uin = (s.it & 1) ? u1 : u0;
     double2* __restrict__ uout = (double2*)((s.it & 1) ? u0 : u1);
     const c2* __restrict__ e = (const c2*)L0.e;
-    c2* __restrict__ rhs = (c2*)L0.rhs;
+    c2* __restrict__ rhs = (c2*)lev_rhs(L0, 0, MODE == 1 ? s.it + 1 : s.it);
     const long P = L0.pitch;
     const long PL = (long)L0.pitch * L0.rows;
     const double mih2 = -I.ih2;
@@ -421,12 +425,15 @@ __device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ ins
             } else {
                 // once per solve, in FP64: ||r_0||^2 and ||b||^2 (same operations as r)
                 r2d += r.x * r.x + r.y * r.y;
-                const double2 zz = make_double2(0.0, 0.0);
-                const double2 w1 = (gx == 1) ? w : zz, w2 = (gx == n) ? ea : zz;
-                const double2 w3 = (gy == 1) ? so : zz, w4 = (gy == n) ? no : zz;
-                const double2 w5 = (z == 1) ? dn : zz, w6 = (z == n) ? up : zz;
-                const double bx = fma(((w1.x + w2.x) + (w3.x + w4.x)) + (w5.x + w6.x), mih2, fma(0.0, mcdiag, fv.x));
-                const double by = fma(((w1.y + w2.y) + (w3.y + w4.y)) + (w5.y + w6.y), mih2, fma(0.0, mcdiag, fv.y));
+                double bx = fv.x, by = fv.y;            // b = f away from the wall
+                if (gx == 1 || gx == n || gy == 1 || gy == n || z == 1 || z == n) {
+                    const double2 zz = make_double2(0.0, 0.0);
+                    const double2 w1 = (gx == 1) ? w : zz, w2 = (gx == n) ? ea : zz;
+                    const double2 w3 = (gy == 1) ? so : zz, w4 = (gy == n) ? no : zz;
+                    const double2 w5 = (z == 1) ? dn : zz, w6 = (z == n) ? up : zz;
+                    bx = fma(((w1.x + w2.x) + (w3.x + w4.x)) + (w5.x + w6.x), mih2, fma(0.0, mcdiag, fv.x));
+                    by = fma(((w1.y + w2.y) + (w3.y + w4.y)) + (w5.y + w6.y), mih2, fma(0.0, mcdiag, fv.y));
+                }
                 b2 += bx * bx + by * by;
             }
         }

@@ -483,12 +483,13 @@ k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const double sigma = insts[item.inst].sigma;
     pdl_wait();
     pdl_trigger();
-    if (st[item.inst].status != HELM_ST_ACTIVE) return;
+    const InstState sv = st[item.inst];
+    if (sv.status != HELM_ST_ACTIVE) return;
     if (L0.n != N0) return;                       // launched for another tail size
     constexpr int TOT = tail_elems<D, N0>();
     constexpr int S = N0 + 2;
     constexpr int ROWS = (D == 3) ? N0 * N0 : N0;
-    const c2* __restrict__ gr = (const c2*)L0.rhs;
+    const c2* __restrict__ gr = (const c2*)lev_rhs(L0, item.level, sv.it);
     const c2* __restrict__ ge = (const c2*)L0.e;
     // the starting iterate is read unless the top level is the exactly solved one (which
     // discards it)

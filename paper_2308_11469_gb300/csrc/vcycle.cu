@@ -37,13 +37,14 @@ k_rbgs(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     pdl_trigger();
     typedef typename C2<R>::T c2;
     const MgItem item = items[blockIdx.y];
-    if (st[item.inst].status != HELM_ST_ACTIVE) return;
+    const InstState sv = st[item.inst];
+    if (sv.status != HELM_ST_ACTIVE) return;
     const LevelDesc L = insts[item.inst].lev[item.level];
     const int n = L.n, half = (n + 1) >> 1;
     const int rows = (D == 3) ? n * n : n;
     const long total = (long)rows * half;
     c2* __restrict__ e = (c2*)L.e;
-    const c2* __restrict__ r = (const c2*)L.rhs;
+    const c2* __restrict__ r = (const c2*)lev_rhs(L, item.level, sv.it);
     const long P = L.pitch;
     const long PL = (long)L.pitch * L.rows;
     const R h2 = (R)(L.h * L.h);
@@ -100,13 +101,14 @@ k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     pdl_trigger();
     typedef typename C2<R>::T c2;
     const MgItem item = items[blockIdx.y];
-    if (st[item.inst].status != HELM_ST_ACTIVE) return;
+    const InstState sv = st[item.inst];
+    if (sv.status != HELM_ST_ACTIVE) return;
     const LevelDesc F = insts[item.inst].lev[item.level];
     const LevelDesc C = insts[item.inst].lev[item.level + 1];
     const int nc = C.n;
     const long total = (D == 3) ? (long)nc * nc * nc : (long)nc * nc;
     const c2* __restrict__ e = (const c2*)F.e;
-    const c2* __restrict__ r = (const c2*)F.rhs;
+    const c2* __restrict__ r = (const c2*)lev_rhs(F, item.level, sv.it);
     c2* __restrict__ cr = (c2*)C.rhs;
     c2* __restrict__ ce = (c2*)C.e;
     const long P = F.pitch;

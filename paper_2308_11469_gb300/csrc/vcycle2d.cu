@@ -98,7 +98,8 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const double sigma = insts[item.inst].sigma;
     pdl_wait();
     pdl_trigger();
-    if (st[item.inst].status != HELM_ST_ACTIVE) return;
+    const InstState sv = st[item.inst];
+    if (sv.status != HELM_ST_ACTIVE) return;
     const int n = L.n;
     const int ntx = (n + TX - 1) / TX;
     const int nty = (n + TY - 1) / TY;
@@ -115,7 +116,7 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const int cpar = (gx0 + gy0) & 1;
     const bool zero = (zero_mode == 2) || (zero_mode == 1 && item.level > 0);
     const c2* __restrict__ ge = (const c2*)L.e;
-    const c2* __restrict__ gr = (const c2*)L.rhs;
+    const c2* __restrict__ gr = (const c2*)lev_rhs(L, item.level, sv.it);
     const int P = L.pitch;
     const int lane = threadIdx.x & 31;
     // stage e (or zeros) and rhs with asynchronous copies: every load of the tile is in
@@ -242,7 +243,8 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const LevelDesc C = insts[item.inst].lev[item.level + 1];
     pdl_wait();
     pdl_trigger();
-    if (st[item.inst].status != HELM_ST_ACTIVE) return;
+    const InstState sv = st[item.inst];
+    if (sv.status != HELM_ST_ACTIVE) return;
     const int n = L.n;
     const int ntx = (n + TX - 1) / TX;
     const int nty = (n + TY - 1) / TY;
@@ -265,7 +267,7 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const int PC = C.pitch;
     const int lane = threadIdx.x & 31;
     const c2* __restrict__ ge2 = (const c2*)L.e2;
-    const c2* __restrict__ gr = (const c2*)L.rhs;
+    const c2* __restrict__ gr = (const c2*)lev_rhs(L, item.level, sv.it);
     const int P = L.pitch;
     // e2 is zero (not written by the descent) when the cycle has no pre-smoothing and the
     // level started from zero: e2_mode 2 = every level, 1 = the levels below the finest
@@ -357,14 +359,15 @@ k_restrict_rhs2d(const InstDesc* __restrict__ insts, const InstState* __restrict
     const LevelDesc C = insts[item.inst].lev[item.level + 1];
     pdl_wait();
     pdl_trigger();
-    if (st[item.inst].status != HELM_ST_ACTIVE) return;
+    const InstState sv = st[item.inst];
+    if (sv.status != HELM_ST_ACTIVE) return;
     const int nc = C.n;
     const int ntx = (nc + RX - 1) / RX;
     if ((int)blockIdx.x >= ntx * ((nc + RY - 1) / RY)) return;
     const int X = 1 + (blockIdx.x % ntx) * RX + (threadIdx.x % RX);
     const int Y = 1 + (blockIdx.x / ntx) * RY + (threadIdx.x / RX);
     if (X > nc || Y > nc) return;
-    const c2* __restrict__ gr = (const c2*)L.rhs;
+    const c2* __restrict__ gr = (const c2*)lev_rhs(L, item.level, sv.it);
     const size_t P = L.pitch;
     const size_t o = (size_t)(2 * Y) * P + 2 * X;
     R ax = 0, ay = 0;
