@@ -46,6 +46,8 @@ FP64_PEAK_TFLOPS = 1.25          # GB300 nominal FP64 rate (FMA = 2 flops)
 # 4-instance 1023^2 launch (dram__bytes_read.sum + dram__bytes_write.sum = 168.07 + 67.24 MB
 # over 4 x 1023^2 points), scaled below to the points of an average launch
 RESIDUAL_DRAM_BYTES_PER_POINT = (168.065024e6 + 67.244032e6) / (4 * 1023 ** 2)
+# the same for the finest level's ascent fused with the residual (None: not yet captured)
+UPRES_DRAM_BYTES_PER_POINT = None
 
 
 def _peaks():
@@ -364,11 +366,17 @@ def main():
                 "share": m_s / total_kernel_ms, "bytes_per_launch": b_y / n_l if n_l else 0,
                 "avg_launch_us": 1e3 * m_s / n_l if n_l else 0}
 
-    if name == "helmholtz_residual_update":
-        pts = by / (48 + 2 * eb)
+    if name in ("helmholtz_residual_update", "ascent_residual_update_2d"):
+        if name == "helmholtz_residual_update":
+            pts = by / (48 + 2 * eb)
+            per_pt = RESIDUAL_DRAM_BYTES_PER_POINT
+        else:
+            # one launch per outer step; instance i takes part in iters_i of them
+            pts = float(n) ** 2 * sum(mixed_iters)
+            per_pt = UPRES_DRAM_BYTES_PER_POINT
         flops = 16.0 * pts
         ach = (flops / nl) / ((ms / nl) / 1e3) / 1e12
-        traffic = RESIDUAL_DRAM_BYTES_PER_POINT * pts / nl
+        traffic = per_pt * pts / nl if per_pt else None
         hv = hbm_line(name, (nl, ms, by))
         hv["traffic"] = traffic
         roofline = {"bound": "alu", "kernel": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS,

@@ -126,10 +126,11 @@ struct Instance {
 };
 
 struct LaunchRec {
-    enum Kind { RBGS, RESTRICT, PROLONG, ZERO, TAIL, RESID, CHECK, DOWN, UP, NKINDS } kind;
+    enum Kind { RBGS, RESTRICT, PROLONG, ZERO, TAIL, RESID, CHECK, DOWN, UP, UPRES, NKINDS } kind;
     int off, cnt, work, color, mode;
     double bytes;   // algorithmic bytes of one launch (each datum it must touch, once)
-    int nmax = 0;   // DOWN: the largest level of the launch
+    int nmax = 0;   // DOWN: the largest level of the launch; UPRES: the level-0 size
+    int ninst = 0;  // UPRES: instances of the launch (folded step control)
 };
 
 struct Engine {
@@ -379,7 +380,25 @@ struct Engine {
             nocc += slots[i] ? 1 : 0;
             if (slots[i] && slots[i]->d.damp != 0.0) damp_any = 1;
         }
-        step.push_back({LaunchRec::RESID, 0, nres, nocc, 1, 1, b_res});
+        // 2D complex64 instances of one size whose level 0 is a fused level: level 0's final
+        // ascent and the residual launch become one kernel (k_upres2d)
+        bool fuse = D == 2 && prec != HELM_PREC_FP64 && nu1 <= 4 && nu2 <= 4 && J > 0 && nocc > 0 &&
+                    !step.empty() && step.back().kind == LaunchRec::UP && step.back().off == ph[0].off &&
+                    ph[0].cnt == nocc;
+        int n_all = -1;
+        for (int i = 0; i < cap && fuse; ++i) {
+            if (!slots[i]) continue;
+            const InstDesc& d = slots[i]->d;
+            if ((n_all >= 0 && d.n != n_all) || d.ltail < 1 || !d.lev[0].rhs2) fuse = false;
+            n_all = d.n;
+        }
+        if (fuse) {
+            const int e2_mode = step.back().mode;
+            step.back() = {LaunchRec::UPRES, ph[0].off, ph[0].cnt, upres2d_tiles(n_all), 1, e2_mode, 0.0,
+                           n_all, nocc};
+        } else {
+            step.push_back({LaunchRec::RESID, 0, nres, nocc, 1, 1, b_res});
+        }
         vcyc_plain.clear();
         vcycle(vcyc_plain, false);
         return HELM_OK;
@@ -399,6 +418,16 @@ struct Engine {
             return b;
         }
         if (L.kind == LaunchRec::CHECK) return 0.0;
+        if (L.kind == LaunchRec::UPRES) {
+            // [e2], r_N, coarse e, u_N, f in; u_{N+1}, r_{N+1} out
+            const bool e2z = (L.mode == 2);
+            for (int i = 0; i < cap; ++i)
+                if (slots[i] && st[i].status == HELM_ST_ACTIVE) {
+                    const InstDesc& d = slots[i]->d;
+                    b += pts(d.n) * ((e2z ? 1.0 : 2.0) * eb + 16.0 + 16.0 + 16.0 + eb) + pts(d.lev[1].n) * eb;
+                }
+            return b;
+        }
         for (int q = L.off; q < L.off + L.cnt; ++q) {
             const MgItem& it = h_items[q];
             if (!slots[it.inst] || st[it.inst].status != HELM_ST_ACTIVE) continue;
@@ -472,6 +501,10 @@ struct Engine {
                 else
                     e = launch_residual(D, prec, d_desc, d_state, d_res + L.off, L.cnt, L.mode, s,
                                         nullptr, 0, 0, 0, 0, damp_any);
+                break;
+            case LaunchRec::UPRES:
+                e = launch_upres2d(d_desc, d_state, d_mg + L.off, L.cnt, L.nmax, nu2, L.mode, s, d_ctrl, cap,
+                                   L.ninst, use_cond ? 1 : 0, (unsigned long long)cond, damp_any);
                 break;
             case LaunchRec::CHECK:
                 e = launch_check(d_state, L.cnt, d_ctrl, use_cond ? 1 : 0,

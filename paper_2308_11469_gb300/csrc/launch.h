@@ -91,6 +91,14 @@ cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* s
                             const ResItem* items, int nitems, int mode, cudaStream_t s,
                             int* ctrl = nullptr, int nscan = 0, int ninst = 0, int use_cond = 0,
                             unsigned long long cond_handle = 0, int damp = 0);
+// 2D, complex64 inner solves: level 0's ascent (launch_up2d with nu2 sweeps, e2_mode)
+// fused with the mode-1 residual launch and its folded step control (same arguments as
+// launch_residual's).  items: the level-0 items of every instance (all of size n), whose
+// level 0 keeps two right-hand-side buffers.  Level 0's e is not written.
+cudaError_t launch_upres2d(const InstDesc* insts, InstState* st, const MgItem* items, int nitems, int n,
+                           int nu2, int e2_mode, cudaStream_t s, int* ctrl, int nscan, int ninst,
+                           int use_cond, unsigned long long cond_handle, int damp);
+int upres2d_tiles(int n);
 int residual_tile_rows(int D);
 int residual_tile_planes(int D);
 int residual_tile_cols(int D);

@@ -23,6 +23,7 @@
 #include "launch.h"
 #include "pdl.cuh"
 #include "fp_bits.cuh"
+#include "sweep2d.cuh"
 
 namespace helm {
 namespace {
@@ -167,6 +168,34 @@ __device__ void step_arrive(const InstState* st, const StepCtl& c)
     if (threadIdx.x == 0) c.ctrl[3] = 0;
 }
 
+// The CTA that wrote an instance's last partial: sum the nb partials in tile order,
+// apply the status rule, and (folded step control) arrive for the step.  The partials are
+// read by the first NTH threads whatever the block size (threads beyond add zeros, which
+// leaves sums and maxima of non-negative values unchanged), so a launch with larger CTAs
+// reduces in the same order as the residual kernels.
+__device__ void instance_last(const InstDesc& I, InstState* stp, int mode, const InstState* st_all,
+                              const StepCtl& c)
+{
+    __shared__ double sa[32], sm[32];
+    const int nb = I.nres_blocks;
+    __threadfence();
+    double ta = 0.0, tm = 0.0;
+    if (threadIdx.x < NTH)
+        for (int b = threadIdx.x; b < nb; b += NTH) {
+            ta += __ldcg(I.part + b);
+            const double v = __ldcg(I.part + nb + b);
+            tm = (mode == 0) ? tm + v : fmax(tm, v);
+        }
+    __syncthreads();
+    double fa = 0.0, fm = 0.0;
+    block_reduce<double>(ta, tm, fa, fm, sa, sm, mode == 0);
+    if (threadIdx.x == 0) {
+        finalize(I, stp, fa, fm, mode);
+        *I.count = 0u;
+    }
+    if (c.ctrl) step_arrive(st_all, c);
+}
+
 // Write this tile's partials; the last tile of the instance reduces them all.
 template <typename T>
 __device__ void tile_done(const InstDesc& I, InstState* stp, int tile, T ta0, T tm0, int mode,
@@ -185,22 +214,29 @@ __device__ void tile_done(const InstDesc& I, InstState* stp, int tile, T ta0, T 
     }
     __syncthreads();
     if (!last) return;
-    __threadfence();
-    double ta = 0.0, tm = 0.0;
-    for (int b = threadIdx.x; b < I.nres_blocks; b += blockDim.x) {
-        ta += __ldcg(I.part + b);
-        const double v = __ldcg(I.part + I.nres_blocks + b);
-        tm = (mode == 0) ? tm + v : fmax(tm, v);
-    }
-    __syncthreads();
-    double fa = 0.0, fm = 0.0;
-    block_reduce<double>(ta, tm, fa, fm, sa, sm, mode == 0);
-    if (threadIdx.x == 0) {
-        finalize(I, stp, fa, fm, mode);
-        *I.count = 0u;
-    }
-    if (c.ctrl) step_arrive(st_all, c);
+    instance_last(I, stp, mode, st_all, c);
 }
+
+// r = f - (Delta_h + k^2 + i p) u at one 2D node from its value c and its four neighbours
+// (a, b west / east, d, u south / north): f - cdiag u - (sum of the neighbours) / h^2, and
+// for DAMP the coupling - i p u.
+template <bool DAMP>
+__device__ __forceinline__ double2 helm_resid2d(double2 c, double2 a, double2 b, double2 d, double2 u,
+                                                double2 fv, double mih2, double mcdiag, double damp)
+{
+    double2 r;
+    r.x = fma((a.x + b.x) + (d.x + u.x), mih2, fma(c.x, mcdiag, fv.x));
+    r.y = fma((a.y + b.y) + (d.y + u.y), mih2, fma(c.y, mcdiag, fv.y));
+    if constexpr (DAMP) {
+        r.x = fma(c.y, damp, r.x);
+        r.y = fma(c.x, -damp, r.y);
+    }
+    return r;
+}
+
+// |v|^2 of an inner-precision complex value, rounded the same way in every kernel
+template <typename C>
+__device__ __forceinline__ auto abs2(C v) -> decltype(v.x) { return fma(v.y, v.y, v.x * v.x); }
 
 // ---------------------------------------------------------------------------
 // 2D: 32 x 32 tiles, u_{N+1} staged in shared memory with a 1-node halo
@@ -248,7 +284,7 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
                 v.x += Inner<R>::widen(ev.x);
                 v.y += Inner<R>::widen(ev.y);
                 if (lx >= 1 && lx <= T2 && ly >= 1 && ly <= T2)
-                    emax2 = fmax(emax2, ev.x * ev.x + ev.y * ev.y);
+                    emax2 = fmax(emax2, abs2(ev));
             }
         }
         U[q] = v;
@@ -270,18 +306,11 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
         const double2 a = U[o - 1], b = U[o + 1], d = U[o - (T2 + 2)], u = U[o + (T2 + 2)];
         if (MODE == 1) uout[gy * S + gx] = c;
         const double2 fv = f[(size_t)(gy - 1) * n + (gx - 1)];
-        // r = f - (Delta_h + k^2) u = f - cdiag u - (sum of the 4 neighbours) / h^2
-        double2 r;
-        r.x = fma((a.x + b.x) + (d.x + u.x), mih2, fma(c.x, mcdiag, fv.x));
-        r.y = fma((a.y + b.y) + (d.y + u.y), mih2, fma(c.y, mcdiag, fv.y));
-        if constexpr (DAMP) {                   // - i p u: the damping couples the lanes
-            r.x = fma(c.y, damp, r.x);
-            r.y = fma(c.x, -damp, r.y);
-        }
+        const double2 r = helm_resid2d<DAMP>(c, a, b, d, u, fv, mih2, mcdiag, damp);
         const c2 ri = Inner<R>::from(r);
         rhs[gy * P + gx] = ri;
         if (MODE == 1) {
-            r2 += ri.x * ri.x + ri.y * ri.y;
+            r2 += abs2(ri);
         } else {
             // once per solve, in FP64: ||r_0||^2 and ||b||^2, b = f - (wall neighbours)/h^2
             // formed with the same operations as r (so r_0 = b bit for bit from a zero start)
@@ -322,6 +351,230 @@ k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
 }
 
 // ---------------------------------------------------------------------------
+// 2D, complex64 inner solves: level 0's ascent fused with the residual launch
+// ---------------------------------------------------------------------------
+// An outer step ends with level 0's prolongation + correction + nu2 sweeps (k_up2d),
+// whose only reader is the residual launch.  k_upres2d does both on a UX x 32 tile: the
+// sweeps run on a window one node wider than the ascent's (halo 2 nu2 + 1), so e_N is
+// final on the tile plus a 1-node ring; u_{N+1} = u_N + e_N is formed there in shared
+// memory, written once, and r_{N+1} follows from the staged values.  e_N never goes to
+// global memory.  The tile is one or two of the residual kernel's 32 x 32 tiles side by
+// side, and each (256 threads) forms its partials with the residual kernel's per-node
+// arithmetic, node-to-thread map and summation order, so iterates, residuals and the
+// relres history are those of the two-launch path bit for bit.  Level 0 keeps r_N and
+// r_{N+1} in separate buffers (step parity), so tiles still sweeping with r_N never see
+// another tile's r_{N+1}.
+// UX: tile width, 64 (512 threads, two residual tiles) or 32 (256 threads, one).
+constexpr int UPY = 32;
+
+template <int NU, int UX> constexpr size_t upres_bytes()
+{
+    constexpr int H = 2 * NU + 1, W = UX + 2 * H, HH = UPY + 2 * H;
+    return (size_t)(UX + 2) * (UPY + 2) * sizeof(double2) +
+           ((size_t)2 * W * HH + (size_t)(W / 2 + 2) * (HH / 2 + 2)) * sizeof(float2);
+}
+
+template <int NU, bool DAMP, int UX>
+__global__ void __launch_bounds__(UX * 8, 1024 / (UX * 8))
+k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
+          const MgItem* __restrict__ items, int e2_mode, StepCtl ctl)
+{
+    typedef float R;
+    typedef float2 c2;
+    constexpr int TX = UX, TY = UPY;
+    constexpr int NTU = UX * 8, NWU = NTU / 32;
+    constexpr int H = 2 * NU + 1;
+    constexpr int W = TX + 2 * H, HH = TY + 2 * H;
+    constexpr int CW = W / 2 + 2, CH = HH / 2 + 2;
+    constexpr int UW = TX + 2, UH = TY + 2;
+    typedef Planes<W> PL;
+    static_assert(TX % T2 == 0 && TY == T2 && NTU == (TX / T2) * NTH, "NTH threads per residual tile");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double sa[NWU], sm[NWU];
+    __shared__ int last;
+    // work item and descriptors are host-written: read them before the wait
+    const MgItem item = items[blockIdx.y];
+    const InstDesc& I = insts[item.inst];
+    const LevelDesc L = I.lev[0];
+    const LevelDesc C = I.lev[1];
+    pdl_wait();
+    pdl_trigger();
+    InstState* stp = st + item.inst;
+    const InstState sv = *stp;
+    if (sv.status != HELM_ST_ACTIVE) {           // uniform over the CTA
+        if (ctl.ctrl && blockIdx.x == 0) step_arrive(st, ctl);
+        return;
+    }
+    const int n = L.n;
+    const int ntx = (n + TX - 1) / TX;
+    if ((int)blockIdx.x >= ntx * ((n + TY - 1) / TY)) return;
+    const int bx = blockIdx.x % ntx, by = blockIdx.x / ntx;
+    const int x0 = 1 + bx * TX, y0 = 1 + by * TY;
+    double2* const U = reinterpret_cast<double2*>(smem_raw);
+    c2* const base = reinterpret_cast<c2*>(smem_raw + (size_t)UW * UH * sizeof(double2));
+    constexpr int PS = HH * PL::WH;
+    c2* const E0 = base;
+    c2* const E1 = base + PS;
+    c2* const R0 = base + 2 * PS;
+    c2* const R1 = base + 3 * PS;
+    c2* const Cs = base + 4 * PS;
+    const int gx0 = x0 - H, gy0 = y0 - H;
+    const int cpar = (gx0 + gy0) & 1;
+    const int cx0 = max(gx0, 0) >> 1, cy0 = max(gy0, 0) >> 1;
+    const int nc1 = C.n + 1;
+    const c2* __restrict__ gce = (const c2*)C.e;
+    const int PC = C.pitch;
+    const c2* __restrict__ ge2 = (const c2*)L.e2;
+    const c2* __restrict__ gr = (const c2*)lev_rhs(L, 0, sv.it);
+    const int P = L.pitch;
+    const int S = n + 2;
+    const double2* __restrict__ uin = I.u[sv.it & 1];
+    const int lane = threadIdx.x & 31;
+    const bool e2z = (e2_mode == 2);             // e2 zero on every level, level 0 included
+    // stage u_N on the tile plus a 1-node ring, the coarse window, e2 and r_N
+    for (int q = threadIdx.x; q < UW * UH; q += NTU) {
+        const int gx = x0 - 1 + q % UW, gy = y0 - 1 + q / UW;
+        const bool in = gx <= n + 1 && gy <= n + 1;
+        cp_async_elem<16>(U + q, uin + (in ? (size_t)gy * S + gx : 0), in);
+    }
+    for (int cy = threadIdx.x >> 5; cy < CH; cy += NWU) {
+        const int Y = cy0 + cy;
+#pragma unroll
+        for (int cx = lane; cx < CW; cx += 32) {
+            const int X = cx0 + cx;
+            const bool in = X <= nc1 && Y <= nc1;
+            cp_async_elem<sizeof(c2)>(Cs + cy * CW + cx, gce + (in ? (size_t)Y * PC + X : 0), in);
+        }
+    }
+    for (int ly = threadIdx.x >> 5; ly < HH; ly += NWU) {
+        const int gy = gy0 + ly;
+        const bool yin = gy >= 1 && gy <= n;
+#pragma unroll
+        for (int lx = lane; lx < W; lx += 32) {
+            const int gx = gx0 + lx;
+            const bool in = yin && gx >= 1 && gx <= n;
+            const size_t g = in ? (size_t)gy * P + gx : 0;
+            const int c = (lx + ly + cpar) & 1;
+            const int o = PL::at(lx, ly);
+            if (e2z) (c ? E1 : E0)[o] = cz<c2>();
+            else cp_async_elem<sizeof(c2)>((c ? E1 : E0) + o, ge2 + g, in);
+            cp_async_elem<sizeof(c2)>((c ? R1 : R0) + o, gr + g, in);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // correction: e2 + multilinear interpolation of the coarse iterate (interior nodes)
+    for (int ly = threadIdx.x >> 5; ly < HH; ly += NWU) {
+        const int gy = gy0 + ly;
+        if (gy < 1 || gy > n) continue;
+        const int Y0 = (gy >> 1) - cy0, Y1 = ((gy + 1) >> 1) - cy0;
+#pragma unroll
+        for (int lx = lane; lx < W; lx += 32) {
+            const int gx = gx0 + lx;
+            if (gx < 1 || gx > n) continue;
+            const int X0 = (gx >> 1) - cx0, X1 = ((gx + 1) >> 1) - cx0;
+            const c2 a = Cs[Y0 * CW + X0], b = Cs[Y0 * CW + X1];
+            const c2 c = Cs[Y1 * CW + X0], d = Cs[Y1 * CW + X1];
+            c2* Ep = (((lx + ly + cpar) & 1) ? E1 : E0) + PL::at(lx, ly);
+            c2 v = *Ep;
+            v.x += (R)0.25 * (((a.x + b.x) + c.x) + d.x);
+            v.y += (R)0.25 * (((a.y + b.y) + c.y) + d.y);
+            *Ep = v;
+        }
+    }
+    __syncthreads();
+    const R h2 = (R)(L.h * L.h);
+    const R dinv = (R)L.dinv;
+    int ring = 2 * NU;                           // the last half-sweep covers ring 1
+#pragma unroll 1
+    for (int s = 0; s < NU; ++s) {
+        half_sweep<R, W, TX, TY, NWU>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, dinv, 0);
+        __syncthreads();
+        half_sweep<R, W, TX, TY, NWU>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, dinv, 1);
+        __syncthreads();
+    }
+    // u_{N+1} = u_N + e_N on the interior nodes of the u window
+    for (int q = threadIdx.x; q < UW * UH; q += NTU) {
+        const int gx = x0 - 1 + q % UW, gy = y0 - 1 + q / UW;
+        if (gx < 1 || gx > n || gy < 1 || gy > n) continue;
+        const int ex = gx - gx0, ey = gy - gy0;
+        const c2 ev = (((ex + ey + cpar) & 1) ? E1 : E0)[PL::at(ex, ey)];
+        double2 v = U[q];
+        v.x += Inner<R>::widen(ev.x);
+        v.y += Inner<R>::widen(ev.y);
+        U[q] = v;
+    }
+    __syncthreads();
+    // r_{N+1}: the threads 256 hf .. 256 hf + 255 take residual tile ((TX / 32) bx + hf, by),
+    // thread t of them the nodes (t mod 32, t / 32 + 8 k) of that tile, as in k_residual2d
+    const int hf = threadIdx.x >> 8;
+    const int t = threadIdx.x & 255;
+    const int rtx = (TX / T2) * bx + hf;
+    double2* __restrict__ uout = I.u[(sv.it + 1) & 1];
+    c2* __restrict__ rhs = (c2*)lev_rhs(L, 0, sv.it + 1);
+    const double2* __restrict__ f = I.f;
+    const double mih2 = -I.ih2;
+    const double mcdiag = -I.cdiag;
+    const double damp = I.damp;
+    R r2 = 0, emax2 = 0;
+    const int lx = (t & 31) + 1 + 32 * hf;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int ly = (t >> 5) + 8 * k + 1;
+        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        if (gx > n || gy > n) continue;
+        const int o = ly * UW + lx;
+        const double2 c = U[o];
+        const double2 a = U[o - 1], b = U[o + 1], d = U[o - UW], u = U[o + UW];
+        uout[(size_t)gy * S + gx] = c;
+        const double2 fv = f[(size_t)(gy - 1) * n + (gx - 1)];
+        const double2 r = helm_resid2d<DAMP>(c, a, b, d, u, fv, mih2, mcdiag, damp);
+        const c2 ri = Inner<R>::from(r);
+        rhs[(size_t)gy * P + gx] = ri;
+        r2 += abs2(ri);
+        const int ex = gx - gx0, ey = gy - gy0;
+        emax2 = fmax(emax2, abs2((((ex + ey + cpar) & 1) ? E1 : E0)[PL::at(ex, ey)]));
+    }
+    // per-half reduction in block_reduce's order (warps of the half, then their values)
+    R a = r2, m = emax2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        const R mo = __shfl_xor_sync(0xffffffffu, m, o);
+        m = m > mo ? m : mo;
+    }
+    const int w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sa[w] = (double)a;
+        sm[w] = (double)m;
+    }
+    __syncthreads();
+    const int nb = I.nres_blocks;
+    const bool two = TX == 2 * T2 && 2 * bx + 1 < I.res_tx;
+    if (t == 0 && (hf == 0 || two)) {
+        double ra = 0.0, rm = 0.0;
+        for (int i = 0; i < NTH / 32; ++i) {
+            ra += sa[8 * hf + i];
+            rm = fmax(rm, sm[8 * hf + i]);
+        }
+        const int tile = by * I.res_tx + rtx;
+        I.part[tile] = ra;
+        I.part[nb + tile] = rm;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned k = two ? 2u : 1u;
+        const unsigned prev = atomicAdd(I.count, k);
+        last = (prev + k == (unsigned)nb);
+    }
+    __syncthreads();
+    if (!last) return;
+    instance_last(I, stp, 1, st, ctl);
+}
+
+// ---------------------------------------------------------------------------
 // 3D: 32 x 8 columns marching over 16 z-planes; u_{N+1} staged once per node in a
 // three-plane ring of shared memory (1-node halo in x and y)
 // ---------------------------------------------------------------------------
@@ -350,7 +603,7 @@ __device__ __forceinline__ R stage_plane3d(double2* Up, const double2* __restric
                 v.x += Inner<R>::widen(ev.x);
                 v.y += Inner<R>::widen(ev.y);
                 if (own && lx >= 1 && lx <= T3X && ly >= 1 && ly <= T3Y)
-                    emax2 = fmax(emax2, ev.x * ev.x + ev.y * ev.y);
+                    emax2 = fmax(emax2, abs2(ev));
             }
         }
         Up[q] = v;
@@ -421,7 +674,7 @@ __device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ ins
             const c2 ri = Inner<R>::from(r);
             rhs[oe] = ri;
             if (MODE == 1) {
-                r2 += ri.x * ri.x + ri.y * ri.y;
+                r2 += abs2(ri);
             } else {
                 // once per solve, in FP64: ||r_0||^2 and ||b||^2 (same operations as r)
                 r2d += r.x * r.x + r.y * r.y;
@@ -752,6 +1005,47 @@ cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* s
     return cudaGetLastError();
 }
 
+// tile width of the fused kernel: 32 (256-thread CTAs, four resident per SM, so CTAs in
+// their smoothing phase and CTAs in their FP64 residual phase share each SM)
+constexpr int UPX = 32;
+
+int upres2d_tiles(int n) { return ((n + UPX - 1) / UPX) * ((n + UPY - 1) / UPY); }
+
+cudaError_t launch_upres2d(const InstDesc* insts, InstState* st, const MgItem* items, int nitems, int n,
+                           int nu2, int e2_mode, cudaStream_t s, int* ctrl, int nscan, int ninst,
+                           int use_cond, unsigned long long cond_handle, int damp)
+{
+    if (nitems <= 0) return cudaSuccess;
+    const StepCtl c{ctrl, nscan, ninst, use_cond, cond_handle};
+    const dim3 g(upres2d_tiles(n), nitems);
+    const dim3 b(UPX * 8);
+#define HELM_UR(NU)                                                                                 \
+    case NU:                                                                                        \
+        if (damp) launch_k(k_upres2d<NU, true, UPX>, g, b, upres_bytes<NU, UPX>(), s, insts, st, items, \
+                           e2_mode, c);                                                             \
+        else launch_k(k_upres2d<NU, false, UPX>, g, b, upres_bytes<NU, UPX>(), s, insts, st, items,     \
+                      e2_mode, c);                                                                  \
+        break;
+    switch (nu2) {
+        HELM_UR(0) HELM_UR(1) HELM_UR(2) HELM_UR(3) HELM_UR(4)
+    default: return cudaErrorInvalidValue;
+    }
+#undef HELM_UR
+    return cudaGetLastError();
+}
+
+template <int NU>
+cudaError_t setup_upres()
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_upres2d<NU, false, UPX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)upres_bytes<NU, UPX>())) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_upres2d<NU, true, UPX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)upres_bytes<NU, UPX>())) != cudaSuccess) return e;
+    if ((e = max_carveout(k_upres2d<NU, false, UPX>)) != cudaSuccess) return e;
+    return max_carveout(k_upres2d<NU, true, UPX>);
+}
+
 cudaError_t setup_outer()
 {
     cudaError_t e;
@@ -773,6 +1067,11 @@ cudaError_t setup_outer()
     HELM_CO(k_residual2d)
     HELM_CO(k_residual3d)
 #undef HELM_CO
+    if ((e = setup_upres<0>()) != cudaSuccess) return e;
+    if ((e = setup_upres<1>()) != cudaSuccess) return e;
+    if ((e = setup_upres<2>()) != cudaSuccess) return e;
+    if ((e = setup_upres<3>()) != cudaSuccess) return e;
+    if ((e = setup_upres<4>()) != cudaSuccess) return e;
     return max_carveout(k_check);
 }
 
