@@ -173,10 +173,10 @@ __device__ void step_arrive(const InstState* st, const StepCtl& c)
 // read by the first NTH threads whatever the block size (threads beyond add zeros, which
 // leaves sums and maxima of non-negative values unchanged), so a launch with larger CTAs
 // reduces in the same order as the residual kernels.
+// sa, sm: shared scratch of one double per warp of the CTA.
 __device__ void instance_last(const InstDesc& I, InstState* stp, int mode, const InstState* st_all,
-                              const StepCtl& c)
+                              const StepCtl& c, double* sa, double* sm)
 {
-    __shared__ double sa[32], sm[32];
     const int nb = I.nres_blocks;
     __threadfence();
     double ta = 0.0, tm = 0.0;
@@ -214,7 +214,7 @@ __device__ void tile_done(const InstDesc& I, InstState* stp, int tile, T ta0, T 
     }
     __syncthreads();
     if (!last) return;
-    instance_last(I, stp, mode, st_all, c);
+    instance_last(I, stp, mode, st_all, c, sa, sm);
 }
 
 // r = f - (Delta_h + k^2 + i p) u at one 2D node from its value c and its four neighbours
@@ -367,15 +367,20 @@ k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
 // UX: tile width, 64 (512 threads, two residual tiles) or 32 (256 threads, one).
 constexpr int UPY = 32;
 
+// The coarse window: fine nodes gx0 .. gx0 + W - 1 (gx0 = x0 - H even when H is odd) read
+// coarse X = gx >> 1 .. (gx + 1) >> 1, i.e. W / 2 + 1 columns from cx0 = gx0 >> 1.
+template <int NU, int UX> constexpr int upres_cw() { return (UX + 2 * (2 * NU + 1)) / 2 + 1; }
+template <int NU> constexpr int upres_ch() { return (UPY + 2 * (2 * NU + 1)) / 2 + 1; }
+
 template <int NU, int UX> constexpr size_t upres_bytes()
 {
     constexpr int H = 2 * NU + 1, W = UX + 2 * H, HH = UPY + 2 * H;
     return (size_t)(UX + 2) * (UPY + 2) * sizeof(double2) +
-           ((size_t)2 * W * HH + (size_t)(W / 2 + 2) * (HH / 2 + 2)) * sizeof(float2);
+           ((size_t)2 * W * HH + (size_t)upres_cw<NU, UX>() * upres_ch<NU>()) * sizeof(float2);
 }
 
 template <int NU, bool DAMP, int UX>
-__global__ void __launch_bounds__(UX * 8, 1024 / (UX * 8))
+__global__ void __launch_bounds__(UX * 8, UX == 32 ? 5 : 2)
 k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
           const MgItem* __restrict__ items, int e2_mode, StepCtl ctl)
 {
@@ -385,8 +390,9 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     constexpr int NTU = UX * 8, NWU = NTU / 32;
     constexpr int H = 2 * NU + 1;
     constexpr int W = TX + 2 * H, HH = TY + 2 * H;
-    constexpr int CW = W / 2 + 2, CH = HH / 2 + 2;
+    constexpr int CW = upres_cw<NU, UX>(), CH = upres_ch<NU>();
     constexpr int UW = TX + 2, UH = TY + 2;
+    static_assert(H % 2 == 1 && TX % 2 == 0 && TY % 2 == 0, "gx0, gy0 even");
     typedef Planes<W> PL;
     static_assert(TX % T2 == 0 && TY == T2 && NTU == (TX / T2) * NTH, "NTH threads per residual tile");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -571,7 +577,8 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     }
     __syncthreads();
     if (!last) return;
-    instance_last(I, stp, 1, st, ctl);
+    __syncthreads();                             // sa / sm are reused
+    instance_last(I, stp, 1, st, ctl, sa, sm);
 }
 
 // ---------------------------------------------------------------------------
