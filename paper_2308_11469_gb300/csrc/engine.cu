@@ -544,11 +544,17 @@ struct Engine {
         return HELM_OK;
     }
 
+    // What the launch plan and its graph depend on: the slot geometry, the cycle, and
+    // whether any instance has a damping term (it selects the residual kernels' variant).
     std::vector<long> current_signature() const
     {
         std::vector<long> sig{cap, nu1, nu2, cycles};
-        for (int i = 0; i < cap; ++i)
+        long damp = 0;
+        for (int i = 0; i < cap; ++i) {
             sig.push_back(slots[i] ? (long)slots[i]->d.n * 4 + (long)slots[i]->d.D : -1L);
+            if (slots[i] && slots[i]->d.damp != 0.0) damp = 1;
+        }
+        sig.push_back(damp);
         return sig;
     }
 

@@ -182,3 +182,26 @@ def test_batch_equals_single_solve(B):
     B.helm_plan_destroy(plan)
     assert r[0] == st and r[1] == iters
     assert np.array_equal(u.cpu().numpy(), u_single)
+
+
+def test_batch_slot_reused_by_a_damped_solve(B):
+    # an undamped solve retires, a damped one of the same size takes its slot: the launch
+    # plan must switch to the residual that carries the damping term
+    q = inputs.gaussian_cavity_2d(2.0, seed=2, n=127)
+    alpha, p = q.k ** 2 + 6.0, 4.0
+    st_ref, it_ref, _, _, u_ref = _solve(B, 2, q.n, q.h, q.k, q.f, q.g, 1, alpha, p, 1e-8, 2000)
+    batch = B.helm_batch_create(0)
+    plain = B.helm_plan_create(2, q.n, q.h, q.k, prec=1)
+    damped = _plan(B, 2, q.n, q.h, q.k, 1, alpha, p)
+    for plan, want in ((plain, None), (damped, u_ref)):
+        u = torch.zeros((q.n + 2,) * 2, dtype=torch.complex128, device=DEV)
+        t = B.helm_batch_submit(batch, plan, _t(q.f), _t(q.g), u, 1e-8, 2000)
+        B.helm_batch_step(batch, 0)
+        r = B.helm_batch_poll(batch, t, 2000)
+        assert r[0] == B.HELM_CONVERGED
+        if want is not None:
+            assert r[1] == it_ref
+            assert np.array_equal(u.cpu().numpy(), want)
+    B.helm_batch_destroy(batch)
+    B.helm_plan_destroy(plain)
+    B.helm_plan_destroy(damped)
