@@ -133,6 +133,35 @@ struct LaunchRec {
     int ninst = 0;  // UPRES: instances of the launch (folded step control)
 };
 
+// The launch plan of one slot geometry: its work-item tables, launch sequences and the
+// captured graph of one outer step (kernel parameters point into d_mg / d_res).
+struct PlanState {
+    std::vector<LaunchRec> step, vcyc_plain;
+    std::vector<MgItem> h_items;
+    MgItem* d_mg = nullptr;
+    size_t mg_cap = 0;
+    ResItem* d_res = nullptr;
+    size_t res_cap = 0;
+    int nres = 0, max_tail = 1, damp_any = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+    std::vector<long> plan_sig, graph_sig;
+
+    void destroy()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (d_mg) cudaFree(d_mg);
+        if (d_res) cudaFree(d_res);
+        exec = nullptr;
+        graph = nullptr;
+        d_mg = nullptr;
+        d_res = nullptr;
+        mg_cap = res_cap = 0;
+    }
+};
+
 struct Engine {
     int D = 2, prec = 1;
     int nu1 = 2, nu2 = 2, cycles = 1;
@@ -161,10 +190,36 @@ struct Engine {
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle cond = 0;
 
+    // Plans of other slot geometries, least recently used first: a batch whose geometry
+    // alternates (solves joining a running batch, then retiring) reuses their graphs.
+    static constexpr size_t PARKED_MAX = 3;
+    std::vector<PlanState> parked;
+
     ~Engine() { release(); }
+
+    void swap_plan(PlanState& p)
+    {
+        std::swap(step, p.step);
+        std::swap(vcyc_plain, p.vcyc_plain);
+        std::swap(h_items, p.h_items);
+        std::swap(d_mg, p.d_mg);
+        std::swap(mg_cap, p.mg_cap);
+        std::swap(d_res, p.d_res);
+        std::swap(res_cap, p.res_cap);
+        std::swap(nres, p.nres);
+        std::swap(max_tail, p.max_tail);
+        std::swap(damp_any, p.damp_any);
+        std::swap(graph, p.graph);
+        std::swap(exec, p.exec);
+        std::swap(cond, p.cond);
+        std::swap(plan_sig, p.plan_sig);
+        std::swap(graph_sig, p.graph_sig);
+    }
 
     void release()
     {
+        for (PlanState& p : parked) p.destroy();
+        parked.clear();
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         exec = nullptr;
@@ -566,9 +621,28 @@ struct Engine {
         if (!dirty) return HELM_OK;
         std::vector<long> sig = current_signature();
         if (sig != plan_sig) {
-            helm_status st = rebuild_plan();
-            if (st != HELM_OK) return st;
-            plan_sig = sig;
+            // park the current plan (a plan invalidated by a temporary rebuild is dropped)
+            PlanState cur;
+            swap_plan(cur);
+            if (!cur.plan_sig.empty()) {
+                parked.push_back(std::move(cur));
+                if (parked.size() > PARKED_MAX) {
+                    parked.front().destroy();
+                    parked.erase(parked.begin());
+                }
+            } else {
+                cur.destroy();
+            }
+            auto it = std::find_if(parked.begin(), parked.end(),
+                                   [&](const PlanState& p) { return p.plan_sig == sig; });
+            if (it != parked.end()) {
+                swap_plan(*it);                 // the engine's fields were empty
+                parked.erase(it);
+            } else {
+                helm_status st = rebuild_plan();
+                if (st != HELM_OK) return st;
+                plan_sig = sig;
+            }
         }
         dirty = false;
         return HELM_OK;
