@@ -49,8 +49,9 @@ FP64_PEAK_TFLOPS = 1.25          # GB300 nominal FP64 rate (FMA = 2 flops)
 # 4-instance 1023^2 launch (dram__bytes_read.sum + dram__bytes_write.sum = 168.07 + 67.24 MB
 # over 4 x 1023^2 points), scaled below to the points of an average launch
 RESIDUAL_DRAM_BYTES_PER_POINT = (168.065024e6 + 67.244032e6) / (4 * 1023 ** 2)
-# the same for the finest level's ascent fused with the residual (None: not yet captured)
-UPRES_DRAM_BYTES_PER_POINT = None
+# the same for the finest level's ascent fused with the residual: one ncu capture of a
+# 4-instance 1023^2 launch (176.66 + 67.18 MB)
+UPRES_DRAM_BYTES_PER_POINT = (176.6592e6 + 67.184128e6) / (4 * 1023 ** 2)
 
 
 def _peaks():
