@@ -264,6 +264,14 @@ HELM_API helm_status helm_batch_step(helm_batch* batch, int max_steps);
 /* Inner schedule (as helm_plan_set_cycle) used by every solve of the batch from the next
  * step on (the batch's solves share their launches, hence one schedule). */
 HELM_API helm_status helm_batch_set_cycle(helm_batch* batch, int nu1, int nu2, int cycles);
+/* Solves of one kernel class (dimension, precision) are spread over `lanes` (1 ..
+ * HELM_MAX_LANES, default 4) independent launch streams: each submission joins the lane
+ * with the fewest solves, and helm_batch_step runs the lanes' step graphs concurrently,
+ * so one lane's FP64 residual overlaps another lane's coarse multigrid levels.  Applies
+ * to later submissions; results do not depend on the lane.  HELM_EINVAL outside the range.
+ * (The lane split is a scheduling choice of this library; the paper has no counterpart.) */
+#define HELM_MAX_LANES 4
+HELM_API helm_status helm_batch_set_lanes(helm_batch* batch, int lanes);
 HELM_API helm_status helm_batch_poll(helm_batch* batch, uint64_t ticket, int* done, int* status,
                             int* iters, double* res_hist);
 /*

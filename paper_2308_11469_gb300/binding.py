@@ -64,6 +64,7 @@ _SIGS = {
     "helm_batch_submit_geom": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, _vp,
                                          _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_uint64)]),
     "helm_batch_set_cycle": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
+    "helm_batch_set_lanes": (C.c_int, [_vp, C.c_int]),
     "helm_plan_autotune": (C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int),
                                      C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "helm_batch_poll": (C.c_int, [_vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -361,6 +362,10 @@ def helm_batch_step(batch: _Batch, max_steps: int = 0) -> None:
 
 def helm_batch_set_cycle(batch: _Batch, nu1: int, nu2: int, cycles: int = 1) -> None:
     _check(load().helm_batch_set_cycle(batch.handle, nu1, nu2, cycles), "helm_batch_set_cycle")
+
+
+def helm_batch_set_lanes(batch: _Batch, lanes: int) -> None:
+    _check(load().helm_batch_set_lanes(batch.handle, int(lanes)), "helm_batch_set_lanes")
 
 
 def helm_batch_poll(batch: _Batch, ticket: int, max_outer: int):

@@ -808,8 +808,12 @@ struct helm_plan {
 struct helm_batch {
     size_t cap_bytes = 0, used = 0;
     int nu1 = 2, nu2 = 2, cycles = 1;           // inner schedule of every engine
+    // Solves of one kernel class are spread over `lanes` engines (each with its own graph
+    // on its own stream, launched concurrently), so one lane's FP64-bound residual runs
+    // beside another lane's latency-bound coarse levels.
+    int lanes = 4;
     cudaStream_t stream = nullptr;
-    std::map<int, std::unique_ptr<Engine>> engines;   // key = 2 * D + prec
+    std::map<int, std::unique_ptr<Engine>> engines;   // key = (2 * D + prec) * HELM_MAX_LANES + lane
     std::map<int, cudaStream_t> eng_streams;
     cudaEvent_t fork = nullptr;
     std::map<int, cudaEvent_t> join;
@@ -1287,7 +1291,17 @@ static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, 
     const size_t need = layout(probe, D, n, h, k, prec, nullptr) +
                         (2 * (size_t)max_outer + 1) * sizeof(double);
     if (b->cap_bytes && b->used + need > b->cap_bytes) return HELM_ENOMEM;
-    const int key = 2 * D + prec;
+    // the lane of this class with the fewest solves in it
+    int key = (2 * D + prec) * HELM_MAX_LANES;
+    {
+        int best = INT_MAX;
+        for (int lane = 0; lane < b->lanes; ++lane) {
+            const int k = (2 * D + prec) * HELM_MAX_LANES + lane;
+            auto e = b->engines.find(k);
+            const int a = (e == b->engines.end()) ? 0 : e->second->active_count();
+            if (a < best) { best = a; key = k; }
+        }
+    }
     Engine* E = nullptr;
     auto it = b->engines.find(key);
     if (it == b->engines.end()) {
@@ -1396,6 +1410,13 @@ static helm_status retire_finished(helm_batch* b)
         E->dirty = true;
     }
     HELM_CK(cudaStreamSynchronize(b->stream));
+    return HELM_OK;
+}
+
+helm_status helm_batch_set_lanes(helm_batch* b, int lanes)
+{
+    if (!b || lanes < 1 || lanes > HELM_MAX_LANES) return HELM_EINVAL;
+    b->lanes = lanes;
     return HELM_OK;
 }
 
