@@ -139,3 +139,34 @@ def test_late_arrivals_join_running_batch(B):
         assert np.array_equal(r[2], hist)
         assert np.array_equal(buf[2].cpu().numpy(), u)
     B.helm_batch_destroy(batch)
+
+
+def test_lanes_do_not_change_results(B):
+    # the same submissions spread over 1, 2 or 4 concurrent lanes give the same results
+    probs = [inputs.gaussian_cavity_2d(k, seed=3, n=127) for k in (1.0, 2.0, 3.0, 4.0)]
+    out = {}
+    for lanes in (1, 2, 4):
+        batch = B.helm_batch_create(0)
+        B.helm_batch_set_lanes(batch, lanes)
+        us, ts, keep = [], [], []
+        for p in probs:
+            plan = B.helm_plan_create(2, p.n, p.h, p.k, prec=1)
+            # the batch reads f and g when it steps: they must outlive the submission
+            f, g = torch.from_numpy(p.f).to(DEV), torch.from_numpy(p.g).to(DEV)
+            u = torch.zeros((p.n + 2,) * 2, dtype=torch.complex128, device=DEV)
+            ts.append(B.helm_batch_submit(batch, plan, f, g, u, 1e-8, 2000))
+            B.helm_plan_destroy(plan)
+            keep.append((f, g))
+            us.append(u)
+        B.helm_batch_step(batch, 0)
+        out[lanes] = [(B.helm_batch_poll(batch, t, 2000), u.cpu().numpy()) for t, u in zip(ts, us)]
+        B.helm_batch_destroy(batch)
+    for lanes in (2, 4):
+        for (r1, u1), (r2, u2) in zip(out[1], out[lanes]):
+            assert r1[0] == r2[0] == B.HELM_CONVERGED and r1[1] == r2[1]
+            assert np.array_equal(r1[2], r2[2]) and np.array_equal(u1, u2)
+    batch = B.helm_batch_create(0)
+    for bad in (0, 5):
+        with pytest.raises(B.HelmError):
+            B.helm_batch_set_lanes(batch, bad)
+    B.helm_batch_destroy(batch)
