@@ -372,15 +372,23 @@ constexpr int UPY = 32;
 template <int NU, int UX> constexpr int upres_cw() { return (UX + 2 * (2 * NU + 1)) / 2 + 1; }
 template <int NU> constexpr int upres_ch() { return (UPY + 2 * (2 * NU + 1)) / 2 + 1; }
 
+// u_N is staged once the sweeps are done, into the space of the rhs planes and the coarse
+// window (dead by then): the CTA needs the iterate planes plus the larger of the two, which
+// lets 6 CTAs share an SM instead of 5.
+constexpr bool UPRES_LATE_U = true;
+
 template <int NU, int UX> constexpr size_t upres_bytes()
 {
     constexpr int H = 2 * NU + 1, W = UX + 2 * H, HH = UPY + 2 * H;
-    return (size_t)(UX + 2) * (UPY + 2) * sizeof(double2) +
-           ((size_t)2 * W * HH + (size_t)upres_cw<NU, UX>() * upres_ch<NU>()) * sizeof(float2);
+    constexpr size_t ub = (size_t)(UX + 2) * (UPY + 2) * sizeof(double2);
+    constexpr size_t planes = (size_t)W * HH * sizeof(float2);          // E0 + E1 (or R0 + R1)
+    constexpr size_t cs = (size_t)upres_cw<NU, UX>() * upres_ch<NU>() * sizeof(float2);
+    if constexpr (UPRES_LATE_U) return planes + (ub > planes + cs ? ub : planes + cs);
+    return ub + 2 * planes + cs;
 }
 
 template <int NU, bool DAMP, int UX>
-__global__ void __launch_bounds__(UX * 8, UX == 32 ? 5 : 2)
+__global__ void __launch_bounds__(UX * 8, UX == 32 ? (UPRES_LATE_U ? 6 : 5) : 2)
 k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
           const MgItem* __restrict__ items, int e2_mode, StepCtl ctl)
 {
@@ -416,9 +424,13 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     if ((int)blockIdx.x >= ntx * ((n + TY - 1) / TY)) return;
     const int bx = blockIdx.x % ntx, by = blockIdx.x / ntx;
     const int x0 = 1 + bx * TX, y0 = 1 + by * TY;
-    double2* const U = reinterpret_cast<double2*>(smem_raw);
-    c2* const base = reinterpret_cast<c2*>(smem_raw + (size_t)UW * UH * sizeof(double2));
     constexpr int PS = HH * PL::WH;
+    // early u: [U][E0 E1 R0 R1 Cs]; late u: [E0 E1][R0 R1 Cs, later U]
+    double2* const U = UPRES_LATE_U
+        ? reinterpret_cast<double2*>(smem_raw + (size_t)2 * PS * sizeof(c2))
+        : reinterpret_cast<double2*>(smem_raw);
+    c2* const base = UPRES_LATE_U ? reinterpret_cast<c2*>(smem_raw)
+                                  : reinterpret_cast<c2*>(smem_raw + (size_t)UW * UH * sizeof(double2));
     c2* const E0 = base;
     c2* const E1 = base + PS;
     c2* const R0 = base + 2 * PS;
@@ -437,12 +449,16 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     const double2* __restrict__ uin = I.u[sv.it & 1];
     const int lane = threadIdx.x & 31;
     const bool e2z = (e2_mode == 2);             // e2 zero on every level, level 0 included
-    // stage u_N on the tile plus a 1-node ring, the coarse window, e2 and r_N
-    for (int q = threadIdx.x; q < UW * UH; q += NTU) {
-        const int gx = x0 - 1 + q % UW, gy = y0 - 1 + q / UW;
-        const bool in = gx <= n + 1 && gy <= n + 1;
-        cp_async_elem<16>(U + q, uin + (in ? (size_t)gy * S + gx : 0), in);
-    }
+    // stage u_N on the tile plus a 1-node ring (now, or after the sweeps), the coarse
+    // window, e2 and r_N
+    auto stage_u = [&]() {
+        for (int q = threadIdx.x; q < UW * UH; q += NTU) {
+            const int gx = x0 - 1 + q % UW, gy = y0 - 1 + q / UW;
+            const bool in = gx <= n + 1 && gy <= n + 1;
+            cp_async_elem<16>(U + q, uin + (in ? (size_t)gy * S + gx : 0), in);
+        }
+    };
+    if (!UPRES_LATE_U) stage_u();
     for (int cy = threadIdx.x >> 5; cy < CH; cy += NWU) {
         const int Y = cy0 + cy;
 #pragma unroll
@@ -497,6 +513,11 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
         half_sweep<R, W, TX, TY, NWU>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, dinv, 0);
         __syncthreads();
         half_sweep<R, W, TX, TY, NWU>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, dinv, 1);
+        __syncthreads();
+    }
+    if (UPRES_LATE_U) {                          // the rhs planes and Cs are dead: u_N there
+        stage_u();
+        cp_async_wait_all();
         __syncthreads();
     }
     // u_{N+1} = u_N + e_N on the interior nodes of the u window
