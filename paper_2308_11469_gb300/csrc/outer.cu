@@ -92,30 +92,46 @@ __device__ void finalize(const InstDesc& I, InstState* stp, double norm2, double
 // order, in FP64).  `sum2`: the second channel is summed (mode 0, ||b||^2) instead of
 // maximised (max |e|^2).  Mode 1 reduces its complex64-derived values in FP32, keeping the
 // shuffle tree off the FP64 pipe; the result (thread 0) is FP64 either way.
-template <typename T>
-__device__ __forceinline__ void block_reduce(T a, T m, double& ra, double& rm, double* sa, double* sm,
-                                             bool sum2)
+// VT > 1: each real thread stands for VT threads of a map VT times the block's size (real
+// thread j for the threads j + blockDim v); virtual warp w + (blockDim / 32) v reduces on
+// real warp w with the same shuffle tree, and the virtual warps' values are summed in
+// order, so the result is that of the larger block.
+template <typename T, int VT = 1>
+__device__ __forceinline__ void block_reduce_v(const T* av, const T* mv, double& ra, double& rm,
+                                               double* sa, double* sm, bool sum2)
 {
+    const int nw = (int)(blockDim.x >> 5);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        const T mo = __shfl_xor_sync(0xffffffffu, m, o);
-        m = sum2 ? m + mo : (m > mo ? m : mo);
-    }
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        sa[w] = (double)a;
-        sm[w] = (double)m;
+    for (int v = 0; v < VT; ++v) {
+        T a = av[v], m = mv[v];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            const T mo = __shfl_xor_sync(0xffffffffu, m, o);
+            m = sum2 ? m + mo : (m > mo ? m : mo);
+        }
+        const int w = (threadIdx.x >> 5) + nw * v;
+        if ((threadIdx.x & 31) == 0) {
+            sa[w] = (double)a;
+            sm[w] = (double)m;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         ra = 0.0;
         rm = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+        for (int i = 0; i < nw * VT; ++i) {
             ra += sa[i];
             rm = sum2 ? rm + sm[i] : fmax(rm, sm[i]);
         }
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void block_reduce(T a, T m, double& ra, double& rm, double* sa, double* sm,
+                                             bool sum2)
+{
+    block_reduce_v<T, 1>(&a, &m, ra, rm, sa, sm, sum2);
 }
 
 // End of an outer step, run by one whole CTA once every instance's status is final: is
@@ -174,21 +190,30 @@ __device__ void step_arrive(const InstState* st, const StepCtl& c)
 // leaves sums and maxima of non-negative values unchanged), so a launch with larger CTAs
 // reduces in the same order as the residual kernels.
 // sa, sm: shared scratch of one double per warp of the CTA.
+// VT: threads of the NTH-thread order per real thread (blockDim.x = NTH / VT; sa, sm hold
+// NTH / 32 doubles).
+template <int VT = 1>
 __device__ void instance_last(const InstDesc& I, InstState* stp, int mode, const InstState* st_all,
                               const StepCtl& c, double* sa, double* sm)
 {
     const int nb = I.nres_blocks;
     __threadfence();
-    double ta = 0.0, tm = 0.0;
-    if (threadIdx.x < NTH)
-        for (int b = threadIdx.x; b < nb; b += NTH) {
-            ta += __ldcg(I.part + b);
-            const double v = __ldcg(I.part + nb + b);
-            tm = (mode == 0) ? tm + v : fmax(tm, v);
-        }
+    double ta[VT], tm[VT];
+#pragma unroll
+    for (int v = 0; v < VT; ++v) {
+        ta[v] = 0.0;
+        tm[v] = 0.0;
+        const int t = threadIdx.x + (int)blockDim.x * v;
+        if (t < NTH)
+            for (int b = t; b < nb; b += NTH) {
+                ta[v] += __ldcg(I.part + b);
+                const double x = __ldcg(I.part + nb + b);
+                tm[v] = (mode == 0) ? tm[v] + x : fmax(tm[v], x);
+            }
+    }
     __syncthreads();
     double fa = 0.0, fm = 0.0;
-    block_reduce<double>(ta, tm, fa, fm, sa, sm, mode == 0);
+    block_reduce_v<double, VT>(ta, tm, fa, fm, sa, sm, mode == 0);
     if (threadIdx.x == 0) {
         finalize(I, stp, fa, fm, mode);
         *I.count = 0u;
@@ -214,7 +239,7 @@ __device__ void tile_done(const InstDesc& I, InstState* stp, int tile, T ta0, T 
     }
     __syncthreads();
     if (!last) return;
-    instance_last(I, stp, mode, st_all, c, sa, sm);
+    instance_last<1>(I, stp, mode, st_all, c, sa, sm);
 }
 
 // r = f - (Delta_h + k^2 + i p) u at one 2D node from its value c and its four neighbours
@@ -354,17 +379,18 @@ k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
 // 2D, complex64 inner solves: level 0's ascent fused with the residual launch
 // ---------------------------------------------------------------------------
 // An outer step ends with level 0's prolongation + correction + nu2 sweeps (k_up2d),
-// whose only reader is the residual launch.  k_upres2d does both on a UX x 32 tile: the
+// whose only reader is the residual launch.  k_upres2d does both on a 32 x 32 tile: the
 // sweeps run on a window one node wider than the ascent's (halo 2 nu2 + 1), so e_N is
 // final on the tile plus a 1-node ring; u_{N+1} = u_N + e_N is formed there in shared
 // memory, written once, and r_{N+1} follows from the staged values.  e_N never goes to
-// global memory.  The tile is one or two of the residual kernel's 32 x 32 tiles side by
-// side, and each (256 threads) forms its partials with the residual kernel's per-node
-// arithmetic, node-to-thread map and summation order, so iterates, residuals and the
-// relres history are those of the two-launch path bit for bit.  Level 0 keeps r_N and
+// global memory.  The tile is one of the residual kernel's 32 x 32 tiles, and its partials
+// are formed with the residual kernel's per-node arithmetic, node-to-thread map and
+// summation order, so iterates, residuals and the relres history are those of the
+// two-launch path bit for bit.  Level 0 keeps r_N and
 // r_{N+1} in separate buffers (step parity), so tiles still sweeping with r_N never see
 // another tile's r_{N+1}.
-// UX: tile width, 64 (512 threads, two residual tiles) or 32 (256 threads, one).
+// The tile is one residual tile of k_residual2d; NTU threads (128 or 256) each stand for
+// 256 / NTU threads of that kernel's map, so partials are formed in its order.
 constexpr int UPY = 32;
 
 // The coarse window: fine nodes gx0 .. gx0 + W - 1 (gx0 = x0 - H even when H is odd) read
@@ -387,24 +413,26 @@ template <int NU, int UX> constexpr size_t upres_bytes()
     return ub + 2 * planes + cs;
 }
 
-template <int NU, bool DAMP, int UX>
-__global__ void __launch_bounds__(UX * 8, UX == 32 ? (UPRES_LATE_U ? 6 : 5) : 2)
+template <int NU, bool DAMP, int NTU>
+__global__ void __launch_bounds__(NTU, NTU == 128 ? 7 : (UPRES_LATE_U ? 6 : 5))
 k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
           const MgItem* __restrict__ items, int e2_mode, StepCtl ctl)
 {
     typedef float R;
     typedef float2 c2;
+    constexpr int UX = T2;
     constexpr int TX = UX, TY = UPY;
-    constexpr int NTU = UX * 8, NWU = NTU / 32;
+    constexpr int NWU = NTU / 32;
+    constexpr int VT = NTH / NTU;                // threads of the residual kernel's map per thread
     constexpr int H = 2 * NU + 1;
     constexpr int W = TX + 2 * H, HH = TY + 2 * H;
     constexpr int CW = upres_cw<NU, UX>(), CH = upres_ch<NU>();
     constexpr int UW = TX + 2, UH = TY + 2;
     static_assert(H % 2 == 1 && TX % 2 == 0 && TY % 2 == 0, "gx0, gy0 even");
     typedef Planes<W> PL;
-    static_assert(TX % T2 == 0 && TY == T2 && NTU == (TX / T2) * NTH, "NTH threads per residual tile");
+    static_assert(TY == T2 && NTH % NTU == 0, "one residual tile, NTH / NTU map threads per thread");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double sa[NWU], sm[NWU];
+    __shared__ double sa[NTH / 32], sm[NTH / 32];
     __shared__ int last;
     // work item and descriptors are host-written: read them before the wait
     const MgItem item = items[blockIdx.y];
@@ -532,74 +560,53 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
         U[q] = v;
     }
     __syncthreads();
-    // r_{N+1}: the threads 256 hf .. 256 hf + 255 take residual tile ((TX / 32) bx + hf, by),
-    // thread t of them the nodes (t mod 32, t / 32 + 8 k) of that tile, as in k_residual2d
-    const int hf = threadIdx.x >> 8;
-    const int t = threadIdx.x & 255;
-    const int rtx = (TX / T2) * bx + hf;
+    // r_{N+1}: thread t of the residual kernel's map takes the nodes (t mod 32, t / 32 + 8 k)
+    // of the tile; real thread j stands for the map's threads j + NTU v, v < VT
     double2* __restrict__ uout = I.u[(sv.it + 1) & 1];
     c2* __restrict__ rhs = (c2*)lev_rhs(L, 0, sv.it + 1);
     const double2* __restrict__ f = I.f;
     const double mih2 = -I.ih2;
     const double mcdiag = -I.cdiag;
     const double damp = I.damp;
-    R r2 = 0, emax2 = 0;
-    const int lx = (t & 31) + 1 + 32 * hf;
+    R r2[VT], em[VT];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int ly = (t >> 5) + 8 * k + 1;
-        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        if (gx > n || gy > n) continue;
-        const int o = ly * UW + lx;
-        const double2 c = U[o];
-        const double2 a = U[o - 1], b = U[o + 1], d = U[o - UW], u = U[o + UW];
-        uout[(size_t)gy * S + gx] = c;
-        const double2 fv = f[(size_t)(gy - 1) * n + (gx - 1)];
-        const double2 r = helm_resid2d<DAMP>(c, a, b, d, u, fv, mih2, mcdiag, damp);
-        const c2 ri = Inner<R>::from(r);
-        rhs[(size_t)gy * P + gx] = ri;
-        r2 += abs2(ri);
-        const int ex = gx - gx0, ey = gy - gy0;
-        emax2 = fmax(emax2, abs2((((ex + ey + cpar) & 1) ? E1 : E0)[PL::at(ex, ey)]));
-    }
-    // per-half reduction in block_reduce's order (warps of the half, then their values)
-    R a = r2, m = emax2;
+    for (int v = 0; v < VT; ++v) {
+        const int t = threadIdx.x + NTU * v;
+        const int lx = (t & 31) + 1;
+        r2[v] = 0;
+        em[v] = 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        const R mo = __shfl_xor_sync(0xffffffffu, m, o);
-        m = m > mo ? m : mo;
-    }
-    const int w = threadIdx.x >> 5;
-    if (lane == 0) {
-        sa[w] = (double)a;
-        sm[w] = (double)m;
-    }
-    __syncthreads();
-    const int nb = I.nres_blocks;
-    const bool two = TX == 2 * T2 && 2 * bx + 1 < I.res_tx;
-    if (t == 0 && (hf == 0 || two)) {
-        double ra = 0.0, rm = 0.0;
-        for (int i = 0; i < NTH / 32; ++i) {
-            ra += sa[8 * hf + i];
-            rm = fmax(rm, sm[8 * hf + i]);
+        for (int k = 0; k < 4; ++k) {
+            const int ly = (t >> 5) + 8 * k + 1;
+            const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+            if (gx > n || gy > n) continue;
+            const int o = ly * UW + lx;
+            const double2 c = U[o];
+            const double2 a = U[o - 1], b = U[o + 1], d = U[o - UW], u = U[o + UW];
+            uout[(size_t)gy * S + gx] = c;
+            const double2 fv = f[(size_t)(gy - 1) * n + (gx - 1)];
+            const double2 r = helm_resid2d<DAMP>(c, a, b, d, u, fv, mih2, mcdiag, damp);
+            const c2 ri = Inner<R>::from(r);
+            rhs[(size_t)gy * P + gx] = ri;
+            r2[v] += abs2(ri);
+            const int ex = gx - gx0, ey = gy - gy0;
+            em[v] = fmax(em[v], abs2((((ex + ey + cpar) & 1) ? E1 : E0)[PL::at(ex, ey)]));
         }
-        const int tile = by * I.res_tx + rtx;
+    }
+    // the tile's partials in k_residual2d's order, then the instance's ticket
+    double ra = 0.0, rm = 0.0;
+    block_reduce_v<R, VT>(r2, em, ra, rm, sa, sm, false);
+    const int nb = I.nres_blocks;
+    if (threadIdx.x == 0) {
+        const int tile = by * I.res_tx + bx;
         I.part[tile] = ra;
         I.part[nb + tile] = rm;
         __threadfence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned k = two ? 2u : 1u;
-        const unsigned prev = atomicAdd(I.count, k);
-        last = (prev + k == (unsigned)nb);
+        last = (atomicAdd(I.count, 1u) == (unsigned)(nb - 1));
     }
     __syncthreads();
     if (!last) return;
-    __syncthreads();                             // sa / sm are reused
-    instance_last(I, stp, 1, st, ctl, sa, sm);
+    instance_last<VT>(I, stp, 1, st, ctl, sa, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -1036,6 +1043,10 @@ cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* s
 // tile width of the fused kernel: 32 (256-thread CTAs, four resident per SM, so CTAs in
 // their smoothing phase and CTAs in their FP64 residual phase share each SM)
 constexpr int UPX = 32;
+// threads of the fused kernel (128 or 256; same results).  128 lets 7 CTAs share an SM, so
+// a 1023^2 instance's 1024 tiles run in one wave, but measured slower (83.8 against
+// 80.1 us per outer step): the CTAs' latency-bound phases want the 8 warps.
+constexpr int UPRES_NT = 256;
 
 int upres2d_tiles(int n) { return ((n + UPX - 1) / UPX) * ((n + UPY - 1) / UPY); }
 
@@ -1046,12 +1057,12 @@ cudaError_t launch_upres2d(const InstDesc* insts, InstState* st, const MgItem* i
     if (nitems <= 0) return cudaSuccess;
     const StepCtl c{ctrl, nscan, ninst, use_cond, cond_handle};
     const dim3 g(upres2d_tiles(n), nitems);
-    const dim3 b(UPX * 8);
+    const dim3 b(UPRES_NT);
 #define HELM_UR(NU)                                                                                 \
     case NU:                                                                                        \
-        if (damp) launch_k(k_upres2d<NU, true, UPX>, g, b, upres_bytes<NU, UPX>(), s, insts, st, items, \
+        if (damp) launch_k(k_upres2d<NU, true, UPRES_NT>, g, b, upres_bytes<NU, UPX>(), s, insts, st, items, \
                            e2_mode, c);                                                             \
-        else launch_k(k_upres2d<NU, false, UPX>, g, b, upres_bytes<NU, UPX>(), s, insts, st, items,     \
+        else launch_k(k_upres2d<NU, false, UPRES_NT>, g, b, upres_bytes<NU, UPX>(), s, insts, st, items,     \
                       e2_mode, c);                                                                  \
         break;
     switch (nu2) {
@@ -1066,12 +1077,12 @@ template <int NU>
 cudaError_t setup_upres()
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_upres2d<NU, false, UPX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(k_upres2d<NU, false, UPRES_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)upres_bytes<NU, UPX>())) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_upres2d<NU, true, UPX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(k_upres2d<NU, true, UPRES_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)upres_bytes<NU, UPX>())) != cudaSuccess) return e;
-    if ((e = max_carveout(k_upres2d<NU, false, UPX>)) != cudaSuccess) return e;
-    return max_carveout(k_upres2d<NU, true, UPX>);
+    if ((e = max_carveout(k_upres2d<NU, false, UPRES_NT>)) != cudaSuccess) return e;
+    return max_carveout(k_upres2d<NU, true, UPRES_NT>);
 }
 
 cudaError_t setup_outer()
