@@ -291,6 +291,51 @@ HELM_API helm_status helm_batch_profile(helm_batch* batch, int max_steps, uint64
 /* Active (submitted, not yet polled done) solves and the workspace bytes they hold. */
 HELM_API helm_status helm_batch_info(const helm_batch* batch, int* active, size_t* bytes_in_use);
 
+/*
+ * Annular problem (Section 2.3; the FD discussion of Section 2.4): the square
+ * [-side/2, side/2]^2 with a square hole |x|, |y| <= hole, Dirichlet data g on the hole,
+ * the Robin condition du/dn - i k u = q on the outer edge, Delta u + k^2 u = f inside.
+ *
+ * Grid: n intervals per axis (n a power of two, 16 <= n <= 16384), h = side / n, node
+ * (i, j) at (-side/2 + i h, -side/2 + j h) stored at i (n + 1) + j.  Hole nodes: the closed
+ * hole (their values are the data g); outer-edge nodes (i or j in {0, n}): the row is the
+ * outward normal derivative as a one-sided difference towards the inward neighbour (the
+ * mean of the two at a corner); other nodes: the 5-point Laplacian.  Solved by the
+ * iteration of Section 2.3 (shift alpha >= k^2, default k^2) in residual form: FP64
+ * residual and solution, inner solves by multigrid cycles in the plan's precision.
+ * The hole must contain a node and stay clear of the outer edge and its first layer at
+ * every multigrid level down to n = 8; otherwise create returns HELM_EINVAL.
+ */
+typedef struct helm_annulus helm_annulus;
+HELM_API helm_status helm_annulus_create(helm_annulus** out, int n, double side, double hole, double k,
+                                         int prec);
+HELM_API helm_status helm_annulus_destroy(helm_annulus* plan);
+/* Shift alpha >= k^2 of Section 2.3's iteration (HELM_EINVAL below k^2 or not finite). */
+HELM_API helm_status helm_annulus_set_shift(helm_annulus* plan, double alpha);
+/* Multigrid cycle per outer step, as helm_plan_set_cycle (default V(2,2), 1 cycle). */
+HELM_API helm_status helm_annulus_set_cycle(helm_annulus* plan, int nu1, int nu2, int cycles);
+/*
+ * data: (n+1)^2 complex128 (device): f on the PDE nodes, q on the outer-edge nodes, g on the
+ * hole nodes.  u: (n+1)^2 complex128 (device, output only): the solution, g on the hole.
+ * The iteration starts from zero (with the hole data); res_hist (host, max_outer + 1
+ * doubles, may be NULL) receives relres_N = ||r_N|| / ||r_0||; *iters the steps made.
+ * Returns HELM_CONVERGED / HELM_MAXITER / HELM_DIVERGED / HELM_ENONFINITE (the cavity's
+ * status rule), or an error.  Synchronous, on a stream of the plan that is ordered after
+ * prior work on the legacy default stream; data and u must not overlap.
+ */
+HELM_API helm_status helm_annulus_solve(helm_annulus* plan, const void* data, void* u, double tol,
+                                        int max_outer, int* iters, double* res_hist);
+/*
+ * Mean exit time E (Delta E = -c_tau, dE/dn = 0 on the outer edge) and expected local time
+ * L (Delta L = 0, dL/dn = 1 on the outer edge), both zero on the hole (Section 2.3's
+ * remarks), into E_out and L_out ((n+1)^2 doubles, device), each solved to relres tol; and
+ * k_*^A = min over the PDE nodes of (-L + sqrt(L^2 + 4 E)) / (2 E) (host, may be NULL).
+ * c_tau = 1 is Eq. (2.10)'s normalisation, 2 Section 3's.  Allocates a k = 0 plan of the
+ * same geometry for the duration of the call.
+ */
+HELM_API helm_status helm_annulus_exit_times(helm_annulus* plan, double c_tau, double tol, int max_outer,
+                                             void* E_out, void* L_out, double* kstar);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,14 @@ _SIGS = {
     "poisson_vcycle": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int]),
     "poisson_vcycle_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_int, _vp, _vp, C.c_int,
                                          C.c_int, _vp]),
+    "helm_annulus_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_double, C.c_double, C.c_double, C.c_int]),
+    "helm_annulus_destroy": (C.c_int, [_vp]),
+    "helm_annulus_set_shift": (C.c_int, [_vp, C.c_double]),
+    "helm_annulus_set_cycle": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
+    "helm_annulus_solve": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int),
+                                     C.POINTER(C.c_double)]),
+    "helm_annulus_exit_times": (C.c_int, [_vp, C.c_double, C.c_double, C.c_int, _vp, _vp,
+                                          C.POINTER(C.c_double)]),
     "helm_batch_create": (C.c_int, [C.POINTER(_vp), C.c_size_t, _vp]),
     "helm_batch_destroy": (C.c_int, [_vp]),
     "helm_batch_submit": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_double, C.c_int,
@@ -299,6 +307,68 @@ def poisson_vcycle_noalloc(ndim: int, n: int, h: float, prec: int, rhs, e, nu1: 
     if st != HELM_EUNSUPPORTED:
         _check(st, "poisson_vcycle_noalloc")
     return st
+
+
+class _Annulus:
+    """Handle returned by helm_annulus_create (owns the C plan)."""
+
+    def __init__(self, handle, n, side, hole, k, prec):
+        self.handle = handle
+        self.n, self.side, self.hole, self.k, self.prec = n, side, hole, k, prec
+
+    def __del__(self):
+        if self.handle is not None and _lib is not None:
+            _lib.helm_annulus_destroy(self.handle)
+            self.handle = None
+
+
+def helm_annulus_create(n: int, side: float = 1.0, hole: float = 0.15, k: float = 0.0,
+                        prec: int = HELM_PREC_MIXED) -> _Annulus:
+    out = C.c_void_p()
+    _check(load().helm_annulus_create(C.byref(out), int(n), float(side), float(hole), float(k), int(prec)),
+           "helm_annulus_create")
+    return _Annulus(out, n, side, hole, k, prec)
+
+
+def helm_annulus_destroy(plan: _Annulus) -> None:
+    if plan.handle is not None:
+        _check(load().helm_annulus_destroy(plan.handle), "helm_annulus_destroy")
+        plan.handle = None
+
+
+def helm_annulus_set_shift(plan: _Annulus, alpha: float) -> None:
+    _check(load().helm_annulus_set_shift(plan.handle, float(alpha)), "helm_annulus_set_shift")
+
+
+def helm_annulus_set_cycle(plan: _Annulus, nu1: int, nu2: int, cycles: int = 1) -> None:
+    _check(load().helm_annulus_set_cycle(plan.handle, nu1, nu2, cycles), "helm_annulus_set_cycle")
+
+
+def helm_annulus_solve(plan: _Annulus, data, u, tol: float, max_outer: int):
+    """data, u: (n+1, n+1) complex128 device tensors.  Returns (status, iters, relres history)."""
+    import torch
+    n = plan.n
+    pd = _ptr(data, torch.complex128, (n + 1, n + 1), "data")
+    pu = _ptr(u, torch.complex128, (n + 1, n + 1), "u")
+    iters = C.c_int()
+    hist = np.zeros(max_outer + 1, dtype=np.float64)
+    st = _check(load().helm_annulus_solve(plan.handle, pd, pu, float(tol), int(max_outer), C.byref(iters),
+                                          hist.ctypes.data_as(C.POINTER(C.c_double))), "helm_annulus_solve")
+    return st, iters.value, hist[: iters.value + 1].copy()
+
+
+def helm_annulus_exit_times(plan: _Annulus, E, L, c_tau: float = 1.0, tol: float = 1e-10,
+                            max_outer: int = 200):
+    """E, L: (n+1, n+1) float64 device tensors (outputs).  Returns (status, k_*^A); the status
+    is HELM_CONVERGED when both solves reached tol (else E, L and k_*^A are not valid)."""
+    import torch
+    n = plan.n
+    pe = _ptr(E, torch.float64, (n + 1, n + 1), "E")
+    pl = _ptr(L, torch.float64, (n + 1, n + 1), "L")
+    ks = C.c_double(0.0)
+    st = _check(load().helm_annulus_exit_times(plan.handle, float(c_tau), float(tol), int(max_outer), pe, pl,
+                                               C.byref(ks)), "helm_annulus_exit_times")
+    return st, ks.value
 
 
 class _Batch:

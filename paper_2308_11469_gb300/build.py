@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libhelm.so")
-SOURCES = ["engine.cu", "outer.cu", "vcycle.cu", "vcycle2d.cu", "tail.cu", "noalloc.cu"]
+SOURCES = ["engine.cu", "outer.cu", "vcycle.cu", "vcycle2d.cu", "tail.cu", "noalloc.cu", "annulus.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code: no contraction of a*b+c into FMAs, so host arithmetic (descriptor constants,
 # closed forms) rounds the same on x86 and Arm hosts

@@ -1,0 +1,793 @@
+// The annular problem (Section 2.3 and the FD discussion of Section 2.4): a square with a
+// square hole, Dirichlet data on the hole, a Robin condition du/dn - i k u = q on the
+// outer edge.
+//
+// Grid: [-side/2, side/2]^2 with N intervals per axis (N a power of two), h = side / N,
+// node (i, j) at (-side/2 + i h, -side/2 + j h), stored at i (N + 1) + j.  Node types:
+// HOLE (|x|, |y| <= hole: Dirichlet, value g), EDGE (i or j in {0, N}: the row is the
+// outward normal derivative, the one-sided difference towards the inward neighbour,
+// averaged over the two normals at a corner), PDE (5-point Delta_h).
+//
+// Outer iteration (FP64, Section 2.3 in residual form, sigma = alpha - k^2 >= 0):
+//   r_N = b - B U_N,  A_sigma e_N = r_N,  U_{N+1} = U_N + e_N,
+// B: PDE rows Delta_h + k^2, EDGE rows d/dn - i k;  A_sigma: PDE rows Delta_h - sigma,
+// EDGE rows d/dn.  With exact inner solves the partial sums are those of the paper's
+// v_n + i w_n (Neumann data -k w_{n-1}, +k v_{n-1} on the outer edge).
+//
+// Inner solve: multigrid V-cycles in the inner precision on rediscretised levels N, N/2,
+// ..., 8 (node types by the same rule at each level; the coarsest solved exactly through a
+// host-computed inverse).  Red-black Gauss-Seidel solves each row by its own equation;
+// the residual is restricted by full weighting at PDE nodes and injected at EDGE nodes;
+// bilinear prolongation.  A coarse level represents the hole only to its own spacing, and
+// the coarse-grid correction is poor in the layer between the fine and the coarse hole
+// edges: after each correction a band of a few nodes around the hole is relaxed several
+// times (one CTA), which restores the cycle's contraction (about 0.3 per V(2,2) cycle).
+#include "../../include/helm.h"
+#include "launch.h"
+#include "pdl.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+namespace helm {
+namespace {
+
+constexpr int AN_NT = 256;
+constexpr int AN_NC = 8;            // coarsest level (solved exactly)
+constexpr int AN_BAND = 4;          // band half-width around the hole, in nodes of the level
+constexpr int AN_BAND_SWEEPS = 4;
+enum : unsigned char { AN_PDE = 0, AN_EDGE = 1, AN_HOLE = 2 };
+
+template <typename R> struct CX;
+template <> struct CX<float> { typedef float2 T; };
+template <> struct CX<double> { typedef double2 T; };
+
+int grid_for(long work) { return (int)std::min<long>((work + AN_NT - 1) / AN_NT, 152L * 16); }
+
+// mean of the inward neighbours of an edge node (two at a corner)
+template <typename T>
+__device__ __forceinline__ T inward_mean(const T* e, int i, int j, int n)
+{
+    const int S = n + 1;
+    T s;
+    s.x = 0;
+    s.y = 0;
+    int c = 0;
+    if (i == 0) { s.x += e[S + j].x; s.y += e[S + j].y; ++c; }
+    if (i == n) { s.x += e[(n - 1) * S + j].x; s.y += e[(n - 1) * S + j].y; ++c; }
+    if (j == 0) { s.x += e[i * S + 1].x; s.y += e[i * S + 1].y; ++c; }
+    if (j == n) { s.x += e[i * S + n - 1].x; s.y += e[i * S + n - 1].y; ++c; }
+    if (c == 2) { s.x *= 0.5f; s.y *= 0.5f; }
+    return s;
+}
+
+// sum of the non-hole neighbours of a PDE node (hole entries of an iterate are zero)
+template <typename T>
+__device__ __forceinline__ T nbr_sum(const T* e, int q, int S)
+{
+    T a = e[q - S], b = e[q + S], c = e[q - 1], d = e[q + 1];
+    T s;
+    s.x = (a.x + b.x) + (c.x + d.x);
+    s.y = (a.y + b.y) + (c.y + d.y);
+    return s;
+}
+
+// Red-black Gauss-Seidel over the box [i0, i1] x [j0, j1] for nodes of colour (i + j) & 1;
+// PDE rows e = (sum of neighbours - h^2 rhs) / (4 + sigma h^2), EDGE rows e = mean of the
+// inward neighbours + h rhs.  pde_only: the band sweeps near the hole.
+template <typename R>
+__global__ void __launch_bounds__(AN_NT)
+k_an_rbgs(typename CX<R>::T* __restrict__ e, const typename CX<R>::T* __restrict__ rhs,
+          const unsigned char* __restrict__ typ, int n, R h, R dinv, int color, int i0, int i1, int j0,
+          int j1)
+{
+    typedef typename CX<R>::T c2;
+    const int S = n + 1;
+    const int half = (j1 - j0 + 2) / 2;
+    const long total = (long)(i1 - i0 + 1) * half;
+    const R h2 = h * h;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int i = i0 + (int)(t / half);
+        const int j = j0 + (((i + j0) & 1) ^ color) + 2 * (int)(t % half);
+        if (j > j1) continue;
+        const int q = i * S + j;
+        const unsigned char ty = typ[q];
+        if (ty == AN_PDE) {
+            const c2 s = nbr_sum(e, q, S);
+            const c2 r = rhs[q];
+            c2 v;
+            v.x = (s.x - h2 * r.x) * dinv;
+            v.y = (s.y - h2 * r.y) * dinv;
+            e[q] = v;
+        } else if (ty == AN_EDGE) {
+            const c2 m = inward_mean(e, i, j, n);
+            const c2 r = rhs[q];
+            c2 v;
+            v.x = m.x + h * r.x;
+            v.y = m.y + h * r.y;
+            e[q] = v;
+        }
+    }
+}
+
+// One CTA: `sweeps` red-black sweeps over the PDE nodes of the ring [b0, b1]^2 minus the
+// hole's index box [lo, hi]^2, through L2 (loads bypass L1 so that each half-sweep sees the
+// CTA's previous writes).
+template <typename R>
+__global__ void __launch_bounds__(1024)
+k_an_band(typename CX<R>::T* e, const typename CX<R>::T* __restrict__ rhs, const unsigned char* __restrict__ typ,
+          int n, R h, R dinv, int b0, int b1, int lo, int hi, int sweeps)
+{
+    typedef typename CX<R>::T c2;
+    const int S = n + 1;
+    const int w = b1 - b0 + 1, th = lo - b0, bh = b1 - hi, hh = hi - lo + 1;
+    const int nA = th * w, nB = bh * w, nC = hh * th, nD = hh * bh;
+    const int total = nA + nB + nC + nD;
+    const R h2 = h * h;
+    for (int s = 0; s < 2 * sweeps; ++s) {
+        const int color = s & 1;
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            int i, j;
+            if (t < nA) { i = b0 + t / w; j = b0 + t % w; }
+            else if (t < nA + nB) { const int u = t - nA; i = hi + 1 + u / w; j = b0 + u % w; }
+            else if (t < nA + nB + nC) { const int u = t - nA - nB; i = lo + u / th; j = b0 + u % th; }
+            else { const int u = t - nA - nB - nC; i = lo + u / bh; j = hi + 1 + u % bh; }
+            if (((i + j) & 1) != color) continue;
+            const int q = i * S + j;
+            if (typ[q] != AN_PDE) continue;
+            const c2 a = __ldcg(e + q - S), b = __ldcg(e + q + S), c = __ldcg(e + q - 1), d = __ldcg(e + q + 1);
+            const c2 r = rhs[q];
+            c2 v;
+            v.x = (((a.x + b.x) + (c.x + d.x)) - h2 * r.x) * dinv;
+            v.y = (((a.y + b.y) + (c.y + d.y)) - h2 * r.y) * dinv;
+            __stcg(e + q, v);
+        }
+        __syncthreads();
+    }
+}
+
+// residual of the level's row at a fine node (zero on the hole)
+template <typename R>
+__device__ __forceinline__ typename CX<R>::T an_resid(const typename CX<R>::T* e, const typename CX<R>::T* rhs,
+                                                      const unsigned char* typ, int i, int j, int n, R h, R sig,
+                                                      bool zero)
+{
+    typedef typename CX<R>::T c2;
+    const int S = n + 1, q = i * S + j;
+    const unsigned char ty = typ[q];
+    c2 r = rhs[q];
+    if (ty == AN_HOLE) { r.x = 0; r.y = 0; return r; }
+    if (zero) return r;
+    const c2 c = e[q];
+    if (ty == AN_PDE) {
+        const c2 s = nbr_sum(e, q, S);
+        const R ih2 = (R)1 / (h * h);
+        r.x -= (s.x - (R)4 * c.x) * ih2 - sig * c.x;
+        r.y -= (s.y - (R)4 * c.y) * ih2 - sig * c.y;
+    } else {
+        const c2 m = inward_mean(e, i, j, n);
+        r.x -= (c.x - m.x) / h;
+        r.y -= (c.y - m.y) / h;
+    }
+    return r;
+}
+
+// coarse rhs: full weighting of the fine residual at PDE nodes, injection at EDGE nodes;
+// coarse iterate := 0
+template <typename R>
+__global__ void __launch_bounds__(AN_NT)
+k_an_restrict(const typename CX<R>::T* __restrict__ ef, const typename CX<R>::T* __restrict__ rf,
+              const unsigned char* __restrict__ tf, int nf, R hf, R sig, typename CX<R>::T* __restrict__ rc,
+              typename CX<R>::T* __restrict__ ec, const unsigned char* __restrict__ tc, int nc, int zero)
+{
+    typedef typename CX<R>::T c2;
+    const int Sc = nc + 1;
+    const long total = (long)Sc * Sc;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int I = (int)(t / Sc), J = (int)(t % Sc);
+        c2 z;
+        z.x = 0;
+        z.y = 0;
+        ec[t] = z;
+        const unsigned char ty = tc[t];
+        if (ty == AN_HOLE) {
+            rc[t] = z;
+        } else if (ty == AN_EDGE) {
+            rc[t] = an_resid<R>(ef, rf, tf, 2 * I, 2 * J, nf, hf, sig, zero != 0);
+        } else {
+            R ax = 0, ay = 0;
+#pragma unroll
+            for (int a = -1; a <= 1; ++a)
+#pragma unroll
+                for (int b = -1; b <= 1; ++b) {
+                    const R wgt = (R)((2 - (a < 0 ? -a : a)) * (2 - (b < 0 ? -b : b)));
+                    const c2 r = an_resid<R>(ef, rf, tf, 2 * I + a, 2 * J + b, nf, hf, sig, zero != 0);
+                    ax += wgt * r.x;
+                    ay += wgt * r.y;
+                }
+            c2 v;
+            v.x = ax * (R)(1.0 / 16.0);
+            v.y = ay * (R)(1.0 / 16.0);
+            rc[t] = v;
+        }
+    }
+}
+
+// fine iterate += bilinear interpolation of the coarse one (fine hole nodes untouched)
+template <typename R>
+__global__ void __launch_bounds__(AN_NT)
+k_an_prolong(const typename CX<R>::T* __restrict__ ec, int nc, typename CX<R>::T* __restrict__ ef,
+             const unsigned char* __restrict__ tf, int nf)
+{
+    typedef typename CX<R>::T c2;
+    const int Sf = nf + 1, Sc = nc + 1;
+    const long total = (long)Sf * Sf;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        if (tf[t] == AN_HOLE) continue;
+        const int i = (int)(t / Sf), j = (int)(t % Sf);
+        const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1;
+        const c2 a = ec[I0 * Sc + J0], b = ec[I1 * Sc + J0], c = ec[I0 * Sc + J1], d = ec[I1 * Sc + J1];
+        c2 v = ef[t];
+        v.x += (R)0.25 * (((a.x + b.x) + c.x) + d.x);
+        v.y += (R)0.25 * (((a.y + b.y) + c.y) + d.y);
+        ef[t] = v;
+    }
+}
+
+// coarsest level: e = Ainv rhs over its m unknowns (map: unknown -> node), one CTA
+template <typename R>
+__global__ void __launch_bounds__(AN_NT)
+k_an_coarse(const typename CX<R>::T* __restrict__ rhs, typename CX<R>::T* __restrict__ e,
+            const double* __restrict__ Ainv, const int* __restrict__ map, int m)
+{
+    typedef typename CX<R>::T c2;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        double ax = 0.0, ay = 0.0;
+        for (int c = 0; c < m; ++c) {
+            const double a = Ainv[(size_t)r * m + c];
+            const c2 v = rhs[map[c]];
+            ax += a * (double)v.x;
+            ay += a * (double)v.y;
+        }
+        c2 o;
+        o.x = (R)ax;
+        o.y = (R)ay;
+        e[map[r]] = o;
+    }
+}
+
+// U := the hole data on hole nodes, 0 elsewhere (both iterate buffers)
+__global__ void __launch_bounds__(AN_NT)
+k_an_init(double2* __restrict__ U0, double2* __restrict__ U1, const double2* __restrict__ data,
+          const unsigned char* __restrict__ typ, long total)
+{
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const double2 v = (typ[t] == AN_HOLE) ? data[t] : make_double2(0.0, 0.0);
+        U0[t] = v;
+        U1[t] = v;
+    }
+}
+
+// Outer step in FP64.  mode 0: V = Uin; mode 1: V = Uin + e (written to Uout).  r = b - B V
+// (PDE: f - (Delta_h V + k^2 V); EDGE: q - (dV/dn - i k V)) is stored, rounded to the inner
+// precision, as the next rhs; per-block sums of |r|^2 (of the stored r) and maxima of |e|^2.
+template <typename R>
+__global__ void __launch_bounds__(AN_NT)
+k_an_step(const double2* __restrict__ Uin, double2* __restrict__ Uout, const typename CX<R>::T* __restrict__ e,
+          const double2* __restrict__ data, const unsigned char* __restrict__ typ, typename CX<R>::T* __restrict__ rhs,
+          int n, double h, double k2, double k, int mode, double* __restrict__ part)
+{
+    typedef typename CX<R>::T c2;
+    const int S = n + 1;
+    const long total = (long)S * S;
+    const double ih2 = 1.0 / (h * h), ih = 1.0 / h;
+    double r2 = 0.0, em = 0.0;
+    auto V = [&](int q) -> double2 {
+        double2 v = Uin[q];
+        if (mode == 1) {
+            const c2 ev = e[q];                 // zero on hole nodes
+            v.x += (double)ev.x;
+            v.y += (double)ev.y;
+        }
+        return v;
+    };
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const unsigned char ty = typ[t];
+        if (ty == AN_HOLE) continue;
+        const int q = (int)t, i = q / S, j = q % S;
+        const double2 c = V(q);
+        if (mode == 1) {
+            Uout[q] = c;
+            const c2 ev = e[q];
+            em = fmax(em, (double)ev.x * ev.x + (double)ev.y * ev.y);
+        }
+        const double2 dv = data[q];
+        double2 r;
+        if (ty == AN_PDE) {
+            const double2 a = V(q - S), b = V(q + S), cc = V(q - 1), d = V(q + 1);
+            r.x = dv.x - (((a.x + b.x) + (cc.x + d.x) - 4.0 * c.x) * ih2 + k2 * c.x);
+            r.y = dv.y - (((a.y + b.y) + (cc.y + d.y) - 4.0 * c.y) * ih2 + k2 * c.y);
+        } else {
+            double mx = 0.0, my = 0.0;
+            int cnt = 0;
+            if (i == 0) { const double2 w = V(q + S); mx += w.x; my += w.y; ++cnt; }
+            if (i == n) { const double2 w = V(q - S); mx += w.x; my += w.y; ++cnt; }
+            if (j == 0) { const double2 w = V(q + 1); mx += w.x; my += w.y; ++cnt; }
+            if (j == n) { const double2 w = V(q - 1); mx += w.x; my += w.y; ++cnt; }
+            if (cnt == 2) { mx *= 0.5; my *= 0.5; }
+            // d/dn V - i k V = (V - mean) / h + (k V.y, -k V.x)
+            r.x = dv.x - ((c.x - mx) * ih + k * c.y);
+            r.y = dv.y - ((c.y - my) * ih - k * c.x);
+        }
+        c2 ri;
+        ri.x = (R)r.x;
+        ri.y = (R)r.y;
+        rhs[q] = ri;
+        r2 += (double)ri.x * ri.x + (double)ri.y * ri.y;
+    }
+    __shared__ double sa[AN_NT / 32], sm[AN_NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+        em = fmax(em, __shfl_xor_sync(0xffffffffu, em, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = r2;
+        sm[threadIdx.x >> 5] = em;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, m = 0.0;
+        for (int w = 0; w < AN_NT / 32; ++w) {
+            a += sa[w];
+            m = fmax(m, sm[w]);
+        }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = m;
+    }
+}
+
+// real part of U -> out (double), and min over PDE nodes of (-L + sqrt(L^2 + 4 E)) / (2 E)
+// (positive doubles order as their bit patterns)
+__global__ void __launch_bounds__(AN_NT)
+k_an_real(const double2* __restrict__ U, double* __restrict__ out, long total)
+{
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x)
+        out[t] = U[t].x;
+}
+
+__global__ void __launch_bounds__(AN_NT)
+k_an_kstar(const double* __restrict__ E, const double* __restrict__ L, const unsigned char* __restrict__ typ,
+           long total, unsigned long long* __restrict__ out)
+{
+    double best = 1e300;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        if (typ[t] != AN_PDE) continue;
+        const double e = E[t], l = L[t];
+        if (!(e > 0.0)) continue;
+        best = fmin(best, (-l + sqrt(l * l + 4.0 * e)) / (2.0 * e));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best < 1e300) atomicMin(out, (unsigned long long)__double_as_longlong(best));
+}
+
+}  // namespace
+}  // namespace helm
+
+using namespace helm;
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct helm_annulus {
+    int N = 0, prec = HELM_PREC_MIXED;
+    double side = 1.0, hole = 0.15, k = 0.0, alpha = 0.0, sigma = 0.0;
+    int nu1 = 2, nu2 = 2, cycles = 1;
+    struct Level {
+        int n;
+        double h;
+        unsigned char* typ;
+        void* e;
+        void* rhs;
+        int b0, b1, lo, hi;               // band ring [b0, b1]^2 minus the hole box [lo, hi]^2
+    };
+    std::vector<Level> lev;
+    double* Ainv = nullptr;
+    int* map = nullptr;
+    int m = 0;
+    double2* U1 = nullptr;
+    double* part = nullptr;
+    double* h_part = nullptr;
+    int nblk = 0;
+    unsigned long long* kmin = nullptr;
+    cudaStream_t stream = nullptr;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+#define AN_CK(call)                                                                             \
+    do {                                                                                        \
+        cudaError_t _e = (call);                                                                \
+        if (_e != cudaSuccess) {                                                                \
+            char _b[200];                                                                       \
+            snprintf(_b, sizeof _b, "%s: %s", #call, cudaGetErrorString(_e));                   \
+            note_error(_b);                                                                     \
+            return HELM_ECUDA;                                                                  \
+        }                                                                                       \
+    } while (0)
+
+// node types of a level (the oracle's rule: closed hole, outer edge rows elsewhere)
+std::vector<unsigned char> an_types(int n, double side, double hole)
+{
+    const double h = side / n, eps = 1e-9 * side;
+    std::vector<unsigned char> t((size_t)(n + 1) * (n + 1), AN_PDE);
+    for (int i = 0; i <= n; ++i)
+        for (int j = 0; j <= n; ++j) {
+            const double x = -0.5 * side + i * h, y = -0.5 * side + j * h;
+            unsigned char v = AN_PDE;
+            if (i == 0 || i == n || j == 0 || j == n) v = AN_EDGE;
+            if (std::fabs(x) <= hole + eps && std::fabs(y) <= hole + eps) v = AN_HOLE;
+            t[(size_t)i * (n + 1) + j] = v;
+        }
+    return t;
+}
+
+bool an_geometry_ok(const std::vector<unsigned char>& t, int n)
+{
+    bool any = false;
+    for (int i = 0; i <= n; ++i)
+        for (int j = 0; j <= n; ++j) {
+            const bool hole = t[(size_t)i * (n + 1) + j] == AN_HOLE;
+            any |= hole;
+            if (hole && (i <= 1 || i >= n - 1 || j <= 1 || j >= n - 1)) return false;
+        }
+    return any;
+}
+
+// dense inverse of the coarsest level's A_sigma on its unknowns (Gauss-Jordan, partial pivots)
+bool an_coarse_inverse(const std::vector<unsigned char>& t, int n, double h, double sigma,
+                       std::vector<double>& inv, std::vector<int>& map)
+{
+    const int S = n + 1;
+    std::vector<int> idx((size_t)S * S, -1);
+    map.clear();
+    for (int q = 0; q < S * S; ++q)
+        if (t[q] != AN_HOLE) { idx[q] = (int)map.size(); map.push_back(q); }
+    const int m = (int)map.size();
+    std::vector<double> A((size_t)m * m, 0.0);
+    for (int r = 0; r < m; ++r) {
+        const int q = map[r], i = q / S, j = q % S;
+        if (t[q] == AN_PDE) {
+            A[(size_t)r * m + r] = -4.0 / (h * h) - sigma;
+            const int nb[4] = {q - S, q + S, q - 1, q + 1};
+            for (int c : nb)
+                if (idx[c] >= 0) A[(size_t)r * m + idx[c]] += 1.0 / (h * h);
+        } else {
+            std::vector<int> in;
+            if (i == 0) in.push_back(q + S);
+            if (i == n) in.push_back(q - S);
+            if (j == 0) in.push_back(q + 1);
+            if (j == n) in.push_back(q - 1);
+            A[(size_t)r * m + r] = 1.0 / h;
+            for (int c : in) A[(size_t)r * m + idx[c]] -= 1.0 / (h * in.size());
+        }
+    }
+    inv.assign((size_t)m * m, 0.0);
+    for (int r = 0; r < m; ++r) inv[(size_t)r * m + r] = 1.0;
+    for (int c = 0; c < m; ++c) {
+        int p = c;
+        for (int r = c + 1; r < m; ++r)
+            if (std::fabs(A[(size_t)r * m + c]) > std::fabs(A[(size_t)p * m + c])) p = r;
+        if (std::fabs(A[(size_t)p * m + c]) < 1e-300) return false;
+        if (p != c)
+            for (int k = 0; k < m; ++k) {
+                std::swap(A[(size_t)p * m + k], A[(size_t)c * m + k]);
+                std::swap(inv[(size_t)p * m + k], inv[(size_t)c * m + k]);
+            }
+        const double d = A[(size_t)c * m + c];
+        for (int k = 0; k < m; ++k) {
+            A[(size_t)c * m + k] /= d;
+            inv[(size_t)c * m + k] /= d;
+        }
+        for (int r = 0; r < m; ++r) {
+            if (r == c) continue;
+            const double f = A[(size_t)r * m + c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < m; ++k) {
+                A[(size_t)r * m + k] -= f * A[(size_t)c * m + k];
+                inv[(size_t)r * m + k] -= f * inv[(size_t)c * m + k];
+            }
+        }
+    }
+    return true;
+}
+
+template <typename R>
+helm_status an_vcycle(helm_annulus* a, int l, bool zero)
+{
+    typedef typename CX<R>::T c2;
+    const auto& L = a->lev[l];
+    cudaStream_t s = a->stream;
+    if (l + 1 == (int)a->lev.size()) {
+        k_an_coarse<R><<<1, AN_NT, 0, s>>>((const c2*)L.rhs, (c2*)L.e, a->Ainv, a->map, a->m);
+        AN_CK(cudaGetLastError());
+        add_launches(1);
+        return HELM_OK;
+    }
+    const R h = (R)L.h, dinv = (R)(1.0 / (4.0 + a->sigma * L.h * L.h));
+    const int half = (L.n + 2) / 2;
+    const int g = grid_for((long)(L.n + 1) * half);
+    for (int sweep = 0; sweep < a->nu1; ++sweep)
+        for (int col = 0; col < 2; ++col) {
+            k_an_rbgs<R><<<g, AN_NT, 0, s>>>((c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, dinv, col, 0, L.n, 0, L.n);
+            add_launches(1);
+        }
+    const auto& C = a->lev[l + 1];
+    k_an_restrict<R><<<grid_for((long)(C.n + 1) * (C.n + 1)), AN_NT, 0, s>>>(
+        (const c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, (R)a->sigma, (c2*)C.rhs, (c2*)C.e, C.typ, C.n,
+        (zero && a->nu1 == 0) ? 1 : 0);
+    add_launches(1);
+    helm_status st = an_vcycle<R>(a, l + 1, true);
+    if (st != HELM_OK) return st;
+    k_an_prolong<R><<<grid_for((long)(L.n + 1) * (L.n + 1)), AN_NT, 0, s>>>((const c2*)C.e, C.n, (c2*)L.e, L.typ,
+                                                                             L.n);
+    k_an_band<R><<<1, 1024, 0, s>>>((c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, dinv, L.b0, L.b1, L.lo, L.hi,
+                                    AN_BAND_SWEEPS);
+    add_launches(2);
+    for (int sweep = 0; sweep < a->nu2; ++sweep)
+        for (int col = 0; col < 2; ++col) {
+            k_an_rbgs<R><<<g, AN_NT, 0, s>>>((c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, dinv, col, 0, L.n, 0, L.n);
+            add_launches(1);
+        }
+    AN_CK(cudaGetLastError());
+    return HELM_OK;
+}
+
+template <typename R>
+helm_status an_solve(helm_annulus* a, const double2* data, double2* u, double tol, int max_outer, int* iters,
+                     double* hist, int* final_status)
+{
+    typedef typename CX<R>::T c2;
+    cudaStream_t s = a->stream;
+    const auto& L0 = a->lev[0];
+    const long total = (long)(a->N + 1) * (a->N + 1);
+    double2* U[2] = {u, a->U1};
+    k_an_init<<<grid_for(total), AN_NT, 0, s>>>(U[0], U[1], data, L0.typ, total);
+    add_launches(1);
+    auto step = [&](int mode, int it) -> helm_status {
+        k_an_step<R><<<a->nblk, AN_NT, 0, s>>>(U[(it - 1) & 1], U[it & 1], (const c2*)L0.e, data, L0.typ,
+                                               (c2*)L0.rhs, a->N, L0.h, a->k * a->k, a->k, mode, a->part);
+        add_launches(1);
+        AN_CK(cudaGetLastError());
+        AN_CK(cudaMemcpyAsync(a->h_part, a->part, 2 * sizeof(double) * a->nblk, cudaMemcpyDeviceToHost, s));
+        AN_CK(cudaStreamSynchronize(s));
+        return HELM_OK;
+    };
+    // start: r_0 = b (mode 0 reads U[0] through the same index as U[(1 - 1) & 1])
+    helm_status st = step(0, 1);
+    if (st != HELM_OK) return st;
+    double r2 = 0.0;
+    for (int b = 0; b < a->nblk; ++b) r2 += a->h_part[2 * b];
+    const double norm0 = std::sqrt(r2);
+    int it = 0, status = HELM_MAXITER, run = 0;
+    double prev = 1.0, rmin = 1.0;
+    if (hist) hist[0] = (norm0 == 0.0) ? 0.0 : 1.0;
+    if (norm0 == 0.0 || !std::isfinite(norm0)) status = std::isfinite(norm0) ? HELM_CONVERGED : HELM_ENONFINITE;
+    else {
+        for (it = 1; it <= max_outer; ++it) {
+            for (int c = 0; c < a->cycles; ++c) {
+                if (c == 0) AN_CK(cudaMemsetAsync(L0.e, 0, total * sizeof(c2), s));
+                st = an_vcycle<R>(a, 0, c == 0);
+                if (st != HELM_OK) return st;
+            }
+            st = step(1, it);
+            if (st != HELM_OK) return st;
+            r2 = 0.0;
+            for (int b = 0; b < a->nblk; ++b) r2 += a->h_part[2 * b];
+            const double rel = std::sqrt(r2) / norm0;
+            if (hist) hist[it] = rel;
+            // the cavity's status rule
+            if (!std::isfinite(rel)) { status = HELM_ENONFINITE; break; }
+            if (rel <= tol) { status = HELM_CONVERGED; break; }
+            if (rel > 1e4) { status = HELM_DIVERGED; break; }
+            run = (rel >= prev) ? run + 1 : 0;
+            prev = rel;
+            rmin = std::min(rmin, rel);
+            if (it >= 20 && run >= 10 && rel >= 2.0 * rmin) { status = HELM_DIVERGED; break; }
+        }
+        if (it > max_outer) it = max_outer;
+    }
+    // the result lives in U[it & 1]: the caller's buffer is U[0]
+    if (it & 1) AN_CK(cudaMemcpyAsync(u, a->U1, total * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    AN_CK(cudaStreamSynchronize(s));
+    if (iters) *iters = it;
+    *final_status = status;
+    return HELM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+helm_status helm_annulus_create(helm_annulus** out, int n, double side, double hole, double k, int prec)
+{
+    if (!out) return HELM_EINVAL;
+    *out = nullptr;
+    if (n < 16 || n > 16384 || (n & (n - 1))) return HELM_EINVAL;
+    if (!(side > 0.0) || !std::isfinite(side) || !(hole > 0.0) || !(hole < 0.5 * side)) return HELM_EINVAL;
+    if (!(k >= 0.0) || !std::isfinite(k) || (prec != HELM_PREC_FP64 && prec != HELM_PREC_MIXED)) return HELM_EINVAL;
+    helm_annulus* a = new helm_annulus();
+    a->N = n;
+    a->side = side;
+    a->hole = hole;
+    a->k = k;
+    a->alpha = k * k;
+    a->sigma = 0.0;
+    a->prec = prec;
+    auto fail = [&](helm_status st) { helm_annulus_destroy(a); return st; };
+    // a blocking stream: its work is ordered after the caller's work on the legacy default
+    // stream (where the inputs were written)
+    if (cudaStreamCreate(&a->stream) != cudaSuccess) return fail(HELM_ECUDA);
+    const size_t eb = prec == HELM_PREC_FP64 ? 16 : 8;
+    for (int m = n; m >= AN_NC; m /= 2) {
+        std::vector<unsigned char> t = an_types(m, side, hole);
+        if (!an_geometry_ok(t, m)) return fail(HELM_EINVAL);
+        helm_annulus::Level L{};
+        L.n = m;
+        L.h = side / m;
+        const size_t pts = (size_t)(m + 1) * (m + 1);
+        void* p = nullptr;
+        if (cudaMalloc(&p, pts + 2 * pts * eb + 512) != cudaSuccess) return fail(HELM_ENOMEM);
+        a->allocs.push_back(p);
+        L.typ = (unsigned char*)p;
+        L.e = (char*)p + ((pts + 255) / 256) * 256;
+        L.rhs = (char*)L.e + ((pts * eb + 255) / 256) * 256;
+        if (cudaMemcpy(L.typ, t.data(), pts, cudaMemcpyHostToDevice) != cudaSuccess) return fail(HELM_ECUDA);
+        if (cudaMemset(L.e, 0, pts * eb) != cudaSuccess || cudaMemset(L.rhs, 0, pts * eb) != cudaSuccess)
+            return fail(HELM_ECUDA);
+        // band: the hole's index box [lo, hi]^2 (centred square) widened by AN_BAND nodes
+        int lo = m, hi = 0;
+        for (int i = 0; i <= m; ++i)
+            if (t[(size_t)i * (m + 1) + m / 2] == AN_HOLE) { lo = std::min(lo, i); hi = std::max(hi, i); }
+        L.lo = lo;
+        L.hi = hi;
+        L.b0 = std::max(1, lo - AN_BAND);
+        L.b1 = std::min(m - 1, hi + AN_BAND);
+        a->lev.push_back(L);
+    }
+    if (a->lev.size() < 2) return fail(HELM_EINVAL);
+    const long total = (long)(n + 1) * (n + 1);
+    a->nblk = grid_for(total);
+    void* p = nullptr;
+    if (cudaMalloc(&p, total * sizeof(double2) + 2 * sizeof(double) * a->nblk + 256) != cudaSuccess)
+        return fail(HELM_ENOMEM);
+    a->allocs.push_back(p);
+    a->U1 = (double2*)p;
+    a->part = (double*)((char*)p + total * sizeof(double2));
+    a->kmin = (unsigned long long*)((char*)a->part + 2 * sizeof(double) * a->nblk);
+    if (cudaMallocHost(&a->h_part, 2 * sizeof(double) * a->nblk) != cudaSuccess) return fail(HELM_ENOMEM);
+    helm_status st = helm_annulus_set_shift(a, a->alpha);
+    if (st != HELM_OK) return fail(st);
+    *out = a;
+    return HELM_OK;
+}
+
+helm_status helm_annulus_destroy(helm_annulus* a)
+{
+    if (!a) return HELM_EINVAL;
+    if (a->stream) cudaStreamSynchronize(a->stream);
+    for (void* p : a->allocs) cudaFree(p);
+    if (a->Ainv) cudaFree(a->Ainv);
+    if (a->h_part) cudaFreeHost(a->h_part);
+    if (a->stream) cudaStreamDestroy(a->stream);
+    delete a;
+    return HELM_OK;
+}
+
+helm_status helm_annulus_set_shift(helm_annulus* a, double alpha)
+{
+    if (!a || !std::isfinite(alpha) || alpha < a->k * a->k) return HELM_EINVAL;
+    a->alpha = alpha;
+    a->sigma = (alpha == a->k * a->k) ? 0.0 : alpha - a->k * a->k;
+    const auto& C = a->lev.back();
+    std::vector<unsigned char> t = an_types(C.n, a->side, a->hole);
+    std::vector<double> inv;
+    std::vector<int> map;
+    if (!an_coarse_inverse(t, C.n, C.h, a->sigma, inv, map)) return HELM_EINVAL;
+    if (a->Ainv) cudaFree(a->Ainv);
+    a->Ainv = nullptr;
+    a->m = (int)map.size();
+    void* p = nullptr;
+    if (cudaMalloc(&p, inv.size() * sizeof(double) + map.size() * sizeof(int)) != cudaSuccess) return HELM_ENOMEM;
+    a->Ainv = (double*)p;
+    a->map = (int*)(a->Ainv + inv.size());
+    AN_CK(cudaMemcpy(a->Ainv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    AN_CK(cudaMemcpy(a->map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return HELM_OK;
+}
+
+helm_status helm_annulus_set_cycle(helm_annulus* a, int nu1, int nu2, int cycles)
+{
+    if (!a || nu1 < 0 || nu1 > 8 || nu2 < 0 || nu2 > 8 || nu1 + nu2 < 1 || cycles < 1 || cycles > 16)
+        return HELM_EINVAL;
+    a->nu1 = nu1;
+    a->nu2 = nu2;
+    a->cycles = cycles;
+    return HELM_OK;
+}
+
+helm_status helm_annulus_solve(helm_annulus* a, const void* data, void* u, double tol, int max_outer, int* iters,
+                               double* res_hist)
+{
+    if (!a || !(tol >= 0.0) || max_outer < 0) return HELM_EINVAL;
+    if (!device_pointer_ok(data) || !device_pointer_ok(u) || data == u) return HELM_EINVAL;
+    int status = HELM_MAXITER;
+    const helm_status st = (a->prec == HELM_PREC_FP64)
+        ? an_solve<double>(a, (const double2*)data, (double2*)u, tol, max_outer, iters, res_hist, &status)
+        : an_solve<float>(a, (const double2*)data, (double2*)u, tol, max_outer, iters, res_hist, &status);
+    return st != HELM_OK ? st : (helm_status)status;
+}
+
+helm_status helm_annulus_exit_times(helm_annulus* a, double c_tau, double tol, int max_outer, void* E_out,
+                                    void* L_out, double* kstar)
+{
+    if (!a || !(c_tau > 0.0) || !std::isfinite(c_tau) || !(tol >= 0.0) || max_outer < 1) return HELM_EINVAL;
+    if (!device_pointer_ok(E_out) || !device_pointer_ok(L_out) || E_out == L_out) return HELM_EINVAL;
+    // Delta E = -c_tau, dE/dn = 0 and Delta L = 0, dL/dn = 1 (zero on the hole): the outer
+    // iteration with k = 0 and no shift, i.e. FP64-refined multigrid solves of A_0
+    helm_annulus* z = nullptr;
+    helm_status st = helm_annulus_create(&z, a->N, a->side, a->hole, 0.0, a->prec);
+    if (st != HELM_OK) return st;
+    helm_annulus_set_cycle(z, a->nu1, a->nu2, a->cycles);
+    const long total = (long)(a->N + 1) * (a->N + 1);
+    std::vector<unsigned char> t = an_types(a->N, a->side, a->hole);
+    std::vector<double2> hd(total);
+    void* buf = nullptr;
+    if (cudaMalloc(&buf, 2 * total * sizeof(double2)) != cudaSuccess) {
+        helm_annulus_destroy(z);
+        return HELM_ENOMEM;
+    }
+    double2* dd = (double2*)buf;
+    double2* U = dd + total;
+    auto done = [&](helm_status s) {
+        cudaFree(buf);
+        helm_annulus_destroy(z);
+        return s;
+    };
+    for (int which = 0; which < 2; ++which) {
+        for (long q = 0; q < total; ++q)
+            hd[q] = make_double2(t[q] == AN_PDE ? (which == 0 ? -c_tau : 0.0) : (t[q] == AN_EDGE && which == 1 ? 1.0 : 0.0),
+                                 0.0);
+        if (cudaMemcpy(dd, hd.data(), total * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
+            return done(HELM_ECUDA);
+        int it = 0;
+        st = helm_annulus_solve(z, dd, U, tol, max_outer, &it, nullptr);
+        if (st != HELM_CONVERGED) return done(st < 0 ? st : HELM_MAXITER);
+        k_an_real<<<grid_for(total), AN_NT, 0, z->stream>>>(U, (double*)(which == 0 ? E_out : L_out), total);
+        add_launches(1);
+    }
+    if (kstar) {
+        const unsigned long long init = 0x7ff0000000000000ull;      // +inf
+        if (cudaMemcpyAsync(z->kmin, &init, sizeof init, cudaMemcpyHostToDevice, z->stream) != cudaSuccess)
+            return done(HELM_ECUDA);
+        k_an_kstar<<<grid_for(total), AN_NT, 0, z->stream>>>((const double*)E_out, (const double*)L_out,
+                                                             z->lev[0].typ, total, z->kmin);
+        add_launches(1);
+        unsigned long long bits = 0;
+        if (cudaMemcpyAsync(&bits, z->kmin, sizeof bits, cudaMemcpyDeviceToHost, z->stream) != cudaSuccess ||
+            cudaStreamSynchronize(z->stream) != cudaSuccess)
+            return done(HELM_ECUDA);
+        double v;
+        memcpy(&v, &bits, sizeof v);
+        *kstar = v;
+    }
+    if (cudaStreamSynchronize(z->stream) != cudaSuccess) return done(HELM_ECUDA);
+    return done(HELM_OK);
+}
+
+}  // extern "C"

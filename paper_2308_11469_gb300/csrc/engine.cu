@@ -829,6 +829,13 @@ struct helm_batch {
     uint64_t next = 1;
 };
 
+namespace helm {
+// shared with the other translation units of the library (annulus.cu)
+void note_error(const char* msg) { snprintf(g_errbuf, sizeof g_errbuf, "%s", msg); }
+void add_launches(uint64_t n) { g_launches += n; }
+bool device_pointer_ok(const void* p) { return check_ptr(p) == HELM_OK; }
+}  // namespace helm
+
 extern "C" {
 
 const char* helm_status_str(int s)

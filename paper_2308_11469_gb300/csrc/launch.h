@@ -125,4 +125,10 @@ cudaError_t launch_pack(int D, int prec, const InstDesc* insts, int inst, int n,
 cudaError_t launch_unpack(int D, int prec, const InstDesc* insts, int inst, int n,
                           void* dst, cudaStream_t s);
 
+// error text of the last failing call (helm_last_error), launch counter (helm_launch_count),
+// device-pointer check of the C ABI (non-null, 16-byte aligned, device or managed memory)
+void note_error(const char* msg);
+void add_launches(uint64_t n);
+bool device_pointer_ok(const void* p);
+
 }  // namespace helm

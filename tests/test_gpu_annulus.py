@@ -1,0 +1,136 @@
+"""GPU parity of the annular problem (square with a square hole, Dirichlet hole, Robin outer
+edge; Section 2.3, Section 2.4) against the oracle, through the C ABI.
+
+* converged solutions against the oracle's direct FD solution (FP64 1e-10 relative L2 at
+  tol 1e-12; mixed 1e-6 at relres 1e-8), with and without a shift alpha > k^2;
+* FP64 iterates and relres history against the oracle's exact-solve iteration (enough
+  multigrid cycles per step);
+* the status on both sides of rho(G) = 1 (dense eigenvalues of the oracle's G);
+* exit time, local time and k_*^A against the oracle;
+* argument checks.
+"""
+import numpy as np
+import pytest
+
+from oracle import annulus as an
+from oracle import iteration as it
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_11469_gb300 import binding, build
+    build.build()
+    binding.load()
+    return binding
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _solve(B, N, k, data, prec, tol, max_outer, alpha=None, cycle=None, hole=0.15):
+    plan = B.helm_annulus_create(N, 1.0, hole, k, prec)
+    if alpha is not None:
+        B.helm_annulus_set_shift(plan, alpha)
+    if cycle:
+        B.helm_annulus_set_cycle(plan, *cycle)
+    d = torch.from_numpy(np.ascontiguousarray(data)).to(DEV)
+    u = torch.empty_like(d)
+    st, iters, hist = B.helm_annulus_solve(plan, d, u, tol, max_outer)
+    B.helm_annulus_destroy(plan)
+    return st, iters, hist, u.cpu().numpy()
+
+
+@pytest.mark.parametrize("N", [32, 64, 256])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_converged_solution_matches_the_direct_solve(B, N, prec):
+    k = 0.8
+    g = an.geometry(N)
+    data = an.scattering_data(g, k)
+    exact = an.solve_direct(g, k, data)
+    tol = 1e-12 if prec == 0 else 1e-8
+    st, iters, hist, u = _solve(B, N, k, data, prec, tol, 2000)
+    assert st == B.HELM_CONVERGED, (st, iters)
+    # the error left at a given relres is up to cond(B) times it, and cond(B) of the Robin
+    # problem grows like N^2: the bounds scale from N = 128
+    grow = max(1.0, (N / 128) ** 2)
+    assert _rel(u, exact) <= (1e-10 if prec == 0 else 1e-6) * grow
+    assert hist[0] == 1.0 and hist[-1] <= tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_shifted_iteration_and_general_data(B, prec):
+    N, k = 64, 1.1
+    g = an.geometry(N)
+    rng = np.random.default_rng(7)
+    data = rng.standard_normal((N + 1, N + 1)) + 1j * rng.standard_normal((N + 1, N + 1))
+    exact = an.solve_direct(g, k, data)
+    tol = 1e-12 if prec == 0 else 1e-8
+    st, iters, hist, u = _solve(B, N, k, data, prec, tol, 3000, alpha=k * k + 2.0)
+    assert st == B.HELM_CONVERGED
+    assert _rel(u, exact) <= (1e-10 if prec == 0 else 1e-6)
+
+
+def test_iterates_match_the_papers_iteration(B):
+    N, k = 32, 0.9
+    g = an.geometry(N)
+    data = an.scattering_data(g, k)
+    ora = an.annulus_iteration(g, k, data, tol=0.0, max_outer=5, keep_iterates=True)
+    # 16 V(2,2) cycles per step, each contracting the increment's error by <= 0.3 here,
+    # leave <= 0.3^16 ~ 4e-9 of each increment: the iterates agree to 1e-8
+    for steps in range(1, 6):
+        st, iters, hist, u = _solve(B, N, k, data, 0, 0.0, steps, cycle=(2, 2, 16))
+        assert st == B.HELM_MAXITER and iters == steps
+        assert _rel(u, ora.iterates[steps]) <= 1e-8
+    assert np.allclose(hist, ora.relres, rtol=1e-8, atol=1e-14)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_status_follows_the_spectral_radius(B, prec):
+    N = 16
+    g = an.geometry(N)
+    for k in (0.9, 1.6):
+        rho = an.spectral_radius(g, k)
+        st, iters, hist, u = _solve(B, N, k, an.scattering_data(g, k), prec, 1e-8, 3000)
+        assert st == (B.HELM_CONVERGED if rho < 1 else B.HELM_DIVERGED), (k, rho, st, iters)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("c_tau", [1.0, 2.0])
+def test_exit_time_local_time_and_k_star(B, prec, c_tau):
+    N = 64
+    g = an.geometry(N)
+    E_o, L_o = an.exit_times(g, c_tau)
+    plan = B.helm_annulus_create(N, 1.0, 0.15, 1.0, prec)
+    E = torch.empty((N + 1, N + 1), dtype=torch.float64, device=DEV)
+    L = torch.empty_like(E)
+    # relres 1e-11 (FP64): the edge-only data of L put the rounding floor of the residual
+    # near 1e-12 at N = 64
+    tol = 1e-11 if prec == 0 else 1e-9
+    st, ks = B.helm_annulus_exit_times(plan, E, L, c_tau=c_tau, tol=tol)
+    B.helm_annulus_destroy(plan)
+    assert st == B.HELM_CONVERGED
+    bound = 1e-9 if prec == 0 else 1e-6
+    assert _rel(E.cpu().numpy(), E_o) <= bound and _rel(L.cpu().numpy(), L_o) <= bound
+    assert ks == pytest.approx(an.k_star_A(g, c_tau), rel=(1e-9 if prec == 0 else 1e-6))
+
+
+def test_argument_checks(B):
+    for args in ((12, 1.0, 0.15, 1.0, 1), (64, 1.0, 0.45, 1.0, 1), (64, 1.0, 0.15, -1.0, 1),
+                 (64, 1.0, 0.15, 1.0, 7), (64, -1.0, 0.15, 1.0, 1)):
+        with pytest.raises(B.HelmError):
+            B.helm_annulus_create(*args)
+    plan = B.helm_annulus_create(64, 1.0, 0.15, 2.0, 1)
+    with pytest.raises(B.HelmError):
+        B.helm_annulus_set_shift(plan, 3.9)
+    B.helm_annulus_set_shift(plan, 4.0)
+    with pytest.raises(B.HelmError):
+        B.helm_annulus_set_cycle(plan, 0, 0, 1)
+    B.helm_annulus_destroy(plan)
