@@ -25,6 +25,7 @@
 #include "../../include/helm.h"
 #include "launch.h"
 #include "pdl.cuh"
+#include "fp_bits.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -271,82 +272,91 @@ k_an_init(double2* __restrict__ U0, double2* __restrict__ U1, const double2* __r
     }
 }
 
-// Outer step in FP64.  mode 0: V = Uin; mode 1: V = Uin + e (written to Uout).  r = b - B V
-// (PDE: f - (Delta_h V + k^2 V); EDGE: q - (dV/dn - i k V)) is stored, rounded to the inner
-// precision, as the next rhs; per-block sums of |r|^2 (of the stored r) and maxima of |e|^2.
+// FP64 <-> inner precision; complex64's format changes run on the integer pipes
+__device__ __forceinline__ double an_widen(float x) { return f2d_bits(x); }
+__device__ __forceinline__ double an_widen(double x) { return x; }
+__device__ __forceinline__ float an_narrow(double x, float) { return d2f_bits(x); }
+__device__ __forceinline__ double an_narrow(double x, double) { return x; }
+
+// U_out = U_in + e on the non-hole nodes (hole nodes keep the data in both buffers);
+// per-block maxima of |e|^2 into part[2 b + 1]
 template <typename R>
 __global__ void __launch_bounds__(AN_NT)
-k_an_step(const double2* __restrict__ Uin, double2* __restrict__ Uout, const typename CX<R>::T* __restrict__ e,
-          const double2* __restrict__ data, const unsigned char* __restrict__ typ, typename CX<R>::T* __restrict__ rhs,
-          int n, double h, double k2, double k, int mode, double* __restrict__ part)
+k_an_update(const double2* __restrict__ Uin, double2* __restrict__ Uout, const typename CX<R>::T* __restrict__ e,
+            const unsigned char* __restrict__ typ, long total, double* __restrict__ part)
+{
+    typedef typename CX<R>::T c2;
+    R em = 0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        if (typ[t] == AN_HOLE) continue;
+        const c2 ev = e[t];
+        double2 v = Uin[t];
+        v.x += an_widen(ev.x);
+        v.y += an_widen(ev.y);
+        Uout[t] = v;
+        const R a = ev.x * ev.x + ev.y * ev.y;
+        em = em > a ? em : a;
+    }
+    __shared__ double sm[AN_NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const R x = __shfl_xor_sync(0xffffffffu, em, o);
+        em = em > x ? em : x;
+    }
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = (double)em;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < AN_NT / 32; ++w) m = fmax(m, sm[w]);
+        part[2 * blockIdx.x + 1] = m;
+    }
+}
+
+// r = b - B U in FP64 (PDE: f - (Delta_h U + k^2 U); EDGE: q - (dU/dn - i k U)), stored,
+// rounded to the inner precision, as the next rhs; per-block sums of |r|^2 (of the stored
+// r) into part[2 b]
+template <typename R>
+__global__ void __launch_bounds__(AN_NT)
+k_an_resid(const double2* __restrict__ U, const double2* __restrict__ data, const unsigned char* __restrict__ typ,
+           typename CX<R>::T* __restrict__ rhs, int n, double h, double k2, double k, double* __restrict__ part)
 {
     typedef typename CX<R>::T c2;
     const int S = n + 1;
     const long total = (long)S * S;
     const double ih2 = 1.0 / (h * h), ih = 1.0 / h;
-    double r2 = 0.0, em = 0.0;
-    auto V = [&](int q) -> double2 {
-        double2 v = Uin[q];
-        if (mode == 1) {
-            const c2 ev = e[q];                 // zero on hole nodes
-            v.x += (double)ev.x;
-            v.y += (double)ev.y;
-        }
-        return v;
-    };
+    R r2 = 0;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
         const unsigned char ty = typ[t];
         if (ty == AN_HOLE) continue;
         const int q = (int)t, i = q / S, j = q % S;
-        const double2 c = V(q);
-        if (mode == 1) {
-            Uout[q] = c;
-            const c2 ev = e[q];
-            em = fmax(em, (double)ev.x * ev.x + (double)ev.y * ev.y);
-        }
+        const double2 c = U[q];
         const double2 dv = data[q];
         double2 r;
         if (ty == AN_PDE) {
-            const double2 a = V(q - S), b = V(q + S), cc = V(q - 1), d = V(q + 1);
+            const double2 a = U[q - S], b = U[q + S], cc = U[q - 1], d = U[q + 1];
             r.x = dv.x - (((a.x + b.x) + (cc.x + d.x) - 4.0 * c.x) * ih2 + k2 * c.x);
             r.y = dv.y - (((a.y + b.y) + (cc.y + d.y) - 4.0 * c.y) * ih2 + k2 * c.y);
         } else {
-            double mx = 0.0, my = 0.0;
-            int cnt = 0;
-            if (i == 0) { const double2 w = V(q + S); mx += w.x; my += w.y; ++cnt; }
-            if (i == n) { const double2 w = V(q - S); mx += w.x; my += w.y; ++cnt; }
-            if (j == 0) { const double2 w = V(q + 1); mx += w.x; my += w.y; ++cnt; }
-            if (j == n) { const double2 w = V(q - 1); mx += w.x; my += w.y; ++cnt; }
-            if (cnt == 2) { mx *= 0.5; my *= 0.5; }
-            // d/dn V - i k V = (V - mean) / h + (k V.y, -k V.x)
-            r.x = dv.x - ((c.x - mx) * ih + k * c.y);
-            r.y = dv.y - ((c.y - my) * ih - k * c.x);
+            const double2 m = inward_mean(U, i, j, n);
+            // dU/dn - i k U = (U - mean) / h + (k U.y, -k U.x)
+            r.x = dv.x - ((c.x - m.x) * ih + k * c.y);
+            r.y = dv.y - ((c.y - m.y) * ih - k * c.x);
         }
         c2 ri;
-        ri.x = (R)r.x;
-        ri.y = (R)r.y;
+        ri.x = an_narrow(r.x, R());
+        ri.y = an_narrow(r.y, R());
         rhs[q] = ri;
-        r2 += (double)ri.x * ri.x + (double)ri.y * ri.y;
+        r2 += ri.x * ri.x + ri.y * ri.y;
     }
-    __shared__ double sa[AN_NT / 32], sm[AN_NT / 32];
+    __shared__ double sa[AN_NT / 32];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-        em = fmax(em, __shfl_xor_sync(0xffffffffu, em, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        sa[threadIdx.x >> 5] = r2;
-        sm[threadIdx.x >> 5] = em;
-    }
+    for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    if ((threadIdx.x & 31) == 0) sa[threadIdx.x >> 5] = (double)r2;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, m = 0.0;
-        for (int w = 0; w < AN_NT / 32; ++w) {
-            a += sa[w];
-            m = fmax(m, sm[w]);
-        }
+        double a = 0.0;
+        for (int w = 0; w < AN_NT / 32; ++w) a += sa[w];
         part[2 * blockIdx.x] = a;
-        part[2 * blockIdx.x + 1] = m;
     }
 }
 
@@ -560,15 +570,20 @@ helm_status an_solve(helm_annulus* a, const double2* data, double2* u, double to
     k_an_init<<<grid_for(total), AN_NT, 0, s>>>(U[0], U[1], data, L0.typ, total);
     add_launches(1);
     auto step = [&](int mode, int it) -> helm_status {
-        k_an_step<R><<<a->nblk, AN_NT, 0, s>>>(U[(it - 1) & 1], U[it & 1], (const c2*)L0.e, data, L0.typ,
-                                               (c2*)L0.rhs, a->N, L0.h, a->k * a->k, a->k, mode, a->part);
+        if (mode == 1) {
+            k_an_update<R><<<a->nblk, AN_NT, 0, s>>>(U[(it - 1) & 1], U[it & 1], (const c2*)L0.e, L0.typ, total,
+                                                     a->part);
+            add_launches(1);
+        }
+        k_an_resid<R><<<a->nblk, AN_NT, 0, s>>>(U[mode == 1 ? (it & 1) : 0], data, L0.typ, (c2*)L0.rhs, a->N,
+                                                L0.h, a->k * a->k, a->k, a->part);
         add_launches(1);
         AN_CK(cudaGetLastError());
         AN_CK(cudaMemcpyAsync(a->h_part, a->part, 2 * sizeof(double) * a->nblk, cudaMemcpyDeviceToHost, s));
         AN_CK(cudaStreamSynchronize(s));
         return HELM_OK;
     };
-    // start: r_0 = b (mode 0 reads U[0] through the same index as U[(1 - 1) & 1])
+    // start: r_0 = b from U[0] (the hole data, zero elsewhere)
     helm_status st = step(0, 1);
     if (st != HELM_OK) return st;
     double r2 = 0.0;

@@ -242,3 +242,17 @@ def materialise(p: Problem) -> Problem:
         f = np.zeros((p.n,) * p.D, dtype=np.complex128)
         g = plane_wave(p.D, p.n, p.h, p.k, p.meta["direction"])
     return Problem(p.D, p.n, p.h, p.k, f, g, p.meta)
+
+
+def annulus_scattering(N: int, k: float, side: float = 1.0, hole: float = 0.15) -> np.ndarray:
+    """Data array of the annular problem's scattering case (Section 2.3): g = -exp(-i k x_1) on
+    the nodes of the closed hole |x|, |y| <= hole of the (N+1)^2 grid on [-side/2, side/2]^2
+    (node (i, j) at (-side/2 + i h, -side/2 + j h), h = side / N); f = 0 and q = 0 elsewhere."""
+    h = side / N
+    x = -0.5 * side + h * np.arange(N + 1)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    eps = 1e-9 * side
+    hole_nodes = (np.abs(X) <= hole + eps) & (np.abs(Y) <= hole + eps)
+    data = np.zeros((N + 1, N + 1), dtype=np.complex128)
+    data[hole_nodes] = -np.exp(-1j * k * X[hole_nodes])
+    return data

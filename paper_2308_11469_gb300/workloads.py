@@ -1,6 +1,6 @@
 """Timings of the method's other workloads on one GPU (one JSON line each).
 
-    python -m paper_2308_11469_gb300.workloads [--only cavity63,cube255,batch512,damped1023,exit1023,spectral1023]
+    python -m paper_2308_11469_gb300.workloads [--only cavity63,cube255,batch512,damped1023,exit1023,spectral1023,annulus1024]
     python -m paper_2308_11469_gb300.workloads --replay cube255|cavity1023 [--steps 4] [--fp64]
 
 * cavity63  63x63 unit-square cavity, plane-wave wall data (theta = pi/6), f = 0:
@@ -15,6 +15,8 @@
             cavity iteration, alpha = k^2 and the rho-minimising alpha), mixed.
 * exit1023  mean exit time and k_*^C of the 1023^2 square and the 255^3 cube.
 * spectral1023  rho(G) against k by GPU power iteration on the 1023^2 cavity.
+* annulus1024  the annular problem (square with a square hole, Robin outer edge) on a
+            1024-interval grid, k = 0.8: mixed and FP64 solves; exit / local time, k_*^A.
 
 Device time comes from CUDA events on the current stream around each call.  The inputs
 are the seeded generators of ``inputs``; result accuracy against exact discrete
@@ -238,8 +240,44 @@ def spectral1023(dev):
     return rows
 
 
+def annulus1024(dev):
+    """The annular problem (square [-1/2, 1/2]^2 with the hole [-0.15, 0.15]^2, Section 2.3's
+    scattering data) on a 1024-interval grid at k = 0.8: single solves to relres 1e-8, mixed
+    and FP64; exit time, local time and k_*^A (both normalisations of E)."""
+    import torch
+    N, k = 1024, 0.8
+    d = torch.from_numpy(inputs.annulus_scattering(N, k)).to(dev)
+    u = torch.empty_like(d)
+    rows = []
+    for prec, name in ((B.HELM_PREC_MIXED, "mixed"), (B.HELM_PREC_FP64, "fp64")):
+        plan = B.helm_annulus_create(N, 1.0, 0.15, k, prec)
+        B.helm_annulus_solve(plan, d, u, 1e-8, 2000)
+        ms, (st, it, hist) = _dev_ms(lambda: B.helm_annulus_solve(plan, d, u, 1e-8, 2000), 3)
+        # algorithmic bytes per fine node and outer step: FP64 step (U in/out 32, data 16, e and
+        # rhs one inner element each) + V(2,2) on level 0 (4 half-sweep pairs reading e, rhs and
+        # writing e: 3 elements each; restriction 2 elements; prolongation 2) x 4/3 for the levels
+        eb = 8 if prec == B.HELM_PREC_MIXED else 16
+        per_node = 48 + 2 * eb + (4 * 3 * eb + 2 * eb + 2 * eb) * 4 / 3
+        bytes_step = per_node * (N + 1) ** 2
+        rows.append({"workload": "annulus1024", "N": N, "k": k, "form": name, "status": B.helm_status_str(st),
+                     "iters": it, "ms_per_solve": ms, "solves_per_s": 1e3 / ms, "us_per_step": 1e3 * ms / max(it, 1),
+                     "model_bytes_per_step": bytes_step,
+                     "model_GBs": bytes_step / (ms / max(it, 1) / 1e3) / 1e9})
+        B.helm_annulus_destroy(plan)
+    E = torch.empty((N + 1, N + 1), dtype=torch.float64, device=dev)
+    L = torch.empty_like(E)
+    plan = B.helm_annulus_create(N, 1.0, 0.15, k, B.HELM_PREC_MIXED)
+    for c_tau in (1.0, 2.0):
+        ms, (st, ks) = _dev_ms(lambda: B.helm_annulus_exit_times(plan, E, L, c_tau=c_tau, tol=1e-8), 1)
+        rows.append({"workload": "annulus1024_exit", "N": N, "c_tau": c_tau, "status": B.helm_status_str(st),
+                     "k_star_A": ks, "max_E": float(E.max()), "max_L": float(L.max()), "ms": ms})
+    B.helm_annulus_destroy(plan)
+    return rows
+
+
 WORKLOADS = {"cavity63": cavity63, "cube255": cube255, "batch512": batch512,
-             "damped1023": damped1023, "exit1023": exit1023, "spectral1023": spectral1023}
+             "damped1023": damped1023, "exit1023": exit1023, "spectral1023": spectral1023,
+             "annulus1024": annulus1024}
 
 
 def main(argv=None) -> int:

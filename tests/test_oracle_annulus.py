@@ -169,3 +169,10 @@ def test_k_star_A_against_the_paper():
     assert abs(ks2[-1] - 0.81) < 0.06
     ks1 = an.k_star_A(an.geometry(80), c_tau=1.0)
     assert 0.9 < ks1 < 0.97
+
+
+def test_input_generator_matches_the_oracles_data():
+    # the product's seeded inputs and the oracle build the scattering data independently
+    from paper_2308_11469_gb300 import inputs
+    for N, k in ((10, 0.7), (64, 1.3)):
+        assert np.array_equal(inputs.annulus_scattering(N, k), an.scattering_data(an.geometry(N), k))
