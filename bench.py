@@ -50,8 +50,8 @@ FP64_PEAK_TFLOPS = 1.25          # GB300 nominal FP64 rate (FMA = 2 flops)
 # over 4 x 1023^2 points), scaled below to the points of an average launch
 RESIDUAL_DRAM_BYTES_PER_POINT = (168.065024e6 + 67.244032e6) / (4 * 1023 ** 2)
 # the same for the finest level's ascent fused with the residual: one ncu capture of a
-# 4-instance 1023^2 launch (176.66 + 67.18 MB)
-UPRES_DRAM_BYTES_PER_POINT = (176.6592e6 + 67.184128e6) / (4 * 1023 ** 2)
+# launch of the bench's replay (one instance per lane: 44.17 MB read + 0.71 MB written)
+UPRES_DRAM_BYTES_PER_POINT = (44.168192e6 + 0.713728e6) / (1023 ** 2)
 
 
 def _peaks():
