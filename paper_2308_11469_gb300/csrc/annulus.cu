@@ -260,6 +260,220 @@ k_an_coarse(const typename CX<R>::T* __restrict__ rhs, typename CX<R>::T* __rest
     }
 }
 
+// ---------------------------------------------------------------------------
+// Coarse tail: the coarsest levels in one CTA, in shared memory
+// ---------------------------------------------------------------------------
+// The same V-cycle as the per-level kernels (sweeps, restriction, prolongation, band
+// sweeps, exact coarsest level), with block-wide barriers between its phases instead of
+// kernel boundaries.  Levels 64, 32, 16, 8 hold about 5.7 K nodes.  In FP64 one SM's
+// arithmetic rate (a small fraction of its FP32 rate) makes the level-64 restriction slower
+// in one CTA than spread over several, so the FP64 tail starts lower.
+constexpr int AN_TAIL_TOP_F = 64;
+constexpr int AN_TAIL_TOP_D = 16;
+constexpr int AN_TAIL_MAX = 4;
+
+struct AnTailLev {
+    int n, b0, b1, lo, hi;
+    double h, dinv;
+    const unsigned char* typ;
+};
+struct AnTail {
+    int L, nu1, nu2, load_e, m;
+    double sigma;
+    AnTailLev lev[AN_TAIL_MAX];
+    const double* Ainv;
+    const int* map;
+};
+
+__host__ __device__ constexpr size_t an_a16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+template <typename R>
+__device__ void an_t_sweep(typename CX<R>::T* e, const typename CX<R>::T* rhs, const unsigned char* typ, int n, R h,
+                           R dinv, int color)
+{
+    typedef typename CX<R>::T c2;
+    const int S = n + 1;
+    const R h2 = h * h;
+    for (int q = threadIdx.x; q < S * S; q += blockDim.x) {
+        const int i = q / S, j = q % S;
+        if (((i + j) & 1) != color) continue;
+        const unsigned char ty = typ[q];
+        if (ty == AN_PDE) {
+            const c2 sn = nbr_sum(e, q, S);
+            const c2 r = rhs[q];
+            c2 v;
+            v.x = (sn.x - h2 * r.x) * dinv;
+            v.y = (sn.y - h2 * r.y) * dinv;
+            e[q] = v;
+        } else if (ty == AN_EDGE) {
+            const c2 mv = inward_mean(e, i, j, n);
+            const c2 r = rhs[q];
+            c2 v;
+            v.x = mv.x + h * r.x;
+            v.y = mv.y + h * r.y;
+            e[q] = v;
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(1024)
+k_an_tail(typename CX<R>::T* __restrict__ eg, const typename CX<R>::T* __restrict__ rg, AnTail T)
+{
+    typedef typename CX<R>::T c2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    c2* E[AN_TAIL_MAX];
+    c2* Rr[AN_TAIL_MAX];
+    unsigned char* Ty[AN_TAIL_MAX];
+    size_t off = 0;
+    for (int l = 0; l < T.L; ++l) {
+        const size_t pts = (size_t)(T.lev[l].n + 1) * (T.lev[l].n + 1);
+        E[l] = reinterpret_cast<c2*>(smem_raw + off);
+        off += an_a16(pts * sizeof(c2));
+        Rr[l] = reinterpret_cast<c2*>(smem_raw + off);
+        off += an_a16(pts * sizeof(c2));
+        Ty[l] = smem_raw + off;
+        off += an_a16(pts);
+    }
+    for (int l = 0; l < T.L; ++l) {
+        const int pts = (T.lev[l].n + 1) * (T.lev[l].n + 1);
+        for (int q = threadIdx.x; q < pts; q += blockDim.x) Ty[l][q] = T.lev[l].typ[q];
+    }
+    {
+        const int pts = (T.lev[0].n + 1) * (T.lev[0].n + 1);
+        c2 z;
+        z.x = 0;
+        z.y = 0;
+        for (int q = threadIdx.x; q < pts; q += blockDim.x) {
+            Rr[0][q] = rg[q];
+            E[0][q] = T.load_e ? eg[q] : z;
+        }
+    }
+    __syncthreads();
+    const R sig = (R)T.sigma;
+    // descent
+    for (int l = 0; l + 1 < T.L; ++l) {
+        const AnTailLev& Lv = T.lev[l];
+        const R h = (R)Lv.h, dinv = (R)Lv.dinv;
+        for (int sw = 0; sw < T.nu1; ++sw)
+            for (int col = 0; col < 2; ++col) {
+                an_t_sweep<R>(E[l], Rr[l], Ty[l], Lv.n, h, dinv, col);
+                __syncthreads();
+            }
+        const int nc = T.lev[l + 1].n, Sc = nc + 1;
+        const bool zero = T.nu1 == 0 && (l > 0 || !T.load_e);
+        for (int q = threadIdx.x; q < Sc * Sc; q += blockDim.x) {
+            const int I = q / Sc, J = q % Sc;
+            c2 z;
+            z.x = 0;
+            z.y = 0;
+            E[l + 1][q] = z;
+            const unsigned char ty = Ty[l + 1][q];
+            if (ty == AN_HOLE) {
+                Rr[l + 1][q] = z;
+            } else if (ty == AN_EDGE) {
+                Rr[l + 1][q] = an_resid<R>(E[l], Rr[l], Ty[l], 2 * I, 2 * J, Lv.n, h, sig, zero);
+            } else {
+                R ax = 0, ay = 0;
+                for (int a = -1; a <= 1; ++a)
+                    for (int b = -1; b <= 1; ++b) {
+                        const R wgt = (R)((2 - (a < 0 ? -a : a)) * (2 - (b < 0 ? -b : b)));
+                        const c2 r = an_resid<R>(E[l], Rr[l], Ty[l], 2 * I + a, 2 * J + b, Lv.n, h, sig, zero);
+                        ax += wgt * r.x;
+                        ay += wgt * r.y;
+                    }
+                c2 v;
+                v.x = ax * (R)(1.0 / 16.0);
+                v.y = ay * (R)(1.0 / 16.0);
+                Rr[l + 1][q] = v;
+            }
+        }
+        __syncthreads();
+    }
+    // the coarsest level, exactly
+    {
+        const int lc = T.L - 1;
+        for (int r = threadIdx.x; r < T.m; r += blockDim.x) {
+            double ax = 0.0, ay = 0.0;
+            for (int c = 0; c < T.m; ++c) {
+                const double a = T.Ainv[(size_t)r * T.m + c];
+                const c2 v = Rr[lc][T.map[c]];
+                ax += a * (double)v.x;
+                ay += a * (double)v.y;
+            }
+            c2 o;
+            o.x = (R)ax;
+            o.y = (R)ay;
+            E[lc][T.map[r]] = o;
+        }
+        __syncthreads();
+    }
+    // ascent
+    for (int l = T.L - 2; l >= 0; --l) {
+        const AnTailLev& Lv = T.lev[l];
+        const int n = Lv.n, S = n + 1, nc = T.lev[l + 1].n, Sc = nc + 1;
+        const R h = (R)Lv.h, dinv = (R)Lv.dinv;
+        for (int q = threadIdx.x; q < S * S; q += blockDim.x) {
+            if (Ty[l][q] == AN_HOLE) continue;
+            const int i = q / S, j = q % S;
+            const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1;
+            const c2 a = E[l + 1][I0 * Sc + J0], b = E[l + 1][I1 * Sc + J0];
+            const c2 c = E[l + 1][I0 * Sc + J1], d = E[l + 1][I1 * Sc + J1];
+            c2 v = E[l][q];
+            v.x += (R)0.25 * (((a.x + b.x) + c.x) + d.x);
+            v.y += (R)0.25 * (((a.y + b.y) + c.y) + d.y);
+            E[l][q] = v;
+        }
+        __syncthreads();
+        // band sweeps around the hole
+        {
+            const int b0 = Lv.b0, b1 = Lv.b1, lo = Lv.lo, hi = Lv.hi;
+            const int w = b1 - b0 + 1, th = lo - b0, bh = b1 - hi, hh = hi - lo + 1;
+            const int nA = th * w, nB = bh * w, nC = hh * th, nD = hh * bh;
+            const int total = nA + nB + nC + nD;
+            const R h2 = h * h;
+            for (int sw = 0; sw < 2 * AN_BAND_SWEEPS; ++sw) {
+                const int color = sw & 1;
+                for (int t = threadIdx.x; t < total; t += blockDim.x) {
+                    int i, j;
+                    if (t < nA) { i = b0 + t / w; j = b0 + t % w; }
+                    else if (t < nA + nB) { const int u = t - nA; i = hi + 1 + u / w; j = b0 + u % w; }
+                    else if (t < nA + nB + nC) { const int u = t - nA - nB; i = lo + u / th; j = b0 + u % th; }
+                    else { const int u = t - nA - nB - nC; i = lo + u / bh; j = hi + 1 + u % bh; }
+                    if (((i + j) & 1) != color) continue;
+                    const int q = i * S + j;
+                    if (Ty[l][q] != AN_PDE) continue;
+                    const c2 sn = nbr_sum(E[l], q, S);
+                    const c2 r = Rr[l][q];
+                    c2 v;
+                    v.x = (sn.x - h2 * r.x) * dinv;
+                    v.y = (sn.y - h2 * r.y) * dinv;
+                    E[l][q] = v;
+                }
+                __syncthreads();
+            }
+        }
+        for (int sw = 0; sw < T.nu2; ++sw)
+            for (int col = 0; col < 2; ++col) {
+                an_t_sweep<R>(E[l], Rr[l], Ty[l], n, h, dinv, col);
+                __syncthreads();
+            }
+    }
+    const int pts = (T.lev[0].n + 1) * (T.lev[0].n + 1);
+    for (int q = threadIdx.x; q < pts; q += blockDim.x) eg[q] = E[0][q];
+}
+
+template <typename R>
+size_t an_tail_bytes(const int* ns, int L)
+{
+    size_t off = 0;
+    for (int l = 0; l < L; ++l) {
+        const size_t pts = (size_t)(ns[l] + 1) * (ns[l] + 1);
+        off += 2 * an_a16(pts * sizeof(typename CX<R>::T)) + an_a16(pts);
+    }
+    return off;
+}
+
 // U := the hole data on hole nodes, 0 elsewhere (both iterate buffers)
 __global__ void __launch_bounds__(AN_NT)
 k_an_init(double2* __restrict__ U0, double2* __restrict__ U1, const double2* __restrict__ data,
@@ -416,6 +630,8 @@ struct helm_annulus {
     unsigned long long* kmin = nullptr;
     cudaStream_t stream = nullptr;
     std::vector<void*> allocs;
+    int t0 = -1;                          // first level of the one-CTA coarse tail
+    size_t tail_bytes = 0;
 };
 
 namespace {
@@ -523,6 +739,25 @@ helm_status an_vcycle(helm_annulus* a, int l, bool zero)
     typedef typename CX<R>::T c2;
     const auto& L = a->lev[l];
     cudaStream_t s = a->stream;
+    if (l == a->t0) {                      // this level and all coarser ones in one CTA
+        AnTail T{};
+        T.L = (int)a->lev.size() - l;
+        T.nu1 = a->nu1;
+        T.nu2 = a->nu2;
+        T.load_e = zero ? 0 : 1;
+        T.m = a->m;
+        T.sigma = a->sigma;
+        T.Ainv = a->Ainv;
+        T.map = a->map;
+        for (int i = 0; i < T.L; ++i) {
+            const auto& V = a->lev[l + i];
+            T.lev[i] = AnTailLev{V.n, V.b0, V.b1, V.lo, V.hi, V.h, 1.0 / (4.0 + a->sigma * V.h * V.h), V.typ};
+        }
+        k_an_tail<R><<<1, 1024, a->tail_bytes, s>>>((c2*)L.e, (const c2*)L.rhs, T);
+        AN_CK(cudaGetLastError());
+        add_launches(1);
+        return HELM_OK;
+    }
     if (l + 1 == (int)a->lev.size()) {
         k_an_coarse<R><<<1, AN_NT, 0, s>>>((const c2*)L.rhs, (c2*)L.e, a->Ainv, a->map, a->m);
         AN_CK(cudaGetLastError());
@@ -676,6 +911,23 @@ helm_status helm_annulus_create(helm_annulus** out, int n, double side, double h
         a->lev.push_back(L);
     }
     if (a->lev.size() < 2) return fail(HELM_EINVAL);
+    // the coarse tail: levels of at most `top` intervals (at most AN_TAIL_MAX of them)
+    const int top = prec == HELM_PREC_FP64 ? AN_TAIL_TOP_D : AN_TAIL_TOP_F;
+    for (int l = 0; l < (int)a->lev.size(); ++l)
+        if (a->lev[l].n <= top) { a->t0 = l; break; }
+    if (a->t0 >= 0 && (int)a->lev.size() - a->t0 <= AN_TAIL_MAX) {
+        int ns[AN_TAIL_MAX];
+        const int L = (int)a->lev.size() - a->t0;
+        for (int i = 0; i < L; ++i) ns[i] = a->lev[a->t0 + i].n;
+        a->tail_bytes = (prec == HELM_PREC_FP64) ? an_tail_bytes<double>(ns, L) : an_tail_bytes<float>(ns, L);
+        const cudaError_t e = (prec == HELM_PREC_FP64)
+            ? cudaFuncSetAttribute(k_an_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a->tail_bytes)
+            : cudaFuncSetAttribute(k_an_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a->tail_bytes);
+        if (e != cudaSuccess) a->t0 = -1;      // no tail: per-level launches all the way down
+        cudaGetLastError();
+    } else {
+        a->t0 = -1;
+    }
     const long total = (long)(n + 1) * (n + 1);
     a->nblk = grid_for(total);
     void* p = nullptr;
