@@ -40,6 +40,8 @@ constexpr int AN_NT = 256;
 constexpr int AN_NC = 8;            // coarsest level (solved exactly)
 constexpr int AN_BAND = 4;          // band half-width around the hole, in nodes of the level
 constexpr int AN_BAND_SWEEPS = 4;
+constexpr bool AN_BAND_SMEM = true;  // band sweeps in shared memory where the ring fits
+constexpr size_t AN_SMEM_MAX = 227 * 1024;
 enum : unsigned char { AN_PDE = 0, AN_EDGE = 1, AN_HOLE = 2 };
 
 template <typename R> struct CX;
@@ -147,6 +149,146 @@ k_an_band(typename CX<R>::T* e, const typename CX<R>::T* __restrict__ rhs, const
             __stcg(e + q, v);
         }
         __syncthreads();
+    }
+}
+
+// The same sweeps with the ring and a 1-node halo around it staged in shared memory: the
+// ring's four strips (rows b0 - 1 .. lo - 1 and hi + 1 .. b1 + 1 across the band's width
+// plus halo; columns b0 - 1 .. lo - 1 and hi + 1 .. b1 + 1 over the hole's rows); nodes
+// of the hole's box read as zero, as they hold in the iterate.  The ring's rhs is staged
+// by ring index.
+struct AnRing {
+    int b0, b1, lo, hi;
+    int w, th, bh, hh, W2, sA, sB, sC, sD, nA, nB, nC, nD;
+    __host__ __device__ AnRing(int b0_, int b1_, int lo_, int hi_) : b0(b0_), b1(b1_), lo(lo_), hi(hi_)
+    {
+        w = b1 - b0 + 1;
+        th = lo - b0;
+        bh = b1 - hi;
+        hh = hi - lo + 1;
+        W2 = w + 2;
+        sA = (th + 1) * W2;
+        sB = (bh + 1) * W2;
+        sC = hh * (th + 1);
+        sD = hh * (bh + 1);
+        nA = th * w;
+        nB = bh * w;
+        nC = hh * th;
+        nD = hh * bh;
+    }
+    __host__ __device__ int stored() const { return sA + sB + sC + sD; }
+    __host__ __device__ int total() const { return nA + nB + nC + nD; }
+    // shared-memory slot of node (i, j) of the window, -1 inside the hole's box
+    __device__ int slot(int i, int j) const
+    {
+        if (i < lo) return (i - (b0 - 1)) * W2 + (j - (b0 - 1));
+        if (i > hi) return sA + (i - (hi + 1)) * W2 + (j - (b0 - 1));
+        if (j < lo) return sA + sB + (i - lo) * (th + 1) + (j - (b0 - 1));
+        if (j > hi) return sA + sB + sC + (i - lo) * (bh + 1) + (j - (hi + 1));
+        return -1;
+    }
+    // node of window slot u
+    __device__ void window_node(int u, int& i, int& j) const
+    {
+        if (u < sA) { i = b0 - 1 + u / W2; j = b0 - 1 + u % W2; return; }
+        u -= sA;
+        if (u < sB) { i = hi + 1 + u / W2; j = b0 - 1 + u % W2; return; }
+        u -= sB;
+        if (u < sC) { i = lo + u / (th + 1); j = b0 - 1 + u % (th + 1); return; }
+        u -= sC;
+        i = lo + u / (bh + 1);
+        j = hi + 1 + u % (bh + 1);
+    }
+    // node of ring index t (the order of k_an_band)
+    __device__ void ring_node(int t, int& i, int& j) const
+    {
+        if (t < nA) { i = b0 + t / w; j = b0 + t % w; return; }
+        t -= nA;
+        if (t < nB) { i = hi + 1 + t / w; j = b0 + t % w; return; }
+        t -= nB;
+        if (t < nC) { i = lo + t / th; j = b0 + t % th; return; }
+        t -= nC;
+        i = lo + t / bh;
+        j = hi + 1 + t % bh;
+    }
+};
+
+template <typename R>
+size_t an_band_bytes(const AnRing& g)
+{
+    const size_t c = sizeof(typename CX<R>::T);
+    return (size_t)g.stored() * c + (size_t)g.total() * c;
+}
+
+// Each thread owns ring indices threadIdx.x + 1024 k (k < AN_BAND_PT) and keeps, for each,
+// the shared-memory slots of the node and of its four neighbours (-1: the hole's box),
+// found once; a half-sweep is then shared-memory loads and the update alone.
+constexpr int AN_BAND_PT = 5;
+
+template <typename R>
+__global__ void __launch_bounds__(1024)
+k_an_band_s(typename CX<R>::T* __restrict__ e, const typename CX<R>::T* __restrict__ rhs,
+            const unsigned char* __restrict__ typ, int n, R h, R dinv, AnRing g, int sweeps)
+{
+    typedef typename CX<R>::T c2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int S = n + 1;
+    const int stored = g.stored(), total = g.total();
+    c2* Es = reinterpret_cast<c2*>(smem_raw);
+    c2* Rs = Es + stored;
+    for (int u = threadIdx.x; u < stored; u += blockDim.x) {
+        int i, j;
+        g.window_node(u, i, j);
+        Es[u] = e[i * S + j];
+    }
+    int self[AN_BAND_PT], nb[AN_BAND_PT][4];
+    unsigned colour = 0;                          // bit k: the owned node's colour
+#pragma unroll
+    for (int k = 0; k < AN_BAND_PT; ++k) {
+        const int t = threadIdx.x + 1024 * k;
+        self[k] = -1;
+        nb[k][0] = nb[k][1] = nb[k][2] = nb[k][3] = -1;
+        if (t < total) {
+            int i, j;
+            g.ring_node(t, i, j);
+            Rs[t] = rhs[i * S + j];
+            if (typ[i * S + j] == AN_PDE) {
+                self[k] = g.slot(i, j);
+                nb[k][0] = g.slot(i - 1, j);
+                nb[k][1] = g.slot(i + 1, j);
+                nb[k][2] = g.slot(i, j - 1);
+                nb[k][3] = g.slot(i, j + 1);
+                colour |= (unsigned)((i + j) & 1) << k;
+            }
+        }
+    }
+    __syncthreads();
+    const R h2 = h * h;
+    c2 z;
+    z.x = 0;
+    z.y = 0;
+    for (int s = 0; s < 2 * sweeps; ++s) {
+        const unsigned color = s & 1;
+#pragma unroll
+        for (int k = 0; k < AN_BAND_PT; ++k) {
+            if (self[k] < 0 || ((colour >> k) & 1u) != color) continue;
+            const c2 a = nb[k][0] < 0 ? z : Es[nb[k][0]], b = nb[k][1] < 0 ? z : Es[nb[k][1]];
+            const c2 c = nb[k][2] < 0 ? z : Es[nb[k][2]], d = nb[k][3] < 0 ? z : Es[nb[k][3]];
+            const c2 r = Rs[threadIdx.x + 1024 * k];
+            c2 v;
+            v.x = (((a.x + b.x) + (c.x + d.x)) - h2 * r.x) * dinv;
+            v.y = (((a.y + b.y) + (c.y + d.y)) - h2 * r.y) * dinv;
+            Es[self[k]] = v;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < AN_BAND_PT; ++k) {
+        const int t = threadIdx.x + 1024 * k;
+        if (self[k] < 0) continue;
+        int i, j;
+        g.ring_node(t, i, j);
+        e[i * S + j] = Es[self[k]];
     }
 }
 
@@ -618,6 +760,7 @@ struct helm_annulus {
         void* e;
         void* rhs;
         int b0, b1, lo, hi;               // band ring [b0, b1]^2 minus the hole box [lo, hi]^2
+        size_t band_bytes;                // shared memory of k_an_band_s (0: the L2 form)
     };
     std::vector<Level> lev;
     double* Ainv = nullptr;
@@ -781,8 +924,12 @@ helm_status an_vcycle(helm_annulus* a, int l, bool zero)
     if (st != HELM_OK) return st;
     k_an_prolong<R><<<grid_for((long)(L.n + 1) * (L.n + 1)), AN_NT, 0, s>>>((const c2*)C.e, C.n, (c2*)L.e, L.typ,
                                                                              L.n);
-    k_an_band<R><<<1, 1024, 0, s>>>((c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, dinv, L.b0, L.b1, L.lo, L.hi,
-                                    AN_BAND_SWEEPS);
+    if (L.band_bytes)
+        k_an_band_s<R><<<1, 1024, L.band_bytes, s>>>((c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, dinv,
+                                                    AnRing(L.b0, L.b1, L.lo, L.hi), AN_BAND_SWEEPS);
+    else
+        k_an_band<R><<<1, 1024, 0, s>>>((c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, dinv, L.b0, L.b1, L.lo,
+                                        L.hi, AN_BAND_SWEEPS);
     add_launches(2);
     for (int sweep = 0; sweep < a->nu2; ++sweep)
         for (int col = 0; col < 2; ++col) {
@@ -908,6 +1055,12 @@ helm_status helm_annulus_create(helm_annulus** out, int n, double side, double h
         L.hi = hi;
         L.b0 = std::max(1, lo - AN_BAND);
         L.b1 = std::min(m - 1, hi + AN_BAND);
+        L.band_bytes = 0;
+        if (AN_BAND_SMEM) {
+            const AnRing g(L.b0, L.b1, L.lo, L.hi);
+            const size_t bb = prec == HELM_PREC_FP64 ? an_band_bytes<double>(g) : an_band_bytes<float>(g);
+            if (bb <= AN_SMEM_MAX && g.total() <= 1024 * AN_BAND_PT) L.band_bytes = bb;
+        }
         a->lev.push_back(L);
     }
     if (a->lev.size() < 2) return fail(HELM_EINVAL);
@@ -927,6 +1080,14 @@ helm_status helm_annulus_create(helm_annulus** out, int n, double side, double h
         cudaGetLastError();
     } else {
         a->t0 = -1;
+    }
+    size_t band_max = 0;
+    for (const auto& L : a->lev) band_max = std::max(band_max, L.band_bytes);
+    if (band_max) {
+        const cudaError_t e = (prec == HELM_PREC_FP64)
+            ? cudaFuncSetAttribute(k_an_band_s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_max)
+            : cudaFuncSetAttribute(k_an_band_s<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_max);
+        if (e != cudaSuccess) return fail(HELM_ECUDA);
     }
     const long total = (long)(n + 1) * (n + 1);
     a->nblk = grid_for(total);
