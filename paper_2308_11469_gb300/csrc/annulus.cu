@@ -41,12 +41,15 @@ constexpr int AN_NC = 8;            // coarsest level (solved exactly)
 constexpr int AN_BAND = 4;          // band half-width around the hole, in nodes of the level
 constexpr int AN_BAND_SWEEPS = 4;
 constexpr bool AN_BAND_SMEM = true;  // band sweeps in shared memory where the ring fits
+constexpr bool AN_TILES = true;      // each side's sweeps of a level in one tile launch
 constexpr size_t AN_SMEM_MAX = 227 * 1024;
 enum : unsigned char { AN_PDE = 0, AN_EDGE = 1, AN_HOLE = 2 };
 
 template <typename R> struct CX;
 template <> struct CX<float> { typedef float2 T; };
 template <> struct CX<double> { typedef double2 T; };
+
+__host__ __device__ constexpr size_t an_a16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 int grid_for(long work) { return (int)std::min<long>((work + AN_NT - 1) / AN_NT, 152L * 16); }
 
@@ -318,6 +321,242 @@ __device__ __forceinline__ typename CX<R>::T an_resid(const typename CX<R>::T* e
     return r;
 }
 
+// ---------------------------------------------------------------------------
+// Tile kernels: a level's sweeps (and its residual + restriction) on a window in shared
+// memory, so that the sweeps of one side of the cycle are one launch
+// ---------------------------------------------------------------------------
+// A window [sy0, sy1] x [sx0, sx1] of the level (clipped to [0, n]) is staged with row
+// stride SW.  Half-sweep k updates the nodes of its colour that lie k + 1 nodes inside
+// every window side that is not a side of the grid, so that each updated node sees the
+// values the per-level kernels would give it; after 2 nu half-sweeps the values are those
+// of the per-level sweeps on the window shrunk by 2 nu (grid sides excepted).
+constexpr int AN_CT = 16;            // coarse nodes per side of a descent tile
+constexpr int AN_FT = 32;            // fine nodes per side of an ascent tile
+
+// mean of the inward neighbours of edge node (i, j) at window index q
+template <typename T>
+__device__ __forceinline__ T inward_mean_w(const T* e, int q, int SW, int i, int j, int n)
+{
+    T s;
+    s.x = 0;
+    s.y = 0;
+    int c = 0;
+    if (i == 0) { s.x += e[q + SW].x; s.y += e[q + SW].y; ++c; }
+    if (i == n) { s.x += e[q - SW].x; s.y += e[q - SW].y; ++c; }
+    if (j == 0) { s.x += e[q + 1].x; s.y += e[q + 1].y; ++c; }
+    if (j == n) { s.x += e[q - 1].x; s.y += e[q - 1].y; ++c; }
+    if (c == 2) { s.x *= 0.5f; s.y *= 0.5f; }
+    return s;
+}
+
+template <typename R>
+__device__ __forceinline__ typename CX<R>::T an_resid_w(const typename CX<R>::T* e, const typename CX<R>::T* rhs,
+                                                        const unsigned char* typ, int q, int SW, int i, int j,
+                                                        int n, R h, R sig, bool zero)
+{
+    typedef typename CX<R>::T c2;
+    const unsigned char ty = typ[q];
+    c2 r = rhs[q];
+    if (ty == AN_HOLE) { r.x = 0; r.y = 0; return r; }
+    if (zero) return r;
+    const c2 c = e[q];
+    if (ty == AN_PDE) {
+        const c2 s = nbr_sum(e, q, SW);
+        const R ih2 = (R)1 / (h * h);
+        r.x -= (s.x - (R)4 * c.x) * ih2 - sig * c.x;
+        r.y -= (s.y - (R)4 * c.y) * ih2 - sig * c.y;
+    } else {
+        const c2 m = inward_mean_w(e, q, SW, i, j, n);
+        r.x -= (c.x - m.x) / h;
+        r.y -= (c.y - m.y) / h;
+    }
+    return r;
+}
+
+struct AnWin {
+    int sx0, sx1, sy0, sy1, SW;
+};
+
+// stage e (or zeros), rhs and the row types of the window
+template <typename R>
+__device__ void an_stage(typename CX<R>::T* E, typename CX<R>::T* Rr, unsigned char* Ty, const AnWin& w,
+                         const typename CX<R>::T* __restrict__ e, const typename CX<R>::T* __restrict__ rhs,
+                         const unsigned char* __restrict__ typ, int n, bool load_e)
+{
+    typedef typename CX<R>::T c2;
+    const int S = n + 1, ww = w.sx1 - w.sx0 + 1, cnt = ww * (w.sy1 - w.sy0 + 1);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int ly = t / ww, lx = t % ww;
+        const int g = (w.sy0 + ly) * S + w.sx0 + lx, q = ly * w.SW + lx;
+        c2 z;
+        z.x = 0;
+        z.y = 0;
+        E[q] = load_e ? e[g] : z;
+        Rr[q] = rhs[g];
+        Ty[q] = typ[g];
+    }
+}
+
+// nu red-black sweeps on the window
+template <typename R>
+__device__ void an_sweeps_w(typename CX<R>::T* E, const typename CX<R>::T* Rr, const unsigned char* Ty,
+                            const AnWin& w, int n, R h, R dinv, int nu)
+{
+    typedef typename CX<R>::T c2;
+    const R h2 = h * h;
+    for (int k = 0; k < 2 * nu; ++k) {
+        const int color = k & 1;
+        const int ux0 = w.sx0 == 0 ? 0 : w.sx0 + k + 1, ux1 = w.sx1 == n ? n : w.sx1 - k - 1;
+        const int uy0 = w.sy0 == 0 ? 0 : w.sy0 + k + 1, uy1 = w.sy1 == n ? n : w.sy1 - k - 1;
+        const int uw = ux1 - ux0 + 1, uh = uy1 - uy0 + 1;
+        const int cnt = (uw > 0 && uh > 0) ? uw * uh : 0;
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const int i = uy0 + t / uw, j = ux0 + t % uw;
+            if (((i + j) & 1) != color) continue;
+            const int q = (i - w.sy0) * w.SW + (j - w.sx0);
+            const unsigned char ty = Ty[q];
+            if (ty == AN_PDE) {
+                const c2 sn = nbr_sum(E, q, w.SW);
+                const c2 r = Rr[q];
+                c2 v;
+                v.x = (sn.x - h2 * r.x) * dinv;
+                v.y = (sn.y - h2 * r.y) * dinv;
+                E[q] = v;
+            } else if (ty == AN_EDGE) {
+                const c2 m = inward_mean_w(E, q, w.SW, i, j, n);
+                const c2 r = Rr[q];
+                c2 v;
+                v.x = m.x + h * r.x;
+                v.y = m.y + h * r.y;
+                E[q] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename R>
+size_t an_win_bytes(int SW)
+{
+    const size_t pts = (size_t)SW * SW;
+    return 2 * an_a16(pts * sizeof(typename CX<R>::T)) + an_a16(pts);
+}
+__host__ __device__ constexpr int an_down_sw(int nu1) { return 2 * AN_CT + 3 + 4 * nu1; }
+__host__ __device__ constexpr int an_up_sw(int nu2) { return AN_FT + 4 * nu2; }
+
+// Descent of one level: nu1 sweeps, then the coarse rhs (full weighting of the residual at
+// coarse PDE nodes, injection at coarse edge nodes, zero on the hole) and a zero coarse
+// iterate for the coarse nodes [I0, I0 + AN_CT) x [J0, J0 + AN_CT); the swept fine iterate
+// goes to e_out on the fine nodes [2 I0, 2 I0 + 2 AN_CT) x [2 J0, 2 J0 + 2 AN_CT): a
+// separate buffer, since other CTAs stage their windows from e_in meanwhile.
+template <typename R>
+__global__ void __launch_bounds__(AN_NT)
+k_an_down(const typename CX<R>::T* __restrict__ e, typename CX<R>::T* __restrict__ e_out,
+          const typename CX<R>::T* __restrict__ rhs,
+          const unsigned char* __restrict__ typ, int n, R h, R dinv, R sig, int nu1, int load_e,
+          typename CX<R>::T* __restrict__ rc, typename CX<R>::T* __restrict__ ec,
+          const unsigned char* __restrict__ tc, int nc)
+{
+    typedef typename CX<R>::T c2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ntc = (nc + AN_CT) / AN_CT;
+    const int I0 = (blockIdx.x / ntc) * AN_CT, J0 = (blockIdx.x % ntc) * AN_CT;
+    const int hw = 2 + 2 * nu1;               // low side; the high side needs 2 nu1
+    AnWin w;
+    w.SW = an_down_sw(nu1);
+    w.sy0 = max(0, 2 * I0 - hw);
+    w.sy1 = min(n, 2 * I0 + 2 * AN_CT + 2 * nu1);
+    w.sx0 = max(0, 2 * J0 - hw);
+    w.sx1 = min(n, 2 * J0 + 2 * AN_CT + 2 * nu1);
+    const size_t pts = (size_t)w.SW * w.SW;
+    c2* E = reinterpret_cast<c2*>(smem_raw);
+    c2* Rr = reinterpret_cast<c2*>(smem_raw + an_a16(pts * sizeof(c2)));
+    unsigned char* Ty = smem_raw + 2 * an_a16(pts * sizeof(c2));
+    an_stage<R>(E, Rr, Ty, w, e, rhs, typ, n, load_e != 0);
+    __syncthreads();
+    an_sweeps_w<R>(E, Rr, Ty, w, n, h, dinv, nu1);
+    const bool zero = nu1 == 0 && load_e == 0;
+    const int Sc = nc + 1, S = n + 1;
+    const int ci1 = min(nc, I0 + AN_CT - 1), cj1 = min(nc, J0 + AN_CT - 1);
+    const int cw = cj1 - J0 + 1, ccnt = cw * (ci1 - I0 + 1);
+    for (int t = threadIdx.x; t < ccnt; t += blockDim.x) {
+        const int I = I0 + t / cw, J = J0 + t % cw;
+        const int qc = I * Sc + J;
+        c2 z;
+        z.x = 0;
+        z.y = 0;
+        ec[qc] = z;
+        const unsigned char ty = tc[qc];
+        if (ty == AN_HOLE) {
+            rc[qc] = z;
+        } else if (ty == AN_EDGE) {
+            const int i = 2 * I, j = 2 * J;
+            rc[qc] = an_resid_w<R>(E, Rr, Ty, (i - w.sy0) * w.SW + (j - w.sx0), w.SW, i, j, n, h, sig, zero);
+        } else {
+            R ax = 0, ay = 0;
+#pragma unroll
+            for (int a = -1; a <= 1; ++a)
+#pragma unroll
+                for (int b = -1; b <= 1; ++b) {
+                    const R wgt = (R)((2 - (a < 0 ? -a : a)) * (2 - (b < 0 ? -b : b)));
+                    const int i = 2 * I + a, j = 2 * J + b;
+                    const c2 r = an_resid_w<R>(E, Rr, Ty, (i - w.sy0) * w.SW + (j - w.sx0), w.SW, i, j, n, h, sig,
+                                               zero);
+                    ax += wgt * r.x;
+                    ay += wgt * r.y;
+                }
+            c2 v;
+            v.x = ax * (R)(1.0 / 16.0);
+            v.y = ay * (R)(1.0 / 16.0);
+            rc[qc] = v;
+        }
+    }
+    {
+        const int fi0 = 2 * I0, fi1 = min(n, 2 * I0 + 2 * AN_CT - 1);
+        const int fj0 = 2 * J0, fj1 = min(n, 2 * J0 + 2 * AN_CT - 1);
+        const int fw = fj1 - fj0 + 1, fcnt = fw * (fi1 - fi0 + 1);
+        for (int t = threadIdx.x; t < fcnt; t += blockDim.x) {
+            const int i = fi0 + t / fw, j = fj0 + t % fw;
+            e_out[i * S + j] = E[(i - w.sy0) * w.SW + (j - w.sx0)];
+        }
+    }
+}
+
+// Ascent sweeps of one level: nu2 sweeps of e_in; the fine nodes [32 by, 32 by + 32) x
+// [32 bx, 32 bx + 32) go to e_out.
+template <typename R>
+__global__ void __launch_bounds__(AN_NT)
+k_an_up(const typename CX<R>::T* __restrict__ e, typename CX<R>::T* __restrict__ e_out,
+        const typename CX<R>::T* __restrict__ rhs,
+        const unsigned char* __restrict__ typ, int n, R h, R dinv, int nu2)
+{
+    typedef typename CX<R>::T c2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nt = (n + AN_FT) / AN_FT;
+    const int i0 = (blockIdx.x / nt) * AN_FT, j0 = (blockIdx.x % nt) * AN_FT;
+    const int hw = 2 * nu2;
+    AnWin w;
+    w.SW = an_up_sw(nu2);
+    w.sy0 = max(0, i0 - hw);
+    w.sy1 = min(n, i0 + AN_FT - 1 + hw);
+    w.sx0 = max(0, j0 - hw);
+    w.sx1 = min(n, j0 + AN_FT - 1 + hw);
+    const size_t pts = (size_t)w.SW * w.SW;
+    c2* E = reinterpret_cast<c2*>(smem_raw);
+    c2* Rr = reinterpret_cast<c2*>(smem_raw + an_a16(pts * sizeof(c2)));
+    unsigned char* Ty = smem_raw + 2 * an_a16(pts * sizeof(c2));
+    an_stage<R>(E, Rr, Ty, w, e, rhs, typ, n, true);
+    __syncthreads();
+    an_sweeps_w<R>(E, Rr, Ty, w, n, h, dinv, nu2);
+    const int S = n + 1;
+    const int fi1 = min(n, i0 + AN_FT - 1), fj1 = min(n, j0 + AN_FT - 1);
+    const int fw = fj1 - j0 + 1, fcnt = fw * (fi1 - i0 + 1);
+    for (int t = threadIdx.x; t < fcnt; t += blockDim.x) {
+        const int i = i0 + t / fw, j = j0 + t % fw;
+        e_out[i * S + j] = E[(i - w.sy0) * w.SW + (j - w.sx0)];
+    }
+}
+
 // coarse rhs: full weighting of the fine residual at PDE nodes, injection at EDGE nodes;
 // coarse iterate := 0
 template <typename R>
@@ -427,7 +666,6 @@ struct AnTail {
     const int* map;
 };
 
-__host__ __device__ constexpr size_t an_a16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 template <typename R>
 __device__ void an_t_sweep(typename CX<R>::T* e, const typename CX<R>::T* rhs, const unsigned char* typ, int n, R h,
@@ -759,6 +997,7 @@ struct helm_annulus {
         unsigned char* typ;
         void* e;
         void* rhs;
+        void* e2;                         // the swept iterate between the tile kernels
         int b0, b1, lo, hi;               // band ring [b0, b1]^2 minus the hole box [lo, hi]^2
         size_t band_bytes;                // shared memory of k_an_band_s (0: the L2 form)
     };
@@ -773,6 +1012,7 @@ struct helm_annulus {
     unsigned long long* kmin = nullptr;
     cudaStream_t stream = nullptr;
     std::vector<void*> allocs;
+    bool tiles = false;                   // the levels above the tail use the tile kernels
     int t0 = -1;                          // first level of the one-CTA coarse tail
     size_t tail_bytes = 0;
 };
@@ -910,32 +1150,52 @@ helm_status an_vcycle(helm_annulus* a, int l, bool zero)
     const R h = (R)L.h, dinv = (R)(1.0 / (4.0 + a->sigma * L.h * L.h));
     const int half = (L.n + 2) / 2;
     const int g = grid_for((long)(L.n + 1) * half);
-    for (int sweep = 0; sweep < a->nu1; ++sweep)
-        for (int col = 0; col < 2; ++col) {
-            k_an_rbgs<R><<<g, AN_NT, 0, s>>>((c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, dinv, col, 0, L.n, 0, L.n);
-            add_launches(1);
-        }
     const auto& C = a->lev[l + 1];
-    k_an_restrict<R><<<grid_for((long)(C.n + 1) * (C.n + 1)), AN_NT, 0, s>>>(
-        (const c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, (R)a->sigma, (c2*)C.rhs, (c2*)C.e, C.typ, C.n,
-        (zero && a->nu1 == 0) ? 1 : 0);
-    add_launches(1);
+    const bool tiles = a->tiles;
+    // with the tile kernels the iterate goes e -> e2 (descent), e2 (correction, band),
+    // e2 -> e (ascent)
+    c2* const ew = (c2*)(tiles ? L.e2 : L.e);
+    if (tiles) {
+        const int ntc = (C.n + AN_CT) / AN_CT;
+        k_an_down<R><<<ntc * ntc, AN_NT, an_win_bytes<R>(an_down_sw(a->nu1)), s>>>(
+            (const c2*)L.e, ew, (const c2*)L.rhs, L.typ, L.n, h, dinv, (R)a->sigma, a->nu1, zero ? 0 : 1, (c2*)C.rhs,
+            (c2*)C.e, C.typ, C.n);
+        add_launches(1);
+    } else {
+        for (int sweep = 0; sweep < a->nu1; ++sweep)
+            for (int col = 0; col < 2; ++col) {
+                k_an_rbgs<R><<<g, AN_NT, 0, s>>>((c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, dinv, col, 0, L.n, 0,
+                                                 L.n);
+                add_launches(1);
+            }
+        k_an_restrict<R><<<grid_for((long)(C.n + 1) * (C.n + 1)), AN_NT, 0, s>>>(
+            (const c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, (R)a->sigma, (c2*)C.rhs, (c2*)C.e, C.typ, C.n,
+            (zero && a->nu1 == 0) ? 1 : 0);
+        add_launches(1);
+    }
     helm_status st = an_vcycle<R>(a, l + 1, true);
     if (st != HELM_OK) return st;
-    k_an_prolong<R><<<grid_for((long)(L.n + 1) * (L.n + 1)), AN_NT, 0, s>>>((const c2*)C.e, C.n, (c2*)L.e, L.typ,
-                                                                             L.n);
+    k_an_prolong<R><<<grid_for((long)(L.n + 1) * (L.n + 1)), AN_NT, 0, s>>>((const c2*)C.e, C.n, ew, L.typ, L.n);
     if (L.band_bytes)
-        k_an_band_s<R><<<1, 1024, L.band_bytes, s>>>((c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, dinv,
+        k_an_band_s<R><<<1, 1024, L.band_bytes, s>>>(ew, (const c2*)L.rhs, L.typ, L.n, h, dinv,
                                                     AnRing(L.b0, L.b1, L.lo, L.hi), AN_BAND_SWEEPS);
     else
-        k_an_band<R><<<1, 1024, 0, s>>>((c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, dinv, L.b0, L.b1, L.lo,
-                                        L.hi, AN_BAND_SWEEPS);
+        k_an_band<R><<<1, 1024, 0, s>>>(ew, (const c2*)L.rhs, L.typ, L.n, h, dinv, L.b0, L.b1, L.lo, L.hi,
+                                        AN_BAND_SWEEPS);
     add_launches(2);
-    for (int sweep = 0; sweep < a->nu2; ++sweep)
-        for (int col = 0; col < 2; ++col) {
-            k_an_rbgs<R><<<g, AN_NT, 0, s>>>((c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, dinv, col, 0, L.n, 0, L.n);
-            add_launches(1);
-        }
+    if (tiles) {                           // nu2 = 0: the launch only moves e2 to e
+        const int nt = (L.n + AN_FT) / AN_FT;
+        k_an_up<R><<<nt * nt, AN_NT, an_win_bytes<R>(an_up_sw(a->nu2)), s>>>(ew, (c2*)L.e, (const c2*)L.rhs,
+                                                                            L.typ, L.n, h, dinv, a->nu2);
+        add_launches(1);
+    } else {
+        for (int sweep = 0; sweep < a->nu2; ++sweep)
+            for (int col = 0; col < 2; ++col) {
+                k_an_rbgs<R><<<g, AN_NT, 0, s>>>((c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, dinv, col, 0, L.n, 0,
+                                                 L.n);
+                add_launches(1);
+            }
+    }
     AN_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -1039,13 +1299,16 @@ helm_status helm_annulus_create(helm_annulus** out, int n, double side, double h
         L.h = side / m;
         const size_t pts = (size_t)(m + 1) * (m + 1);
         void* p = nullptr;
-        if (cudaMalloc(&p, pts + 2 * pts * eb + 512) != cudaSuccess) return fail(HELM_ENOMEM);
+        const size_t pb = ((pts * eb + 255) / 256) * 256;
+        if (cudaMalloc(&p, ((pts + 255) / 256) * 256 + 3 * pb) != cudaSuccess) return fail(HELM_ENOMEM);
         a->allocs.push_back(p);
         L.typ = (unsigned char*)p;
         L.e = (char*)p + ((pts + 255) / 256) * 256;
-        L.rhs = (char*)L.e + ((pts * eb + 255) / 256) * 256;
+        L.rhs = (char*)L.e + pb;
+        L.e2 = (char*)L.rhs + pb;
         if (cudaMemcpy(L.typ, t.data(), pts, cudaMemcpyHostToDevice) != cudaSuccess) return fail(HELM_ECUDA);
-        if (cudaMemset(L.e, 0, pts * eb) != cudaSuccess || cudaMemset(L.rhs, 0, pts * eb) != cudaSuccess)
+        if (cudaMemset(L.e, 0, pts * eb) != cudaSuccess || cudaMemset(L.rhs, 0, pts * eb) != cudaSuccess ||
+            cudaMemset(L.e2, 0, pts * eb) != cudaSuccess)
             return fail(HELM_ECUDA);
         // band: the hole's index box [lo, hi]^2 (centred square) widened by AN_BAND nodes
         int lo = m, hi = 0;
@@ -1080,6 +1343,21 @@ helm_status helm_annulus_create(helm_annulus** out, int n, double side, double h
         cudaGetLastError();
     } else {
         a->t0 = -1;
+    }
+    {
+        const size_t dmax = (prec == HELM_PREC_FP64) ? an_win_bytes<double>(an_down_sw(8)) : an_win_bytes<float>(an_down_sw(8));
+        const size_t umax = (prec == HELM_PREC_FP64) ? an_win_bytes<double>(an_up_sw(8)) : an_win_bytes<float>(an_up_sw(8));
+        cudaError_t e1, e2;
+        if (prec == HELM_PREC_FP64) {
+            e1 = cudaFuncSetAttribute(k_an_down<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dmax);
+            e2 = cudaFuncSetAttribute(k_an_up<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)umax);
+        } else {
+            e1 = cudaFuncSetAttribute(k_an_down<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dmax);
+            e2 = cudaFuncSetAttribute(k_an_up<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)umax);
+        }
+        if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(HELM_ECUDA);
+        // in FP64 the windows' redundant halo sweeps cost more than the launches they save
+        a->tiles = AN_TILES && prec == HELM_PREC_MIXED;
     }
     size_t band_max = 0;
     for (const auto& L : a->lev) band_max = std::max(band_max, L.band_bytes);

@@ -134,3 +134,17 @@ def test_argument_checks(B):
     with pytest.raises(B.HelmError):
         B.helm_annulus_set_cycle(plan, 0, 0, 1)
     B.helm_annulus_destroy(plan)
+
+
+@pytest.mark.parametrize("cycle", [(2, 2, 1), (0, 1, 2), (1, 0, 1)])
+def test_repeated_solve_is_bit_identical(B, cycle):
+    # the tile kernels stage overlapping windows while other CTAs write their swept nodes:
+    # any read of a neighbour's output would show up as run-to-run differences
+    N, k = 512, 0.8
+    g = an.geometry(N)
+    data = an.scattering_data(g, k)
+    runs = [_solve(B, N, k, data, 1, 1e-8, 3000, cycle=cycle) for _ in range(3)]
+    for st, iters, hist, u in runs[1:]:
+        assert st == runs[0][0] and iters == runs[0][1]
+        assert np.array_equal(hist, runs[0][2])
+        assert np.array_equal(u, runs[0][3])
