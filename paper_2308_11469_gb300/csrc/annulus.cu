@@ -42,6 +42,7 @@ constexpr int AN_BAND = 4;          // band half-width around the hole, in nodes
 constexpr int AN_BAND_SWEEPS = 4;
 constexpr bool AN_BAND_SMEM = true;  // band sweeps in shared memory where the ring fits
 constexpr bool AN_TILES = true;      // each side's sweeps of a level in one tile launch
+constexpr bool AN_GRAPHS = true;     // an outer step replayed as one graph launch
 constexpr size_t AN_SMEM_MAX = 227 * 1024;
 enum : unsigned char { AN_PDE = 0, AN_EDGE = 1, AN_HOLE = 2 };
 
@@ -1013,6 +1014,10 @@ struct helm_annulus {
     cudaStream_t stream = nullptr;
     std::vector<void*> allocs;
     bool tiles = false;                   // the levels above the tail use the tile kernels
+    cudaStream_t ls = nullptr;            // where an_vcycle and the step launch (stream, or cap)
+    cudaStream_t cap = nullptr;           // non-blocking stream for capturing a step's graph
+    bool capturing = false;
+    uint64_t captured = 0;                // kernels recorded by the capture in progress
     int t0 = -1;                          // first level of the one-CTA coarse tail
     size_t tail_bytes = 0;
 };
@@ -1116,12 +1121,19 @@ bool an_coarse_inverse(const std::vector<unsigned char>& t, int n, double h, dou
     return true;
 }
 
+// kernels launched (or recorded into a step graph, counted at each replay)
+void an_count(helm_annulus* a, uint64_t n)
+{
+    if (a->capturing) a->captured += n;
+    else add_launches(n);
+}
+
 template <typename R>
 helm_status an_vcycle(helm_annulus* a, int l, bool zero)
 {
     typedef typename CX<R>::T c2;
     const auto& L = a->lev[l];
-    cudaStream_t s = a->stream;
+    cudaStream_t s = a->ls;
     if (l == a->t0) {                      // this level and all coarser ones in one CTA
         AnTail T{};
         T.L = (int)a->lev.size() - l;
@@ -1138,13 +1150,13 @@ helm_status an_vcycle(helm_annulus* a, int l, bool zero)
         }
         k_an_tail<R><<<1, 1024, a->tail_bytes, s>>>((c2*)L.e, (const c2*)L.rhs, T);
         AN_CK(cudaGetLastError());
-        add_launches(1);
+        an_count(a, 1);
         return HELM_OK;
     }
     if (l + 1 == (int)a->lev.size()) {
         k_an_coarse<R><<<1, AN_NT, 0, s>>>((const c2*)L.rhs, (c2*)L.e, a->Ainv, a->map, a->m);
         AN_CK(cudaGetLastError());
-        add_launches(1);
+        an_count(a, 1);
         return HELM_OK;
     }
     const R h = (R)L.h, dinv = (R)(1.0 / (4.0 + a->sigma * L.h * L.h));
@@ -1160,18 +1172,18 @@ helm_status an_vcycle(helm_annulus* a, int l, bool zero)
         k_an_down<R><<<ntc * ntc, AN_NT, an_win_bytes<R>(an_down_sw(a->nu1)), s>>>(
             (const c2*)L.e, ew, (const c2*)L.rhs, L.typ, L.n, h, dinv, (R)a->sigma, a->nu1, zero ? 0 : 1, (c2*)C.rhs,
             (c2*)C.e, C.typ, C.n);
-        add_launches(1);
+        an_count(a, 1);
     } else {
         for (int sweep = 0; sweep < a->nu1; ++sweep)
             for (int col = 0; col < 2; ++col) {
                 k_an_rbgs<R><<<g, AN_NT, 0, s>>>((c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, dinv, col, 0, L.n, 0,
                                                  L.n);
-                add_launches(1);
+                an_count(a, 1);
             }
         k_an_restrict<R><<<grid_for((long)(C.n + 1) * (C.n + 1)), AN_NT, 0, s>>>(
             (const c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, (R)a->sigma, (c2*)C.rhs, (c2*)C.e, C.typ, C.n,
             (zero && a->nu1 == 0) ? 1 : 0);
-        add_launches(1);
+        an_count(a, 1);
     }
     helm_status st = an_vcycle<R>(a, l + 1, true);
     if (st != HELM_OK) return st;
@@ -1182,18 +1194,18 @@ helm_status an_vcycle(helm_annulus* a, int l, bool zero)
     else
         k_an_band<R><<<1, 1024, 0, s>>>(ew, (const c2*)L.rhs, L.typ, L.n, h, dinv, L.b0, L.b1, L.lo, L.hi,
                                         AN_BAND_SWEEPS);
-    add_launches(2);
+    an_count(a, 2);
     if (tiles) {                           // nu2 = 0: the launch only moves e2 to e
         const int nt = (L.n + AN_FT) / AN_FT;
         k_an_up<R><<<nt * nt, AN_NT, an_win_bytes<R>(an_up_sw(a->nu2)), s>>>(ew, (c2*)L.e, (const c2*)L.rhs,
                                                                             L.typ, L.n, h, dinv, a->nu2);
-        add_launches(1);
+        an_count(a, 1);
     } else {
         for (int sweep = 0; sweep < a->nu2; ++sweep)
             for (int col = 0; col < 2; ++col) {
                 k_an_rbgs<R><<<g, AN_NT, 0, s>>>((c2*)L.e, (const c2*)L.rhs, L.typ, L.n, h, dinv, col, 0, L.n, 0,
                                                  L.n);
-                add_launches(1);
+                an_count(a, 1);
             }
     }
     AN_CK(cudaGetLastError());
@@ -1206,28 +1218,81 @@ helm_status an_solve(helm_annulus* a, const double2* data, double2* u, double to
 {
     typedef typename CX<R>::T c2;
     cudaStream_t s = a->stream;
+    a->ls = s;
     const auto& L0 = a->lev[0];
     const long total = (long)(a->N + 1) * (a->N + 1);
     double2* U[2] = {u, a->U1};
     k_an_init<<<grid_for(total), AN_NT, 0, s>>>(U[0], U[1], data, L0.typ, total);
     add_launches(1);
-    auto step = [&](int mode, int it) -> helm_status {
+    // mode 0: the start residual; mode 1: an outer step's update and residual; both end
+    // with the norm partials copied to the host (the caller synchronises)
+    auto enqueue = [&](int mode, int it) -> helm_status {
+        cudaStream_t q = a->ls;
         if (mode == 1) {
-            k_an_update<R><<<a->nblk, AN_NT, 0, s>>>(U[(it - 1) & 1], U[it & 1], (const c2*)L0.e, L0.typ, total,
+            for (int c = 0; c < a->cycles; ++c) {
+                if (c == 0) AN_CK(cudaMemsetAsync(L0.e, 0, total * sizeof(c2), q));
+                const helm_status st = an_vcycle<R>(a, 0, c == 0);
+                if (st != HELM_OK) return st;
+            }
+            k_an_update<R><<<a->nblk, AN_NT, 0, q>>>(U[(it - 1) & 1], U[it & 1], (const c2*)L0.e, L0.typ, total,
                                                      a->part);
-            add_launches(1);
+            an_count(a, 1);
         }
-        k_an_resid<R><<<a->nblk, AN_NT, 0, s>>>(U[mode == 1 ? (it & 1) : 0], data, L0.typ, (c2*)L0.rhs, a->N,
+        k_an_resid<R><<<a->nblk, AN_NT, 0, q>>>(U[mode == 1 ? (it & 1) : 0], data, L0.typ, (c2*)L0.rhs, a->N,
                                                 L0.h, a->k * a->k, a->k, a->part);
-        add_launches(1);
+        an_count(a, 1);
         AN_CK(cudaGetLastError());
-        AN_CK(cudaMemcpyAsync(a->h_part, a->part, 2 * sizeof(double) * a->nblk, cudaMemcpyDeviceToHost, s));
+        AN_CK(cudaMemcpyAsync(a->h_part, a->part, 2 * sizeof(double) * a->nblk, cudaMemcpyDeviceToHost, q));
+        return HELM_OK;
+    };
+    // an outer step of either parity as one graph (its pointers and parameters are fixed for
+    // this solve); without graphs the step's launches are issued one by one
+    cudaGraphExec_t gx[2] = {nullptr, nullptr};
+    uint64_t gn[2] = {0, 0};
+    auto drop_graphs = [&]() {
+        for (int p = 0; p < 2; ++p)
+            if (gx[p]) cudaGraphExecDestroy(gx[p]);
+    };
+    if (AN_GRAPHS && max_outer > 0) {
+        for (int p = 0; p < 2; ++p) {
+            cudaGraph_t gr = nullptr;
+            if (cudaStreamBeginCapture(a->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) break;
+            a->ls = a->cap;
+            a->capturing = true;
+            a->captured = 0;
+            const helm_status est = enqueue(1, p == 1 ? 1 : 2);
+            a->capturing = false;
+            a->ls = s;
+            const cudaError_t ce = cudaStreamEndCapture(a->cap, &gr);
+            if (est != HELM_OK || ce != cudaSuccess || !gr ||
+                cudaGraphInstantiate(&gx[p], gr, 0) != cudaSuccess) {
+                if (gr) cudaGraphDestroy(gr);
+                gx[p] = nullptr;
+                break;
+            }
+            cudaGraphDestroy(gr);
+            gn[p] = a->captured;
+        }
+        if (!gx[0] || !gx[1]) {                // no graphs: launch step by step
+            drop_graphs();
+            gx[0] = gx[1] = nullptr;
+            cudaGetLastError();
+        }
+    }
+    auto step = [&](int mode, int it) -> helm_status {
+        if (mode == 1 && gx[0]) {
+            AN_CK(cudaGraphLaunch(gx[it & 1], s));
+            add_launches(gn[it & 1]);
+        } else {
+            const helm_status st = enqueue(mode, it);
+            if (st != HELM_OK) return st;
+        }
         AN_CK(cudaStreamSynchronize(s));
         return HELM_OK;
     };
     // start: r_0 = b from U[0] (the hole data, zero elsewhere)
     helm_status st = step(0, 1);
-    if (st != HELM_OK) return st;
+    if (st != HELM_OK) { drop_graphs(); return st; }
     double r2 = 0.0;
     for (int b = 0; b < a->nblk; ++b) r2 += a->h_part[2 * b];
     const double norm0 = std::sqrt(r2);
@@ -1237,13 +1302,8 @@ helm_status an_solve(helm_annulus* a, const double2* data, double2* u, double to
     if (norm0 == 0.0 || !std::isfinite(norm0)) status = std::isfinite(norm0) ? HELM_CONVERGED : HELM_ENONFINITE;
     else {
         for (it = 1; it <= max_outer; ++it) {
-            for (int c = 0; c < a->cycles; ++c) {
-                if (c == 0) AN_CK(cudaMemsetAsync(L0.e, 0, total * sizeof(c2), s));
-                st = an_vcycle<R>(a, 0, c == 0);
-                if (st != HELM_OK) return st;
-            }
             st = step(1, it);
-            if (st != HELM_OK) return st;
+            if (st != HELM_OK) { drop_graphs(); return st; }
             r2 = 0.0;
             for (int b = 0; b < a->nblk; ++b) r2 += a->h_part[2 * b];
             const double rel = std::sqrt(r2) / norm0;
@@ -1259,6 +1319,7 @@ helm_status an_solve(helm_annulus* a, const double2* data, double2* u, double to
         }
         if (it > max_outer) it = max_outer;
     }
+    drop_graphs();
     // the result lives in U[it & 1]: the caller's buffer is U[0]
     if (it & 1) AN_CK(cudaMemcpyAsync(u, a->U1, total * sizeof(double2), cudaMemcpyDeviceToDevice, s));
     AN_CK(cudaStreamSynchronize(s));
@@ -1290,6 +1351,8 @@ helm_status helm_annulus_create(helm_annulus** out, int n, double side, double h
     // a blocking stream: its work is ordered after the caller's work on the legacy default
     // stream (where the inputs were written)
     if (cudaStreamCreate(&a->stream) != cudaSuccess) return fail(HELM_ECUDA);
+    if (cudaStreamCreateWithFlags(&a->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(HELM_ECUDA);
+    a->ls = a->stream;
     const size_t eb = prec == HELM_PREC_FP64 ? 16 : 8;
     for (int m = n; m >= AN_NC; m /= 2) {
         std::vector<unsigned char> t = an_types(m, side, hole);
@@ -1391,6 +1454,7 @@ helm_status helm_annulus_destroy(helm_annulus* a)
     if (a->Ainv) cudaFree(a->Ainv);
     if (a->h_part) cudaFreeHost(a->h_part);
     if (a->stream) cudaStreamDestroy(a->stream);
+    if (a->cap) cudaStreamDestroy(a->cap);
     delete a;
     return HELM_OK;
 }
