@@ -385,17 +385,99 @@ __device__ void an_stage(typename CX<R>::T* E, typename CX<R>::T* Rr, unsigned c
                          const unsigned char* __restrict__ typ, int n, bool load_e)
 {
     typedef typename CX<R>::T c2;
-    const int S = n + 1, ww = w.sx1 - w.sx0 + 1, cnt = ww * (w.sy1 - w.sy0 + 1);
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        const int ly = t / ww, lx = t % ww;
-        const int g = (w.sy0 + ly) * S + w.sx0 + lx, q = ly * w.SW + lx;
-        c2 z;
-        z.x = 0;
-        z.y = 0;
-        E[q] = load_e ? e[g] : z;
-        Rr[q] = rhs[g];
-        Ty[q] = typ[g];
+    const int S = n + 1, ww = w.sx1 - w.sx0 + 1, wh = w.sy1 - w.sy0 + 1;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    c2 z;
+    z.x = 0;
+    z.y = 0;
+    for (int ly = threadIdx.x >> 5; ly < wh; ly += nw)
+        for (int lx = lane; lx < ww; lx += 32) {
+            const int g = (w.sy0 + ly) * S + w.sx0 + lx, q = ly * w.SW + lx;
+            E[q] = load_e ? e[g] : z;
+            Rr[q] = rhs[g];
+            Ty[q] = typ[g];
+        }
+}
+
+// Red-black Gauss-Seidel on the nodes of colour `color` in row i, columns ux0..ux1, of
+// arrays with row stride SW whose element 0 is node (oy, ox); the warp's lanes take the
+// row's nodes of that colour.  PDE rows take the 5-point local solve, EDGE rows the mean
+// of their inward neighbours plus h rhs.
+template <typename R>
+__device__ __forceinline__ void an_row(typename CX<R>::T* E, const typename CX<R>::T* Rr, const unsigned char* Ty,
+                                       int SW, int oy, int ox, int i, int ux0, int ux1, int n, R h, R dinv,
+                                       int color)
+{
+    typedef typename CX<R>::T c2;
+    const R h2 = h * h;
+    const int jf = ux0 + ((i + ux0 + color) & 1);
+    for (int j = jf + 2 * (int)(threadIdx.x & 31); j <= ux1; j += 64) {
+        const int q = (i - oy) * SW + (j - ox);
+        const unsigned char ty = Ty[q];
+        if (ty == AN_PDE) {
+            const c2 sn = nbr_sum(E, q, SW);
+            const c2 r = Rr[q];
+            c2 v;
+            v.x = (sn.x - h2 * r.x) * dinv;
+            v.y = (sn.y - h2 * r.y) * dinv;
+            E[q] = v;
+        } else if (ty == AN_EDGE) {
+            const c2 m = inward_mean_w(E, q, SW, i, j, n);
+            const c2 r = Rr[q];
+            c2 v;
+            v.x = m.x + h * r.x;
+            v.y = m.y + h * r.y;
+            E[q] = v;
+        }
     }
+}
+
+// one half-sweep over rows uy0..uy1, a warp per row
+template <typename R>
+__device__ __forceinline__ void an_half(typename CX<R>::T* E, const typename CX<R>::T* Rr, const unsigned char* Ty,
+                                        int SW, int oy, int ox, int uy0, int uy1, int ux0, int ux1, int n, R h,
+                                        R dinv, int color)
+{
+    const int nw = blockDim.x >> 5;
+    for (int i = uy0 + (int)(threadIdx.x >> 5); i <= uy1; i += nw)
+        an_row<R>(E, Rr, Ty, SW, oy, ox, i, ux0, ux1, n, h, dinv, color);
+}
+
+// Full weighting of the residual at coarse PDE nodes, injection at EDGE nodes, zero on the
+// hole, for coarse rows CI0..CI1, columns CJ0..CJ1; Res holds the fine residual with row
+// stride RW, element 0 at fine node (roy, rox).  The coarse value goes to out(I, J).
+template <typename R, typename F>
+__device__ __forceinline__ void an_restrict_res(const typename CX<R>::T* Res, int RW, int roy, int rox,
+                                                const unsigned char* tc, int Sc, int CI0, int CI1, int CJ0, int CJ1,
+                                                F out)
+{
+    typedef typename CX<R>::T c2;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int I = CI0 + (threadIdx.x >> 5); I <= CI1; I += nw)
+        for (int J = CJ0 + lane; J <= CJ1; J += 32) {
+            const unsigned char ty = tc[I * Sc + J];
+            c2 v;
+            if (ty == AN_HOLE) {
+                v.x = 0;
+                v.y = 0;
+            } else if (ty == AN_EDGE) {
+                v = Res[(2 * I - roy) * RW + (2 * J - rox)];
+            } else {
+                R ax = 0, ay = 0;
+#pragma unroll
+                for (int a = -1; a <= 1; ++a)
+#pragma unroll
+                    for (int b = -1; b <= 1; ++b) {
+                        const R wgt = (R)((2 - (a < 0 ? -a : a)) * (2 - (b < 0 ? -b : b)));
+                        const c2 r = Res[(2 * I + a - roy) * RW + (2 * J + b - rox)];
+                        ax += wgt * r.x;
+                        ay += wgt * r.y;
+                    }
+                v.x = ax * (R)(1.0 / 16.0);
+                v.y = ay * (R)(1.0 / 16.0);
+            }
+            out(I, J, v);
+        }
 }
 
 // nu red-black sweeps on the window
@@ -403,46 +485,27 @@ template <typename R>
 __device__ void an_sweeps_w(typename CX<R>::T* E, const typename CX<R>::T* Rr, const unsigned char* Ty,
                             const AnWin& w, int n, R h, R dinv, int nu)
 {
-    typedef typename CX<R>::T c2;
-    const R h2 = h * h;
     for (int k = 0; k < 2 * nu; ++k) {
-        const int color = k & 1;
         const int ux0 = w.sx0 == 0 ? 0 : w.sx0 + k + 1, ux1 = w.sx1 == n ? n : w.sx1 - k - 1;
         const int uy0 = w.sy0 == 0 ? 0 : w.sy0 + k + 1, uy1 = w.sy1 == n ? n : w.sy1 - k - 1;
-        const int uw = ux1 - ux0 + 1, uh = uy1 - uy0 + 1;
-        const int cnt = (uw > 0 && uh > 0) ? uw * uh : 0;
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-            const int i = uy0 + t / uw, j = ux0 + t % uw;
-            if (((i + j) & 1) != color) continue;
-            const int q = (i - w.sy0) * w.SW + (j - w.sx0);
-            const unsigned char ty = Ty[q];
-            if (ty == AN_PDE) {
-                const c2 sn = nbr_sum(E, q, w.SW);
-                const c2 r = Rr[q];
-                c2 v;
-                v.x = (sn.x - h2 * r.x) * dinv;
-                v.y = (sn.y - h2 * r.y) * dinv;
-                E[q] = v;
-            } else if (ty == AN_EDGE) {
-                const c2 m = inward_mean_w(E, q, w.SW, i, j, n);
-                const c2 r = Rr[q];
-                c2 v;
-                v.x = m.x + h * r.x;
-                v.y = m.y + h * r.y;
-                E[q] = v;
-            }
-        }
+        an_half<R>(E, Rr, Ty, w.SW, w.sy0, w.sx0, uy0, uy1, ux0, ux1, n, h, dinv, k & 1);
         __syncthreads();
     }
 }
 
 template <typename R>
-size_t an_win_bytes(int SW)
+__host__ __device__ size_t an_win_bytes(int SW)
 {
     const size_t pts = (size_t)SW * SW;
     return 2 * an_a16(pts * sizeof(typename CX<R>::T)) + an_a16(pts);
 }
 __host__ __device__ constexpr int an_down_sw(int nu1) { return 2 * AN_CT + 3 + 4 * nu1; }
+constexpr int AN_RW = 2 * AN_CT + 1;  // fine residual rows / columns of a descent tile
+template <typename R>
+size_t an_down_bytes(int nu1)
+{
+    return an_win_bytes<R>(an_down_sw(nu1)) + an_a16((size_t)AN_RW * AN_RW * sizeof(typename CX<R>::T));
+}
 __host__ __device__ constexpr int an_up_sw(int nu2) { return AN_FT + 4 * nu2; }
 
 // Descent of one level: nu1 sweeps, then the coarse rhs (full weighting of the residual at
@@ -473,53 +536,35 @@ k_an_down(const typename CX<R>::T* __restrict__ e, typename CX<R>::T* __restrict
     c2* E = reinterpret_cast<c2*>(smem_raw);
     c2* Rr = reinterpret_cast<c2*>(smem_raw + an_a16(pts * sizeof(c2)));
     unsigned char* Ty = smem_raw + 2 * an_a16(pts * sizeof(c2));
+    c2* Res = reinterpret_cast<c2*>(smem_raw + an_win_bytes<R>(w.SW));
     an_stage<R>(E, Rr, Ty, w, e, rhs, typ, n, load_e != 0);
     __syncthreads();
     an_sweeps_w<R>(E, Rr, Ty, w, n, h, dinv, nu1);
     const bool zero = nu1 == 0 && load_e == 0;
     const int Sc = nc + 1, S = n + 1;
     const int ci1 = min(nc, I0 + AN_CT - 1), cj1 = min(nc, J0 + AN_CT - 1);
-    const int cw = cj1 - J0 + 1, ccnt = cw * (ci1 - I0 + 1);
-    for (int t = threadIdx.x; t < ccnt; t += blockDim.x) {
-        const int I = I0 + t / cw, J = J0 + t % cw;
-        const int qc = I * Sc + J;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // the fine residual once per node: rows / columns 2 I0 - 1 .. 2 ci1 + 1 (within the grid)
+    const int roy = 2 * I0 - 1, rox = 2 * J0 - 1;
+    {
+        const int ry0 = max(0, roy), ry1 = min(n, 2 * ci1 + 1), rx0 = max(0, rox), rx1 = min(n, 2 * cj1 + 1);
+        for (int i = ry0 + (threadIdx.x >> 5); i <= ry1; i += nw)
+            for (int j = rx0 + lane; j <= rx1; j += 32)
+                Res[(i - roy) * AN_RW + (j - rox)] =
+                    an_resid_w<R>(E, Rr, Ty, (i - w.sy0) * w.SW + (j - w.sx0), w.SW, i, j, n, h, sig, zero);
+    }
+    __syncthreads();
+    an_restrict_res<R>(Res, AN_RW, roy, rox, tc, Sc, I0, ci1, J0, cj1, [&](int I, int J, c2 v) {
         c2 z;
         z.x = 0;
         z.y = 0;
-        ec[qc] = z;
-        const unsigned char ty = tc[qc];
-        if (ty == AN_HOLE) {
-            rc[qc] = z;
-        } else if (ty == AN_EDGE) {
-            const int i = 2 * I, j = 2 * J;
-            rc[qc] = an_resid_w<R>(E, Rr, Ty, (i - w.sy0) * w.SW + (j - w.sx0), w.SW, i, j, n, h, sig, zero);
-        } else {
-            R ax = 0, ay = 0;
-#pragma unroll
-            for (int a = -1; a <= 1; ++a)
-#pragma unroll
-                for (int b = -1; b <= 1; ++b) {
-                    const R wgt = (R)((2 - (a < 0 ? -a : a)) * (2 - (b < 0 ? -b : b)));
-                    const int i = 2 * I + a, j = 2 * J + b;
-                    const c2 r = an_resid_w<R>(E, Rr, Ty, (i - w.sy0) * w.SW + (j - w.sx0), w.SW, i, j, n, h, sig,
-                                               zero);
-                    ax += wgt * r.x;
-                    ay += wgt * r.y;
-                }
-            c2 v;
-            v.x = ax * (R)(1.0 / 16.0);
-            v.y = ay * (R)(1.0 / 16.0);
-            rc[qc] = v;
-        }
-    }
+        ec[I * Sc + J] = z;
+        rc[I * Sc + J] = v;
+    });
     {
-        const int fi0 = 2 * I0, fi1 = min(n, 2 * I0 + 2 * AN_CT - 1);
-        const int fj0 = 2 * J0, fj1 = min(n, 2 * J0 + 2 * AN_CT - 1);
-        const int fw = fj1 - fj0 + 1, fcnt = fw * (fi1 - fi0 + 1);
-        for (int t = threadIdx.x; t < fcnt; t += blockDim.x) {
-            const int i = fi0 + t / fw, j = fj0 + t % fw;
-            e_out[i * S + j] = E[(i - w.sy0) * w.SW + (j - w.sx0)];
-        }
+        const int fi1 = min(n, 2 * I0 + 2 * AN_CT - 1), fj1 = min(n, 2 * J0 + 2 * AN_CT - 1);
+        for (int i = 2 * I0 + (threadIdx.x >> 5); i <= fi1; i += nw)
+            for (int j = 2 * J0 + lane; j <= fj1; j += 32) e_out[i * S + j] = E[(i - w.sy0) * w.SW + (j - w.sx0)];
     }
 }
 
@@ -549,13 +594,10 @@ k_an_up(const typename CX<R>::T* __restrict__ e, typename CX<R>::T* __restrict__
     an_stage<R>(E, Rr, Ty, w, e, rhs, typ, n, true);
     __syncthreads();
     an_sweeps_w<R>(E, Rr, Ty, w, n, h, dinv, nu2);
-    const int S = n + 1;
+    const int S = n + 1, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int fi1 = min(n, i0 + AN_FT - 1), fj1 = min(n, j0 + AN_FT - 1);
-    const int fw = fj1 - j0 + 1, fcnt = fw * (fi1 - i0 + 1);
-    for (int t = threadIdx.x; t < fcnt; t += blockDim.x) {
-        const int i = i0 + t / fw, j = j0 + t % fw;
-        e_out[i * S + j] = E[(i - w.sy0) * w.SW + (j - w.sx0)];
-    }
+    for (int i = i0 + (threadIdx.x >> 5); i <= fi1; i += nw)
+        for (int j = j0 + lane; j <= fj1; j += 32) e_out[i * S + j] = E[(i - w.sy0) * w.SW + (j - w.sx0)];
 }
 
 // coarse rhs: full weighting of the fine residual at PDE nodes, injection at EDGE nodes;
@@ -620,26 +662,42 @@ k_an_prolong(const typename CX<R>::T* __restrict__ ec, int nc, typename CX<R>::T
     }
 }
 
-// coarsest level: e = Ainv rhs over its m unknowns (map: unknown -> node), one CTA
+// coarsest level: e = Ainv rhs over its m unknowns (map: unknown -> node); a warp per row,
+// its lanes over the columns (coalesced rows of Ainv), partial sums added by a butterfly
 template <typename R>
-__global__ void __launch_bounds__(AN_NT)
-k_an_coarse(const typename CX<R>::T* __restrict__ rhs, typename CX<R>::T* __restrict__ e,
-            const double* __restrict__ Ainv, const int* __restrict__ map, int m)
+__device__ __forceinline__ void an_dense_solve(const typename CX<R>::T* rhs, typename CX<R>::T* e,
+                                               const double* __restrict__ Ainv, const int* __restrict__ map, int m)
 {
     typedef typename CX<R>::T c2;
-    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = threadIdx.x >> 5; r < m; r += nw) {
         double ax = 0.0, ay = 0.0;
-        for (int c = 0; c < m; ++c) {
+        for (int c = lane; c < m; c += 32) {
             const double a = Ainv[(size_t)r * m + c];
             const c2 v = rhs[map[c]];
             ax += a * (double)v.x;
             ay += a * (double)v.y;
         }
-        c2 o;
-        o.x = (R)ax;
-        o.y = (R)ay;
-        e[map[r]] = o;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        }
+        if (lane == 0) {
+            c2 v;
+            v.x = (R)ax;
+            v.y = (R)ay;
+            e[map[r]] = v;
+        }
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(AN_NT)
+k_an_coarse(const typename CX<R>::T* __restrict__ rhs, typename CX<R>::T* __restrict__ e,
+            const double* __restrict__ Ainv, const int* __restrict__ map, int m)
+{
+    an_dense_solve<R>(rhs, e, Ainv, map, m);
 }
 
 // ---------------------------------------------------------------------------
@@ -669,36 +727,7 @@ struct AnTail {
 
 
 template <typename R>
-__device__ void an_t_sweep(typename CX<R>::T* e, const typename CX<R>::T* rhs, const unsigned char* typ, int n, R h,
-                           R dinv, int color)
-{
-    typedef typename CX<R>::T c2;
-    const int S = n + 1;
-    const R h2 = h * h;
-    for (int q = threadIdx.x; q < S * S; q += blockDim.x) {
-        const int i = q / S, j = q % S;
-        if (((i + j) & 1) != color) continue;
-        const unsigned char ty = typ[q];
-        if (ty == AN_PDE) {
-            const c2 sn = nbr_sum(e, q, S);
-            const c2 r = rhs[q];
-            c2 v;
-            v.x = (sn.x - h2 * r.x) * dinv;
-            v.y = (sn.y - h2 * r.y) * dinv;
-            e[q] = v;
-        } else if (ty == AN_EDGE) {
-            const c2 mv = inward_mean(e, i, j, n);
-            const c2 r = rhs[q];
-            c2 v;
-            v.x = mv.x + h * r.x;
-            v.y = mv.y + h * r.y;
-            e[q] = v;
-        }
-    }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(1024, 1)
 k_an_tail(typename CX<R>::T* __restrict__ eg, const typename CX<R>::T* __restrict__ rg, AnTail T)
 {
     typedef typename CX<R>::T c2;
@@ -716,6 +745,8 @@ k_an_tail(typename CX<R>::T* __restrict__ eg, const typename CX<R>::T* __restric
         Ty[l] = smem_raw + off;
         off += an_a16(pts);
     }
+    c2* Res = reinterpret_cast<c2*>(smem_raw + off);     // the top level's residual, once per node
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int l = 0; l < T.L; ++l) {
         const int pts = (T.lev[l].n + 1) * (T.lev[l].n + 1);
         for (int q = threadIdx.x; q < pts; q += blockDim.x) Ty[l][q] = T.lev[l].typ[q];
@@ -736,109 +767,70 @@ k_an_tail(typename CX<R>::T* __restrict__ eg, const typename CX<R>::T* __restric
     for (int l = 0; l + 1 < T.L; ++l) {
         const AnTailLev& Lv = T.lev[l];
         const R h = (R)Lv.h, dinv = (R)Lv.dinv;
-        for (int sw = 0; sw < T.nu1; ++sw)
-            for (int col = 0; col < 2; ++col) {
-                an_t_sweep<R>(E[l], Rr[l], Ty[l], Lv.n, h, dinv, col);
-                __syncthreads();
-            }
+        const int n = Lv.n, S = n + 1;
+        for (int k = 0; k < 2 * T.nu1; ++k) {
+            an_half<R>(E[l], Rr[l], Ty[l], S, 0, 0, 0, n, 0, n, n, h, dinv, k & 1);
+            __syncthreads();
+        }
         const int nc = T.lev[l + 1].n, Sc = nc + 1;
         const bool zero = T.nu1 == 0 && (l > 0 || !T.load_e);
-        for (int q = threadIdx.x; q < Sc * Sc; q += blockDim.x) {
-            const int I = q / Sc, J = q % Sc;
+        for (int i = threadIdx.x >> 5; i <= n; i += nw)
+            for (int j = lane; j <= n; j += 32)
+                Res[i * S + j] = an_resid<R>(E[l], Rr[l], Ty[l], i, j, n, h, sig, zero);
+        __syncthreads();
+        c2* const Ec = E[l + 1];
+        c2* const Rc = Rr[l + 1];
+        an_restrict_res<R>(Res, S, 0, 0, Ty[l + 1], Sc, 0, nc, 0, nc, [&](int I, int J, c2 v) {
             c2 z;
             z.x = 0;
             z.y = 0;
-            E[l + 1][q] = z;
-            const unsigned char ty = Ty[l + 1][q];
-            if (ty == AN_HOLE) {
-                Rr[l + 1][q] = z;
-            } else if (ty == AN_EDGE) {
-                Rr[l + 1][q] = an_resid<R>(E[l], Rr[l], Ty[l], 2 * I, 2 * J, Lv.n, h, sig, zero);
-            } else {
-                R ax = 0, ay = 0;
-                for (int a = -1; a <= 1; ++a)
-                    for (int b = -1; b <= 1; ++b) {
-                        const R wgt = (R)((2 - (a < 0 ? -a : a)) * (2 - (b < 0 ? -b : b)));
-                        const c2 r = an_resid<R>(E[l], Rr[l], Ty[l], 2 * I + a, 2 * J + b, Lv.n, h, sig, zero);
-                        ax += wgt * r.x;
-                        ay += wgt * r.y;
-                    }
-                c2 v;
-                v.x = ax * (R)(1.0 / 16.0);
-                v.y = ay * (R)(1.0 / 16.0);
-                Rr[l + 1][q] = v;
-            }
-        }
+            Ec[I * Sc + J] = z;
+            Rc[I * Sc + J] = v;
+        });
         __syncthreads();
     }
     // the coarsest level, exactly
-    {
-        const int lc = T.L - 1;
-        for (int r = threadIdx.x; r < T.m; r += blockDim.x) {
-            double ax = 0.0, ay = 0.0;
-            for (int c = 0; c < T.m; ++c) {
-                const double a = T.Ainv[(size_t)r * T.m + c];
-                const c2 v = Rr[lc][T.map[c]];
-                ax += a * (double)v.x;
-                ay += a * (double)v.y;
-            }
-            c2 o;
-            o.x = (R)ax;
-            o.y = (R)ay;
-            E[lc][T.map[r]] = o;
-        }
-        __syncthreads();
-    }
+    an_dense_solve<R>(Rr[T.L - 1], E[T.L - 1], T.Ainv, T.map, T.m);
+    __syncthreads();
     // ascent
     for (int l = T.L - 2; l >= 0; --l) {
         const AnTailLev& Lv = T.lev[l];
         const int n = Lv.n, S = n + 1, nc = T.lev[l + 1].n, Sc = nc + 1;
         const R h = (R)Lv.h, dinv = (R)Lv.dinv;
-        for (int q = threadIdx.x; q < S * S; q += blockDim.x) {
-            if (Ty[l][q] == AN_HOLE) continue;
-            const int i = q / S, j = q % S;
-            const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1;
-            const c2 a = E[l + 1][I0 * Sc + J0], b = E[l + 1][I1 * Sc + J0];
-            const c2 c = E[l + 1][I0 * Sc + J1], d = E[l + 1][I1 * Sc + J1];
-            c2 v = E[l][q];
-            v.x += (R)0.25 * (((a.x + b.x) + c.x) + d.x);
-            v.y += (R)0.25 * (((a.y + b.y) + c.y) + d.y);
-            E[l][q] = v;
-        }
+        for (int i = threadIdx.x >> 5; i <= n; i += nw)
+            for (int j = lane; j <= n; j += 32) {
+                const int q = i * S + j;
+                if (Ty[l][q] == AN_HOLE) continue;
+                const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1;
+                const c2 a = E[l + 1][I0 * Sc + J0], b = E[l + 1][I1 * Sc + J0];
+                const c2 c = E[l + 1][I0 * Sc + J1], d = E[l + 1][I1 * Sc + J1];
+                c2 v = E[l][q];
+                v.x += (R)0.25 * (((a.x + b.x) + c.x) + d.x);
+                v.y += (R)0.25 * (((a.y + b.y) + c.y) + d.y);
+                E[l][q] = v;
+            }
         __syncthreads();
-        // band sweeps around the hole
+        // band sweeps around the hole: rows b0..b1 of the ring [b0, b1]^2 minus [lo, hi]^2
+        // (all PDE rows), a warp per row
         {
             const int b0 = Lv.b0, b1 = Lv.b1, lo = Lv.lo, hi = Lv.hi;
-            const int w = b1 - b0 + 1, th = lo - b0, bh = b1 - hi, hh = hi - lo + 1;
-            const int nA = th * w, nB = bh * w, nC = hh * th, nD = hh * bh;
-            const int total = nA + nB + nC + nD;
-            const R h2 = h * h;
-            for (int sw = 0; sw < 2 * AN_BAND_SWEEPS; ++sw) {
-                const int color = sw & 1;
-                for (int t = threadIdx.x; t < total; t += blockDim.x) {
-                    int i, j;
-                    if (t < nA) { i = b0 + t / w; j = b0 + t % w; }
-                    else if (t < nA + nB) { const int u = t - nA; i = hi + 1 + u / w; j = b0 + u % w; }
-                    else if (t < nA + nB + nC) { const int u = t - nA - nB; i = lo + u / th; j = b0 + u % th; }
-                    else { const int u = t - nA - nB - nC; i = lo + u / bh; j = hi + 1 + u % bh; }
-                    if (((i + j) & 1) != color) continue;
-                    const int q = i * S + j;
-                    if (Ty[l][q] != AN_PDE) continue;
-                    const c2 sn = nbr_sum(E[l], q, S);
-                    const c2 r = Rr[l][q];
-                    c2 v;
-                    v.x = (sn.x - h2 * r.x) * dinv;
-                    v.y = (sn.y - h2 * r.y) * dinv;
-                    E[l][q] = v;
+            for (int k = 0; k < 2 * AN_BAND_SWEEPS; ++k) {
+                const int color = k & 1;
+                for (int i = b0 + (threadIdx.x >> 5); i <= b1; i += nw) {
+                    if (i < lo || i > hi) {
+                        an_row<R>(E[l], Rr[l], Ty[l], S, 0, 0, i, b0, b1, n, h, dinv, color);
+                    } else {
+                        an_row<R>(E[l], Rr[l], Ty[l], S, 0, 0, i, b0, lo - 1, n, h, dinv, color);
+                        an_row<R>(E[l], Rr[l], Ty[l], S, 0, 0, i, hi + 1, b1, n, h, dinv, color);
+                    }
                 }
                 __syncthreads();
             }
         }
-        for (int sw = 0; sw < T.nu2; ++sw)
-            for (int col = 0; col < 2; ++col) {
-                an_t_sweep<R>(E[l], Rr[l], Ty[l], n, h, dinv, col);
-                __syncthreads();
-            }
+        for (int k = 0; k < 2 * T.nu2; ++k) {
+            an_half<R>(E[l], Rr[l], Ty[l], S, 0, 0, 0, n, 0, n, n, h, dinv, k & 1);
+            __syncthreads();
+        }
     }
     const int pts = (T.lev[0].n + 1) * (T.lev[0].n + 1);
     for (int q = threadIdx.x; q < pts; q += blockDim.x) eg[q] = E[0][q];
@@ -852,7 +844,7 @@ size_t an_tail_bytes(const int* ns, int L)
         const size_t pts = (size_t)(ns[l] + 1) * (ns[l] + 1);
         off += 2 * an_a16(pts * sizeof(typename CX<R>::T)) + an_a16(pts);
     }
-    return off;
+    return off + an_a16((size_t)(ns[0] + 1) * (ns[0] + 1) * sizeof(typename CX<R>::T));
 }
 
 // U := the hole data on hole nodes, 0 elsewhere (both iterate buffers)
@@ -1169,7 +1161,7 @@ helm_status an_vcycle(helm_annulus* a, int l, bool zero)
     c2* const ew = (c2*)(tiles ? L.e2 : L.e);
     if (tiles) {
         const int ntc = (C.n + AN_CT) / AN_CT;
-        k_an_down<R><<<ntc * ntc, AN_NT, an_win_bytes<R>(an_down_sw(a->nu1)), s>>>(
+        k_an_down<R><<<ntc * ntc, AN_NT, an_down_bytes<R>(a->nu1), s>>>(
             (const c2*)L.e, ew, (const c2*)L.rhs, L.typ, L.n, h, dinv, (R)a->sigma, a->nu1, zero ? 0 : 1, (c2*)C.rhs,
             (c2*)C.e, C.typ, C.n);
         an_count(a, 1);
@@ -1408,7 +1400,7 @@ helm_status helm_annulus_create(helm_annulus** out, int n, double side, double h
         a->t0 = -1;
     }
     {
-        const size_t dmax = (prec == HELM_PREC_FP64) ? an_win_bytes<double>(an_down_sw(8)) : an_win_bytes<float>(an_down_sw(8));
+        const size_t dmax = (prec == HELM_PREC_FP64) ? an_down_bytes<double>(8) : an_down_bytes<float>(8);
         const size_t umax = (prec == HELM_PREC_FP64) ? an_win_bytes<double>(an_up_sw(8)) : an_win_bytes<float>(an_up_sw(8));
         cudaError_t e1, e2;
         if (prec == HELM_PREC_FP64) {
