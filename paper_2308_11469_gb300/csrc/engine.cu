@@ -30,6 +30,10 @@ namespace {
 
 std::atomic<uint64_t> g_launches{0};
 thread_local char g_errbuf[256] = "";
+// engines launched on streams of decreasing priority by predicted work (else all equal)
+constexpr bool g_lane_priority = true;
+
+double lambda_min_of(int D, int n, double h);
 
 #define HELM_CK(call)                                                                     \
     do {                                                                                  \
@@ -669,6 +673,24 @@ struct Engine {
         return c;
     }
 
+    // the largest predicted work among the active instances: outer steps from the closed-form
+    // contraction rho = |alpha + i p| / (lambda_min + sigma) and the tolerance, times n^D
+    double longest_job() const
+    {
+        double w = 0.0;
+        for (auto* p : slots) {
+            if (!p) continue;
+            const InstDesc& d = p->d;
+            const double l = lambda_min_of(d.D, d.n, d.h);
+            const double rho = std::hypot(d.k2 + d.sigma, d.damp) / (l + d.sigma);
+            double steps = d.max_outer;
+            if (rho > 0.0 && rho < 1.0 && d.tol > 0.0 && d.tol < 1.0)
+                steps = std::min(steps, std::log(d.tol) / std::log(rho));
+            w = std::max(w, steps * std::pow((double)d.n, d.D));
+        }
+        return w;
+    }
+
     // Initial residual and norm of one newly started instance.
     helm_status start_instance(int slot, cudaStream_t s)
     {
@@ -814,9 +836,12 @@ struct helm_batch {
     int lanes = 4;
     cudaStream_t stream = nullptr;
     std::map<int, std::unique_ptr<Engine>> engines;   // key = (2 * D + prec) * HELM_MAX_LANES + lane
-    std::map<int, cudaStream_t> eng_streams;
+    // A step launches the engines on streams of decreasing priority, ordered by their
+    // longest predicted job, so the critical path's kernels are scheduled first and the
+    // shorter solves fill the SMs it leaves idle.
+    std::vector<cudaStream_t> rank_streams;
+    std::vector<cudaEvent_t> rank_join;
     cudaEvent_t fork = nullptr;
-    std::map<int, cudaEvent_t> join;
     struct Rec {
         int key = 0, slot = -1;
         int done = 0, status = 0, iters = 0;
@@ -1272,8 +1297,8 @@ helm_status helm_batch_destroy(helm_batch* b)
         }
     cudaStreamSynchronize(b->stream);
     b->engines.clear();
-    for (auto& kv : b->eng_streams) cudaStreamDestroy(kv.second);
-    for (auto& kv : b->join) cudaEventDestroy(kv.second);
+    for (cudaStream_t s : b->rank_streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->rank_join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     delete b;
     return HELM_OK;
@@ -1318,12 +1343,6 @@ static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, 
         ne->nu1 = b->nu1;
         ne->nu2 = b->nu2;
         ne->cycles = b->cycles;
-        cudaStream_t es;
-        HELM_CK(cudaStreamCreateWithFlags(&es, cudaStreamNonBlocking));
-        cudaEvent_t ev;
-        HELM_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        b->eng_streams[key] = es;
-        b->join[key] = ev;
         E = ne.get();
         b->engines[key] = std::move(ne);
     } else {
@@ -1445,16 +1464,49 @@ helm_status helm_batch_set_cycle(helm_batch* b, int nu1, int nu2, int cycles)
     return HELM_OK;
 }
 
+// the stream (and its join event) of launch rank r: priority decreasing with r down to
+// the device's lowest (created on first use)
+static helm_status rank_stream(helm_batch* b, int r, cudaStream_t* s, cudaEvent_t* e)
+{
+    while ((int)b->rank_streams.size() <= r) {
+        const int q = (int)b->rank_streams.size();
+        int least = 0, greatest = 0;
+        HELM_CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        // numerically smaller is higher priority
+        const int prio = g_lane_priority ? std::min(least, greatest + q) : least;
+        cudaStream_t ns;
+        HELM_CK(cudaStreamCreateWithPriority(&ns, cudaStreamNonBlocking, prio));
+        b->rank_streams.push_back(ns);
+        cudaEvent_t ev;
+        HELM_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        b->rank_join.push_back(ev);
+    }
+    *s = b->rank_streams[r];
+    *e = b->rank_join[r];
+    return HELM_OK;
+}
+
 helm_status helm_batch_step(helm_batch* b, int max_steps)
 {
     if (!b || max_steps < 0) return HELM_EINVAL;
-    // launch every engine with work on its own stream, forked from the batch stream
+    // launch every engine with work on its own stream, forked from the batch stream; the
+    // engine with the longest predicted job on the highest-priority stream
     HELM_CK(cudaEventRecord(b->fork, b->stream));
+    std::vector<std::pair<double, int>> order;
+    for (auto& kv : b->engines)
+        if (kv.second->active_count() > 0) order.push_back({kv.second->longest_job(), kv.first});
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first > y.first; });
     std::vector<int> launched;
-    for (auto& kv : b->engines) {
-        Engine* E = kv.second.get();
-        if (E->active_count() == 0) continue;
-        cudaStream_t es = b->eng_streams[kv.first];
+    for (size_t r = 0; r < order.size(); ++r) {
+        const int key = order[r].second;
+        Engine* E = b->engines[key].get();
+        cudaStream_t es;
+        cudaEvent_t ej;
+        {
+            const helm_status st = rank_stream(b, (int)r, &es, &ej);
+            if (st != HELM_OK) return st;
+        }
         HELM_CK(cudaStreamWaitEvent(es, b->fork, 0));
         helm_status st = E->prepare_plan();
         if (st != HELM_OK) return st;
@@ -1482,9 +1534,9 @@ helm_status helm_batch_step(helm_batch* b, int max_steps)
         HELM_CK(cudaMemcpyAsync(E->h_ctrl, E->d_ctrl, 3 * sizeof(int), cudaMemcpyDeviceToHost, es));
         HELM_CK(cudaMemcpyAsync(E->h_state, E->d_state, sizeof(InstState) * E->cap,
                                 cudaMemcpyDeviceToHost, es));
-        HELM_CK(cudaEventRecord(b->join[kv.first], es));
-        HELM_CK(cudaStreamWaitEvent(b->stream, b->join[kv.first], 0));
-        launched.push_back(kv.first);
+        HELM_CK(cudaEventRecord(ej, es));
+        HELM_CK(cudaStreamWaitEvent(b->stream, ej, 0));
+        launched.push_back(key);
     }
     HELM_CK(cudaStreamSynchronize(b->stream));
     for (int key : launched) {
