@@ -166,12 +166,14 @@ HELM_API helm_status helm_plan_coarse(const helm_plan* plan, int* tail_n, int* e
 HELM_API helm_status helm_plan_set_cycle(helm_plan* plan, int nu1, int nu2, int cycles);
 
 /* Autotuner: solves the given problem (f, g, starting iterate u, tol, max_outer as in
- * helm_solve) with each candidate inner schedule -- V(1,0), V(0,1), V(1,1), V(2,1),
- * V(1,2), V(2,2), V(3,3) with one cycle per outer step, V(1,1) with two -- times each
- * converged solve on the plan's stream (best of two after a warm-up run), keeps the
- * fastest in the plan and reports it (outputs may be NULL).  u is restored to the
- * starting iterate.  HELM_DIVERGED if no candidate converged (schedule unchanged).
- * Allocates one temporary copy of u. */
+ * helm_solve) with each candidate inner schedule -- V(1,0), V(0,1), V(0,2), V(0,3),
+ * V(1,1), V(2,1), V(1,2), V(2,2), V(3,3) with one cycle per outer step, V(1,1) with
+ * two -- times each converged solve on the plan's stream (best of two after a warm-up
+ * run), keeps the fastest in the plan and reports it (outputs may be NULL).  Every
+ * tuning solve starts from the given u, so a u that already solves the problem makes
+ * the timings meaningless: pass the starting iterate of the solves to be tuned (zeros
+ * for the paper's start).  u is restored to the starting iterate.  HELM_DIVERGED if no
+ * candidate converged (schedule unchanged).  Allocates one temporary copy of u. */
 HELM_API helm_status helm_plan_autotune(helm_plan* plan, const void* f, const void* g, void* u,
                                         double tol, int max_outer, int* nu1, int* nu2,
                                         int* cycles, double* best_ms);

@@ -1103,8 +1103,8 @@ helm_status helm_plan_autotune(helm_plan* p, const void* f, const void* g, void*
 {
     if (!p) return HELM_EINVAL;
     if (check_ptr(f) || check_ptr(g) || check_ptr(u)) return HELM_EINVAL;
-    static const int cand[][3] = {{1, 0, 1}, {0, 1, 1}, {1, 1, 1}, {2, 1, 1}, {1, 2, 1},
-                                  {2, 2, 1}, {3, 3, 1}, {1, 1, 2}};
+    static const int cand[][3] = {{1, 0, 1}, {0, 1, 1}, {0, 2, 1}, {0, 3, 1}, {1, 1, 1}, {2, 1, 1},
+                                  {1, 2, 1}, {2, 2, 1}, {3, 3, 1}, {1, 1, 2}};
     const size_t ub = p->padded() * 16;
     void* saved = nullptr;
     HELM_CK(cudaMallocAsync(&saved, ub, p->stream));

@@ -42,7 +42,6 @@ k_rbgs(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const LevelDesc L = insts[item.inst].lev[item.level];
     const int n = L.n, half = (n + 1) >> 1;
     const int rows = (D == 3) ? n * n : n;
-    const long total = (long)rows * half;
     c2* __restrict__ e = (c2*)L.e;
     const c2* __restrict__ r = (const c2*)lev_rhs(L, item.level, sv.it);
     const long P = L.pitch;
@@ -52,12 +51,12 @@ k_rbgs(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     // mode 2: the iterate of every level is zero; mode 1: only levels > 0 are (their
     // iterate was cleared by the restriction); mode 0: plain half-sweep.
     const bool zi = (mode == 2) || (mode == 1 && item.level > 0);
-    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
-         q += (long)gridDim.x * blockDim.x) {
-        const int j = (int)(q % half);
-        const int row = (int)(q / half);
-        const int y = (D == 3) ? row % n + 1 : row + 1;
-        const int z = (D == 3) ? row / n + 1 : 0;
+    // a warp per grid row (y, z), its lanes over the row's node pairs
+    const int wpb = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += gridDim.x * wpb) {
+      const int y = (D == 3) ? row % n + 1 : row + 1;
+      const int z = (D == 3) ? row / n + 1 : 0;
+      for (int j = lane; j < half; j += 32) {
         const int xa = 2 * j + 1;                       // pair {xa, xa + 1}
         const int xc = (((xa + y + z) & 1) == color) ? xa : xa + 1;
         const int xo = (xc == xa) ? xa + 1 : xa;
@@ -83,6 +82,7 @@ k_rbgs(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
             e[o] = v;
         }
         if (zi && xo <= n) e[off<D>(L, xo, y, z)] = cz<c2>();
+      }
     }
 }
 
@@ -106,7 +106,7 @@ k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const LevelDesc F = insts[item.inst].lev[item.level];
     const LevelDesc C = insts[item.inst].lev[item.level + 1];
     const int nc = C.n;
-    const long total = (D == 3) ? (long)nc * nc * nc : (long)nc * nc;
+    const int crows = (D == 3) ? nc * nc : nc;
     const c2* __restrict__ e = (const c2*)F.e;
     const c2* __restrict__ r = (const c2*)lev_rhs(F, item.level, sv.it);
     c2* __restrict__ cr = (c2*)C.rhs;
@@ -117,11 +117,12 @@ k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const R sig = (R)insts[item.inst].sigma;
     const R scale = (D == 3) ? (R)(1.0 / 64.0) : (R)(1.0 / 16.0);
     const bool ez = (mode == 2) || (mode == 1 && item.level > 0);
-    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
-         q += (long)gridDim.x * blockDim.x) {
-        const int X = (int)(q % nc) + 1;
-        const int Y = (int)((q / nc) % nc) + 1;
-        const int Z = (D == 3) ? (int)(q / ((long)nc * nc)) + 1 : 0;
+    // a warp per coarse row (Y, Z), its lanes over X
+    const int wpb = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < crows; row += gridDim.x * wpb) {
+      const int Y = (D == 3) ? row % nc + 1 : row + 1;
+      const int Z = (D == 3) ? row / nc + 1 : 0;
+      for (int X = lane + 1; X <= nc; X += 32) {
         R ax = 0, ay = 0;
         const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
         if (ez) {
@@ -171,6 +172,7 @@ k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
         v.y = ay * scale;
         cr[oc] = v;
         ce[oc] = cz<c2>();
+      }
     }
 }
 
@@ -192,15 +194,16 @@ k_prolong(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const LevelDesc F = insts[item.inst].lev[item.level];
     const LevelDesc C = insts[item.inst].lev[item.level + 1];
     const int n = F.n;
-    const long total = (D == 3) ? (long)n * n * n : (long)n * n;
+    const int rows = (D == 3) ? n * n : n;
     c2* __restrict__ e = (c2*)F.e;
     const c2* __restrict__ ce = (const c2*)C.e;
     const bool ez = (mode == 2) || (mode == 1 && item.level > 0);
-    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
-         q += (long)gridDim.x * blockDim.x) {
-        const int x = (int)(q % n) + 1;
-        const int y = (int)((q / n) % n) + 1;
-        const int z = (D == 3) ? (int)(q / ((long)n * n)) + 1 : 0;
+    // a warp per fine row (y, z), its lanes over x
+    const int wpb = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += gridDim.x * wpb) {
+      const int y = (D == 3) ? row % n + 1 : row + 1;
+      const int z = (D == 3) ? row / n + 1 : 0;
+      for (int x = lane + 1; x <= n; x += 32) {
         // per axis: even fine index -> one coarse node (weight 1), odd -> two (1/2 each)
         const int x0 = x >> 1, x1 = (x + 1) >> 1;
         const int y0 = y >> 1, y1 = (y + 1) >> 1;
@@ -233,6 +236,7 @@ k_prolong(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
             v.y += w * vy;
         }
         e[o] = v;
+      }
     }
 }
 

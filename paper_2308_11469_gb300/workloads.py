@@ -80,6 +80,7 @@ def cube255(dev):
     u = torch.zeros_like(g)
     for prec, name in ((B.HELM_PREC_MIXED, "mixed"), (B.HELM_PREC_FP64, "fp64")):
         plan = B.helm_plan_create(3, p.n, p.h, p.k, prec=prec)
+        u.zero_()                      # the tuning solves start from u: the paper's zero start
         sched = B.helm_plan_autotune(plan, f, g, u, 1e-8, 2000)
 
         def run():
@@ -188,6 +189,7 @@ def damped1023(dev):
         lam = B.helm_plan_info(plan)[0]
         for alpha in sorted({q.k ** 2, max(q.k ** 2, p * p / (lam - q.k ** 2))}):
             B.helm_plan_set_cavity(plan, alpha, p)
+            u.zero_()
             sched = B.helm_plan_autotune(plan, f, g, u, 1e-8, 3000)
 
             def run():
