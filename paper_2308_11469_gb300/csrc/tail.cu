@@ -53,6 +53,17 @@ constexpr int YTAB_FLOATS = YN * YP + YP;
 constexpr int YSCR_FLOATS = YTAB_FLOATS + 2 * 2 * YV;
 __device__ float g_ytab[YTAB_FLOATS];
 
+// Exact 2D solve of the n = 15 level in FP64 (the plain FP64 form): the same sine-basis
+// formula with 15 x 15 products, a thread per output.  Table: S[15][16] (S_ab =
+// sin(pi a b / 16)), then s[16] (s_a = sin^2(pi a / 32)); scratch: two 15 x 16 complex
+// buffers.  (A 31 x 31 exact level in FP64 would cost ~60 us per cycle at one SM's FP64
+// rate; at 15 it is ~7 us.)
+constexpr int ZN = 15;
+constexpr int ZP = 16;
+constexpr int ZTAB_DOUBLES = ZN * ZP + ZP;
+constexpr int ZSCR_DOUBLES = ZTAB_DOUBLES + 2 * 2 * ZN * ZP;
+__device__ double g_ztab[ZTAB_DOUBLES];
+
 template <int D, int N> struct Lv {
     static constexpr int S = N + 2;              // padded row length (odd)
     static constexpr int HE = (S + 1) / 2;       // even-x entries of a row, stored first
@@ -71,10 +82,10 @@ template <int D, int N> constexpr int tail_elems() {
     else return 2 * Lv<D, N>::SZ + tail_elems<D, (N - 1) / 2>();
 }
 
-// the level each complex64 tail solves exactly (2D: 31, 3D: 15; none in FP64)
+// the level each tail solves exactly (complex64: 2D 31, 3D 15; FP64: 2D 15, none in 3D)
 template <int D, typename R> constexpr int exact_n()
 {
-    return std::is_same<R, float>::value ? (D == 2 ? XN : YN) : 0;
+    return std::is_same<R, float>::value ? (D == 2 ? XN : YN) : (D == 2 ? ZN : 0);
 }
 
 // does a tail with top size N0 contain its exactly solved level?
@@ -86,7 +97,9 @@ template <int D, typename R, int N0> constexpr bool tail_exact()
 template <int D, typename R, int N0> constexpr size_t tail_bytes()
 {
     return (size_t)tail_elems<D, N0>() * sizeof(typename C2<R>::T) +
-           (tail_exact<D, R, N0>() ? (size_t)(D == 2 ? XSCR_FLOATS : YSCR_FLOATS) * sizeof(float) : 0);
+           (!tail_exact<D, R, N0>() ? 0
+            : std::is_same<R, double>::value ? (size_t)ZSCR_DOUBLES * sizeof(double)
+                                               : (size_t)(D == 2 ? XSCR_FLOATS : YSCR_FLOATS) * sizeof(float));
 }
 
 template <int NWARPS> __device__ __forceinline__ void tsync() {
@@ -410,6 +423,67 @@ __device__ __forceinline__ void y_solve(float2* E, const float2* Rr, float* scr,
     __syncthreads();
 }
 
+// E (level array of n = 15, 2D, FP64) <- exact solution of (Delta_h - sigma) e = Rr with zero
+// walls: e = c S (W o (S r S)) S, c = -h^2 / (n+1)^2, W_ab = 1 / (s_a + s_b + sigma h^2 / 4)
+__device__ __forceinline__ void z_solve(double2* E, const double2* Rr, const double* scr, double h, double sigma)
+{
+    const double* Sm = scr;
+    const double* sv = scr + ZN * ZP;
+    double2* T1 = reinterpret_cast<double2*>(const_cast<double*>(scr) + ZTAB_DOUBLES);
+    double2* T2 = T1 + ZN * ZP;
+    const double c = -(h * h) / (double)((ZN + 1) * (ZN + 1));
+    const double tau = 0.25 * sigma * h * h;
+    const int t = threadIdx.x;
+    const bool act = t < ZN * ZN;
+    const int a = t / ZN, b = t % ZN;
+    auto at = [](int y, int x) { return (y + 1) * (ZN + 2) + ix<ZN>(x + 1); };
+    if (act) {                                   // T1[a][b] = sum_y S[a][y] r[y][b]
+        double ax = 0.0, ay = 0.0;
+        for (int y = 0; y < ZN; ++y) {
+            const double s = Sm[a * ZP + y];
+            const double2 v = Rr[at(y, b)];
+            ax = fma(s, v.x, ax);
+            ay = fma(s, v.y, ay);
+        }
+        T1[a * ZP + b] = make_double2(ax, ay);
+    }
+    __syncthreads();
+    if (act) {                                   // T2[a][b] = c W_ab sum_x T1[a][x] S[x][b]
+        double ax = 0.0, ay = 0.0;
+        for (int x = 0; x < ZN; ++x) {
+            const double s = Sm[x * ZP + b];
+            const double2 v = T1[a * ZP + x];
+            ax = fma(v.x, s, ax);
+            ay = fma(v.y, s, ay);
+        }
+        const double w = c / (sv[a] + sv[b] + tau);
+        T2[a * ZP + b] = make_double2(w * ax, w * ay);
+    }
+    __syncthreads();
+    if (act) {                                   // T1[a][b] = sum_y S[a][y] T2[y][b]
+        double ax = 0.0, ay = 0.0;
+        for (int y = 0; y < ZN; ++y) {
+            const double s = Sm[a * ZP + y];
+            const double2 v = T2[y * ZP + b];
+            ax = fma(s, v.x, ax);
+            ay = fma(s, v.y, ay);
+        }
+        T1[a * ZP + b] = make_double2(ax, ay);
+    }
+    __syncthreads();
+    if (act) {                                   // E[a][b] = sum_x T1[a][x] S[x][b]
+        double ax = 0.0, ay = 0.0;
+        for (int x = 0; x < ZN; ++x) {
+            const double s = Sm[x * ZP + b];
+            const double2 v = T1[a * ZP + x];
+            ax = fma(v.x, s, ax);
+            ay = fma(v.y, s, ay);
+        }
+        E[at(a, b)] = make_double2(ax, ay);
+    }
+    __syncthreads();
+}
+
 // One V(nu1, nu2)-cycle on the level of size N held at `base` (iterate, then rhs).
 // ez: the iterate is zero on entry (a coarse level, or a top level started from zero).
 // lv: this level's descriptor (its dinv); the next coarser level's follows it.
@@ -425,6 +499,9 @@ __device__ void t_vcycle(typename C2<R>::T* base, R h, R sig, const LevelDesc* l
         return;
     } else if constexpr (D == 3 && std::is_same<R, float>::value && N == YN && NWARPS == TNT / 32) {
         y_solve(E, Rr, xscr, (float)h, (float)sig);
+        return;
+    } else if constexpr (D == 2 && std::is_same<R, double>::value && N == ZN && NWARPS == TNT / 32) {
+        z_solve(E, Rr, reinterpret_cast<const double*>(xscr), (double)h, (double)sig);
         return;
     } else if constexpr (N == 1) {
         if (threadIdx.x == 0) {
@@ -520,9 +597,15 @@ k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     if constexpr (tail_exact<D, R, N0>()) {
         // sine tables of the exact level (host-computed)
         xscr = reinterpret_cast<float*>(base + TOT);
-        constexpr int NT4 = (D == 2 ? XTAB_FLOATS : YTAB_FLOATS) / 4;
-        const float4* tab = reinterpret_cast<const float4*>(D == 2 ? g_xtab : g_ytab);
-        for (int i = threadIdx.x; i < NT4; i += TNT) reinterpret_cast<float4*>(xscr)[i] = tab[i];
+        if constexpr (std::is_same<R, double>::value) {
+            constexpr int NT2 = ZTAB_DOUBLES / 2;
+            const double2* tab = reinterpret_cast<const double2*>(g_ztab);
+            for (int i = threadIdx.x; i < NT2; i += TNT) reinterpret_cast<double2*>(xscr)[i] = tab[i];
+        } else {
+            constexpr int NT4 = (D == 2 ? XTAB_FLOATS : YTAB_FLOATS) / 4;
+            const float4* tab = reinterpret_cast<const float4*>(D == 2 ? g_xtab : g_ytab);
+            for (int i = threadIdx.x; i < NT4; i += TNT) reinterpret_cast<float4*>(xscr)[i] = tab[i];
+        }
     }
     t_clear<D, R, N0>(base);
     __syncthreads();
@@ -631,11 +714,13 @@ size_t tail_smem_bytes(int D, int prec, int n)
         size_t s = (size_t)(m + 2);
         tot += 2 * ((D == 3) ? s * s * s : s * s);
     }
-    return tot * elem + (size_t)(tail_exact_n(D, prec) && n >= tail_exact_n(D, prec)
-                                     ? (D == 2 ? XSCR_FLOATS : YSCR_FLOATS) * sizeof(float) : 0);
+    const bool ex = tail_exact_n(D, prec) && n >= tail_exact_n(D, prec);
+    return tot * elem + (!ex ? 0
+                         : prec == 0 ? (size_t)ZSCR_DOUBLES * sizeof(double)
+                                     : (size_t)(D == 2 ? XSCR_FLOATS : YSCR_FLOATS) * sizeof(float));
 }
 
-int tail_exact_n(int D, int prec) { return prec == 0 ? 0 : (D == 2 ? XN : YN); }
+int tail_exact_n(int D, int prec) { return prec == 0 ? (D == 2 ? ZN : 0) : (D == 2 ? XN : YN); }
 
 cudaError_t setup_tail(int D, int prec)
 {
@@ -656,6 +741,18 @@ cudaError_t setup_tail(int D, int prec)
             tab[2 * XN * XP + i] = i < XN ? (float)(si * si) : 0.f;
         }
         const cudaError_t e = cudaMemcpyToSymbol(g_xtab, tab, sizeof tab);
+        if (e != cudaSuccess) return e;
+    }
+    if (D == 2 && prec == 0) {
+        static double tab[ZTAB_DOUBLES];
+        const double pi = 3.14159265358979323846;
+        for (int i = 0; i < ZN; ++i)
+            for (int j = 0; j < ZP; ++j) tab[i * ZP + j] = j < ZN ? std::sin(pi * (i + 1) * (j + 1) / (ZN + 1)) : 0.0;
+        for (int i = 0; i < ZP; ++i) {
+            const double si = std::sin(pi * (i + 1) / (2.0 * (ZN + 1)));
+            tab[ZN * ZP + i] = i < ZN ? si * si : 0.0;
+        }
+        const cudaError_t e = cudaMemcpyToSymbol(g_ztab, tab, sizeof tab);
         if (e != cudaSuccess) return e;
     }
     if (D == 3 && prec != 0) {

@@ -76,7 +76,8 @@ def test_vcycle_elementwise(B, D, n, prec, nus):
 
 
 @pytest.mark.parametrize("D,n,prec,want", [
-    (2, 1023, 1, (63, 31)), (2, 1023, 0, (31, 0)), (2, 31, 1, (31, 31)), (2, 15, 1, (15, 0)),
+    (2, 1023, 1, (63, 31)), (2, 1023, 0, (31, 15)), (2, 31, 1, (31, 31)), (2, 15, 1, (15, 0)),
+    (2, 15, 0, (15, 15)), (2, 7, 0, (7, 0)),
     (3, 255, 1, (15, 15)), (3, 255, 0, (7, 0)), (3, 15, 1, (15, 15)), (3, 7, 1, (7, 0))])
 def test_plan_coarse_hierarchy(B, D, n, prec, want):
     plan = B.helm_plan_create(D, n, 1.0 / (n + 1), 1.0, prec=prec)
