@@ -75,6 +75,14 @@ def test_vcycle_elementwise(B, D, n, prec, nus):
     assert np.max(np.abs(got - expect)) <= tol * scale
 
 
+@pytest.mark.parametrize("n", [127, 255])
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nus", [(5, 5), (6, 1)])
+def test_vcycle_elementwise_generic_2d(B, n, prec, nus):
+    # more than four sweeps per side: the 2D levels run on the generic per-sweep kernels
+    test_vcycle_elementwise(B, 2, n, prec, nus)
+
+
 @pytest.mark.parametrize("D,n,prec,want", [
     (2, 1023, 1, (63, 31)), (2, 1023, 0, (31, 15)), (2, 31, 1, (31, 31)), (2, 15, 1, (15, 0)),
     (2, 15, 0, (15, 15)), (2, 7, 0, (7, 0)),
