@@ -258,8 +258,11 @@ def main():
     def mixed_step(Fs=F, Gs=G, Us=U):
         for u in Us:
             u.zero_()
-        tickets = [B.helm_batch_submit(batch, mixed_plans[i], Fs[i], Gs[i], Us[i], TOL, MAX_OUTER)
-                   for i in range(len(KS))]
+        # longest predicted solve first (rho grows with k): the batch spreads its lanes
+        # longest-job-first
+        tickets = [None] * len(KS)
+        for i in sorted(range(len(KS)), key=lambda j: -KS[j]):
+            tickets[i] = B.helm_batch_submit(batch, mixed_plans[i], Fs[i], Gs[i], Us[i], TOL, MAX_OUTER)
         B.helm_batch_step(batch, 0)
         out = [B.helm_batch_poll(batch, t, MAX_OUTER) for t in tickets]
         return out

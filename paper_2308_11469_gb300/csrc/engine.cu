@@ -35,6 +35,17 @@ constexpr bool g_lane_priority = true;
 
 double lambda_min_of(int D, int n, double h);
 
+// Predicted work of a solve: its outer steps from the closed-form contraction
+// rho = |alpha + i p| / (lambda_min + sigma) (alpha = k^2 + sigma) and the tolerance, times n^D
+double predicted_work(int D, int n, double h, double k2, double sigma, double damp, double tol, int max_outer)
+{
+    const double l = lambda_min_of(D, n, h);
+    const double rho = std::hypot(k2 + sigma, damp) / (l + sigma);
+    double steps = max_outer;
+    if (rho > 0.0 && rho < 1.0 && tol > 0.0 && tol < 1.0) steps = std::min(steps, std::log(tol) / std::log(rho));
+    return steps * std::pow((double)n, D);
+}
+
 #define HELM_CK(call)                                                                     \
     do {                                                                                  \
         cudaError_t _e = (call);                                                          \
@@ -673,21 +684,21 @@ struct Engine {
         return c;
     }
 
-    // the largest predicted work among the active instances: outer steps from the closed-form
-    // contraction rho = |alpha + i p| / (lambda_min + sigma) and the tolerance, times n^D
+    // the largest / the total predicted work of the active instances
     double longest_job() const
     {
         double w = 0.0;
-        for (auto* p : slots) {
-            if (!p) continue;
-            const InstDesc& d = p->d;
-            const double l = lambda_min_of(d.D, d.n, d.h);
-            const double rho = std::hypot(d.k2 + d.sigma, d.damp) / (l + d.sigma);
-            double steps = d.max_outer;
-            if (rho > 0.0 && rho < 1.0 && d.tol > 0.0 && d.tol < 1.0)
-                steps = std::min(steps, std::log(d.tol) / std::log(rho));
-            w = std::max(w, steps * std::pow((double)d.n, d.D));
-        }
+        for (auto* p : slots)
+            if (p) w = std::max(w, predicted_work(p->d.D, p->d.n, p->d.h, p->d.k2, p->d.sigma, p->d.damp, p->d.tol,
+                                                   p->d.max_outer));
+        return w;
+    }
+    double total_work() const
+    {
+        double w = 0.0;
+        for (auto* p : slots)
+            if (p) w += predicted_work(p->d.D, p->d.n, p->d.h, p->d.k2, p->d.sigma, p->d.damp, p->d.tol,
+                                       p->d.max_outer);
         return w;
     }
 
@@ -1323,15 +1334,17 @@ static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, 
     const size_t need = layout(probe, D, n, h, k, prec, nullptr) +
                         (2 * (size_t)max_outer + 1) * sizeof(double);
     if (b->cap_bytes && b->used + need > b->cap_bytes) return HELM_ENOMEM;
-    // the lane of this class with the fewest solves in it
+    // the lane of this class with the least predicted work in it (solves submitted longest
+    // first are then spread as longest-job-first: the longest alone, the rest balanced)
     int key = (2 * D + prec) * HELM_MAX_LANES;
     {
-        int best = INT_MAX;
+        double best = 0.0;
+        bool first = true;
         for (int lane = 0; lane < b->lanes; ++lane) {
-            const int k = (2 * D + prec) * HELM_MAX_LANES + lane;
-            auto e = b->engines.find(k);
-            const int a = (e == b->engines.end()) ? 0 : e->second->active_count();
-            if (a < best) { best = a; key = k; }
+            const int k2 = (2 * D + prec) * HELM_MAX_LANES + lane;
+            auto e = b->engines.find(k2);
+            const double w = (e == b->engines.end()) ? 0.0 : e->second->total_work();
+            if (first || w < best) { best = w; key = k2; first = false; }
         }
     }
     Engine* E = nullptr;
