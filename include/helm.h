@@ -275,6 +275,14 @@ HELM_API helm_status helm_batch_set_cycle(helm_batch* batch, int nu1, int nu2, i
  * (The lane split is a scheduling choice of this library; the paper has no counterpart.) */
 #define HELM_MAX_LANES 4
 HELM_API helm_status helm_batch_set_lanes(helm_batch* batch, int lanes);
+/* Also copy a submitted solve's result to host memory: host_u receives the padded u
+ * ((n+2)^D complex128, the layout of the device u) once the solve has finished, before
+ * helm_batch_poll reports it done.  When a helm_batch_step runs its lanes to completion
+ * (max_steps = 0) the copy is queued on the solve's lane right behind its last step, so it
+ * overlaps the lanes still running; otherwise it is made when the solve retires.  host_u
+ * must stay valid until then; page-locked memory makes the copy asynchronous.  HELM_EINVAL
+ * for an unknown or finished ticket, or a device pointer. */
+HELM_API helm_status helm_batch_set_host_result(helm_batch* batch, uint64_t ticket, void* host_u);
 HELM_API helm_status helm_batch_poll(helm_batch* batch, uint64_t ticket, int* done, int* status,
                             int* iters, double* res_hist);
 /*

@@ -78,6 +78,7 @@ _SIGS = {
     "helm_batch_poll": (C.c_int, [_vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "helm_batch_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_size_t)]),
+    "helm_batch_set_host_result": (C.c_int, [_vp, C.c_uint64, _vp]),
     "helm_batch_profile": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_uint64), C.POINTER(C.c_double),
                                      C.POINTER(C.c_double), C.c_int]),
 }
@@ -448,6 +449,16 @@ def helm_batch_poll(batch: _Batch, ticket: int, max_outer: int):
     if not done.value:
         return None
     return status.value, iters.value, hist[: iters.value + 1].copy()
+
+
+def helm_batch_set_host_result(batch: _Batch, ticket: int, u_host) -> None:
+    """Also copy the solve's result (padded complex128, the device u's layout) into the
+    contiguous host tensor u_host (pinned for an asynchronous copy) once it finishes."""
+    import torch
+    if u_host.device.type != "cpu" or not u_host.is_contiguous() or u_host.dtype != torch.complex128:
+        raise ValueError("u_host: a contiguous complex128 CPU tensor")
+    _check(load().helm_batch_set_host_result(batch.handle, C.c_uint64(ticket), C.c_void_p(u_host.data_ptr())),
+           "helm_batch_set_host_result")
 
 
 def helm_batch_info(batch: _Batch):

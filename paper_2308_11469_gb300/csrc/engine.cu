@@ -860,6 +860,8 @@ struct helm_batch {
         void* u = nullptr;
         size_t ubytes = 0;
         std::vector<double> hist;
+        void* host_u = nullptr;         // helm_batch_set_host_result: the result's host copy
+        bool host_sent = false;         // its copy was queued behind the lane's last step
     };
     std::map<uint64_t, Rec> recs;
     uint64_t next = 1;
@@ -1421,8 +1423,10 @@ static helm_status retire_finished(helm_batch* b)
         Engine* E = b->engines[r.key].get();
         const InstState s = E->h_state[r.slot];
         if (s.status == HELM_ST_ACTIVE || s.status == HELM_ST_IDLE) continue;
-        if (s.it & 1)
+        if ((s.it & 1) && !r.host_sent)
             HELM_CK(cudaMemcpyAsync(r.u, r.inst->d.u[1], r.ubytes, cudaMemcpyDeviceToDevice, b->stream));
+        if (r.host_u && !r.host_sent)
+            HELM_CK(cudaMemcpyAsync(r.host_u, r.u, r.ubytes, cudaMemcpyDeviceToHost, b->stream));
         r.hist.resize(s.it + 1);
         HELM_CK(cudaMemcpyAsync(r.hist.data(), r.inst->d.hist, (s.it + 1) * sizeof(double),
                                 cudaMemcpyDeviceToHost, b->stream));
@@ -1475,6 +1479,15 @@ helm_status helm_batch_set_cycle(helm_batch* b, int nu1, int nu2, int cycles)
         kv.second->plan_sig.clear();
     }
     return HELM_OK;
+}
+
+// the caller's u := the final iterate when it lives in the library's buffer (odd step count)
+__global__ void k_final_u(const InstState* __restrict__ st, double2* __restrict__ u0,
+                          const double2* __restrict__ u1, long count)
+{
+    if (!(st->it & 1)) return;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x)
+        u0[i] = u1[i];
 }
 
 // the stream (and its join event) of launch rank r: priority decreasing with r down to
@@ -1544,6 +1557,19 @@ helm_status helm_batch_step(helm_batch* b, int max_steps)
         } else {
             HELM_CK(cudaGraphLaunch(E->exec, es));
         }
+        // a run to completion ends every solve of the lane: their host copies go out on the
+        // lane's stream now, beside the lanes still running
+        if (max_steps == 0)
+            for (auto& kr : b->recs) {
+                helm_batch::Rec& r = kr.second;
+                if (r.key != key || r.done || !r.inst || !r.host_u || r.host_sent) continue;
+                const long count = (long)(r.ubytes / sizeof(double2));
+                k_final_u<<<(int)std::min<long>((count + 255) / 256, 1216), 256, 0, es>>>(
+                    E->d_state + r.slot, (double2*)r.u, r.inst->d.u[1], count);
+                HELM_CK(cudaGetLastError());
+                HELM_CK(cudaMemcpyAsync(r.host_u, r.u, r.ubytes, cudaMemcpyDeviceToHost, es));
+                r.host_sent = true;
+            }
         HELM_CK(cudaMemcpyAsync(E->h_ctrl, E->d_ctrl, 3 * sizeof(int), cudaMemcpyDeviceToHost, es));
         HELM_CK(cudaMemcpyAsync(E->h_state, E->d_state, sizeof(InstState) * E->cap,
                                 cudaMemcpyDeviceToHost, es));
@@ -1631,6 +1657,22 @@ helm_status helm_batch_poll(helm_batch* b, uint64_t ticket, int* done, int* stat
     if (iters) *iters = r.iters;
     if (res_hist) memcpy(res_hist, r.hist.data(), r.hist.size() * sizeof(double));
     b->recs.erase(it);
+    return HELM_OK;
+}
+
+helm_status helm_batch_set_host_result(helm_batch* b, uint64_t ticket, void* host_u)
+{
+    if (!b || !host_u) return HELM_EINVAL;
+    auto it = b->recs.find(ticket);
+    if (it == b->recs.end() || it->second.done) return HELM_EINVAL;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, host_u) != cudaSuccess || a.type == cudaMemoryTypeDevice ||
+        a.type == cudaMemoryTypeManaged) {
+        cudaGetLastError();
+        return HELM_EINVAL;
+    }
+    it->second.host_u = host_u;
+    it->second.host_sent = false;
     return HELM_OK;
 }
 

@@ -137,7 +137,7 @@ def solve_host_batch(batch, plans, f_host, g_host, u_host, f_dev, g_dev, u_dev, 
 
     plans[i], f_host[i], g_host[i] (pinned complex128 host tensors) describe problem i;
     f_dev[i], g_dev[i], u_dev[i] are its device buffers; the result is copied to
-    u_host[i] (pinned).  The batch must have been created on the current stream.  The
+    u_host[i] (pinned) by the batch as soon as that solve ends.  The batch must have been created on the current stream.  The
     solve whose plan has the largest spectral radius rho (closed form: the most outer
     steps) is uploaded first and started; the other uploads run on a second stream while
     it advances `lead_steps` outer steps; each joins once its data are on the device (the
@@ -156,6 +156,8 @@ def solve_host_batch(batch, plans, f_host, g_host, u_host, f_dev, g_dev, u_dev, 
     u_dev[first].zero_()
     tickets = {first: B.helm_batch_submit(batch, plans[first], f_dev[first], g_dev[first], u_dev[first],
                                           tol, max_outer)}
+    # each result goes to the host right behind its solve's last step, beside the others
+    B.helm_batch_set_host_result(batch, tickets[first], u_host[first])
     side.wait_stream(main)                 # device buffers free of the previous use
     ready = {}
     with torch.cuda.stream(side):
@@ -170,11 +172,11 @@ def solve_host_batch(batch, plans, f_host, g_host, u_host, f_dev, g_dev, u_dev, 
     for i in rest:
         main.wait_event(ready[i])
         tickets[i] = B.helm_batch_submit(batch, plans[i], f_dev[i], g_dev[i], u_dev[i], tol, max_outer)
+        B.helm_batch_set_host_result(batch, tickets[i], u_host[i])
     B.helm_batch_step(batch, 0)
     out = [None] * m
     for i, t in tickets.items():
         out[i] = B.helm_batch_poll(batch, t, max_outer)
-        u_host[i].copy_(u_dev[i], non_blocking=True)
     main.synchronize()
     return out
 

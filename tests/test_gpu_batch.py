@@ -170,3 +170,38 @@ def test_lanes_do_not_change_results(B):
         with pytest.raises(B.HelmError):
             B.helm_batch_set_lanes(batch, bad)
     B.helm_batch_destroy(batch)
+
+
+@pytest.mark.parametrize("chunk", [0, 5])
+def test_host_result_copy(B, chunk):
+    # the result also lands in host memory: behind the lane's last step when the step runs
+    # to completion (chunk 0), at retirement after bounded steps (chunk 5)
+    probs = [inputs.gaussian_cavity_2d(k, seed=2, n=127) for k in (1.0, 2.5, 4.0)]
+    batch = B.helm_batch_create(0)
+    F = [torch.from_numpy(p.f).to(DEV) for p in probs]
+    G = [torch.from_numpy(p.g).to(DEV) for p in probs]
+    U = [torch.zeros_like(g) for g in G]
+    UH = [torch.full(tuple(g.shape), complex(7.0, 7.0), dtype=torch.complex128).pin_memory() for g in G]
+    plans = [B.helm_plan_create(2, p.n, p.h, p.k, prec=1) for p in probs]
+    tickets = [B.helm_batch_submit(batch, plans[i], F[i], G[i], U[i], 1e-8, 2000) for i in range(3)]
+    for t, uh in zip(tickets, UH):
+        B.helm_batch_set_host_result(batch, t, uh)
+    with pytest.raises(B.HelmError):
+        B.helm_batch_set_host_result(batch, 10 ** 9, UH[0])          # unknown ticket
+    with pytest.raises(ValueError):
+        B.helm_batch_set_host_result(batch, tickets[0], U[0])       # a device tensor
+    res = [None] * 3
+    while any(r is None for r in res):
+        B.helm_batch_step(batch, chunk)
+        for i, t in enumerate(tickets):
+            if res[i] is None:
+                res[i] = B.helm_batch_poll(batch, t, 2000)
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        st, it, hist, u = _solo(B, p, 1, 1e-8, 2000)
+        assert res[i][0] == st == B.HELM_CONVERGED and res[i][1] == it
+        assert np.array_equal(UH[i].numpy(), u)
+        assert np.array_equal(U[i].cpu().numpy(), u)
+    B.helm_batch_destroy(batch)
+    for pl in plans:
+        B.helm_plan_destroy(pl)
