@@ -269,9 +269,12 @@ HELM_API helm_status helm_batch_step(helm_batch* batch, int max_steps);
 HELM_API helm_status helm_batch_set_cycle(helm_batch* batch, int nu1, int nu2, int cycles);
 /* Solves of one kernel class (dimension, precision) are spread over `lanes` (1 ..
  * HELM_MAX_LANES, default 4) independent launch streams: each submission joins the lane
- * with the fewest solves, and helm_batch_step runs the lanes' step graphs concurrently,
- * so one lane's FP64 residual overlaps another lane's coarse multigrid levels.  Applies
- * to later submissions; results do not depend on the lane.  HELM_EINVAL outside the range.
+ * with the least predicted work (outer steps from the closed-form contraction and the
+ * tolerance, times n^D), and helm_batch_step runs the lanes' step graphs concurrently on
+ * streams of decreasing priority, the lane holding the longest predicted solve first, so
+ * one lane's FP64 residual overlaps another lane's coarse multigrid levels and the critical
+ * solve is scheduled ahead.  Applies to later submissions; results do not depend on the
+ * lane.  HELM_EINVAL outside the range.
  * (The lane split is a scheduling choice of this library; the paper has no counterpart.) */
 #define HELM_MAX_LANES 4
 HELM_API helm_status helm_batch_set_lanes(helm_batch* batch, int lanes);
