@@ -266,7 +266,8 @@ __device__ __forceinline__ auto abs2(C v) -> decltype(v.x) { return fma(v.y, v.y
 // ---------------------------------------------------------------------------
 // 2D: 32 x 32 tiles, u_{N+1} staged in shared memory with a 1-node halo
 // ---------------------------------------------------------------------------
-constexpr int T2 = 32;
+constexpr int T2 = 32;        // residual tile width (x)
+constexpr int T2Y = 32;       // residual tile height (y), a multiple of 8
 
 // DAMP: the instance has p != 0 (decided once per tile, outside the point loop)
 template <typename R, int MODE, bool DAMP>
@@ -291,14 +292,14 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
     const c2* __restrict__ e = (const c2*)L0.e;
     c2* __restrict__ rhs = (c2*)lev_rhs(L0, 0, MODE == 1 ? s.it + 1 : s.it);   // r_{N+1} / r_0
     const int P = L0.pitch;
-    const int x0 = 1 + item.tx * T2, y0 = 1 + item.ty * T2;
+    const int x0 = 1 + item.tx * T2, y0 = 1 + item.ty * T2Y;
     R emax2 = 0;
-    constexpr int NSTAGE = ((T2 + 2) * (T2 + 2) + NTH - 1) / NTH;
+    constexpr int NSTAGE = ((T2 + 2) * (T2Y + 2) + NTH - 1) / NTH;
     // fixed trip count, fully unrolled: all loads of the tile are issued before their uses
 #pragma unroll
     for (int it = 0; it < NSTAGE; ++it) {
         const int q = threadIdx.x + it * NTH;
-        if (q >= (T2 + 2) * (T2 + 2)) break;
+        if (q >= (T2 + 2) * (T2Y + 2)) break;
         const int lx = q % (T2 + 2), ly = q / (T2 + 2);
         const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
         double2 v = make_double2(0.0, 0.0);
@@ -308,7 +309,7 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
                 const c2 ev = e[gy * P + gx];
                 v.x += Inner<R>::widen(ev.x);
                 v.y += Inner<R>::widen(ev.y);
-                if (lx >= 1 && lx <= T2 && ly >= 1 && ly <= T2)
+                if (lx >= 1 && lx <= T2 && ly >= 1 && ly <= T2Y)
                     emax2 = fmax(emax2, abs2(ev));
             }
         }
@@ -322,7 +323,7 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
     double r2d = 0.0, b2 = 0.0;
     const int lx = (threadIdx.x & 31) + 1;
 #pragma unroll
-    for (int k = 0; k < T2 / 8; ++k) {
+    for (int k = 0; k < T2Y / 8; ++k) {
         const int ly = (threadIdx.x >> 5) + 8 * k + 1;
         const int gx = x0 + lx - 1, gy = y0 + ly - 1;
         if (gx > n || gy > n) continue;
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(NTH, 5)
 k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
              const ResItem* __restrict__ items, int nitems, StepCtl c)
 {
-    __shared__ double2 U[(T2 + 2) * (T2 + 2)];
+    __shared__ double2 U[(T2 + 2) * (T2Y + 2)];
     pdl_wait();
     pdl_trigger();
     for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
@@ -391,7 +392,7 @@ k_residual2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
 // another tile's r_{N+1}.
 // The tile is one residual tile of k_residual2d; NTU threads (128 or 256) each stand for
 // 256 / NTU threads of that kernel's map, so partials are formed in its order.
-constexpr int UPY = 32;
+constexpr int UPY = T2Y;
 
 // The coarse window: fine nodes gx0 .. gx0 + W - 1 (gx0 = x0 - H even when H is odd) read
 // coarse X = gx >> 1 .. (gx + 1) >> 1, i.e. W / 2 + 1 columns from cx0 = gx0 >> 1.
@@ -430,7 +431,7 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     constexpr int UW = TX + 2, UH = TY + 2;
     static_assert(H % 2 == 1 && TX % 2 == 0 && TY % 2 == 0, "gx0, gy0 even");
     typedef Planes<W> PL;
-    static_assert(TY == T2 && NTH % NTU == 0, "one residual tile, NTH / NTU map threads per thread");
+    static_assert(TY == T2Y && NTH % NTU == 0, "one residual tile, NTH / NTU map threads per thread");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sa[NTH / 32], sm[NTH / 32];
     __shared__ int last;
@@ -576,7 +577,7 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
         r2[v] = 0;
         em[v] = 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < TY / 8; ++k) {
             const int ly = (t >> 5) + 8 * k + 1;
             const int gx = x0 + lx - 1, gy = y0 + ly - 1;
             if (gx > n || gy > n) continue;
@@ -995,7 +996,7 @@ inline int blocks_for(long work) {
 
 }  // namespace
 
-int residual_tile_rows(int D) { return D == 2 ? T2 : T3Y; }
+int residual_tile_rows(int D) { return D == 2 ? T2Y : T3Y; }
 int residual_tile_planes(int D) { return D == 2 ? 1 : T3Z; }
 
 cudaError_t run_fp_bits_check(int count, unsigned long long seed, unsigned long long* bad_host)
