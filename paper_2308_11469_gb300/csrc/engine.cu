@@ -703,6 +703,20 @@ struct Engine {
     }
 
     // Initial residual and norm of one newly started instance.
+    // Batches start a submitted instance at its first step, on the stream its lane then
+    // runs on, so the start kernels of the lanes run side by side.
+    std::vector<int> pending;
+    helm_status start_pending(cudaStream_t s)
+    {
+        for (int slot : pending)
+            if (slot < cap && slots[slot]) {
+                const helm_status st = start_instance(slot, s);
+                if (st != HELM_OK) return st;
+            }
+        pending.clear();
+        return HELM_OK;
+    }
+
     helm_status start_instance(int slot, cudaStream_t s)
     {
         Instance* in = slots[slot];
@@ -1383,8 +1397,7 @@ static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, 
     in->d.damp = damp;
     E->slots[slot] = in;
     E->dirty = true;
-    st = E->start_instance(slot, b->stream);
-    if (st != HELM_OK) return st;
+    E->pending.push_back(slot);                 // started by the next step, on its lane
     helm_batch::Rec r;
     r.key = key;
     r.slot = slot;
@@ -1530,10 +1543,12 @@ helm_status helm_batch_step(helm_batch* b, int max_steps)
         cudaStream_t es;
         cudaEvent_t ej;
         {
-            const helm_status st = rank_stream(b, (int)r, &es, &ej);
+            helm_status st = rank_stream(b, (int)r, &es, &ej);
+            if (st != HELM_OK) return st;
+            HELM_CK(cudaStreamWaitEvent(es, b->fork, 0));
+            st = E->start_pending(es);
             if (st != HELM_OK) return st;
         }
-        HELM_CK(cudaStreamWaitEvent(es, b->fork, 0));
         helm_status st = E->prepare_plan();
         if (st != HELM_OK) return st;
         // A bounded chunk after a membership change runs as direct launches (finished
@@ -1598,7 +1613,9 @@ helm_status helm_batch_profile(helm_batch* b, int max_steps, uint64_t* launches,
     for (auto& kv : b->engines) {
         Engine* E = kv.second.get();
         if (E->active_count() == 0) continue;
-        helm_status st = E->prepare_plan();
+        helm_status st = E->start_pending(b->stream);
+        if (st != HELM_OK) return st;
+        st = E->prepare_plan();
         if (st != HELM_OK) return st;
         const size_t nl = E->step.size();
         std::vector<cudaEvent_t> ev(2 * nl);
