@@ -282,9 +282,10 @@ HELM_API helm_status helm_batch_set_lanes(helm_batch* batch, int lanes);
  * ((n+2)^D complex128, the layout of the device u) once the solve has finished, before
  * helm_batch_poll reports it done.  When a helm_batch_step runs its lanes to completion
  * (max_steps = 0) the copy is queued on the solve's lane right behind its last step, so it
- * overlaps the lanes still running; otherwise it is made when the solve retires.  host_u
- * must stay valid until then; page-locked memory makes the copy asynchronous.  HELM_EINVAL
- * for an unknown or finished ticket, or a device pointer. */
+ * overlaps the lanes still running; otherwise, and always for pageable host memory (whose
+ * copy would hold the other lanes' launches), it is made when the solve retires.  host_u
+ * must stay valid until then.  HELM_EINVAL for an unknown or finished ticket, or a device
+ * pointer. */
 HELM_API helm_status helm_batch_set_host_result(helm_batch* batch, uint64_t ticket, void* host_u);
 HELM_API helm_status helm_batch_poll(helm_batch* batch, uint64_t ticket, int* done, int* status,
                             int* iters, double* res_hist);

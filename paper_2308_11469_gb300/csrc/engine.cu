@@ -875,6 +875,7 @@ struct helm_batch {
         size_t ubytes = 0;
         std::vector<double> hist;
         void* host_u = nullptr;         // helm_batch_set_host_result: the result's host copy
+        bool host_pinned = false;       // page-locked: copied behind the lane's last step
         bool host_sent = false;         // its copy was queued behind the lane's last step
     };
     std::map<uint64_t, Rec> recs;
@@ -1577,7 +1578,9 @@ helm_status helm_batch_step(helm_batch* b, int max_steps)
         if (max_steps == 0)
             for (auto& kr : b->recs) {
                 helm_batch::Rec& r = kr.second;
-                if (r.key != key || r.done || !r.inst || !r.host_u || r.host_sent) continue;
+                // (a copy into pageable memory would hold the host, and the other lanes'
+                // launches, until this lane ends: those go out at retirement instead)
+                if (r.key != key || r.done || !r.inst || !r.host_u || !r.host_pinned || r.host_sent) continue;
                 const long count = (long)(r.ubytes / sizeof(double2));
                 k_final_u<<<(int)std::min<long>((count + 255) / 256, 1216), 256, 0, es>>>(
                     E->d_state + r.slot, (double2*)r.u, r.inst->d.u[1], count);
@@ -1689,6 +1692,7 @@ helm_status helm_batch_set_host_result(helm_batch* b, uint64_t ticket, void* hos
         return HELM_EINVAL;
     }
     it->second.host_u = host_u;
+    it->second.host_pinned = a.type == cudaMemoryTypeHost;
     it->second.host_sent = false;
     return HELM_OK;
 }

@@ -172,16 +172,19 @@ def test_lanes_do_not_change_results(B):
     B.helm_batch_destroy(batch)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
 @pytest.mark.parametrize("chunk", [0, 5])
-def test_host_result_copy(B, chunk):
+def test_host_result_copy(B, chunk, pinned):
     # the result also lands in host memory: behind the lane's last step when the step runs
-    # to completion (chunk 0), at retirement after bounded steps (chunk 5)
+    # to completion (chunk 0, page-locked buffers), at retirement otherwise
     probs = [inputs.gaussian_cavity_2d(k, seed=2, n=127) for k in (1.0, 2.5, 4.0)]
     batch = B.helm_batch_create(0)
     F = [torch.from_numpy(p.f).to(DEV) for p in probs]
     G = [torch.from_numpy(p.g).to(DEV) for p in probs]
     U = [torch.zeros_like(g) for g in G]
-    UH = [torch.full(tuple(g.shape), complex(7.0, 7.0), dtype=torch.complex128).pin_memory() for g in G]
+    UH = [torch.full(tuple(g.shape), complex(7.0, 7.0), dtype=torch.complex128) for g in G]
+    if pinned:
+        UH = [x.pin_memory() for x in UH]
     plans = [B.helm_plan_create(2, p.n, p.h, p.k, prec=1) for p in probs]
     tickets = [B.helm_batch_submit(batch, plans[i], F[i], G[i], U[i], 1e-8, 2000) for i in range(3)]
     for t, uh in zip(tickets, UH):
