@@ -203,39 +203,52 @@ k_prolong(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += gridDim.x * wpb) {
       const int y = (D == 3) ? row % n + 1 : row + 1;
       const int z = (D == 3) ? row / n + 1 : 0;
-      for (int x = lane + 1; x <= n; x += 32) {
-        // per axis: even fine index -> one coarse node (weight 1), odd -> two (1/2 each)
-        const int x0 = x >> 1, x1 = (x + 1) >> 1;
-        const int y0 = y >> 1, y1 = (y + 1) >> 1;
-        const int z0 = z >> 1, z1 = (z + 1) >> 1;
-        R vx = 0, vy = 0;
+      // a lane forms the fine pair x = 2p + 1 (coarse columns p, p + 1) and x = 2p + 2
+      // (column p + 1 twice) from the same eight coarse values; per axis an even fine
+      // index takes one coarse node (weight 1), an odd one two (1/2 each)
+      const int y0 = y >> 1, y1 = (y + 1) >> 1;
+      const int z0 = z >> 1, z1 = (z + 1) >> 1;
+      const R w = (D == 3) ? (R)0.125 : (R)0.25;
+      for (int p = lane; 2 * p + 1 <= n; p += 32) {
+        c2 cv[2][2][2];                                 // [iz][iy][column p / p + 1]
         const int nz = (D == 3) ? 2 : 1;
-        for (int iz = 0; iz < nz; ++iz) {
-            const int Z = iz ? z1 : z0;
+#pragma unroll
+        for (int iz = 0; iz < nz; ++iz)
+#pragma unroll
             for (int iy = 0; iy < 2; ++iy) {
-                const int Y = iy ? y1 : y0;
-                for (int ix = 0; ix < 2; ++ix) {
-                    const int X = ix ? x1 : x0;
-                    const c2 c = ce[off<D>(C, X, Y, Z)];
-                    vx += c.x;
-                    vy += c.y;
-                }
+                const size_t oc = off<D>(C, p, iy ? y1 : y0, iz ? z1 : z0);
+                cv[iz][iy][0] = ce[oc];
+                cv[iz][iy][1] = ce[oc + 1];
             }
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int x = 2 * p + 1 + half;
+            if (x > n) break;
+            // each of the 2^D corner reads counts 1/2^D; coincident corners (even index)
+            // are read twice, which gives the weight 1 of an even fine index
+            R vx = 0, vy = 0;
+#pragma unroll
+            for (int iz = 0; iz < nz; ++iz)
+#pragma unroll
+                for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+                    for (int ix = 0; ix < 2; ++ix) {
+                        const c2 c = cv[iz][iy][half ? 1 : ix];
+                        vx += c.x;
+                        vy += c.y;
+                    }
+            const long o = (long)off<D>(F, x, y, z);
+            c2 v;
+            if (ez) {
+                v.x = w * vx;
+                v.y = w * vy;
+            } else {
+                v = e[o];
+                v.x += w * vx;
+                v.y += w * vy;
+            }
+            e[o] = v;
         }
-        // each of the 2^D corner reads counts 1/2^D; coincident corners (even index)
-        // are read twice, which gives the weight 1 of an even fine index.
-        const R w = (D == 3) ? (R)0.125 : (R)0.25;
-        const long o = (long)off<D>(F, x, y, z);
-        c2 v;
-        if (ez) {
-            v.x = w * vx;
-            v.y = w * vy;
-        } else {
-            v = e[o];
-            v.x += w * vx;
-            v.y += w * vy;
-        }
-        e[o] = v;
       }
     }
 }
