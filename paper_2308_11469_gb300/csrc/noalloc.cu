@@ -14,6 +14,10 @@
 // raises the kernels' shared-memory limits, and should therefore come before any stream
 // capture.  Every call reuses the same array and clears the part it uses; calls that
 // overlap on the GPU (two streams, two host threads) race on it.
+//
+// Nothing is copied from host memory: the descriptor, state and work items travel as a
+// kernel argument to a one-block kernel that writes them into the array, so a call only
+// enqueues work and returns without waiting for the stream.
 #include "../../include/helm.h"
 #include "launch.h"
 
@@ -45,6 +49,19 @@ constexpr size_t OFF_LEVELS = OFF_ITEMS + a256(sizeof(MgItem) * HELM_MAXLEV);
 
 inline helm_status fail(helm_status st, const char*) { return st; }
 
+// The array's header (descriptor | state | work items) as one kernel argument.
+struct alignas(16) Header {
+    unsigned char bytes[OFF_LEVELS];
+};
+static_assert(sizeof(Header) <= 4096, "header must fit the kernel-argument space");
+
+__global__ void k_noalloc_header(Header hd, unsigned char* dst)
+{
+    const unsigned int* src = reinterpret_cast<const unsigned int*>(hd.bytes);
+    unsigned int* out = reinterpret_cast<unsigned int*>(dst);
+    for (int i = threadIdx.x; i < (int)(OFF_LEVELS / 4); i += blockDim.x) out[i] = src[i];
+}
+
 helm_status device_scratch(unsigned char** out)
 {
     int dev = 0;
@@ -70,6 +87,9 @@ helm_status device_scratch(unsigned char** out)
     return HELM_OK;
 }
 
+// A 16-byte aligned pointer to managed memory or to memory of the current device (the
+// kernels and the scratch array live on the current device; another GPU's memory would
+// need peer access the library does not set up).
 bool device_ptr(const void* p)
 {
     if (!p || ((uintptr_t)p & 15) != 0) return false;
@@ -78,7 +98,13 @@ bool device_ptr(const void* p)
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -88,6 +114,7 @@ extern "C" helm_status poisson_vcycle_noalloc(int ndim, int n, double h, int pre
 {
     if (ndim != 2 && ndim != 3) return fail(HELM_EINVAL, "ndim must be 2 or 3");
     if (n < 1 || ((n + 1) & n) != 0) return fail(HELM_EINVAL, "n must be 2^m - 1");
+    if (n > (ndim == 2 ? 32767 : 2047)) return fail(HELM_EINVAL, "n beyond the library's grid bounds");
     if (!(h > 0.0)) return fail(HELM_EINVAL, "h must be positive");
     if (prec != HELM_PREC_FP64 && prec != HELM_PREC_MIXED) return fail(HELM_EINVAL, "bad precision");
     if (nu1 < 0 || nu1 > 8 || nu2 < 0 || nu2 > 8 || nu1 + nu2 < 1) return fail(HELM_EINVAL, "bad nu1/nu2");
@@ -109,6 +136,7 @@ extern "C" helm_status poisson_vcycle_noalloc(int ndim, int n, double h, int pre
         d.lev[nl].n = m;
         ++nl;
     }
+    if (lt < 0) return fail(HELM_EUNSUPPORTED, "hierarchy does not reach the tail size");
     d.nlev = nl;
     d.ltail = lt;
     size_t off = OFF_LEVELS;
@@ -144,11 +172,11 @@ extern "C" helm_status poisson_vcycle_noalloc(int ndim, int n, double h, int pre
     s.status = HELM_ST_ACTIVE;
     MgItem items[HELM_MAXLEV];
     for (int l = 0; l < HELM_MAXLEV; ++l) items[l] = MgItem{0, l};
-    unsigned char header[OFF_LEVELS];
-    memset(header, 0, sizeof header);
-    memcpy(header, &d, sizeof d);
-    memcpy(header + OFF_STATE, &s, sizeof s);
-    memcpy(header + OFF_ITEMS, items, sizeof items);
+    Header header;
+    memset(&header, 0, sizeof header);
+    memcpy(header.bytes, &d, sizeof d);
+    memcpy(header.bytes + OFF_STATE, &s, sizeof s);
+    memcpy(header.bytes + OFF_ITEMS, items, sizeof items);
 
     cudaStream_t sm = (cudaStream_t)cuda_stream;
     const InstDesc* dd = (const InstDesc*)base;
@@ -160,7 +188,8 @@ extern "C" helm_status poisson_vcycle_noalloc(int ndim, int n, double h, int pre
     } while (0)
     // rings of the level arrays must be zero; the previous call left its data here
     NA_CK(cudaMemsetAsync(base + OFF_LEVELS, 0, off - OFF_LEVELS, sm));
-    NA_CK(cudaMemcpyAsync(base, header, OFF_LEVELS, cudaMemcpyHostToDevice, sm));
+    k_noalloc_header<<<1, 256, 0, sm>>>(header, base);
+    NA_CK(cudaGetLastError());
     NA_CK(launch_pack(D, pr, dd, 0, n, rhs, 1, sm));
     NA_CK(launch_pack(D, pr, dd, 0, n, e, 0, sm));
     auto pts = [&](int m) { return (D == 3) ? (long)m * m * m : (long)m * m; };
@@ -173,6 +202,9 @@ extern "C" helm_status poisson_vcycle_noalloc(int ndim, int n, double h, int pre
             NA_CK(launch_up2d(pr, dd, ds, di + l, 1, tiles2d(d.lev[l].n), nu2, tile_shape2d(d.lev[l].n),
                               nu1 == 0 ? 1 : 0, sm));
     } else {
+        // without pre-smoothing the coarse iterates are zero on the way down: the
+        // restriction takes rhs alone and the prolongation assigns (as poisson_vcycle)
+        const int zmode = (nu1 == 0) ? 1 : 0;
         for (int l = 0; l < lt; ++l) {
             const int m = d.lev[l].n;
             const int w_rb = (int)(((D == 3) ? (long)m * m : m) * ((m + 1) / 2));
@@ -180,13 +212,13 @@ extern "C" helm_status poisson_vcycle_noalloc(int ndim, int n, double h, int pre
                 NA_CK(launch_rbgs(D, pr, dd, ds, di + l, 1, w_rb, 0, it == 0 ? 1 : 0, sm));
                 NA_CK(launch_rbgs(D, pr, dd, ds, di + l, 1, w_rb, 1, 0, sm));
             }
-            NA_CK(launch_restrict(D, pr, dd, ds, di + l, 1, (int)pts(d.lev[l + 1].n), sm));
+            NA_CK(launch_restrict(D, pr, dd, ds, di + l, 1, (int)pts(d.lev[l + 1].n), sm, zmode));
         }
         NA_CK(launch_tail(D, pr, d.lev[lt].n, dd, ds, di + lt, 1, nu1, nu2, 1, sm));
         for (int l = lt - 1; l >= 0; --l) {
             const int m = d.lev[l].n;
             const int w_rb = (int)(((D == 3) ? (long)m * m : m) * ((m + 1) / 2));
-            NA_CK(launch_prolong(D, pr, dd, ds, di + l, 1, (int)pts(m), sm));
+            NA_CK(launch_prolong(D, pr, dd, ds, di + l, 1, (int)pts(m), sm, zmode));
             for (int it = 0; it < nu2; ++it) {
                 NA_CK(launch_rbgs(D, pr, dd, ds, di + l, 1, w_rb, 0, 0, sm));
                 NA_CK(launch_rbgs(D, pr, dd, ds, di + l, 1, w_rb, 1, 0, sm));
