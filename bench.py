@@ -17,6 +17,24 @@ relres 1e-8.
 * ``roofline``: the kernel with the largest device-time share, from a replay of one
   step with every launch bracketed by CUDA events on the launching stream.
 * ``cpu_baseline``: the CPU oracle (exact sine-basis Poisson solves, all host cores).
+  The same leg states every result's error against the oracle's exact discrete solution
+  (``accuracy`` and each leg's ``accuracy``).
+
+Other configurations, as bounded legs of the same run (each with its own clock sample;
+``--legs`` picks them, ``--legs none`` skips them):
+
+* ``cavity63``: the 63x63 plane-wave cavity (h = 1/64, theta = pi/6), k = 2 to relres
+  1e-10 and k = 5 > k_max (must diverge), mixed and FP64 single solves: microseconds per
+  solve, status against the closed-form prediction, O(h^2) error against the continuum
+  plane wave.
+* ``cube255``: the 255^3 plane-wave + sine cube, k = 4, relres 1e-8, mixed and FP64
+  single solves (autotuned schedules): solves/s.
+* ``batch512``: 512 uneven 2D cavities (n in {63..511}), mixed batch to completion, and
+  the plain FP64 form solving its first 64 alone: solves/s beside the byte-model
+  ceiling.
+* ``served``: Poisson arrivals of mixed 2D (127^2..2047^2) / 3D (63^3..255^3) requests
+  at several rates through the continuous-batching server (HBM cap 120 GB): request
+  latency p50 / p99 (completion - arrival) and solves/s per rate.
 
 Under torchrun each rank solves its own copy of the workload (weak scaling, no
 collective on the data path).  ``--impl reference`` times the CPU oracle instead.
@@ -151,8 +169,10 @@ def cpu_oracle_workload(problems, max_seconds: float = 60.0):
 
 
 def run_reference(args):
-    """CPU oracle arm: each step solves one k of the workload (rotating), so the run stays
-    within minutes; solves/s = 4 / sum over k of the mean time of that k's solves."""
+    """CPU oracle arm: each timed step is the whole workload (the four solves k = 1..4 to
+    relres 1e-8, exact sine-basis inner solves on every host core); each warm-up step is
+    the cheapest solve (k = 1) alone, so the run stays within a few minutes.
+    solves/s = 4 x steps / the timed steps' total time."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
@@ -160,33 +180,286 @@ def run_reference(args):
     from paper_2308_11469_gb300 import inputs
     problems = [inputs.gaussian_cavity_2d(k) for k in KS]
     workers = os.cpu_count() or 1
-    nsteps = max(args.steps, len(KS))
-    for w in range(min(args.warmup, 1)):
+    for w in range(args.warmup):
         p = problems[0]
         it.paper_iteration(p.f, p.g, p.h, p.k, tol=TOL, max_outer=MAX_OUTER, poisson="dst",
                            workers=workers)
-    per_k = {k: [] for k in KS}
-    for s in range(nsteps):
-        p = problems[s % len(KS)]
+    times = []
+    for s in range(args.steps):
         t = time.perf_counter()
-        it.paper_iteration(p.f, p.g, p.h, p.k, tol=TOL, max_outer=MAX_OUTER, poisson="dst",
-                           workers=workers)
-        per_k[p.k].append(time.perf_counter() - t)
-    t_work = sum(float(np.mean(v)) for v in per_k.values())
-    value = len(KS) / t_work
+        for p in problems:
+            it.paper_iteration(p.f, p.g, p.h, p.k, tol=TOL, max_outer=MAX_OUTER, poisson="dst",
+                               workers=workers)
+        times.append(time.perf_counter() - t)
+    t_work = float(np.sum(times))
+    value = len(KS) * args.steps / t_work
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
-        "n_gpus": ws, "steps": nsteps, "warmup": min(args.warmup, 1),
-        "ms_per_step": 1e3 * t_work / len(KS), "higher_is_better": True, "scaling": "weak",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_work / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_GRID, "k": list(KS), "tol": TOL},
+        "config": {"workload": WORKLOAD, "n": N_GRID, "k": list(KS), "tol": TOL,
+                   "solves_per_step": len(KS)},
+        "latency_ms": {"p50": float(1e3 * np.percentile(times, 50)),
+                       "p99": float(1e3 * np.percentile(times, 99)), "per": "step of 4 solves"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": workers, "kind": "oracle",
-                         "sample": f"{nsteps} oracle solves (exact sine-basis inner solves), k "
-                                   f"rotating over {list(KS)}; value = 4 / sum_k mean time"},
+                         "sample": f"{args.steps} steps of the four solves k = {list(KS)} (exact "
+                                   f"sine-basis inner solves); warm-up steps solve k = 1 alone"},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------------------
+# bounded legs for the other configurations (GPU side; their errors against the
+# oracle are formed in the cpu_baseline leg, errors_vs_oracle below)
+# ---------------------------------------------------------------------------
+
+def _ev_ms(torch, fn):
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    out = fn()
+    e.record()
+    e.synchronize()
+    return s.elapsed_time(e), out
+
+
+def bytes_per_point_step(nu1: int, nu2: int, cycles: int, eb: int) -> float:
+    """Algorithmic bytes per fine point of one outer step: the FP64 residual + update
+    (u, f in, u out: 48 B; e in, r out: 2 inner elements) and per V(nu1, nu2) cycle, on
+    every level (x 4/3 for the 2D hierarchy), 3 inner elements per sweep and 2 + 1/4 for
+    each of the restriction and the prolongation (mixed V(2,2): 240 B)."""
+    return 48 + 2 * eb + cycles * 4.0 / 3.0 * (3 * eb * (nu1 + nu2) + 2 * (2 * eb + eb / 4))
+
+
+def leg_cavity63(B, torch, dev):
+    from paper_2308_11469_gb300 import inputs
+    rows, keep = [], {}
+    for k, tol in ((2.0, 1e-10), (5.0, 1e-10)):
+        p = inputs.plane_wave_cavity_2d(k)
+        f = torch.from_numpy(p.f).to(dev)
+        g = torch.from_numpy(p.g).to(dev)
+        u = torch.zeros_like(g)
+        for prec, name in ((B.HELM_PREC_MIXED, "mixed"), (B.HELM_PREC_FP64, "fp64")):
+            plan = B.helm_plan_create(2, p.n, p.h, k, prec=prec)
+            rho = B.helm_plan_info(plan)[2]
+
+            def run():
+                u.zero_()
+                return B.helm_solve(plan, f, g, u, tol, 400)
+            for _ in range(3):
+                run()
+            ts = []
+            for _ in range(10):
+                t, (st, it, hist) = _ev_ms(torch, run)
+                ts.append(t)
+            B.helm_plan_destroy(plan)
+            status = B.helm_status_str(st)
+            row = {"k": k, "form": name, "tol": tol, "status": status, "iters": it,
+                   "relres_last": float(hist[-1]), "us_per_solve_median": 1e3 * float(np.median(ts)),
+                   "rho_closed_form": rho,
+                   "predicted": "converges" if rho < 1 else "diverges",
+                   "status_matches_prediction": (status == "HELM_CONVERGED") == (rho < 1)}
+            if k == 2.0:
+                uh = u.cpu().numpy()
+                keep[("cavity63", name)] = (p, uh)
+                cont = inputs.plane_wave(2, p.n, p.h, k, p.meta["direction"])
+                row["max_err_vs_continuum_plane_wave"] = float(np.max(np.abs(uh - cont)))
+            rows.append(row)
+    return {"rows": rows}, keep
+
+
+def leg_cube255(B, torch, dev, flush):
+    from paper_2308_11469_gb300 import inputs
+    p = inputs.plane_wave_sine_cube(4.0, seed=3, n=255)
+    f = torch.from_numpy(p.f).to(dev)
+    g = torch.from_numpy(p.g).to(dev)
+    u = torch.zeros_like(g)
+    out, keep = {"n": p.n, "k": p.k, "tol": TOL}, {}
+    npts = float(p.n) ** 3
+    for prec, name in ((B.HELM_PREC_MIXED, "mixed"), (B.HELM_PREC_FP64, "fp64")):
+        plan = B.helm_plan_create(3, p.n, p.h, p.k, prec=prec)
+        u.zero_()                             # the tuning solves start from the zero iterate
+        sched = B.helm_plan_autotune(plan, f, g, u, TOL, MAX_OUTER)
+
+        def run():
+            u.zero_()
+            return B.helm_solve(plan, f, g, u, TOL, MAX_OUTER)
+        run()
+        ts = []
+        for _ in range(3):
+            flush.fill_(1)
+            t, (st, it, hist) = _ev_ms(torch, run)
+            ts.append(t)
+        B.helm_plan_destroy(plan)
+        ms = float(np.mean(ts))
+        eb = 8 if prec == B.HELM_PREC_MIXED else 16
+        # 3D: the hierarchy adds 1/7 instead of 1/3
+        bpp = 48 + 2 * eb + sched[2] * 8.0 / 7.0 * (3 * eb * (sched[0] + sched[1]) + 2 * (2 * eb + eb / 8))
+        out[name] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "ms_best": float(min(ts)),
+                     "status": B.helm_status_str(st), "iters": it, "relres_last": float(hist[-1]),
+                     "schedule": {"nu1": sched[0], "nu2": sched[1], "cycles": sched[2]},
+                     "model_bytes_per_solve": bpp * npts * it,
+                     "model_GBs": bpp * npts * it / (ms / 1e3) / 1e9}
+        keep[("cube255", name)] = (p, u.cpu().numpy())
+    out["mixed_over_fp64"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    return out, keep
+
+
+def leg_batch512(B, torch, dev, peak_gbs):
+    from paper_2308_11469_gb300 import inputs
+    probs = inputs.batched_instances(count=512, seed=4)
+    F = [torch.from_numpy(q.f).to(dev) for q in probs]
+    G = [torch.from_numpy(q.g).to(dev) for q in probs]
+    U = [torch.zeros_like(x) for x in G]
+    big = max(range(len(probs)), key=lambda i: (probs[i].n, probs[i].k))
+    q = probs[big]
+    scheds = {}
+    for prec in (B.HELM_PREC_MIXED, B.HELM_PREC_FP64):
+        pl = B.helm_plan_create(2, q.n, q.h, q.k, prec=prec)
+        U[big].zero_()
+        scheds[prec] = B.helm_plan_autotune(pl, F[big], G[big], U[big], TOL, 3000)[:3]
+        B.helm_plan_destroy(pl)
+    batch = B.helm_batch_create(120 << 30)
+    B.helm_batch_set_cycle(batch, *scheds[B.HELM_PREC_MIXED])
+
+    def run_batch():
+        for x in U:
+            x.zero_()
+        ts = [B.helm_batch_submit_geom(batch, 2, q.n, q.h, q.k, B.HELM_PREC_MIXED, F[i], G[i], U[i],
+                                       TOL, 3000) for i, q in enumerate(probs)]
+        B.helm_batch_step(batch, 0)
+        return [B.helm_batch_poll(batch, t, 3000) for t in ts]
+    run_batch()
+    ts = []
+    for _ in range(3):
+        t, res = _ev_ms(torch, run_batch)
+        ts.append(t)
+    B.helm_batch_destroy(batch)
+    ms = float(np.mean(ts))
+    its = [r[1] for r in res]
+    pts_steps = float(sum(q.n ** 2 * r[1] for q, r in zip(probs, res)))
+    nu1, nu2, cyc = scheds[B.HELM_PREC_MIXED]
+    b_run = bytes_per_point_step(nu1, nu2, cyc, 8) * pts_steps
+    b_v22 = bytes_per_point_step(2, 2, 1, 8) * pts_steps
+    out = {"instances": len(probs), "ms_per_batch": ms, "solves_per_s": 512e3 / ms,
+           "converged": int(sum(r[0] == B.HELM_CONVERGED for r in res)),
+           "iters_mean": float(np.mean(its)), "iters_max": int(max(its)),
+           "schedule": dict(zip(("nu1", "nu2", "cycles"), scheds[B.HELM_PREC_MIXED])),
+           "model_bytes_per_batch": b_run, "model_GBs": b_run / (ms / 1e3) / 1e9,
+           "ceiling_solves_per_s_at_peak": 512 / (b_run / (peak_gbs * 1e9)),
+           "ceiling_solves_per_s_v22_model": 512 / (b_v22 / (peak_gbs * 1e9))}
+    keep = {("batch512", "mixed", i): (probs[i], U[i].cpu().numpy()) for i in range(len(probs))}
+    tot, cnt = 0.0, 64
+    its64 = []
+    for i in range(cnt):
+        q = probs[i]
+        pl = B.helm_plan_create(2, q.n, q.h, q.k, prec=B.HELM_PREC_FP64)
+        B.helm_plan_set_cycle(pl, *scheds[B.HELM_PREC_FP64])
+
+        def one():
+            U[i].zero_()
+            return B.helm_solve(pl, F[i], G[i], U[i], TOL, 3000)
+        one()
+        t, r = _ev_ms(torch, one)
+        its64.append(r[1])
+        tot += t
+        B.helm_plan_destroy(pl)
+        keep[("batch512", "fp64", i)] = (q, U[i].cpu().numpy())
+    out["fp64_single_first64"] = {"solves_per_s": cnt * 1e3 / tot, "iters_mean": float(np.mean(its64)),
+                                  "schedule": dict(zip(("nu1", "nu2", "cycles"), scheds[B.HELM_PREC_FP64]))}
+    mixed64 = float(sum(its[:cnt]))
+    out["note"] = ("fp64_single_first64: each of the first 64 instances alone, device time summed; "
+                   f"their mixed outer steps {mixed64:.0f}, fp64 {float(sum(its64)):.0f}")
+    return out, keep
+
+
+SERVED_RATES = (10.0, 100.0, 300.0, 1000.0, 2000.0)
+
+
+def served_count(rate: float) -> int:
+    """Requests per rate: about two seconds of arrivals, at least 30 and at most 400."""
+    return int(min(400, max(30, round(2.0 * rate))))
+
+
+def leg_served(B, torch, dev, rates=SERVED_RATES, seed: int = 5):
+    from paper_2308_11469_gb300 import inputs, serve
+    pool = {}
+    # warm-up: one request of every (dimension, size) class, all at once (engines, plans
+    # and graphs of every class are built outside the measured streams)
+    warm = []
+    rng = np.random.default_rng(seed + 1000)
+    for D, sizes in ((2, (127, 255, 511, 1023, 2047)), (3, (63, 127, 255))):
+        for n in sizes:
+            h = 1.0 / (n + 1)
+            k = 0.5 * inputs.dirichlet_kmax(D, n, h)
+            c, a = inputs.draw_gaussian_params(D, rng)
+            warm.append(inputs.Request(0.0, inputs.Problem(D, n, h, k, None, None,
+                                                           {"kind": "gauss", "centres": c, "amps": a})))
+    jobs, pool = serve.make_jobs(warm, dev, pool)
+    srv = serve.Server(120 << 30, chunk=4)
+    srv.run(jobs, realtime=False)
+    srv.close()
+    del jobs
+    rows, keep = [], {}
+    for rate in rates:
+        count = served_count(rate)
+        reqs = inputs.served_stream(rate, count, seed=seed, materialise=False)
+        jobs, pool = serve.make_jobs(reqs, dev, pool, tol=TOL, max_outer=MAX_OUTER)
+        torch.cuda.synchronize()
+        srv = serve.Server(120 << 30, chunk=4)
+        done = srv.run(jobs, realtime=True)
+        st = serve.latency_stats(done)
+        pts_steps = float(sum((j.n ** j.D) * j.iters for j in done))
+        st.update({"rate_req_per_s": rate, "requests": count,
+                   "converged": int(sum(j.status == B.HELM_CONVERGED for j in done)),
+                   "max_workspace_gb": srv.max_in_use / (1 << 30),
+                   "outer_steps_mean": float(np.mean([j.iters for j in done])),
+                   "point_steps": pts_steps})
+        srv.close()
+        rows.append(st)
+        # a seeded sample of three results per rate, kept for the error check
+        pick = np.random.default_rng(int(rate)).choice(len(done), size=min(3, len(done)), replace=False)
+        for i in pick:
+            j = done[int(i)]
+            key = (j.D, j.n, reqs[j.rid].problem.meta["kind"])
+            keep[("served", rate, j.rid)] = (pool[key][2], j.k, j.u.cpu().numpy())
+        del jobs, done
+        torch.cuda.synchronize()
+    return {"rates": rows, "hbm_cap_gb": 120, "chunk": 4,
+            "mix": "2D n in {127..2047} (70 %) / 3D n in {63, 127, 255}; Gaussian sources or "
+                   "plane-wave wall data (50/50); k ~ U[0.5, 0.9 k_max]; source / wall data "
+                   "materialised once per (D, n, kind), each request its own k and solution"}, keep
+
+
+def errors_vs_oracle(keep, workers: int, budget_s: float = 60.0):
+    """Relative L2 error of each kept result against the oracle's exact discrete
+    solution (sine-basis direct solve), within a CPU-time budget; the served sample is
+    checked last, smallest grids first."""
+    from oracle import fd
+    t0 = time.perf_counter()
+    errs = {}
+
+    def exact_for(p, k):
+        return fd.solve_exact_dst(p.f, p.g, p.h, k, workers=workers)
+
+    order = sorted(keep, key=lambda key: (key[0] == "served",
+                                          keep[key][0].n ** keep[key][0].D if key[0] == "served" else 0))
+    skipped = 0
+    for key in order:
+        if key[0] == "served":
+            p, k, u = keep[key]
+        else:
+            p, u = keep[key]
+            k = p.k
+        if key[0] == "served" and time.perf_counter() - t0 > budget_s:
+            skipped += 1
+            continue
+        ex = exact_for(p, k)
+        errs[key] = float(np.linalg.norm(u - ex) / np.linalg.norm(ex))
+    return errs, skipped, time.perf_counter() - t0
 
 
 def main():
@@ -197,6 +470,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--legs", default="cavity63,cube255,batch512,served",
+                    help="other configurations run after the headline ('none' to skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -362,6 +637,8 @@ def main():
     eb = 8
     top = max(prof.items(), key=lambda kv: kv[1][1])
     name, (nl, ms, by) = top
+    # the FP64 peak the residual kernels are measured against: this device's own FMA rate
+    fp64_tflops, fp64_probe_ms = B.helm_measure_fp64_rate()
 
     def hbm_line(nm, v):
         n_l, m_s, b_y = v
@@ -384,16 +661,27 @@ def main():
         traffic = per_pt * pts / nl if per_pt else None
         hv = hbm_line(name, (nl, ms, by))
         hv["traffic"] = traffic
-        roofline = {"bound": "alu", "kernel": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                    "peak_kind": "nominal FP64 rate (2 FP64 FMA per SM per clock x 152 SMs x "
-                                 "2.07 GHz = 1.26 TFLOP/s; no measured FP64 figure)",
+        hv["bytes_note"] = "fused minimum: every array the fused kernel must read or write, once"
+        roofline = {"bound": "alu", "kernel": name, "achieved": ach, "peak": fp64_tflops,
+                    "unit": "TFLOP/s", "frac": ach / fp64_tflops,
+                    "peak_kind": "measured FP64 FMA rate of this device (helm_measure_fp64_rate: "
+                                 f"8 FMA chains per thread on every SM, best launch {fp64_probe_ms:.3f} ms); "
+                                 f"nominal {FP64_PEAK_TFLOPS} TFLOP/s",
                     "traffic": traffic,
-                    "traffic_source": "ncu DRAM bytes per point of a 4-instance launch x the "
-                                      "average launch's points",
+                    "traffic_source": "ncu DRAM bytes per point of one launch x the average "
+                                      "launch's points",
                     "share": ms / total_kernel_ms,
                     "flops_per_launch": flops / nl, "avg_launch_us": 1e3 * ms / nl,
                     "hbm_view": hv}
+        if name == "ascent_residual_update_2d":
+            # the unfused steps' bytes: residual + update (64 B/pt), prolongation +
+            # correction (2e + e/4 = 18 B/pt), one red-black sweep (3e = 24 B/pt)
+            b106 = 106.0 * pts / nl
+            a106 = b106 / ((ms / nl) / 1e3) / 1e9
+            roofline["hbm_view_unfused_steps"] = {"bound": "hbm", "bytes_per_launch": b106,
+                                                  "achieved": a106, "peak": peak, "unit": "GB/s",
+                                                  "frac": a106 / peak,
+                                                  "peak_kind": f"{peak_kind} hbm_gbs (burst)"}
     else:
         roofline = hbm_line(name, (nl, ms, by))
     mg = {k: v for k, v in prof.items() if k in ("smooth_restrict_2d", "prolong_smooth_2d") and v[0]}
@@ -431,6 +719,32 @@ def main():
         "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches_per_step * args.steps),
     }
 
+    line["fp64_rate_measured_tflops"] = fp64_tflops
+
+    # ---- other configurations: bounded legs, each with its own clock sample ----
+    legs = [] if args.legs in ("", "none") else args.legs.split(",")
+    kept = {}
+    for leg in legs:
+        smp = ClockSampler(local)
+        smp.start()
+        t_leg = time.perf_counter()
+        if leg == "cavity63":
+            res, kp = leg_cavity63(B, torch, dev)
+        elif leg == "cube255":
+            res, kp = leg_cube255(B, torch, dev, flush)
+        elif leg == "batch512":
+            res, kp = leg_batch512(B, torch, dev, peak)
+        elif leg == "served":
+            res, kp = leg_served(B, torch, dev)
+        else:
+            raise SystemExit(f"unknown leg {leg}")
+        res["clocks"] = smp.stop()
+        res["wall_s"] = time.perf_counter() - t_leg
+        line[leg] = res
+        kept.update(kp)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         times, iters, exact, workers = cpu_oracle_workload(problems)
         done = len(times)
@@ -445,6 +759,30 @@ def main():
             if fp64_u is not None:
                 acc["fp64_rel_l2_vs_exact"].append(float(np.linalg.norm(fp64_u[i] - exact[i]) / nrm))
         line["accuracy"] = acc
+        if kept:
+            errs, skipped, t_err = errors_vs_oracle(kept, workers)
+            if "cavity63" in line:
+                for row in line["cavity63"]["rows"]:
+                    e = errs.get(("cavity63", row["form"])) if row["k"] == 2.0 else None
+                    if e is not None:
+                        row["rel_l2_vs_exact"] = e
+            if "cube255" in line:
+                for form in ("mixed", "fp64"):
+                    if ("cube255", form) in errs:
+                        line["cube255"][form]["rel_l2_vs_exact"] = errs[("cube255", form)]
+            if "batch512" in line:
+                for form in ("mixed", "fp64"):
+                    ev = [v for kk, v in errs.items() if kk[0] == "batch512" and kk[1] == form]
+                    if ev:
+                        line["batch512"][f"{form}_rel_l2_vs_exact"] = {
+                            "max": float(max(ev)), "median": float(np.median(ev)), "count": len(ev)}
+            if "served" in line:
+                ev = {kk: v for kk, v in errs.items() if kk[0] == "served"}
+                line["served"]["sample_rel_l2_vs_exact"] = {
+                    "max": float(max(ev.values())) if ev else None, "count": len(ev),
+                    "skipped_for_time": skipped,
+                    "sample": "three seeded requests per rate, smallest grids first within a 60 s budget"}
+            line["accuracy_check_s"] = t_err
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

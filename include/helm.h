@@ -90,6 +90,13 @@ HELM_API uint64_t helm_launch_count(void);
  * allocates 8 bytes of device memory for the count. */
 HELM_API helm_status helm_selftest_conversions(int count, uint64_t seed, uint64_t* mismatches);
 
+/* Diagnostic (no counterpart in the paper): the current device's FP64 FMA rate, the peak
+ * the FP64 residual kernels are measured against.  Every SM runs 8 blocks of 256
+ * threads, each thread 8 independent chains of 4096 fused multiply-adds; *tflops = flops
+ * (2 per FMA) / the best of five timed launches (*ms, CUDA events on the legacy default
+ * stream, after one warm-up launch).  Synchronous; allocates and frees a small buffer. */
+HELM_API helm_status helm_measure_fp64_rate(double* tflops, double* ms);
+
 /*
  * Plan: one cavity geometry (D, n, h), wave number k and precision, with its multigrid
  * hierarchy and workspace allocated on the current CUDA device.
@@ -228,10 +235,13 @@ HELM_API helm_status poisson_vcycle(helm_plan* plan, const void* rhs, void* e, i
  * device that loads it, until the process exits (enough for 2D n <= 511 in complex64,
  * 2D n <= 255 in complex128, 3D n <= 63 in either precision).
  *   ndim, n, h, prec   as helm_plan_create (prec picks complex64 or complex128 arrays).
- *   rhs, e             as poisson_vcycle (interior n^D, device, 16-byte aligned).
+ *   rhs, e             as poisson_vcycle (interior n^D, 16-byte aligned, memory of the
+ *                      current device or managed memory; HELM_EINVAL otherwise).
  *   cuda_stream        stream the work is enqueued on (NULL = legacy default stream).
  * Returns HELM_EUNSUPPORTED, doing nothing, when the grid's multigrid arrays would not fit
- * the 16 MiB array.  Asynchronous: the result is in e once the stream reaches it.
+ * the 16 MiB array.  Asynchronous: the call copies nothing from host memory (its
+ * descriptors travel as kernel arguments), so it returns once the work is enqueued, and
+ * the result is in e once the stream reaches it.
  * The first call on a device (with that device current) looks up the array's device
  * address and raises the kernels' shared-memory limits; make that first call before any
  * stream capture.  Every call reuses the same array (it clears what it uses), so calls

@@ -37,6 +37,7 @@ _SIGS = {
     "helm_last_error": (C.c_char_p, []),
     "helm_launch_count": (C.c_uint64, []),
     "helm_selftest_conversions": (C.c_int, [C.c_int, C.c_uint64, C.POINTER(C.c_uint64)]),
+    "helm_measure_fp64_rate": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "helm_plan_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(C.c_int), C.c_double,
                                    C.c_double, C.c_int, C.c_int, _vp]),
     "helm_plan_destroy": (C.c_int, [_vp]),
@@ -159,6 +160,13 @@ def helm_last_error() -> str:
 
 def helm_launch_count() -> int:
     return int(load().helm_launch_count())
+
+
+def helm_measure_fp64_rate():
+    """(TFLOP/s, ms of the best launch) of the device's FP64 FMA rate."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(load().helm_measure_fp64_rate(C.byref(tf), C.byref(ms)), "helm_measure_fp64_rate")
+    return tf.value, ms.value
 
 
 def helm_selftest_conversions(count: int = 1 << 20, seed: int = 1) -> int:

@@ -920,6 +920,14 @@ helm_status helm_selftest_conversions(int count, uint64_t seed, uint64_t* mismat
     return HELM_OK;
 }
 
+helm_status helm_measure_fp64_rate(double* tflops, double* ms)
+{
+    if (!tflops || !ms) return HELM_EINVAL;
+    HELM_CK(run_fp64_rate(tflops, ms));
+    add_launches(6);
+    return HELM_OK;
+}
+
 helm_status helm_plan_create(helm_plan** out, int ndim, const int* n, double h, double k, int bc,
                              int prec, void* cuda_stream)
 {

@@ -117,6 +117,9 @@ cudaError_t launch_lev_sumsq(int D, int prec, const InstDesc* insts, double* par
 cudaError_t launch_lev_scale(int D, int prec, const InstDesc* insts, double sc, cudaStream_t s);
 int power_iteration_blocks();
 cudaError_t run_fp_bits_check(int count, unsigned long long seed, unsigned long long* bad_host);
+// FP64 FMA rate of the current device (independent chains on every SM), best of 5 timed
+// launches: TFLOP/s (an FMA counts 2 flops) and that launch's milliseconds
+cudaError_t run_fp64_rate(double* tflops, double* ms_best);
 // u[0] and u[1] rings := g ring
 cudaError_t launch_set_ring(int D, const InstDesc* insts, int inst, int n, cudaStream_t s);
 // interior tight <-> level-0 padded/pitched, inner precision

@@ -987,6 +987,24 @@ __global__ void k_fp_bits_check(unsigned long long seed, int count, unsigned lon
     if (local) atomicAdd(bad, local);
 }
 
+// FP64 issue-rate probe: every thread runs 8 independent FMA chains x = x * m + c
+// (m, c kernel arguments, |m| < 1, so nothing overflows or turns subnormal and the
+// compiler cannot fold the loop); the sum of the chains is stored so no chain is dead.
+__global__ void __launch_bounds__(256) k_fp64_rate(int iters, double m, double c, double* sink)
+{
+    double x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = 1.0 + 1e-3 * (threadIdx.x + j);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = fma(x[j], m, c);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t += x[j];
+    if (t == 12345.678) sink[blockIdx.x * blockDim.x + threadIdx.x] = t;   // never true
+}
+
 inline int blocks_for(long work) {
     long b = (work + 255) / 256;
     if (b < 1) b = 1;
@@ -1012,6 +1030,40 @@ cudaError_t run_fp_bits_check(int count, unsigned long long seed, unsigned long 
     return e;
 }
 int residual_tile_cols(int D) { return 32; }
+
+cudaError_t run_fp64_rate(double* tflops, double* ms_best)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    double* sink = nullptr;
+    e = cudaMalloc(&sink, sizeof(double) * blocks * threads);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(a, 0);
+        k_fp64_rate<<<blocks, threads>>>(iters, 0.9999999, 1e-7, sink);
+        cudaEventRecord(b, 0);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float t = 0.0f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&t, a, b);
+        if (rep > 0 && t > 0.0f && t < best) best = t;        // the first launch warms up
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    if (e != cudaSuccess) return e;
+    const double flops = 2.0 * 8.0 * (double)iters * blocks * threads;
+    *ms_best = best;
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return cudaSuccess;
+}
 
 static int g_res_grid = 152 * 5;               // SMs x resident residual CTAs (set up below)
 

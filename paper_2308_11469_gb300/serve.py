@@ -196,6 +196,27 @@ def _pool_key(req):
     return (p.D, p.n, p.meta["kind"])
 
 
+def make_jobs(reqs, dev, pool=None, tol: float = 1e-8, max_outer: int = 2000):
+    """Jobs of a request stream drawn with ``materialise=False``.  Device data: one
+    materialised source / wall-data pair per (D, n, kind), built from the first request
+    of that key and shared by the later ones (each request keeps its own k and its own
+    solution buffer).  Returns (jobs, pool); `pool` maps the key to (f, g, problem)."""
+    import torch
+
+    from . import inputs
+    pool = {} if pool is None else pool
+    jobs = []
+    for i, r in enumerate(reqs):
+        key = _pool_key(r)
+        if key not in pool:
+            p = inputs.materialise(r.problem)
+            pool[key] = (torch.from_numpy(p.f).to(dev), torch.from_numpy(p.g).to(dev), p)
+        f, g, _ = pool[key]
+        p = r.problem
+        jobs.append(Job(i, p.D, p.n, p.h, p.k, f, g, torch.zeros_like(g), r.t_arrival, tol, max_outer))
+    return jobs, pool
+
+
 def main(argv=None) -> int:
     """Serve a seeded stream of mixed 2D / 3D requests and print latency / throughput."""
     import argparse
@@ -221,18 +242,7 @@ def main(argv=None) -> int:
                                 sizes_2d=tuple(int(x) for x in args.sizes_2d.split(",")),
                                 sizes_3d=tuple(int(x) for x in args.sizes_3d.split(",")),
                                 materialise=False)
-    # device data: one materialised source / wall-data pair per (D, n, kind); each request
-    # keeps its own k and its own solution buffer
-    pool = {}
-    jobs = []
-    for i, r in enumerate(reqs):
-        key = _pool_key(r)
-        if key not in pool:
-            p = inputs.materialise(r.problem)
-            pool[key] = (torch.from_numpy(p.f).to(dev), torch.from_numpy(p.g).to(dev))
-        f, g = pool[key]
-        p = r.problem
-        jobs.append(Job(i, p.D, p.n, p.h, p.k, f, g, torch.zeros_like(g), r.t_arrival))
+    jobs, _ = make_jobs(reqs, dev)
     torch.cuda.synchronize()
     srv = Server(int(args.cap_gb * (1 << 30)), chunk=args.chunk)
     done = srv.run(jobs, realtime=True)

@@ -108,3 +108,74 @@ def test_batched_512_instances(B):
         p = probs[i]
         exact = fd.solve_exact_dst(p.f, p.g, p.h, p.k)
         assert _relerr(res[i][3], exact) <= 1e-6, i
+
+
+# ---------------------------------------------------------------------------
+# FP64 at full size: the attainable relres floor, and 1e-10 parity below it
+# ---------------------------------------------------------------------------
+
+def _fp64_to_floor(B, p, max_outer):
+    """Plain FP64 solve run past its rounding floor (tol 0): the outer loop stops at
+    max_outer (or by the stagnation rule).  Returns (status, hist, u)."""
+    plan = B.helm_plan_create(p.D, p.n, p.h, p.k, prec=B.HELM_PREC_FP64)
+    f = torch.from_numpy(p.f).to(DEV)
+    g = torch.from_numpy(p.g).to(DEV)
+    u = torch.zeros_like(g)
+    st, iters, hist = B.helm_solve(plan, f, g, u, 0.0, max_outer)
+    B.helm_plan_destroy(plan)
+    return st, hist, u.cpu().numpy()
+
+
+@pytest.mark.parametrize("k", [2.0, 4.0])
+def test_fp64_floor_and_parity_1023(B, k):
+    # The FP64 residual of a 1023^2 iterate carries rounding ~ eps 8/h^2 |u| per entry, so
+    # relres stalls near 1e-10 (measured, printed), while the increments it drives are
+    # divided by ~8/h^2 again: the iterate itself keeps converging, to ~1e-13.
+    p = inputs.gaussian_cavity_2d(k)
+    st, hist, u = _fp64_to_floor(B, p, 200 if k == 2.0 else 400)
+    assert st in (B.HELM_MAXITER, B.HELM_DIVERGED)
+    exact = fd.solve_exact_dst(p.f, p.g, p.h, p.k)
+    err = _relerr(u, exact)
+    floor = float(np.min(hist))
+    print(f"FP64 1023^2 k={k}: relres floor {floor:.3e} (last {hist[-1]:.3e}, {len(hist) - 1} steps), "
+          f"rel. L2 error vs exact {err:.3e}")
+    assert floor < 1e-9
+    assert err <= 1e-10, err
+
+
+def test_fp64_floor_and_parity_cube_255(B):
+    p = inputs.plane_wave_sine_cube(4.0, seed=3, n=255)
+    st, hist, u = _fp64_to_floor(B, p, 120)
+    assert st in (B.HELM_MAXITER, B.HELM_DIVERGED)
+    exact = fd.solve_exact_dst(p.f, p.g, p.h, p.k)
+    err = _relerr(u, exact)
+    floor = float(np.min(hist))
+    print(f"FP64 255^3 k=4: relres floor {floor:.3e} (last {hist[-1]:.3e}, {len(hist) - 1} steps), "
+          f"rel. L2 error vs exact {err:.3e}")
+    assert floor < 1e-10
+    assert err <= 1e-10, err
+
+
+@pytest.mark.parametrize("D,n,k", [(2, 255, 3.0), (2, 511, 2.0), (3, 63, 4.0)])
+def test_fp64_iterates_match_exact_solve_iterates_large(B, D, n, k):
+    # enough V(2,2) cycles per outer step that each inner solve is exact to rounding: the
+    # GPU iterates are the paper's partial sums, step by step (sine-basis inner solves)
+    h = 1.0 / (n + 1)
+    rng = np.random.default_rng(21 + n)
+    f = rng.standard_normal((n,) * D) + 1j * rng.standard_normal((n,) * D)
+    g = rng.standard_normal((n + 2,) * D) + 1j * rng.standard_normal((n + 2,) * D)
+    N = 5
+    ora = it.paper_iteration(f, g, h, k, tol=0.0, max_outer=N, keep_iterates=True, poisson="dst")
+    plan = B.helm_plan_create(D, n, h, k, prec=B.HELM_PREC_FP64)
+    B.helm_plan_set_cycle(plan, 2, 2, 14)
+    ft = torch.from_numpy(f).to(DEV)
+    gt = torch.from_numpy(g).to(DEV)
+    for steps in (1, 3, N):
+        u = torch.zeros_like(gt)
+        st, iters, hist, einf = B.helm_solve_ex(plan, ft, gt, u, 0.0, steps)
+        assert st == B.HELM_MAXITER and iters == steps
+        err = _relerr(u.cpu().numpy(), ora.iterates[steps])
+        assert err <= 1e-10, (steps, err)
+    B.helm_plan_destroy(plan)
+    assert np.allclose(hist, ora.relres, rtol=1e-8, atol=1e-14)
+    assert np.allclose(einf, ora.einf, rtol=1e-8, atol=0)
