@@ -233,6 +233,21 @@ def spectral_radius(geo: Geometry, k: float, alpha: float | None = None) -> floa
     return float(np.max(np.abs(np.linalg.eigvals(iteration_matrix(geo, k, alpha)))))
 
 
+def singular_extremes(geo: Geometry, k: float, alpha: float | None = None):
+    """(sigma_max, sigma_min) of the dense G (its 2-norm and the inverse's 2-norm
+    reciprocal), from the singular values of G."""
+    sv = np.linalg.svd(iteration_matrix(geo, k, alpha), compute_uv=False)
+    return float(sv[0]), float(sv[-1])
+
+
+def condition_number(geo: Geometry, k: float, alpha: float | None = None) -> float:
+    """2-norm condition number sigma_max / sigma_min of G, the quantity plotted against k
+    beside the spectral radius in Section 2.4's figure (this project's reading: of the
+    matrices A^{-1} and G only G depends on k)."""
+    smax, smin = singular_extremes(geo, k, alpha)
+    return smax / smin
+
+
 def exit_times(geo: Geometry, c_tau: float = 1.0):
     """(E, L) on the (N+1)^2 grid: Delta E = -c_tau, dE/dn = 0; Delta L = 0, dL/dn = 1; both
     zero on the hole."""

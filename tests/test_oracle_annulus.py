@@ -176,3 +176,85 @@ def test_input_generator_matches_the_oracles_data():
     from paper_2308_11469_gb300 import inputs
     for N, k in ((10, 0.7), (64, 1.3)):
         assert np.array_equal(inputs.annulus_scattering(N, k), an.scattering_data(an.geometry(N), k))
+
+
+# ---------------------------------------------------------------------------
+# condition number of G (Section 2.4's figure, right panel)
+# ---------------------------------------------------------------------------
+
+def _sparse_G(geo, k, alpha=None):
+    import scipy.sparse.linalg as spla
+    alpha = k * k if alpha is None else alpha
+    lu = spla.splu(an.operator(geo, sigma=alpha - k * k).tocsc())
+    edge = geo.typ[geo.nodes[:, 0], geo.nodes[:, 1]] == an.EDGE
+    m = np.where(edge, 1j * k, -alpha + 0j)
+
+    def solve(r):
+        return lu.solve(np.ascontiguousarray(r.real)) + 1j * lu.solve(np.ascontiguousarray(r.imag))
+    return solve, m
+
+
+@pytest.mark.parametrize("N,k", [(10, 0.8), (16, 1.2), (20, 1.0)])
+def test_singular_extremes_by_independent_routes(N, k):
+    geo = an.geometry(N)
+    smax, smin = an.singular_extremes(geo, k)
+    solve, m = _sparse_G(geo, k)
+    A = an.operator(geo, sigma=0.0)
+    # sigma_max^2 = top eigenvalue of G^H G by power iteration on sparse solves; the
+    # adjoint solve uses A^T (real), solved densely by sparse LU of the transpose
+    import scipy.sparse.linalg as spla
+    luT = spla.splu(A.T.tocsc())
+
+    def solveT(r):
+        return luT.solve(np.ascontiguousarray(r.real)) + 1j * luT.solve(np.ascontiguousarray(r.imag))
+    rng = np.random.default_rng(N)
+    x = rng.standard_normal(len(m)) + 1j * rng.standard_normal(len(m))
+    for _ in range(300):
+        x = np.conj(m) * solveT(solve(m * x))
+        x /= np.linalg.norm(x)
+    est = np.linalg.norm(solve(m * x))
+    assert abs(est - smax) <= 1e-9 * smax
+    # 1 / sigma_min^2 = top eigenvalue of G^{-1} G^{-H} = M^{-1} A A^T M^{-H}: matrix-vector
+    # products only (no inverse of A)
+    Ad = A.toarray()
+    K = (Ad / m[:, None]) @ (Ad.T / np.conj(m)[None, :])
+    lam = np.max(np.linalg.eigvalsh((K + K.conj().T) / 2))
+    assert abs(1.0 / math.sqrt(lam) - smin) <= 1e-9 * smin
+    # the product of the singular values is |det G| = prod |M_ii| / |det A|
+    sv = np.linalg.svd(an.iteration_matrix(geo, k), compute_uv=False)
+    lu = spla.splu(A.tocsc())
+    logdetA = np.sum(np.log(np.abs(lu.U.diagonal())))
+    assert abs(np.sum(np.log(sv)) - (np.sum(np.log(np.abs(m))) - logdetA)) <= 1e-8 * abs(logdetA)
+
+
+def test_condition_number_bounds_and_trend():
+    geo = an.geometry(16)
+    prev = None
+    for k in (0.4, 0.8, 1.2, 1.6):
+        c = an.condition_number(geo, k)
+        smax, smin = an.singular_extremes(geo, k)
+        ev = np.abs(np.linalg.eigvals(an.iteration_matrix(geo, k)))
+        assert smin <= ev.min() * (1 + 1e-12) and ev.max() <= smax * (1 + 1e-12)
+        assert c >= ev.max() / ev.min() * (1 - 1e-12)
+        # G = k A^{-1} diag(k, 1) diag(-1, i): the PDE columns shrink with k relative to the
+        # edge columns, so the spread of the singular values falls as k grows
+        if prev is not None:
+            assert c < prev
+        prev = c
+
+
+def test_symmetrised_operator_without_corners():
+    # W A (W = 1 on PDE rows, -1/h on outer-edge rows) is symmetric once the corner rows and
+    # columns are dropped, and no row but a corner's own references a corner: the adjoint of
+    # a solve with A is a solve with A between diagonal scalings (plus a corner correction)
+    for N in (10, 16, 20):
+        geo = an.geometry(N)
+        A = an.operator(geo, sigma=0.3).toarray()
+        i, j = geo.nodes[:, 0], geo.nodes[:, 1]
+        edge = geo.typ[i, j] == an.EDGE
+        corner = ((i == 0) | (i == N)) & ((j == 0) | (j == N))
+        w = np.where(edge, -1.0 / geo.h, 1.0)
+        WA = (w[:, None] * A)[~corner][:, ~corner]
+        assert np.allclose(WA, WA.T, rtol=0, atol=1e-12 * np.abs(WA).max())
+        assert np.all(A[~corner][:, corner] == 0.0)
+        assert np.allclose(np.diag(A)[corner], 1.0 / geo.h)
