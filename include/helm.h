@@ -360,6 +360,34 @@ HELM_API helm_status helm_annulus_solve(helm_annulus* plan, const void* data, vo
  */
 HELM_API helm_status helm_annulus_exit_times(helm_annulus* plan, double c_tau, double tol, int max_outer,
                                              void* E_out, void* L_out, double* kstar);
+/*
+ * Spectrum of the iteration matrix G = A_sigma^{-1} M of Section 2.4 (M = -alpha on the
+ * PDE rows, +i k on the outer-edge rows; the partial sums converge iff rho(G) < 1), the
+ * quantities of Section 2.4's figure, measured on the GPU with the plan's multigrid as
+ * A_sigma^{-1} (`cycles` cycles of the plan's V(nu1, nu2) from zero per application, in the
+ * plan's inner precision; 1 <= cycles <= 64).
+ * helm_annulus_spectral_radius: power iteration x <- G x / ||G x|| from a seeded start;
+ *   rho = ||G x|| for the unit x, lambda = x^H G x (the dominant eigenvalue, when it is
+ *   unique in modulus).  Stops when two successive estimates of rho agree to tol
+ *   (relative) twice in a row, or after max_iters.
+ * helm_annulus_condition: the 2-norm condition number of G, cond = sigma_max / sigma_min.
+ *   sigma_max by power iteration on G^H G: the adjoint solve uses that W A_sigma, W = 1 on
+ *   PDE rows and -1/h on outer-edge rows, is symmetric apart from the corner rows (which no
+ *   other row references), so A^{-T} = corners h, elsewhere W A^{-1} W^{-1} after moving
+ *   the corners' couplings to the right-hand side.  sigma_min = 1 / sqrt(lambda_max(A^T D
+ *   A)), D = |M|^{-2}, by Lanczos (stencil applications only, FP64).  Needs k > 0.
+ *   iters_done: the larger of the two loops' counts.
+ * Outputs (host) may be NULL.  Returns HELM_OK when converged, HELM_MAXITER when the
+ * estimates still moved after max_iters (they are returned all the same), or an error.
+ * Synchronous; allocates small reduction buffers (and four FP64 grids for the Lanczos
+ * vectors) for the call.
+ */
+HELM_API helm_status helm_annulus_spectral_radius(helm_annulus* plan, int max_iters, double tol, int cycles,
+                                                  double* rho, double* lambda_re, double* lambda_im,
+                                                  int* iters_done);
+HELM_API helm_status helm_annulus_condition(helm_annulus* plan, int max_iters, double tol, int cycles,
+                                            double* sigma_max, double* sigma_min, double* cond,
+                                            int* iters_done);
 
 #ifdef __cplusplus
 }

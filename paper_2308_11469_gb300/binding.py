@@ -58,6 +58,11 @@ _SIGS = {
     "poisson_vcycle_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_int, _vp, _vp, C.c_int,
                                          C.c_int, _vp]),
     "helm_annulus_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_double, C.c_double, C.c_double, C.c_int]),
+    "helm_annulus_spectral_radius": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                                 C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                                 C.POINTER(C.c_int)]),
+    "helm_annulus_condition": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                           C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "helm_annulus_destroy": (C.c_int, [_vp]),
     "helm_annulus_set_shift": (C.c_int, [_vp, C.c_double]),
     "helm_annulus_set_cycle": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
@@ -378,6 +383,26 @@ def helm_annulus_exit_times(plan: _Annulus, E, L, c_tau: float = 1.0, tol: float
     st = _check(load().helm_annulus_exit_times(plan.handle, float(c_tau), float(tol), int(max_outer), pe, pl,
                                                C.byref(ks)), "helm_annulus_exit_times")
     return st, ks.value
+
+
+def helm_annulus_spectral_radius(plan: _Annulus, max_iters: int = 300, tol: float = 1e-10, cycles: int = 16):
+    """Returns (status, rho, complex dominant eigenvalue, iterations) of G by power
+    iteration (status HELM_OK when converged, HELM_MAXITER otherwise)."""
+    r, lr, li = C.c_double(), C.c_double(), C.c_double()
+    it = C.c_int()
+    st = _check(load().helm_annulus_spectral_radius(plan.handle, int(max_iters), float(tol), int(cycles),
+                                                    C.byref(r), C.byref(lr), C.byref(li), C.byref(it)),
+                "helm_annulus_spectral_radius")
+    return st, r.value, complex(lr.value, li.value), it.value
+
+
+def helm_annulus_condition(plan: _Annulus, max_iters: int = 400, tol: float = 1e-10, cycles: int = 16):
+    """Returns (status, sigma_max, sigma_min, cond, iterations) of G."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    it = C.c_int()
+    st = _check(load().helm_annulus_condition(plan.handle, int(max_iters), float(tol), int(cycles), C.byref(a),
+                                              C.byref(b), C.byref(c), C.byref(it)), "helm_annulus_condition")
+    return st, a.value, b.value, c.value, it.value
 
 
 class _Batch:

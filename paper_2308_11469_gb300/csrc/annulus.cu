@@ -972,6 +972,301 @@ k_an_kstar(const double* __restrict__ E, const double* __restrict__ L, const uns
     if ((threadIdx.x & 31) == 0 && best < 1e300) atomicMin(out, (unsigned long long)__double_as_longlong(best));
 }
 
+
+// ---- spectrum of G = A_sigma^{-1} M (Section 2.4's figure): M = -alpha on PDE rows, +i k
+// on EDGE rows (M^H: -alpha, -i k) ----
+
+__device__ __forceinline__ bool an_corner(int i, int j, int n)
+{
+    return (i == 0 || i == n) && (j == 0 || j == n);
+}
+
+// block sum of three doubles into part[3 b + 0..2]
+__device__ __forceinline__ void an_sum3(double a, double b, double c, double* __restrict__ part)
+{
+    __shared__ double sm[3][AN_NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sm[0][threadIdx.x >> 5] = a;
+        sm[1][threadIdx.x >> 5] = b;
+        sm[2][threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int w = 0; w < AN_NT / 32; ++w) t += sm[threadIdx.x][w];
+        part[3 * blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+// rhs = s M x in the inner precision (hole rows 0)
+template <typename R>
+__global__ void __launch_bounds__(AN_NT)
+k_an_mx(const double2* __restrict__ x, const unsigned char* __restrict__ typ, typename CX<R>::T* __restrict__ rhs,
+        long total, double s, double alpha, double k)
+{
+    typedef typename CX<R>::T c2;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const unsigned char ty = typ[t];
+        const double2 v = x[t];
+        double rx = 0.0, ry = 0.0;
+        if (ty == AN_PDE) {
+            rx = -alpha * s * v.x;
+            ry = -alpha * s * v.y;
+        } else if (ty == AN_EDGE) {            // i k (v.x + i v.y)
+            rx = -k * s * v.y;
+            ry = k * s * v.x;
+        }
+        c2 r;
+        r.x = an_narrow(rx, R());
+        r.y = an_narrow(ry, R());
+        rhs[t] = r;
+    }
+}
+
+// power-iteration bookkeeping: sums of |e|^2 and of conj(x) e (re, im) per block, then x := e
+template <typename R>
+__global__ void __launch_bounds__(AN_NT)
+k_an_pdot(double2* __restrict__ x, const typename CX<R>::T* __restrict__ e, const unsigned char* __restrict__ typ,
+          long total, double* __restrict__ part)
+{
+    double a = 0.0, cr = 0.0, ci = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        if (typ[t] == AN_HOLE) {
+            x[t] = make_double2(0.0, 0.0);
+            continue;
+        }
+        const double ex = an_widen(e[t].x), ey = an_widen(e[t].y);
+        const double2 xv = x[t];
+        a += ex * ex + ey * ey;
+        cr += xv.x * ex + xv.y * ey;
+        ci += xv.x * ey - xv.y * ex;
+        x[t] = make_double2(ex, ey);
+    }
+    an_sum3(a, cr, ci, part);
+}
+
+// Adjoint solve, first half.  With W = 1 on PDE rows and -1/h on EDGE rows, W A_sigma is
+// symmetric once the corner rows and columns are dropped, and no other row references a
+// corner; so A^{-T} y is: corners h y_c; the rest W A^{-1} W^{-1} (y + the corner rows'
+// transposed couplings, +y_c / 2 on each corner's two inward neighbours), the solve taken
+// with zero right-hand side at the corners.  This kernel forms that right-hand side from
+// y = e, writes the corners' part of z = M^H A^{-T} y (-i k h y_c) into x, and sums |y|^2.
+template <typename R>
+__global__ void __launch_bounds__(AN_NT)
+k_an_tprep(const typename CX<R>::T* __restrict__ e, typename CX<R>::T* __restrict__ rhs, double2* __restrict__ x,
+           const unsigned char* __restrict__ typ, int n, double h, double k, double* __restrict__ part)
+{
+    typedef typename CX<R>::T c2;
+    const int S = n + 1;
+    const long total = (long)S * S;
+    double a = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const unsigned char ty = typ[t];
+        c2 r;
+        r.x = 0;
+        r.y = 0;
+        if (ty == AN_HOLE) {
+            rhs[t] = r;
+            x[t] = make_double2(0.0, 0.0);
+            continue;
+        }
+        const int q = (int)t, i = q / S, j = q % S;
+        double yx = an_widen(e[q].x), yy = an_widen(e[q].y);
+        a += yx * yx + yy * yy;
+        if (an_corner(i, j, n)) {
+            rhs[q] = r;
+            x[q] = make_double2(k * h * yy, -k * h * yx);     // -i k h y_c
+            continue;
+        }
+        if (ty == AN_EDGE) {
+            if ((j == 0 || j == n) && (i == 1 || i == n - 1)) {
+                const c2 c = e[(i == 1 ? 0 : n) * S + j];
+                yx += 0.5 * an_widen(c.x);
+                yy += 0.5 * an_widen(c.y);
+            }
+            if ((i == 0 || i == n) && (j == 1 || j == n - 1)) {
+                const c2 c = e[i * S + (j == 1 ? 0 : n)];
+                yx += 0.5 * an_widen(c.x);
+                yy += 0.5 * an_widen(c.y);
+            }
+            yx *= -h;
+            yy *= -h;
+        }
+        r.x = an_narrow(yx, R());
+        r.y = an_narrow(yy, R());
+        rhs[q] = r;
+    }
+    an_sum3(a, 0.0, 0.0, part);
+}
+
+// Adjoint solve, second half: z = M^H W s off the corners (PDE: -alpha s; EDGE: (-i k) (-s / h)
+// = (i k / h) s) into x; sums |z|^2 over every node (the corners' z from k_an_tprep)
+template <typename R>
+__global__ void __launch_bounds__(AN_NT)
+k_an_tfin(const typename CX<R>::T* __restrict__ e, double2* __restrict__ x, const unsigned char* __restrict__ typ,
+          int n, double h, double alpha, double k, double* __restrict__ part)
+{
+    const int S = n + 1;
+    const long total = (long)S * S;
+    double a = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const unsigned char ty = typ[t];
+        if (ty == AN_HOLE) continue;
+        const int q = (int)t, i = q / S, j = q % S;
+        double2 z;
+        if (an_corner(i, j, n)) {
+            z = x[q];
+        } else {
+            const double sx = an_widen(e[q].x), sy = an_widen(e[q].y);
+            if (ty == AN_PDE) {
+                z.x = -alpha * sx;
+                z.y = -alpha * sy;
+            } else {
+                z.x = -k / h * sy;
+                z.y = k / h * sx;
+            }
+            x[q] = z;
+        }
+        a += z.x * z.x + z.y * z.y;
+    }
+    an_sum3(a, 0.0, 0.0, part);
+}
+
+// Lanczos on the real symmetric K = A^T D A, D = diag(1 / alpha^2 on PDE rows, 1 / k^2 on EDGE
+// rows) = (G^{-1})^H G^{-1}: its largest eigenvalue is 1 / sigma_min(G)^2.  y = D A v:
+__global__ void __launch_bounds__(AN_NT)
+k_an_lz_a(const double* __restrict__ v, double* __restrict__ y, const unsigned char* __restrict__ typ, int n,
+          double h, double sigma, double dp, double de)
+{
+    const int S = n + 1;
+    const long total = (long)S * S;
+    const double ih2 = 1.0 / (h * h), ih = 1.0 / h;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const unsigned char ty = typ[t];
+        const int q = (int)t, i = q / S, j = q % S;
+        double r = 0.0;
+        if (ty == AN_PDE) {
+            // hole entries of v are zero
+            r = (((v[q - S] + v[q + S]) + (v[q - 1] + v[q + 1])) - 4.0 * v[q]) * ih2 - sigma * v[q];
+            r *= dp;
+        } else if (ty == AN_EDGE) {
+            double m = 0.0;
+            int c = 0;
+            if (i == 0) { m += v[S + j]; ++c; }
+            if (i == n) { m += v[(n - 1) * S + j]; ++c; }
+            if (j == 0) { m += v[i * S + 1]; ++c; }
+            if (j == n) { m += v[i * S + n - 1]; ++c; }
+            if (c == 2) m *= 0.5;
+            r = (v[q] - m) * ih * de;
+        }
+        y[q] = r;
+    }
+}
+
+// w = A^T y - beta v_prev (A^T gathered: PDE column j: its own row, its PDE neighbours'
+// rows (1/h^2) and its EDGE neighbours' rows (-1/h, j being their inward neighbour); EDGE
+// column: its own row (1/h), its inward neighbour's row (1/h^2), and the rows of the
+// corners whose inward neighbour it is (-1/(2h)); corner column: its own row (1/h));
+// part[3 b] = sum v . w
+__global__ void __launch_bounds__(AN_NT)
+k_an_lz_at(const double* __restrict__ y, const double* __restrict__ v, const double* __restrict__ vp, double beta,
+           double* __restrict__ w, const unsigned char* __restrict__ typ, int n, double h, double sigma,
+           double* __restrict__ part)
+{
+    const int S = n + 1;
+    const long total = (long)S * S;
+    const double ih2 = 1.0 / (h * h), ih = 1.0 / h;
+    double a = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const unsigned char ty = typ[t];
+        const int q = (int)t, i = q / S, j = q % S;
+        double r = 0.0;
+        if (ty == AN_PDE) {
+            r = (-4.0 * ih2 - sigma) * y[q];
+            const int nb[4] = {q - S, q + S, q - 1, q + 1};
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                const unsigned char tn = typ[nb[d]];
+                if (tn == AN_PDE) r += ih2 * y[nb[d]];
+                else if (tn == AN_EDGE) r -= ih * y[nb[d]];
+            }
+        } else if (ty == AN_EDGE) {
+            r = ih * y[q];
+            if (!an_corner(i, j, n)) {
+                const int in = (i == 0) ? S + j : (i == n) ? (n - 1) * S + j : (j == 0) ? i * S + 1 : i * S + n - 1;
+                r += ih2 * y[in];
+                if ((j == 0 || j == n) && (i == 1 || i == n - 1)) r -= 0.5 * ih * y[(i == 1 ? 0 : n) * S + j];
+                if ((i == 0 || i == n) && (j == 1 || j == n - 1)) r -= 0.5 * ih * y[i * S + (j == 1 ? 0 : n)];
+            }
+        }
+        r -= beta * vp[q];
+        w[q] = r;
+        a += v[q] * r;
+    }
+    an_sum3(a, 0.0, 0.0, part);
+}
+
+// w -= a v, part[3 b] = sum w^2
+__global__ void __launch_bounds__(AN_NT)
+k_an_lz_orth(double* __restrict__ w, const double* __restrict__ v, double a, long total, double* __restrict__ part)
+{
+    double s = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const double r = w[t] - a * v[t];
+        w[t] = r;
+        s += r * r;
+    }
+    an_sum3(s, 0.0, 0.0, part);
+}
+
+// v = s w; a seeded start vector when w == nullptr (hole nodes 0); part[3 b] = sum v^2
+__global__ void __launch_bounds__(AN_NT)
+k_an_lz_scale(double* __restrict__ v, const double* __restrict__ w, double s, const unsigned char* __restrict__ typ,
+              long total, double* __restrict__ part)
+{
+    double a = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        double r;
+        if (w) {
+            r = s * w[t];
+        } else {
+            unsigned long long z = 0x9e3779b97f4a7c15ull * (unsigned long long)(t + 1);
+            z = (z ^ (z >> 31)) * 0xbf58476d1ce4e5b9ull;
+            z ^= z >> 29;
+            r = (typ[t] == AN_HOLE) ? 0.0 : ((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+        }
+        v[t] = r;
+        a += r * r;
+    }
+    an_sum3(a, 0.0, 0.0, part);
+}
+
+// complex seeded start vector (hole 0) into x; part: sums of |x|^2
+__global__ void __launch_bounds__(AN_NT)
+k_an_seed(double2* __restrict__ x, const unsigned char* __restrict__ typ, long total, double* __restrict__ part)
+{
+    double a = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        unsigned long long z = 0xd1b54a32d192ed03ull * (unsigned long long)(t + 7);
+        z = (z ^ (z >> 31)) * 0xbf58476d1ce4e5b9ull;
+        z ^= z >> 29;
+        const double re = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        z ^= z >> 31;
+        const double im = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+        const double2 v = (typ[t] == AN_HOLE) ? make_double2(0.0, 0.0) : make_double2(re, im);
+        x[t] = v;
+        a += v.x * v.x + v.y * v.y;
+    }
+    an_sum3(a, 0.0, 0.0, part);
+}
+
 }  // namespace
 }  // namespace helm
 
@@ -1320,6 +1615,223 @@ helm_status an_solve(helm_annulus* a, const double2* data, double2* u, double to
     return HELM_OK;
 }
 
+
+// ---- spectrum of G (Section 2.4's figure) ----
+
+// e := A_sigma^{-1} rhs on level 0 by `cycles` multigrid cycles from zero
+template <typename R>
+helm_status an_apply_inv(helm_annulus* a, int cycles)
+{
+    typedef typename CX<R>::T c2;
+    const auto& L0 = a->lev[0];
+    const long total = (long)(a->N + 1) * (a->N + 1);
+    a->ls = a->stream;
+    for (int c = 0; c < cycles; ++c) {
+        if (c == 0) AN_CK(cudaMemsetAsync(L0.e, 0, total * sizeof(c2), a->stream));
+        const helm_status st = an_vcycle<R>(a, 0, c == 0);
+        if (st != HELM_OK) return st;
+    }
+    return HELM_OK;
+}
+
+// per-call reduction buffers (three doubles per block) and their host copy
+struct AnSums {
+    double* d = nullptr;
+    double* h = nullptr;
+    int nb = 0;
+    ~AnSums()
+    {
+        if (d) cudaFree(d);
+        if (h) cudaFreeHost(h);
+    }
+    helm_status init(int nblk)
+    {
+        nb = nblk;
+        if (cudaMalloc(&d, 3 * sizeof(double) * nb) != cudaSuccess) return HELM_ENOMEM;
+        if (cudaMallocHost(&h, 3 * sizeof(double) * nb) != cudaSuccess) return HELM_ENOMEM;
+        return HELM_OK;
+    }
+    // block sums -> out[0..2] (fixed order)
+    helm_status fetch(cudaStream_t s, double* out)
+    {
+        AN_CK(cudaMemcpyAsync(h, d, 3 * sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+        AN_CK(cudaStreamSynchronize(s));
+        out[0] = out[1] = out[2] = 0.0;
+        for (int b = 0; b < nb; ++b)
+            for (int c = 0; c < 3; ++c) out[c] += h[3 * b + c];
+        return HELM_OK;
+    }
+};
+
+// Power iteration x <- G x / ||G x||: rho ~ ||G x|| (||x|| = 1), lambda ~ x^H G x.
+template <typename R>
+helm_status an_spectral(helm_annulus* a, int max_iter, double tol, int cycles, double* rho, double* lre,
+                        double* lim, int* iters, bool* conv)
+{
+    typedef typename CX<R>::T c2;
+    const auto& L0 = a->lev[0];
+    const long total = (long)(a->N + 1) * (a->N + 1);
+    cudaStream_t s = a->stream;
+    AnSums sums;
+    helm_status st = sums.init(a->nblk);
+    if (st != HELM_OK) return st;
+    double v[3];
+    k_an_seed<<<a->nblk, AN_NT, 0, s>>>(a->U1, L0.typ, total, sums.d);
+    an_count(a, 1);
+    if ((st = sums.fetch(s, v)) != HELM_OK) return st;
+    double sc = 1.0 / std::sqrt(v[0]), prev = 0.0, r = 0.0;
+    int ok = 0, it = 0;
+    *conv = false;
+    for (it = 1; it <= max_iter; ++it) {
+        k_an_mx<R><<<a->nblk, AN_NT, 0, s>>>(a->U1, L0.typ, (c2*)L0.rhs, total, sc, a->alpha, a->k);
+        an_count(a, 1);
+        if ((st = an_apply_inv<R>(a, cycles)) != HELM_OK) return st;
+        k_an_pdot<R><<<a->nblk, AN_NT, 0, s>>>(a->U1, (const c2*)L0.e, L0.typ, total, sums.d);
+        an_count(a, 1);
+        AN_CK(cudaGetLastError());
+        if ((st = sums.fetch(s, v)) != HELM_OK) return st;
+        r = std::sqrt(v[0]);
+        *lre = sc * v[1];
+        *lim = sc * v[2];
+        if (!(r > 0.0) || !std::isfinite(r)) return HELM_ENONFINITE;
+        sc = 1.0 / r;
+        ok = (std::fabs(r - prev) <= tol * r) ? ok + 1 : 0;
+        prev = r;
+        if (ok >= 2) {
+            *conv = true;
+            break;
+        }
+    }
+    *rho = r;
+    *iters = std::min(it, max_iter);
+    return HELM_OK;
+}
+
+// largest eigenvalue of the symmetric tridiagonal matrix (diag a[0..m-1], off-diagonal
+// b[1..m-1]) by bisection on the Sturm count
+double tridiag_max(const std::vector<double>& a, const std::vector<double>& b, int m)
+{
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < m; ++i) {
+        const double r = (i > 0 ? std::fabs(b[i]) : 0.0) + (i + 1 < m ? std::fabs(b[i + 1]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    auto below = [&](double x) {                  // eigenvalues < x
+        int c = 0;
+        double d = 1.0;
+        for (int i = 0; i < m; ++i) {
+            d = a[i] - x - (i > 0 ? b[i] * b[i] / d : 0.0);
+            if (d == 0.0) d = -1e-300;
+            if (d < 0.0) ++c;
+        }
+        return c;
+    };
+    for (int k = 0; k < 200 && hi - lo > 1e-15 * std::max(std::fabs(lo), std::fabs(hi)); ++k) {
+        const double mid = 0.5 * (lo + hi);
+        if (below(mid) >= m) hi = mid;
+        else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// sigma_max(G) by power iteration on G^H G (adjoint solves through the symmetrised
+// operator), sigma_min(G) = 1 / sqrt(lambda_max(A^T D A)) by Lanczos (no solves).
+template <typename R>
+helm_status an_singular(helm_annulus* a, int max_iter, double tol, int cycles, double* smax, double* smin,
+                        int* iters, bool* conv)
+{
+    typedef typename CX<R>::T c2;
+    const auto& L0 = a->lev[0];
+    const int n = a->N;
+    const long total = (long)(n + 1) * (n + 1);
+    cudaStream_t s = a->stream;
+    AnSums sums;
+    helm_status st = sums.init(a->nblk);
+    if (st != HELM_OK) return st;
+    double v[3];
+    // sigma_max
+    k_an_seed<<<a->nblk, AN_NT, 0, s>>>(a->U1, L0.typ, total, sums.d);
+    an_count(a, 1);
+    if ((st = sums.fetch(s, v)) != HELM_OK) return st;
+    double sc = 1.0 / std::sqrt(v[0]), prev = 0.0, est = 0.0;
+    int ok = 0, it1 = 0;
+    bool c1 = false;
+    for (it1 = 1; it1 <= max_iter; ++it1) {
+        k_an_mx<R><<<a->nblk, AN_NT, 0, s>>>(a->U1, L0.typ, (c2*)L0.rhs, total, sc, a->alpha, a->k);
+        an_count(a, 1);
+        if ((st = an_apply_inv<R>(a, cycles)) != HELM_OK) return st;
+        k_an_tprep<R><<<a->nblk, AN_NT, 0, s>>>((const c2*)L0.e, (c2*)L0.rhs, a->U1, L0.typ, n, L0.h, a->k, sums.d);
+        an_count(a, 1);
+        if ((st = sums.fetch(s, v)) != HELM_OK) return st;
+        est = std::sqrt(v[0]);
+        if ((st = an_apply_inv<R>(a, cycles)) != HELM_OK) return st;
+        k_an_tfin<R><<<a->nblk, AN_NT, 0, s>>>((const c2*)L0.e, a->U1, L0.typ, n, L0.h, a->alpha, a->k, sums.d);
+        an_count(a, 1);
+        AN_CK(cudaGetLastError());
+        if ((st = sums.fetch(s, v)) != HELM_OK) return st;
+        if (!(v[0] > 0.0) || !std::isfinite(v[0])) return HELM_ENONFINITE;
+        sc = 1.0 / std::sqrt(v[0]);
+        ok = (std::fabs(est - prev) <= tol * est) ? ok + 1 : 0;
+        prev = est;
+        if (ok >= 2) {
+            c1 = true;
+            break;
+        }
+    }
+    *smax = est;
+    // sigma_min: Lanczos on the real K = A^T D A
+    double* buf = nullptr;
+    if (cudaMalloc(&buf, 4 * total * sizeof(double)) != cudaSuccess) return HELM_ENOMEM;
+    struct Free {
+        double* p;
+        ~Free() { cudaFree(p); }
+    } fr{buf};
+    double *vp = buf, *vc = buf + total, *w = buf + 2 * total, *y = buf + 3 * total;
+    AN_CK(cudaMemsetAsync(vp, 0, total * sizeof(double), s));
+    k_an_lz_scale<<<a->nblk, AN_NT, 0, s>>>(vc, nullptr, 0.0, L0.typ, total, sums.d);
+    if ((st = sums.fetch(s, v)) != HELM_OK) return st;
+    k_an_lz_scale<<<a->nblk, AN_NT, 0, s>>>(vc, vc, 1.0 / std::sqrt(v[0]), L0.typ, total, sums.d);
+    an_count(a, 2);
+    const double dp = 1.0 / (a->alpha * a->alpha), de = 1.0 / (a->k * a->k);
+    std::vector<double> al, be(1, 0.0);
+    double beta = 0.0, theta = 0.0, tprev = 0.0;
+    int it2 = 0;
+    bool c2ok = false;
+    ok = 0;
+    for (it2 = 1; it2 <= max_iter; ++it2) {
+        k_an_lz_a<<<a->nblk, AN_NT, 0, s>>>(vc, y, L0.typ, n, L0.h, a->sigma, dp, de);
+        k_an_lz_at<<<a->nblk, AN_NT, 0, s>>>(y, vc, vp, beta, w, L0.typ, n, L0.h, a->sigma, sums.d);
+        an_count(a, 2);
+        if ((st = sums.fetch(s, v)) != HELM_OK) return st;
+        const double alpha = v[0];
+        k_an_lz_orth<<<a->nblk, AN_NT, 0, s>>>(w, vc, alpha, total, sums.d);
+        an_count(a, 1);
+        AN_CK(cudaGetLastError());
+        if ((st = sums.fetch(s, v)) != HELM_OK) return st;
+        al.push_back(alpha);
+        beta = std::sqrt(v[0]);
+        theta = tridiag_max(al, be, (int)al.size());
+        be.push_back(beta);
+        ok = (std::fabs(theta - tprev) <= tol * theta) ? ok + 1 : 0;
+        tprev = theta;
+        if (ok >= 2 || !(beta > 1e-300 * theta)) {
+            c2ok = true;
+            break;
+        }
+        // v_prev <- v, v <- w / beta (into the old v_prev buffer)
+        k_an_lz_scale<<<a->nblk, AN_NT, 0, s>>>(vp, w, 1.0 / beta, L0.typ, total, sums.d);
+        an_count(a, 1);
+        std::swap(vp, vc);
+    }
+    AN_CK(cudaStreamSynchronize(s));
+    if (!(theta > 0.0) || !std::isfinite(theta)) return HELM_ENONFINITE;
+    *smin = 1.0 / std::sqrt(theta);
+    *iters = std::max(std::min(it1, max_iter), std::min(it2, max_iter));
+    *conv = c1 && c2ok;
+    return HELM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1550,6 +2062,42 @@ helm_status helm_annulus_exit_times(helm_annulus* a, double c_tau, double tol, i
     }
     if (cudaStreamSynchronize(z->stream) != cudaSuccess) return done(HELM_ECUDA);
     return done(HELM_OK);
+}
+
+helm_status helm_annulus_spectral_radius(helm_annulus* a, int max_iters, double tol, int cycles, double* rho,
+                                         double* lambda_re, double* lambda_im, int* iters_done)
+{
+    if (!a || max_iters < 1 || !(tol > 0.0) || cycles < 1 || cycles > 64) return HELM_EINVAL;
+    double r = 0.0, lr = 0.0, li = 0.0;
+    int it = 0;
+    bool conv = false;
+    const helm_status st = (a->prec == HELM_PREC_FP64)
+        ? an_spectral<double>(a, max_iters, tol, cycles, &r, &lr, &li, &it, &conv)
+        : an_spectral<float>(a, max_iters, tol, cycles, &r, &lr, &li, &it, &conv);
+    if (st != HELM_OK) return st;
+    if (rho) *rho = r;
+    if (lambda_re) *lambda_re = lr;
+    if (lambda_im) *lambda_im = li;
+    if (iters_done) *iters_done = it;
+    return conv ? HELM_OK : HELM_MAXITER;
+}
+
+helm_status helm_annulus_condition(helm_annulus* a, int max_iters, double tol, int cycles, double* sigma_max,
+                                   double* sigma_min, double* cond, int* iters_done)
+{
+    if (!a || max_iters < 1 || !(tol > 0.0) || cycles < 1 || cycles > 64 || !(a->k > 0.0)) return HELM_EINVAL;
+    double smax = 0.0, smin = 0.0;
+    int it = 0;
+    bool conv = false;
+    const helm_status st = (a->prec == HELM_PREC_FP64)
+        ? an_singular<double>(a, max_iters, tol, cycles, &smax, &smin, &it, &conv)
+        : an_singular<float>(a, max_iters, tol, cycles, &smax, &smin, &it, &conv);
+    if (st != HELM_OK) return st;
+    if (sigma_max) *sigma_max = smax;
+    if (sigma_min) *sigma_min = smin;
+    if (cond) *cond = smax / smin;
+    if (iters_done) *iters_done = it;
+    return conv ? HELM_OK : HELM_MAXITER;
 }
 
 }  // extern "C"

@@ -148,3 +148,85 @@ def test_repeated_solve_is_bit_identical(B, cycle):
         assert st == runs[0][0] and iters == runs[0][1]
         assert np.array_equal(hist, runs[0][2])
         assert np.array_equal(u, runs[0][3])
+
+
+# ---------------------------------------------------------------------------
+# spectrum of G (Section 2.4's figure) against the oracle's dense matrices
+# ---------------------------------------------------------------------------
+
+def _dense_dominant(geo, k, alpha=None):
+    ev = np.linalg.eigvals(an.iteration_matrix(geo, k, alpha))
+    return ev[np.argmax(np.abs(ev))]
+
+
+@pytest.mark.parametrize("N", [16, 32])
+@pytest.mark.parametrize("k", [0.5, 1.0, 1.3])
+def test_spectral_radius_against_dense(B, N, k):
+    geo = an.geometry(N)
+    lam = _dense_dominant(geo, k)
+    plan = B.helm_annulus_create(N, 1.0, 0.15, k, B.HELM_PREC_FP64)
+    st, rho, lam_gpu, its = B.helm_annulus_spectral_radius(plan, 400, 1e-11, 24)
+    B.helm_annulus_destroy(plan)
+    assert st == B.HELM_OK, its
+    assert abs(rho - abs(lam)) <= 1e-6 * abs(lam), (rho, abs(lam))
+    assert abs(lam_gpu - lam) <= 1e-5 * abs(lam), (lam_gpu, lam)
+
+
+def test_spectral_radius_with_shift_and_mixed(B):
+    N, k = 32, 1.0
+    geo = an.geometry(N)
+    alpha = 1.5
+    want = abs(_dense_dominant(geo, k, alpha))
+    plan = B.helm_annulus_create(N, 1.0, 0.15, k, B.HELM_PREC_FP64)
+    B.helm_annulus_set_shift(plan, alpha)
+    st, rho, _, _ = B.helm_annulus_spectral_radius(plan, 400, 1e-11, 24)
+    B.helm_annulus_destroy(plan)
+    assert st == B.HELM_OK and abs(rho - want) <= 1e-6 * want
+    # complex64 cycles: the operator is applied to ~1e-7, rho to a few 1e-6
+    want = abs(_dense_dominant(geo, k))
+    plan = B.helm_annulus_create(N, 1.0, 0.15, k, B.HELM_PREC_MIXED)
+    st, rho, _, _ = B.helm_annulus_spectral_radius(plan, 400, 1e-7, 24)
+    B.helm_annulus_destroy(plan)
+    assert abs(rho - want) <= 2e-5 * want, (rho, want)
+
+
+@pytest.mark.parametrize("N", [16, 32])
+@pytest.mark.parametrize("k", [0.5, 1.2])
+def test_condition_number_against_dense(B, N, k):
+    geo = an.geometry(N)
+    smax, smin = an.singular_extremes(geo, k)
+    plan = B.helm_annulus_create(N, 1.0, 0.15, k, B.HELM_PREC_FP64)
+    st, gmax, gmin, cond, its = B.helm_annulus_condition(plan, 2000, 1e-11, 24)
+    B.helm_annulus_destroy(plan)
+    assert st == B.HELM_OK, its
+    assert abs(gmax - smax) <= 1e-6 * smax, (gmax, smax)
+    assert abs(gmin - smin) <= 1e-6 * smin, (gmin, smin)
+    assert abs(cond - smax / smin) <= 2e-6 * smax / smin
+
+
+def test_spectral_radius_crossing_follows_dense(B):
+    # the k where rho(G) = 1 on the 16-interval grid: the GPU's status on either side of the
+    # dense crossing
+    geo = an.geometry(16)
+    lo, hi = 0.5, 2.0
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        if abs(_dense_dominant(geo, mid)) < 1.0:
+            lo = mid
+        else:
+            hi = mid
+    kc = 0.5 * (lo + hi)
+    for k, below in ((0.97 * kc, True), (1.03 * kc, False)):
+        plan = B.helm_annulus_create(16, 1.0, 0.15, k, B.HELM_PREC_MIXED)
+        st, rho, _, _ = B.helm_annulus_spectral_radius(plan, 400, 1e-8, 16)
+        B.helm_annulus_destroy(plan)
+        assert (rho < 1.0) == below, (k, kc, rho)
+
+
+def test_spectral_arguments(B):
+    plan = B.helm_annulus_create(16, 1.0, 0.15, 0.0, B.HELM_PREC_FP64)
+    with pytest.raises(B.HelmError):
+        B.helm_annulus_condition(plan, 10, 1e-8, 4)          # k = 0: G is singular
+    with pytest.raises(B.HelmError):
+        B.helm_annulus_spectral_radius(plan, 10, 1e-8, 0)    # no cycle
+    B.helm_annulus_destroy(plan)
