@@ -6,7 +6,10 @@
 //  * multigrid level arrays (library memory): padded (n_l+2)^D with the x pitch rounded
 //    up to a multiple of 16 elements, so every row starts 128/256-byte aligned; the ring
 //    of e is kept zero (homogeneous Dirichlet for the Poisson increments, Eq. (2.7) for
-//    n >= 1), rhs rows use the same indexing (its ring is never read).
+//    n >= 1), rhs rows use the same indexing (its ring is never read).  In 3D each x-row
+//    is stored colour-split: its even-x nodes first (slot x/2), then its odd-x nodes (slot
+//    pitch/2 + x/2); one colour of a row, and the other colour of the rows around it, are
+//    then contiguous, so a red-black half-sweep reads and writes whole sectors (xslot).
 //  * complex numbers are interleaved {re, im} pairs (float2 / double2).  The inner
 //    operator is real, so the real and imaginary parts are two independent lanes of the
 //    same real stencil (Eq. (2.5) with p = 0: the two chains do not couple).
@@ -89,5 +92,13 @@ template <> struct C2<float>  { typedef float2  T; };
 template <> struct C2<double> { typedef double2 T; };
 
 __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Slot of node x within an x-row of a level array: x itself in 2D, the colour-split slot
+// in 3D (even x at x/2, odd x at pitch/2 + x/2; pitch is a multiple of 16).
+template <int D>
+__host__ __device__ __forceinline__ int xslot(int x, int pitch)
+{
+    return (D == 3) ? ((x & 1) ? (pitch >> 1) + (x >> 1) : (x >> 1)) : x;
+}
 
 }  // namespace helm

@@ -635,7 +635,7 @@ __device__ __forceinline__ R stage_plane3d(double2* Up, const double2* __restric
         if (gx <= n + 1 && gy <= n + 1) {
             v = uin[(long)gz * SP + (long)gy * S + gx];
             if (MODE == 1 && gx >= 1 && gx <= n && gy >= 1 && gy <= n && gz >= 1 && gz <= n) {
-                const c2 ev = e[(long)gz * PL + (long)gy * P + gx];
+                const c2 ev = e[(long)gz * PL + (long)gy * P + xslot<3>(gx, (int)P)];
                 v.x += Inner<R>::widen(ev.x);
                 v.y += Inner<R>::widen(ev.y);
                 if (own && lx >= 1 && lx <= T3X && ly >= 1 && ly <= T3Y)
@@ -697,7 +697,7 @@ __device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ ins
             const double2 w = Uc[o - 1], ea = Uc[o + 1], so = Uc[o - (T3X + 2)], no = Uc[o + (T3X + 2)];
             const double2 dn = U[sp][o], up = U[sn][o];
             const long ou = (long)z * SP + (long)gy * S + gx;
-            const long oe = (long)z * PL + (long)gy * P + gx;
+            const long oe = (long)z * PL + (long)gy * P + xslot<3>(gx, (int)P);
             if (MODE == 1) uout[ou] = c;
             const double2 fv = f[((long)(z - 1) * n + (gy - 1)) * n + (gx - 1)];
             double2 r;
@@ -802,7 +802,7 @@ __global__ void k_pack(const InstDesc* __restrict__ insts, int inst, const void*
         const int x = (int)(q % n) + 1;
         const int y = (int)((q / n) % n) + 1;
         const int z = (D == 3) ? (int)(q / ((long)n * n)) + 1 : 0;
-        dst[((D == 3) ? ((long)z * L.rows + y) : (long)y) * L.pitch + x] = s[q];
+        dst[((D == 3) ? ((long)z * L.rows + y) : (long)y) * L.pitch + xslot<D>(x, L.pitch)] = s[q];
     }
 }
 
@@ -823,7 +823,7 @@ __global__ void k_unpack(const InstDesc* __restrict__ insts, int inst, void* __r
         const int x = (int)(q % n) + 1;
         const int y = (int)((q / n) % n) + 1;
         const int z = (D == 3) ? (int)(q / ((long)n * n)) + 1 : 0;
-        d[q] = src[((D == 3) ? ((long)z * L.rows + y) : (long)y) * L.pitch + x];
+        d[q] = src[((D == 3) ? ((long)z * L.rows + y) : (long)y) * L.pitch + xslot<D>(x, L.pitch)];
     }
 }
 
@@ -874,7 +874,7 @@ __device__ __forceinline__ long lev_off(const LevelDesc& L, long q)
 {
     const int n = L.n;
     const long x = q % n + 1, y = (q / n) % n + 1, z = (D == 3) ? q / ((long)n * n) + 1 : 0;
-    return ((D == 3) ? (z * L.rows + y) : y) * (long)L.pitch + x;
+    return ((D == 3) ? (z * L.rows + y) : y) * (long)L.pitch + xslot<D>((int)x, L.pitch);
 }
 
 template <int D, typename R>

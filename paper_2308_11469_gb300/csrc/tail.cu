@@ -632,8 +632,8 @@ k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
             for (int j = 0; j < XJ; ++j) {
                 const int x = lane + 32 * j + 1;
                 if (x > N0) break;
-                Rr[srow + ix<N0>(x)] = gr[grow + x];
-                if (le) E[srow + ix<N0>(x)] = ge[grow + x];
+                Rr[srow + ix<N0>(x)] = gr[grow + xslot<3>(x, L0.pitch)];
+                if (le) E[srow + ix<N0>(x)] = ge[grow + xslot<3>(x, L0.pitch)];
             }
         }
     }
@@ -650,7 +650,7 @@ k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
         for (int j = 0; j < XJ; ++j) {
             const int x = lane + 32 * j + 1;
             if (x > N0) break;
-            go[grow + x] = E[srow + ix<N0>(x)];
+            go[grow + xslot<D>(x, L0.pitch)] = E[srow + ix<N0>(x)];
         }
     }
 }

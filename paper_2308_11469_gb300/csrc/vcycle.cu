@@ -19,8 +19,12 @@ namespace helm {
 namespace {
 
 template <int D>
+__device__ __forceinline__ size_t rowoff(const LevelDesc& L, int y, int z) {
+    return ((D == 3) ? ((size_t)z * L.rows + y) : (size_t)y) * (size_t)L.pitch;
+}
+template <int D>
 __device__ __forceinline__ size_t off(const LevelDesc& L, int x, int y, int z) {
-    return ((D == 3) ? ((size_t)z * L.rows + y) : (size_t)y) * (size_t)L.pitch + x;
+    return rowoff<D>(L, y, z) + xslot<D>(x, L.pitch);
 }
 
 template <typename T> __device__ __forceinline__ T cz() { T v; v.x = 0; v.y = 0; return v; }
@@ -61,14 +65,16 @@ k_rbgs(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
         const int xc = (((xa + y + z) & 1) == color) ? xa : xa + 1;
         const int xo = (xc == xa) ? xa + 1 : xa;
         if (xc <= n) {
-            const long o = (long)off<D>(L, xc, y, z);
+            const long rb = (long)rowoff<D>(L, y, z);
+            const long o = rb + xslot<D>(xc, L.pitch);
             const c2 rr = r[o];
             c2 v;
             if (zi) {                                   // all neighbours are zero
                 v.x = -h2 * rr.x * inv;
                 v.y = -h2 * rr.y * inv;
             } else {
-                const c2 a = e[o - 1], b = e[o + 1], c = e[o - P], d = e[o + P];
+                const c2 a = e[rb + xslot<D>(xc - 1, L.pitch)], b = e[rb + xslot<D>(xc + 1, L.pitch)];
+                const c2 c = e[o - P], d = e[o + P];
                 R sx = a.x + b.x + c.x + d.x;
                 R sy = a.y + b.y + c.y + d.y;
                 if (D == 3) {
@@ -151,8 +157,11 @@ k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
                 const R wy = (dy == 0) ? (R)2 : (R)1;
                 for (int dx = -1; dx <= 1; ++dx) {
                     const R w = wz * wy * ((dx == 0) ? (R)2 : (R)1);
-                    const long o = (long)off<D>(F, 2 * X + dx, 2 * Y + dy, 2 * Z + dz);
-                    const c2 c = e[o], a = e[o - 1], b = e[o + 1], u = e[o - P], d = e[o + P];
+                    const long rb = (long)rowoff<D>(F, 2 * Y + dy, 2 * Z + dz);
+                    const int x = 2 * X + dx;
+                    const long o = rb + xslot<D>(x, F.pitch);
+                    const c2 c = e[o], a = e[rb + xslot<D>(x - 1, F.pitch)], b = e[rb + xslot<D>(x + 1, F.pitch)];
+                    const c2 u = e[o - P], d = e[o + P];
                     R sx = a.x + b.x + u.x + d.x;
                     R sy = a.y + b.y + u.y + d.y;
                     if (D == 3) {
@@ -216,9 +225,9 @@ k_prolong(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
         for (int iz = 0; iz < nz; ++iz)
 #pragma unroll
             for (int iy = 0; iy < 2; ++iy) {
-                const size_t oc = off<D>(C, p, iy ? y1 : y0, iz ? z1 : z0);
-                cv[iz][iy][0] = ce[oc];
-                cv[iz][iy][1] = ce[oc + 1];
+                const size_t rc = rowoff<D>(C, iy ? y1 : y0, iz ? z1 : z0);
+                cv[iz][iy][0] = ce[rc + xslot<D>(p, C.pitch)];
+                cv[iz][iy][1] = ce[rc + xslot<D>(p + 1, C.pitch)];
             }
 #pragma unroll
         for (int half = 0; half < 2; ++half) {

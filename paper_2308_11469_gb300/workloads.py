@@ -1,6 +1,6 @@
 """Timings of the method's other workloads on one GPU (one JSON line each).
 
-    python -m paper_2308_11469_gb300.workloads [--only cavity63,cube255,batch512,damped1023,exit1023,spectral1023,annulus1024]
+    python -m paper_2308_11469_gb300.workloads [--only cavity63,cube255,batch512,damped1023,exit1023,spectral1023,annulus1024,annulus_spectrum]
     python -m paper_2308_11469_gb300.workloads --replay cube255|cavity1023 [--steps 4] [--fp64]
 
 * cavity63  63x63 unit-square cavity, plane-wave wall data (theta = pi/6), f = 0:
@@ -17,6 +17,8 @@
 * spectral1023  rho(G) against k by GPU power iteration on the 1023^2 cavity.
 * annulus1024  the annular problem (square with a square hole, Robin outer edge) on a
             1024-interval grid, k = 0.8: mixed and FP64 solves; exit / local time, k_*^A.
+* annulus_spectrum  rho(G) and cond(G) of that problem's iteration against k on grids of
+            16 ... 1024 intervals, and the k where rho(G) = 1.
 
 Device time comes from CUDA events on the current stream around each call.  The inputs
 are the seeded generators of ``inputs``; result accuracy against exact discrete
@@ -277,9 +279,48 @@ def annulus1024(dev):
     return rows
 
 
+def annulus_spectrum(dev):
+    """Section 2.4's figure on the GPU: rho(G) and cond(G) against k for the square
+    [-1/2, 1/2]^2 with the hole [-0.15, 0.15]^2 on grids of 16 ... 1024 intervals (power
+    iteration and Lanczos with multigrid cycles as A^{-1}), and the k where rho(G) crosses 1
+    (bisection on the power-iteration estimate)."""
+    import torch  # noqa: F401
+    rows = []
+    for N, prec, cyc in ((16, B.HELM_PREC_FP64, 24), (32, B.HELM_PREC_FP64, 24), (64, B.HELM_PREC_FP64, 24),
+                         (256, B.HELM_PREC_MIXED, 12), (1024, B.HELM_PREC_MIXED, 12)):
+        for k in (0.25, 0.5, 0.75, 1.0, 1.25, 1.5):
+            plan = B.helm_annulus_create(N, 1.0, 0.15, k, prec)
+            ms, (st, rho, lam, its) = _dev_ms(lambda: B.helm_annulus_spectral_radius(plan, 300, 1e-8, cyc), 1)
+            row = {"workload": "annulus_spectrum", "N": N, "h": 1.0 / N, "k": k,
+                   "prec": "fp64" if prec == B.HELM_PREC_FP64 else "mixed", "cycles": cyc,
+                   "rho": rho, "lambda": [lam.real, lam.imag], "rho_iters": its,
+                   "rho_status": B.helm_status_str(st), "rho_ms": ms}
+            if N <= 256:
+                ms2, (st2, smax, smin, cond, its2) = _dev_ms(
+                    lambda: B.helm_annulus_condition(plan, 3000, 1e-8, cyc), 1)
+                row.update({"sigma_max": smax, "sigma_min": smin, "cond": cond, "cond_iters": its2,
+                            "cond_status": B.helm_status_str(st2), "cond_ms": ms2})
+            B.helm_annulus_destroy(plan)
+            rows.append(row)
+        # crossing of rho = 1 by bisection in k
+        lo, hi = 0.5, 2.0
+        for _ in range(20 if N <= 256 else 12):
+            mid = 0.5 * (lo + hi)
+            plan = B.helm_annulus_create(N, 1.0, 0.15, mid, prec)
+            st, rho, _, _ = B.helm_annulus_spectral_radius(plan, 300, 1e-8, cyc)
+            B.helm_annulus_destroy(plan)
+            if rho < 1.0:
+                lo = mid
+            else:
+                hi = mid
+        rows.append({"workload": "annulus_spectrum_crossing", "N": N, "h": 1.0 / N,
+                     "k_rho_eq_1": 0.5 * (lo + hi), "bracket": [lo, hi]})
+    return rows
+
+
 WORKLOADS = {"cavity63": cavity63, "cube255": cube255, "batch512": batch512,
              "damped1023": damped1023, "exit1023": exit1023, "spectral1023": spectral1023,
-             "annulus1024": annulus1024}
+             "annulus1024": annulus1024, "annulus_spectrum": annulus_spectrum}
 
 
 def main(argv=None) -> int:
