@@ -23,6 +23,7 @@
 #include "launch.h"
 #include "pdl.cuh"
 #include "fp_bits.cuh"
+#include "fixed_lap.cuh"
 #include "sweep2d.cuh"
 
 namespace helm {
@@ -259,6 +260,72 @@ __device__ __forceinline__ double2 helm_resid2d(double2 c, double2 a, double2 b,
     return r;
 }
 
+// The same residual with the Laplacian numerator summed exactly in fixed point
+// (fixed_lap.cuh): FC, FA, FB, FD, FU are the fixed-point images (scale emax) of the node
+// and its four neighbours, c the node in FP64: f - k^2 u - (numerator) / h^2.
+template <bool DAMP>
+__device__ __forceinline__ double2 helm_resid_fx(double2 c, long long lx, long long ly, double2 fv, double mih2,
+                                                 double mk2, double damp, int emax)
+{
+    double2 r;
+    r.x = fma(fx_to_double(lx, emax), mih2, fma(c.x, mk2, fv.x));
+    r.y = fma(fx_to_double(ly, emax), mih2, fma(c.y, mk2, fv.y));
+    if constexpr (DAMP) {
+        r.x = fma(c.y, damp, r.x);
+        r.y = fma(c.x, -damp, r.y);
+    }
+    return r;
+}
+
+template <bool DAMP>
+__device__ __forceinline__ double2 helm_resid2d_fx(double2 c, longlong2 FC, longlong2 FA, longlong2 FB,
+                                                   longlong2 FD, longlong2 FU, double2 fv, double mih2,
+                                                   double mk2, double damp, int emax)
+{
+    const long long lx = ((FA.x + FB.x) + (FD.x + FU.x)) - 4 * FC.x;
+    const long long ly = ((FA.y + FB.y) + (FD.y + FU.y)) - 4 * FC.y;
+    return helm_resid_fx<DAMP>(c, lx, ly, fv, mih2, mk2, damp, emax);
+}
+
+// scale exponent of a window from its largest biased exponent (see fixed_lap.cuh); -1:
+// no fixed-point scale (a value above 2^1007, an infinity or a NaN)
+__device__ __forceinline__ int fx_scale(int emax_raw)
+{
+    return emax_raw > FX_EMAX ? -1 : max(emax_raw, FX_EMIN);
+}
+
+__device__ __forceinline__ longlong2 fx_fix2(double2 v, int emax)
+{
+    return make_longlong2(fx_fix(v.x, emax), fx_fix(v.y, emax));
+}
+
+__device__ __forceinline__ int fx_exp2(double2 v) { return max(fx_exp(v.x), fx_exp(v.y)); }
+
+// largest of the threads' exponents (one shared word per warp; the caller's barrier
+// follows before any thread reads the result)
+template <int NT>
+__device__ __forceinline__ int block_max_exp(int ex, int* sx)
+{
+    ex = __reduce_max_sync(0xffffffffu, ex);
+    if ((threadIdx.x & 31) == 0) sx[threadIdx.x >> 5] = ex;
+    __syncthreads();
+    int m = sx[0];
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) m = max(m, sx[w]);
+    return m;
+}
+
+// The residual window of a tile is its (TX + 2) x (TY + 2) nodes; its 1-node ring has
+// 2 (TX + 2) + 2 TY nodes, numbered: top row, bottom row, left column, right column.
+template <int TX, int TY>
+__device__ __forceinline__ void ring_node(int t, int& lx, int& ly)
+{
+    if (t < TX + 2) { lx = t; ly = 0; }
+    else if (t < 2 * (TX + 2)) { lx = t - (TX + 2); ly = TY + 1; }
+    else if (t < 2 * (TX + 2) + TY) { lx = 0; ly = t - 2 * (TX + 2) + 1; }
+    else { lx = TX + 1; ly = t - 2 * (TX + 2) - TY + 1; }
+}
+
 // |v|^2 of an inner-precision complex value, rounded the same way in every kernel
 template <typename C>
 __device__ __forceinline__ auto abs2(C v) -> decltype(v.x) { return fma(v.y, v.y, v.x * v.x); }
@@ -294,6 +361,76 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
     const int P = L0.pitch;
     const int x0 = 1 + item.tx * T2, y0 = 1 + item.ty * T2Y;
     R emax2 = 0;
+    if constexpr (MODE == 1) {
+        // u_{N+1} = u_N + e_N: each thread's residual nodes stay in registers (FP64), the
+        // window's ring goes to threads 0 .. RING - 1; the window's largest exponent sets the
+        // fixed-point scale of the exact Laplacian numerators
+        constexpr int KY = T2Y / 8, RING = 2 * (T2 + 2) + 2 * T2Y;
+        static_assert(RING <= NTH, "one ring node per thread");
+        __shared__ int sx[NTH / 32];
+        const int lx = (threadIdx.x & 31) + 1;
+        double2 cv[KY];
+        int ex = 0;
+#pragma unroll
+        for (int k = 0; k < KY; ++k) {
+            const int ly = (threadIdx.x >> 5) + 8 * k + 1;
+            const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+            double2 v = make_double2(0.0, 0.0);
+            if (gx <= n + 1 && gy <= n + 1) v = uin[gy * S + gx];
+            if (gx <= n && gy <= n) {
+                const c2 ev = e[gy * P + gx];
+                v.x += Inner<R>::widen(ev.x);
+                v.y += Inner<R>::widen(ev.y);
+                emax2 = fmax(emax2, abs2(ev));
+            }
+            cv[k] = v;
+            ex = max(ex, fx_exp2(v));
+        }
+        int rlx = 0, rly = 0;
+        double2 rv = make_double2(0.0, 0.0);
+        if (threadIdx.x < RING) {
+            ring_node<T2, T2Y>(threadIdx.x, rlx, rly);
+            const int gx = x0 - 1 + rlx, gy = y0 - 1 + rly;
+            if (gx <= n + 1 && gy <= n + 1) rv = uin[gy * S + gx];
+            if (gx >= 1 && gx <= n && gy >= 1 && gy <= n) {
+                const c2 ev = e[gy * P + gx];
+                rv.x += Inner<R>::widen(ev.x);
+                rv.y += Inner<R>::widen(ev.y);
+            }
+            ex = max(ex, fx_exp2(rv));
+        }
+        const int emx = fx_scale(block_max_exp<NTH>(ex, sx));    // uniform over the CTA
+        longlong2* UF = reinterpret_cast<longlong2*>(U);
+#pragma unroll
+        for (int k = 0; k < KY; ++k) {
+            const int o = ((threadIdx.x >> 5) + 8 * k + 1) * (T2 + 2) + lx;
+            UF[o] = fx_fix2(cv[k], emx);
+        }
+        if (threadIdx.x < RING) UF[rly * (T2 + 2) + rlx] = fx_fix2(rv, emx);
+        __syncthreads();
+        const double mih2 = -I.ih2, mk2 = -I.k2;
+        const double damp = I.damp;
+        R r2 = 0;
+#pragma unroll
+        for (int k = 0; k < KY; ++k) {
+            const int ly = (threadIdx.x >> 5) + 8 * k + 1;
+            const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+            if (gx > n || gy > n) continue;
+            const int o = ly * (T2 + 2) + lx;
+            const double2 c = cv[k];
+            uout[gy * S + gx] = c;
+            const double2 fv = f[(size_t)(gy - 1) * n + (gx - 1)];
+            const double2 r = (emx >= 0)
+                ? helm_resid2d_fx<DAMP>(c, UF[o], UF[o - 1], UF[o + 1], UF[o - (T2 + 2)], UF[o + (T2 + 2)], fv,
+                                        mih2, mk2, damp, emx)
+                : make_double2(fx_nan(), fx_nan());
+            const c2 ri = Inner<R>::from(r);
+            rhs[gy * P + gx] = ri;
+            r2 += abs2(ri);
+        }
+        tile_done<R>(I, stp, item.ty * I.res_tx + item.tx, r2, emax2, MODE, st, c);
+        return;
+    }
     constexpr int NSTAGE = ((T2 + 2) * (T2Y + 2) + NTH - 1) / NTH;
     // fixed trip count, fully unrolled: all loads of the tile are issued before their uses
 #pragma unroll
@@ -549,25 +686,67 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
         cp_async_wait_all();
         __syncthreads();
     }
-    // u_{N+1} = u_N + e_N on the interior nodes of the u window
-    for (int q = threadIdx.x; q < UW * UH; q += NTU) {
-        const int gx = x0 - 1 + q % UW, gy = y0 - 1 + q / UW;
-        if (gx < 1 || gx > n || gy < 1 || gy > n) continue;
-        const int ex = gx - gx0, ey = gy - gy0;
-        const c2 ev = (((ex + ey + cpar) & 1) ? E1 : E0)[PL::at(ex, ey)];
-        double2 v = U[q];
-        v.x += Inner<R>::widen(ev.x);
-        v.y += Inner<R>::widen(ev.y);
-        U[q] = v;
+    // u_{N+1} = u_N + e_N on the window (as k_residual2d forms it): the residual nodes of
+    // each map thread in registers, the ring by the first threads; the window's largest
+    // exponent sets the scale of the exact fixed-point Laplacian numerators
+    constexpr int KY = TY / 8, RING = 2 * (TX + 2) + 2 * TY, RJ = (RING + NTU - 1) / NTU;
+    __shared__ int sx[NWU];
+    double2 cv[VT][KY];
+    int exq = 0;
+    auto upd = [&](int lxw, int lyw) -> double2 {   // window node (lxw, lyw): u_N (+ e_N inside)
+        const int gx = x0 - 1 + lxw, gy = y0 - 1 + lyw;
+        double2 v = U[lyw * UW + lxw];
+        if (gx >= 1 && gx <= n && gy >= 1 && gy <= n) {
+            const int ex = gx - gx0, ey = gy - gy0;
+            const c2 ev = (((ex + ey + cpar) & 1) ? E1 : E0)[PL::at(ex, ey)];
+            v.x += Inner<R>::widen(ev.x);
+            v.y += Inner<R>::widen(ev.y);
+        }
+        return v;
+    };
+#pragma unroll
+    for (int v = 0; v < VT; ++v) {
+        const int t = threadIdx.x + NTU * v;
+#pragma unroll
+        for (int k = 0; k < KY; ++k) {
+            cv[v][k] = upd((t & 31) + 1, (t >> 5) + 8 * k + 1);
+            exq = max(exq, fx_exp2(cv[v][k]));
+        }
     }
+    double2 rv[RJ];
+    int rq[RJ];
+#pragma unroll
+    for (int j = 0; j < RJ; ++j) {
+        const int t = threadIdx.x + NTU * j;
+        rq[j] = -1;
+        rv[j] = make_double2(0.0, 0.0);
+        if (t < RING) {
+            int rlx, rly;
+            ring_node<TX, TY>(t, rlx, rly);
+            rv[j] = upd(rlx, rly);
+            rq[j] = rly * UW + rlx;
+            exq = max(exq, fx_exp2(rv[j]));
+        }
+    }
+    // its barrier also ends the reads of U; uniform over the CTA
+    const int emx = fx_scale(block_max_exp<NTU>(exq, sx));
+    longlong2* UF = reinterpret_cast<longlong2*>(U);
+#pragma unroll
+    for (int v = 0; v < VT; ++v) {
+        const int t = threadIdx.x + NTU * v;
+#pragma unroll
+        for (int k = 0; k < KY; ++k) UF[((t >> 5) + 8 * k + 1) * UW + (t & 31) + 1] = fx_fix2(cv[v][k], emx);
+    }
+#pragma unroll
+    for (int j = 0; j < RJ; ++j)
+        if (rq[j] >= 0) UF[rq[j]] = fx_fix2(rv[j], emx);
     __syncthreads();
     // r_{N+1}: thread t of the residual kernel's map takes the nodes (t mod 32, t / 32 + 8 k)
     // of the tile; real thread j stands for the map's threads j + NTU v, v < VT
     double2* __restrict__ uout = I.u[(sv.it + 1) & 1];
     c2* __restrict__ rhs = (c2*)lev_rhs(L, 0, sv.it + 1);
     const double2* __restrict__ f = I.f;
-    const double mih2 = -I.ih2;
-    const double mcdiag = -I.cdiag;
+    const double mih2 = -I.ih2, mk2 = -I.k2;
     const double damp = I.damp;
     R r2[VT], em[VT];
 #pragma unroll
@@ -582,11 +761,13 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
             const int gx = x0 + lx - 1, gy = y0 + ly - 1;
             if (gx > n || gy > n) continue;
             const int o = ly * UW + lx;
-            const double2 c = U[o];
-            const double2 a = U[o - 1], b = U[o + 1], d = U[o - UW], u = U[o + UW];
+            const double2 c = cv[v][k];
             uout[(size_t)gy * S + gx] = c;
             const double2 fv = f[(size_t)(gy - 1) * n + (gx - 1)];
-            const double2 r = helm_resid2d<DAMP>(c, a, b, d, u, fv, mih2, mcdiag, damp);
+            const double2 r = (emx >= 0)
+                ? helm_resid2d_fx<DAMP>(c, UF[o], UF[o - 1], UF[o + 1], UF[o - UW], UF[o + UW], fv, mih2, mk2,
+                                        damp, emx)
+                : make_double2(fx_nan(), fx_nan());
             const c2 ri = Inner<R>::from(r);
             rhs[(size_t)gy * P + gx] = ri;
             r2[v] += abs2(ri);
@@ -737,16 +918,134 @@ __device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ ins
     else tile_done<R>(I, stp, tile, r2, emax2, MODE, st, c);
 }
 
+// Every outer step (mode 1): the column's planes go through the ring in fixed point
+// (fixed_lap.cuh), each plane on the scale of its own largest exponent; the numerator of
+// plane z is summed on the largest scale of planes z - 1, z, z + 1 (the other planes'
+// values shifted down to it), so every node's numerator is exact up to the truncations.
+// Thread t stages the interior node (t mod 32, t / 32) of each plane and keeps it in FP64
+// for its own residual; threads below the ring size stage one ring node each.
+template <typename R, bool DAMP>
+__device__ __forceinline__ void residual3d_tile_fx(const InstDesc* __restrict__ insts,
+                                                   InstState* __restrict__ st, const ResItem item,
+                                                   longlong2 (*U)[P3], int* sx, const StepCtl& c)
+{
+    typedef typename C2<R>::T c2;
+    static_assert(T3X * T3Y == NTH, "one interior node of a plane per thread");
+    constexpr int RING = 2 * (T3X + 2) + 2 * T3Y;
+    static_assert(RING <= NTH, "one ring node per thread");
+    const InstDesc& I = insts[item.inst];
+    const int n = I.n;
+    const long S = n + 2;
+    const long SP = S * S;
+    InstState* stp = st + item.inst;
+    const InstState s = *stp;
+    if (s.status != HELM_ST_ACTIVE) {           // uniform over the CTA
+        if (c.ctrl && item.tx == 0 && item.ty == 0 && item.tz == 0) step_arrive(st, c);
+        return;
+    }
+    const double2* __restrict__ uin = (s.it & 1) ? I.u[1] : I.u[0];
+    double2* __restrict__ uout = (double2*)((s.it & 1) ? I.u[0] : I.u[1]);
+    const double2* __restrict__ f = I.f;
+    const LevelDesc L0 = I.lev[0];
+    const c2* __restrict__ e = (const c2*)L0.e;
+    c2* __restrict__ rhs = (c2*)lev_rhs(L0, 0, s.it + 1);
+    const long P = L0.pitch;
+    const long PL = (long)L0.pitch * L0.rows;
+    const double mih2 = -I.ih2, mk2 = -I.k2;
+    const double damp = I.damp;
+    const int x0 = 1 + item.tx * T3X, y0 = 1 + item.ty * T3Y, z0 = 1 + item.tz * T3Z;
+    const int z1 = min(z0 + T3Z - 1, n);
+    const int lx = (threadIdx.x & 31) + 1, ly = (threadIdx.x >> 5) + 1;
+    const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+    const bool live = gx <= n && gy <= n;
+    const int o = ly * (T3X + 2) + lx;
+    int rlx = 0, rly = 0;
+    if (threadIdx.x < RING) ring_node<T3X, T3Y>(threadIdx.x, rlx, rly);
+    const int ro = rly * (T3X + 2) + rlx;
+    R r2 = 0, emax2 = 0;
+    // u_{N+1} at window node (wx, wy) of plane gz: u_N, plus e_N at interior nodes
+    auto node = [&](int wx, int wy, int gz, bool own) -> double2 {
+        const int nx = x0 - 1 + wx, ny = y0 - 1 + wy;
+        double2 v = make_double2(0.0, 0.0);
+        if (nx <= n + 1 && ny <= n + 1 && gz <= n + 1) {
+            v = uin[(long)gz * SP + (long)ny * S + nx];
+            if (nx >= 1 && nx <= n && ny >= 1 && ny <= n && gz >= 1 && gz <= n) {
+                const c2 ev = e[(long)gz * PL + (long)ny * P + xslot<3>(nx, (int)P)];
+                v.x += Inner<R>::widen(ev.x);
+                v.y += Inner<R>::widen(ev.y);
+                if (own) emax2 = fmax(emax2, abs2(ev));
+            }
+        }
+        return v;
+    };
+    // stage plane gz into ring slot `slot`: returns its scale exponent (-1: none); the
+    // thread's own node in FP64 goes to `mine`
+    auto stage = [&](int slot, int gz, bool own, double2& mine) -> int {
+        mine = node(lx, ly, gz, own && live);
+        double2 rv = make_double2(0.0, 0.0);
+        if (threadIdx.x < RING) rv = node(rlx, rly, gz, false);
+        const int ep = fx_scale(block_max_exp<NTH>(max(fx_exp2(mine), fx_exp2(rv)), sx));
+        U[slot][o] = fx_fix2(mine, ep);
+        if (threadIdx.x < RING) U[slot][ro] = fx_fix2(rv, ep);
+        return ep;
+    };
+    int ep[3];
+    double2 cur, nxt, dummy;
+    ep[0] = stage(0, z0 - 1, false, dummy);
+    __syncthreads();                            // sx is reused by the next stage
+    ep[1] = stage(1, z0, true, cur);
+    int sp = 0, sc = 1, sn = 2;                 // ring slots of planes z-1, z, z+1
+    for (int z = z0; z <= z1; ++z) {
+        __syncthreads();                        // sx reuse; the oldest slot is free
+        ep[sn] = stage(sn, z + 1, z + 1 <= z1, nxt);
+        __syncthreads();
+        if (live) {
+            const int em = max(max(ep[sp], ep[sc]), ep[sn]);
+            double2 r;
+            if (ep[sp] >= 0 && ep[sc] >= 0 && ep[sn] >= 0) {
+                // shifts to the common scale (arithmetic, so each rounds toward -inf once);
+                // |in-plane part| < 10 * 2^58 and the total < 12 * 2^58 < 2^62
+                const int dc = min(em - ep[sc], 63), dd = min(em - ep[sp], 63), du = min(em - ep[sn], 63);
+                const longlong2* Uc = U[sc];
+                const longlong2 C = Uc[o], W = Uc[o - 1], E = Uc[o + 1];
+                const longlong2 So = Uc[o - (T3X + 2)], No = Uc[o + (T3X + 2)];
+                const longlong2 Dn = U[sp][o], Up = U[sn][o];
+                const long long lx_ = ((((W.x + E.x) + (So.x + No.x)) - 6 * C.x) >> dc) + ((Dn.x >> dd) + (Up.x >> du));
+                const long long ly_ = ((((W.y + E.y) + (So.y + No.y)) - 6 * C.y) >> dc) + ((Dn.y >> dd) + (Up.y >> du));
+                const double2 fv = f[((long)(z - 1) * n + (gy - 1)) * n + (gx - 1)];
+                r = helm_resid_fx<DAMP>(cur, lx_, ly_, fv, mih2, mk2, damp, em);
+            } else {
+                r = make_double2(fx_nan(), fx_nan());
+            }
+            uout[(long)z * SP + (long)gy * S + gx] = cur;
+            const c2 ri = Inner<R>::from(r);
+            rhs[(long)z * PL + (long)gy * P + xslot<3>(gx, (int)P)] = ri;
+            r2 += abs2(ri);
+        }
+        cur = nxt;
+        const int t = sp;
+        sp = sc;
+        sc = sn;
+        sn = t;
+    }
+    const int tile = (item.tz * I.res_ty + item.ty) * I.res_tx + item.tx;
+    tile_done<R>(I, stp, tile, r2, emax2, 1, st, c);
+}
+
 template <typename R, int MODE, bool DAMP>
 __global__ void __launch_bounds__(NTH, 4)
 k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
              const ResItem* __restrict__ items, int nitems, StepCtl c)
 {
     __shared__ double2 U[3][P3];
+    __shared__ int sx[NTH / 32];
     pdl_wait();
     pdl_trigger();
     for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
-        residual3d_tile<R, MODE, DAMP>(insts, st, items[t], U, c);
+        if constexpr (MODE == 1)
+            residual3d_tile_fx<R, DAMP>(insts, st, items[t], reinterpret_cast<longlong2(*)[P3]>(U), sx, c);
+        else
+            residual3d_tile<R, MODE, DAMP>(insts, st, items[t], U, c);
         __syncthreads();
     }
 }
