@@ -796,6 +796,10 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
 // three-plane ring of shared memory (1-node halo in x and y)
 // ---------------------------------------------------------------------------
 constexpr int T3X = 32, T3Y = 8, T3Z = 16;
+// resident CTAs per SM of the 3D residual (40 registers at 6): at 255^3 477 -> 396 us per
+// launch against 4 CTAs of 64 registers; fetching each plane one plane ahead into
+// registers measured slower (412 / 432 / 485 us at 4 / 5 / 6 CTAs)
+constexpr int RES3D_CTAS = 6;
 constexpr int P3 = (T3X + 2) * (T3Y + 2);
 
 template <typename R, int MODE>
@@ -1033,7 +1037,7 @@ __device__ __forceinline__ void residual3d_tile_fx(const InstDesc* __restrict__ 
 }
 
 template <typename R, int MODE, bool DAMP>
-__global__ void __launch_bounds__(NTH, 4)
+__global__ void __launch_bounds__(NTH, RES3D_CTAS)
 k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
              const ResItem* __restrict__ items, int nitems, StepCtl c)
 {
