@@ -243,26 +243,11 @@ __device__ void tile_done(const InstDesc& I, InstState* stp, int tile, T ta0, T 
     instance_last<1>(I, stp, mode, st_all, c, sa, sm);
 }
 
-// r = f - (Delta_h + k^2 + i p) u at one 2D node from its value c and its four neighbours
-// (a, b west / east, d, u south / north): f - cdiag u - (sum of the neighbours) / h^2, and
-// for DAMP the coupling - i p u.
-template <bool DAMP>
-__device__ __forceinline__ double2 helm_resid2d(double2 c, double2 a, double2 b, double2 d, double2 u,
-                                                double2 fv, double mih2, double mcdiag, double damp)
-{
-    double2 r;
-    r.x = fma((a.x + b.x) + (d.x + u.x), mih2, fma(c.x, mcdiag, fv.x));
-    r.y = fma((a.y + b.y) + (d.y + u.y), mih2, fma(c.y, mcdiag, fv.y));
-    if constexpr (DAMP) {
-        r.x = fma(c.y, damp, r.x);
-        r.y = fma(c.x, -damp, r.y);
-    }
-    return r;
-}
-
-// The same residual with the Laplacian numerator summed exactly in fixed point
-// (fixed_lap.cuh): FC, FA, FB, FD, FU are the fixed-point images (scale emax) of the node
-// and its four neighbours, c the node in FP64: f - k^2 u - (numerator) / h^2.
+// r = f - (Delta_h + k^2 + i p) u at one node: f - k^2 u - (numerator) / h^2, the
+// Laplacian numerator (sum of the neighbours - 2D u) summed exactly in fixed point
+// (fixed_lap.cuh) on the scale emax, u in FP64, and for DAMP the coupling - i p u.
+// helm_resid2d_fx: FC, FA, FB, FD, FU are the fixed-point images of the 2D node and its
+// four neighbours (a, b west / east, d, u south / north).
 template <bool DAMP>
 __device__ __forceinline__ double2 helm_resid_fx(double2 c, long long lx, long long ly, double2 fv, double mih2,
                                                  double mk2, double damp, int emax)
@@ -361,131 +346,84 @@ __device__ __forceinline__ void residual2d_tile(const InstDesc* __restrict__ ins
     const int P = L0.pitch;
     const int x0 = 1 + item.tx * T2, y0 = 1 + item.ty * T2Y;
     R emax2 = 0;
-    if constexpr (MODE == 1) {
-        // u_{N+1} = u_N + e_N: each thread's residual nodes stay in registers (FP64), the
-        // window's ring goes to threads 0 .. RING - 1; the window's largest exponent sets the
-        // fixed-point scale of the exact Laplacian numerators
-        constexpr int KY = T2Y / 8, RING = 2 * (T2 + 2) + 2 * T2Y;
-        static_assert(RING <= NTH, "one ring node per thread");
-        __shared__ int sx[NTH / 32];
-        const int lx = (threadIdx.x & 31) + 1;
-        double2 cv[KY];
-        int ex = 0;
+    // The window's values: u_{N+1} = u_N + e_N (mode 1) or the current iterate (mode 0).
+    // Each thread's residual nodes stay in registers (FP64), the window's ring goes to
+    // threads 0 .. RING - 1; the window's largest exponent sets the fixed-point scale of the
+    // exact Laplacian numerators.
+    constexpr int KY = T2Y / 8, RING = 2 * (T2 + 2) + 2 * T2Y;
+    static_assert(RING <= NTH, "one ring node per thread");
+    __shared__ int sx[NTH / 32];
+    const int lx = (threadIdx.x & 31) + 1;
+    double2 cv[KY];
+    int ex = 0;
 #pragma unroll
-        for (int k = 0; k < KY; ++k) {
-            const int ly = (threadIdx.x >> 5) + 8 * k + 1;
-            const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-            double2 v = make_double2(0.0, 0.0);
-            if (gx <= n + 1 && gy <= n + 1) v = uin[gy * S + gx];
-            if (gx <= n && gy <= n) {
-                const c2 ev = e[gy * P + gx];
-                v.x += Inner<R>::widen(ev.x);
-                v.y += Inner<R>::widen(ev.y);
-                emax2 = fmax(emax2, abs2(ev));
-            }
-            cv[k] = v;
-            ex = max(ex, fx_exp2(v));
-        }
-        int rlx = 0, rly = 0;
-        double2 rv = make_double2(0.0, 0.0);
-        if (threadIdx.x < RING) {
-            ring_node<T2, T2Y>(threadIdx.x, rlx, rly);
-            const int gx = x0 - 1 + rlx, gy = y0 - 1 + rly;
-            if (gx <= n + 1 && gy <= n + 1) rv = uin[gy * S + gx];
-            if (gx >= 1 && gx <= n && gy >= 1 && gy <= n) {
-                const c2 ev = e[gy * P + gx];
-                rv.x += Inner<R>::widen(ev.x);
-                rv.y += Inner<R>::widen(ev.y);
-            }
-            ex = max(ex, fx_exp2(rv));
-        }
-        const int emx = fx_scale(block_max_exp<NTH>(ex, sx));    // uniform over the CTA
-        longlong2* UF = reinterpret_cast<longlong2*>(U);
-#pragma unroll
-        for (int k = 0; k < KY; ++k) {
-            const int o = ((threadIdx.x >> 5) + 8 * k + 1) * (T2 + 2) + lx;
-            UF[o] = fx_fix2(cv[k], emx);
-        }
-        if (threadIdx.x < RING) UF[rly * (T2 + 2) + rlx] = fx_fix2(rv, emx);
-        __syncthreads();
-        const double mih2 = -I.ih2, mk2 = -I.k2;
-        const double damp = I.damp;
-        R r2 = 0;
-#pragma unroll
-        for (int k = 0; k < KY; ++k) {
-            const int ly = (threadIdx.x >> 5) + 8 * k + 1;
-            const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-            if (gx > n || gy > n) continue;
-            const int o = ly * (T2 + 2) + lx;
-            const double2 c = cv[k];
-            uout[gy * S + gx] = c;
-            const double2 fv = f[(size_t)(gy - 1) * n + (gx - 1)];
-            const double2 r = (emx >= 0)
-                ? helm_resid2d_fx<DAMP>(c, UF[o], UF[o - 1], UF[o + 1], UF[o - (T2 + 2)], UF[o + (T2 + 2)], fv,
-                                        mih2, mk2, damp, emx)
-                : make_double2(fx_nan(), fx_nan());
-            const c2 ri = Inner<R>::from(r);
-            rhs[gy * P + gx] = ri;
-            r2 += abs2(ri);
-        }
-        tile_done<R>(I, stp, item.ty * I.res_tx + item.tx, r2, emax2, MODE, st, c);
-        return;
-    }
-    constexpr int NSTAGE = ((T2 + 2) * (T2Y + 2) + NTH - 1) / NTH;
-    // fixed trip count, fully unrolled: all loads of the tile are issued before their uses
-#pragma unroll
-    for (int it = 0; it < NSTAGE; ++it) {
-        const int q = threadIdx.x + it * NTH;
-        if (q >= (T2 + 2) * (T2Y + 2)) break;
-        const int lx = q % (T2 + 2), ly = q / (T2 + 2);
-        const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+    for (int k = 0; k < KY; ++k) {
+        const int ly = (threadIdx.x >> 5) + 8 * k + 1;
+        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
         double2 v = make_double2(0.0, 0.0);
-        if (gx <= n + 1 && gy <= n + 1) {
-            v = uin[gy * S + gx];
-            if (MODE == 1 && gx >= 1 && gx <= n && gy >= 1 && gy <= n) {
-                const c2 ev = e[gy * P + gx];
-                v.x += Inner<R>::widen(ev.x);
-                v.y += Inner<R>::widen(ev.y);
-                if (lx >= 1 && lx <= T2 && ly >= 1 && ly <= T2Y)
-                    emax2 = fmax(emax2, abs2(ev));
-            }
+        if (gx <= n + 1 && gy <= n + 1) v = uin[gy * S + gx];
+        if (MODE == 1 && gx <= n && gy <= n) {
+            const c2 ev = e[gy * P + gx];
+            v.x += Inner<R>::widen(ev.x);
+            v.y += Inner<R>::widen(ev.y);
+            emax2 = fmax(emax2, abs2(ev));
         }
-        U[q] = v;
+        cv[k] = v;
+        ex = max(ex, fx_exp2(v));
     }
+    int rlx = 0, rly = 0;
+    double2 rv = make_double2(0.0, 0.0);
+    if (threadIdx.x < RING) {
+        ring_node<T2, T2Y>(threadIdx.x, rlx, rly);
+        const int gx = x0 - 1 + rlx, gy = y0 - 1 + rly;
+        if (gx <= n + 1 && gy <= n + 1) rv = uin[gy * S + gx];
+        if (MODE == 1 && gx >= 1 && gx <= n && gy >= 1 && gy <= n) {
+            const c2 ev = e[gy * P + gx];
+            rv.x += Inner<R>::widen(ev.x);
+            rv.y += Inner<R>::widen(ev.y);
+        }
+        ex = max(ex, fx_exp2(rv));
+    }
+    const int emx = fx_scale(block_max_exp<NTH>(ex, sx));    // uniform over the CTA
+    longlong2* UF = reinterpret_cast<longlong2*>(U);
+#pragma unroll
+    for (int k = 0; k < KY; ++k) UF[((threadIdx.x >> 5) + 8 * k + 1) * (T2 + 2) + lx] = fx_fix2(cv[k], emx);
+    if (threadIdx.x < RING) UF[rly * (T2 + 2) + rlx] = fx_fix2(rv, emx);
     __syncthreads();
-    const double mih2 = -I.ih2;
-    const double mcdiag = -I.cdiag;
+    const double mih2 = -I.ih2, mk2 = -I.k2;
     const double damp = I.damp;
     R r2 = 0;
     double r2d = 0.0, b2 = 0.0;
-    const int lx = (threadIdx.x & 31) + 1;
 #pragma unroll
-    for (int k = 0; k < T2Y / 8; ++k) {
+    for (int k = 0; k < KY; ++k) {
         const int ly = (threadIdx.x >> 5) + 8 * k + 1;
         const int gx = x0 + lx - 1, gy = y0 + ly - 1;
         if (gx > n || gy > n) continue;
         const int o = ly * (T2 + 2) + lx;
-        const double2 c = U[o];
-        const double2 a = U[o - 1], b = U[o + 1], d = U[o - (T2 + 2)], u = U[o + (T2 + 2)];
+        const double2 c = cv[k];
         if (MODE == 1) uout[gy * S + gx] = c;
         const double2 fv = f[(size_t)(gy - 1) * n + (gx - 1)];
-        const double2 r = helm_resid2d<DAMP>(c, a, b, d, u, fv, mih2, mcdiag, damp);
+        const longlong2 A = UF[o - 1], Bq = UF[o + 1], Dq = UF[o - (T2 + 2)], Uq = UF[o + (T2 + 2)];
+        const double2 r = (emx >= 0) ? helm_resid2d_fx<DAMP>(c, UF[o], A, Bq, Dq, Uq, fv, mih2, mk2, damp, emx)
+                                     : make_double2(fx_nan(), fx_nan());
         const c2 ri = Inner<R>::from(r);
         rhs[gy * P + gx] = ri;
         if (MODE == 1) {
             r2 += abs2(ri);
         } else {
-            // once per solve, in FP64: ||r_0||^2 and ||b||^2, b = f - (wall neighbours)/h^2
-            // formed with the same operations as r (so r_0 = b bit for bit from a zero start)
+            // once per solve, in FP64: ||r_0||^2 and ||b||^2, b = f - (wall neighbours) / h^2,
+            // formed with the same operations as r, so that r_0 = b bit for bit from a zero
+            // start (the numerator then holds the wall values alone)
             r2d += r.x * r.x + r.y * r.y;
-            // b = f away from the wall (the same value the general form gives there)
-            double bx = fv.x, by = fv.y;
-            if (gx == 1 || gx == n || gy == 1 || gy == n) {
-                const double2 z = make_double2(0.0, 0.0);
-                const double2 aw = (gx == 1) ? a : z, bw = (gx == n) ? b : z;
-                const double2 dw = (gy == 1) ? d : z, uw = (gy == n) ? u : z;
-                bx = fma((aw.x + bw.x) + (dw.x + uw.x), mih2, fma(0.0, mcdiag, fv.x));
-                by = fma((aw.y + bw.y) + (dw.y + uw.y), mih2, fma(0.0, mcdiag, fv.y));
+            double bx = fv.x, by = fv.y;            // b = f away from the wall
+            if ((gx == 1 || gx == n || gy == 1 || gy == n) && emx >= 0) {
+                const longlong2 z = make_longlong2(0, 0);
+                const longlong2 aw = (gx == 1) ? A : z, bw = (gx == n) ? Bq : z;
+                const longlong2 dw = (gy == 1) ? Dq : z, uw = (gy == n) ? Uq : z;
+                const double2 bb = helm_resid2d_fx<false>(make_double2(0.0, 0.0), z, aw, bw, dw, uw, fv, mih2,
+                                                          mk2, 0.0, emx);
+                bx = bb.x;
+                by = bb.y;
             }
             b2 += bx * bx + by * by;
         }
@@ -802,133 +740,13 @@ constexpr int T3X = 32, T3Y = 8, T3Z = 16;
 constexpr int RES3D_CTAS = 6;
 constexpr int P3 = (T3X + 2) * (T3Y + 2);
 
-template <typename R, int MODE>
-__device__ __forceinline__ R stage_plane3d(double2* Up, const double2* __restrict__ uin,
-                                           const typename C2<R>::T* __restrict__ e, int n, long S,
-                                           long SP, long P, long PL, int x0, int y0, int gz,
-                                           bool own)
-{
-    typedef typename C2<R>::T c2;
-    R emax2 = 0;
-#pragma unroll
-    for (int it = 0; it < (P3 + NTH - 1) / NTH; ++it) {
-        const int q = threadIdx.x + it * NTH;
-        if (q >= P3) break;
-        const int lx = q % (T3X + 2), ly = q / (T3X + 2);
-        const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-        double2 v = make_double2(0.0, 0.0);
-        if (gx <= n + 1 && gy <= n + 1) {
-            v = uin[(long)gz * SP + (long)gy * S + gx];
-            if (MODE == 1 && gx >= 1 && gx <= n && gy >= 1 && gy <= n && gz >= 1 && gz <= n) {
-                const c2 ev = e[(long)gz * PL + (long)gy * P + xslot<3>(gx, (int)P)];
-                v.x += Inner<R>::widen(ev.x);
-                v.y += Inner<R>::widen(ev.y);
-                if (own && lx >= 1 && lx <= T3X && ly >= 1 && ly <= T3Y)
-                    emax2 = fmax(emax2, abs2(ev));
-            }
-        }
-        Up[q] = v;
-    }
-    return emax2;
-}
-
-template <typename R, int MODE, bool DAMP>
-__device__ __forceinline__ void residual3d_tile(const InstDesc* __restrict__ insts,
-                                                InstState* __restrict__ st, const ResItem item,
-                                                double2 (*U)[P3], const StepCtl& c)
-{
-    typedef typename C2<R>::T c2;
-    const InstDesc& I = insts[item.inst];
-    const int n = I.n;
-    const long S = n + 2;
-    const long SP = S * S;
-    const double2* u0 = I.u[0];
-    const double2* u1 = I.u[1];
-    const double2* __restrict__ f = I.f;
-    const LevelDesc L0 = I.lev[0];
-    InstState* stp = st + item.inst;
-    const InstState s = *stp;
-    if (s.status != HELM_ST_ACTIVE) {           // uniform over the CTA
-        if (c.ctrl && item.tx == 0 && item.ty == 0 && item.tz == 0) step_arrive(st, c);
-        return;
-    }
-    const double2* __restrict__ uin = (s.it & 1) ? u1 : u0;
-    double2* __restrict__ uout = (double2*)((s.it & 1) ? u0 : u1);
-    const c2* __restrict__ e = (const c2*)L0.e;
-    c2* __restrict__ rhs = (c2*)lev_rhs(L0, 0, MODE == 1 ? s.it + 1 : s.it);
-    const long P = L0.pitch;
-    const long PL = (long)L0.pitch * L0.rows;
-    const double mih2 = -I.ih2;
-    const double mcdiag = -I.cdiag;
-    const double damp = I.damp;
-    const int x0 = 1 + item.tx * T3X, y0 = 1 + item.ty * T3Y, z0 = 1 + item.tz * T3Z;
-    const int z1 = min(z0 + T3Z - 1, n);
-    const int lx = (threadIdx.x & 31) + 1, ly = (threadIdx.x >> 5) + 1;
-    const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-    const bool live = gx <= n && gy <= n;
-    const int o = ly * (T3X + 2) + lx;
-    R r2 = 0, emax2 = 0;
-    double r2d = 0.0, b2 = 0.0;
-    stage_plane3d<R, MODE>(U[0], uin, e, n, S, SP, P, PL, x0, y0, z0 - 1, false);
-    emax2 = fmax(emax2, stage_plane3d<R, MODE>(U[1], uin, e, n, S, SP, P, PL, x0, y0, z0, true));
-    int sp = 0, sc = 1, sn = 2;                 // ring slots of planes z-1, z, z+1
-    for (int z = z0; z <= z1; ++z) {
-        const R em = stage_plane3d<R, MODE>(U[sn], uin, e, n, S, SP, P, PL, x0, y0, z + 1, z + 1 <= z1);
-        emax2 = fmax(emax2, em);
-        __syncthreads();
-        if (live) {
-            const double2* Uc = U[sc];
-            const double2 c = Uc[o];
-            const double2 w = Uc[o - 1], ea = Uc[o + 1], so = Uc[o - (T3X + 2)], no = Uc[o + (T3X + 2)];
-            const double2 dn = U[sp][o], up = U[sn][o];
-            const long ou = (long)z * SP + (long)gy * S + gx;
-            const long oe = (long)z * PL + (long)gy * P + xslot<3>(gx, (int)P);
-            if (MODE == 1) uout[ou] = c;
-            const double2 fv = f[((long)(z - 1) * n + (gy - 1)) * n + (gx - 1)];
-            double2 r;
-            r.x = fma(((w.x + ea.x) + (so.x + no.x)) + (dn.x + up.x), mih2, fma(c.x, mcdiag, fv.x));
-            r.y = fma(((w.y + ea.y) + (so.y + no.y)) + (dn.y + up.y), mih2, fma(c.y, mcdiag, fv.y));
-            if constexpr (DAMP) {               // - i p u: the damping couples the lanes
-                r.x = fma(c.y, damp, r.x);
-                r.y = fma(c.x, -damp, r.y);
-            }
-            const c2 ri = Inner<R>::from(r);
-            rhs[oe] = ri;
-            if (MODE == 1) {
-                r2 += abs2(ri);
-            } else {
-                // once per solve, in FP64: ||r_0||^2 and ||b||^2 (same operations as r)
-                r2d += r.x * r.x + r.y * r.y;
-                double bx = fv.x, by = fv.y;            // b = f away from the wall
-                if (gx == 1 || gx == n || gy == 1 || gy == n || z == 1 || z == n) {
-                    const double2 zz = make_double2(0.0, 0.0);
-                    const double2 w1 = (gx == 1) ? w : zz, w2 = (gx == n) ? ea : zz;
-                    const double2 w3 = (gy == 1) ? so : zz, w4 = (gy == n) ? no : zz;
-                    const double2 w5 = (z == 1) ? dn : zz, w6 = (z == n) ? up : zz;
-                    bx = fma(((w1.x + w2.x) + (w3.x + w4.x)) + (w5.x + w6.x), mih2, fma(0.0, mcdiag, fv.x));
-                    by = fma(((w1.y + w2.y) + (w3.y + w4.y)) + (w5.y + w6.y), mih2, fma(0.0, mcdiag, fv.y));
-                }
-                b2 += bx * bx + by * by;
-            }
-        }
-        __syncthreads();                        // the oldest plane is overwritten next
-        const int t = sp;
-        sp = sc;
-        sc = sn;
-        sn = t;
-    }
-    const int tile = (item.tz * I.res_ty + item.ty) * I.res_tx + item.tx;
-    if constexpr (MODE == 0) tile_done<double>(I, stp, tile, r2d, b2, MODE, st, c);
-    else tile_done<R>(I, stp, tile, r2, emax2, MODE, st, c);
-}
-
-// Every outer step (mode 1): the column's planes go through the ring in fixed point
+// The column's planes go through the ring in fixed point
 // (fixed_lap.cuh), each plane on the scale of its own largest exponent; the numerator of
 // plane z is summed on the largest scale of planes z - 1, z, z + 1 (the other planes'
 // values shifted down to it), so every node's numerator is exact up to the truncations.
 // Thread t stages the interior node (t mod 32, t / 32) of each plane and keeps it in FP64
 // for its own residual; threads below the ring size stage one ring node each.
-template <typename R, bool DAMP>
+template <typename R, int MODE, bool DAMP>
 __device__ __forceinline__ void residual3d_tile_fx(const InstDesc* __restrict__ insts,
                                                    InstState* __restrict__ st, const ResItem item,
                                                    longlong2 (*U)[P3], int* sx, const StepCtl& c)
@@ -952,7 +770,7 @@ __device__ __forceinline__ void residual3d_tile_fx(const InstDesc* __restrict__ 
     const double2* __restrict__ f = I.f;
     const LevelDesc L0 = I.lev[0];
     const c2* __restrict__ e = (const c2*)L0.e;
-    c2* __restrict__ rhs = (c2*)lev_rhs(L0, 0, s.it + 1);
+    c2* __restrict__ rhs = (c2*)lev_rhs(L0, 0, MODE == 1 ? s.it + 1 : s.it);   // r_{N+1} / r_0
     const long P = L0.pitch;
     const long PL = (long)L0.pitch * L0.rows;
     const double mih2 = -I.ih2, mk2 = -I.k2;
@@ -967,13 +785,15 @@ __device__ __forceinline__ void residual3d_tile_fx(const InstDesc* __restrict__ 
     if (threadIdx.x < RING) ring_node<T3X, T3Y>(threadIdx.x, rlx, rly);
     const int ro = rly * (T3X + 2) + rlx;
     R r2 = 0, emax2 = 0;
-    // u_{N+1} at window node (wx, wy) of plane gz: u_N, plus e_N at interior nodes
+    double r2d = 0.0, b2 = 0.0;
+    // u_{N+1} at window node (wx, wy) of plane gz: u_N, plus e_N at interior nodes (mode 1;
+    // mode 0 takes the iterate as it is)
     auto node = [&](int wx, int wy, int gz, bool own) -> double2 {
         const int nx = x0 - 1 + wx, ny = y0 - 1 + wy;
         double2 v = make_double2(0.0, 0.0);
         if (nx <= n + 1 && ny <= n + 1 && gz <= n + 1) {
             v = uin[(long)gz * SP + (long)ny * S + nx];
-            if (nx >= 1 && nx <= n && ny >= 1 && ny <= n && gz >= 1 && gz <= n) {
+            if (MODE == 1 && nx >= 1 && nx <= n && ny >= 1 && ny <= n && gz >= 1 && gz <= n) {
                 const c2 ev = e[(long)gz * PL + (long)ny * P + xslot<3>(nx, (int)P)];
                 v.x += Inner<R>::widen(ev.x);
                 v.y += Inner<R>::widen(ev.y);
@@ -1005,6 +825,7 @@ __device__ __forceinline__ void residual3d_tile_fx(const InstDesc* __restrict__ 
         __syncthreads();
         if (live) {
             const int em = max(max(ep[sp], ep[sc]), ep[sn]);
+            const double2 fv = f[((long)(z - 1) * n + (gy - 1)) * n + (gx - 1)];
             double2 r;
             if (ep[sp] >= 0 && ep[sc] >= 0 && ep[sn] >= 0) {
                 // shifts to the common scale (arithmetic, so each rounds toward -inf once);
@@ -1016,15 +837,34 @@ __device__ __forceinline__ void residual3d_tile_fx(const InstDesc* __restrict__ 
                 const longlong2 Dn = U[sp][o], Up = U[sn][o];
                 const long long lx_ = ((((W.x + E.x) + (So.x + No.x)) - 6 * C.x) >> dc) + ((Dn.x >> dd) + (Up.x >> du));
                 const long long ly_ = ((((W.y + E.y) + (So.y + No.y)) - 6 * C.y) >> dc) + ((Dn.y >> dd) + (Up.y >> du));
-                const double2 fv = f[((long)(z - 1) * n + (gy - 1)) * n + (gx - 1)];
                 r = helm_resid_fx<DAMP>(cur, lx_, ly_, fv, mih2, mk2, damp, em);
+                if (MODE == 0) {
+                    // once per solve, in FP64: ||r_0||^2 and ||b||^2, b = f - (wall
+                    // neighbours) / h^2, formed with r's operations (r_0 = b bit for bit from
+                    // a zero start: its numerator then holds the wall values alone)
+                    r2d += r.x * r.x + r.y * r.y;
+                    double bx = fv.x, by = fv.y;
+                    if (gx == 1 || gx == n || gy == 1 || gy == n || z == 1 || z == n) {
+                        const longlong2 zz = make_longlong2(0, 0);
+                        const longlong2 w1 = (gx == 1) ? W : zz, w2 = (gx == n) ? E : zz;
+                        const longlong2 w3 = (gy == 1) ? So : zz, w4 = (gy == n) ? No : zz;
+                        const longlong2 w5 = (z == 1) ? Dn : zz, w6 = (z == n) ? Up : zz;
+                        const long long bx_ = ((((w1.x + w2.x) + (w3.x + w4.x)) - 6 * zz.x) >> dc) + ((w5.x >> dd) + (w6.x >> du));
+                        const long long by_ = ((((w1.y + w2.y) + (w3.y + w4.y)) - 6 * zz.y) >> dc) + ((w5.y >> dd) + (w6.y >> du));
+                        const double2 bb = helm_resid_fx<false>(make_double2(0.0, 0.0), bx_, by_, fv, mih2, mk2, 0.0, em);
+                        bx = bb.x;
+                        by = bb.y;
+                    }
+                    b2 += bx * bx + by * by;
+                }
             } else {
                 r = make_double2(fx_nan(), fx_nan());
+                if (MODE == 0) r2d += r.x;
             }
-            uout[(long)z * SP + (long)gy * S + gx] = cur;
+            if (MODE == 1) uout[(long)z * SP + (long)gy * S + gx] = cur;
             const c2 ri = Inner<R>::from(r);
             rhs[(long)z * PL + (long)gy * P + xslot<3>(gx, (int)P)] = ri;
-            r2 += abs2(ri);
+            if (MODE == 1) r2 += abs2(ri);
         }
         cur = nxt;
         const int t = sp;
@@ -1033,7 +873,8 @@ __device__ __forceinline__ void residual3d_tile_fx(const InstDesc* __restrict__ 
         sn = t;
     }
     const int tile = (item.tz * I.res_ty + item.ty) * I.res_tx + item.tx;
-    tile_done<R>(I, stp, tile, r2, emax2, 1, st, c);
+    if constexpr (MODE == 0) tile_done<double>(I, stp, tile, r2d, b2, MODE, st, c);
+    else tile_done<R>(I, stp, tile, r2, emax2, MODE, st, c);
 }
 
 template <typename R, int MODE, bool DAMP>
@@ -1046,10 +887,7 @@ k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     pdl_wait();
     pdl_trigger();
     for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
-        if constexpr (MODE == 1)
-            residual3d_tile_fx<R, DAMP>(insts, st, items[t], reinterpret_cast<longlong2(*)[P3]>(U), sx, c);
-        else
-            residual3d_tile<R, MODE, DAMP>(insts, st, items[t], U, c);
+        residual3d_tile_fx<R, MODE, DAMP>(insts, st, items[t], reinterpret_cast<longlong2(*)[P3]>(U), sx, c);
         __syncthreads();
     }
 }
