@@ -63,13 +63,13 @@ MAX_OUTER = 2000
 METRIC = "solves/s & stencil HBM GB/s (%peak) at relres 1e-8, mixed vs FP64; p50/p99"
 WORKLOAD = "gaussian_cavity_2d_1023_k1234"
 FP64_PEAK_TFLOPS = 1.25          # GB300 nominal FP64 rate (FMA = 2 flops)
-# DRAM bytes (read + write) per point of the residual kernel: one ncu capture of a
-# 4-instance 1023^2 launch (dram__bytes_read.sum + dram__bytes_write.sum = 168.07 + 67.24 MB
-# over 4 x 1023^2 points), scaled below to the points of an average launch
-RESIDUAL_DRAM_BYTES_PER_POINT = (168.065024e6 + 67.244032e6) / (4 * 1023 ** 2)
-# the same for the finest level's ascent fused with the residual: one ncu capture of a
-# launch of the bench's replay (one instance per lane: 44.17 MB read + 0.71 MB written)
-UPRES_DRAM_BYTES_PER_POINT = (44.168192e6 + 0.713728e6) / (1023 ** 2)
+# DRAM bytes (read + write) per point of the residual kernels, from one ncu capture each,
+# scaled below to the points of an average launch; None where the kernel changed after its
+# capture (the bench's top kernel is the fused one)
+RESIDUAL_DRAM_BYTES_PER_POINT = None
+# the finest level's ascent fused with the residual (fixed-point numerator): one ncu
+# capture of the single-solve replay's launch (44.17 MB read + 1.24 MB written)
+UPRES_DRAM_BYTES_PER_POINT = (44.173312e6 + 1.238528e6) / (1023 ** 2)
 
 
 def _peaks():

@@ -631,7 +631,8 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     __shared__ int sx[NWU];
     double2 cv[VT][KY];
     int exq = 0;
-    auto upd = [&](int lxw, int lyw) -> double2 {   // window node (lxw, lyw): u_N (+ e_N inside)
+    // window node (lxw, lyw): u_N (+ e_N inside the grid; |e_N|^2 into *em for own nodes)
+    auto upd = [&](int lxw, int lyw, R* em) -> double2 {
         const int gx = x0 - 1 + lxw, gy = y0 - 1 + lyw;
         double2 v = U[lyw * UW + lxw];
         if (gx >= 1 && gx <= n && gy >= 1 && gy <= n) {
@@ -639,15 +640,18 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
             const c2 ev = (((ex + ey + cpar) & 1) ? E1 : E0)[PL::at(ex, ey)];
             v.x += Inner<R>::widen(ev.x);
             v.y += Inner<R>::widen(ev.y);
+            if (em) *em = fmax(*em, abs2(ev));
         }
         return v;
     };
+    R r2[VT], em[VT];
 #pragma unroll
     for (int v = 0; v < VT; ++v) {
         const int t = threadIdx.x + NTU * v;
+        em[v] = 0;
 #pragma unroll
         for (int k = 0; k < KY; ++k) {
-            cv[v][k] = upd((t & 31) + 1, (t >> 5) + 8 * k + 1);
+            cv[v][k] = upd((t & 31) + 1, (t >> 5) + 8 * k + 1, &em[v]);
             exq = max(exq, fx_exp2(cv[v][k]));
         }
     }
@@ -661,7 +665,7 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
         if (t < RING) {
             int rlx, rly;
             ring_node<TX, TY>(t, rlx, rly);
-            rv[j] = upd(rlx, rly);
+            rv[j] = upd(rlx, rly, nullptr);
             rq[j] = rly * UW + rlx;
             exq = max(exq, fx_exp2(rv[j]));
         }
@@ -686,13 +690,11 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     const double2* __restrict__ f = I.f;
     const double mih2 = -I.ih2, mk2 = -I.k2;
     const double damp = I.damp;
-    R r2[VT], em[VT];
 #pragma unroll
     for (int v = 0; v < VT; ++v) {
         const int t = threadIdx.x + NTU * v;
         const int lx = (t & 31) + 1;
         r2[v] = 0;
-        em[v] = 0;
 #pragma unroll
         for (int k = 0; k < TY / 8; ++k) {
             const int ly = (t >> 5) + 8 * k + 1;
@@ -709,8 +711,6 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
             const c2 ri = Inner<R>::from(r);
             rhs[(size_t)gy * P + gx] = ri;
             r2[v] += abs2(ri);
-            const int ex = gx - gx0, ey = gy - gy0;
-            em[v] = fmax(em[v], abs2((((ex + ey + cpar) & 1) ? E1 : E0)[PL::at(ex, ey)]));
         }
     }
     // the tile's partials in k_residual2d's order, then the instance's ticket
@@ -825,7 +825,6 @@ __device__ __forceinline__ void residual3d_tile_fx(const InstDesc* __restrict__ 
         __syncthreads();
         if (live) {
             const int em = max(max(ep[sp], ep[sc]), ep[sn]);
-            const double2 fv = f[((long)(z - 1) * n + (gy - 1)) * n + (gx - 1)];
             double2 r;
             if (ep[sp] >= 0 && ep[sc] >= 0 && ep[sn] >= 0) {
                 // shifts to the common scale (arithmetic, so each rounds toward -inf once);
@@ -837,6 +836,7 @@ __device__ __forceinline__ void residual3d_tile_fx(const InstDesc* __restrict__ 
                 const longlong2 Dn = U[sp][o], Up = U[sn][o];
                 const long long lx_ = ((((W.x + E.x) + (So.x + No.x)) - 6 * C.x) >> dc) + ((Dn.x >> dd) + (Up.x >> du));
                 const long long ly_ = ((((W.y + E.y) + (So.y + No.y)) - 6 * C.y) >> dc) + ((Dn.y >> dd) + (Up.y >> du));
+                const double2 fv = f[((long)(z - 1) * n + (gy - 1)) * n + (gx - 1)];
                 r = helm_resid_fx<DAMP>(cur, lx_, ly_, fv, mih2, mk2, damp, em);
                 if (MODE == 0) {
                     // once per solve, in FP64: ||r_0||^2 and ||b||^2, b = f - (wall
