@@ -188,6 +188,11 @@ struct Engine {
     int* d_ctrl = nullptr;                     // [0] steps done, [1] step budget, [2] go, [3] arrivals
     int* h_ctrl = nullptr;                     // pinned mirror
     InstState* h_state = nullptr;              // pinned mirror (cap entries)
+    // page-locked staging of a starting instance's descriptor and state (a copy from
+    // pageable memory would wait for the stream; a slot is restaged only after its previous
+    // instance retired, behind a stream synchronisation)
+    InstDesc* h_desc_stage = nullptr;
+    InstState* h_state_stage = nullptr;
     MgItem* d_mg = nullptr;
     size_t mg_cap = 0;
     ResItem* d_res = nullptr;
@@ -244,11 +249,14 @@ struct Engine {
         if (d_ctrl) cudaFree(d_ctrl);
         if (h_ctrl) cudaFreeHost(h_ctrl);
         if (h_state) cudaFreeHost(h_state);
+        if (h_desc_stage) cudaFreeHost(h_desc_stage);
+        if (h_state_stage) cudaFreeHost(h_state_stage);
         if (d_mg) cudaFree(d_mg);
         if (d_res) cudaFree(d_res);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         d_desc = nullptr; d_state = nullptr; d_ctrl = nullptr; h_ctrl = nullptr;
         h_state = nullptr; d_mg = nullptr; d_res = nullptr; cap_stream = nullptr;
+        h_desc_stage = nullptr; h_state_stage = nullptr;
     }
 
     helm_status init(int D_, int prec_)
@@ -275,6 +283,10 @@ struct Engine {
         HELM_CK(cudaMalloc(&nd, sizeof(InstDesc) * nc));
         HELM_CK(cudaMalloc(&ns, sizeof(InstState) * nc));
         HELM_CK(cudaMallocHost(&nh, sizeof(InstState) * nc));
+        InstDesc* hd = nullptr;
+        InstState* hs = nullptr;
+        HELM_CK(cudaMallocHost(&hd, sizeof(InstDesc) * nc));
+        HELM_CK(cudaMallocHost(&hs, sizeof(InstState) * nc));
         std::vector<InstState> idle(nc);
         for (auto& s : idle) { memset(&s, 0, sizeof s); s.status = HELM_ST_IDLE; }
         if (cap > 0) {
@@ -285,9 +297,17 @@ struct Engine {
         if (d_desc) cudaFree(d_desc);
         if (d_state) cudaFree(d_state);
         if (h_state) cudaFreeHost(h_state);
+        if (h_desc_stage) {
+            // the old staging may still feed queued copies of earlier starts
+            HELM_CK(cudaDeviceSynchronize());
+            cudaFreeHost(h_desc_stage);
+        }
+        if (h_state_stage) cudaFreeHost(h_state_stage);
         d_desc = nd;
         d_state = ns;
         h_state = nh;
+        h_desc_stage = hd;
+        h_state_stage = hs;
         slots.resize(nc, nullptr);
         cap = nc;
         dirty = true;
@@ -720,10 +740,11 @@ struct Engine {
     helm_status start_instance(int slot, cudaStream_t s)
     {
         Instance* in = slots[slot];
-        InstState init;
+        InstState& init = h_state_stage[slot];
         memset(&init, 0, sizeof init);
         init.status = HELM_ST_ACTIVE;
-        HELM_CK(cudaMemcpyAsync(d_desc + slot, &in->d, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
+        h_desc_stage[slot] = in->d;
+        HELM_CK(cudaMemcpyAsync(d_desc + slot, h_desc_stage + slot, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
         HELM_CK(cudaMemcpyAsync(d_state + slot, &init, sizeof(InstState), cudaMemcpyHostToDevice, s));
         HELM_CK(launch_set_ring(D, d_desc, slot, in->d.n, s));
         // the instance's own tile list names instance 0: offset the tables to its slot;
@@ -774,17 +795,14 @@ helm_status alloc_instance(Instance& in, int D, int n, double h, double k, int p
     layout(in.d, D, n, h, k, prec, in.ws);
     // rings of the level iterates must be zero; clear everything once
     HELM_CK(cudaMemsetAsync(in.ws, 0, in.ws_bytes, s));
-    // residual tiles of this instance (for its initial residual)
-    std::vector<ResItem> r;
+    // residual tiles of this instance (for its initial residual), listed on the device
     const int tz = res_tz(D, n);
-    for (int z = 0; z < tz; ++z)
-        for (int y = 0; y < in.d.res_ty; ++y)
-            for (int x = 0; x < in.d.res_tx; ++x) r.push_back(ResItem{0, x, y, z});
-    in.nres0 = (int)r.size();
-    const size_t rb = r.size() * sizeof(ResItem);
+    in.nres0 = tz * in.d.res_ty * in.d.res_tx;
+    const size_t rb = (size_t)in.nres0 * sizeof(ResItem);
     if (stream_ordered) HELM_CK(cudaMallocAsync((void**)&in.d_res0, rb, s));
     else HELM_CK(cudaMalloc((void**)&in.d_res0, rb));
-    HELM_CK(cudaMemcpyAsync(in.d_res0, r.data(), rb, cudaMemcpyHostToDevice, s));
+    HELM_CK(launch_fill_res_items(in.d_res0, in.d.res_tx, in.d.res_ty, tz, s));
+    g_launches += 1;
     // history (relres and einf)
     in.hist_cap = max_outer;
     const size_t hb = (2 * (size_t)max_outer + 1) * sizeof(double);
@@ -880,6 +898,10 @@ struct helm_batch {
     };
     std::map<uint64_t, Rec> recs;
     uint64_t next = 1;
+    // page-locked staging of retiring solves' relres histories (one copy per solve, one
+    // synchronisation for all of them)
+    double* h_hist = nullptr;
+    size_t h_hist_cap = 0;
 };
 
 namespace helm {
@@ -1336,6 +1358,7 @@ helm_status helm_batch_destroy(helm_batch* b)
     for (cudaStream_t s : b->rank_streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->rank_join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->h_hist) cudaFreeHost(b->h_hist);
     delete b;
     return HELM_OK;
 }
@@ -1439,25 +1462,45 @@ static helm_status retire_finished(helm_batch* b)
 {
     // retire finished instances: result into the caller's u, histories to the host
     std::vector<helm_batch::Rec*> fin;
+    size_t nh = 0;
     for (auto& kv : b->recs) {
         helm_batch::Rec& r = kv.second;
         if (r.done || !r.inst) continue;
         Engine* E = b->engines[r.key].get();
         const InstState s = E->h_state[r.slot];
         if (s.status == HELM_ST_ACTIVE || s.status == HELM_ST_IDLE) continue;
+        fin.push_back(&r);
+        nh += (size_t)s.it + 1;
+    }
+    if (fin.empty()) return HELM_OK;
+    if (nh > b->h_hist_cap) {
+        if (b->h_hist) cudaFreeHost(b->h_hist);
+        b->h_hist = nullptr;
+        b->h_hist_cap = 0;
+        HELM_CK(cudaMallocHost(&b->h_hist, nh * sizeof(double)));
+        b->h_hist_cap = nh;
+    }
+    size_t off = 0;
+    for (helm_batch::Rec* rp : fin) {
+        helm_batch::Rec& r = *rp;
+        const InstState s = b->engines[r.key]->h_state[r.slot];
         if ((s.it & 1) && !r.host_sent)
             HELM_CK(cudaMemcpyAsync(r.u, r.inst->d.u[1], r.ubytes, cudaMemcpyDeviceToDevice, b->stream));
         if (r.host_u && !r.host_sent)
             HELM_CK(cudaMemcpyAsync(r.host_u, r.u, r.ubytes, cudaMemcpyDeviceToHost, b->stream));
-        r.hist.resize(s.it + 1);
-        HELM_CK(cudaMemcpyAsync(r.hist.data(), r.inst->d.hist, (s.it + 1) * sizeof(double),
+        HELM_CK(cudaMemcpyAsync(b->h_hist + off, r.inst->d.hist, (s.it + 1) * sizeof(double),
                                 cudaMemcpyDeviceToHost, b->stream));
+        off += (size_t)s.it + 1;
         r.status = s.status;
         r.iters = s.it;
-        fin.push_back(&r);
     }
-    if (fin.empty()) return HELM_OK;
     HELM_CK(cudaStreamSynchronize(b->stream));
+    off = 0;
+    for (helm_batch::Rec* rp : fin) {
+        helm_batch::Rec& r = *rp;
+        r.hist.assign(b->h_hist + off, b->h_hist + off + r.iters + 1);
+        off += (size_t)r.iters + 1;
+    }
     for (helm_batch::Rec* rp : fin) {
         helm_batch::Rec& r = *rp;
         Engine* E = b->engines[r.key].get();

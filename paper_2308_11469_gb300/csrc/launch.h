@@ -120,6 +120,9 @@ cudaError_t run_fp_bits_check(int count, unsigned long long seed, unsigned long 
 // FP64 FMA rate of the current device (independent chains on every SM), best of 5 timed
 // launches: TFLOP/s (an FMA counts 2 flops) and that launch's milliseconds
 cudaError_t run_fp64_rate(double* tflops, double* ms_best);
+// the residual tile list of one instance: item q = (instance 0, q mod tx, (q / tx) mod ty,
+// q / (tx ty)), the order the host loops would give (x fastest)
+cudaError_t launch_fill_res_items(ResItem* items, int tx, int ty, int tz, cudaStream_t s);
 // u[0] and u[1] rings := g ring
 cudaError_t launch_set_ring(int D, const InstDesc* insts, int inst, int n, cudaStream_t s);
 // interior tight <-> level-0 padded/pitched, inner precision

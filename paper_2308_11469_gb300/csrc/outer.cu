@@ -1172,6 +1172,22 @@ cudaError_t run_fp_bits_check(int count, unsigned long long seed, unsigned long 
 }
 int residual_tile_cols(int D) { return 32; }
 
+namespace {
+__global__ void k_fill_res_items(ResItem* __restrict__ items, int tx, int ty, int total)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x)
+        items[q] = ResItem{0, q % tx, (q / tx) % ty, q / (tx * ty)};
+}
+}  // namespace
+
+cudaError_t launch_fill_res_items(ResItem* items, int tx, int ty, int tz, cudaStream_t s)
+{
+    const int total = tx * ty * tz;
+    if (total <= 0) return cudaSuccess;
+    k_fill_res_items<<<(total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024, 256, 0, s>>>(items, tx, ty, total);
+    return cudaGetLastError();
+}
+
 cudaError_t run_fp64_rate(double* tflops, double* ms_best)
 {
     int dev = 0, sms = 0;
