@@ -316,14 +316,16 @@ def leg_batch512(B, torch, dev, peak_gbs):
     U = [torch.zeros_like(x) for x in G]
     big = max(range(len(probs)), key=lambda i: (probs[i].n, probs[i].k))
     q = probs[big]
-    scheds = {}
+    scheds, tiles = {}, {}
     for prec in (B.HELM_PREC_MIXED, B.HELM_PREC_FP64):
         pl = B.helm_plan_create(2, q.n, q.h, q.k, prec=prec)
         U[big].zero_()
         scheds[prec] = B.helm_plan_autotune(pl, F[big], G[big], U[big], TOL, 3000)[:3]
+        tiles[prec] = B.helm_plan_tiles(pl)
         B.helm_plan_destroy(pl)
     batch = B.helm_batch_create(120 << 30)
     B.helm_batch_set_cycle(batch, *scheds[B.HELM_PREC_MIXED])
+    B.helm_batch_set_tiles(batch, tiles[B.HELM_PREC_MIXED])
 
     def run_batch():
         for x in U:
@@ -348,6 +350,7 @@ def leg_batch512(B, torch, dev, peak_gbs):
            "converged": int(sum(r[0] == B.HELM_CONVERGED for r in res)),
            "iters_mean": float(np.mean(its)), "iters_max": int(max(its)),
            "schedule": dict(zip(("nu1", "nu2", "cycles"), scheds[B.HELM_PREC_MIXED])),
+           "tiles": ("auto", "large", "small")[tiles[B.HELM_PREC_MIXED]],
            "model_bytes_per_batch": b_run, "model_GBs": b_run / (ms / 1e3) / 1e9,
            "ceiling_solves_per_s_at_peak": 512 / (b_run / (peak_gbs * 1e9)),
            "ceiling_solves_per_s_v22_model": 512 / (b_v22 / (peak_gbs * 1e9))}
@@ -358,6 +361,7 @@ def leg_batch512(B, torch, dev, peak_gbs):
         q = probs[i]
         pl = B.helm_plan_create(2, q.n, q.h, q.k, prec=B.HELM_PREC_FP64)
         B.helm_plan_set_cycle(pl, *scheds[B.HELM_PREC_FP64])
+        B.helm_plan_set_tiles(pl, tiles[B.HELM_PREC_FP64])
 
         def one():
             U[i].zero_()
@@ -523,12 +527,16 @@ def main():
     # costliest solve of the step (k = 4) and used by every solve of each form
     U[-1].zero_()
     sched_mixed = B.helm_plan_autotune(mixed_plans[-1], F[-1], G[-1], U[-1], TOL, MAX_OUTER)
+    tiles_mixed = B.helm_plan_tiles(mixed_plans[-1])
     B.helm_batch_set_cycle(batch, *sched_mixed[:3])
+    B.helm_batch_set_tiles(batch, tiles_mixed)
     sched_fp64 = None
     if not args.no_fp64:
         sched_fp64 = B.helm_plan_autotune(fp64_plans[-1], F[-1], G[-1], U[-1], TOL, MAX_OUTER)
+        tiles_fp64 = B.helm_plan_tiles(fp64_plans[-1])
         for pl in fp64_plans:
             B.helm_plan_set_cycle(pl, *sched_fp64[:3])
+            B.helm_plan_set_tiles(pl, tiles_fp64)
 
     def mixed_step(Fs=F, Gs=G, Us=U):
         for u in Us:
@@ -705,9 +713,11 @@ def main():
         "config": {"workload": WORKLOAD, "n": n, "h": h, "k": list(KS), "tol": TOL,
                    "solves_per_step": len(KS),
                    "form": "mixed complex64 V-cycles + FP64 refinement, 4-instance batch",
-                   "schedule_mixed": {"nu1": sched_mixed[0], "nu2": sched_mixed[1], "cycles": sched_mixed[2]},
+                   "schedule_mixed": {"nu1": sched_mixed[0], "nu2": sched_mixed[1], "cycles": sched_mixed[2],
+                                      "tiles": ("auto", "large", "small")[tiles_mixed]},
                    "schedule_fp64": (None if sched_fp64 is None else
-                                     {"nu1": sched_fp64[0], "nu2": sched_fp64[1], "cycles": sched_fp64[2]}),
+                                     {"nu1": sched_fp64[0], "nu2": sched_fp64[1], "cycles": sched_fp64[2],
+                                      "tiles": ("auto", "large", "small")[tiles_fp64]}),
                    "l2": "flushed between timed steps (256 MB write)"},
         "latency_ms": {"p50": float(np.percentile(t_mixed, 50)), "p99": float(np.percentile(t_mixed, 99)),
                        "per": "step of 4 solves"},

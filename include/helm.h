@@ -180,11 +180,28 @@ HELM_API helm_status helm_plan_set_cycle(helm_plan* plan, int nu1, int nu2, int 
  * run), keeps the fastest in the plan and reports it (outputs may be NULL).  Every
  * tuning solve starts from the given u, so a u that already solves the problem makes
  * the timings meaningless: pass the starting iterate of the solves to be tuned (zeros
- * for the paper's start).  u is restored to the starting iterate.  HELM_DIVERGED if no
- * candidate converged (schedule unchanged).  Allocates one temporary copy of u. */
+ * for the paper's start).  u is restored to the starting iterate.  2D plans then time the
+ * three tile-shape policies (helm_plan_set_tiles) with the chosen schedule and keep the
+ * fastest.  HELM_DIVERGED if no candidate converged (schedule unchanged).  Allocates one
+ * temporary copy of u. */
 HELM_API helm_status helm_plan_autotune(helm_plan* plan, const void* f, const void* g, void* u,
                                         double tol, int max_outer, int* nu1, int* nu2,
                                         int* cycles, double* best_ms);
+
+/* Tile shape of the 2D fused multigrid level kernels (this project's tuning, no paper
+ * counterpart): HELM_TILES_AUTO = 64 x 32 tiles, or 32 x 16 on levels up to 511 where
+ * the large tiles would give fewer than two per SM; HELM_TILES_LARGE = 64 x 32 everywhere;
+ * HELM_TILES_SMALL = 32 x 16 on every level up to 511.  The solutions agree to the
+ * inner precision's rounding (each shape is its own kernel instantiation, whose FP32
+ * arithmetic may round differently in the last bit).  helm_plan_autotune tries the three policies
+ * with its chosen schedule (2D plans) and keeps the fastest; helm_plan_tiles reports it,
+ * helm_batch_set_tiles applies a policy to every solve of a batch.  HELM_EINVAL for an
+ * unknown policy; 3D plans ignore it. */
+#define HELM_TILES_AUTO 0
+#define HELM_TILES_LARGE 1
+#define HELM_TILES_SMALL 2
+HELM_API helm_status helm_plan_set_tiles(helm_plan* plan, int policy);
+HELM_API helm_status helm_plan_tiles(const helm_plan* plan, int* policy);
 
 /*
  * Solve (Delta_h + k^2) u = f, u = g on the wall, by the outer Poisson iteration
@@ -277,6 +294,7 @@ HELM_API helm_status helm_batch_step(helm_batch* batch, int max_steps);
 /* Inner schedule (as helm_plan_set_cycle) used by every solve of the batch from the next
  * step on (the batch's solves share their launches, hence one schedule). */
 HELM_API helm_status helm_batch_set_cycle(helm_batch* batch, int nu1, int nu2, int cycles);
+HELM_API helm_status helm_batch_set_tiles(helm_batch* batch, int policy);
 /* Solves of one kernel class (dimension, precision) are spread over `lanes` (1 ..
  * HELM_MAX_LANES, default 4) independent launch streams: each submission joins the lane
  * with the least predicted work (outer steps from the closed-form contraction and the

@@ -46,6 +46,9 @@ _SIGS = {
     "helm_plan_set_cycle": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
     "helm_plan_coarse": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "helm_plan_set_cavity": (C.c_int, [_vp, C.c_double, C.c_double]),
+    "helm_plan_set_tiles": (C.c_int, [_vp, C.c_int]),
+    "helm_plan_tiles": (C.c_int, [_vp, C.POINTER(C.c_int)]),
+    "helm_batch_set_tiles": (C.c_int, [_vp, C.c_int]),
     "helm_exit_time": (C.c_int, [_vp, C.c_double, C.c_int, _vp, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
     "helm_spectral_radius": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
@@ -260,6 +263,25 @@ def helm_spectral_radius(plan: _Plan, max_iters: int = 200, tol: float = 1e-10, 
 
 def helm_plan_set_cycle(plan: _Plan, nu1: int, nu2: int, cycles: int = 1) -> None:
     _check(load().helm_plan_set_cycle(plan.handle, nu1, nu2, cycles), "helm_plan_set_cycle")
+
+
+HELM_TILES_AUTO = 0
+HELM_TILES_LARGE = 1
+HELM_TILES_SMALL = 2
+
+
+def helm_plan_set_tiles(plan: _Plan, policy: int) -> None:
+    _check(load().helm_plan_set_tiles(plan.handle, int(policy)), "helm_plan_set_tiles")
+
+
+def helm_plan_tiles(plan: _Plan) -> int:
+    v = C.c_int()
+    _check(load().helm_plan_tiles(plan.handle, C.byref(v)), "helm_plan_tiles")
+    return v.value
+
+
+def helm_batch_set_tiles(batch, policy: int) -> None:
+    _check(load().helm_batch_set_tiles(batch.handle, int(policy)), "helm_batch_set_tiles")
 
 
 def helm_plan_autotune(plan: _Plan, f, g, u, tol: float, max_outer: int):

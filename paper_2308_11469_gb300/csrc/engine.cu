@@ -180,6 +180,10 @@ struct PlanState {
 struct Engine {
     int D = 2, prec = 1;
     int nu1 = 2, nu2 = 2, cycles = 1;
+    // 2D tile shape of the fused level kernels: HELM_TILES_AUTO (64 x 32, or 32 x 16 where
+    // the large tiles would leave the GPU under-filled), _LARGE (64 x 32 wherever allowed),
+    // _SMALL (32 x 16 on levels up to 511)
+    int tiles = HELM_TILES_AUTO;
     cudaStream_t cap_stream = nullptr;
     int cap = 0;                               // descriptor slots
     std::vector<Instance*> slots;              // nullptr = free
@@ -359,7 +363,9 @@ struct Engine {
             // one tile shape per launch (that of its largest level) and the matching grid
             if (D == 2) {
                 // small tiles only where the large ones would leave the GPU under-filled
-                p.shape = (tile_shape2d(p.nmax) == 1 && p.cnt * tiles2d_for(p.nmax, 0) < 2 * 152) ? 1 : 0;
+                if (tiles == HELM_TILES_LARGE) p.shape = 0;
+                else if (tiles == HELM_TILES_SMALL) p.shape = tile_shape2d(p.nmax);
+                else p.shape = (tile_shape2d(p.nmax) == 1 && p.cnt * tiles2d_for(p.nmax, 0) < 2 * 152) ? 1 : 0;
                 for (int q = p.off; q < p.off + p.cnt; ++q)
                     p.tiles = std::max(p.tiles, tiles2d_for(slots[items[q].inst]->d.lev[items[q].level].n, p.shape));
             }
@@ -638,7 +644,7 @@ struct Engine {
     // whether any instance has a damping term (it selects the residual kernels' variant).
     std::vector<long> current_signature() const
     {
-        std::vector<long> sig{cap, nu1, nu2, cycles};
+        std::vector<long> sig{cap, nu1, nu2, cycles, tiles};
         long damp = 0;
         for (int i = 0; i < cap; ++i) {
             sig.push_back(slots[i] ? (long)slots[i]->d.n * 4 + (long)slots[i]->d.D : -1L);
@@ -873,6 +879,7 @@ struct helm_plan {
 struct helm_batch {
     size_t cap_bytes = 0, used = 0;
     int nu1 = 2, nu2 = 2, cycles = 1;           // inner schedule of every engine
+    int tiles = HELM_TILES_AUTO;                // 2D tile-shape policy of every engine
     // Solves of one kernel class are spread over `lanes` engines (each with its own graph
     // on its own stream, launched concurrently), so one lane's FP64-bound residual runs
     // beside another lane's latency-bound coarse levels.
@@ -1170,30 +1177,53 @@ helm_status helm_plan_autotune(helm_plan* p, const void* f, const void* g, void*
     cudaEvent_t e0, e1;
     HELM_CK(cudaEventCreate(&e0));
     HELM_CK(cudaEventCreate(&e1));
-    const int s1 = p->eng.nu1, s2 = p->eng.nu2, sc = p->eng.cycles;
-    int bi = -1;
+    const int s1 = p->eng.nu1, s2 = p->eng.nu2, sc = p->eng.cycles, st0 = p->eng.tiles;
+    // best of two timed solves after a first one that builds the graph; HELM_CONVERGED and
+    // the time, or the first solve's outcome
+    auto time_solve = [&](float* ms_out) -> helm_status {
+        float best = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            HELM_CK(cudaMemcpyAsync(u, saved, ub, cudaMemcpyDeviceToDevice, p->stream));
+            HELM_CK(cudaEventRecord(e0, p->stream));
+            const helm_status out = helm_solve(p, f, g, u, tol, max_outer, nullptr, nullptr);
+            HELM_CK(cudaEventRecord(e1, p->stream));
+            HELM_CK(cudaEventSynchronize(e1));
+            if (out != HELM_CONVERGED) return out;
+            float ms = 0.f;
+            HELM_CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0 && (best == 0.f || ms < best)) best = ms;
+        }
+        *ms_out = best;
+        return HELM_CONVERGED;
+    };
+    int bi = -1, bt = st0;
     float bms = 0.f;
     helm_status st = HELM_OK;
     for (int c = 0; c < (int)(sizeof cand / sizeof cand[0]); ++c) {
         st = helm_plan_set_cycle(p, cand[c][0], cand[c][1], cand[c][2]);
         if (st != HELM_OK) break;
-        float best = 0.f;
-        helm_status out = HELM_OK;
-        for (int rep = 0; rep < 3; ++rep) {               // first run builds the graph
-            HELM_CK(cudaMemcpyAsync(u, saved, ub, cudaMemcpyDeviceToDevice, p->stream));
-            HELM_CK(cudaEventRecord(e0, p->stream));
-            out = helm_solve(p, f, g, u, tol, max_outer, nullptr, nullptr);
-            HELM_CK(cudaEventRecord(e1, p->stream));
-            HELM_CK(cudaEventSynchronize(e1));
-            if (out != HELM_CONVERGED) break;
-            float ms = 0.f;
-            HELM_CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep > 0 && (best == 0.f || ms < best)) best = ms;
-        }
+        float ms = 0.f;
+        const helm_status out = time_solve(&ms);
         if (out < 0) { st = out; break; }
-        if (out == HELM_CONVERGED && (bi < 0 || best < bms)) {
+        if (out == HELM_CONVERGED && (bi < 0 || ms < bms)) {
             bi = c;
-            bms = best;
+            bms = ms;
+        }
+    }
+    // 2D: the tile-shape policies of the fused level kernels, with the chosen schedule
+    if (st == HELM_OK && bi >= 0 && p->D == 2) {
+        helm_plan_set_cycle(p, cand[bi][0], cand[bi][1], cand[bi][2]);
+        for (int pol = HELM_TILES_AUTO; pol <= HELM_TILES_SMALL; ++pol) {
+            if (pol == st0) continue;
+            p->eng.tiles = pol;
+            p->eng.dirty = true;
+            float ms = 0.f;
+            const helm_status out = time_solve(&ms);
+            if (out < 0) { st = out; break; }
+            if (out == HELM_CONVERGED && ms < bms) {
+                bt = pol;
+                bms = ms;
+            }
         }
     }
     HELM_CK(cudaMemcpyAsync(u, saved, ub, cudaMemcpyDeviceToDevice, p->stream));
@@ -1201,19 +1231,34 @@ helm_status helm_plan_autotune(helm_plan* p, const void* f, const void* g, void*
     HELM_CK(cudaStreamSynchronize(p->stream));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (st != HELM_OK) {
+    if (st != HELM_OK || bi < 0) {                         // error, or nothing converged: keep the old schedule
         helm_plan_set_cycle(p, s1, s2, sc);
-        return st;
-    }
-    if (bi < 0) {                                          // nothing converged: keep the old schedule
-        helm_plan_set_cycle(p, s1, s2, sc);
-        return HELM_DIVERGED;
+        p->eng.tiles = st0;
+        p->eng.dirty = true;
+        return st != HELM_OK ? st : HELM_DIVERGED;
     }
     helm_plan_set_cycle(p, cand[bi][0], cand[bi][1], cand[bi][2]);
+    p->eng.tiles = bt;
+    p->eng.dirty = true;
     if (nu1_out) *nu1_out = cand[bi][0];
     if (nu2_out) *nu2_out = cand[bi][1];
     if (cycles_out) *cycles_out = cand[bi][2];
     if (best_ms) *best_ms = bms;
+    return HELM_OK;
+}
+
+helm_status helm_plan_set_tiles(helm_plan* p, int policy)
+{
+    if (!p || policy < HELM_TILES_AUTO || policy > HELM_TILES_SMALL) return HELM_EINVAL;
+    p->eng.tiles = policy;
+    p->eng.dirty = true;
+    return HELM_OK;
+}
+
+helm_status helm_plan_tiles(const helm_plan* p, int* policy)
+{
+    if (!p || !policy) return HELM_EINVAL;
+    *policy = p->eng.tiles;
     return HELM_OK;
 }
 
@@ -1404,6 +1449,7 @@ static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, 
         ne->nu1 = b->nu1;
         ne->nu2 = b->nu2;
         ne->cycles = b->cycles;
+        ne->tiles = b->tiles;
         E = ne.get();
         b->engines[key] = std::move(ne);
     } else {
@@ -1525,6 +1571,18 @@ helm_status helm_batch_set_lanes(helm_batch* b, int lanes)
 {
     if (!b || lanes < 1 || lanes > HELM_MAX_LANES) return HELM_EINVAL;
     b->lanes = lanes;
+    return HELM_OK;
+}
+
+helm_status helm_batch_set_tiles(helm_batch* b, int policy)
+{
+    if (!b || policy < HELM_TILES_AUTO || policy > HELM_TILES_SMALL) return HELM_EINVAL;
+    b->tiles = policy;
+    for (auto& kv : b->engines) {
+        kv.second->tiles = policy;
+        kv.second->dirty = true;
+        kv.second->plan_sig.clear();
+    }
     return HELM_OK;
 }
 

@@ -208,3 +208,41 @@ def test_host_result_copy(B, chunk, pinned):
     B.helm_batch_destroy(batch)
     for pl in plans:
         B.helm_plan_destroy(pl)
+
+
+def test_tile_policies_give_the_same_solutions(B):
+    """The 2D tile-shape policy changes only how the levels are cut into tiles (each shape is
+    its own kernel instantiation, so the FP32 cycle may round differently in the last bit):
+    a batch of uneven sizes converges under each policy to the same solutions within the
+    mixed-precision tolerance, and the autotuner keeps one of the policies."""
+    probs = inputs.batched_instances(count=12, seed=9)
+    outs = []
+    for pol in (B.HELM_TILES_AUTO, B.HELM_TILES_LARGE, B.HELM_TILES_SMALL):
+        batch = B.helm_batch_create(0)
+        B.helm_batch_set_tiles(batch, pol)
+        bufs, tickets = [], []
+        for q in probs:
+            f = torch.from_numpy(q.f).to(DEV)
+            g = torch.from_numpy(q.g).to(DEV)
+            u = torch.zeros_like(g)
+            tickets.append(B.helm_batch_submit_geom(batch, 2, q.n, q.h, q.k, B.HELM_PREC_MIXED, f, g, u,
+                                                    1e-8, 3000))
+            bufs.append(u)
+        B.helm_batch_step(batch, 0)
+        res = [B.helm_batch_poll(batch, t, 3000) for t in tickets]
+        assert all(r[0] == B.HELM_CONVERGED for r in res)
+        outs.append([u.cpu().numpy() for u in bufs])
+        B.helm_batch_destroy(batch)
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(a)
+    q = max(probs, key=lambda p: p.n)
+    plan = B.helm_plan_create(2, q.n, q.h, q.k, prec=B.HELM_PREC_MIXED)
+    f = torch.from_numpy(q.f).to(DEV)
+    g = torch.from_numpy(q.g).to(DEV)
+    u = torch.zeros_like(g)
+    B.helm_plan_autotune(plan, f, g, u, 1e-8, 3000)
+    assert B.helm_plan_tiles(plan) in (B.HELM_TILES_AUTO, B.HELM_TILES_LARGE, B.HELM_TILES_SMALL)
+    with pytest.raises(B.HelmError):
+        B.helm_plan_set_tiles(plan, 7)
+    B.helm_plan_destroy(plan)
