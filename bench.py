@@ -388,7 +388,8 @@ def served_count(rate: float) -> int:
     return int(min(400, max(30, round(2.0 * rate))))
 
 
-def leg_served(B, torch, dev, rates=SERVED_RATES, seed: int = 5):
+def leg_served(B, torch, dev, schedules, rates=SERVED_RATES, seed: int = 5):
+    """schedules: {ndim: (nu1, nu2, cycles)}, the tuned schedule of each dimension's solves."""
     from paper_2308_11469_gb300 import inputs, serve
     pool = {}
     # warm-up: one request of every (dimension, size) class, all at once (engines, plans
@@ -403,7 +404,7 @@ def leg_served(B, torch, dev, rates=SERVED_RATES, seed: int = 5):
             warm.append(inputs.Request(0.0, inputs.Problem(D, n, h, k, None, None,
                                                            {"kind": "gauss", "centres": c, "amps": a})))
     jobs, pool = serve.make_jobs(warm, dev, pool)
-    srv = serve.Server(120 << 30, chunk=4)
+    srv = serve.Server(120 << 30, chunk=4, class_schedules=schedules)
     srv.run(jobs, realtime=False)
     srv.close()
     del jobs
@@ -413,7 +414,7 @@ def leg_served(B, torch, dev, rates=SERVED_RATES, seed: int = 5):
         reqs = inputs.served_stream(rate, count, seed=seed, materialise=False)
         jobs, pool = serve.make_jobs(reqs, dev, pool, tol=TOL, max_outer=MAX_OUTER)
         torch.cuda.synchronize()
-        srv = serve.Server(120 << 30, chunk=4)
+        srv = serve.Server(120 << 30, chunk=4, class_schedules=schedules)
         done = srv.run(jobs, realtime=True)
         st = serve.latency_stats(done)
         pts_steps = float(sum((j.n ** j.D) * j.iters for j in done))
@@ -433,6 +434,7 @@ def leg_served(B, torch, dev, rates=SERVED_RATES, seed: int = 5):
         del jobs, done
         torch.cuda.synchronize()
     return {"rates": rows, "hbm_cap_gb": 120, "chunk": 4,
+            "schedules": {f"{d}D": dict(zip(("nu1", "nu2", "cycles"), v)) for d, v in schedules.items()},
             "mix": "2D n in {127..2047} (70 %) / 3D n in {63, 127, 255}; Gaussian sources or "
                    "plane-wave wall data (50/50); k ~ U[0.5, 0.9 k_max]; source / wall data "
                    "materialised once per (D, n, kind), each request its own k and solution"}, keep
@@ -745,7 +747,12 @@ def main():
         elif leg == "batch512":
             res, kp = leg_batch512(B, torch, dev, peak)
         elif leg == "served":
-            res, kp = leg_served(B, torch, dev)
+            # each dimension's solves on its tuned schedule: the headline's for 2D, the cube
+            # leg's for 3D (V(0,2), the cube's tuned schedule, when that leg did not run)
+            s3 = line.get("cube255", {}).get("mixed", {}).get("schedule")
+            scheds = {2: tuple(sched_mixed[:3]),
+                      3: (s3["nu1"], s3["nu2"], s3["cycles"]) if s3 else (0, 2, 1)}
+            res, kp = leg_served(B, torch, dev, scheds)
         else:
             raise SystemExit(f"unknown leg {leg}")
         res["clocks"] = smp.stop()

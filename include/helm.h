@@ -294,6 +294,12 @@ HELM_API helm_status helm_batch_step(helm_batch* batch, int max_steps);
 /* Inner schedule (as helm_plan_set_cycle) used by every solve of the batch from the next
  * step on (the batch's solves share their launches, hence one schedule). */
 HELM_API helm_status helm_batch_set_cycle(helm_batch* batch, int nu1, int nu2, int cycles);
+/* As helm_batch_set_cycle for the solves of one kernel class only (dimension ndim and
+ * precision prec): a batch mixing 2D and 3D solves can run each class with its own tuned
+ * schedule (their launches are separate anyway).  helm_batch_set_cycle resets every class
+ * to the batch-wide schedule.  No paper counterpart (scheduling). */
+HELM_API helm_status helm_batch_set_cycle_class(helm_batch* batch, int ndim, int prec, int nu1, int nu2,
+                                                int cycles);
 HELM_API helm_status helm_batch_set_tiles(helm_batch* batch, int policy);
 /* Solves of one kernel class (dimension, precision) are spread over `lanes` (1 ..
  * HELM_MAX_LANES, default 4) independent launch streams: each submission joins the lane

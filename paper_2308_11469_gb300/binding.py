@@ -49,6 +49,7 @@ _SIGS = {
     "helm_plan_set_tiles": (C.c_int, [_vp, C.c_int]),
     "helm_plan_tiles": (C.c_int, [_vp, C.POINTER(C.c_int)]),
     "helm_batch_set_tiles": (C.c_int, [_vp, C.c_int]),
+    "helm_batch_set_cycle_class": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "helm_exit_time": (C.c_int, [_vp, C.c_double, C.c_int, _vp, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
     "helm_spectral_radius": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
@@ -278,6 +279,11 @@ def helm_plan_tiles(plan: _Plan) -> int:
     v = C.c_int()
     _check(load().helm_plan_tiles(plan.handle, C.byref(v)), "helm_plan_tiles")
     return v.value
+
+
+def helm_batch_set_cycle_class(batch, ndim: int, prec: int, nu1: int, nu2: int, cycles: int = 1) -> None:
+    _check(load().helm_batch_set_cycle_class(batch.handle, int(ndim), int(prec), int(nu1), int(nu2), int(cycles)),
+           "helm_batch_set_cycle_class")
 
 
 def helm_batch_set_tiles(batch, policy: int) -> None:

@@ -880,6 +880,9 @@ struct helm_batch {
     size_t cap_bytes = 0, used = 0;
     int nu1 = 2, nu2 = 2, cycles = 1;           // inner schedule of every engine
     int tiles = HELM_TILES_AUTO;                // 2D tile-shape policy of every engine
+    // per kernel class (2 D + prec): a schedule set by helm_batch_set_cycle_class, used
+    // instead of the batch-wide one by that class's engines ({0, 0, 0}: none)
+    int cls_sched[8][3] = {};
     // Solves of one kernel class are spread over `lanes` engines (each with its own graph
     // on its own stream, launched concurrently), so one lane's FP64-bound residual runs
     // beside another lane's latency-bound coarse levels.
@@ -1446,9 +1449,10 @@ static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, 
         std::unique_ptr<Engine> ne(new Engine());
         helm_status st = ne->init(D, prec);
         if (st != HELM_OK) return st;
-        ne->nu1 = b->nu1;
-        ne->nu2 = b->nu2;
-        ne->cycles = b->cycles;
+        const int* cs = b->cls_sched[2 * D + prec];
+        ne->nu1 = cs[2] ? cs[0] : b->nu1;
+        ne->nu2 = cs[2] ? cs[1] : b->nu2;
+        ne->cycles = cs[2] ? cs[2] : b->cycles;
         ne->tiles = b->tiles;
         E = ne.get();
         b->engines[key] = std::move(ne);
@@ -1586,6 +1590,26 @@ helm_status helm_batch_set_tiles(helm_batch* b, int policy)
     return HELM_OK;
 }
 
+helm_status helm_batch_set_cycle_class(helm_batch* b, int ndim, int prec, int nu1, int nu2, int cycles)
+{
+    if (!b || (ndim != 2 && ndim != 3) || (prec != HELM_PREC_FP64 && prec != HELM_PREC_MIXED)) return HELM_EINVAL;
+    if (nu1 < 0 || nu1 > 8 || nu2 < 0 || nu2 > 8 || nu1 + nu2 < 1 || cycles < 1 || cycles > 16)
+        return HELM_EINVAL;
+    const int c = 2 * ndim + prec;
+    b->cls_sched[c][0] = nu1;
+    b->cls_sched[c][1] = nu2;
+    b->cls_sched[c][2] = cycles;
+    for (auto& kv : b->engines) {
+        if (kv.first / HELM_MAX_LANES != c) continue;
+        kv.second->nu1 = nu1;
+        kv.second->nu2 = nu2;
+        kv.second->cycles = cycles;
+        kv.second->dirty = true;
+        kv.second->plan_sig.clear();
+    }
+    return HELM_OK;
+}
+
 helm_status helm_batch_set_cycle(helm_batch* b, int nu1, int nu2, int cycles)
 {
     if (!b) return HELM_EINVAL;
@@ -1594,6 +1618,7 @@ helm_status helm_batch_set_cycle(helm_batch* b, int nu1, int nu2, int cycles)
     b->nu1 = nu1;
     b->nu2 = nu2;
     b->cycles = cycles;
+    memset(b->cls_sched, 0, sizeof b->cls_sched);       // one schedule for every class again
     for (auto& kv : b->engines) {
         kv.second->nu1 = nu1;
         kv.second->nu2 = nu2;

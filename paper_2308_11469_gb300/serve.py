@@ -52,13 +52,18 @@ class Server:
                    the request waits in the queue until solves retire).
     chunk          outer steps per batch launch between admission / retirement checks.
     prec           inner precision of every solve (HELM_PREC_MIXED by default).
+    schedule       (nu1, nu2, cycles) of every solve (None: the library's default V(2,2)).
+    class_schedules  {ndim: (nu1, nu2, cycles)}: a schedule per dimension (2D and 3D solves
+                   run in separate kernel classes, each with its own tuned cycle).
     """
 
     def __init__(self, hbm_cap_bytes: int, chunk: int = 4, prec: int = B.HELM_PREC_MIXED,
-                 schedule=None, clock=time.perf_counter):
+                 schedule=None, clock=time.perf_counter, class_schedules=None):
         self.batch = B.helm_batch_create(hbm_cap_bytes)
         if schedule is not None:
             B.helm_batch_set_cycle(self.batch, *schedule)
+        for ndim, sch in (class_schedules or {}).items():
+            B.helm_batch_set_cycle_class(self.batch, ndim, prec, *sch)
         self.chunk = chunk
         self.prec = prec
         self.clock = clock
@@ -234,6 +239,8 @@ def main(argv=None) -> int:
     ap.add_argument("--chunk", type=int, default=4)
     ap.add_argument("--sizes-2d", default="127,255,511,1023,2047")
     ap.add_argument("--sizes-3d", default="63,127,255")
+    ap.add_argument("--sched-2d", default="0,1,1", help="nu1,nu2,cycles of the 2D solves")
+    ap.add_argument("--sched-3d", default="0,2,1", help="nu1,nu2,cycles of the 3D solves")
     args = ap.parse_args(argv)
     build.build()
     B.load()
@@ -244,7 +251,9 @@ def main(argv=None) -> int:
                                 materialise=False)
     jobs, _ = make_jobs(reqs, dev)
     torch.cuda.synchronize()
-    srv = Server(int(args.cap_gb * (1 << 30)), chunk=args.chunk)
+    scheds = {2: tuple(int(x) for x in args.sched_2d.split(",")),
+              3: tuple(int(x) for x in args.sched_3d.split(","))}
+    srv = Server(int(args.cap_gb * (1 << 30)), chunk=args.chunk, class_schedules=scheds)
     done = srv.run(jobs, realtime=True)
     stats = latency_stats(done)
     stats.update({"rate": args.rate, "requests": args.count, "chunk": args.chunk,

@@ -246,3 +246,38 @@ def test_tile_policies_give_the_same_solutions(B):
     with pytest.raises(B.HelmError):
         B.helm_plan_set_tiles(plan, 7)
     B.helm_plan_destroy(plan)
+
+
+def test_class_schedules_equal_solo_solves(B):
+    """A batch mixing 2D and 3D solves with a schedule per dimension gives each solve the
+    iterates of a single solve on that schedule, bit for bit."""
+    probs = _mix()
+    sched = {2: (0, 1, 1), 3: (0, 2, 1)}
+    tol, max_outer = 1e-8, 2000
+    batch = B.helm_batch_create(0)
+    for d, sc in sched.items():
+        B.helm_batch_set_cycle_class(batch, d, B.HELM_PREC_MIXED, *sc)
+    keep, tickets = [], []
+    for p in probs:
+        f = torch.from_numpy(p.f).to(DEV)
+        g = torch.from_numpy(p.g).to(DEV)
+        u = torch.zeros_like(g)
+        keep.append((f, g, u))
+        tickets.append(B.helm_batch_submit_geom(batch, p.D, p.n, p.h, p.k, B.HELM_PREC_MIXED, f, g, u, tol,
+                                                max_outer))
+    B.helm_batch_step(batch, 0)
+    results = [B.helm_batch_poll(batch, t, max_outer) for t in tickets]
+    B.helm_batch_destroy(batch)
+    for i, p in enumerate(probs):
+        plan = B.helm_plan_create(p.D, p.n, p.h, p.k, prec=B.HELM_PREC_MIXED)
+        B.helm_plan_set_cycle(plan, *sched[p.D])
+        f, g, _ = keep[i]
+        u = torch.zeros_like(g)
+        st, it, hist = B.helm_solve(plan, f, g, u, tol, max_outer)
+        B.helm_plan_destroy(plan)
+        assert results[i][0] == st == B.HELM_CONVERGED
+        assert results[i][1] == it
+        assert np.array_equal(results[i][2], hist)
+        assert np.array_equal(keep[i][2].cpu().numpy(), u.cpu().numpy())
+    with pytest.raises(B.HelmError):
+        B.helm_batch_set_cycle_class(B.helm_batch_create(0), 4, B.HELM_PREC_MIXED, 0, 1, 1)
