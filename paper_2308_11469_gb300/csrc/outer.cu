@@ -582,20 +582,29 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
             const size_t g = in ? (size_t)gy * P + gx : 0;
             const int c = (lx + ly + cpar) & 1;
             const int o = PL::at(lx, ly);
-            if (e2z) (c ? E1 : E0)[o] = cz<c2>();
-            else cp_async_elem<sizeof(c2)>((c ? E1 : E0) + o, ge2 + g, in);
+            // with post-smoothing the first half-sweep overwrites every interior colour-0
+            // node it reads later, without reading their old values: colour 0 needs e2
+            // only off the interior (the walls' zeros, which the sweeps read)
+            if (NU == 0 || c || !in) {
+                if (e2z) (c ? E1 : E0)[o] = cz<c2>();
+                else cp_async_elem<sizeof(c2)>((c ? E1 : E0) + o, ge2 + g, in);
+            }
             cp_async_elem<sizeof(c2)>((c ? R1 : R0) + o, gr + g, in);
         }
     }
     cp_async_wait_all();
     __syncthreads();
-    // correction: e2 + multilinear interpolation of the coarse iterate (interior nodes)
+    // correction: e2 + multilinear interpolation of the coarse iterate (interior nodes);
+    // with post-smoothing only on colour 1 (the first half-sweep overwrites colour 0, and
+    // the outermost ring's colour-0 nodes it leaves are never read)
     for (int ly = threadIdx.x >> 5; ly < HH; ly += NWU) {
         const int gy = gy0 + ly;
         if (gy < 1 || gy > n) continue;
         const int Y0 = (gy >> 1) - cy0, Y1 = ((gy + 1) >> 1) - cy0;
+        const int lx0 = (NU == 0) ? lane : 2 * lane + ((ly + cpar + 1) & 1);
+        const int dlx = (NU == 0) ? 32 : 64;
 #pragma unroll
-        for (int lx = lane; lx < W; lx += 32) {
+        for (int lx = lx0; lx < W; lx += dlx) {
             const int gx = gx0 + lx;
             if (gx < 1 || gx > n) continue;
             const int X0 = (gx >> 1) - cx0, X1 = ((gx + 1) >> 1) - cx0;
