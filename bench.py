@@ -313,7 +313,12 @@ def leg_batch512(B, torch, dev, peak_gbs):
     probs = inputs.batched_instances(count=512, seed=4)
     F = [torch.from_numpy(q.f).to(dev) for q in probs]
     G = [torch.from_numpy(q.g).to(dev) for q in probs]
-    U = [torch.zeros_like(x) for x in G]
+    # the solutions as views of one buffer: one fill clears every starting iterate
+    Uall = torch.zeros(sum(x.numel() for x in G), dtype=torch.complex128, device=dev)
+    U, off = [], 0
+    for x in G:
+        U.append(Uall[off:off + x.numel()].view(x.shape))
+        off += x.numel()
     big = max(range(len(probs)), key=lambda i: (probs[i].n, probs[i].k))
     q = probs[big]
     scheds, tiles = {}, {}
@@ -327,13 +332,14 @@ def leg_batch512(B, torch, dev, peak_gbs):
     B.helm_batch_set_cycle(batch, *scheds[B.HELM_PREC_MIXED])
     B.helm_batch_set_tiles(batch, tiles[B.HELM_PREC_MIXED])
 
+    jobs = [(2, q.n, q.h, q.k, F[i], G[i], U[i]) for i, q in enumerate(probs)]
+
     def run_batch():
-        for x in U:
-            x.zero_()
-        ts = [B.helm_batch_submit_geom(batch, 2, q.n, q.h, q.k, B.HELM_PREC_MIXED, F[i], G[i], U[i],
-                                       TOL, 3000) for i, q in enumerate(probs)]
+        Uall.zero_()
+        ts = B.helm_batch_submit_many(batch, jobs, B.HELM_PREC_MIXED, TOL, 3000)
+        assert len(ts) == len(jobs)
         B.helm_batch_step(batch, 0)
-        return [B.helm_batch_poll(batch, t, 3000) for t in ts]
+        return [(st, it) for _, st, it in B.helm_batch_poll_many(batch, ts)]
     run_batch()
     ts = []
     for _ in range(3):

@@ -291,6 +291,20 @@ HELM_API helm_status helm_batch_submit_geom(helm_batch* batch, int ndim, int n, 
                                             int prec, const void* f, const void* g, void* u,
                                             double tol, int max_outer, uint64_t* ticket);
 HELM_API helm_status helm_batch_step(helm_batch* batch, int max_steps);
+/* Many submissions in one call (no paper counterpart: a serving loop admitting a burst of
+ * requests): solve i is helm_batch_submit_geom(batch, ndim[i], n[i], h[i], k[i], prec,
+ * f[i], g[i], u[i], tol, max_outer, &tickets[i]), in order.  Stops at the first solve the
+ * memory cap refuses (HELM_ENOMEM) or an invalid one (its error); *admitted = the solves
+ * submitted before it. */
+HELM_API helm_status helm_batch_submit_many(helm_batch* batch, int count, const int* ndim, const int* n,
+                                            const double* h, const double* k, int prec,
+                                            const void* const* f, const void* const* g, void* const* u,
+                                            double tol, int max_outer, uint64_t* tickets, int* admitted);
+/* As helm_batch_poll for `count` tickets without the histories: done[i], and for the
+ * finished ones status[i] and iters[i] (either array may be NULL); a finished solve's
+ * record is released as by helm_batch_poll.  HELM_EINVAL for an unknown ticket. */
+HELM_API helm_status helm_batch_poll_many(helm_batch* batch, int count, const uint64_t* tickets, int* done,
+                                          int* status, int* iters);
 /* Inner schedule (as helm_plan_set_cycle) used by every solve of the batch from the next
  * step on (the batch's solves share their launches, hence one schedule). */
 HELM_API helm_status helm_batch_set_cycle(helm_batch* batch, int nu1, int nu2, int cycles);

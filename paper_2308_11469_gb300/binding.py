@@ -50,6 +50,12 @@ _SIGS = {
     "helm_plan_tiles": (C.c_int, [_vp, C.POINTER(C.c_int)]),
     "helm_batch_set_tiles": (C.c_int, [_vp, C.c_int]),
     "helm_batch_set_cycle_class": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "helm_batch_submit_many": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                         C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
+                                         C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.c_double, C.c_int,
+                                         C.POINTER(C.c_uint64), C.POINTER(C.c_int)]),
+    "helm_batch_poll_many": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_uint64), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "helm_exit_time": (C.c_int, [_vp, C.c_double, C.c_int, _vp, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
     "helm_spectral_radius": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
@@ -279,6 +285,41 @@ def helm_plan_tiles(plan: _Plan) -> int:
     v = C.c_int()
     _check(load().helm_plan_tiles(plan.handle, C.byref(v)), "helm_plan_tiles")
     return v.value
+
+
+def helm_batch_submit_many(batch, jobs, prec: int, tol: float, max_outer: int):
+    """jobs: sequence of (ndim, n, h, k, f, g, u) with complex128 contiguous device tensors
+    (f interior n^D, g and u padded (n+2)^D).  Returns the tickets of the admitted prefix
+    (shorter than jobs when the memory cap stopped the submission)."""
+    import torch
+    m = len(jobs)
+    nd = (C.c_int * m)()
+    nn = (C.c_int * m)()
+    hh = (C.c_double * m)()
+    kk = (C.c_double * m)()
+    pf, pg, pu = (_vp * m)(), (_vp * m)(), (_vp * m)()
+    for i, (d, n, h, k, f, g, u) in enumerate(jobs):
+        for t, cnt, name in ((f, n ** d, "f"), (g, (n + 2) ** d, "g"), (u, (n + 2) ** d, "u")):
+            if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous() or t.numel() != cnt:
+                raise HelmError(HELM_EINVAL, f"helm_batch_submit_many: job {i}: bad {name}")
+        nd[i], nn[i], hh[i], kk[i] = int(d), int(n), float(h), float(k)
+        pf[i], pg[i], pu[i] = f.data_ptr(), g.data_ptr(), u.data_ptr()
+    tk = (C.c_uint64 * m)()
+    adm = C.c_int(0)
+    st = load().helm_batch_submit_many(batch.handle, m, nd, nn, hh, kk, int(prec), pf, pg, pu, float(tol),
+                                       int(max_outer), tk, C.byref(adm))
+    if st != HELM_ENOMEM:
+        _check(st, "helm_batch_submit_many")
+    return [tk[i] for i in range(adm.value)]
+
+
+def helm_batch_poll_many(batch, tickets):
+    """Returns [(done, status, iters)] for the tickets (status / iters valid when done)."""
+    m = len(tickets)
+    tk = (C.c_uint64 * m)(*tickets)
+    dn, stt, its = (C.c_int * m)(), (C.c_int * m)(), (C.c_int * m)()
+    _check(load().helm_batch_poll_many(batch.handle, m, tk, dn, stt, its), "helm_batch_poll_many")
+    return [(dn[i], stt[i], its[i]) for i in range(m)]
 
 
 def helm_batch_set_cycle_class(batch, ndim: int, prec: int, nu1: int, nu2: int, cycles: int = 1) -> None:

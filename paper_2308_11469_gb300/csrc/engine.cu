@@ -135,6 +135,7 @@ struct Instance {
     size_t ws_bytes = 0;
     double* hist = nullptr;      // device: relres (cap + 1) then einf (cap)
     int hist_cap = -1;
+    bool hist_sep = false;       // hist has its own allocation (regrown by a longer solve)
     bool stream_ordered = false; // allocated with cudaMallocAsync
     ResItem* d_res0 = nullptr;   // this instance's residual tiles (initial residual)
     int nres0 = 0;
@@ -782,19 +783,27 @@ struct Engine {
     }
 };
 
+// One allocation per instance: the workspace (levels, u[1], partials), then its residual
+// tile list, then the relres / increment histories.
 helm_status alloc_instance(Instance& in, int D, int n, double h, double k, int prec,
                            int max_outer, cudaStream_t s, bool stream_ordered)
 {
     in.prec = prec;
     in.stream_ordered = stream_ordered;
     in.ws_bytes = layout(in.d, D, n, h, k, prec, nullptr);
+    const int tz = res_tz(D, n);
+    in.nres0 = tz * in.d.res_ty * in.d.res_tx;
+    const size_t rb = align256((size_t)in.nres0 * sizeof(ResItem));
+    in.hist_cap = max_outer;
+    const size_t hb = (2 * (size_t)max_outer + 1) * sizeof(double);
+    const size_t total = align256(in.ws_bytes) + rb + hb;
     if (stream_ordered) {
-        HELM_CK(cudaMallocAsync((void**)&in.ws, in.ws_bytes, s));
+        HELM_CK(cudaMallocAsync((void**)&in.ws, total, s));
     } else {
-        cudaError_t e = cudaMalloc((void**)&in.ws, in.ws_bytes);
+        cudaError_t e = cudaMalloc((void**)&in.ws, total);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            snprintf(g_errbuf, sizeof g_errbuf, "cudaMalloc(%zu): %s", in.ws_bytes, cudaGetErrorString(e));
+            snprintf(g_errbuf, sizeof g_errbuf, "cudaMalloc(%zu): %s", total, cudaGetErrorString(e));
             return HELM_ENOMEM;
         }
     }
@@ -802,18 +811,10 @@ helm_status alloc_instance(Instance& in, int D, int n, double h, double k, int p
     // rings of the level iterates must be zero; clear everything once
     HELM_CK(cudaMemsetAsync(in.ws, 0, in.ws_bytes, s));
     // residual tiles of this instance (for its initial residual), listed on the device
-    const int tz = res_tz(D, n);
-    in.nres0 = tz * in.d.res_ty * in.d.res_tx;
-    const size_t rb = (size_t)in.nres0 * sizeof(ResItem);
-    if (stream_ordered) HELM_CK(cudaMallocAsync((void**)&in.d_res0, rb, s));
-    else HELM_CK(cudaMalloc((void**)&in.d_res0, rb));
+    in.d_res0 = (ResItem*)(in.ws + align256(in.ws_bytes));
     HELM_CK(launch_fill_res_items(in.d_res0, in.d.res_tx, in.d.res_ty, tz, s));
     g_launches += 1;
-    // history (relres and einf)
-    in.hist_cap = max_outer;
-    const size_t hb = (2 * (size_t)max_outer + 1) * sizeof(double);
-    if (stream_ordered) HELM_CK(cudaMallocAsync((void**)&in.hist, hb, s));
-    else HELM_CK(cudaMalloc((void**)&in.hist, hb));
+    in.hist = (double*)((char*)in.d_res0 + rb);
     in.d.hist = in.hist;
     in.d.einf = in.hist + max_outer + 1;
     return HELM_OK;
@@ -821,15 +822,12 @@ helm_status alloc_instance(Instance& in, int D, int n, double h, double k, int p
 
 void free_instance(Instance& in, cudaStream_t s)
 {
-    if (in.stream_ordered) {
-        if (in.ws) cudaFreeAsync(in.ws, s);
-        if (in.d_res0) cudaFreeAsync(in.d_res0, s);
-        if (in.hist) cudaFreeAsync(in.hist, s);
-    } else {
-        if (in.ws) cudaFree(in.ws);
-        if (in.d_res0) cudaFree(in.d_res0);
-        if (in.hist) cudaFree(in.hist);
+    if (in.ws) {
+        if (in.stream_ordered) cudaFreeAsync(in.ws, s);
+        else cudaFree(in.ws);
     }
+    if (in.hist_sep && in.hist) cudaFree(in.hist);
+    in.hist_sep = false;
     in.ws = nullptr;
     in.d_res0 = nullptr;
     in.hist = nullptr;
@@ -1118,10 +1116,12 @@ helm_status helm_solve_ex(helm_plan* p, const void* f, const void* g, void* u, d
     Instance& in = p->inst;
     if (max_outer > in.hist_cap) {
         HELM_CK(cudaStreamSynchronize(p->stream));
-        if (in.hist) cudaFree(in.hist);
+        if (in.hist_sep && in.hist) cudaFree(in.hist);   // else it lives in the workspace allocation
         in.hist = nullptr;
+        in.hist_sep = false;
         const size_t hb = (2 * (size_t)max_outer + 1) * sizeof(double);
         if (cudaMalloc((void**)&in.hist, hb) != cudaSuccess) { cudaGetLastError(); return HELM_ENOMEM; }
+        in.hist_sep = true;
         in.hist_cap = max_outer;
         in.d.hist = in.hist;
         in.d.einf = in.hist + max_outer + 1;
@@ -1506,6 +1506,39 @@ helm_status helm_batch_submit_geom(helm_batch* b, int ndim, int n, double h, dou
                                    int max_outer, uint64_t* ticket)
 {
     return submit_impl(b, ndim, n, h, k, prec, f, g, u, tol, max_outer, ticket);
+}
+
+helm_status helm_batch_submit_many(helm_batch* b, int count, const int* ndim, const int* n, const double* h,
+                                   const double* k, int prec, const void* const* f, const void* const* g,
+                                   void* const* u, double tol, int max_outer, uint64_t* tickets, int* admitted)
+{
+    if (!b || count < 0 || !admitted || (count > 0 && (!ndim || !n || !h || !k || !f || !g || !u || !tickets)))
+        return HELM_EINVAL;
+    *admitted = 0;
+    for (int i = 0; i < count; ++i) {
+        const helm_status st = submit_impl(b, ndim[i], n[i], h[i], k[i], prec, f[i], g[i], u[i], tol, max_outer,
+                                           &tickets[i]);
+        if (st != HELM_OK) return st;                 // HELM_ENOMEM: the rest wait for retirements
+        *admitted = i + 1;
+    }
+    return HELM_OK;
+}
+
+helm_status helm_batch_poll_many(helm_batch* b, int count, const uint64_t* tickets, int* done, int* status,
+                                 int* iters)
+{
+    if (!b || count < 0 || (count > 0 && (!tickets || !done))) return HELM_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        auto it = b->recs.find(tickets[i]);
+        if (it == b->recs.end()) return HELM_EINVAL;
+        helm_batch::Rec& r = it->second;
+        done[i] = r.done;
+        if (!r.done) continue;
+        if (status) status[i] = r.status;
+        if (iters) iters[i] = r.iters;
+        b->recs.erase(it);
+    }
+    return HELM_OK;
 }
 
 static helm_status retire_finished(helm_batch* b)

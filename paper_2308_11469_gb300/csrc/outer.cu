@@ -886,8 +886,10 @@ __device__ __forceinline__ void residual3d_tile_fx(const InstDesc* __restrict__ 
     else tile_done<R>(I, stp, tile, r2, emax2, MODE, st, c);
 }
 
+// (the start residual, once per solve, also forms ||b||: it runs at 4 CTAs per SM, whose 64
+// registers cut its spills from 260 to 88 bytes)
 template <typename R, int MODE, bool DAMP>
-__global__ void __launch_bounds__(NTH, RES3D_CTAS)
+__global__ void __launch_bounds__(NTH, MODE == 1 ? RES3D_CTAS : 4)
 k_residual3d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
              const ResItem* __restrict__ items, int nitems, StepCtl c)
 {

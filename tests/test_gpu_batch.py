@@ -281,3 +281,49 @@ def test_class_schedules_equal_solo_solves(B):
         assert np.array_equal(keep[i][2].cpu().numpy(), u.cpu().numpy())
     with pytest.raises(B.HelmError):
         B.helm_batch_set_cycle_class(B.helm_batch_create(0), 4, B.HELM_PREC_MIXED, 0, 1, 1)
+
+
+def test_submit_many_equals_single_submissions(B):
+    """Bulk submission and polling give the results of one-by-one submission bit for bit,
+    and a memory cap admits a prefix (the rest wait)."""
+    probs = inputs.batched_instances(count=16, seed=13)
+    tol, max_outer = 1e-8, 3000
+    data = [(torch.from_numpy(q.f).to(DEV), torch.from_numpy(q.g).to(DEV)) for q in probs]
+    U1 = [torch.zeros_like(g) for _, g in data]
+    batch = B.helm_batch_create(0)
+    ts = [B.helm_batch_submit_geom(batch, 2, q.n, q.h, q.k, B.HELM_PREC_MIXED, f, g, u, tol, max_outer)
+          for q, (f, g), u in zip(probs, data, U1)]
+    B.helm_batch_step(batch, 0)
+    r1 = [B.helm_batch_poll(batch, t, max_outer) for t in ts]
+    B.helm_batch_destroy(batch)
+    U2 = [torch.zeros_like(g) for _, g in data]
+    batch = B.helm_batch_create(0)
+    jobs = [(2, q.n, q.h, q.k, f, g, u) for q, (f, g), u in zip(probs, data, U2)]
+    ts = B.helm_batch_submit_many(batch, jobs, B.HELM_PREC_MIXED, tol, max_outer)
+    assert len(ts) == len(jobs)
+    B.helm_batch_step(batch, 0)
+    r2 = B.helm_batch_poll_many(batch, ts)
+    assert B.helm_batch_info(batch) == (0, 0)
+    B.helm_batch_destroy(batch)
+    for a, b, u1, u2 in zip(r1, r2, U1, U2):
+        assert b[0] == 1 and (a[0], a[1]) == (b[1], b[2])
+        assert torch.equal(u1, u2)
+    # a cap below the whole set: a prefix is admitted, the rest after retirements (each
+    # solve's reservation read from a batch holding it alone)
+    need = []
+    for q, (f, g) in zip(probs[:3], data[:3]):
+        b1 = B.helm_batch_create(0)
+        u = torch.zeros_like(g)
+        t = B.helm_batch_submit_geom(b1, 2, q.n, q.h, q.k, B.HELM_PREC_MIXED, f, g, u, tol, max_outer)
+        need.append(B.helm_batch_info(b1)[1])
+        B.helm_batch_step(b1, 0)
+        B.helm_batch_poll(b1, t, max_outer)
+        B.helm_batch_destroy(b1)
+    batch = B.helm_batch_create(int(need[0] + need[1] + need[2] // 2))
+    U3 = [torch.zeros_like(g) for _, g in data[:3]]
+    ts = B.helm_batch_submit_many(batch, [(2, q.n, q.h, q.k, f, g, u) for q, (f, g), u in
+                                         zip(probs[:3], data[:3], U3)], B.HELM_PREC_MIXED, tol, max_outer)
+    assert len(ts) == 2
+    B.helm_batch_step(batch, 0)
+    assert all(d == 1 for d, _, _ in B.helm_batch_poll_many(batch, ts))
+    B.helm_batch_destroy(batch)
