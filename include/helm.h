@@ -301,10 +301,12 @@ HELM_API helm_status helm_batch_submit_many(helm_batch* batch, int count, const 
                                             const void* const* f, const void* const* g, void* const* u,
                                             double tol, int max_outer, uint64_t* tickets, int* admitted);
 /* As helm_batch_poll for `count` tickets without the histories: done[i], and for the
- * finished ones status[i] and iters[i] (either array may be NULL); a finished solve's
- * record is released as by helm_batch_poll.  HELM_EINVAL for an unknown ticket. */
-HELM_API helm_status helm_batch_poll_many(helm_batch* batch, int count, const uint64_t* tickets, int* done,
-                                          int* status, int* iters);
+ * finished ones status[i] and iters[i] (either array may be NULL).  release = 1: each
+ * finished solve's record is released as by helm_batch_poll (its history discarded);
+ * release = 0: nothing is released (helm_batch_poll then returns the history and releases
+ * it).  HELM_EINVAL for an unknown ticket. */
+HELM_API helm_status helm_batch_poll_many(helm_batch* batch, int count, const uint64_t* tickets, int release,
+                                          int* done, int* status, int* iters);
 /* Inner schedule (as helm_plan_set_cycle) used by every solve of the batch from the next
  * step on (the batch's solves share their launches, hence one schedule). */
 HELM_API helm_status helm_batch_set_cycle(helm_batch* batch, int nu1, int nu2, int cycles);

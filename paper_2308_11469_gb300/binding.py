@@ -54,7 +54,7 @@ _SIGS = {
                                          C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
                                          C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.c_double, C.c_int,
                                          C.POINTER(C.c_uint64), C.POINTER(C.c_int)]),
-    "helm_batch_poll_many": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_uint64), C.POINTER(C.c_int),
+    "helm_batch_poll_many": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_uint64), C.c_int, C.POINTER(C.c_int),
                                        C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "helm_exit_time": (C.c_int, [_vp, C.c_double, C.c_int, _vp, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
@@ -313,12 +313,15 @@ def helm_batch_submit_many(batch, jobs, prec: int, tol: float, max_outer: int):
     return [tk[i] for i in range(adm.value)]
 
 
-def helm_batch_poll_many(batch, tickets):
-    """Returns [(done, status, iters)] for the tickets (status / iters valid when done)."""
+def helm_batch_poll_many(batch, tickets, release: bool = True):
+    """Returns [(done, status, iters)] for the tickets (status / iters valid when done);
+    release=False keeps the finished solves' records (helm_batch_poll then returns the
+    history)."""
     m = len(tickets)
     tk = (C.c_uint64 * m)(*tickets)
     dn, stt, its = (C.c_int * m)(), (C.c_int * m)(), (C.c_int * m)()
-    _check(load().helm_batch_poll_many(batch.handle, m, tk, dn, stt, its), "helm_batch_poll_many")
+    _check(load().helm_batch_poll_many(batch.handle, m, tk, 1 if release else 0, dn, stt, its),
+           "helm_batch_poll_many")
     return [(dn[i], stt[i], its[i]) for i in range(m)]
 
 

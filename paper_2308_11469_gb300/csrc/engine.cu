@@ -1524,8 +1524,8 @@ helm_status helm_batch_submit_many(helm_batch* b, int count, const int* ndim, co
     return HELM_OK;
 }
 
-helm_status helm_batch_poll_many(helm_batch* b, int count, const uint64_t* tickets, int* done, int* status,
-                                 int* iters)
+helm_status helm_batch_poll_many(helm_batch* b, int count, const uint64_t* tickets, int release, int* done,
+                                 int* status, int* iters)
 {
     if (!b || count < 0 || (count > 0 && (!tickets || !done))) return HELM_EINVAL;
     for (int i = 0; i < count; ++i) {
@@ -1536,7 +1536,7 @@ helm_status helm_batch_poll_many(helm_batch* b, int count, const uint64_t* ticke
         if (!r.done) continue;
         if (status) status[i] = r.status;
         if (iters) iters[i] = r.iters;
-        b->recs.erase(it);
+        if (release) b->recs.erase(it);
     }
     return HELM_OK;
 }

@@ -76,19 +76,27 @@ class Server:
         self.queue.append(job)
 
     def admit(self) -> int:
-        """Admit queued jobs in arrival order while the memory cap allows."""
+        """Admit queued jobs in arrival order while the memory cap allows (one library call
+        per run of jobs sharing a tolerance and step budget)."""
         n = 0
         while self.queue:
-            job = self.queue[0]
-            t = B.helm_batch_submit_geom(self.batch, job.D, job.n, job.h, job.k, self.prec,
-                                         job.f, job.g, job.u, job.tol, job.max_outer)
-            if t is None:
+            head = self.queue[0]
+            run = []
+            for job in self.queue:
+                if job.tol != head.tol or job.max_outer != head.max_outer:
+                    break
+                run.append(job)
+            ts = B.helm_batch_submit_many(self.batch, [(j.D, j.n, j.h, j.k, j.f, j.g, j.u) for j in run],
+                                          self.prec, head.tol, head.max_outer)
+            now = self.clock()
+            for job, t in zip(run, ts):
+                job.ticket = t
+                job.t_admit = now
+                self.active[t] = job
+                self.queue.popleft()
+            n += len(ts)
+            if len(ts) < len(run):
                 break                       # over the cap: wait for retirements
-            job.ticket = t
-            job.t_admit = self.clock()
-            self.active[t] = job
-            self.queue.popleft()
-            n += 1
         a, used = B.helm_batch_info(self.batch)
         self.max_in_use = max(self.max_in_use, used)
         return n
@@ -100,13 +108,14 @@ class Server:
         B.helm_batch_step(self.batch, self.chunk)
         now = self.clock()
         fin = []
-        for t, job in list(self.active.items()):
-            r = B.helm_batch_poll(self.batch, t, job.max_outer)
-            if r is not None:
-                job.status, job.iters, job.hist = r
-                job.t_done = now
-                fin.append(job)
-                del self.active[t]
+        tickets = list(self.active)
+        for t, (done, _, _) in zip(tickets, B.helm_batch_poll_many(self.batch, tickets, release=False)):
+            if not done:
+                continue
+            job = self.active.pop(t)
+            job.status, job.iters, job.hist = B.helm_batch_poll(self.batch, t, job.max_outer)
+            job.t_done = now
+            fin.append(job)
         self.done.extend(fin)
         return fin
 

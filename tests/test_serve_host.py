@@ -37,6 +37,19 @@ class FakeBatch:
             return (0, self.steps[rid], np.ones(self.steps[rid] + 1))
         return None
 
+    def submit_many(self, jobs):
+        out = []
+        for job in jobs:
+            t = self.submit(job[4])          # the job's f carries its request id here
+            if t is None:
+                break
+            out.append(t)
+        return out
+
+    def peek(self, t):
+        rid, s = self.live[t]
+        return (1, 0, self.steps[rid]) if s >= self.steps[rid] else (0, 0, 0)
+
 
 @pytest.fixture
 def fake(monkeypatch):
@@ -51,6 +64,9 @@ def fake(monkeypatch):
                         lambda b, D, n, h, k, prec, f, g, u, tol, mo: b.submit(f))
     monkeypatch.setattr(binding, "helm_batch_step", lambda b, k: b.step(k))
     monkeypatch.setattr(binding, "helm_batch_poll", lambda b, t, mo: b.poll(t))
+    monkeypatch.setattr(binding, "helm_batch_submit_many", lambda b, jobs, prec, tol, mo: b.submit_many(jobs))
+    monkeypatch.setattr(binding, "helm_batch_poll_many",
+                        lambda b, ts, release=True: [b.peek(t) for t in ts])
     monkeypatch.setattr(binding, "helm_batch_info",
                         lambda b: (len(b.live), sum(b.cost[r] for r, _ in b.live.values())))
     monkeypatch.setattr(binding, "helm_batch_destroy", lambda b: None)
