@@ -182,7 +182,8 @@ HELM_API helm_status helm_plan_set_cycle(helm_plan* plan, int nu1, int nu2, int 
  * the timings meaningless: pass the starting iterate of the solves to be tuned (zeros
  * for the paper's start).  u is restored to the starting iterate.  2D plans then time the
  * three tile-shape policies (helm_plan_set_tiles) with the chosen schedule and keep the
- * fastest.  HELM_DIVERGED if no candidate converged (schedule unchanged).  Allocates one
+ * fastest, and 2D complex64 plans then the coarse-level policies HELM_COARSE_AUTO and
+ * HELM_COARSE_CTA (helm_plan_set_coarse_mode).  HELM_DIVERGED if no candidate converged (schedule unchanged).  Allocates one
  * temporary copy of u. */
 HELM_API helm_status helm_plan_autotune(helm_plan* plan, const void* f, const void* g, void* u,
                                         double tol, int max_outer, int* nu1, int* nu2,
@@ -202,6 +203,26 @@ HELM_API helm_status helm_plan_autotune(helm_plan* plan, const void* f, const vo
 #define HELM_TILES_SMALL 2
 HELM_API helm_status helm_plan_set_tiles(helm_plan* plan, int policy);
 HELM_API helm_status helm_plan_tiles(const helm_plan* plan, int* policy);
+
+/* Where the coarse levels of 2D complex64 V-cycles run (this project's scheduling, no paper
+ * counterpart; the cycle's operations are the same either way).  HELM_COARSE_CTA: the
+ * levels above 63 in the fused tile kernels, levels 63 and below (31 solved exactly) in one
+ * CTA per solve.  HELM_COARSE_CLUSTER: for cycles without pre-smoothing (nu1 = 0, nu2 = 1
+ * or 2) of solves with n >= 511, levels 255, 127, 63 and the exact level 31 in one launch of
+ * an 8-CTA thread-block cluster per solve (row bands per CTA, rhs halos exchanged through
+ * distributed shared memory), replacing four fused level launches and the one-CTA tail;
+ * other schedules and sizes keep the CTA form.  HELM_COARSE_AUTO (default): the cluster where
+ * it applies to every solve of the launch and the clusters fit in one wave (at most 19
+ * solves), else the CTA form; also the CTA form when the device cannot hold one cluster.
+ * The results agree to the inner precision's rounding.  helm_plan_coarse_mode reports the
+ * policy and, if cluster_used is not NULL, whether the plan's last built outer step used the
+ * cluster (0 before its first solve).  helm_batch_set_coarse_mode applies a policy to every
+ * solve of a batch.  HELM_EINVAL for an unknown mode. */
+#define HELM_COARSE_AUTO 0
+#define HELM_COARSE_CTA 1
+#define HELM_COARSE_CLUSTER 2
+HELM_API helm_status helm_plan_set_coarse_mode(helm_plan* plan, int mode);
+HELM_API helm_status helm_plan_coarse_mode(const helm_plan* plan, int* mode, int* cluster_used);
 
 /*
  * Solve (Delta_h + k^2) u = f, u = g on the wall, by the outer Poisson iteration
@@ -317,6 +338,7 @@ HELM_API helm_status helm_batch_set_cycle(helm_batch* batch, int nu1, int nu2, i
 HELM_API helm_status helm_batch_set_cycle_class(helm_batch* batch, int ndim, int prec, int nu1, int nu2,
                                                 int cycles);
 HELM_API helm_status helm_batch_set_tiles(helm_batch* batch, int policy);
+HELM_API helm_status helm_batch_set_coarse_mode(helm_batch* batch, int mode);
 /* Solves of one kernel class (dimension, precision) are spread over `lanes` (1 ..
  * HELM_MAX_LANES, default 4) independent launch streams: each submission joins the lane
  * with the least predicted work (outer steps from the closed-form contraction and the

@@ -49,6 +49,9 @@ _SIGS = {
     "helm_plan_set_tiles": (C.c_int, [_vp, C.c_int]),
     "helm_plan_tiles": (C.c_int, [_vp, C.POINTER(C.c_int)]),
     "helm_batch_set_tiles": (C.c_int, [_vp, C.c_int]),
+    "helm_plan_set_coarse_mode": (C.c_int, [_vp, C.c_int]),
+    "helm_plan_coarse_mode": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "helm_batch_set_coarse_mode": (C.c_int, [_vp, C.c_int]),
     "helm_batch_set_cycle_class": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "helm_batch_submit_many": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                          C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
@@ -101,7 +104,8 @@ _SIGS = {
 
 KERNEL_KINDS = ["rbgs_half_sweep", "residual_restrict", "prolong_correct", "zero",
                 "coarse_tail", "helmholtz_residual_update", "convergence_check",
-                "smooth_restrict_2d", "prolong_smooth_2d", "ascent_residual_update_2d"]
+                "smooth_restrict_2d", "prolong_smooth_2d", "ascent_residual_update_2d",
+                "cluster_tail"]
 
 _lib = None
 
@@ -287,6 +291,22 @@ def helm_plan_tiles(plan: _Plan) -> int:
     return v.value
 
 
+HELM_COARSE_AUTO = 0
+HELM_COARSE_CTA = 1
+HELM_COARSE_CLUSTER = 2
+
+
+def helm_plan_set_coarse_mode(plan: _Plan, mode: int) -> None:
+    _check(load().helm_plan_set_coarse_mode(plan.handle, int(mode)), "helm_plan_set_coarse_mode")
+
+
+def helm_plan_coarse_mode(plan: _Plan) -> tuple[int, int]:
+    """(policy, whether the last built outer step used the cluster tail)."""
+    m, used = C.c_int(), C.c_int()
+    _check(load().helm_plan_coarse_mode(plan.handle, C.byref(m), C.byref(used)), "helm_plan_coarse_mode")
+    return m.value, used.value
+
+
 def helm_batch_submit_many(batch, jobs, prec: int, tol: float, max_outer: int):
     """jobs: sequence of (ndim, n, h, k, f, g, u) with complex128 contiguous device tensors
     (f interior n^D, g and u padded (n+2)^D).  Returns the tickets of the admitted prefix
@@ -332,6 +352,10 @@ def helm_batch_set_cycle_class(batch, ndim: int, prec: int, nu1: int, nu2: int, 
 
 def helm_batch_set_tiles(batch, policy: int) -> None:
     _check(load().helm_batch_set_tiles(batch.handle, int(policy)), "helm_batch_set_tiles")
+
+
+def helm_batch_set_coarse_mode(batch, mode: int) -> None:
+    _check(load().helm_batch_set_coarse_mode(batch.handle, int(mode)), "helm_batch_set_coarse_mode")
 
 
 def helm_plan_autotune(plan: _Plan, f, g, u, tol: float, max_outer: int):

@@ -142,7 +142,7 @@ struct Instance {
 };
 
 struct LaunchRec {
-    enum Kind { RBGS, RESTRICT, PROLONG, ZERO, TAIL, RESID, CHECK, DOWN, UP, UPRES, NKINDS } kind;
+    enum Kind { RBGS, RESTRICT, PROLONG, ZERO, TAIL, RESID, CHECK, DOWN, UP, UPRES, CTAIL, NKINDS } kind;
     int off, cnt, work, color, mode;
     double bytes;   // algorithmic bytes of one launch (each datum it must touch, once)
     int nmax = 0;   // DOWN: the largest level of the launch; UPRES: the level-0 size
@@ -185,6 +185,11 @@ struct Engine {
     // the large tiles would leave the GPU under-filled), _LARGE (64 x 32 wherever allowed),
     // _SMALL (32 x 16 on levels up to 511)
     int tiles = HELM_TILES_AUTO;
+    // coarse levels of 2D complex64 cycles without pre-smoothing: HELM_COARSE_AUTO (levels
+    // 255 and below in one 8-CTA cluster per instance when every instance is at least 511
+    // and the clusters fit in one wave), _CTA (one-CTA tail from level 63, fused kernels
+    // above), _CLUSTER (the cluster wherever it applies)
+    int coarse = HELM_COARSE_AUTO;
     cudaStream_t cap_stream = nullptr;
     int cap = 0;                               // descriptor slots
     std::vector<Instance*> slots;              // nullptr = free
@@ -273,6 +278,7 @@ struct Engine {
         HELM_CK(cudaMallocHost(&h_ctrl, 4 * sizeof(int)));
         HELM_CK(setup_tail(D, prec == HELM_PREC_FP64 ? 0 : 1));
         if (D == 2) HELM_CK(setup_2d(prec == HELM_PREC_FP64 ? 0 : 1));
+        if (D == 2 && prec != HELM_PREC_FP64) ctail_setup();
         HELM_CK(setup_generic(D, prec == HELM_PREC_FP64 ? 0 : 1));
         HELM_CK(setup_outer());
         return grow(4);
@@ -430,18 +436,39 @@ struct Engine {
             HELM_CK(cudaMemcpy(d_res, res.data(), res.size() * sizeof(ResItem), cudaMemcpyHostToDevice));
         nres = (int)res.size();
 
+        // cluster tail: every instance has a level 255 below its top (n >= 511), the cycle
+        // has no pre-smoothing (every level it runs starts from zero) and nu2 <= 2
+        bool use_ct = false;
+        if (D == 2 && prec != HELM_PREC_FP64 && nu1 == 0 && (nu2 == 1 || nu2 == 2) &&
+            coarse != HELM_COARSE_CTA && J >= 3) {
+            int nocc = 0;
+            bool all = true;
+            for (int i = 0; i < cap; ++i) {
+                if (!slots[i]) continue;
+                const InstDesc& d = slots[i]->d;
+                ++nocc;
+                if (d.ltail < 3 || d.lev[d.ltail - 2].n != 255 || d.lev[d.ltail].n != 63) all = false;
+            }
+            use_ct = all && nocc > 0 && (coarse == HELM_COARSE_CLUSTER || nocc * 8 <= 152) &&
+                     ctail_setup() == 1;
+        }
         auto tail = [&](std::vector<LaunchRec>& out, bool zero_start) {
             for (const TailGroup& tg : tails)
                 out.push_back({LaunchRec::TAIL, tg.off, tg.cnt, tg.n0, 0, zero_start ? 0 : 1, tg.bytes});
         };
         auto vcycle2d = [&](std::vector<LaunchRec>& out, bool zero_start) {
-            for (int j = 0; j < J; ++j)
+            const int Jf = use_ct ? J - 2 : J;         // levels of the fused tile kernels
+            for (int j = 0; j < Jf; ++j)
                 out.push_back({LaunchRec::DOWN, ph[j].off, ph[j].cnt, ph[j].tiles, ph[j].shape,
                                zero_start ? 2 : 1, 0.0, ph[j].nmax});
-            tail(out, zero_start);
+            if (use_ct)
+                out.push_back({LaunchRec::CTAIL, ph[Jf].off, ph[Jf].cnt, 0, 0, 0,
+                               2.0 * pts(255) * eb * ph[Jf].cnt});
+            else
+                tail(out, zero_start);
             // without pre-smoothing the descent leaves e2 unwritten where the iterate was zero
             const int e2_mode = (nu1 == 0) ? (zero_start ? 2 : 1) : 0;
-            for (int j = J - 1; j >= 0; --j)
+            for (int j = Jf - 1; j >= 0; --j)
                 out.push_back({LaunchRec::UP, ph[j].off, ph[j].cnt, ph[j].tiles, ph[j].shape, e2_mode, 0.0});
         };
         auto vcycle = [&](std::vector<LaunchRec>& out, bool zero_start) {
@@ -545,6 +572,7 @@ struct Engine {
             }
             case LaunchRec::ZERO: b += pts(n) * eb; break;
             case LaunchRec::TAIL: b += 2.0 * pts(n) * eb; break;
+            case LaunchRec::CTAIL: b += 2.0 * pts(n) * eb; break;
             case LaunchRec::DOWN: {
                 const bool zero = (L.mode == 2) || (L.mode == 1 && it.level > 0);
                 if (zero && nu1 == 0) b += (pts(n) + pts(nc)) * eb;      // rhs in, coarse rhs out
@@ -582,6 +610,9 @@ struct Engine {
             case LaunchRec::TAIL:
                 e = launch_tail(D, prec, L.work, d_desc, d_state, d_mg + L.off, L.cnt, nu1, nu2,
                                 L.mode, s);
+                break;
+            case LaunchRec::CTAIL:
+                e = launch_ctail(d_desc, d_state, d_mg + L.off, L.cnt, nu2, s);
                 break;
             case LaunchRec::DOWN:
                 e = launch_down2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu1, L.mode, L.color, s,
@@ -645,7 +676,7 @@ struct Engine {
     // whether any instance has a damping term (it selects the residual kernels' variant).
     std::vector<long> current_signature() const
     {
-        std::vector<long> sig{cap, nu1, nu2, cycles, tiles};
+        std::vector<long> sig{cap, nu1, nu2, cycles, tiles, coarse};
         long damp = 0;
         for (int i = 0; i < cap; ++i) {
             sig.push_back(slots[i] ? (long)slots[i]->d.n * 4 + (long)slots[i]->d.D : -1L);
@@ -878,6 +909,7 @@ struct helm_batch {
     size_t cap_bytes = 0, used = 0;
     int nu1 = 2, nu2 = 2, cycles = 1;           // inner schedule of every engine
     int tiles = HELM_TILES_AUTO;                // 2D tile-shape policy of every engine
+    int coarse = HELM_COARSE_AUTO;              // coarse-level policy of every engine
     // per kernel class (2 D + prec): a schedule set by helm_batch_set_cycle_class, used
     // instead of the batch-wide one by that class's engines ({0, 0, 0}: none)
     int cls_sched[8][3] = {};
@@ -1180,7 +1212,7 @@ helm_status helm_plan_autotune(helm_plan* p, const void* f, const void* g, void*
     cudaEvent_t e0, e1;
     HELM_CK(cudaEventCreate(&e0));
     HELM_CK(cudaEventCreate(&e1));
-    const int s1 = p->eng.nu1, s2 = p->eng.nu2, sc = p->eng.cycles, st0 = p->eng.tiles;
+    const int s1 = p->eng.nu1, s2 = p->eng.nu2, sc = p->eng.cycles, st0 = p->eng.tiles, cm0 = p->eng.coarse;
     // best of two timed solves after a first one that builds the graph; HELM_CONVERGED and
     // the time, or the first solve's outcome
     auto time_solve = [&](float* ms_out) -> helm_status {
@@ -1199,7 +1231,7 @@ helm_status helm_plan_autotune(helm_plan* p, const void* f, const void* g, void*
         *ms_out = best;
         return HELM_CONVERGED;
     };
-    int bi = -1, bt = st0;
+    int bi = -1, bt = st0, bc = cm0;
     float bms = 0.f;
     helm_status st = HELM_OK;
     for (int c = 0; c < (int)(sizeof cand / sizeof cand[0]); ++c) {
@@ -1229,6 +1261,22 @@ helm_status helm_plan_autotune(helm_plan* p, const void* f, const void* g, void*
             }
         }
     }
+    // 2D complex64: the one-CTA coarse tail against the cluster tail (where it applies)
+    if (st == HELM_OK && bi >= 0 && p->D == 2 && p->prec != HELM_PREC_FP64) {
+        p->eng.tiles = bt;
+        for (int cm = HELM_COARSE_AUTO; cm <= HELM_COARSE_CTA; ++cm) {
+            if (cm == cm0) continue;
+            p->eng.coarse = cm;
+            p->eng.dirty = true;
+            float ms = 0.f;
+            const helm_status out = time_solve(&ms);
+            if (out < 0) { st = out; break; }
+            if (out == HELM_CONVERGED && ms < bms) {
+                bc = cm;
+                bms = ms;
+            }
+        }
+    }
     HELM_CK(cudaMemcpyAsync(u, saved, ub, cudaMemcpyDeviceToDevice, p->stream));
     HELM_CK(cudaFreeAsync(saved, p->stream));
     HELM_CK(cudaStreamSynchronize(p->stream));
@@ -1237,11 +1285,13 @@ helm_status helm_plan_autotune(helm_plan* p, const void* f, const void* g, void*
     if (st != HELM_OK || bi < 0) {                         // error, or nothing converged: keep the old schedule
         helm_plan_set_cycle(p, s1, s2, sc);
         p->eng.tiles = st0;
+        p->eng.coarse = cm0;
         p->eng.dirty = true;
         return st != HELM_OK ? st : HELM_DIVERGED;
     }
     helm_plan_set_cycle(p, cand[bi][0], cand[bi][1], cand[bi][2]);
     p->eng.tiles = bt;
+    p->eng.coarse = bc;
     p->eng.dirty = true;
     if (nu1_out) *nu1_out = cand[bi][0];
     if (nu2_out) *nu2_out = cand[bi][1];
@@ -1262,6 +1312,26 @@ helm_status helm_plan_tiles(const helm_plan* p, int* policy)
 {
     if (!p || !policy) return HELM_EINVAL;
     *policy = p->eng.tiles;
+    return HELM_OK;
+}
+
+helm_status helm_plan_set_coarse_mode(helm_plan* p, int mode)
+{
+    if (!p || mode < HELM_COARSE_AUTO || mode > HELM_COARSE_CLUSTER) return HELM_EINVAL;
+    p->eng.coarse = mode;
+    p->eng.dirty = true;
+    return HELM_OK;
+}
+
+helm_status helm_plan_coarse_mode(const helm_plan* p, int* mode, int* cluster_used)
+{
+    if (!p || !mode) return HELM_EINVAL;
+    *mode = p->eng.coarse;
+    if (cluster_used) {
+        int used = 0;
+        for (const LaunchRec& L : p->eng.step) used |= (L.kind == LaunchRec::CTAIL) ? 1 : 0;
+        *cluster_used = used;
+    }
     return HELM_OK;
 }
 
@@ -1454,6 +1524,7 @@ static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, 
         ne->nu2 = cs[2] ? cs[1] : b->nu2;
         ne->cycles = cs[2] ? cs[2] : b->cycles;
         ne->tiles = b->tiles;
+        ne->coarse = b->coarse;
         E = ne.get();
         b->engines[key] = std::move(ne);
     } else {
@@ -1617,6 +1688,18 @@ helm_status helm_batch_set_tiles(helm_batch* b, int policy)
     b->tiles = policy;
     for (auto& kv : b->engines) {
         kv.second->tiles = policy;
+        kv.second->dirty = true;
+        kv.second->plan_sig.clear();
+    }
+    return HELM_OK;
+}
+
+helm_status helm_batch_set_coarse_mode(helm_batch* b, int mode)
+{
+    if (!b || mode < HELM_COARSE_AUTO || mode > HELM_COARSE_CLUSTER) return HELM_EINVAL;
+    b->coarse = mode;
+    for (auto& kv : b->engines) {
+        kv.second->coarse = mode;
         kv.second->dirty = true;
         kv.second->plan_sig.clear();
     }

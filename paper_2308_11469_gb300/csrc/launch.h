@@ -55,6 +55,13 @@ size_t tail_smem_bytes(int D, int prec, int n);
 int tail_exact_n(int D, int prec);
 // raise the tail kernel's dynamic shared-memory limit (once, before any capture)
 cudaError_t setup_tail(int D, int prec);
+// cluster tail (2D complex64, cycles without pre-smoothing, level 255 below the top): one
+// 8-CTA cluster per item runs levels 255 (the item's level), 127, 63 and the exact level 31
+// and writes level 255's iterate; nu2 in {1, 2}.  ctail_setup() sets its attributes once and
+// tells whether a cluster of it fits on the device (1) or not (0).
+int ctail_setup();
+cudaError_t launch_ctail(const InstDesc* insts, const InstState* st, const MgItem* items, int nitems,
+                         int nu2, cudaStream_t s);
 // shared-memory carve-out preferences of the generic and outer kernels
 cudaError_t setup_generic(int D, int prec);
 cudaError_t setup_outer();

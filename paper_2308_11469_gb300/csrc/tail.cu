@@ -20,11 +20,15 @@
 #include <cmath>
 #include <type_traits>
 
+#include <cooperative_groups.h>
+
 #include "launch.h"
 #include "pdl.cuh"
 
 namespace helm {
 namespace {
+
+namespace cg = cooperative_groups;
 
 constexpr int TNT = 1024;
 
@@ -655,6 +659,347 @@ k_tail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster tail (2D, complex64): levels 255, 127 and 63 in row bands over an 8-CTA
+// thread-block cluster, the n = 31 level solved exactly (sine basis) in every CTA
+// ---------------------------------------------------------------------------
+// Used for cycles without pre-smoothing (nu1 = 0) whose level 255 is below the top, so
+// every level the cluster runs starts from a zero iterate: the descent is the full
+// weighting of the rhs, the ascent assigns the prolongation and smooths.  CTA k of the
+// cluster owns rows 32k+1..32k+32 of level 255, 16k+1..16k+16 of level 127, 8k+1..8k+8 of
+// level 63 and 4k+1..4k+4 of level 31.
+//
+//  * Descent: level 255's rhs rows 32k+1-(2 nu2-1) .. 32k+39 are staged from global memory;
+//    each CTA restricts its own rows of every level plus the rows just below them that its
+//    next restriction reads (levels 127: 16k+1..16k+19, 63: 8k+1..8k+9, 31: own), the extra
+//    rows equal to their owners' values (same inputs, same operations).  One cluster barrier,
+//    then every CTA copies from its neighbours' shared memory (distributed shared memory)
+//    the other rhs rows its windows need; of level 31, all of them.
+//  * Every CTA solves level 31 exactly from the same rhs: the same values in every CTA.
+//  * Ascent: a CTA prolongs and smooths a window of rows around its band wide enough that
+//    its final values are right where the next finer level reads them: a half-sweep
+//    updates rows one closer to the band than the previous one (2 nu2 half-sweeps need 2
+//    nu2 extra rows of the prolonged iterate and 2 nu2 - 1 of the rhs, per side), the
+//    halo values being recomputed from the same inputs as the owner's.  No exchange is
+//    needed on the way up; level 255's rhs window is staged again for its sweeps.
+//
+// Operations, colours and weights are those of the one-CTA tail and of the fused tile
+// kernels (full weighting in the same order, the prolongation's four-corner sum, the
+// half-sweep formula), so the cycle is the same.
+constexpr int CT_CS = 8;                                   // CTAs per cluster
+constexpr int CT_NA = 255, CT_NB = 127, CT_NC = 63;
+constexpr int CT_SA = CT_NA + 2, CT_SB = CT_NB + 2, CT_SC = CT_NC + 2, CT_SX = XN + 2;
+
+constexpr int fdiv2(int a) { return a >= 0 ? a / 2 : -((1 - a) / 2); }    // floor(a / 2)
+
+// Row windows of CTA k (first row = band * k + OFF, ROWS rows) for nu2 = V.  F_l: rows
+// of level l whose final values the next finer level's window reads.
+template <int V> struct CtWin {
+    // level 255: F = own rows; iterate F +- 2V, rhs F +- (2V - 1)
+    static constexpr int EA_OFF = 1 - 2 * V, EA_ROWS = 32 + 4 * V;
+    static constexpr int RA_OFF = 2 - 2 * V, RA_ROWS = (31 + 2 * V > 39 ? 31 + 2 * V : 39) - RA_OFF + 1;
+    // level 127: F = [16k - V, 16k + 16 + V] (coarse rows of level 255's iterate window)
+    static constexpr int FB_LO = -V, FB_HI = 16 + V;
+    static constexpr int EB_OFF = FB_LO - 2 * V, EB_ROWS = FB_HI - FB_LO + 4 * V + 1;
+    static constexpr int RB_OFF = FB_LO - (2 * V - 1);
+    static constexpr int RB_ROWS = (FB_HI + 2 * V - 1 > 19 ? FB_HI + 2 * V - 1 : 19) - RB_OFF + 1;
+    // level 63: F = coarse rows of level 127's iterate window
+    static constexpr int FC_LO = fdiv2(EB_OFF), FC_HI = fdiv2(EB_OFF + EB_ROWS);
+    static constexpr int EC_OFF = FC_LO - 2 * V, EC_ROWS = FC_HI - FC_LO + 4 * V + 1;
+    static constexpr int RC_OFF = FC_LO - (2 * V - 1), RC_ROWS = FC_HI - FC_LO + 4 * V - 1;
+    // shared memory (float2 units): level 255's iterate window, whose space holds levels 63
+    // and 31 and the sine scratch until level 255 is prolonged; level 127's windows; level
+    // 255's rhs window (staged once, read by the restriction and the last sweeps)
+    static constexpr int O_EC = 0;
+    static constexpr int O_RC = O_EC + EC_ROWS * CT_SC;
+    static constexpr int O_EX = O_RC + RC_ROWS * CT_SC;
+    static constexpr int O_RX = O_EX + CT_SX * CT_SX;
+    static constexpr int O_SCR = (O_RX + CT_SX * CT_SX + 1) & ~1;        // 16-byte aligned
+    static constexpr int A_WORDS = EA_ROWS * CT_SA;
+    static constexpr int O_EB = (A_WORDS + 1) & ~1;
+    static constexpr int O_RB = O_EB + EB_ROWS * CT_SB;
+    static constexpr int O_RA = O_RB + RB_ROWS * CT_SB;
+    static constexpr size_t BYTES = (size_t)(O_RA + RA_ROWS * CT_SA) * sizeof(float2);
+    static_assert(O_SCR * 2 + XSCR_FLOATS <= 2 * A_WORDS, "levels 63 and 31 inside level 255's window");
+    static_assert(BYTES <= 232448, "shared memory of one CTA");
+};
+
+// element (x, y) of a row window of a level with n = N whose first row is `lo`
+template <int N> __device__ __forceinline__ int bw(int lo, int y, int x)
+{
+    return (y - lo) * (N + 2) + ix<N>(x);
+}
+
+// coarse rows [Ya, Yb] (within 1..NC) of the full weighting of the fine rhs window
+template <int N>
+__device__ __forceinline__ void ct_restrict(const float2* Rf, int flo, float2* Rc, int clo, int Ya, int Yb)
+{
+    constexpr int NC = (N - 1) / 2;
+    const int lane = threadIdx.x & 31;
+    Ya = max(Ya, 1);
+    Yb = min(Yb, NC);
+    for (int Y = Ya + (int)(threadIdx.x >> 5); Y <= Yb; Y += TNT / 32) {
+        for (int X = lane + 1; X <= NC; X += 32) {
+            float ax = 0.f, ay = 0.f;
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const float wy = (dy == 0) ? 2.f : 1.f;
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const float w = wy * ((dx == 0) ? 2.f : 1.f);
+                    const float2 rr = Rf[bw<N>(flo, 2 * Y + dy, 2 * X + dx)];
+                    ax += w * rr.x;
+                    ay += w * rr.y;
+                }
+            }
+            float2 v;
+            v.x = ax * (1.f / 16.f);
+            v.y = ay * (1.f / 16.f);
+            Rc[bw<NC>(clo, Y, X)] = v;
+        }
+    }
+}
+
+// fine rows [ya, yb] (within 1..N) of the window := multilinear interpolation of the coarse
+// window (the fine iterate is zero: 0 + the interpolation, as the correction of a zero
+// iterate rounds).  A lane forms the pair x = 2q + 1 (coarse columns q, q + 1) and x = 2q + 2
+// (column q + 1 twice) from the same coarse words, summed in the order of the tile kernels:
+// ((row y0 col 0 + row y0 col 1) + row y1 col 0) + row y1 col 1.
+template <int N>
+__device__ __forceinline__ void ct_prolong(float2* Ef, int flo, const float2* Ec, int clo, int ya, int yb)
+{
+    constexpr int NC = (N - 1) / 2;
+    constexpr int S = N + 2, SC = NC + 2;
+    constexpr int HE = Lv<2, N>::HE;
+    const int lane = threadIdx.x & 31;
+    ya = max(ya, 1);
+    yb = min(yb, N);
+    for (int y = ya + (int)(threadIdx.x >> 5); y <= yb; y += TNT / 32) {
+        const int row = (y - flo) * S;
+        const int r0 = ((y >> 1) - clo) * SC, r1 = (((y + 1) >> 1) - clo) * SC;
+        for (int q = lane; q <= NC; q += 32) {
+            const float2 a0 = Ec[r0 + ix<NC>(q)], a1 = Ec[r0 + ix<NC>(q + 1)];
+            const float2 b0 = Ec[r1 + ix<NC>(q)], b1 = Ec[r1 + ix<NC>(q + 1)];
+            float2 v;
+            v.x = 0.f + 0.25f * (((a0.x + a1.x) + b0.x) + b1.x);
+            v.y = 0.f + 0.25f * (((a0.y + a1.y) + b0.y) + b1.y);
+            Ef[row + HE + q] = v;                            // x = 2q + 1
+            if (q < NC) {                                    // x = 2q + 2
+                v.x = 0.f + 0.25f * (((a1.x + a1.x) + b1.x) + b1.x);
+                v.y = 0.f + 0.25f * (((a1.y + a1.y) + b1.y) + b1.y);
+                Ef[row + q + 1] = v;
+            }
+        }
+    }
+}
+
+// half-sweep of colour `color` on rows [ya, yb] (within 1..N) of the iterate window; the
+// new values of rows [olo, ohi] also go to the level's global array `go` (row pitch P)
+template <int N>
+__device__ __forceinline__ void ct_sweep(float2* E, int elo, const float2* Rr, int rlo, int ya, int yb,
+                                         float h2, float dinv, int color, float2* go = nullptr,
+                                         int olo = 0, int ohi = -1, int P = 0, bool keep = true)
+{
+    constexpr int S = N + 2, HE = Lv<2, N>::HE;
+    const int lane = threadIdx.x & 31;
+    ya = max(ya, 1);
+    yb = min(yb, N);
+    for (int y = ya + (int)(threadIdx.x >> 5); y <= yb; y += TNT / 32) {
+        const int xs = 1 + (((1 + y) & 1) ^ color);
+        const int p = xs & 1;
+        const int erow = (y - elo) * S, rrow = (y - rlo) * S;
+        const bool out = go != nullptr && y >= olo && y <= ohi;
+        for (int x = xs + 2 * lane; x <= N; x += 64) {
+            const int m = x >> 1;
+            const int oe = erow + m + (p ? HE : 0);
+            const float2 a = E[erow + m + (p ? 0 : HE - 1)], b = E[erow + m + (p ? 1 : HE)];
+            const float2 c = E[oe - S], d = E[oe + S];
+            const float2 rr = Rr[rrow + m + (p ? HE : 0)];
+            const float sx = a.x + b.x + c.x + d.x;
+            const float sy = a.y + b.y + c.y + d.y;
+            float2 v;
+            v.x = (sx - h2 * rr.x) * dinv;
+            v.y = (sy - h2 * rr.y) * dinv;
+            if (keep) E[oe] = v;
+            if (out) go[(size_t)y * P + x] = v;
+        }
+    }
+}
+
+// One rhs window to be completed from the CTAs that own its rows: rows [ya, yb] within 1..N
+// and outside [lo_have, hi_have] (rows this CTA holds already); CTA o owns rows band*o + 1
+// .. band*o + band and keeps them in its window starting at row wmul*o + off (wmul = band
+// for a band window, 0 for a whole-level array).
+struct CtPull {
+    float2* W;
+    int lo, ya, yb, lo_have, hi_have, band, wmul, off;
+    __device__ int held() const { return max(0, min(hi_have, yb) - max(lo_have, ya) + 1); }
+    __device__ int count() const { return max(0, yb - ya + 1) - held(); }
+    // the i-th missing row
+    __device__ int row(int i) const
+    {
+        const int y = ya + i;
+        return (held() == 0 || y < max(lo_have, ya)) ? y : y + held();
+    }
+};
+
+// copy the missing rows of three windows (levels 127, 63 and 31, S = 129, 65, 33 words):
+// a warp per row, every remote word of a row loaded before any is stored
+__device__ __forceinline__ void ct_pull3(cg::cluster_group& cl, CtPull p0, CtPull p1, CtPull p2)
+{
+    const int lane = threadIdx.x & 31;
+    const int n0 = p0.count(), n1 = p1.count(), n2 = p2.count();
+    for (int w = (int)(threadIdx.x >> 5); w < n0 + n1 + n2; w += TNT / 32) {
+        CtPull p = p2;
+        int i = w - n0 - n1, S = CT_SX;
+        if (w < n0) {
+            p = p0;
+            i = w;
+            S = CT_SB;
+        } else if (w < n0 + n1) {
+            p = p1;
+            i = w - n0;
+            S = CT_SC;
+        }
+        const int y = p.row(i);
+        const int o = (y - 1) / p.band;
+        const float2* src = cl.map_shared_rank(p.W, o) + (y - (p.wmul * o + p.off)) * S;
+        float2* dst = p.W + (y - p.lo) * S;
+        float2 v[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+            if (lane + 32 * j < S) v[j] = src[lane + 32 * j];
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+            if (lane + 32 * j < S) dst[lane + 32 * j] = v[j];
+    }
+}
+
+// cluster barrier halves: arrive releases this thread's shared-memory writes to the
+// cluster, wait acquires those of every thread that arrived
+__device__ __forceinline__ void ct_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+// (relaxed: this thread's loads from the other CTAs have completed, their values are used)
+__device__ __forceinline__ void ct_arrive_relaxed() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
+__device__ __forceinline__ void ct_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+template <int V>
+__global__ void __cluster_dims__(CT_CS, 1, 1) __launch_bounds__(TNT)
+k_ctail(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
+        const MgItem* __restrict__ items)
+{
+    typedef CtWin<V> W;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* base = reinterpret_cast<float2*>(smem_raw);
+    cg::cluster_group cl = cg::this_cluster();
+    const int k = (int)cl.block_rank();
+    float2* EA = base;
+    float2* EC = base + W::O_EC;
+    float2* RC = base + W::O_RC;
+    float2* EX = base + W::O_EX;
+    float2* RX = base + W::O_RX;
+    float* xscr = reinterpret_cast<float*>(base + W::O_SCR);
+    float2* EB = base + W::O_EB;
+    float2* RB = base + W::O_RB;
+    float2* RA = base + W::O_RA;
+    const int loEA = 32 * k + W::EA_OFF, loRA = 32 * k + W::RA_OFF;
+    const int loEB = 16 * k + W::EB_OFF, loRB = 16 * k + W::RB_OFF;
+    const int loEC = 8 * k + W::EC_OFF, loRC = 8 * k + W::RC_OFF;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // before the wait (nothing here depends on the predecessor): descriptors, the sine
+    // tables, and the coarse iterate windows cleared (their rings and outer rows stay zero)
+    const MgItem item = items[blockIdx.x / CT_CS];
+    const LevelDesc LA = insts[item.inst].lev[item.level];
+    const float dinvA = (float)LA.dinv;
+    const float dinvB = (float)insts[item.inst].lev[item.level + 1].dinv;
+    const float dinvC = (float)insts[item.inst].lev[item.level + 2].dinv;
+    const float sig = (float)insts[item.inst].sigma;
+    {
+        constexpr int NT4 = XTAB_FLOATS / 4;
+        const float4* tab = reinterpret_cast<const float4*>(g_xtab);
+        for (int i = threadIdx.x; i < NT4; i += TNT) reinterpret_cast<float4*>(xscr)[i] = tab[i];
+    }
+    for (int i = threadIdx.x; i < W::EB_ROWS * CT_SB; i += TNT) EB[i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < W::EC_ROWS * CT_SC; i += TNT) EC[i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < CT_SX * CT_SX; i += TNT) EX[i] = make_float2(0.f, 0.f);
+    pdl_wait();
+    pdl_trigger();
+    const InstState sv = st[item.inst];
+    // every CTA of the cluster reads the same status and size: all leave together
+    if (sv.status != HELM_ST_ACTIVE || LA.n != CT_NA) return;
+    const float2* __restrict__ gr = (const float2*)lev_rhs(LA, item.level, sv.it);
+    const int PA = LA.pitch;
+    // level 255's rhs window, staged once: the descent reads its rows 32k+1 .. 32k+39, the
+    // last sweeps rows 32k+1-(2 nu2-1) .. 32k+32+(2 nu2-1)
+    for (int r = warp; r < W::RA_ROWS; r += TNT / 32) {
+        const int y = loRA + r;
+        if (y < 1 || y > CT_NA) continue;
+        for (int x = lane + 1; x <= CT_NA; x += 32)
+            cp_async_elem<8>(RA + bw<CT_NA>(loRA, y, x), gr + (size_t)y * PA + x, true);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // descent: own rows of every level plus the rows below them the next restriction reads
+    ct_restrict<CT_NA>(RA, loRA, RB, loRB, 16 * k + 1, 16 * k + 19);
+    __syncthreads();
+    ct_restrict<CT_NB>(RB, loRB, RC, loRC, 8 * k + 1, 8 * k + 9);
+    __syncthreads();
+    ct_restrict<CT_NC>(RC, loRC, RX, 0, 4 * k + 1, 4 * k + 4);
+    ct_arrive();
+    ct_wait();
+    // the rhs rows of the windows held by the neighbours; level 31's whole rhs.  Then this
+    // CTA has read the last of its neighbours' memory.
+    {
+        const CtPull pb{RB, loRB, max(loRB, 1), min(loRB + W::RB_ROWS - 1, CT_NB), 16 * k + 1,
+                        min(16 * k + 19, CT_NB), 16, 16, W::RB_OFF};
+        const CtPull pc{RC, loRC, max(loRC, 1), min(loRC + W::RC_ROWS - 1, CT_NC), 8 * k + 1,
+                        min(8 * k + 9, CT_NC), 8, 8, W::RC_OFF};
+        const CtPull px{RX, 0, 1, XN, 4 * k + 1, min(4 * k + 4, XN), 4, 0, 0};
+        ct_pull3(cl, pb, pc, px);
+    }
+    __syncthreads();
+    ct_arrive_relaxed();
+    const float hA = (float)LA.h;
+    x_solve(EX, RX, xscr, 8.f * hA, sig);
+    // ascent: level 63 on its window
+    ct_prolong<CT_NC>(EC, loEC, EX, 0, loEC, loEC + W::EC_ROWS - 1);
+    __syncthreads();
+    for (int s = 1; s <= 2 * V; ++s) {
+        ct_sweep<CT_NC>(EC, loEC, RC, loRC, 8 * k + W::FC_LO - (2 * V - s), 8 * k + W::FC_HI + (2 * V - s),
+                        (4.f * hA) * (4.f * hA), dinvC, (s - 1) & 1);
+        __syncthreads();
+    }
+    ct_prolong<CT_NB>(EB, loEB, EC, loEC, loEB, loEB + W::EB_ROWS - 1);
+    __syncthreads();
+    for (int s = 1; s <= 2 * V; ++s) {
+        ct_sweep<CT_NB>(EB, loEB, RB, loRB, 16 * k + W::FB_LO - (2 * V - s), 16 * k + W::FB_HI + (2 * V - s),
+                        (2.f * hA) * (2.f * hA), dinvB, (s - 1) & 1);
+        __syncthreads();
+    }
+    // the neighbours are done with this CTA's level-63 and level-31 rhs, which share level
+    // 255's iterate window: zero its ring and outer rows, then assign its interior
+    ct_wait();
+    for (int r = warp; r < W::EA_ROWS; r += TNT / 32) {
+        const int y = loEA + r;
+        if (y >= 1 && y <= CT_NA) {
+            if (lane < 2) EA[r * CT_SA + ix<CT_NA>(lane ? CT_NA + 1 : 0)] = make_float2(0.f, 0.f);
+        } else {
+            for (int x = lane; x < CT_SA; x += 32) EA[r * CT_SA + x] = make_float2(0.f, 0.f);
+        }
+    }
+    ct_prolong<CT_NA>(EA, loEA, EB, loEB, loEA, loEA + W::EA_ROWS - 1);
+    __syncthreads();
+    // level 255's sweeps; the last half-sweep of each colour also writes the CTA's own rows
+    // of the iterate to global memory (the very last one only there)
+    float2* __restrict__ go = (float2*)LA.e;
+    const int own_hi = min(32 * k + 32, CT_NA);
+    for (int s = 1; s <= 2 * V; ++s) {
+        const bool last = s >= 2 * V - 1;
+        ct_sweep<CT_NA>(EA, loEA, RA, loRA, 32 * k + 1 - (2 * V - s), 32 * k + 32 + (2 * V - s), hA * hA, dinvA,
+                        (s - 1) & 1, last ? go : nullptr, 32 * k + 1, own_hi, PA, s < 2 * V);
+        if (s < 2 * V) __syncthreads();
+    }
+}
+
 template <int D, typename R, int N0>
 cudaError_t tl(const InstDesc* insts, const InstState* st, const MgItem* items, int nitems,
                int nu1, int nu2, int load_e, cudaStream_t s)
@@ -703,6 +1048,28 @@ cudaError_t tail_attrs()
     }
     return cudaSuccess;
 }
+
+template <int V>
+cudaError_t ctail_attrs()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_ctail<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)CtWin<V>::BYTES);
+    if (e != cudaSuccess) return e;
+    return max_carveout(k_ctail<V>);
+}
+
+// can one cluster of the kernel be resident on this device?
+template <int V>
+bool ctail_fits()
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CT_CS);
+    cfg.blockDim = dim3(TNT);
+    cfg.dynamicSmemBytes = CtWin<V>::BYTES;
+    int nc = 0;
+    return cudaOccupancyMaxActiveClusters(&nc, k_ctail<V>, &cfg) == cudaSuccess && nc >= 1;
+}
+
 
 }  // namespace
 
@@ -780,6 +1147,31 @@ cudaError_t launch_tail(int D, int prec, int n0, const InstDesc* insts, const In
                          : tail_dispatch<2, float>(n0, insts, st, items, nitems, nu1, nu2, load_e, s);
     return prec == 0 ? tail_dispatch<3, double>(n0, insts, st, items, nitems, nu1, nu2, load_e, s)
                      : tail_dispatch<3, float>(n0, insts, st, items, nitems, nu1, nu2, load_e, s);
+}
+
+int ctail_setup()
+{
+    static int ok = -1;
+    if (ok < 0) {
+        ok = 0;
+        if (ctail_attrs<1>() == cudaSuccess && ctail_attrs<2>() == cudaSuccess && ctail_fits<1>() &&
+            ctail_fits<2>())
+            ok = 1;
+        cudaGetLastError();
+    }
+    return ok;
+}
+
+cudaError_t launch_ctail(const InstDesc* insts, const InstState* st, const MgItem* items, int nitems,
+                         int nu2, cudaStream_t s)
+{
+    if (nu2 == 1)
+        launch_k(k_ctail<1>, dim3(CT_CS * nitems), dim3(TNT), CtWin<1>::BYTES, s, insts, st, items);
+    else if (nu2 == 2)
+        launch_k(k_ctail<2>, dim3(CT_CS * nitems), dim3(TNT), CtWin<2>::BYTES, s, insts, st, items);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 }  // namespace helm
