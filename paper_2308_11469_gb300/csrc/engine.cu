@@ -142,7 +142,7 @@ struct Instance {
 };
 
 struct LaunchRec {
-    enum Kind { RBGS, RESTRICT, PROLONG, ZERO, TAIL, RESID, CHECK, DOWN, UP, UPRES, CTAIL, NKINDS } kind;
+    enum Kind { RBGS, RESTRICT, PROLONG, ZERO, TAIL, RESID, CHECK, DOWN, UP, UPRES, CTAIL, DOWN2, NKINDS } kind;
     int off, cnt, work, color, mode;
     double bytes;   // algorithmic bytes of one launch (each datum it must touch, once)
     int nmax = 0;   // DOWN: the largest level of the launch; UPRES: the level-0 size
@@ -458,9 +458,19 @@ struct Engine {
         };
         auto vcycle2d = [&](std::vector<LaunchRec>& out, bool zero_start) {
             const int Jf = use_ct ? J - 2 : J;         // levels of the fused tile kernels
-            for (int j = 0; j < Jf; ++j)
-                out.push_back({LaunchRec::DOWN, ph[j].off, ph[j].cnt, ph[j].tiles, ph[j].shape,
-                               zero_start ? 2 : 1, 0.0, ph[j].nmax});
+            // without pre-smoothing from a zero start every descent step restricts rhs alone:
+            // two of them per launch
+            const bool pairs = nu1 == 0 && zero_start;
+            for (int j = 0; j < Jf;) {
+                if (pairs && j + 1 < Jf) {
+                    out.push_back({LaunchRec::DOWN2, ph[j].off, ph[j].cnt, 0, 0, 2, 0.0, ph[j].nmax});
+                    j += 2;
+                } else {
+                    out.push_back({LaunchRec::DOWN, ph[j].off, ph[j].cnt, ph[j].tiles, ph[j].shape,
+                                   zero_start ? 2 : 1, 0.0, ph[j].nmax});
+                    j += 1;
+                }
+            }
             if (use_ct)
                 out.push_back({LaunchRec::CTAIL, ph[Jf].off, ph[Jf].cnt, 0, 0, 0,
                                2.0 * pts(255) * eb * ph[Jf].cnt});
@@ -573,6 +583,7 @@ struct Engine {
             case LaunchRec::ZERO: b += pts(n) * eb; break;
             case LaunchRec::TAIL: b += 2.0 * pts(n) * eb; break;
             case LaunchRec::CTAIL: b += 2.0 * pts(n) * eb; break;
+            case LaunchRec::DOWN2: b += (pts(n) + pts(nc) + pts((nc - 1) / 2)) * eb; break;
             case LaunchRec::DOWN: {
                 const bool zero = (L.mode == 2) || (L.mode == 1 && it.level > 0);
                 if (zero && nu1 == 0) b += (pts(n) + pts(nc)) * eb;      // rhs in, coarse rhs out
@@ -613,6 +624,9 @@ struct Engine {
                 break;
             case LaunchRec::CTAIL:
                 e = launch_ctail(d_desc, d_state, d_mg + L.off, L.cnt, nu2, s);
+                break;
+            case LaunchRec::DOWN2:
+                e = launch_restrict2_2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.nmax, s);
                 break;
             case LaunchRec::DOWN:
                 e = launch_down2d(prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, nu1, L.mode, L.color, s,

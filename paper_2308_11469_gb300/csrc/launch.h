@@ -84,6 +84,11 @@ cudaError_t launch_up2d(int prec, const InstDesc* insts, const InstState* st, co
 int tile_shape2d(int n);
 int tiles2d(int n);
 int tiles2d_for(int n, int shape);
+// two descent steps of cycles without pre-smoothing from a zero iterate in one launch:
+// every item (instance, level l) gets level l+1's and level l+2's rhs by full weighting;
+// nmax: the largest level l of the launch
+cudaError_t launch_restrict2_2d(int prec, const InstDesc* insts, const InstState* st, const MgItem* items,
+                                int nitems, int nmax, cudaStream_t s);
 cudaError_t setup_2d(int prec);
 
 // ---- outer FP64 iteration (outer.cu) ----

@@ -339,6 +339,118 @@ k_restrict_rhs2d(const InstDesc* __restrict__ insts, const InstState* __restrict
     ((c2*)C.rhs)[(size_t)Y * C.pitch + X] = v;
 }
 
+// Two such descent steps in one launch: level l+1's rhs = full weighting of level l's rhs,
+// level l+2's rhs = full weighting of that (same weights, order and scaling as
+// k_restrict_rhs2d, so the values are the same).  A CTA owns a 16 x 16 tile of level l+2:
+// it stages the 68 x 68 window of level l's rhs the tile depends on (16-byte copies from a
+// 16-byte aligned column), forms the 33 x 33 level-(l+1) nodes the tile reads, writes the
+// 32 x 32 of them it owns (level l+1 columns 32 i + 1 .. 32 i + 32 for tile column i) and
+// the tile.
+constexpr int R2T = 16;                    // level l+2 tile edge
+constexpr int R2W1 = 2 * R2T + 1;          // level l+1 window edge
+constexpr int R2W0 = 4 * R2T + 4;          // level l window edge
+constexpr int R2NT = 256;
+
+template <typename R> constexpr size_t restrict2_bytes()
+{
+    return ((size_t)R2W0 * R2W0 + (size_t)R2W1 * R2W1) * 2 * sizeof(R);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(R2NT)
+k_restrict2_rhs2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
+                  const MgItem* __restrict__ items)
+{
+    typedef typename C2<R>::T c2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    c2* W0 = reinterpret_cast<c2*>(smem_raw);           // level l window
+    c2* W1 = W0 + R2W0 * R2W0;                           // level l+1 window
+    const MgItem item = items[blockIdx.y];
+    const LevelDesc L0 = insts[item.inst].lev[item.level];
+    const LevelDesc L1 = insts[item.inst].lev[item.level + 1];
+    const LevelDesc L2 = insts[item.inst].lev[item.level + 2];
+    pdl_wait();
+    pdl_trigger();
+    const InstState sv = st[item.inst];
+    if (sv.status != HELM_ST_ACTIVE) return;
+    const int n0 = L0.n, n1 = L1.n, n2 = L2.n;
+    const int ntx = (n2 + R2T - 1) / R2T;
+    if ((int)blockIdx.x >= ntx * ntx) return;
+    const int X2a = 1 + (blockIdx.x % ntx) * R2T, Y2a = 1 + (blockIdx.x / ntx) * R2T;
+    const int c0 = 4 * X2a - 4, r0 = 4 * Y2a - 4;       // level l window origin
+    const c2* __restrict__ g0 = (const c2*)lev_rhs(L0, item.level, sv.it);
+    const int P0 = L0.pitch;
+    // stage: 16-byte chunks (two complex64 or one complex128), zero outside the array
+    constexpr int EPC = 16 / (int)sizeof(c2);             // elements per chunk
+    constexpr int CPR = R2W0 / EPC;                       // chunks per window row
+    for (int q = threadIdx.x; q < R2W0 * CPR; q += R2NT) {
+        const int r = q / CPR, cc = (q % CPR) * EPC;
+        const int gy = r0 + r, gx = c0 + cc;
+        const bool in = gy <= n0 + 1 && gx < P0;
+        const c2* src = g0 + (in ? (size_t)gy * P0 + gx : 0);
+        const unsigned d = (unsigned)__cvta_generic_to_shared(W0 + r * R2W0 + cc);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(in ? 16 : 0)
+                     : "memory");
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    // level l+1 window: node (2 X2a - 1 + x1, 2 Y2a - 1 + y1); its fine node (2 X1 + dx, ...)
+    // is window element (2 x1 + 2 + dx, 2 y1 + 2 + dy)
+    c2* __restrict__ g1 = (c2*)L1.rhs;
+    const int P1 = L1.pitch;
+    for (int q = threadIdx.x; q < R2W1 * R2W1; q += R2NT) {
+        const int y1 = q / R2W1, x1 = q % R2W1;
+        const int X1 = 2 * X2a - 1 + x1, Y1 = 2 * Y2a - 1 + y1;
+        c2 v;
+        v.x = 0;
+        v.y = 0;
+        if (X1 <= n1 && Y1 <= n1) {
+            R ax = 0, ay = 0;
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const R wy = (dy == 0) ? (R)2 : (R)1;
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const R wgt = wy * ((dx == 0) ? (R)2 : (R)1);
+                    const c2 r = W0[(2 * y1 + 2 + dy) * R2W0 + 2 * x1 + 2 + dx];
+                    ax += wgt * r.x;
+                    ay += wgt * r.y;
+                }
+            }
+            v.x = ax * (R)(1.0 / 16.0);
+            v.y = ay * (R)(1.0 / 16.0);
+            if (x1 < 2 * R2T && y1 < 2 * R2T) g1[(size_t)Y1 * P1 + X1] = v;
+        }
+        W1[q] = v;
+    }
+    __syncthreads();
+    // the level l+2 tile: node (X2a + x2, Y2a + y2) reads window element (2 x2 + 1 + dx, ...)
+    c2* __restrict__ g2 = (c2*)L2.rhs;
+    const int P2 = L2.pitch;
+    {
+        const int x2 = threadIdx.x % R2T, y2 = threadIdx.x / R2T;
+        const int X2 = X2a + x2, Y2 = Y2a + y2;
+        if (X2 <= n2 && Y2 <= n2) {
+            R ax = 0, ay = 0;
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const R wy = (dy == 0) ? (R)2 : (R)1;
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const R wgt = wy * ((dx == 0) ? (R)2 : (R)1);
+                    const c2 r = W1[(2 * y2 + 1 + dy) * R2W1 + 2 * x2 + 1 + dx];
+                    ax += wgt * r.x;
+                    ay += wgt * r.y;
+                }
+            }
+            c2 v;
+            v.x = ax * (R)(1.0 / 16.0);
+            v.y = ay * (R)(1.0 / 16.0);
+            g2[(size_t)Y2 * P2 + X2] = v;
+        }
+    }
+}
+
 template <int NU, int TX, int TY> constexpr size_t down_bytes(size_t eb) {
     return 2 * (size_t)(TX + 2 * (2 * NU + 2)) * (TY + 2 * (2 * NU + 2)) * eb;
 }
@@ -379,6 +491,10 @@ cudaError_t set_all()
 {
     cudaError_t e;
     if ((e = max_carveout(k_restrict_rhs2d<R>)) != cudaSuccess) return e;
+    if ((e = max_carveout(k_restrict2_rhs2d<R>)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_restrict2_rhs2d<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)restrict2_bytes<R>())) != cudaSuccess)
+        return e;
     if ((e = set_attrs<R, 0>()) != cudaSuccess) return e;
     if ((e = set_attrs<R, 1>()) != cudaSuccess) return e;
     if ((e = set_attrs<R, 2>()) != cudaSuccess) return e;
@@ -467,6 +583,18 @@ cudaError_t launch_down2d(int prec, const InstDesc* insts, const InstState* st, 
                                 : down<float, 1>(nu1, g, insts, st, items, zero_mode, s);
     return prec == 0 ? down<double, 0>(nu1, g, insts, st, items, zero_mode, s)
                      : down<float, 0>(nu1, g, insts, st, items, zero_mode, s);
+}
+
+cudaError_t launch_restrict2_2d(int prec, const InstDesc* insts, const InstState* st, const MgItem* items,
+                                int nitems, int nmax, cudaStream_t s)
+{
+    const int n2 = ((nmax - 1) / 2 - 1) / 2;
+    if (n2 < 1) return cudaErrorInvalidValue;
+    const int t = (n2 + R2T - 1) / R2T;
+    dim3 g(t * t, nitems);
+    if (prec == 0) launch_k(k_restrict2_rhs2d<double>, g, dim3(R2NT), restrict2_bytes<double>(), s, insts, st, items);
+    else launch_k(k_restrict2_rhs2d<float>, g, dim3(R2NT), restrict2_bytes<float>(), s, insts, st, items);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_up2d(int prec, const InstDesc* insts, const InstState* st, const MgItem* items,
