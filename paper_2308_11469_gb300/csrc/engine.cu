@@ -459,10 +459,11 @@ struct Engine {
         auto vcycle2d = [&](std::vector<LaunchRec>& out, bool zero_start) {
             const int Jf = use_ct ? J - 2 : J;         // levels of the fused tile kernels
             // without pre-smoothing from a zero start every descent step restricts rhs alone:
-            // two of them per launch
+            // two of them per launch, where every instance of the second phase is in the
+            // first (no instance has its top level at the second)
             const bool pairs = nu1 == 0 && zero_start;
             for (int j = 0; j < Jf;) {
-                if (pairs && j + 1 < Jf) {
+                if (pairs && j + 1 < Jf && ph[j + 1].cnt == ph[j].cnt) {
                     out.push_back({LaunchRec::DOWN2, ph[j].off, ph[j].cnt, 0, 0, 2, 0.0, ph[j].nmax});
                     j += 2;
                 } else {

@@ -283,6 +283,42 @@ def test_class_schedules_equal_solo_solves(B):
         B.helm_batch_set_cycle_class(B.helm_batch_create(0), 4, B.HELM_PREC_MIXED, 0, 1, 1)
 
 
+@pytest.mark.parametrize("sizes", [(127, 255), (63, 127, 255, 511), (511, 1023)])
+def test_mixed_sizes_v01_equal_solo_solves(B, sizes):
+    """Instances of different sizes in one launch sequence on V(0, 1) (descent steps paired
+    per launch where every instance shares both levels, the cluster tail where all are at
+    least 511): each result is that of a single solve, bit for bit."""
+    probs = []
+    for i, n in enumerate(sizes):
+        probs += inputs.batched_instances(count=1, seed=60 + i, sizes=(n,), probs=(1.0,))
+    tol, max_outer = 1e-8, 3000
+    batch = B.helm_batch_create(0)
+    B.helm_batch_set_cycle(batch, 0, 1, 1)
+    B.helm_batch_set_lanes(batch, 1)
+    keep, tickets = [], []
+    for p in probs:
+        f = torch.from_numpy(p.f).to(DEV)
+        g = torch.from_numpy(p.g).to(DEV)
+        u = torch.zeros_like(g)
+        keep.append((f, g, u))
+        tickets.append(B.helm_batch_submit_geom(batch, p.D, p.n, p.h, p.k, B.HELM_PREC_MIXED, f, g, u, tol,
+                                                max_outer))
+    B.helm_batch_step(batch, 0)
+    results = [B.helm_batch_poll(batch, t, max_outer) for t in tickets]
+    B.helm_batch_destroy(batch)
+    for i, p in enumerate(probs):
+        plan = B.helm_plan_create(p.D, p.n, p.h, p.k, prec=B.HELM_PREC_MIXED)
+        B.helm_plan_set_cycle(plan, 0, 1, 1)
+        f, g, _ = keep[i]
+        u = torch.zeros_like(g)
+        st, it, hist = B.helm_solve(plan, f, g, u, tol, max_outer)
+        B.helm_plan_destroy(plan)
+        assert results[i][0] == st == B.HELM_CONVERGED, (p.n, results[i][0], st)
+        assert results[i][1] == it
+        assert np.array_equal(results[i][2], hist)
+        assert np.array_equal(keep[i][2].cpu().numpy(), u.cpu().numpy())
+
+
 def test_submit_many_equals_single_submissions(B):
     """Bulk submission and polling give the results of one-by-one submission bit for bit,
     and a memory cap admits a prefix (the rest wait)."""
