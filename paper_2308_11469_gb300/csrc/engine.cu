@@ -491,8 +491,8 @@ struct Engine {
             for (int j = 0; j < J; ++j) {
                 for (int s = 0; s < nu1; ++s) {
                     const int mode = (s == 0) ? (zero_start ? 2 : 1) : 0;
-                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 0, mode, ph[j].b_rb});
-                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 1, 0, ph[j].b_rb});
+                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 0, mode, ph[j].b_rb, ph[j].nmax});
+                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 1, 0, ph[j].b_rb, ph[j].nmax});
                 }
                 out.push_back({LaunchRec::RESTRICT, ph[j].off, ph[j].cnt, ph[j].w_rs, 0, zmode, ph[j].b_rs});
             }
@@ -500,8 +500,8 @@ struct Engine {
             for (int j = J - 1; j >= 0; --j) {
                 out.push_back({LaunchRec::PROLONG, ph[j].off, ph[j].cnt, ph[j].w_pr, 0, zmode, ph[j].b_pr});
                 for (int s = 0; s < nu2; ++s) {
-                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 0, 0, ph[j].b_rb});
-                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 1, 0, ph[j].b_rb});
+                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 0, 0, ph[j].b_rb, ph[j].nmax});
+                    out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 1, 0, ph[j].b_rb, ph[j].nmax});
                 }
             }
         };
@@ -608,7 +608,7 @@ struct Engine {
             cudaError_t e = cudaSuccess;
             switch (L.kind) {
             case LaunchRec::RBGS:
-                e = launch_rbgs(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, L.color, L.mode, s);
+                e = launch_rbgs(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, L.color, L.mode, s, L.nmax);
                 break;
             case LaunchRec::RESTRICT:
                 e = launch_restrict(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s, L.mode);

@@ -30,9 +30,10 @@ inline int tail_top(int D, int prec_is_fp64)
 // mode 0: plain half-sweep; modes 1/2: first half-sweep of a pre-smoothing whose
 // iterate is known to be zero on levels > 0 (mode 1) or on every level (mode 2): it
 // writes both colours (this colour from rhs alone, the other colour as zero).
+// nmax: the largest level of the launch (0 if not known: the generic kernel)
 cudaError_t launch_rbgs(int D, int prec, const InstDesc* insts, const InstState* st,
                         const MgItem* items, int nitems, int work, int color, int mode,
-                        cudaStream_t s);
+                        cudaStream_t s, int nmax = 0);
 // coarse rhs := full weighting of (rhs - (Delta_h - sigma) e) on level l, coarse e := 0;
 // mode 2 / 1 (no pre-smoothing): the iterate is zero on every level / levels > 0, the
 // residual is rhs and the coarse iterate is left to the prolongation

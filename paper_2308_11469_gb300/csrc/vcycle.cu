@@ -93,6 +93,140 @@ k_rbgs(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
 }
 
 // ---------------------------------------------------------------------------
+// 3D half-sweep marching in z with the planes staged by asynchronous copies
+// ---------------------------------------------------------------------------
+// The same half-sweep as k_rbgs<3, R> mode 0 (same operands, same summation order), for
+// levels whose colour-split rows fit shared memory.  A CTA owns TY rows (y) over a chunk of
+// planes (z).  For every row (y', z') around them it needs one half of the row: the half
+// holding the other colour (x parity 1 - p(y', z'), p = the parity of the updated x in that
+// row); for its own rows the rhs half of the updated colour.  Plane by plane these halves are
+// copied (16-byte cp.async, whole halves: pitch / 2 elements, 16-byte aligned) into rings:
+// other-colour halves of rows y0-1 .. y0+TY of planes p-1 .. p+L+1 (L planes in flight) and
+// rhs halves of rows y0 .. y0+TY-1 of planes p .. p+L.  In those halves the node at x of the
+// updated colour finds its y- and z-neighbours at the same index j (x = 2j + p... / 2j) and its
+// x-neighbours at j, j+1 (odd x) or j-1, j (even x).  No shared-memory word is written by the
+// sweep; results go straight to global memory.
+template <typename R> struct Rb3p {
+    static constexpr int TY = sizeof(R) == 4 ? 8 : 4;      // rows per CTA (a warp per row)
+    static constexpr int L = 1;                            // planes in flight
+    static constexpr int OS = L + 3, RS = L + 1;           // ring slots
+    static constexpr int MAX_HP = 264;                     // pitch / 2 of n = 511
+    static size_t bytes(int hp) {
+        return (size_t)(OS * (TY + 2) + RS * TY) * hp * sizeof(typename C2<R>::T);
+    }
+};
+
+template <typename R>
+__global__ void __launch_bounds__(32 * Rb3p<R>::TY)
+k_rbgs3p(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
+         const MgItem* __restrict__ items, int color, int zchunk)
+{
+    typedef typename C2<R>::T c2;
+    typedef Rb3p<R> K;
+    constexpr int TY = K::TY, L = K::L;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const MgItem item = items[blockIdx.y];
+    const LevelDesc Lv = insts[item.inst].lev[item.level];
+    pdl_wait();
+    pdl_trigger();
+    const InstState sv = st[item.inst];
+    if (sv.status != HELM_ST_ACTIVE) return;
+    const int n = Lv.n;
+    const int nyb = (n + TY - 1) / TY, nzc = (n + zchunk - 1) / zchunk;
+    if ((int)blockIdx.x >= nyb * nzc) return;
+    const int y0 = 1 + (int)(blockIdx.x % nyb) * TY;
+    const int z0 = 1 + (int)(blockIdx.x / nyb) * zchunk;
+    const int z1 = min(z0 + zchunk, n + 1);                // own planes [z0, z1)
+    const int HP = Lv.pitch >> 1;
+    const size_t PR = (size_t)Lv.pitch, PL = (size_t)Lv.pitch * Lv.rows;
+    c2* __restrict__ e = (c2*)Lv.e;
+    const c2* __restrict__ r = (const c2*)lev_rhs(Lv, item.level, sv.it);
+    c2* O = reinterpret_cast<c2*>(smem_raw);               // [OS][TY + 2][HP]
+    c2* Rs = O + K::OS * (TY + 2) * HP;                    // [RS][TY][HP]
+    constexpr int EPC = 16 / (int)sizeof(c2);               // elements per 16-byte chunk
+    const int CPR = HP / EPC;                               // chunks per half row
+    // copies: a warp per half row, its lanes over the row's 16-byte chunks (no division)
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // other-colour halves of rows y0-1 .. y0+TY of plane zp (zero past the last wall row)
+    auto stage_o = [&](int zp) {
+        c2* dst = O + (zp % K::OS) * (TY + 2) * HP;
+        for (int i = w; i < TY + 2; i += TY) {
+            const int yy = y0 - 1 + i;
+            const bool in = yy <= n + 1;
+            const int half = ((color + yy + zp) & 1) ? 0 : HP;   // the other colour's x parity
+            const c2* src = in ? e + zp * PL + yy * PR + half : e;
+            const unsigned d = (unsigned)__cvta_generic_to_shared(dst + i * HP);
+            for (int c = lane; c < CPR; c += 32)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d + 16 * c),
+                             "l"(src + (in ? EPC * c : 0)), "r"(in ? 16 : 0) : "memory");
+        }
+    };
+    // rhs halves (updated colour) of rows y0 .. y0+TY-1 of plane zp
+    auto stage_r = [&](int zp) {
+        c2* dst = Rs + (zp % K::RS) * TY * HP;
+        const int yy = y0 + w;
+        const bool in = yy <= n;
+        const int half = ((color + yy + zp) & 1) ? HP : 0;
+        const c2* src = in ? r + zp * PL + yy * PR + half : r;
+        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + w * HP);
+        for (int c = lane; c < CPR; c += 32)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d + 16 * c),
+                         "l"(src + (in ? EPC * c : 0)), "r"(in ? 16 : 0) : "memory");
+    };
+    auto commit = []() { asm volatile("cp.async.commit_group;\n" ::: "memory"); };
+    // group of plane p: the other-colour halves of plane p + 1 and the rhs of plane p; before
+    // them the halves of planes z0 - 1 and z0
+    stage_o(z0 - 1);
+    stage_o(z0);
+    commit();
+    for (int p = z0; p < z0 + L; ++p) {
+        if (p < z1) {
+            stage_o(p + 1);
+            stage_r(p);
+        }
+        commit();
+    }
+    const R h2 = (R)(Lv.h * Lv.h);
+    const R inv = (R)Lv.dinv;
+    const int y = y0 + w;
+    const int jmax = (n - 1) >> 1;
+    for (int p = z0; p < z1; ++p) {
+        if (p + L < z1) {
+            stage_o(p + L + 1);
+            stage_r(p + L);
+        }
+        commit();
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(L) : "memory");
+        __syncthreads();
+        if (y <= n) {
+            const int px = (color + y + p) & 1;           // parity of the updated x
+            const c2* oc = O + (p % K::OS) * (TY + 2) * HP + (w + 1) * HP;
+            const c2* on = O + ((p - 1) % K::OS) * (TY + 2) * HP + (w + 1) * HP;
+            const c2* op = O + ((p + 1) % K::OS) * (TY + 2) * HP + (w + 1) * HP;
+            const c2* rr_ = Rs + (p % K::RS) * TY * HP + w * HP;
+            c2* out = e + p * PL + y * PR + (px ? HP : 0);
+#pragma unroll 4
+            for (int j = lane + (px ? 0 : 1); j <= jmax; j += 32) {
+                const int xa = px ? j : j - 1;                 // x - 1 in the other half
+                const c2 a = oc[xa], b = oc[xa + 1];
+                const c2 c = oc[j - HP], d = oc[j + HP];      // rows y - 1, y + 1
+                R sx = a.x + b.x + c.x + d.x;
+                R sy = a.y + b.y + c.y + d.y;
+                const c2 f = on[j], g = op[j];
+                sx += f.x + g.x;
+                sy += f.y + g.y;
+                const c2 rv = rr_[j];
+                c2 v;
+                v.x = (sx - h2 * rv.x) * inv;
+                v.y = (sy - h2 * rv.y) * inv;
+                out[j] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Residual + full-weighting restriction
 // ---------------------------------------------------------------------------
 // mode 2 / 1: the fine iterate is zero on every level / on levels > 0 (no pre-smoothing
@@ -293,6 +427,12 @@ template <int D, typename R>
 static cudaError_t carve()
 {
     cudaError_t e;
+    if (D == 3) {
+        if ((e = max_carveout(k_rbgs3p<R>)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_rbgs3p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)Rb3p<R>::bytes(Rb3p<float>::MAX_HP))) != cudaSuccess)
+            return e;
+    }
     if ((e = max_carveout(k_rbgs<D, R>)) != cudaSuccess) return e;
     if ((e = max_carveout(k_restrict<D, R>)) != cudaSuccess) return e;
     if ((e = max_carveout(k_prolong<D, R>)) != cudaSuccess) return e;
@@ -307,8 +447,25 @@ cudaError_t setup_generic(int D, int prec)
 
 cudaError_t launch_rbgs(int D, int prec, const InstDesc* insts, const InstState* st,
                         const MgItem* items, int nitems, int work, int color, int mode,
-                        cudaStream_t s)
+                        cudaStream_t s, int nmax)
 {
+    // 3D plain half-sweeps of levels 127 .. 511: the plane-marching form
+    const int hp = (nmax + 2 + 15) / 16 * 8;
+    if (D == 3 && prec != 0 && mode == 0 && nmax >= 127 && hp <= Rb3p<float>::MAX_HP) {
+        const int ty = prec == 0 ? Rb3p<double>::TY : Rb3p<float>::TY;
+        const size_t sm = prec == 0 ? Rb3p<double>::bytes(hp) : Rb3p<float>::bytes(hp);
+        const int per_sm = (int)(227 * 1024 / (sm + 1024));
+        const int nyb = (nmax + ty - 1) / ty;
+        // z chunks so that the launch is about one wave of resident CTAs
+        int nzc = (152 * (per_sm < 1 ? 1 : per_sm)) / (nyb * nitems);
+        nzc = nzc < 1 ? 1 : (nzc > nmax / 4 ? nmax / 4 : nzc);     // at least 4 planes a CTA
+        const int zchunk = (nmax + nzc - 1) / nzc;
+        nzc = (nmax + zchunk - 1) / zchunk;
+        dim3 g(nyb * nzc, nitems);
+        if (prec == 0) launch_k(k_rbgs3p<double>, g, dim3(32 * ty), sm, s, insts, st, items, color, zchunk);
+        else launch_k(k_rbgs3p<float>, g, dim3(32 * ty), sm, s, insts, st, items, color, zchunk);
+        return cudaGetLastError();
+    }
     dim3 g = mg_grid(work, nitems);
     if (D == 2 && prec == 0) launch_k(k_rbgs<2, double>, dim3(g), dim3(256), 0, s, insts, st, items, color, mode);
     else if (D == 2) launch_k(k_rbgs<2, float>, dim3(g), dim3(256), 0, s, insts, st, items, color, mode);
