@@ -614,7 +614,9 @@ struct Engine {
                 e = launch_restrict(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s, L.mode);
                 break;
             case LaunchRec::PROLONG:
-                e = launch_prolong(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s, L.mode);
+                // the sweeps that follow start with colour 0
+                e = launch_prolong(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s, L.mode,
+                                   nu2 > 0 ? 1 : 0);
                 break;
             case LaunchRec::ZERO:
                 e = launch_zero(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s);

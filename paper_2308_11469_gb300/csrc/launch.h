@@ -39,9 +39,11 @@ cudaError_t launch_rbgs(int D, int prec, const InstDesc* insts, const InstState*
 // residual is rhs and the coarse iterate is left to the prolongation
 cudaError_t launch_restrict(int D, int prec, const InstDesc* insts, const InstState* st,
                             const MgItem* items, int nitems, int work, cudaStream_t s, int mode = 0);
-// e_l += prolongation of e_{l+1}; mode 2 / 1: e_l := prolongation where e_l is zero
+// e_l += prolongation of e_{l+1}; mode 2 / 1: e_l := prolongation where e_l is zero;
+// skip0: colour-0 nodes are left alone (a colour-0 half-sweep comes next)
 cudaError_t launch_prolong(int D, int prec, const InstDesc* insts, const InstState* st,
-                           const MgItem* items, int nitems, int work, cudaStream_t s, int mode = 0);
+                           const MgItem* items, int nitems, int work, cudaStream_t s, int mode = 0,
+                           int skip0 = 0);
 // zero the iterate of the listed levels (ring included)
 cudaError_t launch_zero(int D, int prec, const InstDesc* insts, const InstState* st,
                         const MgItem* items, int nitems, int work, cudaStream_t s);

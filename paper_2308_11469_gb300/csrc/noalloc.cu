@@ -218,7 +218,7 @@ extern "C" helm_status poisson_vcycle_noalloc(int ndim, int n, double h, int pre
         for (int l = lt - 1; l >= 0; --l) {
             const int m = d.lev[l].n;
             const int w_rb = (int)(((D == 3) ? (long)m * m : m) * ((m + 1) / 2));
-            NA_CK(launch_prolong(D, pr, dd, ds, di + l, 1, (int)pts(m), sm, zmode));
+            NA_CK(launch_prolong(D, pr, dd, ds, di + l, 1, (int)pts(m), sm, zmode, nu2 > 0 ? 1 : 0));
             for (int it = 0; it < nu2; ++it) {
                 NA_CK(launch_rbgs(D, pr, dd, ds, di + l, 1, w_rb, 0, 0, sm));
                 NA_CK(launch_rbgs(D, pr, dd, ds, di + l, 1, w_rb, 1, 0, sm));

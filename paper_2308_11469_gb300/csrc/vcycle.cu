@@ -323,11 +323,13 @@ k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
 // Multilinear prolongation + correction
 // ---------------------------------------------------------------------------
 // mode 2 / 1: the fine iterate is zero on every level / on levels > 0 (no pre-smoothing
-// from a zero iterate): e := interpolation instead of e += interpolation.
+// from a zero iterate): e := interpolation instead of e += interpolation.  skip0: the next
+// operation is a half-sweep of colour 0, which overwrites every colour-0 node without
+// reading its value: only colour-1 nodes are corrected.
 template <int D, typename R>
 __global__ void __launch_bounds__(256)
 k_prolong(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
-          const MgItem* __restrict__ items, int mode)
+          const MgItem* __restrict__ items, int mode, int skip0)
 {
     pdl_wait();
     pdl_trigger();
@@ -367,6 +369,7 @@ k_prolong(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
         for (int half = 0; half < 2; ++half) {
             const int x = 2 * p + 1 + half;
             if (x > n) break;
+            if (skip0 && ((x + y + z) & 1) == 0) continue;
             // each of the 2^D corner reads counts 1/2^D; coincident corners (even index)
             // are read twice, which gives the weight 1 of an even fine index
             R vx = 0, vy = 0;
@@ -486,13 +489,13 @@ cudaError_t launch_restrict(int D, int prec, const InstDesc* insts, const InstSt
 }
 
 cudaError_t launch_prolong(int D, int prec, const InstDesc* insts, const InstState* st,
-                           const MgItem* items, int nitems, int work, cudaStream_t s, int mode)
+                           const MgItem* items, int nitems, int work, cudaStream_t s, int mode, int skip0)
 {
     dim3 g = mg_grid(work, nitems);
-    if (D == 2 && prec == 0) launch_k(k_prolong<2, double>, dim3(g), dim3(256), 0, s, insts, st, items, mode);
-    else if (D == 2) launch_k(k_prolong<2, float>, dim3(g), dim3(256), 0, s, insts, st, items, mode);
-    else if (prec == 0) launch_k(k_prolong<3, double>, dim3(g), dim3(256), 0, s, insts, st, items, mode);
-    else launch_k(k_prolong<3, float>, dim3(g), dim3(256), 0, s, insts, st, items, mode);
+    if (D == 2 && prec == 0) launch_k(k_prolong<2, double>, dim3(g), dim3(256), 0, s, insts, st, items, mode, skip0);
+    else if (D == 2) launch_k(k_prolong<2, float>, dim3(g), dim3(256), 0, s, insts, st, items, mode, skip0);
+    else if (prec == 0) launch_k(k_prolong<3, double>, dim3(g), dim3(256), 0, s, insts, st, items, mode, skip0);
+    else launch_k(k_prolong<3, float>, dim3(g), dim3(256), 0, s, insts, st, items, mode, skip0);
     return cudaGetLastError();
 }
 
