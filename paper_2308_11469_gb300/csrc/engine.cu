@@ -494,7 +494,7 @@ struct Engine {
                     out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 0, mode, ph[j].b_rb, ph[j].nmax});
                     out.push_back({LaunchRec::RBGS, ph[j].off, ph[j].cnt, ph[j].w_rb, 1, 0, ph[j].b_rb, ph[j].nmax});
                 }
-                out.push_back({LaunchRec::RESTRICT, ph[j].off, ph[j].cnt, ph[j].w_rs, 0, zmode, ph[j].b_rs});
+                out.push_back({LaunchRec::RESTRICT, ph[j].off, ph[j].cnt, ph[j].w_rs, 0, zmode, ph[j].b_rs, ph[j].nmax});
             }
             tail(out, zero_start);
             for (int j = J - 1; j >= 0; --j) {
@@ -611,7 +611,7 @@ struct Engine {
                 e = launch_rbgs(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, L.color, L.mode, s, L.nmax);
                 break;
             case LaunchRec::RESTRICT:
-                e = launch_restrict(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s, L.mode);
+                e = launch_restrict(D, prec, d_desc, d_state, d_mg + L.off, L.cnt, L.work, s, L.mode, L.nmax);
                 break;
             case LaunchRec::PROLONG:
                 // the sweeps that follow start with colour 0

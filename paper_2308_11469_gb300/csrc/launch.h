@@ -38,7 +38,8 @@ cudaError_t launch_rbgs(int D, int prec, const InstDesc* insts, const InstState*
 // mode 2 / 1 (no pre-smoothing): the iterate is zero on every level / levels > 0, the
 // residual is rhs and the coarse iterate is left to the prolongation
 cudaError_t launch_restrict(int D, int prec, const InstDesc* insts, const InstState* st,
-                            const MgItem* items, int nitems, int work, cudaStream_t s, int mode = 0);
+                            const MgItem* items, int nitems, int work, cudaStream_t s, int mode = 0,
+                            int nmax = 0);
 // e_l += prolongation of e_{l+1}; mode 2 / 1: e_l := prolongation where e_l is zero;
 // skip0: colour-0 nodes are left alone (a colour-0 half-sweep comes next)
 cudaError_t launch_prolong(int D, int prec, const InstDesc* insts, const InstState* st,

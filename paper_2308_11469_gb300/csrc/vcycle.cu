@@ -319,6 +319,118 @@ k_restrict(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     }
 }
 
+// 3D restriction of the rhs alone (a zero iterate, modes 2 / 1) marching in z: a CTA owns
+// TYC coarse rows over a chunk of coarse planes; the fine rows 2 Y0 - 1 .. 2 Y0 + 2 TYC - 1 of
+// the fine planes 2 Z - 1 .. 2 Z + 1 are staged whole (16-byte cp.async) in a ring of five
+// fine planes (three in use, the next coarse plane's two in flight); the weights and the
+// order of the 27-term sums are k_restrict's.
+template <typename R> struct Rs3p {
+    static constexpr int TYC = 4;                          // coarse rows per CTA
+    static constexpr int NT = 256;                         // two warps per coarse row
+    static constexpr int NS = 5;                           // fine-plane slots
+    static constexpr int MAX_P = 528;                      // pitch of n = 511
+    static size_t bytes(int pitch) {
+        return (size_t)NS * (2 * TYC + 1) * pitch * sizeof(typename C2<R>::T);
+    }
+};
+
+template <typename R>
+__global__ void __launch_bounds__(Rs3p<R>::NT)
+k_restrict3p(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
+             const MgItem* __restrict__ items, int zchunk)
+{
+    typedef typename C2<R>::T c2;
+    typedef Rs3p<R> K;
+    constexpr int TYC = K::TYC, FR = 2 * TYC + 1;         // fine rows per plane slot
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const MgItem item = items[blockIdx.y];
+    const LevelDesc F = insts[item.inst].lev[item.level];
+    const LevelDesc C = insts[item.inst].lev[item.level + 1];
+    pdl_wait();
+    pdl_trigger();
+    const InstState sv = st[item.inst];
+    if (sv.status != HELM_ST_ACTIVE) return;
+    const int n = F.n, nc = C.n;
+    const int nyb = (nc + TYC - 1) / TYC, nzc = (nc + zchunk - 1) / zchunk;
+    if ((int)blockIdx.x >= nyb * nzc) return;
+    const int Y0 = 1 + (int)(blockIdx.x % nyb) * TYC;
+    const int Z0 = 1 + (int)(blockIdx.x / nyb) * zchunk;
+    const int Z1 = min(Z0 + zchunk, nc + 1);               // own coarse planes [Z0, Z1)
+    const int P = F.pitch, HP = P >> 1;
+    const size_t PR = (size_t)P, PL = (size_t)P * F.rows;
+    const c2* __restrict__ r = (const c2*)lev_rhs(F, item.level, sv.it);
+    c2* W = reinterpret_cast<c2*>(smem_raw);               // [NS][FR][P]
+    constexpr int EPC = 16 / (int)sizeof(c2);
+    const int CPR = P / EPC;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int y0f = 2 * Y0 - 1;                            // first fine row of a slot
+    // fine plane f: rows y0f .. y0f + FR - 1 whole (zero past the last wall row), a warp per row
+    auto stage = [&](int f) {
+        c2* dst = W + (f % K::NS) * FR * P;
+        for (int i = w; i < FR; i += K::NT / 32) {
+            const int yy = y0f + i;
+            const bool in = yy <= n + 1;
+            const c2* src = in ? r + f * PL + yy * PR : r;
+            const unsigned d = (unsigned)__cvta_generic_to_shared(dst + i * P);
+            for (int c = lane; c < CPR; c += 32)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d + 16 * c),
+                             "l"(src + (in ? EPC * c : 0)), "r"(in ? 16 : 0) : "memory");
+        }
+    };
+    auto commit = []() { asm volatile("cp.async.commit_group;\n" ::: "memory"); };
+    stage(2 * Z0 - 1);
+    stage(2 * Z0);
+    stage(2 * Z0 + 1);
+    commit();
+    if (Z0 + 1 < Z1) {
+        stage(2 * Z0 + 2);
+        stage(2 * Z0 + 3);
+    }
+    commit();
+    c2* __restrict__ cr = (c2*)C.rhs;
+    const size_t PRc = (size_t)C.pitch, PLc = (size_t)C.pitch * C.rows;
+    const R scale = (R)(1.0 / 64.0);
+    const int cy = w >> 1;                                  // coarse row of the warp
+    const int Y = Y0 + cy;
+    for (int Z = Z0; Z < Z1; ++Z) {
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        __syncthreads();
+        if (Y <= nc) {
+            for (int X = 1 + lane + 32 * (w & 1); X <= nc; X += 64) {
+                R ax = 0, ay = 0;
+#pragma unroll
+                for (int dz = -1; dz <= 1; ++dz) {
+                    const R wz = (dz == 0) ? (R)2 : (R)1;
+                    const c2* pl = W + ((2 * Z + dz) % K::NS) * FR * P;
+#pragma unroll
+                    for (int dy = -1; dy <= 1; ++dy) {
+                        const R wy = (dy == 0) ? (R)2 : (R)1;
+                        const c2* row = pl + (2 * cy + 1 + dy) * P;   // fine row 2Y + dy
+#pragma unroll
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const R wgt = wz * wy * ((dx == 0) ? (R)2 : (R)1);
+                            const int x = 2 * X + dx;
+                            const c2 rr = row[(x & 1) ? HP + (x >> 1) : (x >> 1)];
+                            ax += wgt * rr.x;
+                            ay += wgt * rr.y;
+                        }
+                    }
+                }
+                c2 v;
+                v.x = ax * scale;
+                v.y = ay * scale;
+                cr[Z * PLc + Y * PRc + xslot<3>(X, C.pitch)] = v;
+            }
+        }
+        __syncthreads();
+        if (Z + 2 < Z1) {
+            stage(2 * Z + 4);
+            stage(2 * Z + 5);
+        }
+        commit();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Multilinear prolongation + correction
 // ---------------------------------------------------------------------------
@@ -430,7 +542,11 @@ template <int D, typename R>
 static cudaError_t carve()
 {
     cudaError_t e;
-    if (D == 3) {
+    if (D == 3 && sizeof(R) == 4) {                        // the z-marching forms are complex64 only
+        if ((e = max_carveout(k_restrict3p<R>)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_restrict3p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)Rs3p<R>::bytes(Rs3p<float>::MAX_P))) != cudaSuccess)
+            return e;
         if ((e = max_carveout(k_rbgs3p<R>)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(k_rbgs3p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)Rb3p<R>::bytes(Rb3p<float>::MAX_HP))) != cudaSuccess)
@@ -478,8 +594,24 @@ cudaError_t launch_rbgs(int D, int prec, const InstDesc* insts, const InstState*
 }
 
 cudaError_t launch_restrict(int D, int prec, const InstDesc* insts, const InstState* st,
-                            const MgItem* items, int nitems, int work, cudaStream_t s, int mode)
+                            const MgItem* items, int nitems, int work, cudaStream_t s, int mode, int nmax)
 {
+    // 3D complex64 restriction of the rhs alone (every iterate of the launch zero) from fine
+    // levels 127 .. 511: the z-marching form
+    const int pitch = (nmax + 2 + 15) / 16 * 16;
+    if (D == 3 && prec != 0 && mode == 2 && nmax >= 127 && pitch <= Rs3p<float>::MAX_P) {
+        const int nc = (nmax - 1) / 2;
+        const size_t sm = Rs3p<float>::bytes(pitch);
+        const int per_sm = (int)(227 * 1024 / (sm + 1024));
+        const int nyb = (nc + Rs3p<float>::TYC - 1) / Rs3p<float>::TYC;
+        int nzc = (152 * (per_sm < 1 ? 1 : per_sm)) / (nyb * nitems);
+        nzc = nzc < 1 ? 1 : (nzc > nc / 4 ? nc / 4 : nzc);      // at least 4 coarse planes a CTA
+        const int zchunk = (nc + nzc - 1) / nzc;
+        nzc = (nc + zchunk - 1) / zchunk;
+        launch_k(k_restrict3p<float>, dim3(nyb * nzc, nitems), dim3(Rs3p<float>::NT), sm, s, insts, st, items,
+                 zchunk);
+        return cudaGetLastError();
+    }
     dim3 g = mg_grid(work, nitems);
     if (D == 2 && prec == 0) launch_k(k_restrict<2, double>, dim3(g), dim3(256), 0, s, insts, st, items, mode);
     else if (D == 2) launch_k(k_restrict<2, float>, dim3(g), dim3(256), 0, s, insts, st, items, mode);
