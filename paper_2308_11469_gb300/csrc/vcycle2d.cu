@@ -350,6 +350,7 @@ constexpr int R2T = 16;                    // level l+2 tile edge
 constexpr int R2W1 = 2 * R2T + 1;          // level l+1 window edge
 constexpr int R2W0 = 4 * R2T + 4;          // level l window edge
 constexpr int R2NT = 256;
+static_assert(R2T * R2T <= R2NT, "a thread per node of the level l+2 tile");
 
 template <typename R> constexpr size_t restrict2_bytes()
 {
@@ -430,7 +431,7 @@ k_restrict2_rhs2d(const InstDesc* __restrict__ insts, const InstState* __restric
     {
         const int x2 = threadIdx.x % R2T, y2 = threadIdx.x / R2T;
         const int X2 = X2a + x2, Y2 = Y2a + y2;
-        if (X2 <= n2 && Y2 <= n2) {
+        if (y2 < R2T && X2 <= n2 && Y2 <= n2) {
             R ax = 0, ay = 0;
 #pragma unroll
             for (int dy = -1; dy <= 1; ++dy) {
