@@ -182,8 +182,8 @@ HELM_API helm_status helm_plan_set_cycle(helm_plan* plan, int nu1, int nu2, int 
  * the timings meaningless: pass the starting iterate of the solves to be tuned (zeros
  * for the paper's start).  u is restored to the starting iterate.  2D plans then time the
  * three tile-shape policies (helm_plan_set_tiles) with the chosen schedule and keep the
- * fastest, and 2D complex64 plans then the coarse-level policies HELM_COARSE_AUTO and
- * HELM_COARSE_CTA (helm_plan_set_coarse_mode).  HELM_DIVERGED if no candidate converged (schedule unchanged).  Allocates one
+ * fastest, and 2D complex64 plans then the three coarse-level policies
+ * (helm_plan_set_coarse_mode).  HELM_DIVERGED if no candidate converged (schedule unchanged).  Allocates one
  * temporary copy of u. */
 HELM_API helm_status helm_plan_autotune(helm_plan* plan, const void* f, const void* g, void* u,
                                         double tol, int max_outer, int* nu1, int* nu2,
@@ -211,9 +211,13 @@ HELM_API helm_status helm_plan_tiles(const helm_plan* plan, int* policy);
  * or 2) of solves with n >= 511, levels 255, 127, 63 and the exact level 31 in one launch of
  * an 8-CTA thread-block cluster per solve (row bands per CTA, rhs halos exchanged through
  * distributed shared memory), replacing four fused level launches and the one-CTA tail;
- * other schedules and sizes keep the CTA form.  HELM_COARSE_AUTO (default): the cluster where
- * it applies to every solve of the launch and the clusters fit in one wave (at most 19
- * solves), else the CTA form; also the CTA form when the device cannot hold one cluster.
+ * other schedules and sizes keep the CTA form; with it, level 1's ascent (prolongation and
+ * sweeps) is formed inside the fused finest-level kernel of same-size solves instead of its
+ * own launch (the lowest latency for a solve running alone; more work per outer step, which
+ * costs throughput when several solves share the GPU).  HELM_COARSE_AUTO (default): the
+ * cluster where it applies to every solve of the launch and the clusters fit in one wave (at
+ * most 19 solves), level 1 keeping its own launch; else the CTA form; also the CTA form when
+ * the device cannot hold one cluster.
  * The results agree to the inner precision's rounding.  helm_plan_coarse_mode reports the
  * policy and, if cluster_used is not NULL, whether the plan's last built outer step used the
  * cluster (0 before its first solve).  helm_batch_set_coarse_mode applies a policy to every

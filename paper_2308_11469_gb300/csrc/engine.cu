@@ -187,8 +187,9 @@ struct Engine {
     int tiles = HELM_TILES_AUTO;
     // coarse levels of 2D complex64 cycles without pre-smoothing: HELM_COARSE_AUTO (levels
     // 255 and below in one 8-CTA cluster per instance when every instance is at least 511
-    // and the clusters fit in one wave), _CTA (one-CTA tail from level 63, fused kernels
-    // above), _CLUSTER (the cluster wherever it applies)
+    // and the clusters fit in one wave), _CTA (one-CTA tail from level 63), _CLUSTER (the
+    // cluster wherever it applies, and level 1's ascent inside the fused finest kernel: the
+    // lowest latency for a solve alone, more work per step when solves share the GPU)
     int coarse = HELM_COARSE_AUTO;
     cudaStream_t cap_stream = nullptr;
     int cap = 0;                               // descriptor slots
@@ -529,8 +530,15 @@ struct Engine {
         }
         if (fuse) {
             const int e2_mode = step.back().mode;
-            step.back() = {LaunchRec::UPRES, ph[0].off, ph[0].cnt, upres2d_tiles(n_all), 1, e2_mode, 0.0,
-                           n_all, nocc};
+            // level 1's ascent inside the fused kernel too (its launch dropped): no
+            // pre-smoothing (level 1's iterate and e2 zero), level 1 a fused level of every
+            // instance, its ascent the launch right before
+            const size_t m = step.size();
+            const bool l1f = nu1 == 0 && J >= 2 && m >= 2 && step[m - 2].kind == LaunchRec::UP &&
+                             step[m - 2].off == ph[1].off && ph[1].cnt == nocc && coarse == HELM_COARSE_CLUSTER;
+            step.back() = {LaunchRec::UPRES, ph[0].off, ph[0].cnt, upres2d_tiles(n_all), l1f ? 1 : 0, e2_mode,
+                           0.0, n_all, nocc};
+            if (l1f) step.erase(step.end() - 2);
         } else {
             step.push_back({LaunchRec::RESID, 0, nres, nocc, 1, 1, b_res});
         }
@@ -560,6 +568,7 @@ struct Engine {
                 if (slots[i] && st[i].status == HELM_ST_ACTIVE) {
                     const InstDesc& d = slots[i]->d;
                     b += pts(d.n) * ((e2z ? 1.0 : 2.0) * eb + 16.0 + 16.0 + 16.0 + eb) + pts(d.lev[1].n) * eb;
+                    if (L.color) b += pts(d.lev[2].n) * eb;       // level 1 fused: its rhs, level 2's e
                 }
             return b;
         }
@@ -647,9 +656,9 @@ struct Engine {
                     e = launch_residual(D, prec, d_desc, d_state, d_res + L.off, L.cnt, L.mode, s,
                                         nullptr, 0, 0, 0, 0, damp_any);
                 break;
-            case LaunchRec::UPRES:
+            case LaunchRec::UPRES:     // color: level 1 fused
                 e = launch_upres2d(d_desc, d_state, d_mg + L.off, L.cnt, L.nmax, nu2, L.mode, s, d_ctrl, cap,
-                                   L.ninst, use_cond ? 1 : 0, (unsigned long long)cond, damp_any);
+                                   L.ninst, use_cond ? 1 : 0, (unsigned long long)cond, damp_any, L.color);
                 break;
             case LaunchRec::CHECK:
                 e = launch_check(d_state, L.cnt, d_ctrl, use_cond ? 1 : 0,
@@ -1281,7 +1290,7 @@ helm_status helm_plan_autotune(helm_plan* p, const void* f, const void* g, void*
     // 2D complex64: the one-CTA coarse tail against the cluster tail (where it applies)
     if (st == HELM_OK && bi >= 0 && p->D == 2 && p->prec != HELM_PREC_FP64) {
         p->eng.tiles = bt;
-        for (int cm = HELM_COARSE_AUTO; cm <= HELM_COARSE_CTA; ++cm) {
+        for (int cm = HELM_COARSE_AUTO; cm <= HELM_COARSE_CLUSTER; ++cm) {
             if (cm == cm0) continue;
             p->eng.coarse = cm;
             p->eng.dirty = true;

@@ -111,9 +111,12 @@ cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* s
 // fused with the mode-1 residual launch and its folded step control (same arguments as
 // launch_residual's).  items: the level-0 items of every instance (all of size n), whose
 // level 0 keeps two right-hand-side buffers.  Level 0's e is not written.
+// l1f: level 1's ascent (prolongation from level 2 + nu2 sweeps, its iterate zero before, no
+// pre-smoothing) is formed inside each tile on the coarse window it reads, in place of
+// level 1's own ascent launch (every instance: level 1 a fused level, its e2 zero).
 cudaError_t launch_upres2d(const InstDesc* insts, InstState* st, const MgItem* items, int nitems, int n,
                            int nu2, int e2_mode, cudaStream_t s, int* ctrl, int nscan, int ninst,
-                           int use_cond, unsigned long long cond_handle, int damp);
+                           int use_cond, unsigned long long cond_handle, int damp, int l1f = 0);
 int upres2d_tiles(int n);
 int residual_tile_rows(int D);
 int residual_tile_planes(int D);

@@ -479,17 +479,27 @@ template <int NU> constexpr int upres_ch() { return (UPY + 2 * (2 * NU + 1)) / 2
 // lets 6 CTAs share an SM instead of 5.
 constexpr bool UPRES_LATE_U = true;
 
-template <int NU, int UX> constexpr size_t upres_bytes()
+// With level 1 fused (L1F), level 1's final iterate on the coarse window comes from its own
+// ascent formed in the tile: level 2's iterate on the window W2 below it, level 1's rhs and
+// prolonged iterate on the coarse window widened by 2 nu2 nodes each side (W1).
+template <int NU, int UX> constexpr int upres_w1x() { return upres_cw<NU, UX>() + 4 * NU; }
+template <int NU> constexpr int upres_w1y() { return upres_ch<NU>() + 4 * NU; }
+template <int NU, int UX> constexpr int upres_w2x() { return upres_w1x<NU, UX>() / 2 + 2; }
+template <int NU> constexpr int upres_w2y() { return upres_w1y<NU>() / 2 + 2; }
+
+template <int NU, int UX, bool L1F = false> constexpr size_t upres_bytes()
 {
     constexpr int H = 2 * NU + 1, W = UX + 2 * H, HH = UPY + 2 * H;
     constexpr size_t ub = (size_t)(UX + 2) * (UPY + 2) * sizeof(double2);
     constexpr size_t planes = (size_t)W * HH * sizeof(float2);          // E0 + E1 (or R0 + R1)
-    constexpr size_t cs = (size_t)upres_cw<NU, UX>() * upres_ch<NU>() * sizeof(float2);
+    constexpr size_t cs = L1F ? (size_t)(2 * upres_w1x<NU, UX>() * upres_w1y<NU>() +
+                                         upres_w2x<NU, UX>() * upres_w2y<NU>()) * sizeof(float2)
+                              : (size_t)upres_cw<NU, UX>() * upres_ch<NU>() * sizeof(float2);
     if constexpr (UPRES_LATE_U) return planes + (ub > planes + cs ? ub : planes + cs);
     return ub + 2 * planes + cs;
 }
 
-template <int NU, bool DAMP, int NTU>
+template <int NU, bool DAMP, int NTU, bool L1F>
 __global__ void __launch_bounds__(NTU, NTU == 128 ? 7 : (UPRES_LATE_U ? 6 : 5))
 k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
           const MgItem* __restrict__ items, int e2_mode, StepCtl ctl)
@@ -563,13 +573,42 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
         }
     };
     if (!UPRES_LATE_U) stage_u();
-    for (int cy = threadIdx.x >> 5; cy < CH; cy += NWU) {
-        const int Y = cy0 + cy;
+    // level 1 fused: its window W1 (origin c1x0, c1y0 = the coarse window's minus 2 nu2),
+    // level 2's iterate under it (origin c1 >> 1) and level 1's rhs; level 1's iterate is
+    // zero before its prolongation (no pre-smoothing), and its window starts cleared so that
+    // the walls and the unassigned outer nodes read zero
+    constexpr int W1X = upres_w1x<NU, UX>(), W1Y = upres_w1y<NU>();
+    constexpr int W2X = upres_w2x<NU, UX>(), W2Y = upres_w2y<NU>();
+    c2* const E1w = Cs;
+    c2* const R1w = Cs + W1X * W1Y;
+    c2* const C2w = Cs + 2 * W1X * W1Y;
+    const int c1x0 = cx0 - 2 * NU, c1y0 = cy0 - 2 * NU;
+    const int c2x0 = c1x0 >> 1, c2y0 = c1y0 >> 1;          // floor
+    if constexpr (L1F) {
+        const LevelDesc C2l = I.lev[2];
+        const c2* __restrict__ g2e = (const c2*)C2l.e;
+        const c2* __restrict__ g1r = (const c2*)C.rhs;
+        const int n1 = C.n, n2 = C2l.n, P2 = C2l.pitch;
+        for (int q = threadIdx.x; q < W2X * W2Y; q += NTU) {
+            const int X = c2x0 + q % W2X, Y = c2y0 + q / W2X;
+            const bool in = X >= 0 && X <= n2 + 1 && Y >= 0 && Y <= n2 + 1;
+            cp_async_elem<sizeof(c2)>(C2w + q, g2e + (in ? (size_t)Y * P2 + X : 0), in);
+        }
+        for (int q = threadIdx.x; q < W1X * W1Y; q += NTU) {
+            const int X = c1x0 + q % W1X, Y = c1y0 + q / W1X;
+            const bool in = X >= 1 && X <= n1 && Y >= 1 && Y <= n1;
+            cp_async_elem<sizeof(c2)>(R1w + q, g1r + (in ? (size_t)Y * PC + X : 0), in);
+            E1w[q] = cz<c2>();
+        }
+    } else {
+        for (int cy = threadIdx.x >> 5; cy < CH; cy += NWU) {
+            const int Y = cy0 + cy;
 #pragma unroll
-        for (int cx = lane; cx < CW; cx += 32) {
-            const int X = cx0 + cx;
-            const bool in = X <= nc1 && Y <= nc1;
-            cp_async_elem<sizeof(c2)>(Cs + cy * CW + cx, gce + (in ? (size_t)Y * PC + X : 0), in);
+            for (int cx = lane; cx < CW; cx += 32) {
+                const int X = cx0 + cx;
+                const bool in = X <= nc1 && Y <= nc1;
+                cp_async_elem<sizeof(c2)>(Cs + cy * CW + cx, gce + (in ? (size_t)Y * PC + X : 0), in);
+            }
         }
     }
     for (int ly = threadIdx.x >> 5; ly < HH; ly += NWU) {
@@ -594,6 +633,54 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     }
     cp_async_wait_all();
     __syncthreads();
+    if constexpr (L1F) {
+        // level 1's ascent on the window, as k_up2d forms it: e := 0 + the interpolation of
+        // level 2 (colour 1 only when sweeps follow: the first half-sweep overwrites colour 0
+        // without reading it), then nu2 sweeps, each half-sweep one node closer to the coarse
+        // window, whose values end final
+        const int n1 = C.n;
+        for (int q = threadIdx.x; q < W1X * W1Y; q += NTU) {
+            const int i = q % W1X, j = q / W1X;
+            const int X = c1x0 + i, Y = c1y0 + j;
+            if (X < 1 || X > n1 || Y < 1 || Y > n1) continue;
+            if (NU > 0 && ((X + Y) & 1) == 0) continue;
+            const int X0 = (X >> 1) - c2x0, X1 = ((X + 1) >> 1) - c2x0;
+            const int Y0 = (Y >> 1) - c2y0, Y1 = ((Y + 1) >> 1) - c2y0;
+            const c2 a = C2w[Y0 * W2X + X0], b = C2w[Y0 * W2X + X1];
+            const c2 c = C2w[Y1 * W2X + X0], d = C2w[Y1 * W2X + X1];
+            c2 v;
+            v.x = (R)0 + (R)0.25 * (((a.x + b.x) + c.x) + d.x);
+            v.y = (R)0 + (R)0.25 * (((a.y + b.y) + c.y) + d.y);
+            E1w[q] = v;
+        }
+        __syncthreads();
+        const R h21 = (R)(C.h * C.h);
+        const R dinv1 = (R)C.dinv;
+#pragma unroll 1
+        for (int sw = 1; sw <= 2 * NU; ++sw) {
+            const int color = (sw - 1) & 1, ring1 = 2 * NU - sw;
+            const int xa = max(cx0 - ring1, 1), xb = min(cx0 + CW - 1 + ring1, n1);
+            const int ya = max(cy0 - ring1, 1), yb = min(cy0 + CH - 1 + ring1, n1);
+            for (int Y = ya + (int)(threadIdx.x >> 5); Y <= yb; Y += NWU) {
+                const int xs = xa + (((xa + Y) & 1) ^ color);
+                const int j = Y - c1y0;
+                for (int X = xs + 2 * lane; X <= xb; X += 64) {
+                    const int o1 = j * W1X + (X - c1x0);
+                    const c2 a = E1w[o1 - 1], b = E1w[o1 + 1], c = E1w[o1 - W1X], d = E1w[o1 + W1X];
+                    const c2 rr = R1w[o1];
+                    c2 v;
+                    v.x = ((a.x + b.x + c.x + d.x) - h21 * rr.x) * dinv1;
+                    v.y = ((a.y + b.y + c.y + d.y) - h21 * rr.y) * dinv1;
+                    E1w[o1] = v;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // level 1's final iterate on the coarse window (its own buffer, or the fused window's
+    // centre)
+    constexpr int CSTR = L1F ? W1X : CW;
+    const c2* const Cr = L1F ? E1w + 2 * NU * W1X + 2 * NU : Cs;
     // correction: e2 + multilinear interpolation of the coarse iterate (interior nodes);
     // with post-smoothing only on colour 1 (the first half-sweep overwrites colour 0, and
     // the outermost ring's colour-0 nodes it leaves are never read)
@@ -608,8 +695,8 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
             const int gx = gx0 + lx;
             if (gx < 1 || gx > n) continue;
             const int X0 = (gx >> 1) - cx0, X1 = ((gx + 1) >> 1) - cx0;
-            const c2 a = Cs[Y0 * CW + X0], b = Cs[Y0 * CW + X1];
-            const c2 c = Cs[Y1 * CW + X0], d = Cs[Y1 * CW + X1];
+            const c2 a = Cr[Y0 * CSTR + X0], b = Cr[Y0 * CSTR + X1];
+            const c2 c = Cr[Y1 * CSTR + X0], d = Cr[Y1 * CSTR + X1];
             c2* Ep = (((lx + ly + cpar) & 1) ? E1 : E0) + PL::at(lx, ly);
             c2 v = *Ep;
             v.x += (R)0.25 * (((a.x + b.x) + c.x) + d.x);
@@ -1273,7 +1360,7 @@ int upres2d_tiles(int n) { return ((n + UPX - 1) / UPX) * ((n + UPY - 1) / UPY);
 
 cudaError_t launch_upres2d(const InstDesc* insts, InstState* st, const MgItem* items, int nitems, int n,
                            int nu2, int e2_mode, cudaStream_t s, int* ctrl, int nscan, int ninst,
-                           int use_cond, unsigned long long cond_handle, int damp)
+                           int use_cond, unsigned long long cond_handle, int damp, int l1f)
 {
     if (nitems <= 0) return cudaSuccess;
     const StepCtl c{ctrl, nscan, ninst, use_cond, cond_handle};
@@ -1281,10 +1368,15 @@ cudaError_t launch_upres2d(const InstDesc* insts, InstState* st, const MgItem* i
     const dim3 b(UPRES_NT);
 #define HELM_UR(NU)                                                                                 \
     case NU:                                                                                        \
-        if (damp) launch_k(k_upres2d<NU, true, UPRES_NT>, g, b, upres_bytes<NU, UPX>(), s, insts, st, items, \
-                           e2_mode, c);                                                             \
-        else launch_k(k_upres2d<NU, false, UPRES_NT>, g, b, upres_bytes<NU, UPX>(), s, insts, st, items,     \
-                      e2_mode, c);                                                                  \
+        if (l1f) {                                                                                  \
+            if (damp) launch_k(k_upres2d<NU, true, UPRES_NT, true>, g, b, upres_bytes<NU, UPX, true>(), s, \
+                               insts, st, items, e2_mode, c);                                       \
+            else launch_k(k_upres2d<NU, false, UPRES_NT, true>, g, b, upres_bytes<NU, UPX, true>(), s,    \
+                          insts, st, items, e2_mode, c);                                            \
+        } else if (damp) launch_k(k_upres2d<NU, true, UPRES_NT, false>, g, b, upres_bytes<NU, UPX>(), s, \
+                                  insts, st, items, e2_mode, c);                                    \
+        else launch_k(k_upres2d<NU, false, UPRES_NT, false>, g, b, upres_bytes<NU, UPX>(), s, insts, st, \
+                      items, e2_mode, c);                                                           \
         break;
     switch (nu2) {
         HELM_UR(0) HELM_UR(1) HELM_UR(2) HELM_UR(3) HELM_UR(4)
@@ -1294,16 +1386,23 @@ cudaError_t launch_upres2d(const InstDesc* insts, InstState* st, const MgItem* i
     return cudaGetLastError();
 }
 
+template <int NU, bool L1F>
+cudaError_t setup_upres_v()
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_upres2d<NU, false, UPRES_NT, L1F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)upres_bytes<NU, UPX, L1F>())) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_upres2d<NU, true, UPRES_NT, L1F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)upres_bytes<NU, UPX, L1F>())) != cudaSuccess) return e;
+    if ((e = max_carveout(k_upres2d<NU, false, UPRES_NT, L1F>)) != cudaSuccess) return e;
+    return max_carveout(k_upres2d<NU, true, UPRES_NT, L1F>);
+}
+
 template <int NU>
 cudaError_t setup_upres()
 {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_upres2d<NU, false, UPRES_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)upres_bytes<NU, UPX>())) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_upres2d<NU, true, UPRES_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)upres_bytes<NU, UPX>())) != cudaSuccess) return e;
-    if ((e = max_carveout(k_upres2d<NU, false, UPRES_NT>)) != cudaSuccess) return e;
-    return max_carveout(k_upres2d<NU, true, UPRES_NT>);
+    const cudaError_t e = setup_upres_v<NU, false>();
+    return e != cudaSuccess ? e : setup_upres_v<NU, true>();
 }
 
 cudaError_t setup_outer()
