@@ -215,8 +215,8 @@ HELM_API helm_status helm_plan_tiles(const helm_plan* plan, int* policy);
  * sweeps) is formed inside the fused finest-level kernel of same-size solves instead of its
  * own launch (the lowest latency for a solve running alone; more work per outer step, which
  * costs throughput when several solves share the GPU).  HELM_COARSE_AUTO (default): the
- * cluster where it applies to every solve of the launch and the clusters fit in one wave (at
- * most 19 solves), level 1 keeping its own launch; else the CTA form; also the CTA form when
+ * cluster where it applies to every solve of the launch and all their clusters can be
+ * resident at once (15 on a GB300), level 1 keeping its own launch; else the CTA form; also the CTA form when
  * the device cannot hold one cluster.
  * The results agree to the inner precision's rounding.  helm_plan_coarse_mode reports the
  * policy and, if cluster_used is not NULL, whether the plan's last built outer step used the

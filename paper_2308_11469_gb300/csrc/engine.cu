@@ -187,7 +187,7 @@ struct Engine {
     int tiles = HELM_TILES_AUTO;
     // coarse levels of 2D complex64 cycles without pre-smoothing: HELM_COARSE_AUTO (levels
     // 255 and below in one 8-CTA cluster per instance when every instance is at least 511
-    // and the clusters fit in one wave), _CTA (one-CTA tail from level 63), _CLUSTER (the
+    // and their clusters are resident at once), _CTA (one-CTA tail from level 63), _CLUSTER (the
     // cluster wherever it applies, and level 1's ascent inside the fused finest kernel: the
     // lowest latency for a solve alone, more work per step when solves share the GPU)
     int coarse = HELM_COARSE_AUTO;
@@ -450,8 +450,8 @@ struct Engine {
                 ++nocc;
                 if (d.ltail < 3 || d.lev[d.ltail - 2].n != 255 || d.lev[d.ltail].n != 63) all = false;
             }
-            use_ct = all && nocc > 0 && (coarse == HELM_COARSE_CLUSTER || nocc * 8 <= 152) &&
-                     ctail_setup() == 1;
+            const int maxc = ctail_setup();        // clusters resident at once
+            use_ct = all && nocc > 0 && maxc > 0 && (coarse == HELM_COARSE_CLUSTER || nocc <= maxc);
         }
         auto tail = [&](std::vector<LaunchRec>& out, bool zero_start) {
             for (const TailGroup& tg : tails)

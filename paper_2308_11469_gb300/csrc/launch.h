@@ -62,7 +62,7 @@ cudaError_t setup_tail(int D, int prec);
 // cluster tail (2D complex64, cycles without pre-smoothing, level 255 below the top): one
 // 8-CTA cluster per item runs levels 255 (the item's level), 127, 63 and the exact level 31
 // and writes level 255's iterate; nu2 in {1, 2}.  ctail_setup() sets its attributes once and
-// tells whether a cluster of it fits on the device (1) or not (0).
+// returns how many of its clusters can be resident at once (0: none fits).
 int ctail_setup();
 cudaError_t launch_ctail(const InstDesc* insts, const InstState* st, const MgItem* items, int nitems,
                          int nu2, cudaStream_t s);

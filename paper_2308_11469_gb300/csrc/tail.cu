@@ -1058,16 +1058,16 @@ cudaError_t ctail_attrs()
     return max_carveout(k_ctail<V>);
 }
 
-// can one cluster of the kernel be resident on this device?
+// how many clusters of the kernel can be resident on this device at once (0: none)
 template <int V>
-bool ctail_fits()
+int ctail_fits()
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CT_CS);
     cfg.blockDim = dim3(TNT);
     cfg.dynamicSmemBytes = CtWin<V>::BYTES;
     int nc = 0;
-    return cudaOccupancyMaxActiveClusters(&nc, k_ctail<V>, &cfg) == cudaSuccess && nc >= 1;
+    return cudaOccupancyMaxActiveClusters(&nc, k_ctail<V>, &cfg) == cudaSuccess ? nc : 0;
 }
 
 
@@ -1154,9 +1154,10 @@ int ctail_setup()
     static int ok = -1;
     if (ok < 0) {
         ok = 0;
-        if (ctail_attrs<1>() == cudaSuccess && ctail_attrs<2>() == cudaSuccess && ctail_fits<1>() &&
-            ctail_fits<2>())
-            ok = 1;
+        if (ctail_attrs<1>() == cudaSuccess && ctail_attrs<2>() == cudaSuccess) {
+            const int a = ctail_fits<1>(), b = ctail_fits<2>();
+            ok = a < b ? a : b;
+        }
         cudaGetLastError();
     }
     return ok;
