@@ -363,6 +363,23 @@ HELM_API helm_status helm_batch_set_lanes(helm_batch* batch, int lanes);
  * must stay valid until then.  HELM_EINVAL for an unknown or finished ticket, or a device
  * pointer. */
 HELM_API helm_status helm_batch_set_host_result(helm_batch* batch, uint64_t ticket, void* host_u);
+
+/* Submit a solve whose data are in host memory (the end-to-end entry point: a caller with
+ * host arrays needs no device memory of its own).  f_host (n^D complex128) and g_host
+ * ((n+2)^D complex128, the wall data on the ring) are read; u_host ((n+2)^D complex128)
+ * receives the padded solution when the solve ends (as helm_batch_set_host_result).  The
+ * batch allocates the solve's device copies with its workspace (counted against the memory
+ * cap), uploads f and g on its own upload stream in submission order and starts the solve
+ * from zero (the paper's start) once they are on the device, so a solve submitted first
+ * runs while the later ones upload.  With page-locked host memory the copies are
+ * asynchronous and the result goes to the host right behind the solve's last step; with
+ * pageable memory each upload returns once its data are copied and the result is copied
+ * when the solve retires.  The host arrays must stay valid until the solve is polled.
+ * HELM_EINVAL for device or managed pointers, overlapping f / g with u, or the conditions of
+ * helm_batch_submit; HELM_ENOMEM over the cap (nothing queued).  No paper counterpart. */
+HELM_API helm_status helm_batch_submit_host(helm_batch* batch, const helm_plan* plan, const void* f_host,
+                                            const void* g_host, void* u_host, double tol, int max_outer,
+                                            uint64_t* ticket);
 HELM_API helm_status helm_batch_poll(helm_batch* batch, uint64_t ticket, int* done, int* status,
                             int* iters, double* res_hist);
 /*

@@ -98,6 +98,7 @@ _SIGS = {
                                   C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "helm_batch_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_size_t)]),
     "helm_batch_set_host_result": (C.c_int, [_vp, C.c_uint64, _vp]),
+    "helm_batch_submit_host": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_uint64)]),
     "helm_batch_profile": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_uint64), C.POINTER(C.c_double),
                                      C.POINTER(C.c_double), C.c_int]),
 }
@@ -588,6 +589,28 @@ def helm_batch_set_host_result(batch: _Batch, ticket: int, u_host) -> None:
         raise ValueError("u_host: a contiguous complex128 CPU tensor")
     _check(load().helm_batch_set_host_result(batch.handle, C.c_uint64(ticket), C.c_void_p(u_host.data_ptr())),
            "helm_batch_set_host_result")
+
+
+def helm_batch_submit_host(batch: _Batch, plan: _Plan, f_host, g_host, u_host, tol: float, max_outer: int):
+    """Submit a solve from host tensors (contiguous complex128 CPU tensors; page-locked for
+    asynchronous copies): f_host interior n^D, g_host the padded wall data, u_host receives
+    the padded solution.  The library uploads, solves from zero and copies the result back.
+    Returns a ticket, or None when the memory cap does not admit the solve yet."""
+    import torch
+    D, n = plan.D, plan.n
+    for t, shape, name in ((f_host, (n,) * D, "f_host"), (g_host, (n + 2,) * D, "g_host"),
+                           (u_host, (n + 2,) * D, "u_host")):
+        if (t.device.type != "cpu" or not t.is_contiguous() or t.dtype != torch.complex128
+                or tuple(t.shape) != shape):
+            raise ValueError(f"{name}: a contiguous complex128 CPU tensor of shape {shape}")
+    tk = C.c_uint64()
+    st = load().helm_batch_submit_host(batch.handle, plan.handle, C.c_void_p(f_host.data_ptr()),
+                                       C.c_void_p(g_host.data_ptr()), C.c_void_p(u_host.data_ptr()),
+                                       float(tol), int(max_outer), C.byref(tk))
+    if st == HELM_ENOMEM:
+        return None
+    _check(st, "helm_batch_submit_host")
+    return tk.value
 
 
 def helm_batch_info(batch: _Batch):

@@ -139,6 +139,9 @@ struct Instance {
     bool stream_ordered = false; // allocated with cudaMallocAsync
     ResItem* d_res0 = nullptr;   // this instance's residual tiles (initial residual)
     int nres0 = 0;
+    char* io = nullptr;          // library-owned f, g, u (solves submitted from host memory)
+    size_t io_bytes = 0;
+    cudaEvent_t ready = nullptr; // their upload done (waited for before the solve starts)
 };
 
 struct LaunchRec {
@@ -804,6 +807,7 @@ struct Engine {
     helm_status start_instance(int slot, cudaStream_t s)
     {
         Instance* in = slots[slot];
+        if (in->ready) HELM_CK(cudaStreamWaitEvent(s, in->ready, 0));   // its upload from host memory
         InstState& init = h_state_stage[slot];
         memset(&init, 0, sizeof init);
         init.status = HELM_ST_ACTIVE;
@@ -843,7 +847,7 @@ struct Engine {
 // One allocation per instance: the workspace (levels, u[1], partials), then its residual
 // tile list, then the relres / increment histories.
 helm_status alloc_instance(Instance& in, int D, int n, double h, double k, int prec,
-                           int max_outer, cudaStream_t s, bool stream_ordered)
+                           int max_outer, cudaStream_t s, bool stream_ordered, size_t io_bytes = 0)
 {
     in.prec = prec;
     in.stream_ordered = stream_ordered;
@@ -853,7 +857,7 @@ helm_status alloc_instance(Instance& in, int D, int n, double h, double k, int p
     const size_t rb = align256((size_t)in.nres0 * sizeof(ResItem));
     in.hist_cap = max_outer;
     const size_t hb = (2 * (size_t)max_outer + 1) * sizeof(double);
-    const size_t total = align256(in.ws_bytes) + rb + hb;
+    const size_t total = align256(in.ws_bytes) + rb + align256(hb) + io_bytes;
     if (stream_ordered) {
         HELM_CK(cudaMallocAsync((void**)&in.ws, total, s));
     } else {
@@ -874,6 +878,8 @@ helm_status alloc_instance(Instance& in, int D, int n, double h, double k, int p
     in.hist = (double*)((char*)in.d_res0 + rb);
     in.d.hist = in.hist;
     in.d.einf = in.hist + max_outer + 1;
+    in.io = io_bytes ? (char*)in.hist + align256(hb) : nullptr;
+    in.io_bytes = io_bytes;
     return HELM_OK;
 }
 
@@ -884,6 +890,9 @@ void free_instance(Instance& in, cudaStream_t s)
         else cudaFree(in.ws);
     }
     if (in.hist_sep && in.hist) cudaFree(in.hist);
+    if (in.ready) cudaEventDestroy(in.ready);
+    in.ready = nullptr;
+    in.io = nullptr;
     in.hist_sep = false;
     in.ws = nullptr;
     in.d_res0 = nullptr;
@@ -944,6 +953,10 @@ struct helm_batch {
     // beside another lane's latency-bound coarse levels.
     int lanes = 4;
     cudaStream_t stream = nullptr;
+    // uploads of solves submitted from host memory (helm_batch_submit_host), in submission
+    // order, so that the first solve starts while the others' data are still coming in
+    cudaStream_t up_stream = nullptr;
+    cudaEvent_t up_fork = nullptr;
     std::map<int, std::unique_ptr<Engine>> engines;   // key = (2 * D + prec) * HELM_MAX_LANES + lane
     // A step launches the engines on streams of decreasing priority, ordered by their
     // longest predicted job, so the critical path's kernels are scheduled first and the
@@ -1501,15 +1514,22 @@ helm_status helm_batch_destroy(helm_batch* b)
     b->engines.clear();
     for (cudaStream_t s : b->rank_streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->rank_join) cudaEventDestroy(e);
+    if (b->up_stream) cudaStreamDestroy(b->up_stream);
+    if (b->up_fork) cudaEventDestroy(b->up_fork);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->h_hist) cudaFreeHost(b->h_hist);
     delete b;
     return HELM_OK;
 }
 
+static helm_status set_host_result_rec(helm_batch::Rec& r, void* host_u);
+
+// host: f, g, u are host pointers (helm_batch_submit_host): the solve's own device copies
+// are part of its allocation, f and g uploaded on the batch's upload stream, u zeroed, and
+// the result copied to u when the solve ends
 static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, int prec,
                                const void* f, const void* g, void* u, double tol, int max_outer,
-                               uint64_t* ticket, double sigma = 0.0, double damp = 0.0)
+                               uint64_t* ticket, double sigma = 0.0, double damp = 0.0, bool host = false)
 {
     if (!b || !ticket) return HELM_EINVAL;
     if (D != 2 && D != 3) return HELM_EINVAL;
@@ -1517,14 +1537,27 @@ static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, 
     if (!(h > 0.0) || !std::isfinite(h) || !(k >= 0.0) || !std::isfinite(k)) return HELM_EINVAL;
     if (prec != HELM_PREC_FP64 && prec != HELM_PREC_MIXED) return HELM_EINVAL;
     if (max_outer < 0 || !(tol >= 0.0)) return HELM_EINVAL;
-    if (check_ptr(f) || check_ptr(g) || check_ptr(u)) return HELM_EINVAL;
     const size_t S = (size_t)n + 2;
     const size_t fb = (D == 3 ? (size_t)n * n * n : (size_t)n * n) * 16;
     const size_t ub = (D == 3 ? S * S * S : S * S) * 16;
+    if (host) {
+        if (!f || !g || !u) return HELM_EINVAL;
+        cudaPointerAttributes a;
+        for (const void* q : {f, g, (const void*)u}) {
+            if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+                cudaGetLastError();
+                return HELM_EINVAL;
+            }
+            if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return HELM_EINVAL;
+        }
+    } else if (check_ptr(f) || check_ptr(g) || check_ptr(u)) {
+        return HELM_EINVAL;
+    }
     if (overlap(f, fb, u, ub) || overlap(g, ub, u, ub)) return HELM_EINVAL;
+    const size_t io_bytes = host ? align256(fb) + 2 * align256(ub) : 0;
     InstDesc probe{};
     const size_t need = layout(probe, D, n, h, k, prec, nullptr) +
-                        (2 * (size_t)max_outer + 1) * sizeof(double);
+                        (2 * (size_t)max_outer + 1) * sizeof(double) + io_bytes;
     if (b->cap_bytes && b->used + need > b->cap_bytes) return HELM_ENOMEM;
     // the lane of this class with the least predicted work in it (solves submitted longest
     // first are then spread as longest-job-first: the longest alone, the rest balanced)
@@ -1565,11 +1598,33 @@ static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, 
         if (st != HELM_OK) return st;
     }
     Instance* in = new Instance();
-    helm_status st = alloc_instance(*in, D, n, h, k, prec, max_outer, b->stream, true);
+    helm_status st = alloc_instance(*in, D, n, h, k, prec, max_outer, b->stream, true, io_bytes);
     if (st != HELM_OK) { free_instance(*in, b->stream); delete in; return st; }
-    in->d.u[0] = (double2*)u;
-    in->d.f = (const double2*)f;
-    in->d.g = (const double2*)g;
+    void* ud = u;
+    const void* fd = f;
+    const void* gd = g;
+    if (host) {
+        // the device copies: the upload stream waits for the allocation (stream-ordered on
+        // the batch stream), then copies f and g and zeroes u (the paper's start; the ring
+        // is set from g when the solve starts); the solve's first step waits for it
+        fd = in->io;
+        gd = in->io + align256(fb);
+        ud = in->io + align256(fb) + align256(ub);
+        if (!b->up_stream) {
+            HELM_CK(cudaStreamCreateWithFlags(&b->up_stream, cudaStreamNonBlocking));
+            HELM_CK(cudaEventCreateWithFlags(&b->up_fork, cudaEventDisableTiming));
+        }
+        HELM_CK(cudaEventCreateWithFlags(&in->ready, cudaEventDisableTiming));
+        HELM_CK(cudaEventRecord(b->up_fork, b->stream));
+        HELM_CK(cudaStreamWaitEvent(b->up_stream, b->up_fork, 0));
+        HELM_CK(cudaMemcpyAsync((void*)fd, f, fb, cudaMemcpyHostToDevice, b->up_stream));
+        HELM_CK(cudaMemcpyAsync((void*)gd, g, ub, cudaMemcpyHostToDevice, b->up_stream));
+        HELM_CK(cudaMemsetAsync(ud, 0, ub, b->up_stream));
+        HELM_CK(cudaEventRecord(in->ready, b->up_stream));
+    }
+    in->d.u[0] = (double2*)ud;
+    in->d.f = (const double2*)fd;
+    in->d.g = (const double2*)gd;
     in->d.tol = tol;
     in->d.max_outer = max_outer;
     set_shift(in->d, sigma);
@@ -1581,8 +1636,12 @@ static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, 
     r.key = key;
     r.slot = slot;
     r.inst = in;
-    r.u = u;
+    r.u = ud;
     r.ubytes = ub;
+    if (host) {
+        st = set_host_result_rec(r, u);
+        if (st != HELM_OK) return st;
+    }
     const uint64_t t = b->next++;
     b->recs[t] = r;
     b->used += need;
@@ -1689,7 +1748,7 @@ static helm_status retire_finished(helm_batch* b)
                                 cudaMemcpyHostToDevice, b->stream));
         InstDesc probe{};
         b->used -= layout(probe, r.inst->d.D, r.inst->d.n, r.inst->d.h, 0.0, r.inst->prec, nullptr) +
-                   (2 * (size_t)r.inst->hist_cap + 1) * sizeof(double);
+                   (2 * (size_t)r.inst->hist_cap + 1) * sizeof(double) + r.inst->io_bytes;
         free_instance(*r.inst, b->stream);
         delete r.inst;
         r.inst = nullptr;
@@ -1956,21 +2015,34 @@ helm_status helm_batch_poll(helm_batch* b, uint64_t ticket, int* done, int* stat
     return HELM_OK;
 }
 
-helm_status helm_batch_set_host_result(helm_batch* b, uint64_t ticket, void* host_u)
+static helm_status set_host_result_rec(helm_batch::Rec& r, void* host_u)
 {
-    if (!b || !host_u) return HELM_EINVAL;
-    auto it = b->recs.find(ticket);
-    if (it == b->recs.end() || it->second.done) return HELM_EINVAL;
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, host_u) != cudaSuccess || a.type == cudaMemoryTypeDevice ||
         a.type == cudaMemoryTypeManaged) {
         cudaGetLastError();
         return HELM_EINVAL;
     }
-    it->second.host_u = host_u;
-    it->second.host_pinned = a.type == cudaMemoryTypeHost;
-    it->second.host_sent = false;
+    r.host_u = host_u;
+    r.host_pinned = a.type == cudaMemoryTypeHost;
+    r.host_sent = false;
     return HELM_OK;
+}
+
+helm_status helm_batch_set_host_result(helm_batch* b, uint64_t ticket, void* host_u)
+{
+    if (!b || !host_u) return HELM_EINVAL;
+    auto it = b->recs.find(ticket);
+    if (it == b->recs.end() || it->second.done) return HELM_EINVAL;
+    return set_host_result_rec(it->second, host_u);
+}
+
+helm_status helm_batch_submit_host(helm_batch* b, const helm_plan* p, const void* f_host, const void* g_host,
+                                   void* u_host, double tol, int max_outer, uint64_t* ticket)
+{
+    if (!p) return HELM_EINVAL;
+    return submit_impl(b, p->D, p->n, p->h, p->k, p->prec, f_host, g_host, u_host, tol, max_outer, ticket,
+                       p->sigma, p->damp, true);
 }
 
 helm_status helm_batch_info(const helm_batch* b, int* active, size_t* bytes)

@@ -144,54 +144,30 @@ class Server:
         B.helm_batch_destroy(self.batch)
 
 
-def solve_host_batch(batch, plans, f_host, g_host, u_host, f_dev, g_dev, u_dev, tol: float,
-                     max_outer: int, lead_steps: int = 4):
-    """Solve problems whose data live in pinned host memory, overlapping the transfers
-    with the solves.
+def solve_host_batch(batch, plans, f_host, g_host, u_host, tol: float, max_outer: int):
+    """Solve problems whose data live in host memory through the library's host entry
+    point (``helm_batch_submit_host``: the library uploads f and g, solves from zero and
+    copies each result into u_host[i] as soon as that solve ends).
 
-    plans[i], f_host[i], g_host[i] (pinned complex128 host tensors) describe problem i;
-    f_dev[i], g_dev[i], u_dev[i] are its device buffers; the result is copied to
-    u_host[i] (pinned) by the batch as soon as that solve ends.  The batch must have been created on the current stream.  The
-    solve whose plan has the largest spectral radius rho (closed form: the most outer
-    steps) is uploaded first and started; the other uploads run on a second stream while
-    it advances `lead_steps` outer steps; each joins once its data are on the device (the
-    batch stream waits for its upload), and all then run to completion.  Each solve's
-    arithmetic depends only on its own data, so the results equal those of submitting
-    them together.  Returns [(status, iters, relres history)] in input order.
+    plans[i], f_host[i], g_host[i] (complex128 CPU tensors, page-locked for asynchronous
+    copies) describe problem i; u_host[i] receives its padded solution.  The solves are
+    submitted in decreasing order of the closed-form spectral radius rho (the most outer
+    steps first): the library uploads in submission order on its own stream and starts each
+    solve once its data are on the device, so the longest solve runs while the others
+    upload.  Returns [(status, iters, relres history)] in input order.
     """
-    import torch
     m = len(plans)
-    main = torch.cuda.current_stream()
-    side = torch.cuda.Stream()
     order = sorted(range(m), key=lambda i: -B.helm_plan_info(plans[i])[2])
-    first, rest = order[0], order[1:]
-    f_dev[first].copy_(f_host[first], non_blocking=True)
-    g_dev[first].copy_(g_host[first], non_blocking=True)
-    u_dev[first].zero_()
-    tickets = {first: B.helm_batch_submit(batch, plans[first], f_dev[first], g_dev[first], u_dev[first],
-                                          tol, max_outer)}
-    # each result goes to the host right behind its solve's last step, beside the others
-    B.helm_batch_set_host_result(batch, tickets[first], u_host[first])
-    side.wait_stream(main)                 # device buffers free of the previous use
-    ready = {}
-    with torch.cuda.stream(side):
-        for i in rest:
-            f_dev[i].copy_(f_host[i], non_blocking=True)
-            g_dev[i].copy_(g_host[i], non_blocking=True)
-            u_dev[i].zero_()
-            ready[i] = torch.cuda.Event()
-            ready[i].record(side)
-    if rest and lead_steps > 0:
-        B.helm_batch_step(batch, lead_steps)
-    for i in rest:
-        main.wait_event(ready[i])
-        tickets[i] = B.helm_batch_submit(batch, plans[i], f_dev[i], g_dev[i], u_dev[i], tol, max_outer)
-        B.helm_batch_set_host_result(batch, tickets[i], u_host[i])
+    tickets = {}
+    for i in order:
+        t = B.helm_batch_submit_host(batch, plans[i], f_host[i], g_host[i], u_host[i], tol, max_outer)
+        if t is None:
+            raise RuntimeError("solve_host_batch: the batch's memory cap does not admit every solve")
+        tickets[i] = t
     B.helm_batch_step(batch, 0)
     out = [None] * m
     for i, t in tickets.items():
         out[i] = B.helm_batch_poll(batch, t, max_outer)
-    main.synchronize()
     return out
 
 

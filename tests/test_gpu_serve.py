@@ -59,21 +59,21 @@ def test_served_stream_equals_solo(B):
         assert np.linalg.norm(j.u.cpu().numpy() - exact) / ref <= bound
 
 
-def test_host_batch_equals_solo(B):
-    # problems in pinned host memory, uploads overlapped with the longest solve: results
-    # and histories equal each solve alone
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_batch_equals_solo(B, pinned):
+    # problems in host memory through the library's host entry point (uploads in submission
+    # order, the longest solve first): results and histories equal each solve alone
     from paper_2308_11469_gb300 import serve
     probs = [inputs.gaussian_cavity_2d(k, seed=2, n=n) for k, n in ((1.0, 127), (3.0, 255), (4.0, 127))]
     plans = [B.helm_plan_create(2, p.n, p.h, p.k, prec=1) for p in probs]
-    fh = [torch.from_numpy(p.f).pin_memory() for p in probs]
-    gh = [torch.from_numpy(p.g).pin_memory() for p in probs]
-    uh = [torch.empty_like(g).pin_memory() for g in gh]
-    fd_ = [torch.empty(f.shape, dtype=f.dtype, device=DEV) for f in fh]
-    gd = [torch.empty(g.shape, dtype=g.dtype, device=DEV) for g in gh]
-    ud = [torch.empty(g.shape, dtype=g.dtype, device=DEV) for g in gh]
+    pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
+    fh = [pin(torch.from_numpy(p.f)) for p in probs]
+    gh = [pin(torch.from_numpy(p.g)) for p in probs]
+    uh = [pin(torch.full_like(g, 7.0)) for g in gh]        # overwritten by the results
     batch = B.helm_batch_create(0)
     for rep in range(2):                       # the second pass reuses the batch's plans
-        out = serve.solve_host_batch(batch, plans, fh, gh, uh, fd_, gd, ud, 1e-8, 2000)
+        out = serve.solve_host_batch(batch, plans, fh, gh, uh, 1e-8, 2000)
+        assert B.helm_batch_info(batch) == (0, 0)
         for i, p in enumerate(probs):
             u = torch.zeros((p.n + 2,) * 2, dtype=torch.complex128, device=DEV)
             st, it, hist = B.helm_solve(plans[i], torch.from_numpy(p.f).to(DEV),
@@ -81,6 +81,9 @@ def test_host_batch_equals_solo(B):
             assert out[i][0] == st == B.HELM_CONVERGED and out[i][1] == it
             assert np.array_equal(out[i][2], hist)
             assert np.array_equal(uh[i].numpy(), u.cpu().numpy())
+    with pytest.raises(ValueError):
+        B.helm_batch_submit_host(batch, plans[0], fh[0].to(DEV), gh[0], uh[0], 1e-8, 10)
     B.helm_batch_destroy(batch)
     for pl in plans:
         B.helm_plan_destroy(pl)
+
