@@ -343,9 +343,11 @@ HELM_API helm_status helm_batch_set_cycle_class(helm_batch* batch, int ndim, int
                                                 int cycles);
 HELM_API helm_status helm_batch_set_tiles(helm_batch* batch, int policy);
 HELM_API helm_status helm_batch_set_coarse_mode(helm_batch* batch, int mode);
-/* Solves of one kernel class (dimension, precision) are spread over `lanes` (1 ..
- * HELM_MAX_LANES, default 4) independent launch streams: each submission joins the lane
- * with the least predicted work (outer steps from the closed-form contraction and the
+/* Solves of one kernel class (dimension, precision) and grid size share engines of their
+ * own (every launch of an engine covers one size, so the size-specific fused kernels apply)
+ * and are spread over `lanes` (1 .. HELM_MAX_LANES, default 4) of them, each with its own
+ * launch stream: each submission joins the lane of its class and size with the least
+ * predicted work (outer steps from the closed-form contraction and the
  * tolerance, times n^D), and helm_batch_step runs the lanes' step graphs concurrently on
  * streams of decreasing priority, the lane holding the longest predicted solve first, so
  * one lane's FP64 residual overlaps another lane's coarse multigrid levels and the critical

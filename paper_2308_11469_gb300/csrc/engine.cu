@@ -957,7 +957,8 @@ struct helm_batch {
     // order, so that the first solve starts while the others' data are still coming in
     cudaStream_t up_stream = nullptr;
     cudaEvent_t up_fork = nullptr;
-    std::map<int, std::unique_ptr<Engine>> engines;   // key = (2 * D + prec) * HELM_MAX_LANES + lane
+    // key = engine_key(class 2 D + prec, grid-size group log2(n + 1), lane)
+    std::map<int, std::unique_ptr<Engine>> engines;
     // A step launches the engines on streams of decreasing priority, ordered by their
     // longest predicted job, so the critical path's kernels are scheduled first and the
     // shorter solves fill the SMs it leaves idle.
@@ -1524,6 +1525,20 @@ helm_status helm_batch_destroy(helm_batch* b)
 
 static helm_status set_host_result_rec(helm_batch::Rec& r, void* host_u);
 
+// Engines are keyed by kernel class, grid size and lane: the solves of one size share
+// their engines (so every launch of an engine covers one size: the fused finest-level
+// kernel, paired descents and cluster tails apply, and no phase of the level-aligned plan
+// is empty for some solves), and each size's solves are spread over `lanes` engines.
+constexpr int KEY_SIZES = 16;                   // log2(n + 1) <= 15
+inline int engine_key(int cls, int sizeg, int lane) { return (cls * KEY_SIZES + sizeg) * HELM_MAX_LANES + lane; }
+inline int engine_class(int key) { return key / (KEY_SIZES * HELM_MAX_LANES); }
+inline int size_group(int n)
+{
+    int g = 0;
+    while (g < KEY_SIZES - 1 && (2 << g) - 1 < n) ++g;
+    return g + 1 < KEY_SIZES ? g + 1 : KEY_SIZES - 1;
+}
+
 // host: f, g, u are host pointers (helm_batch_submit_host): the solve's own device copies
 // are part of its allocation, f and g uploaded on the batch's upload stream, u zeroed, and
 // the result copied to u when the solve ends
@@ -1559,14 +1574,16 @@ static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, 
     const size_t need = layout(probe, D, n, h, k, prec, nullptr) +
                         (2 * (size_t)max_outer + 1) * sizeof(double) + io_bytes;
     if (b->cap_bytes && b->used + need > b->cap_bytes) return HELM_ENOMEM;
-    // the lane of this class with the least predicted work in it (solves submitted longest
-    // first are then spread as longest-job-first: the longest alone, the rest balanced)
-    int key = (2 * D + prec) * HELM_MAX_LANES;
+    // the lane of this class and size with the least predicted work in it (solves submitted
+    // longest first are then spread as longest-job-first: the longest alone, the rest
+    // balanced)
+    const int sg = size_group(n);
+    int key = engine_key(2 * D + prec, sg, 0);
     {
         double best = 0.0;
         bool first = true;
         for (int lane = 0; lane < b->lanes; ++lane) {
-            const int k2 = (2 * D + prec) * HELM_MAX_LANES + lane;
+            const int k2 = engine_key(2 * D + prec, sg, lane);
             auto e = b->engines.find(k2);
             const double w = (e == b->engines.end()) ? 0.0 : e->second->total_work();
             if (first || w < best) { best = w; key = k2; first = false; }
@@ -1801,7 +1818,7 @@ helm_status helm_batch_set_cycle_class(helm_batch* b, int ndim, int prec, int nu
     b->cls_sched[c][1] = nu2;
     b->cls_sched[c][2] = cycles;
     for (auto& kv : b->engines) {
-        if (kv.first / HELM_MAX_LANES != c) continue;
+        if (engine_class(kv.first) != c) continue;
         kv.second->nu1 = nu1;
         kv.second->nu2 = nu2;
         kv.second->cycles = cycles;
