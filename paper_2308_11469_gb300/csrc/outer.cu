@@ -916,7 +916,9 @@ __device__ __forceinline__ void residual3d_tile_fx(const InstDesc* __restrict__ 
     ep[1] = stage(1, z0, true, cur);
     int sp = 0, sc = 1, sn = 2;                 // ring slots of planes z-1, z, z+1
     for (int z = z0; z <= z1; ++z) {
-        __syncthreads();                        // sx reuse; the oldest slot is free
+        // no barrier needed here: stage writes sx before, and the oldest slot after, the
+        // barrier inside its exponent reduction, which every thread reaches only once done
+        // with the previous plane (its reads of sx and of that slot)
         ep[sn] = stage(sn, z + 1, z + 1 <= z1, nxt);
         __syncthreads();
         if (live) {
