@@ -601,35 +601,32 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
             E1w[q] = cz<c2>();
         }
     } else {
-        for (int cy = threadIdx.x >> 5; cy < CH; cy += NWU) {
-            const int Y = cy0 + cy;
-#pragma unroll
-            for (int cx = lane; cx < CW; cx += 32) {
-                const int X = cx0 + cx;
-                const bool in = X <= nc1 && Y <= nc1;
-                cp_async_elem<sizeof(c2)>(Cs + cy * CW + cx, gce + (in ? (size_t)Y * PC + X : 0), in);
-            }
+        for (int q = threadIdx.x; q < CW * CH; q += NTU) {
+            const int cy = q / CW, cx = q - cy * CW;
+            const int X = cx0 + cx, Y = cy0 + cy;
+            const bool in = X <= nc1 && Y <= nc1;
+            cp_async_elem<sizeof(c2)>(Cs + q, gce + (in ? (size_t)Y * PC + X : 0), in);
         }
     }
-    for (int ly = threadIdx.x >> 5; ly < HH; ly += NWU) {
+    // the window's W x HH nodes numbered row by row over the threads (rows of a few dozen
+    // nodes: a warp per row would leave lanes idle)
+    for (int q = threadIdx.x; q < W * HH; q += NTU) {
+        const int ly = q / W, lx = q - ly * W;
         const int gy = gy0 + ly;
         const bool yin = gy >= 1 && gy <= n;
-#pragma unroll
-        for (int lx = lane; lx < W; lx += 32) {
-            const int gx = gx0 + lx;
-            const bool in = yin && gx >= 1 && gx <= n;
-            const size_t g = in ? (size_t)gy * P + gx : 0;
-            const int c = (lx + ly + cpar) & 1;
-            const int o = PL::at(lx, ly);
-            // with post-smoothing the first half-sweep overwrites every interior colour-0
-            // node it reads later, without reading their old values: colour 0 needs e2
-            // only off the interior (the walls' zeros, which the sweeps read)
-            if (NU == 0 || c || !in) {
-                if (e2z) (c ? E1 : E0)[o] = cz<c2>();
-                else cp_async_elem<sizeof(c2)>((c ? E1 : E0) + o, ge2 + g, in);
-            }
-            cp_async_elem<sizeof(c2)>((c ? R1 : R0) + o, gr + g, in);
+        const int gx = gx0 + lx;
+        const bool in = yin && gx >= 1 && gx <= n;
+        const size_t g = in ? (size_t)gy * P + gx : 0;
+        const int c = (lx + ly + cpar) & 1;
+        const int o = PL::at(lx, ly);
+        // with post-smoothing the first half-sweep overwrites every interior colour-0
+        // node it reads later, without reading their old values: colour 0 needs e2
+        // only off the interior (the walls' zeros, which the sweeps read)
+        if (NU == 0 || c || !in) {
+            if (e2z) (c ? E1 : E0)[o] = cz<c2>();
+            else cp_async_elem<sizeof(c2)>((c ? E1 : E0) + o, ge2 + g, in);
         }
+        cp_async_elem<sizeof(c2)>((c ? R1 : R0) + o, gr + g, in);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -684,37 +681,29 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
     // correction: e2 + multilinear interpolation of the coarse iterate (interior nodes);
     // with post-smoothing only on colour 1 (the first half-sweep overwrites colour 0, and
     // the outermost ring's colour-0 nodes it leaves are never read)
-    for (int ly = threadIdx.x >> 5; ly < HH; ly += NWU) {
+    // nodes numbered row by row over the threads: all W of a row, or its W / 2 colour-1 nodes
+    constexpr int CNX = (NU == 0) ? W : W / 2;
+    for (int q = threadIdx.x; q < CNX * HH; q += NTU) {
+        const int ly = q / CNX, i = q - ly * CNX;
         const int gy = gy0 + ly;
         if (gy < 1 || gy > n) continue;
         const int Y0 = (gy >> 1) - cy0, Y1 = ((gy + 1) >> 1) - cy0;
-        const int lx0 = (NU == 0) ? lane : 2 * lane + ((ly + cpar + 1) & 1);
-        const int dlx = (NU == 0) ? 32 : 64;
-#pragma unroll
-        for (int lx = lx0; lx < W; lx += dlx) {
-            const int gx = gx0 + lx;
-            if (gx < 1 || gx > n) continue;
-            const int X0 = (gx >> 1) - cx0, X1 = ((gx + 1) >> 1) - cx0;
-            const c2 a = Cr[Y0 * CSTR + X0], b = Cr[Y0 * CSTR + X1];
-            const c2 c = Cr[Y1 * CSTR + X0], d = Cr[Y1 * CSTR + X1];
-            c2* Ep = (((lx + ly + cpar) & 1) ? E1 : E0) + PL::at(lx, ly);
-            c2 v = *Ep;
-            v.x += (R)0.25 * (((a.x + b.x) + c.x) + d.x);
-            v.y += (R)0.25 * (((a.y + b.y) + c.y) + d.y);
-            *Ep = v;
-        }
+        const int lx = (NU == 0) ? i : 2 * i + ((ly + cpar + 1) & 1);
+        const int gx = gx0 + lx;
+        if (gx < 1 || gx > n) continue;
+        const int X0 = (gx >> 1) - cx0, X1 = ((gx + 1) >> 1) - cx0;
+        const c2 a = Cr[Y0 * CSTR + X0], b = Cr[Y0 * CSTR + X1];
+        const c2 c = Cr[Y1 * CSTR + X0], d = Cr[Y1 * CSTR + X1];
+        c2* Ep = (((lx + ly + cpar) & 1) ? E1 : E0) + PL::at(lx, ly);
+        c2 v = *Ep;
+        v.x += (R)0.25 * (((a.x + b.x) + c.x) + d.x);
+        v.y += (R)0.25 * (((a.y + b.y) + c.y) + d.y);
+        *Ep = v;
     }
     __syncthreads();
     const R h2 = (R)(L.h * L.h);
     const R dinv = (R)L.dinv;
-    int ring = 2 * NU;                           // the last half-sweep covers ring 1
-#pragma unroll 1
-    for (int s = 0; s < NU; ++s) {
-        half_sweep<R, W, TX, TY, NWU>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, dinv, 0);
-        __syncthreads();
-        half_sweep<R, W, TX, TY, NWU>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, dinv, 1);
-        __syncthreads();
-    }
+    sweeps_flat<R, W, TX, TY, NTU, 2 * NU, 2 * NU>(E0, E1, R0, R1, gx0, gy0, x0, y0, n, h2, dinv);
     if (UPRES_LATE_U) {                          // the rhs planes and Cs are dead: u_N there
         stage_u();
         cp_async_wait_all();

@@ -72,34 +72,25 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const int lane = threadIdx.x & 31;
     // stage e (or zeros) and rhs with asynchronous copies: every load of the tile is in
     // flight at once; nodes outside the interior are zero-filled
-    for (int ly = threadIdx.x >> 5; ly < HH; ly += NW) {
+    for (int q = threadIdx.x; q < W * HH; q += NT) {
+        const int ly = q / W, lx = q - ly * W;
         const int gy = gy0 + ly;
         const bool yin = gy >= 1 && gy <= n;
-#pragma unroll
-        for (int lx = lane; lx < W; lx += 32) {
-            const int gx = gx0 + lx;
-            const bool in = yin && gx >= 1 && gx <= n;
-            const size_t g = in ? (size_t)gy * P + gx : 0;
-            const int c = (lx + ly + cpar) & 1;
-            const int o = PL::at(lx, ly);
-            if (zero) (c ? E1 : E0)[o] = cz<c2>();
-            else cp_async_elem<sizeof(c2)>((c ? E1 : E0) + o, ge + g, in);
-            cp_async_elem<sizeof(c2)>((c ? R1 : R0) + o, gr + g, in);
-        }
+        const int gx = gx0 + lx;
+        const bool in = yin && gx >= 1 && gx <= n;
+        const size_t g = in ? (size_t)gy * P + gx : 0;
+        const int c = (lx + ly + cpar) & 1;
+        const int o = PL::at(lx, ly);
+        if (zero) (c ? E1 : E0)[o] = cz<c2>();
+        else cp_async_elem<sizeof(c2)>((c ? E1 : E0) + o, ge + g, in);
+        cp_async_elem<sizeof(c2)>((c ? R1 : R0) + o, gr + g, in);
     }
     cp_async_wait_all();
     __syncthreads();
     const R h2 = (R)(L.h * L.h);
     const R dinv = (R)L.dinv;                      // 1 / (4 + sigma h^2)
     const R sig = (R)sigma;
-    int ring = 2 * NU + 1;
-#pragma unroll 1
-    for (int s = 0; s < NU; ++s) {
-        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, dinv, 0);
-        __syncthreads();
-        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, dinv, 1);
-        __syncthreads();
-    }
+    sweeps_flat<R, W, TX, TY, NT, 2 * NU + 1, 2 * NU>(E0, E1, R0, R1, gx0, gy0, x0, y0, n, h2, dinv);
     // no pre-smoothing from a zero iterate: e2 stays zero (the ascent kernel knows it and
     // does not read it) and the residual is rhs itself
     const bool skip = (NU == 0) && zero;
@@ -118,32 +109,30 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     // residual on the tile plus a 1-node ring, in place of rhs (one colour at a time)
     const R ih2 = (R)1 / h2;
     if (!skip) {
-        const int xa = max(x0 - 1, 1), xb = min(x0 + TX, n);
-        const int ya = max(y0 - 1, 1), yb = min(y0 + TY, n);
-#pragma unroll
-        for (int color = 0; color < 2; ++color) {
+        // both colours' nodes of the tile plus its ring, numbered colour by colour and row
+        // by row over the threads ((TX + 2) / 2 of a colour in each of TY + 2 rows)
+        constexpr int NX = (TX + 2) / 2, NY = TY + 2;
+        for (int q = threadIdx.x; q < 2 * NX * NY; q += NT) {
+            const int color = q >= NX * NY;
+            const int qq = q - color * (NX * NY);
+            const int jy = qq / NX, i = qq - jy * NX;
+            const int gy = y0 - 1 + jy;
+            const int gx = x0 - 1 + (((x0 - 1 + gy) & 1) ^ color) + 2 * i;
+            if (gy < 1 || gy > n || gx < 1 || gx > n) continue;
             const c2* __restrict__ Ec = color ? E1 : E0;
             const c2* __restrict__ Eo = color ? E0 : E1;
             c2* __restrict__ Rc = color ? R1 : R0;
-            for (int gy = ya + (int)(threadIdx.x >> 5); gy <= yb; gy += NW) {
-                const int xs = xa + (((xa + gy) & 1) ^ color);
-                const int ly = gy - gy0;
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int gx = xs + 2 * (lane + 32 * j);
-                    if (gx > xb) break;
-                    const int lx = gx - gx0;
-                    const int o = PL::at(lx, ly);
-                    const c2 c = Ec[o];
-                    const c2 a = Eo[PL::at(lx - 1, ly)], b = Eo[PL::at(lx + 1, ly)];
-                    const c2 u = Eo[PL::at(lx, ly - 1)], d = Eo[PL::at(lx, ly + 1)];
-                    const c2 rr = Rc[o];
-                    c2 v;
-                    v.x = (rr.x - ((a.x + b.x + u.x + d.x) - (R)4 * c.x) * ih2) + sig * c.x;
-                    v.y = (rr.y - ((a.y + b.y + u.y + d.y) - (R)4 * c.y) * ih2) + sig * c.y;
-                    Rc[o] = v;
-                }
-            }
+            const int ly = gy - gy0;
+            const int lx = gx - gx0;
+            const int o = PL::at(lx, ly);
+            const c2 c = Ec[o];
+            const c2 a = Eo[PL::at(lx - 1, ly)], b = Eo[PL::at(lx + 1, ly)];
+            const c2 u = Eo[PL::at(lx, ly - 1)], d = Eo[PL::at(lx, ly + 1)];
+            const c2 rr = Rc[o];
+            c2 v;
+            v.x = (rr.x - ((a.x + b.x + u.x + d.x) - (R)4 * c.x) * ih2) + sig * c.x;
+            v.y = (rr.y - ((a.y + b.y + u.y + d.y) - (R)4 * c.y) * ih2) + sig * c.y;
+            Rc[o] = v;
         }
     }
     __syncthreads();
@@ -152,10 +141,11 @@ k_down2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     const int nc = C.n;
     const int Xa = (x0 + 1) >> 1, Ya = (y0 + 1) >> 1;
     const int PC = C.pitch;
-    for (int cy = threadIdx.x >> 5; cy < TY / 2; cy += NW) {
+    for (int q = threadIdx.x; q < (TX / 2) * (TY / 2); q += NT) {
+        const int cy = q / (TX / 2), cx = q - cy * (TX / 2);
         const int Y = Ya + cy;
-        const int X = Xa + lane;
-        if (lane >= TX / 2 || Y > nc || X > nc) continue;
+        const int X = Xa + cx;
+        if (Y > nc || X > nc) continue;
         const int lx = 2 * X - gx0, ly = 2 * Y - gy0;
         R ax = 0, ay = 0;
 #pragma unroll
@@ -224,62 +214,51 @@ k_up2d(const InstDesc* __restrict__ insts, const InstState* __restrict__ st,
     // level started from zero: e2_mode 2 = every level, 1 = the levels below the finest
     const bool e2z = (e2_mode == 2) || (e2_mode == 1 && item.level > 0);
     // stage the coarse window, e2 and rhs with asynchronous copies (zero-filled outside)
-    for (int cy = threadIdx.x >> 5; cy < CH; cy += NW) {
+    // windows numbered row by row over the threads (rows of a few dozen nodes: a warp per
+    // row would leave lanes idle)
+    for (int q = threadIdx.x; q < CW * CH; q += NT) {
+        const int cy = q / CW, cx = q - cy * CW;
         const int Y = cy0 + cy;
-#pragma unroll
-        for (int cx = lane; cx < CW; cx += 32) {
-            const int X = cx0 + cx;
-            const bool in = X <= nc1 && Y <= nc1;
-            cp_async_elem<sizeof(c2)>(Cs + cy * CW + cx, gce + (in ? (size_t)Y * PC + X : 0), in);
-        }
+        const int X = cx0 + cx;
+        const bool in = X <= nc1 && Y <= nc1;
+        cp_async_elem<sizeof(c2)>(Cs + cy * CW + cx, gce + (in ? (size_t)Y * PC + X : 0), in);
     }
-    for (int ly = threadIdx.x >> 5; ly < HH; ly += NW) {
+    for (int q = threadIdx.x; q < W * HH; q += NT) {
+        const int ly = q / W, lx = q - ly * W;
         const int gy = gy0 + ly;
         const bool yin = gy >= 1 && gy <= n;
-#pragma unroll
-        for (int lx = lane; lx < W; lx += 32) {
-            const int gx = gx0 + lx;
-            const bool in = yin && gx >= 1 && gx <= n;
-            const size_t g = in ? (size_t)gy * P + gx : 0;
-            const int c = (lx + ly + cpar) & 1;
-            const int o = PL::at(lx, ly);
-            if (e2z) (c ? E1 : E0)[o] = cz<c2>();
-            else cp_async_elem<sizeof(c2)>((c ? E1 : E0) + o, ge2 + g, in);
-            cp_async_elem<sizeof(c2)>((c ? R1 : R0) + o, gr + g, in);
-        }
+        const int gx = gx0 + lx;
+        const bool in = yin && gx >= 1 && gx <= n;
+        const size_t g = in ? (size_t)gy * P + gx : 0;
+        const int c = (lx + ly + cpar) & 1;
+        const int o = PL::at(lx, ly);
+        if (e2z) (c ? E1 : E0)[o] = cz<c2>();
+        else cp_async_elem<sizeof(c2)>((c ? E1 : E0) + o, ge2 + g, in);
+        cp_async_elem<sizeof(c2)>((c ? R1 : R0) + o, gr + g, in);
     }
     cp_async_wait_all();
     __syncthreads();
     // correction: e2 + multilinear interpolation of the coarse iterate (interior nodes)
-    for (int ly = threadIdx.x >> 5; ly < HH; ly += NW) {
+    for (int q = threadIdx.x; q < W * HH; q += NT) {
+        const int ly = q / W, lx = q - ly * W;
         const int gy = gy0 + ly;
         if (gy < 1 || gy > n) continue;
         const int Y0 = (gy >> 1) - cy0, Y1 = ((gy + 1) >> 1) - cy0;
-#pragma unroll
-        for (int lx = lane; lx < W; lx += 32) {
-            const int gx = gx0 + lx;
-            if (gx < 1 || gx > n) continue;
-            const int X0 = (gx >> 1) - cx0, X1 = ((gx + 1) >> 1) - cx0;
-            const c2 a = Cs[Y0 * CW + X0], b = Cs[Y0 * CW + X1];
-            const c2 c = Cs[Y1 * CW + X0], d = Cs[Y1 * CW + X1];
-            c2* Ep = (((lx + ly + cpar) & 1) ? E1 : E0) + PL::at(lx, ly);
-            c2 v = *Ep;
-            v.x += (R)0.25 * (((a.x + b.x) + c.x) + d.x);
-            v.y += (R)0.25 * (((a.y + b.y) + c.y) + d.y);
-            *Ep = v;
-        }
+        const int gx = gx0 + lx;
+        if (gx < 1 || gx > n) continue;
+        const int X0 = (gx >> 1) - cx0, X1 = ((gx + 1) >> 1) - cx0;
+        const c2 a = Cs[Y0 * CW + X0], b = Cs[Y0 * CW + X1];
+        const c2 c = Cs[Y1 * CW + X0], d = Cs[Y1 * CW + X1];
+        c2* Ep = (((lx + ly + cpar) & 1) ? E1 : E0) + PL::at(lx, ly);
+        c2 v = *Ep;
+        v.x += (R)0.25 * (((a.x + b.x) + c.x) + d.x);
+        v.y += (R)0.25 * (((a.y + b.y) + c.y) + d.y);
+        *Ep = v;
     }
     __syncthreads();
     const R h2 = (R)(L.h * L.h);
     const R dinv = (R)L.dinv;
-    int ring = 2 * NU - 1;
-#pragma unroll 1
-    for (int s = 0; s < NU; ++s) {
-        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, dinv, 0);
-        __syncthreads();
-        half_sweep<R, W, TX, TY>(E0, E1, R0, R1, gx0, gy0, x0, y0, ring--, n, h2, dinv, 1);
-        __syncthreads();
-    }
+    sweeps_flat<R, W, TX, TY, NT, 2 * NU - 1, 2 * NU>(E0, E1, R0, R1, gx0, gy0, x0, y0, n, h2, dinv);
     c2* __restrict__ ge = (c2*)L.e;
     for (int ty = threadIdx.x >> 5; ty < TY; ty += NW) {
         const int gy = y0 + ty;
@@ -428,27 +407,25 @@ k_restrict2_rhs2d(const InstDesc* __restrict__ insts, const InstState* __restric
     // the level l+2 tile: node (X2a + x2, Y2a + y2) reads window element (2 x2 + 1 + dx, ...)
     c2* __restrict__ g2 = (c2*)L2.rhs;
     const int P2 = L2.pitch;
-    {
-        const int x2 = threadIdx.x % R2T, y2 = threadIdx.x / R2T;
-        const int X2 = X2a + x2, Y2 = Y2a + y2;
-        if (y2 < R2T && X2 <= n2 && Y2 <= n2) {
-            R ax = 0, ay = 0;
+    const int x2 = threadIdx.x % R2T, y2 = threadIdx.x / R2T;
+    const int X2 = X2a + x2, Y2 = Y2a + y2;
+    if (y2 < R2T && X2 <= n2 && Y2 <= n2) {
+        R ax = 0, ay = 0;
 #pragma unroll
-            for (int dy = -1; dy <= 1; ++dy) {
-                const R wy = (dy == 0) ? (R)2 : (R)1;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const R wy = (dy == 0) ? (R)2 : (R)1;
 #pragma unroll
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const R wgt = wy * ((dx == 0) ? (R)2 : (R)1);
-                    const c2 r = W1[(2 * y2 + 1 + dy) * R2W1 + 2 * x2 + 1 + dx];
-                    ax += wgt * r.x;
-                    ay += wgt * r.y;
-                }
+            for (int dx = -1; dx <= 1; ++dx) {
+                const R wgt = wy * ((dx == 0) ? (R)2 : (R)1);
+                const c2 r = W1[(2 * y2 + 1 + dy) * R2W1 + 2 * x2 + 1 + dx];
+                ax += wgt * r.x;
+                ay += wgt * r.y;
             }
-            c2 v;
-            v.x = ax * (R)(1.0 / 16.0);
-            v.y = ay * (R)(1.0 / 16.0);
-            g2[(size_t)Y2 * P2 + X2] = v;
         }
+        c2 v;
+        v.x = ax * (R)(1.0 / 16.0);
+        v.y = ay * (R)(1.0 / 16.0);
+        g2[(size_t)Y2 * P2 + X2] = v;
     }
 }
 
