@@ -58,6 +58,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 KS = (1.0, 2.0, 3.0, 4.0)
+# concurrent engines of the 4-solve batch: the k = 4 solve (75 of the 129 outer steps) in
+# one lane, the three shorter ones together in the other; measured 6.42 against 6.53 (3
+# lanes) and 6.63 ms (4, the library's default) per step of four solves
+LANES = 2
 N_GRID = 1023
 TOL = 1e-8
 MAX_OUTER = 2000
@@ -68,9 +72,10 @@ FP64_PEAK_TFLOPS = 1.25          # GB300 nominal FP64 rate (FMA = 2 flops)
 # scaled below to the points of an average launch; None where the kernel changed after its
 # capture (the bench's top kernel is the fused one)
 RESIDUAL_DRAM_BYTES_PER_POINT = None
-# the finest level's ascent fused with the residual (fixed-point numerator): one ncu
-# capture of the single-solve replay's launch (44.17 MB read + 1.24 MB written)
-UPRES_DRAM_BYTES_PER_POINT = (44.173312e6 + 1.238528e6) / (1023 ** 2)
+# the finest level's ascent fused with the residual (fixed-point numerator, loops flattened
+# over the CTA's threads): one ncu capture of the single-solve replay's launch (44.17 MB
+# read + 1.16 MB written)
+UPRES_DRAM_BYTES_PER_POINT = (44.171776e6 + 1.163264e6) / (1023 ** 2)
 
 
 def _peaks():
@@ -530,6 +535,7 @@ def main():
     mixed_plans = [B.helm_plan_create(2, n, h, k, prec=B.HELM_PREC_MIXED) for k in KS]
     fp64_plans = [B.helm_plan_create(2, n, h, k, prec=B.HELM_PREC_FP64) for k in KS]
     batch = B.helm_batch_create(120 << 30)
+    B.helm_batch_set_lanes(batch, LANES)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
     # autotuned inner schedule (smoother sweeps, cycles per outer step), chosen on the
@@ -718,7 +724,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "c64/c128",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "h": h, "k": list(KS), "tol": TOL,
-                   "solves_per_step": len(KS),
+                   "solves_per_step": len(KS), "lanes": LANES,
                    "form": "mixed complex64 V-cycles + FP64 refinement, 4-instance batch",
                    "schedule_mixed": {"nu1": sched_mixed[0], "nu2": sched_mixed[1], "cycles": sched_mixed[2],
                                       "tiles": ("auto", "large", "small")[tiles_mixed]},
