@@ -216,8 +216,11 @@ HELM_API helm_status helm_plan_tiles(const helm_plan* plan, int* policy);
  * own launch (the lowest latency for a solve running alone; more work per outer step, which
  * costs throughput when several solves share the GPU).  HELM_COARSE_AUTO (default): the
  * cluster where it applies to every solve of the launch and all their clusters can be
- * resident at once (15 on a GB300), level 1 keeping its own launch; else the CTA form; also the CTA form when
- * the device cannot hold one cluster.
+ * resident at once (15 on a GB300); else the CTA form; also the CTA form when the device
+ * cannot hold one cluster.  Level 1's ascent is fused as with HELM_COARSE_CLUSTER where the
+ * launch is a critical path: a plan's own solve, or, in a batch step, the lane with the
+ * longest predicted solve when it holds that solve alone; the other lanes keep its own
+ * launch.
  * The results agree to the inner precision's rounding.  helm_plan_coarse_mode reports the
  * policy and, if cluster_used is not NULL, whether the plan's last built outer step used the
  * cluster (0 before its first solve).  helm_batch_set_coarse_mode applies a policy to every

@@ -194,6 +194,11 @@ struct Engine {
     // cluster wherever it applies, and level 1's ascent inside the fused finest kernel: the
     // lowest latency for a solve alone, more work per step when solves share the GPU)
     int coarse = HELM_COARSE_AUTO;
+    // With HELM_COARSE_AUTO, whether this engine is the caller's critical path: a plan's own
+    // solve, or a batch's highest-priority lane holding a single solve.  Such an engine
+    // forms level 1's ascent inside the fused finest kernel (as HELM_COARSE_CLUSTER does),
+    // trading throughput it does not need for latency.
+    bool latency = false;
     cudaStream_t cap_stream = nullptr;
     int cap = 0;                               // descriptor slots
     std::vector<Instance*> slots;              // nullptr = free
@@ -538,7 +543,8 @@ struct Engine {
             // instance, its ascent the launch right before
             const size_t m = step.size();
             const bool l1f = nu1 == 0 && J >= 2 && m >= 2 && step[m - 2].kind == LaunchRec::UP &&
-                             step[m - 2].off == ph[1].off && ph[1].cnt == nocc && coarse == HELM_COARSE_CLUSTER;
+                             step[m - 2].off == ph[1].off && ph[1].cnt == nocc &&
+                             (coarse == HELM_COARSE_CLUSTER || (coarse == HELM_COARSE_AUTO && latency));
             step.back() = {LaunchRec::UPRES, ph[0].off, ph[0].cnt, upres2d_tiles(n_all), l1f ? 1 : 0, e2_mode,
                            0.0, n_all, nocc};
             if (l1f) step.erase(step.end() - 2);
@@ -705,7 +711,7 @@ struct Engine {
     // whether any instance has a damping term (it selects the residual kernels' variant).
     std::vector<long> current_signature() const
     {
-        std::vector<long> sig{cap, nu1, nu2, cycles, tiles, coarse};
+        std::vector<long> sig{cap, nu1, nu2, cycles, tiles, coarse, latency ? 1L : 0L};
         long damp = 0;
         for (int i = 0; i < cap; ++i) {
             sig.push_back(slots[i] ? (long)slots[i]->d.n * 4 + (long)slots[i]->d.D : -1L);
@@ -1056,6 +1062,7 @@ helm_status helm_plan_create(helm_plan** out, int ndim, const int* n, double h, 
     p->stream = (cudaStream_t)cuda_stream;
     helm_status st = p->eng.init(ndim, prec);
     if (st != HELM_OK) return st;
+    p->eng.latency = true;                     // a plan's solve runs alone
     st = alloc_instance(p->inst, ndim, n[0], h, k, prec, 1024, p->stream, false);
     if (st != HELM_OK) return st;
     p->eng.slots[0] = &p->inst;
@@ -1878,20 +1885,35 @@ static helm_status rank_stream(helm_batch* b, int r, cudaStream_t* s, cudaEvent_
     return HELM_OK;
 }
 
+// The engines with work, longest predicted job first (the launch order of a step and the
+// priority order of its streams).  The first is the step's critical path: holding a single
+// solve, it runs in latency mode (Engine::latency); the others do not.
+static std::vector<int> rank_engines(helm_batch* b)
+{
+    std::vector<std::pair<double, int>> order;
+    for (auto& kv : b->engines)
+        if (kv.second->active_count() > 0) order.push_back({kv.second->longest_job(), kv.first});
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first > y.first; });
+    std::vector<int> keys;
+    for (size_t r = 0; r < order.size(); ++r) {
+        Engine* E = b->engines[order[r].second].get();
+        E->latency = r == 0 && E->active_count() == 1;
+        keys.push_back(order[r].second);
+    }
+    return keys;
+}
+
 helm_status helm_batch_step(helm_batch* b, int max_steps)
 {
     if (!b || max_steps < 0) return HELM_EINVAL;
     // launch every engine with work on its own stream, forked from the batch stream; the
     // engine with the longest predicted job on the highest-priority stream
     HELM_CK(cudaEventRecord(b->fork, b->stream));
-    std::vector<std::pair<double, int>> order;
-    for (auto& kv : b->engines)
-        if (kv.second->active_count() > 0) order.push_back({kv.second->longest_job(), kv.first});
-    std::stable_sort(order.begin(), order.end(),
-                     [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first > y.first; });
+    const std::vector<int> order = rank_engines(b);
     std::vector<int> launched;
     for (size_t r = 0; r < order.size(); ++r) {
-        const int key = order[r].second;
+        const int key = order[r];
         Engine* E = b->engines[key].get();
         cudaStream_t es;
         cudaEvent_t ej;
@@ -1965,9 +1987,8 @@ helm_status helm_batch_profile(helm_batch* b, int max_steps, uint64_t* launches,
         ms[k] = 0.0;
         bytes[k] = 0.0;
     }
-    for (auto& kv : b->engines) {
-        Engine* E = kv.second.get();
-        if (E->active_count() == 0) continue;
+    for (const int key : rank_engines(b)) {
+        Engine* E = b->engines[key].get();
         helm_status st = E->start_pending(b->stream);
         if (st != HELM_OK) return st;
         st = E->prepare_plan();
