@@ -73,9 +73,12 @@ FP64_PEAK_TFLOPS = 1.25          # GB300 nominal FP64 rate (FMA = 2 flops)
 # capture (the bench's top kernel is the fused one)
 RESIDUAL_DRAM_BYTES_PER_POINT = None
 # the finest level's ascent fused with the residual (fixed-point numerator, loops flattened
-# over the CTA's threads): one ncu capture of the single-solve replay's launch (44.17 MB
-# read + 1.16 MB written)
-UPRES_DRAM_BYTES_PER_POINT = (44.171776e6 + 1.163264e6) / (1023 ** 2)
+# over the CTA's threads): one ncu capture of the paired replay's launch (two instances,
+# 73.21 MB read + 17.23 MB written)
+UPRES_DRAM_BYTES_PER_POINT = (73.205760e6 + 17.231104e6) / (2 * 1023 ** 2)
+# the same kernel forming level 1's ascent too (the latency lane's form): one capture of
+# the single-solve replay's launch (44.67 MB read + 1.02 MB written)
+UPRES_L1_DRAM_BYTES_PER_POINT = (44.667904e6 + 1.023488e6) / (1023 ** 2)
 
 
 def _peaks():
@@ -642,8 +645,10 @@ def main():
     # ---- per-kernel replay of one step (events around every launch) ----
     for u in U:
         u.zero_()
+    # submitted as the timed step submits them (longest first), so the lanes hold the same
+    # solves and run the same forms of their steps
     tickets = [B.helm_batch_submit(batch, mixed_plans[i], F[i], G[i], U[i], TOL, MAX_OUTER)
-               for i in range(len(KS))]
+               for i in sorted(range(len(KS)), key=lambda j: -KS[j])]
     prof = B.helm_batch_profile(batch, 0)
     for t in tickets:
         B.helm_batch_poll(batch, t, MAX_OUTER)
@@ -669,14 +674,22 @@ def main():
                 "share": m_s / total_kernel_ms, "bytes_per_launch": b_y / n_l if n_l else 0,
                 "avg_launch_us": 1e3 * m_s / n_l if n_l else 0}
 
-    if name in ("helmholtz_residual_update", "ascent_residual_update_2d"):
+    if name in ("helmholtz_residual_update", "ascent_residual_update_2d", "ascent_l1_residual_update_2d"):
         if name == "helmholtz_residual_update":
             pts = by / (48 + 2 * eb)
             per_pt = RESIDUAL_DRAM_BYTES_PER_POINT
         else:
-            # one launch per outer step; instance i takes part in iters_i of them
-            pts = float(n) ** 2 * sum(mixed_iters)
-            per_pt = UPRES_DRAM_BYTES_PER_POINT
+            # the instance-steps a kind's launches covered, from its algorithmic bytes (the
+            # library's model per 1023^2 instance-step: e2 (zero without pre-smoothing), r_N,
+            # u_N, f in and u', r out at level 0, level 1's e; with level 1 fused, level 1's
+            # rhs instead of its e plus level 2's e)
+            n1, n2 = (n - 1) // 2, (n - 3) // 4
+            per_is = n * n * ((1 if sched_mixed[0] == 0 else 2) * eb + 48 + eb) + n1 * n1 * eb
+            if name == "ascent_l1_residual_update_2d":
+                per_is += n2 * n2 * eb
+            pts = float(n) ** 2 * round(by / per_is)
+            per_pt = UPRES_L1_DRAM_BYTES_PER_POINT if name == "ascent_l1_residual_update_2d" \
+                else UPRES_DRAM_BYTES_PER_POINT
         flops = 16.0 * pts
         ach = (flops / nl) / ((ms / nl) / 1e3) / 1e12
         traffic = per_pt * pts / nl if per_pt else None
@@ -694,10 +707,12 @@ def main():
                     "share": ms / total_kernel_ms,
                     "flops_per_launch": flops / nl, "avg_launch_us": 1e3 * ms / nl,
                     "hbm_view": hv}
-        if name == "ascent_residual_update_2d":
+        if name in ("ascent_residual_update_2d", "ascent_l1_residual_update_2d"):
             # the unfused steps' bytes: residual + update (64 B/pt), prolongation +
-            # correction (2e + e/4 = 18 B/pt), one red-black sweep (3e = 24 B/pt)
-            b106 = 106.0 * pts / nl
+            # correction (2e + e/4 = 18 B/pt), one red-black sweep (3e = 24 B/pt); with
+            # level 1 fused, its prolongation, correction and sweep on a quarter of the
+            # points (10.5 B/pt)
+            b106 = (116.5 if name == "ascent_l1_residual_update_2d" else 106.0) * pts / nl
             a106 = b106 / ((ms / nl) / 1e3) / 1e9
             roofline["hbm_view_unfused_steps"] = {"bound": "hbm", "bytes_per_launch": b106,
                                                   "achieved": a106, "peak": peak, "unit": "GB/s",

@@ -394,9 +394,11 @@ HELM_API helm_status helm_batch_poll(helm_batch* batch, uint64_t ticket, int* do
  * 3 zeroing, 4 coarse-level tail, 5 Helmholtz residual + update + norm, 6 convergence
  * check, 7 fused 2D smoothing + residual + restriction, 8 fused 2D prolongation +
  * correction + smoothing, 9 the finest level's prolongation + correction + smoothing fused
- * with the Helmholtz residual + update + norm (2D complex64 batches of one size)):
- * launches[k], device milliseconds ms[k] and algorithmic bytes bytes[k] (each datum a
- * launch must read or write, counted once).  nkinds >= 10.
+ * with the Helmholtz residual + update + norm (2D complex64 batches of one size), 10 the
+ * cluster tail (levels 255 ... 31 of 2D complex64 cycles in one 8-CTA cluster per solve),
+ * 11 two descent steps (rhs restrictions) in one launch, 12 kind 9 with level 1's ascent
+ * formed inside it too): launches[k], device milliseconds ms[k] and algorithmic bytes
+ * bytes[k] (each datum a launch must read or write, counted once).  nkinds >= 13.
  */
 HELM_API helm_status helm_batch_profile(helm_batch* batch, int max_steps, uint64_t* launches,
                                         double* ms, double* bytes, int nkinds);

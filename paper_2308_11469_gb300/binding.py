@@ -106,7 +106,7 @@ _SIGS = {
 KERNEL_KINDS = ["rbgs_half_sweep", "residual_restrict", "prolong_correct", "zero",
                 "coarse_tail", "helmholtz_residual_update", "convergence_check",
                 "smooth_restrict_2d", "prolong_smooth_2d", "ascent_residual_update_2d",
-                "cluster_tail", "restrict_two_levels_2d"]
+                "cluster_tail", "restrict_two_levels_2d", "ascent_l1_residual_update_2d"]
 
 _lib = None
 

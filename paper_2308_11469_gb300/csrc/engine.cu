@@ -145,7 +145,9 @@ struct Instance {
 };
 
 struct LaunchRec {
-    enum Kind { RBGS, RESTRICT, PROLONG, ZERO, TAIL, RESID, CHECK, DOWN, UP, UPRES, CTAIL, DOWN2, NKINDS } kind;
+    // UPRES1 names, in helm_batch_profile only, an UPRES launch that also forms level 1's
+    // ascent (color 1); steps hold it as UPRES
+    enum Kind { RBGS, RESTRICT, PROLONG, ZERO, TAIL, RESID, CHECK, DOWN, UP, UPRES, CTAIL, DOWN2, UPRES1, NKINDS } kind;
     int off, cnt, work, color, mode;
     double bytes;   // algorithmic bytes of one launch (each datum it must touch, once)
     int nmax = 0;   // DOWN: the largest level of the launch; UPRES: the level-0 size
@@ -2021,7 +2023,8 @@ helm_status helm_batch_profile(helm_batch* b, int max_steps, uint64_t* launches,
             for (size_t i = 0; i < nl; ++i) {
                 float t = 0.f;
                 HELM_CK(cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]));
-                const int k = (int)E->step[i].kind;
+                int k = (int)E->step[i].kind;
+                if (k == LaunchRec::UPRES && E->step[i].color) k = LaunchRec::UPRES1;
                 launches[k] += 1;
                 ms[k] += t;
                 bytes[k] += lb[i];

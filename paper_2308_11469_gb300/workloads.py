@@ -1,7 +1,7 @@
 """Timings of the method's other workloads on one GPU (one JSON line each).
 
     python -m paper_2308_11469_gb300.workloads [--only cavity63,cube255,batch512,damped1023,exit1023,spectral1023,annulus1024,annulus_spectrum]
-    python -m paper_2308_11469_gb300.workloads --replay cube255|cavity1023 [--steps 4] [--fp64]
+    python -m paper_2308_11469_gb300.workloads --replay cube255|cavity1023 [--steps 4] [--fp64] [--pair]
 
 * cavity63  63x63 unit-square cavity, plane-wave wall data (theta = pi/6), f = 0:
             k = 2 to relres 1e-10 and k = 5 (above k_max: the iteration diverges), mixed
@@ -147,10 +147,13 @@ def batch512(dev):
     return rows
 
 
-def replay(dev, which: str, steps: int, prec: int = B.HELM_PREC_MIXED):
+def replay(dev, which: str, steps: int, prec: int = B.HELM_PREC_MIXED, pair: bool = False):
     """Per-kernel device time of `steps` outer steps of one solve, every launch made
     directly between CUDA events (so a profiler sees each kernel; the graph's
-    conditional loop hides them): the 255^3 cube or the 1023^2 Gaussian cavity (k = 4)."""
+    conditional loop hides them): the 255^3 cube or the 1023^2 Gaussian cavity (k = 4).
+    A solve alone is a critical path and runs the latency form of its step; `pair` submits
+    two copies of it to one engine, whose launches then each cover both instances in the
+    throughput form (2D: level 1's ascent in its own launch)."""
     import torch
     p = (inputs.plane_wave_sine_cube(4.0, seed=3, n=255) if which == "cube255"
          else inputs.gaussian_cavity_2d(4.0))
@@ -161,15 +164,19 @@ def replay(dev, which: str, steps: int, prec: int = B.HELM_PREC_MIXED):
     sched = B.helm_plan_autotune(plan, f, g, u, 1e-8, 2000)[:3]
     batch = B.helm_batch_create(0)
     B.helm_batch_set_cycle(batch, *sched)
-    u.zero_()
-    B.helm_batch_submit(batch, plan, f, g, u, 1e-8, 2000)
+    B.helm_batch_set_lanes(batch, 1)
+    us = [u] + ([torch.zeros_like(g)] if pair else [])
+    for x in us:
+        x.zero_()
+        B.helm_batch_submit(batch, plan, f, g, x, 1e-8, 2000)
     prof = B.helm_batch_profile(batch, steps)
     B.helm_batch_destroy(batch)
     B.helm_plan_destroy(plan)
     rows = []
     for kind, (nl, ms, by) in prof.items():
         if nl:
-            rows.append({"workload": f"replay_{which}", "prec": "mixed" if prec else "fp64",
+            rows.append({"workload": f"replay_{which}" + ("_pair" if pair else ""),
+                         "prec": "mixed" if prec else "fp64",
                          "schedule": dict(zip(("nu1", "nu2", "cycles"), sched)), "kernel": kind,
                          "launches": nl, "us_per_launch": 1e3 * ms / nl,
                          "model_GBs": by / (ms / 1e3) / 1e9})
@@ -334,13 +341,15 @@ def main(argv=None) -> int:
                     help="per-kernel replay of a few outer steps of one solve instead")
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--fp64", action="store_true", help="replay the plain FP64 form")
+    ap.add_argument("--pair", action="store_true",
+                    help="replay two copies of the solve in one engine (the throughput form)")
     args = ap.parse_args(argv)
     build.build()
     B.load()
     dev = torch.device("cuda", torch.cuda.current_device())
     if args.replay:
         for row in replay(dev, args.replay, args.steps,
-                          B.HELM_PREC_FP64 if args.fp64 else B.HELM_PREC_MIXED):
+                          B.HELM_PREC_FP64 if args.fp64 else B.HELM_PREC_MIXED, args.pair):
             print(json.dumps(row), flush=True)
         return 0
     for name in args.only.split(","):
