@@ -821,7 +821,9 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
 constexpr int T3X = 32, T3Y = 8, T3Z = 16;
 // resident CTAs per SM of the 3D residual (40 registers at 6): at 255^3 477 -> 396 us per
 // launch against 4 CTAs of 64 registers; fetching each plane one plane ahead into
-// registers measured slower (412 / 432 / 485 us at 4 / 5 / 6 CTAs)
+// registers measured slower (412 / 432 / 485 us at 4 / 5 / 6 CTAs), and so did a two-deep
+// cp.async ring of the next planes' words in shared memory (425 against 385 us: 5 CTAs
+// per SM, and the copies' issue cost on a kernel bound by its integer work)
 constexpr int RES3D_CTAS = 6;
 constexpr int P3 = (T3X + 2) * (T3Y + 2);
 
