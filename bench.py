@@ -674,52 +674,62 @@ def main():
                 "share": m_s / total_kernel_ms, "bytes_per_launch": b_y / n_l if n_l else 0,
                 "avg_launch_us": 1e3 * m_s / n_l if n_l else 0}
 
-    if name in ("helmholtz_residual_update", "ascent_residual_update_2d", "ascent_l1_residual_update_2d"):
-        if name == "helmholtz_residual_update":
-            pts = by / (48 + 2 * eb)
-            per_pt = RESIDUAL_DRAM_BYTES_PER_POINT
+    fused = ("helmholtz_residual_update", "ascent_residual_update_2d", "ascent_l1_residual_update_2d")
+
+    def roofline_of(name, nl, ms, by):
+        if name in fused:
+            if name == "helmholtz_residual_update":
+                pts = by / (48 + 2 * eb)
+                per_pt = RESIDUAL_DRAM_BYTES_PER_POINT
+            else:
+                # the instance-steps a kind's launches covered, from its algorithmic bytes (the
+                # library's model per 1023^2 instance-step: e2 (zero without pre-smoothing), r_N,
+                # u_N, f in and u', r out at level 0, level 1's e; with level 1 fused, level 1's
+                # rhs instead of its e plus level 2's e)
+                n1, n2 = (n - 1) // 2, (n - 3) // 4
+                per_is = n * n * ((1 if sched_mixed[0] == 0 else 2) * eb + 48 + eb) + n1 * n1 * eb
+                if name == "ascent_l1_residual_update_2d":
+                    per_is += n2 * n2 * eb
+                pts = float(n) ** 2 * round(by / per_is)
+                per_pt = UPRES_L1_DRAM_BYTES_PER_POINT if name == "ascent_l1_residual_update_2d" \
+                    else UPRES_DRAM_BYTES_PER_POINT
+            flops = 16.0 * pts
+            ach = (flops / nl) / ((ms / nl) / 1e3) / 1e12
+            traffic = per_pt * pts / nl if per_pt else None
+            hv = hbm_line(name, (nl, ms, by))
+            hv["traffic"] = traffic
+            hv["bytes_note"] = "fused minimum: every array the fused kernel must read or write, once"
+            roofline = {"bound": "alu", "kernel": name, "achieved": ach, "peak": fp64_tflops,
+                        "unit": "TFLOP/s", "frac": ach / fp64_tflops,
+                        "peak_kind": "measured FP64 FMA rate of this device (helm_measure_fp64_rate: "
+                                     f"8 FMA chains per thread on every SM, best launch {fp64_probe_ms:.3f} ms); "
+                                     f"nominal {FP64_PEAK_TFLOPS} TFLOP/s",
+                        "traffic": traffic,
+                        "traffic_source": "ncu DRAM bytes per point of one launch x the average "
+                                          "launch's points",
+                        "share": ms / total_kernel_ms,
+                        "flops_per_launch": flops / nl, "avg_launch_us": 1e3 * ms / nl,
+                        "hbm_view": hv}
+            if name in ("ascent_residual_update_2d", "ascent_l1_residual_update_2d"):
+                # the unfused steps' bytes: residual + update (64 B/pt), prolongation +
+                # correction (2e + e/4 = 18 B/pt), one red-black sweep (3e = 24 B/pt); with
+                # level 1 fused, its prolongation, correction and sweep on a quarter of the
+                # points (10.5 B/pt)
+                b106 = (116.5 if name == "ascent_l1_residual_update_2d" else 106.0) * pts / nl
+                a106 = b106 / ((ms / nl) / 1e3) / 1e9
+                roofline["hbm_view_unfused_steps"] = {"bound": "hbm", "bytes_per_launch": b106,
+                                                      "achieved": a106, "peak": peak, "unit": "GB/s",
+                                                      "frac": a106 / peak,
+                                                      "peak_kind": f"{peak_kind} hbm_gbs (burst)"}
         else:
-            # the instance-steps a kind's launches covered, from its algorithmic bytes (the
-            # library's model per 1023^2 instance-step: e2 (zero without pre-smoothing), r_N,
-            # u_N, f in and u', r out at level 0, level 1's e; with level 1 fused, level 1's
-            # rhs instead of its e plus level 2's e)
-            n1, n2 = (n - 1) // 2, (n - 3) // 4
-            per_is = n * n * ((1 if sched_mixed[0] == 0 else 2) * eb + 48 + eb) + n1 * n1 * eb
-            if name == "ascent_l1_residual_update_2d":
-                per_is += n2 * n2 * eb
-            pts = float(n) ** 2 * round(by / per_is)
-            per_pt = UPRES_L1_DRAM_BYTES_PER_POINT if name == "ascent_l1_residual_update_2d" \
-                else UPRES_DRAM_BYTES_PER_POINT
-        flops = 16.0 * pts
-        ach = (flops / nl) / ((ms / nl) / 1e3) / 1e12
-        traffic = per_pt * pts / nl if per_pt else None
-        hv = hbm_line(name, (nl, ms, by))
-        hv["traffic"] = traffic
-        hv["bytes_note"] = "fused minimum: every array the fused kernel must read or write, once"
-        roofline = {"bound": "alu", "kernel": name, "achieved": ach, "peak": fp64_tflops,
-                    "unit": "TFLOP/s", "frac": ach / fp64_tflops,
-                    "peak_kind": "measured FP64 FMA rate of this device (helm_measure_fp64_rate: "
-                                 f"8 FMA chains per thread on every SM, best launch {fp64_probe_ms:.3f} ms); "
-                                 f"nominal {FP64_PEAK_TFLOPS} TFLOP/s",
-                    "traffic": traffic,
-                    "traffic_source": "ncu DRAM bytes per point of one launch x the average "
-                                      "launch's points",
-                    "share": ms / total_kernel_ms,
-                    "flops_per_launch": flops / nl, "avg_launch_us": 1e3 * ms / nl,
-                    "hbm_view": hv}
-        if name in ("ascent_residual_update_2d", "ascent_l1_residual_update_2d"):
-            # the unfused steps' bytes: residual + update (64 B/pt), prolongation +
-            # correction (2e + e/4 = 18 B/pt), one red-black sweep (3e = 24 B/pt); with
-            # level 1 fused, its prolongation, correction and sweep on a quarter of the
-            # points (10.5 B/pt)
-            b106 = (116.5 if name == "ascent_l1_residual_update_2d" else 106.0) * pts / nl
-            a106 = b106 / ((ms / nl) / 1e3) / 1e9
-            roofline["hbm_view_unfused_steps"] = {"bound": "hbm", "bytes_per_launch": b106,
-                                                  "achieved": a106, "peak": peak, "unit": "GB/s",
-                                                  "frac": a106 / peak,
-                                                  "peak_kind": f"{peak_kind} hbm_gbs (burst)"}
-    else:
-        roofline = hbm_line(name, (nl, ms, by))
+            roofline = hbm_line(name, (nl, ms, by))
+        return roofline
+
+    roofline = roofline_of(name, nl, ms, by)
+    # the other form of the fused finest kernel, where the step ran both (the latency form
+    # in the critical-path lane, the throughput form covering the other lane's solves)
+    other_fused = [k for k in fused[1:] if k != name and prof.get(k, (0,))[0]]
+    roofline_other = roofline_of(other_fused[0], *prof[other_fused[0]]) if other_fused else None
     mg = {k: v for k, v in prof.items() if k in ("smooth_restrict_2d", "prolong_smooth_2d") and v[0]}
     roofline_mg = None
     if mg:
@@ -753,7 +763,8 @@ def main():
         "fp64_single": fp64,
         "stencil_GBs": stencil_gbs, "stencil_frac_of_peak": stencil_gbs / peak,
         "model_bytes_per_step": model_bytes,
-        "roofline": roofline, "roofline_multigrid": roofline_mg, "kernels": kernels,
+        "roofline": roofline, "roofline_fused_other_form": roofline_other,
+        "roofline_multigrid": roofline_mg, "kernels": kernels,
         "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches_per_step * args.steps),
     }
 

@@ -363,3 +363,41 @@ def test_submit_many_equals_single_submissions(B):
     B.helm_batch_step(batch, 0)
     assert all(d == 1 for d, _, _ in B.helm_batch_poll_many(batch, ts))
     B.helm_batch_destroy(batch)
+
+
+def test_latency_lane_fuses_level_1_and_equals_solo(B):
+    # four 1023^2 cavities, k = 1..4, in two lanes, submitted longest first: the k = 4
+    # solve alone in the highest-priority lane runs the latency form of its step (level 1's
+    # ascent inside the fused finest kernel, one launch per outer step), the three shorter
+    # ones share the other lane in the throughput form; every result is that of the solve
+    # alone, bit for bit
+    ks = (4.0, 3.0, 2.0, 1.0)
+    probs = [inputs.gaussian_cavity_2d(k) for k in ks]
+    tol, max_outer = 1e-6, 400
+    batch = B.helm_batch_create(0)
+    B.helm_batch_set_cycle(batch, 0, 1, 1)
+    B.helm_batch_set_lanes(batch, 2)
+    # the batch reads f, g and u through their device pointers: the tensors stay alive
+    fs = [torch.from_numpy(p.f).to(DEV) for p in probs]
+    gs = [torch.from_numpy(p.g).to(DEV) for p in probs]
+    us = [torch.zeros_like(g) for g in gs]
+    plans, tickets = [], []
+    for i, p in enumerate(probs):
+        pl = B.helm_plan_create(2, p.n, p.h, p.k, prec=B.HELM_PREC_MIXED)
+        B.helm_plan_set_cycle(pl, 0, 1, 1)
+        plans.append(pl)
+        tickets.append(B.helm_batch_submit(batch, pl, fs[i], gs[i], us[i], tol, max_outer))
+    prof = B.helm_batch_profile(batch, 0)
+    res = [B.helm_batch_poll(batch, t, max_outer) for t in tickets]
+    B.helm_batch_destroy(batch)
+    iters = [r[1] for r in res]
+    assert all(r[0] == B.HELM_CONVERGED for r in res) and min(iters) > 0
+    assert prof["ascent_l1_residual_update_2d"][0] == iters[0]
+    assert prof["ascent_residual_update_2d"][0] == max(iters[1:])
+    for i, p in enumerate(probs):
+        u = torch.zeros_like(us[i])
+        st, it, hist = B.helm_solve(plans[i], fs[i], gs[i], u, tol, max_outer)
+        assert st == B.HELM_CONVERGED and it == iters[i] and np.array_equal(hist, res[i][2])
+        assert np.array_equal(u.cpu().numpy(), us[i].cpu().numpy())
+    for pl in plans:
+        B.helm_plan_destroy(pl)
