@@ -1313,8 +1313,6 @@ cudaError_t run_fp64_rate(double* tflops, double* ms_best)
     return cudaSuccess;
 }
 
-static int g_res_grid = 152 * 5;               // SMs x resident residual CTAs (set up below)
-
 cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* st,
                             const ResItem* items, int nitems, int mode, cudaStream_t s,
                             int* ctrl, int nscan, int ninst, int use_cond,
@@ -1327,7 +1325,6 @@ cudaError_t launch_residual(int D, int prec, const InstDesc* insts, InstState* s
     // persistent CTAs double-buffer their next tile with asynchronous copies (1023^2, one
     // instance: 43 us against 48-49 us); 32 x 32 tiles beat 32 x 8/16/40/64 rows
     const int grid = nitems;
-    (void)g_res_grid;
 #define HELM_RES(K, RR)                                                                        \
     (damp ? (mode ? launch_k(K<RR, 1, true>, dim3(grid), dim3(NTH), 0, s, insts, st, items, nitems, c)  \
                   : launch_k(K<RR, 0, true>, dim3(grid), dim3(NTH), 0, s, insts, st, items, nitems, c)) \
@@ -1401,12 +1398,6 @@ cudaError_t setup_upres()
 cudaError_t setup_outer()
 {
     cudaError_t e;
-    int dev = 0, sms = 0, per = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_residual2d<float, 1, false>, NTH, 0)) != cudaSuccess)
-        return e;
-    if (sms > 0 && per > 0) g_res_grid = sms * per;
 #define HELM_CO(K)                                                                   \
     if ((e = max_carveout(K<float, 0, false>)) != cudaSuccess) return e;             \
     if ((e = max_carveout(K<float, 1, false>)) != cudaSuccess) return e;             \
