@@ -854,8 +854,11 @@ struct Engine {
 
 // One allocation per instance: the workspace (levels, u[1], partials), then its residual
 // tile list, then the relres / increment histories.
+// With `init`, the workspace's zeroing and tile list are left to the caller's batched
+// set-up (launch_init_workspaces), described in *init; else done here on `s`.
 helm_status alloc_instance(Instance& in, int D, int n, double h, double k, int prec,
-                           int max_outer, cudaStream_t s, bool stream_ordered, size_t io_bytes = 0)
+                           int max_outer, cudaStream_t s, bool stream_ordered, size_t io_bytes = 0,
+                           WsInit* init = nullptr)
 {
     in.prec = prec;
     in.stream_ordered = stream_ordered;
@@ -877,12 +880,17 @@ helm_status alloc_instance(Instance& in, int D, int n, double h, double k, int p
         }
     }
     layout(in.d, D, n, h, k, prec, in.ws);
-    // rings of the level iterates must be zero; clear everything once
-    HELM_CK(cudaMemsetAsync(in.ws, 0, in.ws_bytes, s));
-    // residual tiles of this instance (for its initial residual), listed on the device
+    // rings of the level iterates must be zero (everything is cleared once), and the
+    // residual tiles of this instance (for its initial residual) are listed on the device
     in.d_res0 = (ResItem*)(in.ws + align256(in.ws_bytes));
-    HELM_CK(launch_fill_res_items(in.d_res0, in.d.res_tx, in.d.res_ty, tz, s));
-    g_launches += 1;
+    if (init) {
+        *init = WsInit{(unsigned char*)in.ws, (unsigned long long)in.ws_bytes, in.d_res0, in.d.res_tx, in.d.res_ty,
+                       tz, 0};
+    } else {
+        HELM_CK(cudaMemsetAsync(in.ws, 0, in.ws_bytes, s));
+        HELM_CK(launch_fill_res_items(in.d_res0, in.d.res_tx, in.d.res_ty, tz, s));
+        g_launches += 1;
+    }
     in.hist = (double*)((char*)in.d_res0 + rb);
     in.d.hist = in.hist;
     in.d.einf = in.hist + max_outer + 1;
@@ -990,6 +998,13 @@ struct helm_batch {
     // synchronisation for all of them)
     double* h_hist = nullptr;
     size_t h_hist_cap = 0;
+    // workspaces of the solves submitted since the batch last ran: zeroed, and their tile
+    // lists written, by one launch before its next step (records staged page-locked, then
+    // copied to the device)
+    std::vector<WsInit> init_pending;
+    WsInit* h_init = nullptr;
+    WsInit* d_init = nullptr;
+    size_t init_cap = 0;
 };
 
 namespace helm {
@@ -1528,6 +1543,8 @@ helm_status helm_batch_destroy(helm_batch* b)
     if (b->up_fork) cudaEventDestroy(b->up_fork);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->h_hist) cudaFreeHost(b->h_hist);
+    if (b->h_init) cudaFreeHost(b->h_init);
+    if (b->d_init) cudaFree(b->d_init);
     delete b;
     return HELM_OK;
 }
@@ -1624,8 +1641,10 @@ static helm_status submit_impl(helm_batch* b, int D, int n, double h, double k, 
         if (st != HELM_OK) return st;
     }
     Instance* in = new Instance();
-    helm_status st = alloc_instance(*in, D, n, h, k, prec, max_outer, b->stream, true, io_bytes);
+    WsInit wi{};
+    helm_status st = alloc_instance(*in, D, n, h, k, prec, max_outer, b->stream, true, io_bytes, &wi);
     if (st != HELM_OK) { free_instance(*in, b->stream); delete in; return st; }
+    b->init_pending.push_back(wi);
     void* ud = u;
     const void* fd = f;
     const void* gd = g;
@@ -1887,6 +1906,31 @@ static helm_status rank_stream(helm_batch* b, int r, cudaStream_t* s, cudaEvent_
     return HELM_OK;
 }
 
+// The workspace set-up of the solves submitted since the batch last ran, in one launch on
+// the batch stream (the lanes fork from it after this).  The staging buffer is reused only
+// after the previous step's closing synchronisation.
+static helm_status flush_init(helm_batch* b)
+{
+    const size_t n = b->init_pending.size();
+    if (n == 0) return HELM_OK;
+    if (n > b->init_cap) {
+        if (b->h_init) cudaFreeHost(b->h_init);
+        if (b->d_init) cudaFree(b->d_init);
+        b->h_init = nullptr;
+        b->d_init = nullptr;
+        b->init_cap = 0;
+        HELM_CK(cudaMallocHost(&b->h_init, n * sizeof(WsInit)));
+        HELM_CK(cudaMalloc(&b->d_init, n * sizeof(WsInit)));
+        b->init_cap = n;
+    }
+    memcpy(b->h_init, b->init_pending.data(), n * sizeof(WsInit));
+    HELM_CK(cudaMemcpyAsync(b->d_init, b->h_init, n * sizeof(WsInit), cudaMemcpyHostToDevice, b->stream));
+    HELM_CK(launch_init_workspaces(b->d_init, (int)n, b->stream));
+    g_launches += (n + 65534) / 65535;
+    b->init_pending.clear();
+    return HELM_OK;
+}
+
 // The engines with work, longest predicted job first (the launch order of a step and the
 // priority order of its streams).  The first is the step's critical path: holding a single
 // solve, it runs in latency mode (Engine::latency); the others do not.
@@ -1909,6 +1953,10 @@ static std::vector<int> rank_engines(helm_batch* b)
 helm_status helm_batch_step(helm_batch* b, int max_steps)
 {
     if (!b || max_steps < 0) return HELM_EINVAL;
+    {
+        const helm_status st = flush_init(b);
+        if (st != HELM_OK) return st;
+    }
     // launch every engine with work on its own stream, forked from the batch stream; the
     // engine with the longest predicted job on the highest-priority stream
     HELM_CK(cudaEventRecord(b->fork, b->stream));
@@ -1988,6 +2036,10 @@ helm_status helm_batch_profile(helm_batch* b, int max_steps, uint64_t* launches,
         launches[k] = 0;
         ms[k] = 0.0;
         bytes[k] = 0.0;
+    }
+    {
+        const helm_status st = flush_init(b);
+        if (st != HELM_OK) return st;
     }
     for (const int key : rank_engines(b)) {
         Engine* E = b->engines[key].get();

@@ -142,6 +142,16 @@ cudaError_t run_fp64_rate(double* tflops, double* ms_best);
 // the residual tile list of one instance: item q = (instance 0, q mod tx, (q / tx) mod ty,
 // q / (tx ty)), the order the host loops would give (x fastest)
 cudaError_t launch_fill_res_items(ResItem* items, int tx, int ty, int tz, cudaStream_t s);
+// A new instance's workspace set-up: ws[0, bytes) zeroed (ws 16-byte aligned) and its
+// residual tile list (tx x ty x tz tiles, instance 0) written at items.  One launch sets up
+// `count` instances from a device array of these records.
+struct WsInit {
+    unsigned char* ws;
+    unsigned long long bytes;
+    ResItem* items;
+    int tx, ty, tz, pad;
+};
+cudaError_t launch_init_workspaces(const WsInit* recs, int count, cudaStream_t s);
 // u[0] and u[1] rings := g ring
 cudaError_t launch_set_ring(int D, const InstDesc* insts, int inst, int n, cudaStream_t s);
 // interior tight <-> level-0 padded/pitched, inner precision

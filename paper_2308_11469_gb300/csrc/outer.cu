@@ -1269,7 +1269,36 @@ __global__ void k_fill_res_items(ResItem* __restrict__ items, int tx, int ty, in
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x)
         items[q] = ResItem{0, q % tx, (q / tx) % ty, q / (tx * ty)};
 }
+
+// blockIdx.y = record; the record's blocks stride over its 16-byte words (then the bytes
+// of a ragged end) and its tile list
+__global__ void __launch_bounds__(256) k_init_ws(const WsInit* __restrict__ recs)
+{
+    const WsInit r = recs[blockIdx.y];
+    const unsigned long long n16 = r.bytes >> 4;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long t0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    uint4* w = reinterpret_cast<uint4*>(r.ws);
+    for (unsigned long long q = t0; q < n16; q += stride) w[q] = make_uint4(0u, 0u, 0u, 0u);
+    for (unsigned long long q = (n16 << 4) + t0; q < r.bytes; q += stride) r.ws[q] = 0;
+    const unsigned long long total = (unsigned long long)r.tx * r.ty * r.tz;
+    for (unsigned long long q = t0; q < total; q += stride) {
+        const int qi = (int)q;
+        r.items[qi] = ResItem{0, qi % r.tx, (qi / r.tx) % r.ty, qi / (r.tx * r.ty)};
+    }
+}
 }  // namespace
+
+cudaError_t launch_init_workspaces(const WsInit* recs, int count, cudaStream_t s)
+{
+    for (int off = 0; off < count; off += 65535) {
+        const int m = count - off < 65535 ? count - off : 65535;
+        k_init_ws<<<dim3(128, m), 256, 0, s>>>(recs + off);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 cudaError_t launch_fill_res_items(ResItem* items, int tx, int ty, int tz, cudaStream_t s)
 {
