@@ -214,6 +214,13 @@ struct Engine {
     // instance retired, behind a stream synchronisation)
     InstDesc* h_desc_stage = nullptr;
     InstState* h_state_stage = nullptr;
+    // the starts of the solves submitted since the last step, one launch of each kind for
+    // all of them: their slots (page-locked staging, device copy) and residual tiles
+    int* h_start_slots = nullptr;
+    int* d_start_slots = nullptr;
+    size_t start_cap = 0;
+    ResItem* d_start_items = nullptr;
+    size_t start_items_cap = 0;
     MgItem* d_mg = nullptr;
     size_t mg_cap = 0;
     ResItem* d_res = nullptr;
@@ -272,12 +279,17 @@ struct Engine {
         if (h_state) cudaFreeHost(h_state);
         if (h_desc_stage) cudaFreeHost(h_desc_stage);
         if (h_state_stage) cudaFreeHost(h_state_stage);
+        if (h_start_slots) cudaFreeHost(h_start_slots);
+        if (d_start_slots) cudaFree(d_start_slots);
+        if (d_start_items) cudaFree(d_start_items);
         if (d_mg) cudaFree(d_mg);
         if (d_res) cudaFree(d_res);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         d_desc = nullptr; d_state = nullptr; d_ctrl = nullptr; h_ctrl = nullptr;
         h_state = nullptr; d_mg = nullptr; d_res = nullptr; cap_stream = nullptr;
         h_desc_stage = nullptr; h_state_stage = nullptr;
+        h_start_slots = nullptr; d_start_slots = nullptr; d_start_items = nullptr;
+        start_cap = 0; start_items_cap = 0;
     }
 
     helm_status init(int D_, int prec_)
@@ -803,12 +815,79 @@ struct Engine {
     std::vector<int> pending;
     helm_status start_pending(cudaStream_t s)
     {
+        std::vector<int> ps;
         for (int slot : pending)
-            if (slot < cap && slots[slot]) {
+            if (slot < cap && slots[slot]) ps.push_back(slot);
+        pending.clear();
+        std::sort(ps.begin(), ps.end());
+        ps.erase(std::unique(ps.begin(), ps.end()), ps.end());
+        bool one_size = true;
+        for (int slot : ps) one_size = one_size && slots[slot]->d.n == slots[ps[0]]->d.n;
+        if (ps.size() <= 1 || !one_size) {
+            for (int slot : ps) {
                 const helm_status st = start_instance(slot, s);
                 if (st != HELM_OK) return st;
             }
-        pending.clear();
+            return HELM_OK;
+        }
+        // their uploads from host memory; descriptors and initial states, one copy per run
+        // of consecutive slots
+        for (int slot : ps)
+            if (slots[slot]->ready) HELM_CK(cudaStreamWaitEvent(s, slots[slot]->ready, 0));
+        for (int slot : ps) {
+            InstState& init = h_state_stage[slot];
+            memset(&init, 0, sizeof init);
+            init.status = HELM_ST_ACTIVE;
+            h_desc_stage[slot] = slots[slot]->d;
+        }
+        for (size_t i = 0; i < ps.size();) {
+            size_t j = i + 1;
+            while (j < ps.size() && ps[j] == ps[j - 1] + 1) ++j;
+            const int a = ps[i], c = (int)(j - i);
+            HELM_CK(cudaMemcpyAsync(d_desc + a, h_desc_stage + a, c * sizeof(InstDesc), cudaMemcpyHostToDevice, s));
+            HELM_CK(cudaMemcpyAsync(d_state + a, h_state_stage + a, c * sizeof(InstState), cudaMemcpyHostToDevice,
+                                    s));
+            i = j;
+        }
+        // the slots, those without a damping term first (it selects the residual kernel's
+        // variant, as for a single start)
+        const int m = (int)ps.size();
+        if ((size_t)m > start_cap) {
+            if (h_start_slots) cudaFreeHost(h_start_slots);
+            if (d_start_slots) cudaFree(d_start_slots);
+            h_start_slots = nullptr;
+            d_start_slots = nullptr;
+            start_cap = 0;
+            HELM_CK(cudaMallocHost(&h_start_slots, m * sizeof(int)));
+            HELM_CK(cudaMalloc(&d_start_slots, m * sizeof(int)));
+            start_cap = m;
+        }
+        int m0 = 0;
+        for (int slot : ps)
+            if (slots[slot]->d.damp == 0.0) h_start_slots[m0++] = slot;
+        int q = m0;
+        for (int slot : ps)
+            if (slots[slot]->d.damp != 0.0) h_start_slots[q++] = slot;
+        HELM_CK(cudaMemcpyAsync(d_start_slots, h_start_slots, m * sizeof(int), cudaMemcpyHostToDevice, s));
+        const InstDesc& d0 = slots[ps[0]]->d;
+        HELM_CK(launch_set_ring_many(D, d_desc, d_start_slots, m, d0.n, s));
+        const int tx = d0.res_tx, ty = d0.res_ty, tz = res_tz(D, d0.n), T = tx * ty * tz;
+        if ((size_t)m * T > start_items_cap) {
+            if (d_start_items) cudaFree(d_start_items);
+            d_start_items = nullptr;
+            start_items_cap = 0;
+            HELM_CK(cudaMalloc(&d_start_items, (size_t)m * T * sizeof(ResItem)));
+            start_items_cap = (size_t)m * T;
+        }
+        HELM_CK(launch_fill_res_many(d_start_items, d_start_slots, m, tx, ty, tz, s));
+        // the initial residuals; the last tile of each instance records its relres_0 and
+        // initial status
+        if (m0 > 0)
+            HELM_CK(launch_residual(D, prec, d_desc, d_state, d_start_items, m0 * T, 0, s, nullptr, 0, 0, 0, 0, 0));
+        if (m > m0)
+            HELM_CK(launch_residual(D, prec, d_desc, d_state, d_start_items + (size_t)m0 * T, (m - m0) * T, 0, s,
+                                    nullptr, 0, 0, 0, 0, 1));
+        g_launches += 2 + (m0 > 0 ? 1 : 0) + (m > m0 ? 1 : 0);
         return HELM_OK;
     }
 

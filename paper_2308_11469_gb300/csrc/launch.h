@@ -154,6 +154,10 @@ struct WsInit {
 cudaError_t launch_init_workspaces(const WsInit* recs, int count, cudaStream_t s);
 // u[0] and u[1] rings := g ring
 cudaError_t launch_set_ring(int D, const InstDesc* insts, int inst, int n, cudaStream_t s);
+// the same for the m instances insts[slots[j]] (device list), all of size n
+cudaError_t launch_set_ring_many(int D, const InstDesc* insts, const int* slots, int m, int n, cudaStream_t s);
+// the residual tiles (tx x ty x tz each) of instances slots[0 .. m) into items, in order
+cudaError_t launch_fill_res_many(ResItem* items, const int* slots, int m, int tx, int ty, int tz, cudaStream_t s);
 // interior tight <-> level-0 padded/pitched, inner precision
 cudaError_t launch_pack(int D, int prec, const InstDesc* insts, int inst, int n,
                         const void* src, int which /*0 = e, 1 = rhs*/, cudaStream_t s);

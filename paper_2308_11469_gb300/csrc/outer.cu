@@ -1016,6 +1016,42 @@ __global__ void k_set_ring(const InstDesc* __restrict__ insts, int inst)
     }
 }
 
+// k_set_ring for several instances of one size: instance slots[blockIdx.y]
+template <int D>
+__global__ void k_set_ring_many(const InstDesc* __restrict__ insts, const int* __restrict__ slots)
+{
+    pdl_wait();
+    pdl_trigger();
+    const InstDesc& I = insts[slots[blockIdx.y]];
+    const int n = I.n, S = n + 2;
+    const long total = (D == 3) ? (long)S * S * S : (long)S * S;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
+         q += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(q % S);
+        const int y = (int)((q / S) % S);
+        const int z = (D == 3) ? (int)(q / ((long)S * S)) : 1;
+        const bool ring = x == 0 || x == S - 1 || y == 0 || y == S - 1 ||
+                          (D == 3 && (z == 0 || z == S - 1));
+        if (ring) {
+            const double2 v = I.g[q];
+            I.u[0][q] = v;
+            I.u[1][q] = v;
+        }
+    }
+}
+
+// the residual tiles of instances slots[0 .. m): T = tx * ty * tz tiles each, in order
+__global__ void k_fill_res_many(ResItem* __restrict__ items, const int* __restrict__ slots, int tx, int ty,
+                                int T, int total)
+{
+    pdl_wait();
+    pdl_trigger();
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        const int j = q / T, t = q - j * T;
+        items[q] = ResItem{slots[j], t % tx, (t / tx) % ty, t / (tx * ty)};
+    }
+}
+
 template <int D, typename R>
 __global__ void k_pack(const InstDesc* __restrict__ insts, int inst, const void* __restrict__ src,
                        int which)
@@ -1501,6 +1537,29 @@ cudaError_t launch_set_ring(int D, const InstDesc* insts, int inst, int n, cudaS
     const long work = (D == 3) ? S * S * S : S * S;
     if (D == 2) launch_k(k_set_ring<2>, dim3(blocks_for(work)), dim3(256), 0, s, insts, inst);
     else launch_k(k_set_ring<3>, dim3(blocks_for(work)), dim3(256), 0, s, insts, inst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_ring_many(int D, const InstDesc* insts, const int* slots, int m, int n, cudaStream_t s)
+{
+    const long S = n + 2;
+    const long work = (D == 3) ? S * S * S : S * S;
+    for (int off = 0; off < m; off += 65535) {
+        const int c = m - off < 65535 ? m - off : 65535;
+        if (D == 2) launch_k(k_set_ring_many<2>, dim3(blocks_for(work), c), dim3(256), 0, s, insts, slots + off);
+        else launch_k(k_set_ring_many<3>, dim3(blocks_for(work), c), dim3(256), 0, s, insts, slots + off);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_fill_res_many(ResItem* items, const int* slots, int m, int tx, int ty, int tz, cudaStream_t s)
+{
+    const int T = tx * ty * tz, total = m * T;
+    if (total <= 0) return cudaSuccess;
+    const int blocks = (total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024;
+    launch_k(k_fill_res_many, dim3(blocks), dim3(256), 0, s, items, slots, tx, ty, T, total);
     return cudaGetLastError();
 }
 
