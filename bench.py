@@ -5,9 +5,11 @@ Dirichlet cavity (h = 1/1024, g = 0, f = 8 seeded Gaussians of width 0.02) to
 relres 1e-8.
 
 * headline (``value``): mixed precision -- complex64 multigrid V-cycles, complex128
-  residual and solution (iterative refinement) -- the four solves advanced together
-  as one batch (one launch per kernel covers all active instances, each solve retires
-  when it converges), a whole batch step being one CUDA-graph launch.
+  residual and solution (iterative refinement) -- the four solves advanced together as
+  one batch in two concurrent lanes: the k = 4 solve alone on the highest-priority
+  stream (the latency form of its step), the three shorter ones in the other lane (each
+  of its launches covers their active instances); each solve retires when it converges,
+  and each lane's run is one CUDA-graph launch.
 * ``fp64_single``: the plain FP64 form, each solve alone (complex128 everywhere).
 * ``e2e``: the headline measured through the C ABI's host entry point
   (``helm_batch_submit_host`` via ``serve.solve_host_batch``): pinned host -> device
