@@ -205,3 +205,28 @@ def test_batch_slot_reused_by_a_damped_solve(B):
     B.helm_batch_destroy(batch)
     B.helm_plan_destroy(plain)
     B.helm_plan_destroy(damped)
+
+
+def test_batch_starts_damped_and_undamped_together(B):
+    # solves of one size started together by one engine: those without a damping term and
+    # those with one take separate initial-residual launches (the kernel variant differs);
+    # every result is that of the solve alone, bit for bit
+    q = inputs.gaussian_cavity_2d(2.0, seed=2, n=127)
+    cases = [(q.k ** 2, 0.0), (q.k ** 2 + 6.0, 4.0), (q.k ** 2, 0.0), (q.k ** 2 + 3.0, 2.0)]
+    refs = [_solve(B, 2, q.n, q.h, q.k, q.f, q.g, 1, a, p, 1e-8, 2000) for a, p in cases]
+    batch = B.helm_batch_create(0)
+    B.helm_batch_set_lanes(batch, 1)
+    f, g = _t(q.f), _t(q.g)                      # alive until the batch has run
+    plans = [_plan(B, 2, q.n, q.h, q.k, 1, a, p) for a, p in cases]
+    us = [torch.zeros((q.n + 2,) * 2, dtype=torch.complex128, device=DEV) for _ in cases]
+    tickets = [B.helm_batch_submit(batch, pl, f, g, u, 1e-8, 2000) for pl, u in zip(plans, us)]
+    B.helm_batch_step(batch, 0)
+    for i, t in enumerate(tickets):
+        r = B.helm_batch_poll(batch, t, 2000)
+        st, iters, hist, _, u_ref = refs[i]
+        assert r[0] == st == B.HELM_CONVERGED and r[1] == iters
+        assert np.array_equal(r[2], hist)
+        assert np.array_equal(us[i].cpu().numpy(), u_ref)
+    B.helm_batch_destroy(batch)
+    for pl in plans:
+        B.helm_plan_destroy(pl)
