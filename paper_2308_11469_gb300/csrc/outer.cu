@@ -600,6 +600,9 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
             cp_async_elem<sizeof(c2)>(R1w + q, g1r + (in ? (size_t)Y * PC + X : 0), in);
             E1w[q] = cz<c2>();
         }
+        // level 1's words form the first group of copies: its ascent starts on them while
+        // level 0's window is still arriving
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
     } else {
         for (int q = threadIdx.x; q < CW * CH; q += NTU) {
             const int cy = q / CW, cx = q - cy * CW;
@@ -628,7 +631,12 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
         }
         cp_async_elem<sizeof(c2)>((c ? R1 : R0) + o, gr + g, in);
     }
-    cp_async_wait_all();
+    if constexpr (L1F) {
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+        cp_async_wait_all();
+    }
     __syncthreads();
     if constexpr (L1F) {
         // level 1's ascent on the window, as k_up2d forms it: e := 0 + the interpolation of
@@ -673,6 +681,8 @@ k_upres2d(const InstDesc* __restrict__ insts, InstState* __restrict__ st,
             }
             __syncthreads();
         }
+        cp_async_wait_all();                     // level 0's window
+        __syncthreads();
     }
     // level 1's final iterate on the coarse window (its own buffer, or the fused window's
     // centre)
