@@ -78,9 +78,10 @@ RESIDUAL_DRAM_BYTES_PER_POINT = None
 # over the CTA's threads): one ncu capture of the paired replay's launch (two instances,
 # 73.21 MB read + 17.23 MB written)
 UPRES_DRAM_BYTES_PER_POINT = (73.205760e6 + 17.231104e6) / (2 * 1023 ** 2)
-# the same kernel forming level 1's ascent too (the latency lane's form): one capture of
-# the single-solve replay's launch (44.67 MB read + 1.02 MB written)
-UPRES_L1_DRAM_BYTES_PER_POINT = (44.667904e6 + 1.023488e6) / (1023 ** 2)
+# the same kernel forming level 1's ascent too (the latency lane's form, level 1's words
+# as their own copy group): one capture of the single-solve replay's launch (44.66 MB read
+# + 1.07 MB written)
+UPRES_L1_DRAM_BYTES_PER_POINT = (44.662016e6 + 1.065728e6) / (1023 ** 2)
 
 
 def _peaks():
